@@ -1,0 +1,302 @@
+"""Plain FP64 CPU oracle of the GRPIC time step (arXiv:2503.04558, Sec. 2 and
+App. A-C), written in C (``grpic_oracle.c``) and wrapped here with ctypes.
+
+TEST INFRASTRUCTURE, NOT PRODUCT CODE: only ``tests/``, ``__graft_entry__.smoke()``
+and the cpu_baseline / reference leg of ``bench.py`` may import this package.
+It shares no code with the CUDA path and never imports it.
+
+Array conventions (an interface both sides implement independently):
+  field arrays are float64 of shape (nth+1, ld), row j = theta index,
+  column c = i + ng (ng = 2) where i is the r index of the component's own
+  lattice (integer or half-integer, Fig. Yee of the paper).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+import os
+import subprocess
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "grpic_oracle.c")
+_LIBDIR = os.path.join(_HERE, "_lib")
+_LIB = os.path.join(_LIBDIR, "liboracle.so")
+
+DEAD = np.uint32(0x80000000)
+NG = 2
+
+WALD, WALD_A0, MONOPOLE, SPLIT_MONOPOLE = 0, 1, 2, 3
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc -O2 -ffp-contract=off (no FMA contraction)."""
+    os.makedirs(_LIBDIR, exist_ok=True)
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-std=c11", "-shared", "-fPIC",
+                               "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+class Cfg(C.Structure):
+    _fields_ = [("nr", C.c_int), ("nth", C.c_int), ("ng", C.c_int), ("ld", C.c_int),
+                ("a", C.c_double), ("r_in", C.c_double), ("r_out", C.c_double),
+                ("dx1", C.c_double), ("dth", C.c_double),
+                ("dt", C.c_double), ("beta_s", C.c_double),
+                ("n_fld_iter", C.c_int), ("n_push_iter", C.c_int),
+                ("damp_cells", C.c_int), ("damp_max", C.c_double),
+                ("qm", C.c_double * 4), ("qw", C.c_double * 4), ("massive", C.c_int * 4)]
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = C.CDLL(build())
+        d, i, l, p = C.c_double, C.c_int, C.c_long, C.c_void_p
+        pc = C.POINTER(Cfg)
+        sig = {
+            "orc_metric_eval": (None, [d, d, d, p]),
+            "orc_closed_fields": (None, [i, d, d, d, d, p]),
+            "orc_gauss_legendre": (None, [p, p]),
+            "orc_areas": (None, [pc, p, p, p, p, p, p]),
+            "orc_init_fields": (None, [pc, i, d, p, p, p, p, p, p]),
+            "orc_field_update": (None, [pc, p, p, p, p, p, p, p, p, p]),
+            "orc_circulations": (None, [pc] + [p] * 12),
+            "orc_geodesic_rhs": (None, [d, d, p, p]),
+            "orc_boris": (None, [d, d, d, d, d, p, p, p]),
+            "orc_push_values": (None, [d, d, i, d, i, p, p, p]),
+            "orc_push_analytic": (i, [i, d, d, d, i, d, i, p, l, l, p]),
+            "orc_interp": (None, [pc, p, p, p, p, p, p, d, d, p]),
+            "orc_deposit_one": (None, [pc, p, p, p, d, d, d, d, d, d]),
+            "orc_push_deposit": (i, [pc, l, p, p, p, p, p, p, p, p, p, p, p, p, p, p, p, p]),
+            "orc_cell_keys": (None, [pc, l, p, p, p, p]),
+            "orc_counting_sort": (l, [l, l, p, p]),
+            "orc_rho": (None, [pc, l, p, p, p, p]),
+            "orc_divD": (None, [pc, p, p, p]),
+            "orc_divB": (None, [pc, p, p, p]),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(_lib, name)
+            fn.restype = res
+            fn.argtypes = args
+    return _lib
+
+
+def _p(a: np.ndarray):
+    assert a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data_as(C.c_void_p)
+
+
+# --------------------------------------------------------------------------
+# configuration
+# --------------------------------------------------------------------------
+def horizon(a: float) -> float:
+    """Outer horizon r_H = 1 + sqrt(1 - a^2) (M = 1)."""
+    return 1.0 + math.sqrt(1.0 - a * a)
+
+
+def make_cfg(nr, nth, a, r_in, r_out, dt=None, cfl=0.5, beta_s=0.53, n_fld_iter=7, n_push_iter=3,
+             damp_cells=None, damp_max=0.1, qm=(-1.0, 1.0, 1.0, 0.0), qw=(-1e-3, 1e-3, 1e-3, 0.0),
+             massive=(1, 1, 1, 0)) -> Cfg:
+    """Grid uniform in ln r and theta; dt from the CFL reading
+    dt = cfl * min(dr, r dtheta) at r_in when not given."""
+    c = Cfg()
+    c.nr, c.nth, c.ng = nr, nth, NG
+    c.ld = nr + 2 * NG
+    c.a, c.r_in, c.r_out = a, r_in, r_out
+    c.dx1 = math.log(r_out / r_in) / nr
+    c.dth = math.pi / nth
+    if dt is None:
+        dr = r_in * (math.exp(c.dx1) - 1.0)
+        dt = cfl * min(dr, r_in * c.dth)
+    c.dt = dt
+    c.beta_s = beta_s
+    c.n_fld_iter, c.n_push_iter = n_fld_iter, n_push_iter
+    c.damp_cells = max(8, nr // 32) if damp_cells is None else damp_cells
+    c.damp_max = damp_max
+    for k in range(4):
+        c.qm[k], c.qw[k], c.massive[k] = qm[k], qw[k], massive[k]
+    return c
+
+
+def field_shape(c: Cfg):
+    return (c.nth + 1, c.ld)
+
+
+def zeros_fields(c: Cfg, n=6):
+    return [np.zeros(field_shape(c)) for _ in range(n)]
+
+
+# --------------------------------------------------------------------------
+# wrappers
+# --------------------------------------------------------------------------
+METRIC_KEYS = ["alpha", "beta", "g_rr", "g_rp", "g_thth", "g_pp", "gi_rr", "gi_rp", "gi_thth", "gi_pp",
+               "sqrtg", "da_r", "da_th", "db_r", "db_th", "dgi_rr_r", "dgi_rr_th", "dgi_rp_r", "dgi_rp_th",
+               "dgi_thth_r", "dgi_thth_th", "dgi_pp_r", "dgi_pp_th"]
+
+
+def metric(a, r, th) -> dict:
+    out = np.zeros(23)
+    lib().orc_metric_eval(a, r, th, _p(out))
+    return dict(zip(METRIC_KEYS, out))
+
+
+def closed_fields(kind, a, B0, r, th) -> dict:
+    out = np.zeros(16)
+    lib().orc_closed_fields(kind, a, B0, r, th, _p(out))
+    return {"At": out[0], "Aph": out[1], "E": out[2:5].copy(), "sgB": out[5:8].copy(),
+            "D": out[10:13].copy(), "B": out[13:16].copy()}
+
+
+def gauss_legendre():
+    x, w = np.zeros(10), np.zeros(10)
+    lib().orc_gauss_legendre(_p(x), _p(w))
+    return x, w
+
+
+def areas(c: Cfg):
+    arrs = zeros_fields(c)
+    lib().orc_areas(C.byref(c), *[_p(x) for x in arrs])
+    return arrs[:3], arrs[3:]
+
+
+def init_fields(c: Cfg, kind: int, B0: float):
+    arrs = zeros_fields(c)
+    lib().orc_init_fields(C.byref(c), kind, B0, *[_p(x) for x in arrs])
+    return arrs[:3], arrs[3:]
+
+
+def field_update(c: Cfg, D, B, J):
+    """In place: D, B lists of 3 arrays; J list of 3 current densities."""
+    lib().orc_field_update(C.byref(c), *[_p(x) for x in list(D) + list(B) + list(J)])
+
+
+def circulations(c: Cfg, D, B):
+    out = zeros_fields(c)
+    lib().orc_circulations(C.byref(c), *[_p(x) for x in list(D) + list(B) + out])
+    return out[:3], out[3:]
+
+
+def geodesic_rhs(a, eps, y):
+    y = np.ascontiguousarray(y, dtype=np.float64)
+    f = np.zeros(6)
+    lib().orc_geodesic_rhs(a, eps, _p(y), _p(f))
+    return f
+
+
+def boris(a, r, th, qm, dt, Dv, Bv, u):
+    u = np.array(u, dtype=np.float64)
+    lib().orc_boris(a, r, th, qm, dt, _p(np.asarray(Dv, np.float64)), _p(np.asarray(Bv, np.float64)), _p(u))
+    return u
+
+
+def push_values(a, qm, massive, dt, n_iter, Dv, Bv, y):
+    y = np.array(y, dtype=np.float64)
+    lib().orc_push_values(a, qm, massive, dt, n_iter, _p(np.asarray(Dv, np.float64)),
+                          _p(np.asarray(Bv, np.float64)), _p(y))
+    return y
+
+
+def push_analytic(kind, B0, a, qm, massive, dt, n_iter, y, nsteps, every):
+    y = np.array(y, dtype=np.float64)
+    nsamp = nsteps // every if every > 0 else 0
+    traj = np.zeros((max(nsamp, 1), 6))
+    n = lib().orc_push_analytic(kind, B0, a, qm, massive, dt, n_iter, _p(y), nsteps, every, _p(traj))
+    return y, traj[:n]
+
+
+def interp(c: Cfg, D, B, x1, x2):
+    out = np.zeros(6)
+    lib().orc_interp(C.byref(c), *[_p(x) for x in list(D) + list(B)], x1, x2, _p(out))
+    return out
+
+
+def deposit_one(c: Cfg, qw, x1a, x2a, x1b, x2b, dphi):
+    JrA, JtA, Jph = zeros_fields(c, 3)
+    lib().orc_deposit_one(C.byref(c), _p(JrA), _p(JtA), _p(Jph), qw, x1a, x2a, x1b, x2b, dphi)
+    return JrA, JtA, Jph
+
+
+class Particles:
+    """SoA particle state of the FP64 path: r, theta, covariant u_i, tag
+    (species in bits 0-1, DEAD in bit 31)."""
+
+    def __init__(self, r, th, u1, u2, u3, tag):
+        self.r = np.ascontiguousarray(r, np.float64)
+        self.th = np.ascontiguousarray(th, np.float64)
+        self.u1 = np.ascontiguousarray(u1, np.float64)
+        self.u2 = np.ascontiguousarray(u2, np.float64)
+        self.u3 = np.ascontiguousarray(u3, np.float64)
+        self.tag = np.ascontiguousarray(tag, np.uint32)
+
+    @property
+    def n(self):
+        return self.r.shape[0]
+
+    def copy(self):
+        return Particles(self.r.copy(), self.th.copy(), self.u1.copy(), self.u2.copy(), self.u3.copy(),
+                         self.tag.copy())
+
+    def take(self, idx):
+        return Particles(self.r[idx], self.th[idx], self.u1[idx], self.u2[idx], self.u3[idx], self.tag[idx])
+
+
+def push_deposit(c: Cfg, P: Particles, D, B):
+    """Push + deposit in place; returns (status, J list, dphi array)."""
+    J = zeros_fields(c, 3)
+    dphi = np.zeros(P.n)
+    st = lib().orc_push_deposit(C.byref(c), P.n, _p(P.r), _p(P.th), _p(P.u1), _p(P.u2), _p(P.u3), _p(P.tag),
+                                _p(dphi), *[_p(x) for x in list(D) + list(B) + J])
+    return st, J, dphi
+
+
+def cell_keys(c: Cfg, P: Particles):
+    k = np.zeros(P.n, np.int32)
+    lib().orc_cell_keys(C.byref(c), P.n, _p(P.r), _p(P.th), _p(P.tag), _p(k))
+    return k
+
+
+def counting_sort(keys: np.ndarray, nkeys: int):
+    keys = np.ascontiguousarray(keys, np.int32)
+    perm = np.zeros(keys.shape[0], np.int64)
+    live = lib().orc_counting_sort(keys.shape[0], nkeys, _p(keys), _p(perm))
+    return perm, live
+
+
+def sort(c: Cfg, P: Particles) -> Particles:
+    keys = cell_keys(c, P)
+    perm, live = counting_sort(keys, c.nr * c.nth)
+    return P.take(perm[:live])
+
+
+def rho(c: Cfg, P: Particles):
+    out = np.zeros(field_shape(c))
+    lib().orc_rho(C.byref(c), P.n, _p(P.r), _p(P.th), _p(P.tag), _p(out))
+    return out
+
+
+def divD(c: Cfg, D):
+    out = np.zeros(field_shape(c))
+    lib().orc_divD(C.byref(c), _p(D[0]), _p(D[1]), _p(out))
+    return out
+
+
+def divB(c: Cfg, B):
+    out = np.zeros(field_shape(c))
+    lib().orc_divB(C.byref(c), _p(B[0]), _p(B[1]), _p(out))
+    return out
+
+
+def step(c: Cfg, P: Particles, D, B, do_sort=True):
+    """One time step in the paper's order (Fig. stepping): push + deposit from
+    fields n, field update n -> n+1 with J^{n+1/2}, then the sort by cell."""
+    st, J, dphi = push_deposit(c, P, D, B)
+    field_update(c, D, B, J)
+    if do_sort:
+        P = sort(c, P)
+    return st, P, J

@@ -1,0 +1,1073 @@
+/*
+ * grpic_oracle.c -- plain, slow FP64 CPU oracle of one GRPIC time step as
+ * defined in Chen, Luepker & Yuan, "Introducing APERTURE: a GPU-based general
+ * relativistic particle-in-cell simulation framework" (arXiv:2503.04558).
+ *
+ * TEST INFRASTRUCTURE, NOT PRODUCT CODE.  Only tests/, __graft_entry__.smoke()
+ * and the cpu_baseline / reference leg of bench.py may load this library.  It
+ * shares no source with the CUDA path (no headers, no helpers, no tables) and
+ * the CUDA path never calls it.
+ *
+ * Every routine takes the paper's steps in the paper's order and notation with
+ * plain loops; no blocking, fusion or reordering.  Built with
+ * -O2 -ffp-contract=off.  Where the paper is silent, garbled or inconsistent
+ * the adopted reading is named in the comment (and listed in the design notes):
+ *   - field corrector prefactor is dt, not dt/2 (Eq. fld-corrector with
+ *     alpha+beta = 1; "alpha = beta = 1/2 is Heun's method");
+ *   - E_phi's shift term carries the 1/2 of the two-point average (Eq. auxE);
+ *   - the rotating Wald B^phi is the printed closed form (Eq. wald-solution-ks);
+ *   - J^phi = +q (dphi/dt) <S> / dV (Eq. j-phi-deposit; sign and volume fixed
+ *     so that the 3-current is a vector);
+ *   - dphi = 1 for all phi integrals (2D axisymmetric cells);
+ *   - edge lengths are coordinate extents: primal r_{i+1}-r_i for the B update,
+ *     dual r_{i+1/2}-r_{i-1/2} for the D update (App. B);
+ *   - CIC shape in logical (x1 = ln(r/r_in)/dx1, x2 = theta/dtheta) space;
+ *   - axis reflection theta -> -theta, u_theta -> -u_theta (Sec. 2.1 BCs);
+ *   - the first step of the Strang split is a full Boris step at fields n
+ *     (bundled convention, Sec. 2.2 and Fig. stepping).
+ *
+ * Parity pins: see tests/test_oracle_*.py; every exported function here is
+ * pinned by at least one test against something other than itself.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORC_OK 0
+#define ORC_ERANGE 4
+#define ORC_ENAN 5
+#define ORC_DEAD 0x80000000u
+
+#ifndef M_PI
+#define M_PI 3.14159265358979323846
+#endif
+
+/* ------------------------------------------------------------------------ */
+/* Run configuration (grid of Sec. 2.1 / Fig. Yee, solver settings Sec. 2).  */
+/* Field arrays are (nth+1) rows x ld columns, row j = theta index, column   */
+/* c = i + ng where i is the r index (integer or half-integer location).     */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    int nr, nth, ng, ld;
+    double a, r_in, r_out, dx1, dth;
+    double dt, beta_s;
+    int n_fld_iter, n_push_iter;
+    int damp_cells;
+    double damp_max;
+    double qm[4];      /* q/m per species                                    */
+    double qw[4];      /* deposited macro charge q*w per species             */
+    int massive[4];    /* epsilon in u^0 (1 massive, 0 photon)               */
+} orc_cfg;
+
+/* ------------------------------------------------------------------------ */
+/* Kerr-Schild 3+1 metric, App. A (Eqs. ks-coefficients, ks-variables,       */
+/* gamma-inverse, ks-alpha-beta) with analytic r and theta derivatives.      */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    double alpha, beta;                     /* lapse, shift beta^r            */
+    double g_rr, g_rp, g_thth, g_pp;        /* gamma_ij                        */
+    double gi_rr, gi_rp, gi_thth, gi_pp;    /* gamma^ij                        */
+    double sqrtg;                           /* sqrt(det gamma_ij)              */
+    double da[2], db[2];                    /* d_r, d_theta of alpha, beta^r   */
+    double dgi_rr[2], dgi_rp[2], dgi_thth[2], dgi_pp[2];
+} orc_metric;
+
+static void metric_at(double a, double r, double th, orc_metric *m)
+{
+    double s = sin(th), c = cos(th);
+    double rho2 = r * r + a * a * c * c;
+    double Delta = r * r + a * a - 2.0 * r;
+    double Sigma = (r * r + a * a) * (r * r + a * a) - a * a * Delta * s * s;
+    double z = 2.0 * r / rho2;
+
+    /* Eq. ks-coefficients: gamma_ij = g_ij */
+    m->g_rr = 1.0 + z;
+    m->g_thth = rho2;
+    m->g_pp = Sigma * s * s / rho2;
+    m->g_rp = -a * s * s * (1.0 + z);
+    /* Eq. gamma-inverse */
+    m->gi_rr = (a * a + r * r) / rho2 - 2.0 * r / (rho2 + 2.0 * r);
+    m->gi_rp = a / rho2;
+    m->gi_thth = 1.0 / rho2;
+    m->gi_pp = 1.0 / (rho2 * s * s);
+    /* Eq. ks-alpha-beta */
+    m->alpha = 1.0 / sqrt(1.0 + z);
+    m->beta = z / (1.0 + z);
+    /* sqrt(gamma) from its definition, the determinant of gamma_ij */
+    m->sqrtg = sqrt(m->g_thth * (m->g_rr * m->g_pp - m->g_rp * m->g_rp));
+
+    /* analytic derivatives, index 0 = d/dr, 1 = d/dtheta */
+    double drho2[2] = {2.0 * r, -2.0 * a * a * c * s};
+    double rho4 = rho2 * rho2;
+    double dz[2];
+    dz[0] = 2.0 / rho2 - 2.0 * r * drho2[0] / rho4;
+    dz[1] = -2.0 * r * drho2[1] / rho4;
+    for (int k = 0; k < 2; ++k) {
+        double opz = 1.0 + z;
+        m->da[k] = -0.5 * pow(opz, -1.5) * dz[k];
+        m->db[k] = dz[k] / (opz * opz);
+        m->dgi_rp[k] = -a * drho2[k] / rho4;
+        m->dgi_thth[k] = -drho2[k] / rho4;
+    }
+    /* gamma^rr = (a^2+r^2)/rho^2 - z/(1+z) */
+    m->dgi_rr[0] = 2.0 * r / rho2 - (a * a + r * r) * drho2[0] / rho4 - m->db[0];
+    m->dgi_rr[1] = -(a * a + r * r) * drho2[1] / rho4 - m->db[1];
+    /* gamma^phiphi = 1/(rho^2 sin^2) */
+    m->dgi_pp[0] = -drho2[0] / (rho4 * s * s);
+    m->dgi_pp[1] = -(drho2[1] * s * s + rho2 * 2.0 * s * c) / (rho4 * s * s * s * s);
+}
+
+/* out[0..29]: alpha, beta, g_rr, g_rp, g_thth, g_pp, gi_rr, gi_rp, gi_thth,
+ * gi_pp, sqrtg, da[2], db[2], dgi_rr[2], dgi_rp[2], dgi_thth[2], dgi_pp[2] */
+void orc_metric_eval(double a, double r, double th, double *out)
+{
+    orc_metric m;
+    metric_at(a, r, th, &m);
+    double v[23] = {m.alpha, m.beta, m.g_rr, m.g_rp, m.g_thth, m.g_pp,
+                    m.gi_rr, m.gi_rp, m.gi_thth, m.gi_pp, m.sqrtg,
+                    m.da[0], m.da[1], m.db[0], m.db[1],
+                    m.dgi_rr[0], m.dgi_rr[1], m.dgi_rp[0], m.dgi_rp[1],
+                    m.dgi_thth[0], m.dgi_thth[1], m.dgi_pp[0], m.dgi_pp[1]};
+    memcpy(out, v, sizeof v);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Analytic initial fields, Sec. 3.3 and App. C.                             */
+/* kind 0: rotating Wald (Eqs. wald-vector-potential, wald-solution-ks)      */
+/* kind 1: non-rotating Wald in the spinning metric (Eq.                     */
+/*         vacuum-nonrotating-wald: E_i = 0, A_phi = B0 gamma_phiphi / 2)    */
+/* kind 2: monopole (App. C)   kind 3: split monopole = sgn(cos th) monopole */
+/* Returned: A_t, A_phi, E_i (covariant), sqrt(gamma) B^i (contravariant).   */
+/* ------------------------------------------------------------------------ */
+static void closed_fields(int kind, double a, double B0, double r, double th,
+                          double *At, double *Aph, double E[3], double sgB[3])
+{
+    double s = sin(th), c = cos(th);
+    double rho2 = r * r + a * a * c * c, rho4 = rho2 * rho2;
+    double Delta = r * r + a * a - 2.0 * r;
+    if (kind == 0) {
+        *At = B0 * (a * r * (1.0 + c * c) / rho2 - a);
+        *Aph = B0 * 0.5 * s * s * (r * r + a * a - 2.0 * a * a * r * (1.0 + c * c) / rho2);
+        sgB[0] = B0 * (Delta + 2.0 * r * (r * r * r * r - a * a * a * a) / rho4) * s * c;
+        sgB[1] = -B0 * (r + a * a * (1.0 + c * c) * (2.0 * r * r - rho2) / rho4) * s * s;
+        sgB[2] = -B0 * (2.0 * a * r * (a * a - r * r) / rho4 - a) * s * c;
+        E[0] = B0 * a * (1.0 + c * c) * (a * a * c * c - r * r) / rho4;
+        E[1] = B0 * 2.0 * a * r * (a * a - r * r) * s * c / rho4;
+        E[2] = 0.0;
+    } else if (kind == 1) {
+        orc_metric m;
+        metric_at(a, r, th, &m);
+        /* gamma_phiphi = Sigma sin^2 / rho^2; derivatives written out */
+        double Sigma = (r * r + a * a) * (r * r + a * a) - a * a * Delta * s * s;
+        double dS_dr = 4.0 * r * (r * r + a * a) - a * a * (2.0 * r - 2.0) * s * s;
+        double dS_dth = -a * a * Delta * 2.0 * s * c;
+        double drho2_dr = 2.0 * r, drho2_dth = -2.0 * a * a * c * s;
+        double gpp_r = (dS_dr * s * s * rho2 - Sigma * s * s * drho2_dr) / rho4;
+        double gpp_th = ((dS_dth * s * s + Sigma * 2.0 * s * c) * rho2 - Sigma * s * s * drho2_dth) / rho4;
+        *At = 0.0;
+        *Aph = 0.5 * B0 * m.g_pp;
+        sgB[0] = 0.5 * B0 * gpp_th;
+        sgB[1] = -0.5 * B0 * gpp_r;
+        sgB[2] = 0.0;
+        E[0] = E[1] = E[2] = 0.0;
+    } else {
+        double sg = 1.0;
+        if (kind == 3) sg = (c > 0.0) ? 1.0 : ((c < 0.0) ? -1.0 : 0.0);
+        *At = sg * B0 * a * c / rho2;
+        *Aph = -sg * B0 * c * (r * r + a * a) / rho2;
+        sgB[0] = sg * B0 * (a * a + r * r) * (r * r - a * a * c * c) * s / rho4;
+        sgB[1] = -sg * B0 * 2.0 * a * a * r * s * s * c / rho4;
+        sgB[2] = sg * B0 * a * (r * r - a * a * c * c) * s / rho4;
+        E[0] = -sg * B0 * 2.0 * a * r * c / rho4;
+        E[1] = -sg * B0 * a * (r * r - a * a * c * c) * s / rho4;
+        E[2] = 0.0;
+    }
+}
+
+/* D^j = gamma^{ji} (E_i - e_ikl beta^k B^l) / alpha, from Eq. E-H-B-D solved
+ * for D.  With beta = (beta^r, 0, 0): e_{theta r phi} = -sqrt(gamma),
+ * e_{phi r theta} = +sqrt(gamma). */
+static void closed_D(int kind, double a, double B0, double r, double th, double D[3], double Bup[3])
+{
+    orc_metric m;
+    double At, Aph, E[3], sgB[3];
+    metric_at(a, r, th, &m);
+    closed_fields(kind, a, B0, r, th, &At, &Aph, E, sgB);
+    double Ep_r = E[0];
+    double Ep_th = E[1] + m.beta * sgB[2];
+    double Ep_ph = E[2] - m.beta * sgB[1];
+    D[0] = (m.gi_rr * Ep_r + m.gi_rp * Ep_ph) / m.alpha;
+    D[1] = m.gi_thth * Ep_th / m.alpha;
+    D[2] = (m.gi_rp * Ep_r + m.gi_pp * Ep_ph) / m.alpha;
+    for (int k = 0; k < 3; ++k) Bup[k] = sgB[k] / m.sqrtg;
+}
+
+/* out[0..9]: At, Aph, E_r, E_th, E_ph, sg*B^r, sg*B^th, sg*B^ph, then D^r..D^ph
+ * follow in out[10..12] and B^r..B^ph in out[13..15]. */
+void orc_closed_fields(int kind, double a, double B0, double r, double th, double *out)
+{
+    double At, Aph, E[3], sgB[3], D[3], Bu[3];
+    closed_fields(kind, a, B0, r, th, &At, &Aph, E, sgB);
+    closed_D(kind, a, B0, r, th, D, Bu);
+    double v[16] = {At, Aph, E[0], E[1], E[2], sgB[0], sgB[1], sgB[2], 0, 0, D[0], D[1], D[2], Bu[0], Bu[1], Bu[2]};
+    memcpy(out, v, sizeof v);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Gauss-Legendre quadrature (Sec. 2.1: "a simple 10-point Gauss            */
+/* quadrature"); nodes by Newton's method on the Legendre recurrence.        */
+/* ------------------------------------------------------------------------ */
+#define NGL 10
+static double gl_x[NGL], gl_w[NGL];
+static int gl_ready = 0;
+
+static void gl_init(void)
+{
+    if (gl_ready) return;
+    int n = NGL;
+    for (int k = 0; k < n; ++k) {
+        double x = cos(M_PI * (k + 0.75) / (n + 0.5));
+        double dp = 0.0;
+        for (int it = 0; it < 100; ++it) {
+            double p0 = 1.0, p1 = x;
+            for (int l = 2; l <= n; ++l) {
+                double p2 = ((2.0 * l - 1.0) * x * p1 - (l - 1.0) * p0) / l;
+                p0 = p1;
+                p1 = p2;
+            }
+            dp = n * (x * p1 - p0) / (x * x - 1.0);
+            double dx = p1 / dp;
+            x -= dx;
+            if (fabs(dx) < 1e-16) break;
+        }
+        /* recompute derivative at the converged node */
+        double p0 = 1.0, p1 = x;
+        for (int l = 2; l <= n; ++l) {
+            double p2 = ((2.0 * l - 1.0) * x * p1 - (l - 1.0) * p0) / l;
+            p0 = p1;
+            p1 = p2;
+        }
+        dp = n * (x * p1 - p0) / (x * x - 1.0);
+        gl_x[k] = x;
+        gl_w[k] = 2.0 / ((1.0 - x * x) * dp * dp);
+    }
+    gl_ready = 1;
+}
+
+void orc_gauss_legendre(double *x, double *w)
+{
+    gl_init();
+    memcpy(x, gl_x, sizeof gl_x);
+    memcpy(w, gl_w, sizeof gl_w);
+}
+
+static double sqrtg_at(double a, double r, double th)
+{
+    orc_metric m;
+    metric_at(a, r, th, &m);
+    return m.sqrtg;
+}
+
+/* integral of sqrt(gamma) over theta in [t0,t1] at fixed r (dphi = 1) */
+static double int_th(double a, double r, double t0, double t1)
+{
+    gl_init();
+    double h = 0.5 * (t1 - t0), mid = 0.5 * (t1 + t0), s = 0.0;
+    for (int k = 0; k < NGL; ++k) s += gl_w[k] * sqrtg_at(a, r, mid + h * gl_x[k]);
+    return h * s;
+}
+/* integral over r in [r0,r1] at fixed theta */
+static double int_r(double a, double r0, double r1, double th)
+{
+    gl_init();
+    double h = 0.5 * (r1 - r0), mid = 0.5 * (r1 + r0), s = 0.0;
+    for (int k = 0; k < NGL; ++k) s += gl_w[k] * sqrtg_at(a, mid + h * gl_x[k], th);
+    return h * s;
+}
+/* 10 x 10 point rule over [r0,r1] x [t0,t1] */
+static double int_rth(double a, double r0, double r1, double t0, double t1)
+{
+    gl_init();
+    double hr = 0.5 * (r1 - r0), mr = 0.5 * (r1 + r0);
+    double ht = 0.5 * (t1 - t0), mt = 0.5 * (t1 + t0), s = 0.0;
+    for (int k = 0; k < NGL; ++k)
+        for (int l = 0; l < NGL; ++l)
+            s += gl_w[k] * gl_w[l] * sqrtg_at(a, mr + hr * gl_x[k], mt + ht * gl_x[l]);
+    return hr * ht * s;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Grid geometry: log-r x theta, Fig. Yee staggering                        */
+/*   D^r, B^th, J^r  at (i+1/2, j)   D^th, B^r, J^th at (i, j+1/2)          */
+/*   D^ph, J^ph, rho at (i, j)       B^ph            at (i+1/2, j+1/2)      */
+/* ------------------------------------------------------------------------ */
+static double r_of(const orc_cfg *c, double x1) { return c->r_in * exp(x1 * c->dx1); }
+
+enum { LOC_DR = 0, LOC_DT, LOC_DP, LOC_BR, LOC_BT, LOC_BP };
+/* stagger (in r, in theta) of each location, in cells */
+static const double STAG_R[6] = {0.5, 0.0, 0.0, 0.0, 0.5, 0.5};
+static const double STAG_T[6] = {0.0, 0.5, 0.0, 0.5, 0.0, 0.5};
+
+typedef struct {
+    orc_cfg c;
+    int n;            /* (nth+1)*ld */
+    /* area elements, Eq. area-element; A^D_i at D^i locations, A^B_i at B^i */
+    double *AD[3], *AB[3];
+    /* point metric products at every location (Eqs. auxE, auxH) */
+    double *ag_rr[6], *ag_rp[6], *ag_thth[6], *ag_pp[6], *sgb[6];
+    double *dr_prim, *dr_dual;   /* per column */
+} orc_geom;
+
+#define IDX(c, i, j) ((j) * (c)->ld + (i) + (c)->ng)
+
+static void geom_free(orc_geom *g)
+{
+    for (int k = 0; k < 3; ++k) { free(g->AD[k]); free(g->AB[k]); }
+    for (int k = 0; k < 6; ++k) { free(g->ag_rr[k]); free(g->ag_rp[k]); free(g->ag_thth[k]); free(g->ag_pp[k]); free(g->sgb[k]); }
+    free(g->dr_prim); free(g->dr_dual);
+}
+
+static void geom_build(const orc_cfg *c, orc_geom *g)
+{
+    memset(g, 0, sizeof *g);
+    g->c = *c;
+    g->n = (c->nth + 1) * c->ld;
+    for (int k = 0; k < 3; ++k) {
+        g->AD[k] = calloc(g->n, sizeof(double));
+        g->AB[k] = calloc(g->n, sizeof(double));
+    }
+    for (int k = 0; k < 6; ++k) {
+        g->ag_rr[k] = calloc(g->n, sizeof(double));
+        g->ag_rp[k] = calloc(g->n, sizeof(double));
+        g->ag_thth[k] = calloc(g->n, sizeof(double));
+        g->ag_pp[k] = calloc(g->n, sizeof(double));
+        g->sgb[k] = calloc(g->n, sizeof(double));
+    }
+    g->dr_prim = calloc(c->ld, sizeof(double));
+    g->dr_dual = calloc(c->ld, sizeof(double));
+    double dth = c->dth, a = c->a;
+    for (int i = -c->ng; i < c->ld - c->ng; ++i) {
+        g->dr_prim[i + c->ng] = r_of(c, i + 1.0) - r_of(c, i);
+        g->dr_dual[i + c->ng] = r_of(c, i + 0.5) - r_of(c, i - 0.5);
+    }
+    for (int j = 0; j <= c->nth; ++j) {
+        double tlo = (j - 0.5) * dth, thi = (j + 0.5) * dth; /* dual theta range */
+        if (tlo < 0.0) tlo = 0.0;
+        if (thi > M_PI) thi = M_PI;
+        for (int i = -c->ng; i < c->ld - c->ng; ++i) {
+            int q = IDX(c, i, j);
+            double ri = r_of(c, i), rh = r_of(c, i + 0.5);
+            double rml = r_of(c, i - 0.5), rp1 = r_of(c, i + 1.0);
+            /* D^r face: r = r_{i+1/2}, theta in dual range */
+            g->AD[0][q] = int_th(a, rh, tlo, thi);
+            /* D^phi face: dual r and theta ranges */
+            g->AD[2][q] = int_rth(a, rml, rh, tlo, thi);
+            /* B^th face: theta = theta_j, primal r range */
+            g->AB[1][q] = int_r(a, ri, rp1, j * dth);
+            if (j < c->nth) {
+                /* D^th face: theta = theta_{j+1/2}, dual r range */
+                g->AD[1][q] = int_r(a, rml, rh, (j + 0.5) * dth);
+                /* B^r face: r = r_i, primal theta range */
+                g->AB[0][q] = int_th(a, ri, j * dth, (j + 1) * dth);
+                /* B^ph face: primal r and theta ranges */
+                g->AB[2][q] = int_rth(a, ri, rp1, j * dth, (j + 1) * dth);
+            }
+            for (int L = 0; L < 6; ++L) {
+                if (STAG_T[L] > 0.0 && j == c->nth) continue;
+                orc_metric m;
+                metric_at(a, r_of(c, i + STAG_R[L]), (j + STAG_T[L]) * dth, &m);
+                g->ag_rr[L][q] = m.alpha * m.g_rr;
+                g->ag_rp[L][q] = m.alpha * m.g_rp;
+                g->ag_thth[L][q] = m.alpha * m.g_thth;
+                g->ag_pp[L][q] = m.alpha * m.g_pp;
+                g->sgb[L][q] = m.sqrtg * m.beta;
+            }
+        }
+    }
+}
+
+/* The tables depend only on the grid; keep the last one (a plain cache, the
+ * values are identical to a fresh build). */
+static orc_geom g_cache;
+static int g_cache_ok = 0;
+static const orc_geom *geom_get(const orc_cfg *c)
+{
+    if (g_cache_ok && g_cache.c.nr == c->nr && g_cache.c.nth == c->nth && g_cache.c.ng == c->ng &&
+        g_cache.c.ld == c->ld && g_cache.c.a == c->a && g_cache.c.r_in == c->r_in &&
+        g_cache.c.r_out == c->r_out && g_cache.c.dx1 == c->dx1 && g_cache.c.dth == c->dth) {
+        g_cache.c = *c;
+        return &g_cache;
+    }
+    if (g_cache_ok) geom_free(&g_cache);
+    geom_build(c, &g_cache);
+    g_cache_ok = 1;
+    return &g_cache;
+}
+
+/* Export the area tables (for pins P14 and parity of the tables). */
+void orc_areas(const orc_cfg *c, double *AD0, double *AD1, double *AD2, double *AB0, double *AB1, double *AB2)
+{
+    const orc_geom *g = geom_get(c);
+    size_t bytes = (size_t)g->n * sizeof(double);
+    memcpy(AD0, g->AD[0], bytes); memcpy(AD1, g->AD[1], bytes); memcpy(AD2, g->AD[2], bytes);
+    memcpy(AB0, g->AB[0], bytes); memcpy(AB1, g->AB[1], bytes); memcpy(AB2, g->AB[2], bytes);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Field boundary conditions, Sec. 2.1: axis D^phi = B^theta = 0; inner     */
+/* guard cells copy the first physical cell (zero derivative); the outer     */
+/* guard cells are filled the same way (the damping layer lies inside).      */
+/* ------------------------------------------------------------------------ */
+static void apply_bc(const orc_cfg *c, double *D[3], double *B[3])
+{
+    double *half_r[3] = {D[0], B[1], B[2]};   /* last physical i = nr-1 */
+    double *int_r[3] = {D[1], D[2], B[0]};    /* last physical i = nr   */
+    for (int j = 0; j <= c->nth; ++j) {
+        for (int k = 0; k < 3; ++k) {
+            for (int i = -c->ng; i < 0; ++i) {
+                half_r[k][IDX(c, i, j)] = half_r[k][IDX(c, 0, j)];
+                int_r[k][IDX(c, i, j)] = int_r[k][IDX(c, 0, j)];
+            }
+            for (int i = c->nr; i < c->ld - c->ng; ++i) half_r[k][IDX(c, i, j)] = half_r[k][IDX(c, c->nr - 1, j)];
+            for (int i = c->nr + 1; i < c->ld - c->ng; ++i) int_r[k][IDX(c, i, j)] = int_r[k][IDX(c, c->nr, j)];
+        }
+    }
+    for (int i = -c->ng; i < c->ld - c->ng; ++i) {
+        D[2][IDX(c, i, 0)] = 0.0;
+        D[2][IDX(c, i, c->nth)] = 0.0;
+        B[1][IDX(c, i, 0)] = 0.0;
+        B[1][IDX(c, i, c->nth)] = 0.0;
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Initial fields (App. C): B^r, B^theta by Stokes' theorem on A_phi over    */
+/* each primal face; B^phi as the face average of the closed form; D^j      */
+/* pointwise from the closed-form E_i and B^l.                               */
+/* ------------------------------------------------------------------------ */
+static double Aphi_at(int kind, double a, double B0, double r, double th)
+{
+    double At, Aph, E[3], sgB[3];
+    closed_fields(kind, a, B0, r, th, &At, &Aph, E, sgB);
+    return Aph;
+}
+
+void orc_init_fields(const orc_cfg *c, int kind, double B0, double *D0, double *D1, double *D2,
+                     double *B0r, double *B1, double *B2)
+{
+    orc_geom g = *geom_get(c); /* shallow copy of the cached tables */
+    double *D[3] = {D0, D1, D2}, *B[3] = {B0r, B1, B2};
+    double a = c->a, dth = c->dth;
+    for (int k = 0; k < 3; ++k) {
+        memset(D[k], 0, sizeof(double) * g.n);
+        memset(B[k], 0, sizeof(double) * g.n);
+    }
+    gl_init();
+    for (int j = 0; j <= c->nth; ++j) {
+        for (int i = -c->ng; i < c->ld - c->ng; ++i) {
+            int q = IDX(c, i, j);
+            double ri = r_of(c, i), rp1 = r_of(c, i + 1.0);
+            if (j < c->nth) {
+                /* B^r A^B_r = A_phi(r_i, th_{j+1}) - A_phi(r_i, th_j) */
+                B[0][q] = (Aphi_at(kind, a, B0, ri, (j + 1) * dth) - Aphi_at(kind, a, B0, ri, j * dth)) / g.AB[0][q];
+                /* B^ph A^B_ph = integral of sqrt(gamma) B^phi over the face */
+                double hr = 0.5 * (rp1 - ri), mr = 0.5 * (rp1 + ri);
+                double ht = 0.5 * dth, mt = (j + 0.5) * dth, s = 0.0;
+                for (int kk = 0; kk < NGL; ++kk)
+                    for (int l = 0; l < NGL; ++l) {
+                        double At, Aph, E[3], sgB[3];
+                        closed_fields(kind, a, B0, mr + hr * gl_x[kk], mt + ht * gl_x[l], &At, &Aph, E, sgB);
+                        s += gl_w[kk] * gl_w[l] * sgB[2];
+                    }
+                B[2][q] = hr * ht * s / g.AB[2][q];
+            }
+            if (j > 0 && j < c->nth) {
+                /* B^th A^B_th = -(A_phi(r_{i+1}, th_j) - A_phi(r_i, th_j)) */
+                B[1][q] = -(Aphi_at(kind, a, B0, rp1, j * dth) - Aphi_at(kind, a, B0, ri, j * dth)) / g.AB[1][q];
+            }
+            double Dv[3], Bu[3];
+            closed_D(kind, a, B0, r_of(c, i + 0.5), j * dth, Dv, Bu);
+            D[0][q] = Dv[0];
+            if (j < c->nth) {
+                closed_D(kind, a, B0, r_of(c, i), (j + 0.5) * dth, Dv, Bu);
+                D[1][q] = Dv[1];
+            }
+            if (j > 0 && j < c->nth) {
+                closed_D(kind, a, B0, r_of(c, i), j * dth, Dv, Bu);
+                D[2][q] = Dv[2];
+            }
+        }
+    }
+    apply_bc(c, D, B);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Auxiliary fields, Eqs. auxH and auxE (metric factors multiplied before   */
+/* the two-point averages), and the circulations of Eqs. D-update and        */
+/* B-update.  Evaluated over every index whose neighbours exist.             */
+/* ------------------------------------------------------------------------ */
+static void aux_fields(const orc_geom *g, double *const D[3], double *const B[3], double *E[3], double *H[3])
+{
+    const orc_cfg *c = &g->c;
+    for (int k = 0; k < 3; ++k) {
+        memset(E[k], 0, sizeof(double) * g->n);
+        memset(H[k], 0, sizeof(double) * g->n);
+    }
+    int ilo = -c->ng + 1, ihi = c->ld - c->ng - 2;
+    for (int j = 0; j <= c->nth; ++j) {
+        for (int i = ilo; i <= ihi; ++i) {
+            int q = IDX(c, i, j), qm = IDX(c, i - 1, j), qp = IDX(c, i + 1, j);
+            if (j < c->nth) {
+                /* H_r at B^r location (i, j+1/2) */
+                H[0][q] = g->ag_rr[LOC_BR][q] * B[0][q]
+                        + 0.5 * (g->ag_rp[LOC_BP][q] * B[2][q] + g->ag_rp[LOC_BP][qm] * B[2][qm]);
+                /* H_phi at B^phi location (i+1/2, j+1/2) */
+                H[2][q] = g->ag_pp[LOC_BP][q] * B[2][q]
+                        + 0.5 * (g->ag_rp[LOC_BR][q] * B[0][q] + g->ag_rp[LOC_BR][qp] * B[0][qp])
+                        - 0.5 * (g->sgb[LOC_DT][q] * D[1][q] + g->sgb[LOC_DT][qp] * D[1][qp]);
+                /* E_theta at D^th location (i, j+1/2) */
+                E[1][q] = g->ag_thth[LOC_DT][q] * D[1][q]
+                        - 0.5 * (g->sgb[LOC_BP][q] * B[2][q] + g->sgb[LOC_BP][qm] * B[2][qm]);
+            }
+            /* H_theta at B^th location (i+1/2, j) */
+            H[1][q] = g->ag_thth[LOC_BT][q] * B[1][q]
+                    + 0.5 * (g->sgb[LOC_DP][q] * D[2][q] + g->sgb[LOC_DP][qp] * D[2][qp]);
+            /* E_r at D^r location (i+1/2, j) */
+            E[0][q] = g->ag_rr[LOC_DR][q] * D[0][q]
+                    + 0.5 * (g->ag_rp[LOC_DP][q] * D[2][q] + g->ag_rp[LOC_DP][qp] * D[2][qp]);
+            /* E_phi at D^ph location (i, j); the shift term takes the 1/2 of the
+             * two-point average like every other average in Eq. auxE */
+            E[2][q] = g->ag_pp[LOC_DP][q] * D[2][q]
+                    + 0.5 * (g->ag_rp[LOC_DR][q] * D[0][q] + g->ag_rp[LOC_DR][qm] * D[0][qm])
+                    + 0.5 * (g->sgb[LOC_BT][q] * B[1][q] + g->sgb[LOC_BT][qm] * B[1][qm]);
+        }
+    }
+}
+
+/* C_H (into CD) and C_E (into CB) on the physical index ranges; dphi = 1 */
+static void circulations(const orc_geom *g, double *E[3], double *H[3], double *CD[3], double *CB[3])
+{
+    const orc_cfg *c = &g->c;
+    for (int k = 0; k < 3; ++k) {
+        memset(CD[k], 0, sizeof(double) * g->n);
+        memset(CB[k], 0, sizeof(double) * g->n);
+    }
+    for (int j = 0; j <= c->nth; ++j) {
+        for (int i = 0; i <= c->nr; ++i) {
+            int q = IDX(c, i, j), qm = IDX(c, i - 1, j), qp = IDX(c, i + 1, j);
+            int qjm = IDX(c, i, j - 1), qjp = IDX(c, i, j + 1);
+            if (i < c->nr) {
+                /* D^r (Eq. D-update; on the axis only the interior H_phi edge
+                 * contributes, Eq. Dr-axis with the half-width face area) */
+                double hp = (j < c->nth) ? H[2][q] : 0.0;
+                double hm = (j > 0) ? H[2][qjm] : 0.0;
+                CD[0][q] = (hp - hm) / g->AD[0][q];
+            }
+            if (j < c->nth) {
+                /* D^theta */
+                CD[1][q] = (H[2][qm] - H[2][q]) / g->AD[1][q];
+                /* B^r (Eq. B-update) */
+                CB[0][q] = -(E[2][qjp] - E[2][q]) / g->AB[0][q];
+            }
+            if (j > 0 && j < c->nth) {
+                /* D^phi with dual edge lengths */
+                CD[2][q] = ((H[1][q] - H[1][qm]) * c->dth + (H[0][qjm] - H[0][q]) * g->dr_dual[i + c->ng]) / g->AD[2][q];
+                if (i < c->nr) /* B^theta (zero on the axis) */
+                    CB[1][q] = -(E[2][q] - E[2][qp]) / g->AB[1][q];
+            }
+            if (i < c->nr && j < c->nth) {
+                /* B^phi with primal edge lengths */
+                CB[2][q] = -((E[1][qp] - E[1][q]) * c->dth + (E[0][q] - E[0][qjp]) * g->dr_prim[i + c->ng]) / g->AB[2][q];
+            }
+        }
+    }
+}
+
+static int is_phys(const orc_cfg *c, int comp, int i, int j)
+{
+    /* comp 0..2 = D^r, D^th, D^ph, 3..5 = B^r, B^th, B^ph */
+    int half_r = (comp == 0 || comp == 4 || comp == 5);
+    int half_t = (comp == 1 || comp == 3 || comp == 5);
+    if (i < 0) return 0;
+    if (half_r ? (i > c->nr - 1) : (i > c->nr)) return 0;
+    if (half_t ? (j > c->nth - 1) : (j > c->nth)) return 0;
+    return 1;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Field update n -> n+1, Eqs. fld-predictor and fld-corrector:             */
+/*   predictor  X~ = X^n + dt (C(X^n) - J)                                   */
+/*   corrector  X  = X^n + dt (alpha_s C(X^n) + beta_s C(X~)) - dt J,        */
+/*              iterated n_fld_iter times, X~ <- latest iterate              */
+/* J^r, J^th, J^ph are current densities (already divided by A^D).           */
+/* Boundary conditions after every stage; outer damping once per step:       */
+/*   f <- f (1 - damp_max s^3), s = depth into the last damp_cells cells.    */
+/* ------------------------------------------------------------------------ */
+void orc_field_update(const orc_cfg *c, double *D0, double *D1, double *D2, double *B0r, double *B1, double *B2,
+                      const double *J0, const double *J1, const double *J2)
+{
+    orc_geom g = *geom_get(c); /* shallow copy of the cached tables */
+    int n = g.n;
+    double *Dn[3] = {D0, D1, D2}, *Bn[3] = {B0r, B1, B2};
+    const double *J[3] = {J0, J1, J2};
+    double *E[3], *H[3], *CDn[3], *CBn[3], *CD[3], *CB[3], *Dt[3], *Bt[3];
+    for (int k = 0; k < 3; ++k) {
+        E[k] = malloc(n * sizeof(double)); H[k] = malloc(n * sizeof(double));
+        CDn[k] = malloc(n * sizeof(double)); CBn[k] = malloc(n * sizeof(double));
+        CD[k] = malloc(n * sizeof(double)); CB[k] = malloc(n * sizeof(double));
+        Dt[k] = malloc(n * sizeof(double)); Bt[k] = malloc(n * sizeof(double));
+    }
+    double dt = c->dt, bs = c->beta_s, as = 1.0 - c->beta_s;
+
+    aux_fields(&g, Dn, Bn, E, H);
+    circulations(&g, E, H, CDn, CBn);
+    /* predictor */
+    for (int k = 0; k < 3; ++k) {
+        memcpy(Dt[k], Dn[k], n * sizeof(double));
+        memcpy(Bt[k], Bn[k], n * sizeof(double));
+    }
+    for (int j = 0; j <= c->nth; ++j)
+        for (int i = 0; i <= c->nr; ++i) {
+            int q = IDX(c, i, j);
+            for (int k = 0; k < 3; ++k) {
+                if (is_phys(c, k, i, j)) Dt[k][q] = Dn[k][q] + (CDn[k][q] - J[k][q]) * dt;
+                if (is_phys(c, 3 + k, i, j)) Bt[k][q] = Bn[k][q] + CBn[k][q] * dt;
+            }
+        }
+    apply_bc(c, Dt, Bt);
+    /* correctors */
+    for (int it = 0; it < c->n_fld_iter; ++it) {
+        aux_fields(&g, Dt, Bt, E, H);
+        circulations(&g, E, H, CD, CB);
+        for (int j = 0; j <= c->nth; ++j)
+            for (int i = 0; i <= c->nr; ++i) {
+                int q = IDX(c, i, j);
+                for (int k = 0; k < 3; ++k) {
+                    if (is_phys(c, k, i, j)) Dt[k][q] = Dn[k][q] + dt * (as * CDn[k][q] + bs * CD[k][q]) - J[k][q] * dt;
+                    if (is_phys(c, 3 + k, i, j)) Bt[k][q] = Bn[k][q] + dt * (as * CBn[k][q] + bs * CB[k][q]);
+                }
+            }
+        apply_bc(c, Dt, Bt);
+    }
+    /* outer damping layer */
+    if (c->damp_cells > 0 && c->damp_max > 0.0) {
+        double x0 = c->nr - c->damp_cells;
+        for (int j = 0; j <= c->nth; ++j)
+            for (int i = 0; i <= c->nr; ++i) {
+                int q = IDX(c, i, j);
+                for (int comp = 0; comp < 6; ++comp) {
+                    if (!is_phys(c, comp, i, j)) continue;
+                    double x = i + ((comp == 0 || comp == 4 || comp == 5) ? 0.5 : 0.0);
+                    double s = (x - x0) / c->damp_cells;
+                    if (s <= 0.0) continue;
+                    if (s > 1.0) s = 1.0;
+                    double f = 1.0 - c->damp_max * s * s * s;
+                    if (comp < 3) Dt[comp][q] *= f; else Bt[comp - 3][q] *= f;
+                }
+            }
+        apply_bc(c, Dt, Bt);
+    }
+    for (int k = 0; k < 3; ++k) {
+        memcpy(Dn[k], Dt[k], n * sizeof(double));
+        memcpy(Bn[k], Bt[k], n * sizeof(double));
+        free(E[k]); free(H[k]); free(CDn[k]); free(CBn[k]); free(CD[k]); free(CB[k]); free(Dt[k]); free(Bt[k]);
+    }
+}
+
+/* circulations of the given fields, for pins (C_H into CD*, C_E into CB*) */
+void orc_circulations(const orc_cfg *c, double *D0, double *D1, double *D2, double *B0r, double *B1, double *B2,
+                      double *CD0, double *CD1, double *CD2, double *CB0, double *CB1, double *CB2)
+{
+    orc_geom g = *geom_get(c); /* shallow copy of the cached tables */
+    double *D[3] = {D0, D1, D2}, *B[3] = {B0r, B1, B2};
+    double *CD[3] = {CD0, CD1, CD2}, *CB[3] = {CB0, CB1, CB2};
+    double *E[3], *H[3];
+    for (int k = 0; k < 3; ++k) { E[k] = malloc(g.n * sizeof(double)); H[k] = malloc(g.n * sizeof(double)); }
+    aux_fields(&g, D, B, E, H);
+    circulations(&g, E, H, CD, CB);
+    for (int k = 0; k < 3; ++k) { free(E[k]); free(H[k]); }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Particle pusher, Sec. 2.2                                                 */
+/* ------------------------------------------------------------------------ */
+
+/* right-hand sides X^i, U_i of Eq. particle-eom without the Lorentz force;
+ * y = (r, theta, phi, u_r, u_theta, u_phi); U_phi = 0 by axisymmetry */
+static void geo_rhs(double a, double eps, const double y[6], double f[6])
+{
+    orc_metric m;
+    metric_at(a, y[0], y[1], &m);
+    double ur = y[3], ut = y[4], up = y[5];
+    double uu = m.gi_rr * ur * ur + 2.0 * m.gi_rp * ur * up + m.gi_thth * ut * ut + m.gi_pp * up * up;
+    double u0 = sqrt(eps + uu) / m.alpha;
+    f[0] = (m.gi_rr * ur + m.gi_rp * up) / u0 - m.beta;
+    f[1] = m.gi_thth * ut / u0;
+    f[2] = (m.gi_rp * ur + m.gi_pp * up) / u0;
+    for (int k = 0; k < 2; ++k) {
+        double dguu = ur * ur * m.dgi_rr[k] + 2.0 * ur * up * m.dgi_rp[k] + ut * ut * m.dgi_thth[k] + up * up * m.dgi_pp[k];
+        f[3 + k] = -m.alpha * u0 * m.da[k] + ur * m.db[k] - dguu / (2.0 * u0);
+    }
+    f[5] = 0.0;
+}
+
+void orc_geodesic_rhs(double a, double eps, const double *y, double *f) { geo_rhs(a, eps, y, f); }
+
+static void lower(const orc_metric *m, const double v[3], double o[3])
+{
+    o[0] = m->g_rr * v[0] + m->g_rp * v[2];
+    o[1] = m->g_thth * v[1];
+    o[2] = m->g_rp * v[0] + m->g_pp * v[2];
+}
+static void raise_(const orc_metric *m, const double v[3], double o[3])
+{
+    o[0] = m->gi_rr * v[0] + m->gi_rp * v[2];
+    o[1] = m->gi_thth * v[1];
+    o[2] = m->gi_rp * v[0] + m->gi_pp * v[2];
+}
+/* covariant cross product (e_ijk v^j w^k), e_ijk = sqrt(gamma) eps_ijk */
+static void cross(double sg, const double v[3], const double w[3], double o[3])
+{
+    o[0] = sg * (v[1] * w[2] - v[2] * w[1]);
+    o[1] = sg * (v[2] * w[0] - v[0] * w[2]);
+    o[2] = sg * (v[0] * w[1] - v[1] * w[0]);
+}
+
+/* Generalized Boris step over a full dt at fields n, Eqs. boris-plus-minus,
+ * u0bar, boris-scheme. Dv, Bv contravariant D^j, B^k at the particle. */
+static void boris(const orc_metric *m, double qm, double dt, const double Dv[3], const double Bv[3], double u[3])
+{
+    double Dl[3], um[3], uup[3], t[3], tl[3], s[3], cr[3], ut[3], up[3];
+    lower(m, Dv, Dl);
+    double h = qm * m->alpha * dt / 2.0;
+    for (int k = 0; k < 3; ++k) um[k] = u[k] + h * Dl[k];
+    raise_(m, um, uup);
+    double uu = um[0] * uup[0] + um[1] * uup[1] + um[2] * uup[2];
+    double u0b = sqrt(1.0 + uu) / m->alpha;
+    for (int k = 0; k < 3; ++k) t[k] = qm * Bv[k] * dt / (2.0 * u0b);
+    lower(m, t, tl);
+    double tt = t[0] * tl[0] + t[1] * tl[1] + t[2] * tl[2];
+    for (int k = 0; k < 3; ++k) s[k] = 2.0 * t[k] / (1.0 + tt);
+    cross(m->sqrtg, uup, t, cr);
+    for (int k = 0; k < 3; ++k) ut[k] = um[k] + cr[k];
+    double utu[3];
+    raise_(m, ut, utu);
+    cross(m->sqrtg, utu, s, cr);
+    for (int k = 0; k < 3; ++k) up[k] = um[k] + cr[k];
+    for (int k = 0; k < 3; ++k) u[k] = up[k] + h * Dl[k];
+}
+
+void orc_boris(double a, double r, double th, double qm, double dt, const double *Dv, const double *Bv, double *u)
+{
+    orc_metric m;
+    metric_at(a, r, th, &m);
+    boris(&m, qm, dt, Dv, Bv, u);
+}
+
+/* Boris (skipped for photons or q = 0) then the geodesic predictor (Eq.
+ * geodesic-predictor) and n_iter trapezoidal correctors (Eq.
+ * geodesic-corrector), each re-evaluated at the latest iterate. y[2] = phi. */
+static void push_core(double a, double qm, int massive, double dt, int n_iter,
+                      const double Dv[3], const double Bv[3], double y[6])
+{
+    if (massive && qm != 0.0) {
+        orc_metric m;
+        metric_at(a, y[0], y[1], &m);
+        boris(&m, qm, dt, Dv, Bv, &y[3]);
+    }
+    double eps = massive ? 1.0 : 0.0;
+    double y0[6], f0[6], yt[6], ft[6];
+    memcpy(y0, y, sizeof y0);
+    geo_rhs(a, eps, y0, f0);
+    for (int k = 0; k < 6; ++k) yt[k] = y0[k] + f0[k] * dt;
+    for (int it = 0; it < n_iter; ++it) {
+        geo_rhs(a, eps, yt, ft);
+        for (int k = 0; k < 6; ++k) yt[k] = y0[k] + 0.5 * dt * (ft[k] + f0[k]);
+    }
+    memcpy(y, yt, sizeof yt);
+}
+
+/* one push with given field values (for pins of the pusher) */
+void orc_push_values(double a, double qm, int massive, double dt, int n_iter, const double *Dv, const double *Bv, double *y)
+{
+    push_core(a, qm, massive, dt, n_iter, Dv, Bv, y);
+}
+
+/* nsteps pushes with fields from the closed-form solution evaluated at x^n
+ * (no grid); y is advanced in place and every `every` steps the state is
+ * appended to traj (6 doubles per sample). Returns the number of samples. */
+int orc_push_analytic(int kind, double B0, double a, double qm, int massive, double dt, int n_iter,
+                      double *y, long nsteps, long every, double *traj)
+{
+    int ns = 0;
+    for (long s = 0; s < nsteps; ++s) {
+        double Dv[3] = {0, 0, 0}, Bv[3] = {0, 0, 0};
+        if (B0 != 0.0) closed_D(kind, a, B0, y[0], y[1], Dv, Bv);
+        push_core(a, qm, massive, dt, n_iter, Dv, Bv, y);
+        if (every > 0 && (s + 1) % every == 0) {
+            memcpy(traj + 6 * ns, y, 6 * sizeof(double));
+            ++ns;
+        }
+    }
+    return ns;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Field interpolation to the particle: bilinear CIC in logical coordinates */
+/* on each component's own staggered lattice.  Rows beyond the axis mirror  */
+/* the first interior row; theta components change sign there, r and phi   */
+/* components do not (the map (theta, phi) -> (-theta, phi + pi)).          */
+/* ------------------------------------------------------------------------ */
+static double row_val(const orc_cfg *c, const double *F, int i, int j, double par)
+{
+    if (j < 0) return par * F[IDX(c, i, -1 - j)];
+    if (j > c->nth) return par * F[IDX(c, i, 2 * c->nth - j)];
+    return F[IDX(c, i, j)];
+}
+static double row_val_half(const orc_cfg *c, const double *F, int i, int j, double par)
+{
+    /* half-theta lattice: row j is theta_{j+1/2}; row -1 mirrors row 0 and
+     * row nth mirrors row nth-1 */
+    if (j < 0) return par * F[IDX(c, i, -1 - j)];
+    if (j > c->nth - 1) return par * F[IDX(c, i, 2 * c->nth - 1 - j)];
+    return F[IDX(c, i, j)];
+}
+
+static double interp(const orc_cfg *c, const double *F, double x1, double x2, double sr, int half_t, double par)
+{
+    double xi = x1 - sr, eta = x2 - (half_t ? 0.5 : 0.0);
+    int i = (int)floor(xi);
+    int j = (int)floor(eta);
+    if (!half_t && j > c->nth - 1) j = c->nth - 1;
+    double f = xi - i, gg = eta - j;
+    double v00, v10, v01, v11;
+    if (half_t) {
+        v00 = row_val_half(c, F, i, j, par); v10 = row_val_half(c, F, i + 1, j, par);
+        v01 = row_val_half(c, F, i, j + 1, par); v11 = row_val_half(c, F, i + 1, j + 1, par);
+    } else {
+        v00 = row_val(c, F, i, j, par); v10 = row_val(c, F, i + 1, j, par);
+        v01 = row_val(c, F, i, j + 1, par); v11 = row_val(c, F, i + 1, j + 1, par);
+    }
+    return (1 - f) * (1 - gg) * v00 + f * (1 - gg) * v10 + (1 - f) * gg * v01 + f * gg * v11;
+}
+
+static void interp_fields(const orc_cfg *c, double *const D[3], double *const B[3], double x1, double x2,
+                          double Dv[3], double Bv[3])
+{
+    Dv[0] = interp(c, D[0], x1, x2, 0.5, 0, 1.0);
+    Dv[1] = interp(c, D[1], x1, x2, 0.0, 1, -1.0);
+    Dv[2] = interp(c, D[2], x1, x2, 0.0, 0, 1.0);
+    Bv[0] = interp(c, B[0], x1, x2, 0.0, 1, 1.0);
+    Bv[1] = interp(c, B[1], x1, x2, 0.5, 0, 1.0);
+    Bv[2] = interp(c, B[2], x1, x2, 0.5, 1, 1.0);
+}
+
+void orc_interp(const orc_cfg *c, double *D0, double *D1, double *D2, double *B0r, double *B1, double *B2,
+                double x1, double x2, double *out6)
+{
+    double *D[3] = {D0, D1, D2}, *B[3] = {B0r, B1, B2};
+    interp_fields(c, D, B, x1, x2, out6, out6 + 3);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Charge-conserving deposit, Sec. 2.3: Esirkepov decomposition of Eq.      */
+/* esirkepov-decomp with CIC S_ij, local prefix sums for J^r A_r and         */
+/* J^th A_th (from Eq. J-integral-eqn), J^phi by Eq. j-phi-deposit.          */
+/* ------------------------------------------------------------------------ */
+static double W1(double d)
+{
+    d = fabs(d);
+    return d < 1.0 ? 1.0 - d : 0.0;
+}
+
+static int jcell(const orc_cfg *c, double x2)
+{
+    int j = (int)floor(x2);
+    if (j > c->nth - 1) j = c->nth - 1;
+    return j;
+}
+
+/* JrA at D^r locations, JtA at D^th locations, Jph at vertices (divided by
+ * dV = A^D_phi, dphi = 1). */
+static void deposit_one(const orc_cfg *c, const double *dV, double *JrA, double *JtA, double *Jph,
+                        double qw, double r0x, double t0x, double r1x, double t1x, double dphi)
+{
+    int b1 = (int)floor(r0x) < (int)floor(r1x) ? (int)floor(r0x) : (int)floor(r1x);
+    int j0 = jcell(c, t0x), j1 = jcell(c, t1x);
+    int b2 = j0 < j1 ? j0 : j1;
+    if (b2 > c->nth - 2) b2 = c->nth - 2;
+    double Wr[3][3], Wt[3][3];
+    for (int A = 0; A < 3; ++A)
+        for (int Bb = 0; Bb < 3; ++Bb) {
+            int k = b1 + A, l = b2 + Bb;
+            double S00 = W1(r0x - k) * W1(t0x - l);
+            double S11 = W1(r1x - k) * W1(t1x - l);
+            double S10 = W1(r1x - k) * W1(t0x - l); /* r at n+1, theta at n */
+            double S01 = W1(r0x - k) * W1(t1x - l); /* r at n, theta at n+1 */
+            Wr[A][Bb] = S11 - S01 + S10 - S00;
+            Wt[A][Bb] = S11 - S10 + S01 - S00;
+            double sbar = S11 / 3.0 + S10 / 6.0 + S01 / 6.0 + S00 / 3.0;
+            if (sbar != 0.0) Jph[IDX(c, k, l)] += qw * (dphi / c->dt) * sbar / dV[IDX(c, k, l)];
+        }
+    for (int Bb = 0; Bb < 3; ++Bb) {
+        double acc = 0.0;
+        for (int A = 0; A < 2; ++A) {
+            acc += Wr[A][Bb];
+            JrA[IDX(c, b1 + A, b2 + Bb)] += -qw / (2.0 * c->dt) * acc;
+        }
+    }
+    for (int A = 0; A < 3; ++A) {
+        double acc = 0.0;
+        for (int Bb = 0; Bb < 2; ++Bb) {
+            acc += Wt[A][Bb];
+            JtA[IDX(c, b1 + A, b2 + Bb)] += -qw / (2.0 * c->dt) * acc;
+        }
+    }
+}
+
+/* single-particle deposit into caller arrays (for pins P10, P12) */
+void orc_deposit_one(const orc_cfg *c, double *JrA, double *JtA, double *Jph, double qw,
+                     double r0x, double t0x, double r1x, double t1x, double dphi)
+{
+    orc_geom g = *geom_get(c); /* shallow copy of the cached tables */
+    deposit_one(c, g.AD[2], JrA, JtA, Jph, qw, r0x, t0x, r1x, t1x, dphi);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Push + deposit over all particles (Fig. stepping): Boris at x^n with     */
+/* fields n, geodesic to x^{n+1}, axis reflection, Esirkepov deposit from   */
+/* x^n to x^{n+1}; then J = (J A)/A^D.  Particles that leave [r_in, r_out)  */
+/* are flagged dead after their deposit; moves of more than one cell or     */
+/* non-finite states flag the particle dead and set a status.               */
+/* ------------------------------------------------------------------------ */
+int orc_push_deposit(const orc_cfg *c, long np, double *pr, double *pth, double *pu1, double *pu2, double *pu3,
+                     uint32_t *tag, double *dphi_out,
+                     double *D0, double *D1, double *D2, double *B0r, double *B1, double *B2,
+                     double *J0, double *J1, double *J2)
+{
+    orc_geom g = *geom_get(c); /* shallow copy of the cached tables */
+    double *D[3] = {D0, D1, D2}, *B[3] = {B0r, B1, B2};
+    memset(J0, 0, g.n * sizeof(double));
+    memset(J1, 0, g.n * sizeof(double));
+    memset(J2, 0, g.n * sizeof(double));
+    int status = ORC_OK;
+    double lnrin = log(c->r_in);
+    for (long p = 0; p < np; ++p) {
+        if (tag[p] & ORC_DEAD) { if (dphi_out) dphi_out[p] = 0.0; continue; }
+        int sp = tag[p] & 3u;
+        double y[6] = {pr[p], pth[p], 0.0, pu1[p], pu2[p], pu3[p]};
+        double x1a = (log(y[0]) - lnrin) / c->dx1, x2a = y[1] / c->dth;
+        double Dv[3], Bv[3];
+        interp_fields(c, D, B, x1a, x2a, Dv, Bv);
+        push_core(c->a, c->qm[sp], c->massive[sp], c->dt, c->n_push_iter, Dv, Bv, y);
+        /* axis reflection */
+        if (y[1] < 0.0) { y[1] = -y[1]; y[4] = -y[4]; }
+        if (y[1] > M_PI) { y[1] = 2.0 * M_PI - y[1]; y[4] = -y[4]; }
+        int bad = 0;
+        for (int k = 0; k < 6; ++k) if (!isfinite(y[k])) bad = 1;
+        if (bad) { tag[p] |= ORC_DEAD; status = status ? status : ORC_ENAN; if (dphi_out) dphi_out[p] = 0.0; continue; }
+        double x1b = (log(y[0]) - lnrin) / c->dx1, x2b = y[1] / c->dth;
+        int di = (int)floor(x1b) - (int)floor(x1a);
+        int dj = jcell(c, x2b) - jcell(c, x2a);
+        if (di < -1 || di > 1 || dj < -1 || dj > 1) {
+            tag[p] |= ORC_DEAD; status = status ? status : ORC_ERANGE;
+            if (dphi_out) dphi_out[p] = 0.0;
+            continue;
+        }
+        deposit_one(c, g.AD[2], J0, J1, J2, c->qw[sp], x1a, x2a, x1b, x2b, y[2]);
+        pr[p] = y[0]; pth[p] = y[1]; pu1[p] = y[3]; pu2[p] = y[4]; pu3[p] = y[5];
+        if (dphi_out) dphi_out[p] = y[2];
+        if (y[0] < c->r_in || y[0] >= c->r_out) tag[p] |= ORC_DEAD;
+    }
+    /* "after finishing the current deposition loop, we divide the results by
+     * A^D_r and A^D_theta" (Sec. 2.3) */
+    for (int q = 0; q < g.n; ++q) {
+        if (g.AD[0][q] != 0.0) J0[q] /= g.AD[0][q];
+        if (g.AD[1][q] != 0.0) J1[q] /= g.AD[1][q];
+    }
+    return status;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Stable counting sort by cell key (cell = j*nr + i; dead -> nr*nth), with */
+/* the dead particles dropped.  perm[k] = old index of new slot k.          */
+/* Returns the number of live particles.                                    */
+/* ------------------------------------------------------------------------ */
+static long cell_key(const orc_cfg *c, double r, double th, uint32_t tag)
+{
+    long ncell = (long)c->nr * c->nth;
+    if (tag & ORC_DEAD) return ncell;
+    double x1 = (log(r) - log(c->r_in)) / c->dx1;
+    int i = (int)floor(x1);
+    int j = jcell(c, th / c->dth);
+    if (i < 0 || i >= c->nr || j < 0) return ncell;
+    return (long)j * c->nr + i;
+}
+
+void orc_cell_keys(const orc_cfg *c, long np, const double *pr, const double *pth, const uint32_t *tag, int32_t *key)
+{
+    for (long p = 0; p < np; ++p) key[p] = (int32_t)cell_key(c, pr[p], pth[p], tag[p]);
+}
+
+long orc_counting_sort(long np, long nkeys, const int32_t *key, int64_t *perm)
+{
+    long *count = calloc(nkeys + 1, sizeof(long));
+    for (long p = 0; p < np; ++p) count[key[p]]++;
+    long run = 0;
+    for (long k = 0; k <= nkeys; ++k) { long t = count[k]; count[k] = run; run += t; }
+    for (long p = 0; p < np; ++p) perm[count[key[p]]++] = p;
+    long live = 0;
+    /* live = number with key < nkeys (dead key == nkeys sorts last) */
+    for (long p = 0; p < np; ++p) if (key[p] < nkeys) ++live;
+    free(count);
+    return live;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Diagnostics: charge density rho = sum q w S / dV at vertices; discrete   */
+/* div D (Eq. D-B-evolution, first line, in the integral form of Eq.         */
+/* J-integral-eqn); div B flux sum per primal cell.                          */
+/* ------------------------------------------------------------------------ */
+void orc_rho(const orc_cfg *c, long np, const double *pr, const double *pth, const uint32_t *tag, double *rho)
+{
+    orc_geom g = *geom_get(c); /* shallow copy of the cached tables */
+    memset(rho, 0, g.n * sizeof(double));
+    double lnrin = log(c->r_in);
+    for (long p = 0; p < np; ++p) {
+        if (tag[p] & ORC_DEAD) continue;
+        double x1 = (log(pr[p]) - lnrin) / c->dx1, x2 = pth[p] / c->dth;
+        int i = (int)floor(x1), j = jcell(c, x2);
+        for (int A = 0; A < 2; ++A)
+            for (int Bb = 0; Bb < 2; ++Bb) {
+                int k = i + A, l = j + Bb;
+                double S = W1(x1 - k) * W1(x2 - l);
+                rho[IDX(c, k, l)] += c->qw[tag[p] & 3u] * S / g.AD[2][IDX(c, k, l)];
+            }
+    }
+}
+
+void orc_divD(const orc_cfg *c, const double *D0, const double *D1, double *divD)
+{
+    orc_geom g = *geom_get(c); /* shallow copy of the cached tables */
+    memset(divD, 0, g.n * sizeof(double));
+    for (int j = 0; j <= c->nth; ++j)
+        for (int i = -c->ng + 1; i < c->ld - c->ng; ++i) {
+            int q = IDX(c, i, j), qm = IDX(c, i - 1, j);
+            double flux = D0[q] * g.AD[0][q] - D0[qm] * g.AD[0][qm];
+            if (j < c->nth) flux += D1[q] * g.AD[1][q];
+            if (j > 0) flux -= D1[IDX(c, i, j - 1)] * g.AD[1][IDX(c, i, j - 1)];
+            divD[q] = flux / g.AD[2][q];
+        }
+}
+
+void orc_divB(const orc_cfg *c, const double *B0r, const double *B1, double *divB)
+{
+    orc_geom g = *geom_get(c); /* shallow copy of the cached tables */
+    memset(divB, 0, g.n * sizeof(double));
+    for (int j = 0; j < c->nth; ++j)
+        for (int i = -c->ng; i < c->ld - c->ng - 1; ++i) {
+            int q = IDX(c, i, j), qp = IDX(c, i + 1, j), qj = IDX(c, i, j + 1);
+            divB[q] = B0r[qp] * g.AB[0][qp] - B0r[q] * g.AB[0][q] + B1[qj] * g.AB[1][qj] - B1[q] * g.AB[1][q];
+        }
+}
