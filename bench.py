@@ -1,0 +1,381 @@
+#!/usr/bin/env python3
+"""Benchmark of the GRPIC time step on GB300 (one JSON line on stdout).
+
+Workload: the production configuration -- 2048 x 2048 log-r x theta mesh,
+a = 0.99, r in [0.9 r_H, 100], split-monopole initial field, 100 particles per
+cell (4.19e8 e+/e-), thermal momenta (Maxwell-Juttner T = 0.3), absorbing
+outer layer, CFL 0.5.  A step is one pass of the whole hot path: push with
+fused deposit, field update (1 predictor + 7 correctors), stable sort by cell.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision 64|32]
+                  [--impl ours|reference]
+
+--impl reference times the FP64 CPU oracle (test infrastructure) on a bounded
+sample of the same workload on the host cores.  Under torchrun every rank runs
+an independent replica (the step has no cross-GPU exchange on one GPU's
+domain); rank 0 prints the whole-job figures.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "particle push+deposit/s and cell-updates/s at 1 GB300; FP32 form vs FP64 plain"
+UNIT = "particle-steps/s"
+
+# production workload
+NR = NTH = 2048
+SPIN = 0.99
+R_OUT = 100.0
+PPC = 100
+THERMAL_T = 0.3
+B0 = 1.0
+
+
+def horizon(a):
+    return 1.0 + math.sqrt(1.0 - a * a)
+
+
+def workload_config(precision, nr=NR, nth=NTH):
+    from paper_2503_04558_gb300 import grpic as G
+    rin = 0.9 * horizon(SPIN)
+    qw = 1e-3
+    return G.Config(nr, nth, SPIN, rin, R_OUT, q_weight=(-qw, qw, qw, 0.0), precision=precision, sort_every=1,
+                    fp64_radius=1.5 * horizon(SPIN))
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return d, "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for k, nm in enumerate(names):
+                if f[5 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+def run_ours(args, rank, world):
+    import torch
+    from paper_2503_04558_gb300 import build, grpic as G, synth
+
+    build.build()
+    G.load()
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    prec = args.precision
+    cfg = workload_config(prec)
+    ctx = G.Context(cfg)
+    F = G.Fields(cfg)
+    ctx.init_fields(F, G.SPLIT_MONOPOLE, B0)
+    n = cfg.n_r * cfg.n_theta * PPC
+    S = G.ParticleSet(cfg, n)
+    gen = synth.particles_torch(cfg.n_r, cfg.n_theta, cfg.r_in, cfg.r_out, n, seed=1234 + rank,
+                                thermal_T=THERMAL_T, device=dev)
+    if prec == 64:
+        S.load(gen["r"], gen["th"], gen["u1"], gen["u2"], gen["u3"], gen["tag"])
+    else:
+        x1 = (torch.log(gen["r"]) - math.log(cfg.r_in)) / cfg.dx1
+        x2 = gen["th"] / cfg.dth
+        i = torch.floor(x1).clamp(0, cfg.n_r - 1)
+        j = torch.floor(x2).clamp(0, cfg.n_theta - 1)
+        cell = (j * cfg.n_r + i).to(torch.int32)
+        S.load((x1 - i).float(), (x2 - j).float(), gen["u1"].float(), gen["u2"].float(), gen["u3"].float(),
+               gen["tag"], cell)
+    del gen
+    torch.cuda.empty_cache()
+    stream = torch.cuda.current_stream()
+
+    def one_step(ev=None):
+        if ev is not None:
+            ev[0].record(stream)
+        ctx.push(S, F)
+        if ev is not None:
+            ev[1].record(stream)
+        ctx.field_update(F)
+        if ev is not None:
+            ev[2].record(stream)
+        ctx.sort(S)
+
+    for _ in range(args.warmup):
+        one_step()
+    st = ctx.sync()
+    if st != 0:
+        raise RuntimeError(f"device status {st} during warm-up")
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(dev.index) as clk:
+        start.record(stream)
+        for k in range(args.steps):
+            one_step(evs[k])
+        stop.record(stream)
+        torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    total_ms = start.elapsed_time(stop)
+    push_ms = [e[0].elapsed_time(e[1]) for e in evs]
+    field_ms = [e[1].elapsed_time(e[2]) for e in evs]
+    st = ctx.sync()
+    if st != 0:
+        raise RuntimeError(f"device status {st} in the timed region")
+    live = S.live()
+
+    # end to end through host buffers (pinned), copies inside the timed region
+    e2e = None
+    if args.e2e_steps > 0:
+        e2e = run_e2e(args, ctx, S, F, cfg, stream)
+
+    res = dict(total_ms=total_ms, push_ms=push_ms, field_ms=field_ms, n=n, live=live, cells=cfg.n_r * cfg.n_theta,
+               clocks=clk.summary(), e2e=e2e, cfg=cfg)
+    return res
+
+
+def run_e2e(args, ctx, S, F, cfg, stream):
+    """Host-resident state: every step copies the particle and field arrays
+    host->device from pinned memory, runs the step through the library and
+    copies the state back."""
+    import torch
+    arrs = [t for t in S.a.arrays() if t is not None]
+    n = S.n
+    host = [torch.empty(t[:n].shape, dtype=t.dtype, pin_memory=True) for t in arrs]
+    fields = F.D + F.B
+    hostf = [torch.empty(t.shape, dtype=t.dtype, pin_memory=True) for t in fields]
+    for h, t in zip(host, arrs):
+        h.copy_(t[:n])
+    for h, t in zip(hostf, fields):
+        h.copy_(t)
+    torch.cuda.synchronize()
+    h2d = sum(h.numel() * h.element_size() for h in host + hostf)
+    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    start.record(stream)
+    for _ in range(args.e2e_steps):
+        cur = [t for t in S.a.arrays() if t is not None]
+        for h, t in zip(host, cur):
+            t[:n].copy_(h, non_blocking=True)
+        for h, t in zip(hostf, fields):
+            t.copy_(h, non_blocking=True)
+        S.count.fill_(n)
+        ctx.step(S, F, 1)
+        cur = [t for t in S.a.arrays() if t is not None]
+        for h, t in zip(host, cur):
+            h.copy_(t[:n], non_blocking=True)
+        for h, t in zip(hostf, fields):
+            h.copy_(t, non_blocking=True)
+    stop.record(stream)
+    torch.cuda.synchronize()
+    ms = start.elapsed_time(stop) / args.e2e_steps
+    return {"value": n / (ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": h2d,
+            "ms_per_step": ms, "steps": args.e2e_steps}
+
+
+# ---------------------------------------------------------------------------
+# oracle timing on the host (bounded sample of the workload)
+# ---------------------------------------------------------------------------
+def oracle_sample(steps, n_side=128):
+    """The FP64 oracle on an n_side^2 sub-grid of the workload (same spin,
+    radial range, field, particles per cell and momenta), single-threaded.
+    Returns particle-steps/s and cell-updates/s of the oracle's step."""
+    import oracle as O
+    from paper_2503_04558_gb300 import synth
+    rin = 0.9 * horizon(SPIN)
+    c = O.make_cfg(n_side, n_side, SPIN, rin, R_OUT, qw=(-1e-3, 1e-3, 1e-3, 0.0))
+    D, B = O.init_fields(c, O.SPLIT_MONOPOLE, B0)
+    n = n_side * n_side * PPC
+    P = O.Particles(*synth.particles(n_side, n_side, c.r_in, c.r_out, n, seed=7, thermal_T=THERMAL_T))
+    t_push = t_field = t_sort = 0.0
+    done = 0
+    for _ in range(steps):
+        t0 = time.perf_counter()
+        st, J, _ = O.push_deposit(c, P, D, B)
+        t1 = time.perf_counter()
+        O.field_update(c, D, B, J)
+        t2 = time.perf_counter()
+        done += P.n
+        P = O.sort(c, P)
+        t3 = time.perf_counter()
+        t_push += t1 - t0
+        t_field += t2 - t1
+        t_sort += t3 - t2
+    tot = t_push + t_field + t_sort
+    return {"value": done / tot, "push_deposit_per_s": done / t_push,
+            "cell_updates_per_s": n_side * n_side * steps / t_field, "seconds": tot, "particles": n,
+            "steps": steps, "grid": f"{n_side}x{n_side}"}
+
+
+def cpu_baseline_block(steps=2, n_side=128):
+    s = oracle_sample(steps, n_side)
+    return {"value": s["value"], "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{s['grid']} sub-grid of the 2048x2048 workload, {PPC} ppc ({s['particles']} particles), "
+                      f"{s['steps']} steps, FP64, single thread, {s['seconds']:.1f} s",
+            "push_deposit_per_s": s["push_deposit_per_s"], "cell_updates_per_s": s["cell_updates_per_s"]}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", 0))
+    if rank != 0:
+        return
+    for _ in range(args.warmup):
+        oracle_sample(1, 64)
+    t0 = time.perf_counter()
+    s = oracle_sample(args.steps, 96)
+    wall = time.perf_counter() - t0
+    val = s["value"]
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * s["seconds"] / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "GRPIC step, 2048x2048 log-r x theta, a=0.99, split monopole, 100 ppc "
+                                   "(4.19e8 e+/e-), thermal T=0.3; oracle on a 96x96 sub-grid sample",
+                       "sample_grid": s["grid"], "sample_particles": s["particles"]},
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{s['grid']} sub-grid, {PPC} ppc, {args.steps} steps, single thread"},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "wall_s": wall}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=4)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", type=int, default=64, choices=[64, 32])
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    rank = int(os.environ.get("RANK", 0))
+    if world > 1:
+        torch.distributed.init_process_group("nccl")
+    res = run_ours(args, rank, world)
+    total_ms = res["total_ms"]
+    if world > 1:
+        t = torch.tensor([total_ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    if rank == 0:
+        cfg = res["cfg"]
+        n, cells = res["n"], res["cells"]
+        ms = total_ms / args.steps
+        value = world * n * args.steps / (total_ms * 1e-3)
+        push_ms = statistics.mean(res["push_ms"])
+        field_ms = statistics.mean(res["field_ms"])
+        pk, pk_kind = peaks()
+        esz = 8 if args.precision == 64 else 4
+        # algorithmic bytes of one push+deposit launch: read and write the
+        # particle state (r, theta, u_r, u_theta, u_phi, tag [, cell])
+        bpp = (5 * esz + 4) * 2 + (4 if args.precision == 32 else 0) * 2
+        achieved_gbs = n * bpp / (push_ms * 1e-3) / 1e9
+        roof = {"kernel": "push+deposit", "bound": "hbm", "achieved": achieved_gbs, "peak": pk["hbm_gbs"],
+                "unit": "GB/s", "frac": achieved_gbs / pk["hbm_gbs"], "traffic": None,
+                "peak_source": f"{pk_kind} hbm_gbs", "bytes_per_particle": bpp}
+        if args.precision == 64:
+            # FP64 arithmetic bounds this kernel on GB300;
+            # flops counted per particle-step from the kernel's DP instructions
+            fpp = float(os.environ.get("GRPIC_FP64_FLOP_PER_PARTICLE", "0")) or None
+            fp64_peak = float(os.environ.get("GRPIC_FP64_PEAK_TFLOPS", "1.25"))
+            if fpp:
+                ach = n * fpp / (push_ms * 1e-3) / 1e12
+                roof = {"kernel": "push+deposit", "bound": "alu", "achieved": ach, "peak": fp64_peak,
+                        "unit": "TFLOP/s", "frac": ach / fp64_peak, "traffic": None,
+                        "hbm_frac": achieved_gbs / pk["hbm_gbs"], "flop_per_particle": fpp}
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64" if args.precision == 64 else "f32", "data": "synthetic",
+                "config": {"workload": "GRPIC step (push+deposit, field update 1+7 stages, sort), 2048x2048 "
+                                       "log-r x theta, a=0.99, r in [0.9 r_H, 100], split monopole, 100 ppc, thermal "
+                                       "T=0.3, FP%d" % args.precision,
+                           "particles": n, "cells": cells, "parallelism": f"replicas x{world}",
+                           "l2": "inputs larger than L2 (particle state %.1f GB)" % (n * (5 * esz + 4) / 1e9)},
+                "push_deposit_per_s": world * n / (push_ms * 1e-3),
+                "cell_updates_per_s": world * cells / (field_ms * 1e-3),
+                "push_ms": push_ms, "field_ms": field_ms, "sort_ms": ms - push_ms - field_ms,
+                "live_particles": res["live"], "roofline": roof, "clocks": res["clocks"],
+                "gpu_launches": args.steps * (1 + 1 + cfg.n_field_iter + 7),
+                "e2e": res["e2e"]}
+        if not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline_block()
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

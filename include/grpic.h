@@ -1,0 +1,201 @@
+/*
+ * grpic.h -- C ABI of the GB300 GRPIC time-step library (libgrpic.so).
+ *
+ * Method: Chen, Luepker & Yuan, "Introducing APERTURE: a GPU-based general
+ * relativistic particle-in-cell simulation framework", arXiv:2503.04558.
+ * The calls follow the paper's statement of the problem: the Kerr-Schild
+ * 3+1 metric and log-r x theta Yee mesh (Sec. 2, App. A), the D/B field
+ * solver (Sec. 2.1, App. B), the generalized Boris + geodesic pusher
+ * (Sec. 2.2), the Esirkepov deposit (Sec. 2.3) and the step order of
+ * Fig. stepping.  A particle sort by cell (not in the paper) keeps the
+ * deposit coherent.
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * Units M = 1, c = 1, Heaviside-Lorentz (Sec. 2.1).  Index i runs in r,
+ * j in theta.  Logical coordinates x1 = ln(r/r_in)/dx1, x2 = theta/dtheta with
+ * dx1 = ln(r_out/r_in)/n_r and dtheta = pi/n_theta.  Cell key = j*n_r + i.
+ *
+ * Field arrays (caller-owned device memory): every component is a row-major
+ * array of (n_theta+1) rows and `ld` columns (ld >= n_r + 4), element type
+ * double (precision 64) or float (precision 32).  Row j is the theta index;
+ * column c = i + 2 holds the r index i of the component's own lattice
+ * (Fig. Yee): D^r, B^theta, J^r at (i+1/2, j); D^theta, B^r, J^theta at
+ * (i, j+1/2); D^phi, J^phi at (i, j); B^phi at (i+1/2, j+1/2).  Two guard
+ * columns on each side hold the zero-derivative copies of Sec. 2.1.
+ * J holds the integrated currents of the deposit, J^r A^D_r, J^theta A^D_theta
+ * and J^phi dV (the quantities of Eq. J-integral-eqn with dphi = 1), which the
+ * field update divides by the face areas.
+ *
+ * Particles (caller-owned device memory, structure of arrays):
+ *   precision 64: x1 = r, x2 = theta (double), u1..u3 = covariant u_r,
+ *                 u_theta, u_phi (double); `cell` unused.
+ *   precision 32: cell = j*n_r + i (int32), x1, x2 = offsets in [0,1] inside
+ *                 the cell in logical units (float), u1..u3 float.
+ *   tag: species in bits 0-1 (indexes q_over_m/q_weight/massive), bit 31 =
+ *   dead.  `n` is the number of slots the call may touch; if `d_count` is not
+ *   NULL it points at a device int64 holding the live count, which bounds
+ *   every kernel and which grpic_sort rewrites.
+ *
+ * Errors: argument errors return at once.  Errors found on the device (a
+ * particle moving more than one cell, a non-finite state, a wait that ran
+ * out) are latched in a device status word; they surface as the return value
+ * of grpic_sync() (or of the next call that synchronizes).  No call traps or
+ * throws.  Every call is asynchronous on the CUDA stream passed as `stream`
+ * (a cudaStream_t; NULL = the legacy default stream).
+ */
+#ifndef GRPIC_H
+#define GRPIC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    GRPIC_OK = 0,
+    GRPIC_EINVAL = 1,    /* invalid argument                                  */
+    GRPIC_ENOMEM = 2,    /* device allocation failed                          */
+    GRPIC_ECUDA = 3,     /* CUDA runtime error                                */
+    GRPIC_ERANGE = 4,    /* a particle moved more than one cell in a step     */
+    GRPIC_ENAN = 5,      /* a particle state became non-finite                */
+    GRPIC_EOVERFLOW = 6, /* capacity exceeded                                 */
+    GRPIC_ECONVERGE = 7, /* an iteration did not converge                     */
+    GRPIC_ETIMEOUT = 8   /* a device-side wait gave up                        */
+} grpic_status;
+
+typedef struct grpic_ctx grpic_ctx;
+
+typedef enum { GRPIC_METRIC_KERR_SCHILD = 0 } grpic_metric;
+
+/* Analytic initial fields (App. C and Sec. 3.2). */
+typedef enum {
+    GRPIC_FIELD_WALD = 0,           /* rotating Wald solution, Eq. wald-solution-ks */
+    GRPIC_FIELD_WALD_A0 = 1,        /* a = 0 Wald in the spinning metric, Eq. vacuum-nonrotating-wald */
+    GRPIC_FIELD_MONOPOLE = 2,       /* monopole, App. C                              */
+    GRPIC_FIELD_SPLIT_MONOPOLE = 3  /* sgn(cos theta) x monopole                     */
+} grpic_field_kind;
+
+/* log-r x theta mesh (Sec. 2.1): n_r x n_theta cells, r in [r_in, r_out],
+ * theta in [0, pi]; outer damping layer over the last damp_cells cells with
+ * factor 1 - damp_max s^3 (s = depth into the layer, 0..1). */
+typedef struct {
+    int32_t n_r, n_theta;
+    double r_in, r_out;
+    int32_t damp_cells;
+    double damp_max;
+} grpic_grid;
+
+/* Solver settings.  beta_field is the semi-implicit weight beta of Eq.
+ * fld-corrector (alpha = 1 - beta), n_field_iter its number of corrector
+ * iterations N; n_push_iter the number of trapezoidal corrector iterations of
+ * Eq. geodesic-corrector.  Per species s (tag bits 0-1): q_over_m[s] is q/m
+ * in the Lorentz force, q_weight[s] the macro charge q*w deposited, massive[s]
+ * the epsilon of u^0 (1 massive, 0 photon: no Boris step, Sec. 2.2).
+ * precision: 64 (FP64 path) or 32 (FP32 form).  fp64_radius: in the FP32 form,
+ * metric evaluations at r < fp64_radius run in FP64 (<= 0: never). */
+typedef struct {
+    double dt;
+    double beta_field;
+    int32_t n_field_iter;
+    int32_t n_push_iter;
+    double q_over_m[4];
+    double q_weight[4];
+    int32_t massive[4];
+    int32_t precision;
+    int32_t sort_every;
+    double fp64_radius;
+} grpic_params;
+
+typedef struct {
+    int64_t n;          /* slots the call may touch (upper bound of the live count) */
+    int64_t capacity;   /* allocated slots of every array                          */
+    int64_t *d_count;   /* optional device int64: live count (bounds kernels)      */
+    void *x1, *x2;      /* r, theta (double) | in-cell offsets (float)             */
+    void *u1, *u2, *u3; /* covariant u_r, u_theta, u_phi                           */
+    uint32_t *tag;      /* species | dead bit                                      */
+    int32_t *cell;      /* precision 32 only: cell key                             */
+} grpic_particles;
+
+typedef struct {
+    void *D[3];   /* D^r, D^theta, D^phi   */
+    void *B[3];   /* B^r, B^theta, B^phi   */
+    void *J[3];   /* J^r A_r, J^theta A_theta, J^phi dV (deposit output) */
+    int64_t ld;   /* row stride in elements, >= n_r + 4 */
+} grpic_fields;
+
+/* Create a context: validates the grid and parameters (a in [0,1),
+ * 0 < r_in < r_out, n_r, n_theta >= 4 and even n_theta, dt > 0, precision 64
+ * or 32), computes on the current device the face areas of Eq. area-element
+ * by 10-point Gauss-Legendre quadrature and the metric coefficient products of
+ * Eqs. auxE/auxH, and allocates the field-solver and sort scratch.  The
+ * context owns only those tables and scratch.  *out = NULL on failure. */
+grpic_status grpic_init(grpic_metric metric, double spin, const grpic_grid *grid, const grpic_params *params,
+                        grpic_ctx **out);
+
+/* Fill D and B with an analytic solution of App. C: B^r, B^theta by Stokes'
+ * theorem on A_phi over each face, B^phi as the face average of the closed
+ * form, D^j = gamma^{ji}(E_i - e_ikl beta^k B^l)/alpha at each D location
+ * (Eq. E-H-B-D); guard cells and axis values per Sec. 2.1.  J is zeroed. */
+grpic_status grpic_init_fields(grpic_ctx *ctx, grpic_field_kind kind, double B0, grpic_fields *f, void *stream);
+
+/* Push + deposit (Sec. 2.2-2.3, Fig. stepping): for every live particle,
+ * interpolate D, B at x^n, one full generalized Boris step (Eqs.
+ * boris-plus-minus, u0bar, boris-scheme; skipped for photons), the geodesic
+ * predictor and n_push_iter correctors (Eqs. geodesic-predictor/-corrector),
+ * axis reflection, then the Esirkepov deposit of the move x^n -> x^{n+1}
+ * (Eqs. esirkepov-decomp, j-phi-deposit) into f->J (zeroed first).
+ * Particles that leave [r_in, r_out) are marked dead after their deposit.
+ * The cell keys of the new positions are kept in the context for grpic_sort. */
+grpic_status grpic_push(grpic_ctx *ctx, grpic_particles *p, grpic_fields *f, void *stream);
+
+/* Deposit only: adds the Esirkepov currents of the moves from `before` to
+ * `after` (same slots, precision-matched), with the azimuthal displacement
+ * dphi[k] (device array of double or float), into f->J (not zeroed). */
+grpic_status grpic_deposit(grpic_ctx *ctx, const grpic_particles *before, const grpic_particles *after,
+                           const void *dphi, grpic_fields *f, void *stream);
+
+/* Field update n -> n+1 (Eqs. fld-predictor, fld-corrector, App. B) with
+ * the currents in f->J: one predictor and n_field_iter correctors, the axis
+ * and inner-boundary conditions after every stage (Eq. Dr-axis for D^r on the
+ * axis), the outer damping layer once at the end. */
+grpic_status grpic_field_update(grpic_ctx *ctx, grpic_fields *f, void *stream);
+
+/* Stable sort of the particles by cell key (dead particles last, dropped).
+ * Keys are recomputed from the particle positions.  The sorted arrays are
+ * written to `scratch` (same layout and capacity); on return the two structs'
+ * array pointers are swapped so *p holds the sorted state.  The new live count
+ * is written to p->d_count when given (p->n is left as an upper bound). */
+grpic_status grpic_sort(grpic_ctx *ctx, grpic_particles *p, grpic_particles *scratch, void *stream);
+
+/* nsteps full steps in the order of Fig. stepping: grpic_push (with deposit),
+ * grpic_field_update, and grpic_sort every params.sort_every steps (0 = never). */
+grpic_status grpic_step(grpic_ctx *ctx, grpic_particles *p, grpic_particles *scratch, grpic_fields *f, int nsteps,
+                        void *stream);
+
+/* Diagnostics at vertices: rho = sum q w S / dV (cloud in cell) into rho[]
+ * and the discrete div D of Eq. J-integral-eqn's integral form into divD[];
+ * both (n_theta+1) x ld arrays of the field precision (device). */
+grpic_status grpic_diagnostics(grpic_ctx *ctx, const grpic_particles *p, const grpic_fields *f, void *rho, void *divD,
+                               void *stream);
+
+/* Copy the face areas of Eq. area-element (A^D_r, A^D_theta, A^D_phi = dV,
+ * A^B_r, A^B_theta, A^B_phi) into six caller device arrays of
+ * (n_theta+1) x ld doubles. */
+grpic_status grpic_get_areas(grpic_ctx *ctx, double *const out[6], int64_t ld, void *stream);
+
+/* Wait for the context's work on `stream`, read and clear the device status
+ * word, and return the first device error recorded (GRPIC_OK if none). */
+grpic_status grpic_sync(grpic_ctx *ctx, void *stream);
+
+/* Human-readable description of the last error seen by the context. */
+const char *grpic_last_error(const grpic_ctx *ctx);
+
+/* Free the context's tables and scratch (never the caller's buffers). */
+void grpic_destroy(grpic_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GRPIC_H */

@@ -1,0 +1,369 @@
+// grpic_api.cu -- the extern "C" boundary declared in include/grpic.h.
+// Argument checking, context (tables + scratch) management and the order of
+// the per-step kernels (Fig. stepping of arXiv:2503.04558: push with deposit,
+// field update, then the sort by cell).
+#include "grpic_internal.cuh"
+
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <utility>
+
+using namespace grpic;
+
+namespace {
+
+grpic_status fail(grpic_ctx *ctx, grpic_status st, const char *msg)
+{
+    if (ctx) snprintf(ctx->err, sizeof ctx->err, "%s", msg);
+    return st;
+}
+
+grpic_status cuda_fail(grpic_ctx *ctx, cudaError_t e, const char *where)
+{
+    if (ctx) snprintf(ctx->err, sizeof ctx->err, "%s: %s", where, cudaGetErrorString(e));
+    return GRPIC_ECUDA;
+}
+
+// Gauss-Legendre nodes/weights on [-1,1]: roots of P_n by Newton iteration on
+// the three-term recurrence (the textbook construction).
+void gauss_legendre(int n, double *x, double *w)
+{
+    for (int k = 0; k < n; ++k) {
+        double z = std::cos(M_PI * (k + 0.75) / (n + 0.5));
+        double pn = 0.0, dpn = 1.0;
+        for (int iter = 0; iter < 64; ++iter) {
+            double pm1 = 1.0, p = z;
+            for (int l = 2; l <= n; ++l) {
+                double pp = ((2 * l - 1) * z * p - (l - 1) * pm1) / l;
+                pm1 = p;
+                p = pp;
+            }
+            pn = p;
+            dpn = n * (z * pn - pm1) / (z * z - 1.0);
+            double step = pn / dpn;
+            z -= step;
+            if (std::fabs(step) < 1e-17) break;
+        }
+        double pm1 = 1.0, p = z;
+        for (int l = 2; l <= n; ++l) {
+            double pp = ((2 * l - 1) * z * p - (l - 1) * pm1) / l;
+            pm1 = p;
+            p = pp;
+        }
+        dpn = n * (z * p - pm1) / (z * z - 1.0);
+        x[k] = z;
+        w[k] = 2.0 / ((1.0 - z * z) * dpn * dpn);
+    }
+}
+
+__global__ void to_float(const double *a, float *b, size_t n)
+{
+    size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) b[i] = (float)a[i];
+}
+
+cudaStream_t S(void *stream) { return (cudaStream_t)stream; }
+
+bool fields_ok(const grpic_ctx *ctx, const grpic_fields *f)
+{
+    if (!f || f->ld < ctx->g.nr + 2 * NG) return false;
+    for (int k = 0; k < 3; ++k)
+        if (!f->D[k] || !f->B[k] || !f->J[k]) return false;
+    return true;
+}
+
+bool particles_ok(const grpic_ctx *ctx, const grpic_particles *p)
+{
+    if (!p || p->n < 0 || p->capacity < p->n) return false;
+    if (p->n == 0) return true;
+    if (!p->x1 || !p->x2 || !p->u1 || !p->u2 || !p->u3 || !p->tag) return false;
+    if (ctx->prm.precision == 32 && !p->cell) return false;
+    if (p->n > INT32_MAX) return false;  // slot indices of the sort are int32
+    return true;
+}
+
+size_t fsize(const grpic_ctx *ctx) { return ctx->prm.precision == 64 ? sizeof(double) : sizeof(float); }
+
+grpic_status ensure_field_scratch(grpic_ctx *ctx, int64_t ld)
+{
+    static_assert(sizeof(int64_t) == 8, "");
+    // 18 arrays: C^n (6) and two iterate buffers (12), stride ld
+    size_t need = 18 * (size_t)(ctx->g.nth + 1) * (size_t)ld * fsize(ctx);
+    if (ctx->fscratch && ctx->fscratch_ld == ld) return GRPIC_OK;
+    if (ctx->fscratch) cudaFree(ctx->fscratch);
+    ctx->fscratch = nullptr;
+    cudaError_t e = cudaMalloc(&ctx->fscratch, need);
+    if (e != cudaSuccess) return fail(ctx, GRPIC_ENOMEM, "field scratch allocation failed");
+    cudaMemset(ctx->fscratch, 0, need);
+    ctx->fscratch_ld = ld;
+    return GRPIC_OK;
+}
+
+grpic_status ensure_particle_scratch(grpic_ctx *ctx, int64_t n)
+{
+    if (n <= ctx->keys_cap) return GRPIC_OK;
+    if (ctx->d_keys) cudaFree(ctx->d_keys);
+    if (ctx->d_perm) cudaFree(ctx->d_perm);
+    ctx->d_keys = nullptr;
+    ctx->d_perm = nullptr;
+    ctx->keys_cap = 0;
+    if (cudaMalloc(&ctx->d_keys, sizeof(int32_t) * (size_t)n) != cudaSuccess ||
+        cudaMalloc(&ctx->d_perm, sizeof(int32_t) * (size_t)n) != cudaSuccess)
+        return fail(ctx, GRPIC_ENOMEM, "particle scratch allocation failed");
+    ctx->keys_cap = n;
+    ctx->perm_cap = n;
+    return GRPIC_OK;
+}
+
+grpic_status sort_impl(grpic_ctx *ctx, grpic_particles *p, grpic_particles *q, cudaStream_t s)
+{
+    int64_t ncell = (int64_t)ctx->g.nr * ctx->g.nth;
+    grpic_status st = ensure_particle_scratch(ctx, p->n);
+    if (st) return st;
+    if (!(ctx->keys_valid && ctx->keys_tag == p->tag)) {
+        cudaMemsetAsync(ctx->d_count, 0, sizeof(int32_t) * (ncell + 1), s);
+        cudaError_t e = launch_keys(ctx, p, s);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "keys");
+    }
+    cudaError_t e = launch_sort(ctx, p, q, s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "sort");
+    ctx->keys_valid = 0;
+    // the sorted state now lives in q's arrays: swap the array pointers
+    std::swap(p->x1, q->x1);
+    std::swap(p->x2, q->x2);
+    std::swap(p->u1, q->u1);
+    std::swap(p->u2, q->u2);
+    std::swap(p->u3, q->u3);
+    std::swap(p->tag, q->tag);
+    std::swap(p->cell, q->cell);
+    return GRPIC_OK;
+}
+
+grpic_status push_impl(grpic_ctx *ctx, grpic_particles *p, grpic_fields *f, bool histogram, cudaStream_t s)
+{
+    int64_t ncell = (int64_t)ctx->g.nr * ctx->g.nth;
+    grpic_status st = ensure_particle_scratch(ctx, p->n);
+    if (st) return st;
+    size_t bytes = (size_t)(ctx->g.nth + 1) * f->ld * fsize(ctx);
+    for (int k = 0; k < 3; ++k) cudaMemsetAsync(f->J[k], 0, bytes, s);
+    if (histogram) cudaMemsetAsync(ctx->d_count, 0, sizeof(int32_t) * (ncell + 1), s);
+    cudaError_t e = (ctx->prm.precision == 64) ? launch_push64(ctx, p, f, histogram, s)
+                                                : launch_push32(ctx, p, f, histogram, s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "push");
+    ctx->keys_valid = histogram ? 1 : 0;
+    ctx->keys_tag = p->tag;
+    return GRPIC_OK;
+}
+
+grpic_status field_impl(grpic_ctx *ctx, grpic_fields *f, cudaStream_t s)
+{
+    grpic_status st = ensure_field_scratch(ctx, f->ld);
+    if (st) return st;
+    cudaError_t e = (ctx->prm.precision == 64) ? launch_field64(ctx, f, s) : launch_field32(ctx, f, s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "field update");
+    return GRPIC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+grpic_status grpic_init(grpic_metric metric, double spin, const grpic_grid *grid, const grpic_params *prm,
+                        grpic_ctx **out)
+{
+    if (!out) return GRPIC_EINVAL;
+    *out = nullptr;
+    if (metric != GRPIC_METRIC_KERR_SCHILD || !grid || !prm) return GRPIC_EINVAL;
+    if (!(spin >= 0.0 && spin < 1.0)) return GRPIC_EINVAL;
+    if (grid->n_r < 4 || grid->n_theta < 4 || (grid->n_theta & 1)) return GRPIC_EINVAL;
+    if ((int64_t)grid->n_r * grid->n_theta > (int64_t)1 << 28) return GRPIC_EINVAL;
+    if (!(grid->r_in > 0.0 && grid->r_out > grid->r_in)) return GRPIC_EINVAL;
+    if (grid->damp_cells < 0 || grid->damp_cells > grid->n_r || !(grid->damp_max >= 0.0 && grid->damp_max <= 1.0))
+        return GRPIC_EINVAL;
+    if (!(prm->dt > 0.0) || prm->n_field_iter < 0 || prm->n_push_iter < 0 || prm->n_push_iter > 64 ||
+        prm->n_field_iter > 64)
+        return GRPIC_EINVAL;
+    if (prm->precision != 64 && prm->precision != 32) return GRPIC_EINVAL;
+    if (!(prm->beta_field >= 0.0 && prm->beta_field <= 1.0)) return GRPIC_EINVAL;
+
+    grpic_ctx *ctx = new (std::nothrow) grpic_ctx();
+    if (!ctx) return GRPIC_ENOMEM;
+    memset((void *)ctx, 0, sizeof *ctx);
+    cudaGetDevice(&ctx->device);
+    ctx->grid = *grid;
+    ctx->prm = *prm;
+    GridDev &g = ctx->g;
+    g.nr = grid->n_r;
+    g.nth = grid->n_theta;
+    g.ld_tab = grid->n_r + 2 * NG;
+    g.a = spin;
+    g.r_in = grid->r_in;
+    g.r_out = grid->r_out;
+    g.dx1 = std::log(grid->r_out / grid->r_in) / grid->n_r;
+    g.dth = M_PI / grid->n_theta;
+    g.ln_rin = std::log(grid->r_in);
+    gauss_legendre(NGL, ctx->gl_x, ctx->gl_w);
+    ctx->slab = (size_t)(g.nth + 1) * g.ld_tab;
+    int64_t ncell = (int64_t)g.nr * g.nth;
+
+    cudaError_t e = cudaSuccess;
+    e = cudaMalloc(&ctx->tab, sizeof(double) * ctx->slab * T_COUNT);
+    if (e == cudaSuccess) e = cudaMalloc(&ctx->col1d, sizeof(double) * 4 * g.ld_tab);
+    if (e == cudaSuccess) e = cudaMalloc(&ctx->d_status, 64);
+    if (e == cudaSuccess) e = cudaMalloc(&ctx->d_count, sizeof(int32_t) * (ncell + 2));
+    if (e == cudaSuccess) e = cudaMalloc(&ctx->d_offset, sizeof(int32_t) * (ncell + 3));
+    if (e == cudaSuccess) e = cudaMalloc(&ctx->d_cursor, sizeof(int32_t) * (ncell + 3));
+    if (e == cudaSuccess) e = cudaMalloc(&ctx->d_blocksum, sizeof(int32_t) * 8192);
+    if (e == cudaSuccess) e = cudaMalloc(&ctx->d_bigseg, sizeof(int32_t) * (ncell + 1));
+    if (e != cudaSuccess) {
+        grpic_destroy(ctx);
+        return GRPIC_ENOMEM;
+    }
+    cudaMemset(ctx->d_status, 0, 64);
+    // q*w per species next to the status word (read by the diagnostics)
+    cudaMemcpy((char *)ctx->d_status + 16, prm->q_weight, 4 * sizeof(double), cudaMemcpyHostToDevice);
+    e = launch_tables(ctx, 0);
+    if (e == cudaSuccess) e = sort_setup();
+    if (e == cudaSuccess && prm->precision == 32) {
+        e = cudaMalloc(&ctx->tab32, sizeof(float) * ctx->slab * T_COUNT);
+        if (e == cudaSuccess) e = cudaMalloc(&ctx->col1d32, sizeof(float) * 4 * g.ld_tab);
+        if (e == cudaSuccess) {
+            size_t n = ctx->slab * T_COUNT;
+            to_float<<<(unsigned)((n + 255) / 256), 256>>>(ctx->tab, ctx->tab32, n);
+            to_float<<<(unsigned)((4 * g.ld_tab + 255) / 256), 256>>>(ctx->col1d, ctx->col1d32, 4 * g.ld_tab);
+            e = cudaGetLastError();
+        }
+    }
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+        grpic_destroy(ctx);
+        return GRPIC_ECUDA;
+    }
+    *out = ctx;
+    return GRPIC_OK;
+}
+
+grpic_status grpic_init_fields(grpic_ctx *ctx, grpic_field_kind kind, double B0, grpic_fields *f, void *stream)
+{
+    if (!ctx) return GRPIC_EINVAL;
+    if (!fields_ok(ctx, f) || kind < GRPIC_FIELD_WALD || kind > GRPIC_FIELD_SPLIT_MONOPOLE)
+        return fail(ctx, GRPIC_EINVAL, "grpic_init_fields: bad fields or kind");
+    cudaError_t e = launch_init_fields(ctx, (int)kind, B0, f, S(stream));
+    return e == cudaSuccess ? GRPIC_OK : cuda_fail(ctx, e, "init_fields");
+}
+
+grpic_status grpic_push(grpic_ctx *ctx, grpic_particles *p, grpic_fields *f, void *stream)
+{
+    if (!ctx) return GRPIC_EINVAL;
+    if (!particles_ok(ctx, p) || !fields_ok(ctx, f)) return fail(ctx, GRPIC_EINVAL, "grpic_push: bad arguments");
+    return push_impl(ctx, p, f, true, S(stream));
+}
+
+grpic_status grpic_deposit(grpic_ctx *ctx, const grpic_particles *before, const grpic_particles *after,
+                           const void *dphi, grpic_fields *f, void *stream)
+{
+    if (!ctx) return GRPIC_EINVAL;
+    if (!particles_ok(ctx, before) || !particles_ok(ctx, after) || !fields_ok(ctx, f) || before->n != after->n ||
+        (before->n > 0 && !dphi))
+        return fail(ctx, GRPIC_EINVAL, "grpic_deposit: bad arguments");
+    cudaError_t e = launch_deposit(ctx, before, after, dphi, f, S(stream));
+    return e == cudaSuccess ? GRPIC_OK : cuda_fail(ctx, e, "deposit");
+}
+
+grpic_status grpic_field_update(grpic_ctx *ctx, grpic_fields *f, void *stream)
+{
+    if (!ctx) return GRPIC_EINVAL;
+    if (!fields_ok(ctx, f)) return fail(ctx, GRPIC_EINVAL, "grpic_field_update: bad fields");
+    return field_impl(ctx, f, S(stream));
+}
+
+grpic_status grpic_sort(grpic_ctx *ctx, grpic_particles *p, grpic_particles *scratch, void *stream)
+{
+    if (!ctx) return GRPIC_EINVAL;
+    if (!particles_ok(ctx, p) || !particles_ok(ctx, scratch) || scratch->capacity < p->n)
+        return fail(ctx, GRPIC_EINVAL, "grpic_sort: bad arguments");
+    return sort_impl(ctx, p, scratch, S(stream));
+}
+
+grpic_status grpic_step(grpic_ctx *ctx, grpic_particles *p, grpic_particles *scratch, grpic_fields *f, int nsteps,
+                        void *stream)
+{
+    if (!ctx) return GRPIC_EINVAL;
+    int every = ctx->prm.sort_every;
+    if (nsteps < 0 || !particles_ok(ctx, p) || !fields_ok(ctx, f) ||
+        (every > 0 && (!particles_ok(ctx, scratch) || scratch->capacity < p->n)))
+        return fail(ctx, GRPIC_EINVAL, "grpic_step: bad arguments");
+    for (int k = 0; k < nsteps; ++k) {
+        bool sort_now = every > 0 && ((ctx->step_count + 1) % every == 0);
+        grpic_status st = push_impl(ctx, p, f, sort_now, S(stream));
+        if (st) return st;
+        st = field_impl(ctx, f, S(stream));
+        if (st) return st;
+        if (sort_now) {
+            st = sort_impl(ctx, p, scratch, S(stream));
+            if (st) return st;
+        }
+        ctx->step_count++;
+    }
+    return GRPIC_OK;
+}
+
+grpic_status grpic_diagnostics(grpic_ctx *ctx, const grpic_particles *p, const grpic_fields *f, void *rho, void *divD,
+                               void *stream)
+{
+    if (!ctx) return GRPIC_EINVAL;
+    if (!fields_ok(ctx, f) || !divD || (rho && !particles_ok(ctx, p)))
+        return fail(ctx, GRPIC_EINVAL, "grpic_diagnostics: bad arguments");
+    cudaError_t e = launch_diag(ctx, rho ? p : nullptr, f, rho, divD, S(stream));
+    return e == cudaSuccess ? GRPIC_OK : cuda_fail(ctx, e, "diagnostics");
+}
+
+grpic_status grpic_get_areas(grpic_ctx *ctx, double *const out[6], int64_t ld, void *stream)
+{
+    if (!ctx) return GRPIC_EINVAL;
+    if (!out || ld < ctx->g.ld_tab) return fail(ctx, GRPIC_EINVAL, "grpic_get_areas: bad arguments");
+    const int slots[6] = {T_ADR, T_ADT, T_ADP, T_ABR, T_ABT, T_ABP};
+    for (int k = 0; k < 6; ++k) {
+        if (!out[k]) return fail(ctx, GRPIC_EINVAL, "grpic_get_areas: null output");
+        cudaError_t e = cudaMemcpy2DAsync(out[k], ld * sizeof(double), ctx->tab + slots[k] * ctx->slab,
+                                          ctx->g.ld_tab * sizeof(double), ctx->g.ld_tab * sizeof(double),
+                                          ctx->g.nth + 1, cudaMemcpyDeviceToDevice, S(stream));
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "get_areas");
+    }
+    return GRPIC_OK;
+}
+
+grpic_status grpic_sync(grpic_ctx *ctx, void *stream)
+{
+    if (!ctx) return GRPIC_EINVAL;
+    cudaError_t e = cudaStreamSynchronize(S(stream));
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "sync");
+    int st = 0;
+    e = cudaMemcpy(&st, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "sync status read");
+    if (st) {
+        cudaMemset(ctx->d_status, 0, sizeof(int));
+        const char *what = st == GRPIC_ERANGE ? "a particle moved more than one cell"
+                           : st == GRPIC_ENAN ? "a particle state became non-finite"
+                           : st == GRPIC_ETIMEOUT ? "a device-side wait timed out"
+                                                  : "device error";
+        snprintf(ctx->err, sizeof ctx->err, "%s", what);
+    }
+    return (grpic_status)st;
+}
+
+const char *grpic_last_error(const grpic_ctx *ctx) { return ctx ? ctx->err : "null context"; }
+
+void grpic_destroy(grpic_ctx *ctx)
+{
+    if (!ctx) return;
+    void *ptrs[] = {ctx->tab, ctx->col1d, ctx->tab32, ctx->col1d32, ctx->fscratch, ctx->d_status, ctx->d_keys,
+                    ctx->d_count, ctx->d_offset, ctx->d_cursor, ctx->d_blocksum, ctx->d_perm, ctx->d_bigseg};
+    for (void *q : ptrs)
+        if (q) cudaFree(q);
+    delete ctx;
+}
+
+}  // extern "C"

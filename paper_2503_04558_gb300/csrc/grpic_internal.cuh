@@ -1,0 +1,150 @@
+// grpic_internal.cuh -- context layout and device math shared by the CUDA
+// translation units of libgrpic (sm_103a).
+//
+// Kerr-Schild 3+1 quantities follow App. A of arXiv:2503.04558 (Eqs.
+// ks-coefficients, ks-variables, gamma-inverse, ks-alpha-beta).  The
+// determinant is used in its closed form sqrt(gamma) = rho^2 sin(theta)
+// sqrt(1+z) (from sqrt(-g) = rho^2 sin(theta) = alpha sqrt(gamma)).
+#pragma once
+
+#include <cmath>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/grpic.h"
+
+namespace grpic {
+
+constexpr int NG = 2;                   // guard columns on each side in r
+constexpr uint32_t DEAD = 0x80000000u;  // tag bit of a dead particle
+constexpr int NGL = 10;                 // Gauss-Legendre points per dimension
+
+// Table slots (each (n_theta+1) x ld_tab doubles).
+enum TabSlot {
+    T_INV_ADR = 0, T_INV_ADT, T_INV_ADP, T_INV_ABR, T_INV_ABT, T_INV_ABP,
+    T_ADR, T_ADT, T_ADP, T_ABR, T_ABT, T_ABP,
+    T_AGRR_DR, T_AGRP_DR,            // at D^r   (i+1/2, j)
+    T_AGTT_DT, T_SGB_DT,             // at D^th  (i, j+1/2)
+    T_AGPP_DP, T_AGRP_DP, T_SGB_DP,  // at D^ph  (i, j)
+    T_AGRR_BR, T_AGRP_BR,            // at B^r   (i, j+1/2)
+    T_AGTT_BT, T_SGB_BT,             // at B^th  (i+1/2, j)
+    T_AGPP_BP, T_AGRP_BP, T_SGB_BP,  // at B^ph  (i+1/2, j+1/2)
+    T_COUNT
+};
+
+struct GridDev {
+    int nr, nth, ld_tab;
+    double a, r_in, r_out, dx1, dth, ln_rin;
+};
+
+}  // namespace grpic
+
+struct grpic_ctx {
+    int device;
+    grpic_grid grid;
+    grpic_params prm;
+    grpic::GridDev g;
+    double gl_x[grpic::NGL], gl_w[grpic::NGL];
+    // device tables (FP64) and their FP32 copies
+    double *tab;        // T_COUNT slabs
+    double *col1d;      // per column: dr_prim, dr_dual, damp_int, damp_half (4 x ld_tab)
+    float *tab32;       // FP32 copies of tab (precision 32 only)
+    float *col1d32;
+    size_t slab;        // elements per slab = (nth+1)*ld_tab
+    // field-solver scratch: Cn[6], two iterate buffers[12] in field precision
+    void *fscratch;
+    int64_t fscratch_ld;
+    // status word and sort scratch
+    int *d_status;
+    int32_t *d_keys;      // per particle key of the last push
+    int64_t keys_cap;
+    int32_t *d_count;     // ncells+1 histogram
+    int32_t *d_offset;    // ncells+2 exclusive scan
+    int32_t *d_cursor;    // ncells+1 running fill
+    int32_t *d_blocksum;  // scan partials
+    int32_t *d_perm;      // new slot -> old slot
+    int32_t *d_bigseg;    // list of oversized segments
+    int64_t perm_cap;
+    int keys_valid;       // keys/histogram of the current order are valid
+    const uint32_t *keys_tag;  // tag array of the particles those keys belong to
+    int64_t step_count;
+    char err[256];
+};
+
+namespace grpic {
+
+// ---------------------------------------------------------------------------
+// Kerr-Schild geometry on the device.
+// ---------------------------------------------------------------------------
+struct KS {
+    double alpha, beta;                 // lapse, radial shift
+    double g_rr, g_rp, g_tt, g_pp;      // gamma_ij  (t = theta)
+    double gi_rr, gi_rp, gi_tt, gi_pp;  // gamma^ij
+    double sqrtg;
+};
+
+__host__ __device__ inline void ks_point(double a, double r, double th, KS &m)
+{
+    double s, c;
+#ifdef __CUDA_ARCH__
+    sincos(th, &s, &c);
+#else
+    s = std::sin(th);
+    c = std::cos(th);
+#endif
+    double s2 = s * s, a2 = a * a;
+    double rho2 = r * r + a2 * c * c;
+    double irho2 = 1.0 / rho2;
+    double z = 2.0 * r * irho2;
+    double opz = 1.0 + z;
+    double iopz = 1.0 / opz;
+    double Dl = r * r + a2 - 2.0 * r;
+    double Sg = (r * r + a2) * (r * r + a2) - a2 * Dl * s2;
+    m.alpha = sqrt(iopz);
+    m.beta = z * iopz;
+    m.g_rr = opz;
+    m.g_tt = rho2;
+    m.g_pp = Sg * s2 * irho2;
+    m.g_rp = -a * s2 * opz;
+    m.gi_rr = (a2 + r * r) * irho2 - m.beta;
+    m.gi_rp = a * irho2;
+    m.gi_tt = irho2;
+    m.gi_pp = irho2 / s2;
+    m.sqrtg = rho2 * s * sqrt(opz);
+}
+
+__host__ __device__ inline double ks_sqrtg(double a, double r, double th)
+{
+    double s, c;
+#ifdef __CUDA_ARCH__
+    sincos(th, &s, &c);
+#else
+    s = std::sin(th);
+    c = std::cos(th);
+#endif
+    double rho2 = r * r + a * a * c * c;
+    return rho2 * s * sqrt(1.0 + 2.0 * r / rho2);
+}
+
+__host__ __device__ inline double r_of(const GridDev &g, double x1) { return g.r_in * exp(x1 * g.dx1); }
+
+__device__ inline void set_status(int *st, int code) { atomicCAS(st, 0, code); }
+
+}  // namespace grpic
+
+// entry points implemented in the kernel translation units (host side)
+namespace grpic {
+cudaError_t launch_tables(grpic_ctx *ctx, cudaStream_t s);
+cudaError_t launch_init_fields(grpic_ctx *ctx, int kind, double B0, const grpic_fields *f, cudaStream_t s);
+cudaError_t launch_push64(grpic_ctx *ctx, grpic_particles *p, grpic_fields *f, bool histogram, cudaStream_t s);
+cudaError_t launch_push32(grpic_ctx *ctx, grpic_particles *p, grpic_fields *f, bool histogram, cudaStream_t s);
+cudaError_t launch_deposit(grpic_ctx *ctx, const grpic_particles *b, const grpic_particles *a, const void *dphi,
+                           grpic_fields *f, cudaStream_t s);
+cudaError_t launch_field64(grpic_ctx *ctx, grpic_fields *f, cudaStream_t s);
+cudaError_t launch_field32(grpic_ctx *ctx, grpic_fields *f, cudaStream_t s);
+cudaError_t launch_keys(grpic_ctx *ctx, const grpic_particles *p, cudaStream_t s);
+cudaError_t sort_setup();
+cudaError_t launch_sort(grpic_ctx *ctx, grpic_particles *p, grpic_particles *scratch, cudaStream_t s);
+cudaError_t launch_diag(grpic_ctx *ctx, const grpic_particles *p, const grpic_fields *f, void *rho, void *divD,
+                        cudaStream_t s);
+}  // namespace grpic

@@ -1,0 +1,441 @@
+// grpic_push64.cu -- FP64 particle push fused with the charge-conserving
+// deposit (arXiv:2503.04558 Sec. 2.2-2.3, Fig. stepping).
+//
+// One thread per particle (structure of arrays, coalesced loads):
+//   1. interpolate D^j, B^j at x^n, each from its own staggered lattice
+//      (bilinear cloud-in-cell in logical coordinates);
+//   2. one full generalized Boris step at fields n (Eqs. boris-plus-minus,
+//      u0bar, boris-scheme), skipped for photons;
+//   3. geodesic predictor + n_iter trapezoidal correctors (Eqs.
+//      geodesic-predictor, geodesic-corrector) on (r, theta, phi, u_r, u_theta);
+//      U_phi = 0 so u_phi is left untouched;
+//   4. axis reflection, range / finiteness checks;
+//   5. Esirkepov deposit of x^n -> x^{n+1} (Eq. esirkepov-decomp with a local
+//      prefix sum, Eq. j-phi-deposit) into the integrated currents
+//      J^r A_r, J^theta A_theta, J^phi dV.  With CIC weights the prefix sums
+//      factor per dimension:  J^r A_r(k+1/2, l) = -qw/(2dt) P_r(k) (S1_t + S0_t)(l)
+//      with P_r(k) = sum_{k'<=k} (S1_r - S0_r)(k'), and likewise for theta.
+//      A warp whose particles all start in one cell (the usual case after the
+//      sort) reduces its 4x4-window contributions with shuffles and issues one
+//      set of FP64 atomics; otherwise each lane issues its own;
+//   6. cell key of x^{n+1} (dead -> n_cells) and a warp-aggregated histogram
+//      for the sort.
+#include "grpic_internal.cuh"
+
+namespace grpic {
+namespace {
+
+struct Push64Args {
+    GridDev g;
+    double dt;
+    int n_iter;
+    double qm[4], qw[4];
+    int massive[4];
+    int64_t n;
+    const int64_t *d_count;
+    double *r, *th, *u1, *u2, *u3;
+    uint32_t *tag;
+    const double *D0, *D1, *D2, *B0, *B1, *B2;
+    double *J0, *J1, *J2;
+    int64_t ld;
+    int32_t *keys;
+    int32_t *count;
+    int histogram;
+    int *status;
+};
+
+struct Rhs {
+    double xr, xt, xp, ur, ut;
+};
+
+// Right-hand sides of Eq. particle-eom without F_i, with the analytic
+// Kerr-Schild derivatives of alpha, beta^r and gamma^{jk}.
+__device__ __forceinline__ void geo_rhs(double a, double eps, double r, double th, double ur, double ut, double up,
+                                        Rhs &f)
+{
+    double s, c;
+    sincos(th, &s, &c);
+    double a2 = a * a, r2 = r * r;
+    double rho2 = r2 + a2 * c * c;
+    double ir = 1.0 / rho2;
+    double ir2 = ir * ir;
+    double z = 2.0 * r * ir;
+    double iopz = 1.0 / (1.0 + z);
+    double alpha = sqrt(iopz);
+    double beta = z * iopz;
+    double is2 = 1.0 / (s * s);
+    double grr = (a2 + r2) * ir - beta, grp = a * ir, gtt = ir, gpp = ir * is2;
+    double drho_t = -2.0 * a2 * c * s;
+    double dz_r = 2.0 * ir * (1.0 - 2.0 * r2 * ir);
+    double dz_t = -2.0 * r * drho_t * ir2;
+    double ka = -0.5 * alpha * iopz;  // d alpha / dz
+    double kb = iopz * iopz;          // d beta / dz
+    double da_r = ka * dz_r, da_t = ka * dz_t;
+    double db_r = kb * dz_r, db_t = kb * dz_t;
+    double dgrr_r = 2.0 * r * ir - (a2 + r2) * 2.0 * r * ir2 - db_r;
+    double dgrr_t = -(a2 + r2) * drho_t * ir2 - db_t;
+    double dgrp_r = -a * 2.0 * r * ir2, dgrp_t = -a * drho_t * ir2;
+    double dgtt_r = -2.0 * r * ir2, dgtt_t = -drho_t * ir2;
+    double dgpp_r = -2.0 * r * ir2 * is2;
+    double dgpp_t = -drho_t * ir2 * is2 - 2.0 * s * c * ir * is2 * is2;
+
+    double uu = grr * ur * ur + 2.0 * grp * ur * up + gtt * ut * ut + gpp * up * up;
+    double au0 = sqrt(eps + uu);   // alpha u^0
+    double iu0 = alpha / au0;      // 1 / u^0
+    f.xr = (grr * ur + grp * up) * iu0 - beta;
+    f.xt = gtt * ut * iu0;
+    f.xp = (grp * ur + gpp * up) * iu0;
+    double h = 0.5 * iu0;
+    f.ur = -au0 * da_r + ur * db_r - h * (ur * ur * dgrr_r + 2.0 * ur * up * dgrp_r + ut * ut * dgtt_r + up * up * dgpp_r);
+    f.ut = -au0 * da_t + ur * db_t - h * (ur * ur * dgrr_t + 2.0 * ur * up * dgrp_t + ut * ut * dgtt_t + up * up * dgpp_t);
+}
+
+// Generalized Boris step over dt at the particle (u covariant, D, B contravariant)
+__device__ __forceinline__ void boris(double a, double r, double th, double qm, double dt, const double D[3],
+                                      const double B[3], double u[3])
+{
+    KS m;
+    ks_point(a, r, th, m);
+    double Dl0 = m.g_rr * D[0] + m.g_rp * D[2];
+    double Dl1 = m.g_tt * D[1];
+    double Dl2 = m.g_rp * D[0] + m.g_pp * D[2];
+    double h = 0.5 * qm * m.alpha * dt;
+    double um0 = u[0] + h * Dl0, um1 = u[1] + h * Dl1, um2 = u[2] + h * Dl2;
+    // raised u^-
+    double v0 = m.gi_rr * um0 + m.gi_rp * um2, v1 = m.gi_tt * um1, v2 = m.gi_rp * um0 + m.gi_pp * um2;
+    double u0b = sqrt(1.0 + um0 * v0 + um1 * v1 + um2 * v2) / m.alpha;
+    double kt = 0.5 * qm * dt / u0b;
+    double t0 = kt * B[0], t1 = kt * B[1], t2 = kt * B[2];
+    double tt = t0 * (m.g_rr * t0 + m.g_rp * t2) + t1 * (m.g_tt * t1) + t2 * (m.g_rp * t0 + m.g_pp * t2);
+    double ks = 2.0 / (1.0 + tt);
+    double s0 = ks * t0, s1 = ks * t1, s2 = ks * t2;
+    double sg = m.sqrtg;
+    // u~ = u^- + e_ijk v^j t^k
+    double w0 = um0 + sg * (v1 * t2 - v2 * t1);
+    double w1 = um1 + sg * (v2 * t0 - v0 * t2);
+    double w2 = um2 + sg * (v0 * t1 - v1 * t0);
+    double x0 = m.gi_rr * w0 + m.gi_rp * w2, x1 = m.gi_tt * w1, x2 = m.gi_rp * w0 + m.gi_pp * w2;
+    // u^+ = u^- + e_ijk (raised u~)^j s^k, then the second electric half kick
+    u[0] = um0 + sg * (x1 * s2 - x2 * s1) + h * Dl0;
+    u[1] = um1 + sg * (x2 * s0 - x0 * s2) + h * Dl1;
+    u[2] = um2 + sg * (x0 * s1 - x1 * s0) + h * Dl2;
+}
+
+// bilinear weights on a lattice staggered by (sr, st) cells
+struct Stencil {
+    int c0, r0, r1;       // column of the lower corner, the two row indices
+    double w00, w10, w01, w11;
+    double p0, p1;        // parities of the two rows (reflection across the axis)
+};
+
+__device__ __forceinline__ void stencil(const GridDev &g, double x1, double x2, bool half_r, bool half_t, double par,
+                                        Stencil &S)
+{
+    double xi = half_r ? x1 - 0.5 : x1;
+    double fi = floor(xi);
+    int i = (int)fi;
+    double f = xi - fi;
+    int j;
+    double gfr;
+    S.p0 = S.p1 = 1.0;
+    if (half_t) {
+        double eta = x2 - 0.5;
+        double fj = floor(eta);
+        j = (int)fj;
+        gfr = eta - fj;
+        // half-theta rows: -1 mirrors 0, nth mirrors nth-1
+        S.r0 = j;
+        S.r1 = j + 1;
+        if (S.r0 < 0) { S.r0 = -1 - S.r0; S.p0 = par; }
+        if (S.r1 > g.nth - 1) { S.r1 = 2 * g.nth - 1 - S.r1; S.p1 = par; }
+    } else {
+        double fj = floor(x2);
+        j = (int)fj;
+        if (j > g.nth - 1) j = g.nth - 1;
+        gfr = x2 - j;
+        S.r0 = j;
+        S.r1 = j + 1;
+    }
+    S.c0 = i + NG;
+    S.w00 = (1.0 - f) * (1.0 - gfr);
+    S.w10 = f * (1.0 - gfr);
+    S.w01 = (1.0 - f) * gfr;
+    S.w11 = f * gfr;
+}
+
+__device__ __forceinline__ double gather(const double *__restrict__ F, int64_t ld, const Stencil &S)
+{
+    const double *a = F + (size_t)S.r0 * ld + S.c0;
+    const double *b = F + (size_t)S.r1 * ld + S.c0;
+    return S.p0 * (S.w00 * __ldg(a) + S.w10 * __ldg(a + 1)) + S.p1 * (S.w01 * __ldg(b) + S.w11 * __ldg(b + 1));
+}
+
+__device__ __forceinline__ double W1(double d)
+{
+    d = fabs(d);
+    return d < 1.0 ? 1.0 - d : 0.0;
+}
+
+__device__ __forceinline__ int jcell(const GridDev &g, double x2)
+{
+    int j = (int)floor(x2);
+    return j > g.nth - 1 ? g.nth - 1 : j;
+}
+
+constexpr int NWIN = 40;  // 12 J^r A_r + 12 J^theta A_theta + 16 J^phi dV
+
+__global__ void __launch_bounds__(256) push64_kernel(Push64Args A)
+{
+    const GridDev &g = A.g;
+    int64_t n = A.d_count ? *A.d_count : A.n;
+    if (n > A.n) n = A.n;
+    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const unsigned FULL = 0xffffffffu;
+    int lane = threadIdx.x & 31;
+    int ncell = g.nr * g.nth;
+
+    bool live = false;
+    uint32_t tag = DEAD;
+    double r = 0, th = 0, u[3] = {0, 0, 0};
+    if (p < n) {
+        tag = A.tag[p];
+        if (!(tag & DEAD)) {
+            live = true;
+            r = A.r[p];
+            th = A.th[p];
+            u[0] = A.u1[p];
+            u[1] = A.u2[p];
+            u[2] = A.u3[p];
+        }
+    }
+
+    bool dep = false;
+    double win[NWIN];
+    int i0 = 0, j0 = 0, key = -1;
+    if (live) {
+        // a state outside the domain (or non-finite) would index the fields out
+        // of range: refuse it before any gather
+        bool inside = isfinite(r) && isfinite(th) && isfinite(u[0]) && r >= g.r_in && r < g.r_out && th >= 0.0 &&
+                      th <= M_PI;
+        if (!inside) {
+            set_status(A.status, (isfinite(r) && isfinite(th)) ? GRPIC_ERANGE : GRPIC_ENAN);
+            tag |= DEAD;
+            live = false;
+        }
+    }
+    if (live) {
+        int sp = tag & 3u;
+        double x1a = (log(r) - g.ln_rin) / g.dx1, x2a = th / g.dth;
+        if (x1a >= (double)g.nr) x1a = nextafter((double)g.nr, 0.0);  // rounding just below r_out
+        if (x1a < 0.0) x1a = 0.0;
+        if (A.massive[sp] && A.qm[sp] != 0.0) {
+            Stencil Sh0, S0h, S00, Shh;
+            stencil(g, x1a, x2a, true, false, 1.0, Sh0);   // D^r, B^theta
+            stencil(g, x1a, x2a, false, true, -1.0, S0h);  // D^theta (odd across the axis)
+            stencil(g, x1a, x2a, false, false, 1.0, S00);  // D^phi
+            stencil(g, x1a, x2a, true, true, 1.0, Shh);    // B^phi
+            double Dv[3], Bv[3];
+            Dv[0] = gather(A.D0, A.ld, Sh0);
+            Dv[1] = gather(A.D1, A.ld, S0h);
+            Dv[2] = gather(A.D2, A.ld, S00);
+            Bv[1] = gather(A.B1, A.ld, Sh0);
+            Bv[2] = gather(A.B2, A.ld, Shh);
+            S0h.p0 = S0h.p1 = 1.0;  // B^r is even across the axis
+            Bv[0] = gather(A.B0, A.ld, S0h);
+            boris(g.a, r, th, A.qm[sp], A.dt, Dv, Bv, u);
+        }
+        // geodesic predictor-corrector (Sec. 2.2)
+        double eps = A.massive[sp] ? 1.0 : 0.0;
+        Rhs f0, ft;
+        geo_rhs(g.a, eps, r, th, u[0], u[1], u[2], f0);
+        double dt = A.dt;
+        double rt = r + dt * f0.xr, tt = th + dt * f0.xt, pt = dt * f0.xp;
+        double urt = u[0] + dt * f0.ur, utt = u[1] + dt * f0.ut;
+        for (int it = 0; it < A.n_iter; ++it) {
+            geo_rhs(g.a, eps, rt, tt, urt, utt, u[2], ft);
+            double h = 0.5 * dt;
+            rt = r + h * (ft.xr + f0.xr);
+            tt = th + h * (ft.xt + f0.xt);
+            pt = h * (ft.xp + f0.xp);
+            urt = u[0] + h * (ft.ur + f0.ur);
+            utt = u[1] + h * (ft.ut + f0.ut);
+        }
+        // axis reflection
+        if (tt < 0.0) { tt = -tt; utt = -utt; }
+        if (tt > M_PI) { tt = 2.0 * M_PI - tt; utt = -utt; }
+        bool finite = isfinite(rt) && isfinite(tt) && isfinite(pt) && isfinite(urt) && isfinite(utt) && rt > 0.0;
+        if (!finite) {
+            set_status(A.status, GRPIC_ENAN);
+            tag |= DEAD;
+            live = false;
+        } else {
+            double x1b = (log(rt) - g.ln_rin) / g.dx1, x2b = tt / g.dth;
+            i0 = (int)floor(x1a);
+            j0 = jcell(g, x2a);
+            int di = (int)floor(x1b) - i0, dj = jcell(g, x2b) - j0;
+            if (di < -1 || di > 1 || dj < -1 || dj > 1) {
+                set_status(A.status, GRPIC_ERANGE);
+                tag |= DEAD;
+                live = false;
+            } else {
+                // Esirkepov window: columns i0-1..i0+2, rows j0-1..j0+2
+                int sp2 = tag & 3u;
+                double qw = A.qw[sp2];
+                double S0r[4], S1r[4], S0t[4], S1t[4];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    S0r[k] = W1(x1a - (i0 - 1 + k));
+                    S1r[k] = W1(x1b - (i0 - 1 + k));
+                    S0t[k] = W1(x2a - (j0 - 1 + k));
+                    S1t[k] = W1(x2b - (j0 - 1 + k));
+                }
+                double cr = -qw / (2.0 * dt);
+                double cp = qw * pt / dt;
+                double Pr = 0.0;
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    Pr += S1r[k] - S0r[k];
+#pragma unroll
+                    for (int l = 0; l < 4; ++l) win[k * 4 + l] = cr * Pr * (S1t[l] + S0t[l]);
+                }
+                double Pt = 0.0;
+#pragma unroll
+                for (int l = 0; l < 3; ++l) {
+                    Pt += S1t[l] - S0t[l];
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) win[12 + k * 3 + l] = cr * (S1r[k] + S0r[k]) * Pt;
+                }
+#pragma unroll
+                for (int k = 0; k < 4; ++k)
+#pragma unroll
+                    for (int l = 0; l < 4; ++l)
+                        win[24 + k * 4 + l] = cp * (S1r[k] * S1t[l] * (1.0 / 3.0) + S1r[k] * S0t[l] * (1.0 / 6.0) +
+                                                    S0r[k] * S1t[l] * (1.0 / 6.0) + S0r[k] * S0t[l] * (1.0 / 3.0));
+                dep = true;
+                r = rt;
+                th = tt;
+                u[0] = urt;
+                u[1] = utt;
+                if (rt < g.r_in || rt >= g.r_out) tag |= DEAD;
+                key = (tag & DEAD) ? ncell : (jcell(g, x2b) * g.nr + (int)floor(x1b));
+            }
+        }
+    }
+    if (p < n) {
+        if (dep) {
+            A.r[p] = r;
+            A.th[p] = th;
+            A.u1[p] = u[0];
+            A.u2[p] = u[1];
+            A.u3[p] = u[2];
+        }
+        if (tag & DEAD) key = ncell;
+        A.tag[p] = tag;
+        A.keys[p] = key;
+    }
+
+    // ---- deposit: warp-uniform start cell -> shuffle reduction -------------
+    int wkey = dep ? (j0 * g.nr + i0) : -1;
+    unsigned act = __ballot_sync(FULL, dep);
+    if (act) {
+        int ref = __shfl_sync(FULL, wkey, __ffs(act) - 1);
+        bool uniform = __all_sync(FULL, !dep || wkey == ref);
+        if (uniform) {
+            int ri0 = __shfl_sync(FULL, i0, __ffs(act) - 1);
+            int rj0 = __shfl_sync(FULL, j0, __ffs(act) - 1);
+#pragma unroll
+            for (int v = 0; v < NWIN; ++v) {
+                double x = dep ? win[v] : 0.0;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(FULL, x, o);
+                win[v] = x;
+            }
+            if (lane == 0) {
+                i0 = ri0;
+                j0 = rj0;
+                dep = true;
+            } else {
+                dep = false;
+            }
+        }
+        if (dep) {
+#pragma unroll
+            for (int k = 0; k < 3; ++k)
+#pragma unroll
+                for (int l = 0; l < 4; ++l) {
+                    int row = j0 - 1 + l;
+                    double v = win[k * 4 + l];
+                    if (v != 0.0 && row >= 0 && row <= g.nth)
+                        atomicAdd(A.J0 + (size_t)row * A.ld + (i0 - 1 + k + NG), v);
+                }
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+#pragma unroll
+                for (int l = 0; l < 3; ++l) {
+                    int row = j0 - 1 + l;
+                    double v = win[12 + k * 3 + l];
+                    if (v != 0.0 && row >= 0 && row <= g.nth - 1)
+                        atomicAdd(A.J1 + (size_t)row * A.ld + (i0 - 1 + k + NG), v);
+                }
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+#pragma unroll
+                for (int l = 0; l < 4; ++l) {
+                    int row = j0 - 1 + l;
+                    double v = win[24 + k * 4 + l];
+                    if (v != 0.0 && row >= 0 && row <= g.nth)
+                        atomicAdd(A.J2 + (size_t)row * A.ld + (i0 - 1 + k + NG), v);
+                }
+        }
+    }
+
+    // ---- histogram of the new keys (warp-aggregated) -----------------------
+    if (A.histogram) {
+        int hk = (p < n) ? key : -1;
+        unsigned peers = __match_any_sync(FULL, hk);
+        if (hk >= 0 && lane == __ffs(peers) - 1) atomicAdd(A.count + hk, __popc(peers));
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_push64(grpic_ctx *ctx, grpic_particles *p, grpic_fields *f, bool histogram, cudaStream_t s)
+{
+    Push64Args A;
+    A.g = ctx->g;
+    A.dt = ctx->prm.dt;
+    A.n_iter = ctx->prm.n_push_iter;
+    for (int k = 0; k < 4; ++k) {
+        A.qm[k] = ctx->prm.q_over_m[k];
+        A.qw[k] = ctx->prm.q_weight[k];
+        A.massive[k] = ctx->prm.massive[k];
+    }
+    A.n = p->n;
+    A.d_count = p->d_count;
+    A.r = (double *)p->x1;
+    A.th = (double *)p->x2;
+    A.u1 = (double *)p->u1;
+    A.u2 = (double *)p->u2;
+    A.u3 = (double *)p->u3;
+    A.tag = p->tag;
+    A.D0 = (const double *)f->D[0];
+    A.D1 = (const double *)f->D[1];
+    A.D2 = (const double *)f->D[2];
+    A.B0 = (const double *)f->B[0];
+    A.B1 = (const double *)f->B[1];
+    A.B2 = (const double *)f->B[2];
+    A.J0 = (double *)f->J[0];
+    A.J1 = (double *)f->J[1];
+    A.J2 = (double *)f->J[2];
+    A.ld = f->ld;
+    A.keys = ctx->d_keys;
+    A.count = ctx->d_count;
+    A.histogram = histogram ? 1 : 0;
+    A.status = ctx->d_status;
+    if (p->n <= 0) return cudaSuccess;
+    int64_t blocks = (p->n + 255) / 256;
+    push64_kernel<<<(unsigned)blocks, 256, 0, s>>>(A);
+    return cudaGetLastError();
+}
+
+}  // namespace grpic

@@ -1,0 +1,352 @@
+"""Thin ctypes binding of libgrpic (include/grpic.h).
+
+Argument marshalling only: every step of the time step runs in the CUDA
+kernels of the library.  torch tensors provide the device memory and the
+stream.  Importing this module does not need a GPU; loading the library does,
+and every call fails loudly (RuntimeError) if the library is missing.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+import os
+from dataclasses import dataclass
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_lib", "libgrpic.so")
+
+OK, EINVAL, ENOMEM, ECUDA, ERANGE, ENAN, EOVERFLOW, ECONVERGE, ETIMEOUT = range(9)
+STATUS_NAMES = ["OK", "EINVAL", "ENOMEM", "ECUDA", "ERANGE", "ENAN", "EOVERFLOW", "ECONVERGE", "ETIMEOUT"]
+WALD, WALD_A0, MONOPOLE, SPLIT_MONOPOLE = 0, 1, 2, 3
+DEAD = 0x80000000
+NG = 2
+
+# names the header declares (checked by the CPU test of the boundary)
+EXPORTS = ["grpic_init", "grpic_init_fields", "grpic_push", "grpic_deposit", "grpic_field_update", "grpic_sort",
+           "grpic_step", "grpic_diagnostics", "grpic_get_areas", "grpic_sync", "grpic_last_error", "grpic_destroy"]
+
+
+class Grid(C.Structure):
+    _fields_ = [("n_r", C.c_int32), ("n_theta", C.c_int32), ("r_in", C.c_double), ("r_out", C.c_double),
+                ("damp_cells", C.c_int32), ("damp_max", C.c_double)]
+
+
+class Params(C.Structure):
+    _fields_ = [("dt", C.c_double), ("beta_field", C.c_double), ("n_field_iter", C.c_int32),
+                ("n_push_iter", C.c_int32), ("q_over_m", C.c_double * 4), ("q_weight", C.c_double * 4),
+                ("massive", C.c_int32 * 4), ("precision", C.c_int32), ("sort_every", C.c_int32),
+                ("fp64_radius", C.c_double)]
+
+
+class ParticlesC(C.Structure):
+    _fields_ = [("n", C.c_int64), ("capacity", C.c_int64), ("d_count", C.c_void_p),
+                ("x1", C.c_void_p), ("x2", C.c_void_p), ("u1", C.c_void_p), ("u2", C.c_void_p),
+                ("u3", C.c_void_p), ("tag", C.c_void_p), ("cell", C.c_void_p)]
+
+
+class FieldsC(C.Structure):
+    _fields_ = [("D", C.c_void_p * 3), ("B", C.c_void_p * 3), ("J", C.c_void_p * 3), ("ld", C.c_int64)]
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libgrpic.so; raise if it has not been built."""
+    global _lib
+    if _lib is not None and path == LIB_PATH:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"libgrpic.so not found at {path}: build it with __graft_entry__.build()")
+    lib = C.CDLL(path)
+    v, p, i, d, i64 = C.c_void_p, C.POINTER, C.c_int, C.c_double, C.c_int64
+    sig = {
+        "grpic_init": [i, d, p(Grid), p(Params), p(v)],
+        "grpic_init_fields": [v, i, d, p(FieldsC), v],
+        "grpic_push": [v, p(ParticlesC), p(FieldsC), v],
+        "grpic_deposit": [v, p(ParticlesC), p(ParticlesC), v, p(FieldsC), v],
+        "grpic_field_update": [v, p(FieldsC), v],
+        "grpic_sort": [v, p(ParticlesC), p(ParticlesC), v],
+        "grpic_step": [v, p(ParticlesC), p(ParticlesC), p(FieldsC), i, v],
+        "grpic_diagnostics": [v, p(ParticlesC), p(FieldsC), v, v, v],
+        "grpic_get_areas": [v, v * 6, i64, v],
+        "grpic_sync": [v, v],
+    }
+    for name, args in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = C.c_int
+    lib.grpic_last_error.argtypes = [v]
+    lib.grpic_last_error.restype = C.c_char_p
+    lib.grpic_destroy.argtypes = [v]
+    lib.grpic_destroy.restype = None
+    if path == LIB_PATH:
+        _lib = lib
+    return lib
+
+
+class GrpicError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES[status] if 0 <= status < len(STATUS_NAMES) else status}: {msg}")
+        self.status = status
+
+
+def horizon(a: float) -> float:
+    return 1.0 + math.sqrt(1.0 - a * a)
+
+
+@dataclass
+class Config:
+    """Grid + solver settings of one run.  dt defaults to
+    cfl * min(dr, r dtheta) at r_in."""
+    n_r: int
+    n_theta: int
+    a: float
+    r_in: float
+    r_out: float
+    dt: float | None = None
+    cfl: float = 0.5
+    beta_field: float = 0.53
+    n_field_iter: int = 7
+    n_push_iter: int = 3
+    damp_cells: int | None = None
+    damp_max: float = 0.1
+    q_over_m: tuple = (-1.0, 1.0, 1.0, 0.0)
+    q_weight: tuple = (-1e-3, 1e-3, 1e-3, 0.0)
+    massive: tuple = (1, 1, 1, 0)
+    precision: int = 64
+    sort_every: int = 1
+    fp64_radius: float = 0.0
+
+    def __post_init__(self):
+        self.dx1 = math.log(self.r_out / self.r_in) / self.n_r
+        self.dth = math.pi / self.n_theta
+        if self.dt is None:
+            dr = self.r_in * (math.exp(self.dx1) - 1.0)
+            self.dt = self.cfl * min(dr, self.r_in * self.dth)
+        if self.damp_cells is None:
+            self.damp_cells = max(8, self.n_r // 32)
+        self.ld = self.n_r + 2 * NG
+
+    def grid_c(self):
+        return Grid(self.n_r, self.n_theta, self.r_in, self.r_out, self.damp_cells, self.damp_max)
+
+    def params_c(self):
+        p = Params()
+        p.dt, p.beta_field = self.dt, self.beta_field
+        p.n_field_iter, p.n_push_iter = self.n_field_iter, self.n_push_iter
+        for k in range(4):
+            p.q_over_m[k], p.q_weight[k], p.massive[k] = self.q_over_m[k], self.q_weight[k], self.massive[k]
+        p.precision, p.sort_every, p.fp64_radius = self.precision, self.sort_every, self.fp64_radius
+        return p
+
+
+def _ptr(t):
+    return C.c_void_p(t.data_ptr()) if t is not None else C.c_void_p(0)
+
+
+def _stream(stream=None):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+class Fields:
+    """D, B, J on the device as (n_theta+1, ld) tensors of the run's precision."""
+
+    def __init__(self, cfg: Config, device="cuda", ld=None):
+        import torch
+        dt = torch.float64 if cfg.precision == 64 else torch.float32
+        self.ld = ld or cfg.ld
+        shape = (cfg.n_theta + 1, self.ld)
+        self.D = [torch.zeros(shape, dtype=dt, device=device) for _ in range(3)]
+        self.B = [torch.zeros(shape, dtype=dt, device=device) for _ in range(3)]
+        self.J = [torch.zeros(shape, dtype=dt, device=device) for _ in range(3)]
+
+    def c(self):
+        f = FieldsC()
+        for k in range(3):
+            f.D[k] = self.D[k].data_ptr()
+            f.B[k] = self.B[k].data_ptr()
+            f.J[k] = self.J[k].data_ptr()
+        f.ld = self.ld
+        return f
+
+
+class Particles:
+    """Structure-of-arrays particle buffer (one of the two sort buffers)."""
+
+    def __init__(self, cfg: Config, capacity: int, device="cuda"):
+        import torch
+        fdt = torch.float64 if cfg.precision == 64 else torch.float32
+        cap = max(int(capacity), 1)
+        self.capacity = cap
+        self.x1 = torch.zeros(cap, dtype=fdt, device=device)
+        self.x2 = torch.zeros(cap, dtype=fdt, device=device)
+        self.u1 = torch.zeros(cap, dtype=fdt, device=device)
+        self.u2 = torch.zeros(cap, dtype=fdt, device=device)
+        self.u3 = torch.zeros(cap, dtype=fdt, device=device)
+        self.tag = torch.full((cap,), DEAD, dtype=torch.int64, device=device).to(torch.int32)
+        self.cell = torch.zeros(cap, dtype=torch.int32, device=device) if cfg.precision == 32 else None
+
+    def arrays(self):
+        return [self.x1, self.x2, self.u1, self.u2, self.u3, self.tag, self.cell]
+
+
+class ParticleSet:
+    """Two particle buffers (sort ping-pong), the live count on the device and
+    the C struct the library sees."""
+
+    def __init__(self, cfg: Config, capacity: int, device="cuda"):
+        import torch
+        self.cfg = cfg
+        self.a = Particles(cfg, capacity, device)
+        self.b = Particles(cfg, capacity, device)
+        self.count = torch.zeros(1, dtype=torch.int64, device=device)
+        self.n = 0
+        self._sc = self._struct(self.a)
+        self._ss = self._struct(self.b)
+
+    def _struct(self, P):
+        s = ParticlesC()
+        s.n = self.n
+        s.capacity = P.capacity
+        s.d_count = self.count.data_ptr()
+        s.x1, s.x2, s.u1, s.u2, s.u3 = (t.data_ptr() for t in (P.x1, P.x2, P.u1, P.u2, P.u3))
+        s.tag = P.tag.data_ptr()
+        s.cell = P.cell.data_ptr() if P.cell is not None else 0
+        return s
+
+    def load(self, x1, x2, u1, u2, u3, tag, cell=None):
+        """Copy host or device arrays into the current buffer; n = len(x1)."""
+        import torch
+        n = int(len(x1))
+        if n > self.a.capacity:
+            raise ValueError("capacity exceeded")
+        dev = self.a.x1.device
+        self.a.x1[:n].copy_(torch.as_tensor(x1).to(dev))
+        self.a.x2[:n].copy_(torch.as_tensor(x2).to(dev))
+        self.a.u1[:n].copy_(torch.as_tensor(u1).to(dev))
+        self.a.u2[:n].copy_(torch.as_tensor(u2).to(dev))
+        self.a.u3[:n].copy_(torch.as_tensor(u3).to(dev))
+        t = torch.as_tensor(tag)
+        if t.dtype != torch.int32:
+            t = t.to(torch.int64).to(torch.int32) if t.dtype != torch.uint32 else t.view(torch.int32)
+        self.a.tag[:n].copy_(t.to(dev))
+        if cell is not None:
+            self.a.cell[:n].copy_(torch.as_tensor(cell).to(dev))
+        self.a.tag[n:].fill_(DEAD - (1 << 32))
+        self.n = n
+        self.count.fill_(n)
+        self._sc = self._struct(self.a)
+        self._ss = self._struct(self.b)
+
+    def sync_ptrs(self):
+        """After the library swapped the array pointers, swap the Python buffers too."""
+        if self._sc.x1 != self.a.x1.data_ptr():
+            self.a, self.b = self.b, self.a
+
+    def live(self) -> int:
+        return int(self.count.item())
+
+    def host(self):
+        """Live particles as numpy arrays (synchronizes)."""
+        n = self.live()
+        out = {k: getattr(self.a, k)[:n].cpu().numpy() for k in ("x1", "x2", "u1", "u2", "u3")}
+        out["tag"] = self.a.tag[:n].cpu().numpy().view("uint32")
+        if self.a.cell is not None:
+            out["cell"] = self.a.cell[:n].cpu().numpy()
+        return out
+
+
+class Context:
+    """Owns one grpic_ctx (tables + scratch) for a Config."""
+
+    def __init__(self, cfg: Config):
+        import torch
+        torch.cuda.current_device()
+        self.lib = load()
+        self.cfg = cfg
+        self._g = cfg.grid_c()
+        self._p = cfg.params_c()
+        h = C.c_void_p()
+        st = self.lib.grpic_init(0, cfg.a, C.byref(self._g), C.byref(self._p), C.byref(h))
+        if st != OK:
+            raise GrpicError(st, "grpic_init failed")
+        self.h = h
+
+    def _check(self, st, what):
+        if st != OK:
+            msg = self.lib.grpic_last_error(self.h)
+            raise GrpicError(st, f"{what}: {msg.decode() if msg else ''}")
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.grpic_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # --- entry points -----------------------------------------------------
+    def init_fields(self, F: Fields, kind=WALD, B0=1.0, stream=None):
+        fc = F.c()
+        self._check(self.lib.grpic_init_fields(self.h, kind, B0, C.byref(fc), _stream(stream)), "grpic_init_fields")
+
+    def push(self, P: ParticleSet, F: Fields, stream=None):
+        P._sc.n = P.n
+        fc = F.c()
+        self._check(self.lib.grpic_push(self.h, C.byref(P._sc), C.byref(fc), _stream(stream)), "grpic_push")
+
+    def deposit(self, before: ParticleSet, after: ParticleSet, dphi, F: Fields, stream=None):
+        fc = F.c()
+        before._sc.n = before.n
+        after._sc.n = after.n
+        self._check(self.lib.grpic_deposit(self.h, C.byref(before._sc), C.byref(after._sc), _ptr(dphi), C.byref(fc),
+                                           _stream(stream)), "grpic_deposit")
+
+    def field_update(self, F: Fields, stream=None):
+        fc = F.c()
+        self._check(self.lib.grpic_field_update(self.h, C.byref(fc), _stream(stream)), "grpic_field_update")
+
+    def sort(self, P: ParticleSet, stream=None):
+        P._sc.n = P.n
+        P._ss.n = P.n
+        self._check(self.lib.grpic_sort(self.h, C.byref(P._sc), C.byref(P._ss), _stream(stream)), "grpic_sort")
+        P.sync_ptrs()
+
+    def step(self, P: ParticleSet, F: Fields, nsteps=1, stream=None):
+        P._sc.n = P.n
+        P._ss.n = P.n
+        fc = F.c()
+        self._check(self.lib.grpic_step(self.h, C.byref(P._sc), C.byref(P._ss), C.byref(fc), nsteps,
+                                        _stream(stream)), "grpic_step")
+        P.sync_ptrs()
+
+    def diagnostics(self, P: ParticleSet | None, F: Fields, stream=None):
+        import torch
+        dt = torch.float64 if self.cfg.precision == 64 else torch.float32
+        shape = (self.cfg.n_theta + 1, F.ld)
+        rho = torch.zeros(shape, dtype=dt, device=F.D[0].device) if P is not None else None
+        div = torch.zeros(shape, dtype=dt, device=F.D[0].device)
+        if P is not None:
+            P._sc.n = P.n
+        fc = F.c()
+        self._check(self.lib.grpic_diagnostics(self.h, C.byref(P._sc) if P is not None else None, C.byref(fc),
+                                               _ptr(rho), _ptr(div), _stream(stream)), "grpic_diagnostics")
+        return rho, div
+
+    def areas(self, stream=None):
+        import torch
+        ld = self.cfg.ld
+        out = [torch.zeros((self.cfg.n_theta + 1, ld), dtype=torch.float64, device="cuda") for _ in range(6)]
+        arr = (C.c_void_p * 6)(*[t.data_ptr() for t in out])
+        self._check(self.lib.grpic_get_areas(self.h, arr, ld, _stream(stream)), "grpic_get_areas")
+        return out
+
+    def sync(self, stream=None) -> int:
+        """Wait for the stream and return (and clear) the device status."""
+        return self.lib.grpic_sync(self.h, _stream(stream))

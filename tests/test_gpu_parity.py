@@ -1,0 +1,299 @@
+"""GPU parity of the FP64 CUDA path against the FP64 oracle, through the C ABI.
+
+Bar (element by element on the same seeded inputs): cell indices and sort
+order bit-exact; FP64 fields, currents and momenta within 1e-10 relative
+(max-norm per array); charge-conservation residual below 1e-12 of max|rho|."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from gpu_common import configs, relerr, flux_form, logical
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+A09 = 0.9
+RH = 1.0 + math.sqrt(1 - A09 * A09)
+TOL = 1e-10
+
+
+@pytest.fixture(scope="module")
+def G():
+    from paper_2503_04558_gb300 import build, grpic
+    build.build()
+    grpic.load()
+    return grpic
+
+
+def gpu_fields(G, gc, kind=O.WALD, B0=1.0):
+    ctx = G.Context(gc)
+    F = G.Fields(gc)
+    ctx.init_fields(F, kind, B0)
+    return ctx, F
+
+
+def host(t):
+    return t.detach().cpu().numpy()
+
+
+def test_tables_match_oracle(G):
+    oc, gc = configs(40, 36, A09, 0.9 * RH, 30.0)
+    ctx = G.Context(gc)
+    got = [host(t) for t in ctx.areas()]
+    AD, AB = O.areas(oc)
+    for k, ref in enumerate(AD + AB):
+        assert relerr(got[k], ref) < 1e-13, k
+
+
+@pytest.mark.parametrize("kind", [O.WALD, O.WALD_A0, O.MONOPOLE, O.SPLIT_MONOPOLE])
+def test_init_fields_match_oracle(G, kind):
+    oc, gc = configs(48, 40, A09, 0.9 * RH, 40.0)
+    ctx, F = gpu_fields(G, gc, kind, 1.3)
+    D, B = O.init_fields(oc, kind, 1.3)
+    for k in range(3):
+        assert relerr(host(F.D[k]), D[k]) < 1e-12, ("D", k)
+        assert relerr(host(F.B[k]), B[k]) < 1e-12, ("B", k)
+
+
+@pytest.mark.parametrize("damp", [0.0, 0.1])
+def test_field_update_matches_oracle(G, damp):
+    oc, gc = configs(40, 32, A09, 0.9 * RH, 30.0, damp_max=damp)
+    ctx, F = gpu_fields(G, gc, O.WALD_A0, 1.0)
+    D, B = O.init_fields(oc, O.WALD_A0, 1.0)
+    rng = np.random.default_rng(5)
+    Jd = [rng.normal(size=O.field_shape(oc)) * 0.05 for _ in range(3)]
+    Jf = flux_form(oc, Jd)
+    for k in range(3):
+        F.J[k].copy_(torch.from_numpy(Jf[k]))
+    for _ in range(3):
+        ctx.field_update(F)
+        O.field_update(oc, D, B, Jd)
+    assert ctx.sync() == 0
+    for k in range(3):
+        assert relerr(host(F.D[k]), D[k]) < 1e-12, ("D", k)
+        assert relerr(host(F.B[k]), B[k]) < 1e-12, ("B", k)
+
+
+def make_particles(oc, n, seed=0, sigma=0.1):
+    from paper_2503_04558_gb300 import synth
+    return O.Particles(*synth.particles(oc.nr, oc.nth, oc.r_in, oc.r_out, n, seed=seed, sigma=sigma))
+
+
+def load_set(G, gc, P):
+    S = G.ParticleSet(gc, P.n + 16)
+    S.load(P.r, P.th, P.u1, P.u2, P.u3, P.tag)
+    return S
+
+
+def test_push_deposit_matches_oracle(G):
+    oc, gc = configs(32, 32, A09, 0.9 * RH, 20.0, qw=(-0.01, 0.01, 0.01, 0.0))
+    ctx, F = gpu_fields(G, gc, O.WALD, 2.0)
+    D, B = O.init_fields(oc, O.WALD, 2.0)
+    P = make_particles(oc, 20000, seed=3, sigma=0.5)
+    S = load_set(G, gc, P)
+    ctx.push(S, F)
+    assert ctx.sync() == 0
+    st, J, _ = O.push_deposit(oc, P, D, B)
+    assert st == 0
+    h = S.host()
+    assert np.array_equal(h["tag"], P.tag)
+    for k, ref in zip(("x1", "x2", "u1", "u2", "u3"), (P.r, P.th, P.u1, P.u2, P.u3)):
+        assert relerr(h[k], ref) < 1e-12, k
+    for k, ref in enumerate(flux_form(oc, J)):
+        assert relerr(host(F.J[k]), ref) < 1e-11, ("J", k)
+
+
+def test_sort_is_bit_exact(G):
+    """grpic_sort only moves data: on shuffled particles its output must equal
+    the oracle's stable counting sort bit for bit (dead particles dropped)."""
+    oc, gc = configs(24, 20, A09, 0.9 * RH, 20.0)
+    ctx = G.Context(gc)
+    P = make_particles(oc, 9000, seed=9)
+    rng = np.random.default_rng(1)
+    P = P.take(rng.permutation(P.n))
+    P.tag[::97] |= O.DEAD
+    S = load_set(G, gc, P)
+    ctx.sort(S)
+    assert ctx.sync() == 0
+    Q = O.sort(oc, P)
+    h = S.host()
+    assert S.live() == Q.n
+    for k, ref in zip(("x1", "x2", "u1", "u2", "u3", "tag"), (Q.r, Q.th, Q.u1, Q.u2, Q.u3, Q.tag)):
+        assert np.array_equal(h[k], ref), k
+
+
+def charge_residual(G, ctx, S, F, rho0_div0, oc):
+    rho, div = ctx.diagnostics(S, F)
+    res = host(div) - host(rho) - rho0_div0
+    last = oc.nr - oc.damp_cells - 1
+    sl = (slice(0, oc.nth + 1), slice(oc.ng + 1, oc.ng + last + 1))
+    return float(np.max(np.abs(res[sl]))), float(np.max(np.abs(host(rho)[sl])))
+
+
+@pytest.fixture(scope="module")
+def config1(G):
+    """Config 1: 128 x 128, a = 0.9, r in [0.9 r_H, 50], rotating Wald B0 = 1,
+    2e5 e+/e- uniform per cell (seed 0), Gaussian u sigma = 0.1, CFL 0.5,
+    20 steps, sort every step; GPU and oracle side by side."""
+    oc, gc = configs(128, 128, A09, 0.9 * RH, 50.0)
+    ctx, F = gpu_fields(G, gc, O.WALD, 1.0)
+    D, B = O.init_fields(oc, O.WALD, 1.0)
+    P = make_particles(oc, 200000, seed=0, sigma=0.1)
+    S = load_set(G, gc, P)
+    rho0, div0 = ctx.diagnostics(S, F)
+    base = host(div0) - host(rho0)
+    worst = 0.0
+    for step in range(20):
+        ctx.step(S, F, 1)
+        st, P, J = O.step(oc, P, D, B)
+        assert st == 0
+        res, rmax = charge_residual(G, ctx, S, F, base, oc)
+        worst = max(worst, res / rmax)
+    assert ctx.sync() == 0
+    return dict(oc=oc, ctx=ctx, F=F, S=S, P=P, D=D, B=B, charge=worst)
+
+
+def test_config1_fields_after_20_steps(config1):
+    c = config1
+    for k in range(3):
+        assert relerr(host(c["F"].D[k]), c["D"][k]) < TOL, ("D", k)
+        assert relerr(host(c["F"].B[k]), c["B"][k]) < TOL, ("B", k)
+
+
+def test_config1_particles_after_20_steps(config1):
+    c = config1
+    P, oc = c["P"], c["oc"]
+    h = c["S"].host()
+    assert len(h["x1"]) == P.n
+    # cell indices bit-exact (particles within 1e-13 of a face excluded and counted)
+    x1g, x2g = logical(oc, h["x1"], h["x2"])
+    x1o, x2o = logical(oc, P.r, P.th)
+    near = (np.abs(x1o - np.round(x1o)) < 1e-13) | (np.abs(x2o - np.round(x2o)) < 1e-13)
+    assert near.sum() == 0
+    kg = np.floor(x2g).astype(int) * oc.nr + np.floor(x1g).astype(int)
+    ko = np.floor(x2o).astype(int) * oc.nr + np.floor(x1o).astype(int)
+    assert np.array_equal(kg, ko)
+    assert np.array_equal(h["tag"], P.tag)
+    for k, ref in zip(("x1", "x2", "u1", "u2", "u3"), (P.r, P.th, P.u1, P.u2, P.u3)):
+        assert relerr(h[k], ref) < TOL, k
+
+
+def test_config1_charge_conservation(config1):
+    assert config1["charge"] < 1e-12, config1["charge"]
+
+
+# ---------------------------------------------------------------------------
+# edge cases
+# ---------------------------------------------------------------------------
+def run_one(G, oc, gc, P, kind=O.WALD, B0=1.0):
+    ctx, F = gpu_fields(G, gc, kind, B0)
+    D, B = O.init_fields(oc, kind, B0)
+    S = load_set(G, gc, P)
+    ctx.push(S, F)
+    st_g = ctx.sync()
+    Q = P.copy()
+    st_o, J, _ = O.push_deposit(oc, Q, D, B)
+    return ctx, F, S, Q, J, st_g, st_o
+
+
+def test_zero_particles(G):
+    oc, gc = configs(16, 16, A09, 0.9 * RH, 20.0)
+    ctx, F = gpu_fields(G, gc)
+    S = G.ParticleSet(gc, 8)
+    ctx.step(S, F, 2)
+    assert ctx.sync() == 0
+    assert S.live() == 0
+
+
+def single(oc, r, th, u, sp=1):
+    return O.Particles(np.array([r]), np.array([th]), np.array([u[0]]), np.array([u[1]]), np.array([u[2]]),
+                       np.array([sp], np.uint32))
+
+
+@pytest.mark.parametrize("name,x1,x2,u", [
+    ("interior", 5.3, 7.6, (0.3, 0.5, 1.0)),
+    ("on_r_face", 6.0, 7.5, (0.0, 0.0, 0.0)),
+    ("on_theta_face", 6.4, 8.0, (0.1, -0.2, 0.3)),
+    ("crosses_axis", 9.5, 0.05, (0.0, -40.0, 0.0)),
+    ("crosses_pi", 9.5, 15.85, (0.0, 40.0, 0.0)),
+    ("leaves_inner", 0.05, 8.0, (-3.0, 0.0, 0.0)),
+    ("leaves_outer", 15.99, 8.0, (30.0, 0.0, 0.0)),
+])
+def test_single_particle_edge_cases(G, name, x1, x2, u):
+    oc, gc = configs(16, 16, A09, 0.9 * RH, 20.0, qw=(-0.1, 0.1, 0.1, 0.0))
+    r = oc.r_in * math.exp(x1 * oc.dx1)
+    th = x2 * oc.dth
+    P = single(oc, r, th, (u[0], u[1] * r, u[2] * r))
+    ctx, F, S, Q, J, st_g, st_o = run_one(G, oc, gc, P)
+    assert st_g == st_o == 0
+    h = S.host() if S.live() else None
+    g_tag = int(S.a.tag[0].item()) & 0xFFFFFFFF
+    assert g_tag == int(Q.tag[0])
+    gr = S.a.x1[:1].cpu().numpy()
+    assert relerr(gr, Q.r) < 1e-13
+    assert relerr(S.a.u2[:1].cpu().numpy(), Q.u2) < 1e-12
+    for k, ref in enumerate(flux_form(oc, J)):
+        assert relerr(host(F.J[k]), ref) < 1e-12, ("J", k)
+    if name == "crosses_axis":
+        assert Q.th[0] >= 0 and Q.u2[0] > 0
+    if name.startswith("leaves"):
+        assert (Q.tag[0] & O.DEAD) != 0
+    del h
+
+
+def test_nan_input_sets_status(G):
+    from paper_2503_04558_gb300 import grpic as GG
+    oc, gc = configs(16, 16, A09, 0.9 * RH, 20.0)
+    P = single(oc, 3.0, 1.0, (float("nan"), 0.0, 0.0))
+    ctx, F = gpu_fields(G, gc)
+    S = load_set(G, gc, P)
+    ctx.push(S, F)
+    assert ctx.sync() == GG.ENAN
+    assert int(S.a.tag[0].item()) & 0xFFFFFFFF & O.DEAD
+    assert ctx.sync() == 0  # status cleared after being read
+
+
+def test_too_fast_particle_sets_range_status(G):
+    """With a time step 20x the CFL limit a light-speed particle crosses more
+    than one cell: the move is refused, the particle flagged dead, no current."""
+    from paper_2503_04558_gb300 import grpic as GG
+    oc0, _ = configs(16, 16, A09, 0.9 * RH, 20.0)
+    oc, gc = configs(16, 16, A09, 0.9 * RH, 20.0, dt=20 * oc0.dt)
+    P = single(oc, 2.0, 1.0, (1e4, 0.0, 0.0))
+    ctx, F = gpu_fields(G, gc)
+    S = load_set(G, gc, P)
+    ctx.push(S, F)
+    assert ctx.sync() == GG.ERANGE
+    assert np.all(host(F.J[0]) == 0)
+
+
+def test_invalid_arguments_are_rejected(G):
+    from paper_2503_04558_gb300 import grpic as GG
+    with pytest.raises(GG.GrpicError):
+        GG.Context(GG.Config(16, 15, 0.9, 1.3, 20.0))     # odd n_theta
+    with pytest.raises(GG.GrpicError):
+        GG.Context(GG.Config(16, 16, 1.0, 1.3, 20.0))     # a = 1
+    oc, gc = configs(16, 16, A09, 0.9 * RH, 20.0)
+    ctx = GG.Context(gc)
+    S = GG.ParticleSet(gc, 8)
+    S.n = 4
+    S._ss.capacity = 2   # scratch smaller than the particle count
+    S._sc.n = 4
+    import ctypes as C
+    st = ctx.lib.grpic_sort(ctx.h, C.byref(S._sc), C.byref(S._ss), None)
+    assert st == GG.EINVAL
+
+
+def test_photons_follow_geodesics_without_deposit(G):
+    oc, gc = configs(16, 16, A09, 0.9 * RH, 20.0)
+    P = make_particles(oc, 400, seed=4, sigma=0.5)
+    P.tag[:] = 3   # photons: massless, no charge, no Boris step
+    ctx, F, S, Q, J, st_g, st_o = run_one(G, oc, gc, P)
+    assert st_g == st_o == 0
+    h = S.host()
+    for k, ref in zip(("x1", "x2", "u1", "u2", "u3"), (Q.r, Q.th, Q.u1, Q.u2, Q.u3)):
+        assert relerr(h[k], ref) < 1e-12, k
+    for k in range(3):
+        assert np.all(host(F.J[k]) == 0)
