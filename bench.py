@@ -133,11 +133,11 @@ def run_ours(args, rank, world):
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
     torch.cuda.set_device(dev)
     prec = args.precision
-    cfg = workload_config(prec)
+    cfg = workload_config(prec, args.grid, args.grid)
     ctx = G.Context(cfg)
     F = G.Fields(cfg)
     ctx.init_fields(F, G.SPLIT_MONOPOLE, B0)
-    n = cfg.n_r * cfg.n_theta * PPC
+    n = cfg.n_r * cfg.n_theta * args.ppc
     S = G.ParticleSet(cfg, n)
     gen = synth.particles_torch(cfg.n_r, cfg.n_theta, cfg.r_in, cfg.r_out, n, seed=1234 + rank,
                                 thermal_T=THERMAL_T, device=dev)
@@ -315,6 +315,8 @@ def main():
     ap.add_argument("--precision", type=int, default=64, choices=[64, 32])
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--grid", type=int, default=NR, help="cells per dimension (profiling runs use smaller grids)")
+    ap.add_argument("--ppc", type=int, default=PPC, help="particles per cell")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
@@ -359,9 +361,9 @@ def main():
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f64" if args.precision == 64 else "f32", "data": "synthetic",
-                "config": {"workload": "GRPIC step (push+deposit, field update 1+7 stages, sort), 2048x2048 "
-                                       "log-r x theta, a=0.99, r in [0.9 r_H, 100], split monopole, 100 ppc, thermal "
-                                       "T=0.3, FP%d" % args.precision,
+                "config": {"workload": "GRPIC step (push+deposit, field update 1+7 stages, sort), %dx%d "
+                                       "log-r x theta, a=0.99, r in [0.9 r_H, 100], split monopole, %d ppc, thermal "
+                                       "T=0.3, FP%d" % (args.grid, args.grid, args.ppc, args.precision),
                            "particles": n, "cells": cells, "parallelism": f"replicas x{world}",
                            "l2": "inputs larger than L2 (particle state %.1f GB)" % (n * (5 * esz + 4) / 1e9)},
                 "push_deposit_per_s": world * n / (push_ms * 1e-3),

@@ -94,7 +94,10 @@ typedef struct {
  * in the Lorentz force, q_weight[s] the macro charge q*w deposited, massive[s]
  * the epsilon of u^0 (1 massive, 0 photon: no Boris step, Sec. 2.2).
  * precision: 64 (FP64 path) or 32 (FP32 form).  fp64_radius: in the FP32 form,
- * metric evaluations at r < fp64_radius run in FP64 (<= 0: never). */
+ * metric evaluations of particles in cells whose inner edge lies below
+ * fp64_radius run in FP64 (<= 0: never).  push_tol: in the FP32 form, the geodesic corrector stops
+ * once the FP64-measured change of the iterate falls below push_tol (<= 0:
+ * always n_push_iter correctors); the FP64 path always runs n_push_iter. */
 typedef struct {
     double dt;
     double beta_field;
@@ -106,6 +109,7 @@ typedef struct {
     int32_t precision;
     int32_t sort_every;
     double fp64_radius;
+    double push_tol;
 } grpic_params;
 
 typedef struct {

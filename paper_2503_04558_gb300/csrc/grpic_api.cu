@@ -217,6 +217,15 @@ grpic_status grpic_init(grpic_metric metric, double spin, const grpic_grid *grid
     if (e == cudaSuccess) e = cudaMalloc(&ctx->d_cursor, sizeof(int32_t) * (ncell + 3));
     if (e == cudaSuccess) e = cudaMalloc(&ctx->d_blocksum, sizeof(int32_t) * 8192);
     if (e == cudaSuccess) e = cudaMalloc(&ctx->d_bigseg, sizeof(int32_t) * (ncell + 1));
+    if (e == cudaSuccess) {
+        e = cudaMalloc(&ctx->rcol, sizeof(double) * g.ld_tab);
+        if (e == cudaSuccess) {
+            double *h = (double *)malloc(sizeof(double) * g.ld_tab);
+            for (int c = 0; c < g.ld_tab; ++c) h[c] = g.r_in * std::exp((c - NG) * g.dx1);
+            e = cudaMemcpy(ctx->rcol, h, sizeof(double) * g.ld_tab, cudaMemcpyHostToDevice);
+            free(h);
+        }
+    }
     if (e != cudaSuccess) {
         grpic_destroy(ctx);
         return GRPIC_ENOMEM;
@@ -359,7 +368,7 @@ const char *grpic_last_error(const grpic_ctx *ctx) { return ctx ? ctx->err : "nu
 void grpic_destroy(grpic_ctx *ctx)
 {
     if (!ctx) return;
-    void *ptrs[] = {ctx->tab, ctx->col1d, ctx->tab32, ctx->col1d32, ctx->fscratch, ctx->d_status, ctx->d_keys,
+    void *ptrs[] = {ctx->rcol, ctx->tab, ctx->col1d, ctx->tab32, ctx->col1d32, ctx->fscratch, ctx->d_status, ctx->d_keys,
                     ctx->d_count, ctx->d_offset, ctx->d_cursor, ctx->d_blocksum, ctx->d_perm, ctx->d_bigseg};
     for (void *q : ptrs)
         if (q) cudaFree(q);

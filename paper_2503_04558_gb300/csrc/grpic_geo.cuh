@@ -1,0 +1,94 @@
+// grpic_geo.cuh -- Kerr-Schild metric pieces needed by the pusher, templated
+// on the arithmetic type (double for the FP64 path and the FP64 islands of the
+// FP32 form, float for the FP32 form).
+//
+// KSGeo holds alpha, beta^r, gamma^{ij} and their analytic r and theta
+// derivatives (App. A, Eqs. gamma-inverse, ks-alpha-beta); geo_rhs assembles
+// the right-hand sides X^i, U_i of Eq. particle-eom (without the Lorentz force).
+#pragma once
+
+#include "grpic_internal.cuh"
+
+namespace grpic {
+
+template <typename T>
+struct KSGeo {
+    T alpha, beta, grr, grp, gtt, gpp;
+    T da_r, da_t, db_r, db_t;
+    T dgrr_r, dgrr_t, dgrp_r, dgrp_t, dgtt_r, dgtt_t, dgpp_r, dgpp_t;
+};
+
+template <typename T>
+struct RhsT {
+    T xr, xt, xp, ur, ut;
+};
+
+__device__ __forceinline__ void sincos_t(double x, double *s, double *c) { sincos(x, s, c); }
+__device__ __forceinline__ void sincos_t(float x, float *s, float *c) { sincosf(x, s, c); }
+__device__ __forceinline__ double sqrt_t(double x) { return sqrt(x); }
+__device__ __forceinline__ float sqrt_t(float x) { return sqrtf(x); }
+
+// metric + derivatives at (r, theta) given sin/cos of theta
+template <typename T>
+__device__ __forceinline__ void ks_geo_sc(T a, T r, T s, T c, KSGeo<T> &m)
+{
+    T a2 = a * a, r2 = r * r;
+    T rho2 = r2 + a2 * c * c;
+    T ir = T(1) / rho2;
+    T ir2 = ir * ir;
+    T z = T(2) * r * ir;
+    T iopz = T(1) / (T(1) + z);
+    m.alpha = sqrt_t(iopz);
+    m.beta = z * iopz;
+    T is2 = T(1) / (s * s);
+    m.grr = (a2 + r2) * ir - m.beta;
+    m.grp = a * ir;
+    m.gtt = ir;
+    m.gpp = ir * is2;
+    T drho_t = T(-2) * a2 * c * s;
+    T dz_r = T(2) * ir * (T(1) - T(2) * r2 * ir);
+    T dz_t = T(-2) * r * drho_t * ir2;
+    T ka = T(-0.5) * m.alpha * iopz;  // d alpha / dz
+    T kb = iopz * iopz;               // d beta / dz
+    m.da_r = ka * dz_r;
+    m.da_t = ka * dz_t;
+    m.db_r = kb * dz_r;
+    m.db_t = kb * dz_t;
+    m.dgrr_r = T(2) * r * ir - (a2 + r2) * T(2) * r * ir2 - m.db_r;
+    m.dgrr_t = -(a2 + r2) * drho_t * ir2 - m.db_t;
+    m.dgrp_r = -a * T(2) * r * ir2;
+    m.dgrp_t = -a * drho_t * ir2;
+    m.dgtt_r = T(-2) * r * ir2;
+    m.dgtt_t = -drho_t * ir2;
+    m.dgpp_r = T(-2) * r * ir2 * is2;
+    m.dgpp_t = -drho_t * ir2 * is2 - T(2) * s * c * ir * is2 * is2;
+}
+
+template <typename T>
+__device__ __forceinline__ void ks_geo(T a, T r, T th, KSGeo<T> &m)
+{
+    T s, c;
+    sincos_t(th, &s, &c);
+    ks_geo_sc(a, r, s, c, m);
+}
+
+// X^i = gamma^{ij} u_j / u^0 - beta^i,
+// U_i = -alpha u^0 d_i alpha + u_k d_i beta^k - u_j u_k d_i gamma^{jk} / (2 u^0)
+template <typename M, typename T>
+__device__ __forceinline__ void geo_rhs_m(const KSGeo<M> &m, T eps, T ur, T ut, T up, RhsT<T> &f)
+{
+    T grr = (T)m.grr, grp = (T)m.grp, gtt = (T)m.gtt, gpp = (T)m.gpp, alpha = (T)m.alpha;
+    T uu = grr * ur * ur + T(2) * grp * ur * up + gtt * ut * ut + gpp * up * up;
+    T au0 = sqrt_t(eps + uu);  // alpha u^0
+    T iu0 = alpha / au0;       // 1 / u^0
+    f.xr = (grr * ur + grp * up) * iu0 - (T)m.beta;
+    f.xt = gtt * ut * iu0;
+    f.xp = (grp * ur + gpp * up) * iu0;
+    T h = T(0.5) * iu0;
+    f.ur = -au0 * (T)m.da_r + ur * (T)m.db_r -
+           h * (ur * ur * (T)m.dgrr_r + T(2) * ur * up * (T)m.dgrp_r + ut * ut * (T)m.dgtt_r + up * up * (T)m.dgpp_r);
+    f.ut = -au0 * (T)m.da_t + ur * (T)m.db_t -
+           h * (ur * ur * (T)m.dgrr_t + T(2) * ur * up * (T)m.dgrp_t + ut * ut * (T)m.dgtt_t + up * up * (T)m.dgpp_t);
+}
+
+}  // namespace grpic

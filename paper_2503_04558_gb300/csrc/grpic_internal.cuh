@@ -51,6 +51,7 @@ struct grpic_ctx {
     float *tab32;       // FP32 copies of tab (precision 32 only)
     float *col1d32;
     size_t slab;        // elements per slab = (nth+1)*ld_tab
+    double *rcol;       // r at integer columns r_in exp(i dx1), index i + NG
     // field-solver scratch: Cn[6], two iterate buffers[12] in field precision
     void *fscratch;
     int64_t fscratch_ld;

@@ -1,10 +1,475 @@
-// grpic_push32.cu -- FP32 form of the push + deposit (placeholder until the
-// FP32 kernel lands).
-#include "grpic_internal.cuh"
+// grpic_push32.cu -- FP32 form of the push fused with the deposit.
+//
+// Same algorithm as the FP64 path (arXiv:2503.04558 Sec. 2.2-2.3): Boris at
+// fields n, geodesic predictor + trapezoidal correctors, axis reflection,
+// Esirkepov deposit.  What changes is the number format:
+//   * a particle is an int32 cell key plus FP32 offsets (o1, o2) in [0, 1]
+//     inside the cell (logical units) and FP32 covariant momenta; the geodesic
+//     is integrated for r - r_i (r_i the cell's inner edge) and for o2
+//     (dx2/dt = X^th / dtheta), so the trapezoidal rule acts on r and theta as
+//     in the paper while the position keeps FP32 precision relative to its
+//     cell whatever the grid size;
+//   * fields, tables and deposited currents are FP32;
+//   * FP64 is kept for (i) the metric (alpha, beta, gamma^ij and derivatives)
+//     of particles in cells whose inner edge lies below fp64_radius (the FP64
+//     island near the horizon), (ii) the corrector's
+//     convergence test: after each corrector the change of the iterate is
+//     measured in FP64 and the iteration stops once it is below the tolerance
+//     (at most n_push_iter correctors).
+#include "grpic_geo.cuh"
 
 namespace grpic {
-cudaError_t launch_push32(grpic_ctx *, grpic_particles *, grpic_fields *, bool, cudaStream_t)
+namespace {
+
+struct Push32Args {
+    GridDev g;
+    float dt;
+    int n_iter;
+    double tol;
+    float qm[4], qw[4];
+    int massive[4];
+    double r64;
+    int i64;  // first column whose inner edge is at or beyond fp64_radius
+    int64_t n;
+    const int64_t *d_count;
+    int32_t *cell;
+    float *o1, *o2, *u1, *u2, *u3;
+    uint32_t *tag;
+    const float *D0, *D1, *D2, *B0, *B1, *B2;
+    float *J0, *J1, *J2;
+    int64_t ld;
+    const double *rcol;  // r at integer columns, index i + NG
+    int32_t *keys;
+    int32_t *count;
+    int histogram;
+    int *status;
+};
+
+template <typename T>
+struct KSPoint {
+    T alpha, g_rr, g_rp, g_tt, g_pp, gi_rr, gi_rp, gi_tt, gi_pp, sqrtg;
+};
+
+template <typename T>
+__device__ __forceinline__ void ks_point_t(T a, T r, T th, KSPoint<T> &m)
 {
-    return cudaErrorNotSupported;
+    T s, c;
+    sincos_t(th, &s, &c);
+    T s2 = s * s, a2 = a * a;
+    T rho2 = r * r + a2 * c * c;
+    T irho2 = T(1) / rho2;
+    T z = T(2) * r * irho2;
+    T opz = T(1) + z;
+    T Dl = r * r + a2 - T(2) * r;
+    T Sg = (r * r + a2) * (r * r + a2) - a2 * Dl * s2;
+    m.alpha = sqrt_t(T(1) / opz);
+    m.g_rr = opz;
+    m.g_tt = rho2;
+    m.g_pp = Sg * s2 * irho2;
+    m.g_rp = -a * s2 * opz;
+    m.gi_rr = (a2 + r * r) * irho2 - z / opz;
+    m.gi_rp = a * irho2;
+    m.gi_tt = irho2;
+    m.gi_pp = irho2 / s2;
+    m.sqrtg = rho2 * s * sqrt_t(opz);
 }
+
+// generalized Boris step in FP32 with a metric of type M
+template <typename M>
+__device__ __forceinline__ void boris32(const KSPoint<M> &mm, float qm, float dt, const float D[3], const float B[3],
+                                        float u[3])
+{
+    float alpha = (float)mm.alpha, grr = (float)mm.g_rr, grp = (float)mm.g_rp, gtt = (float)mm.g_tt,
+          gpp = (float)mm.g_pp;
+    float irr = (float)mm.gi_rr, irp = (float)mm.gi_rp, itt = (float)mm.gi_tt, ipp = (float)mm.gi_pp;
+    float sg = (float)mm.sqrtg;
+    float Dl0 = grr * D[0] + grp * D[2], Dl1 = gtt * D[1], Dl2 = grp * D[0] + gpp * D[2];
+    float h = 0.5f * qm * alpha * dt;
+    float um0 = u[0] + h * Dl0, um1 = u[1] + h * Dl1, um2 = u[2] + h * Dl2;
+    float v0 = irr * um0 + irp * um2, v1 = itt * um1, v2 = irp * um0 + ipp * um2;
+    float u0b = sqrtf(1.0f + um0 * v0 + um1 * v1 + um2 * v2) / alpha;
+    float kt = 0.5f * qm * dt / u0b;
+    float t0 = kt * B[0], t1 = kt * B[1], t2 = kt * B[2];
+    float tt = t0 * (grr * t0 + grp * t2) + t1 * (gtt * t1) + t2 * (grp * t0 + gpp * t2);
+    float ks = 2.0f / (1.0f + tt);
+    float s0 = ks * t0, s1 = ks * t1, s2 = ks * t2;
+    float w0 = um0 + sg * (v1 * t2 - v2 * t1);
+    float w1 = um1 + sg * (v2 * t0 - v0 * t2);
+    float w2 = um2 + sg * (v0 * t1 - v1 * t0);
+    float x0 = irr * w0 + irp * w2, x1 = itt * w1, x2 = irp * w0 + ipp * w2;
+    u[0] = um0 + sg * (x1 * s2 - x2 * s1) + h * Dl0;
+    u[1] = um1 + sg * (x2 * s0 - x0 * s2) + h * Dl1;
+    u[2] = um2 + sg * (x0 * s1 - x1 * s0) + h * Dl2;
+}
+
+// right-hand side at r = r_i + dr (dr = r - r_i relative to the cell's inner
+// edge, so the trapezoidal rule acts on r exactly as in Eq. geodesic-corrector)
+// and theta = (j + o2) dtheta; metric in type M.  Returns d(dr)/dt and d(o2)/dt.
+template <typename M>
+__device__ __forceinline__ void rhs_off(const GridDev &g, double rci, int j, float dr, float o2, float eps, float ur,
+                                        float ut, float up, RhsT<float> &f)
+{
+    M r, th;
+    if (sizeof(M) == 8) {
+        r = (M)(rci + (double)dr);
+        th = (M)(((double)j + (double)o2) * g.dth);
+    } else {
+        r = (M)rci + (M)dr;
+        th = (M)(((float)j + o2) * (float)g.dth);
+    }
+    KSGeo<M> m;
+    ks_geo<M>((M)g.a, r, th, m);
+    RhsT<float> fx;
+    geo_rhs_m<M, float>(m, eps, ur, ut, up, fx);
+    f.xr = fx.xr;
+    f.xt = fx.xt * (float)(1.0 / g.dth);
+    f.xp = fx.xp;
+    f.ur = fx.ur;
+    f.ut = fx.ut;
+}
+
+struct St32 {
+    int c0, r0, r1;
+    float w00, w10, w01, w11, p0, p1;
+};
+
+// bilinear stencil from cell (i, j) and offsets; half_r / half_t stagger
+__device__ __forceinline__ void stencil32(const GridDev &g, int i, int j, float o1, float o2, bool half_r, bool half_t,
+                                          float par, St32 &S)
+{
+    int is = i;
+    float f = o1;
+    if (half_r) {
+        f = o1 - 0.5f;
+        if (f < 0.0f) { f += 1.0f; is = i - 1; }
+    }
+    int js = j;
+    float gg = o2;
+    S.p0 = S.p1 = 1.0f;
+    if (half_t) {
+        gg = o2 - 0.5f;
+        if (gg < 0.0f) { gg += 1.0f; js = j - 1; }
+        S.r0 = js;
+        S.r1 = js + 1;
+        if (S.r0 < 0) { S.r0 = -1 - S.r0; S.p0 = par; }
+        if (S.r1 > g.nth - 1) { S.r1 = 2 * g.nth - 1 - S.r1; S.p1 = par; }
+    } else {
+        S.r0 = js;
+        S.r1 = js + 1;
+    }
+    S.c0 = is + NG;
+    S.w00 = (1.0f - f) * (1.0f - gg);
+    S.w10 = f * (1.0f - gg);
+    S.w01 = (1.0f - f) * gg;
+    S.w11 = f * gg;
+}
+
+__device__ __forceinline__ float gather32(const float *__restrict__ F, int64_t ld, const St32 &S)
+{
+    const float *a = F + (size_t)S.r0 * ld + S.c0;
+    const float *b = F + (size_t)S.r1 * ld + S.c0;
+    return S.p0 * (S.w00 * __ldg(a) + S.w10 * __ldg(a + 1)) + S.p1 * (S.w01 * __ldg(b) + S.w11 * __ldg(b + 1));
+}
+
+__device__ __forceinline__ float W1f(float d)
+{
+    d = fabsf(d);
+    return d < 1.0f ? 1.0f - d : 0.0f;
+}
+
+constexpr int NWIN = 40;
+
+template <typename M>
+__device__ __forceinline__ void push_one(const Push32Args &A, int i, int j, float &o1, float &o2, float u[3], int sp,
+                                         float &dphi)
+{
+    const GridDev &g = A.g;
+    double rci = A.rcol[i + NG];
+    if (A.massive[sp] && A.qm[sp] != 0.0f) {
+        St32 Sh0, S0h, S00, Shh;
+        stencil32(g, i, j, o1, o2, true, false, 1.0f, Sh0);
+        stencil32(g, i, j, o1, o2, false, true, -1.0f, S0h);
+        stencil32(g, i, j, o1, o2, false, false, 1.0f, S00);
+        stencil32(g, i, j, o1, o2, true, true, 1.0f, Shh);
+        float Dv[3], Bv[3];
+        Dv[0] = gather32(A.D0, A.ld, Sh0);
+        Dv[1] = gather32(A.D1, A.ld, S0h);
+        Dv[2] = gather32(A.D2, A.ld, S00);
+        Bv[1] = gather32(A.B1, A.ld, Sh0);
+        Bv[2] = gather32(A.B2, A.ld, Shh);
+        S0h.p0 = S0h.p1 = 1.0f;
+        Bv[0] = gather32(A.B0, A.ld, S0h);
+        KSPoint<M> mm;
+        M r, th;
+        if (sizeof(M) == 8) {
+            r = (M)(rci + (double)((float)rci * expm1f(o1 * (float)g.dx1)));
+            th = (M)(((double)j + (double)o2) * g.dth);
+        } else {
+            r = (M)rci * (M)(1.0f + expm1f(o1 * (float)g.dx1));
+            th = (M)(((float)j + o2) * (float)g.dth);
+        }
+        ks_point_t<M>((M)g.a, r, th, mm);
+        boris32<M>(mm, A.qm[sp], A.dt, Dv, Bv, u);
+    }
+    float eps = A.massive[sp] ? 1.0f : 0.0f;
+    float dt = A.dt, h = 0.5f * dt;
+    float rcf = (float)rci, dx1f = (float)g.dx1;
+    float d0 = rcf * expm1f(o1 * dx1f);  // r - r_i
+    RhsT<float> f0, ft;
+    rhs_off<M>(g, rci, j, d0, o2, eps, u[0], u[1], u[2], f0);
+    float a1 = d0 + dt * f0.xr, a2 = o2 + dt * f0.xt, ap = dt * f0.xp;
+    float b1 = u[0] + dt * f0.ur, b2 = u[1] + dt * f0.ut;
+    for (int it = 0; it < A.n_iter; ++it) {
+        rhs_off<M>(g, rci, j, a1, a2, eps, b1, b2, u[2], ft);
+        float n1 = d0 + h * (ft.xr + f0.xr), n2 = o2 + h * (ft.xt + f0.xt);
+        float nb1 = u[0] + h * (ft.ur + f0.ur), nb2 = u[1] + h * (ft.ut + f0.ut);
+        ap = h * (ft.xp + f0.xp);
+        // convergence test of the implicit iteration, in FP64
+        double d = fmax(fmax(fabs((double)n1 - (double)a1) / (double)rcf, fabs((double)n2 - (double)a2)),
+                        fmax(fabs((double)nb1 - (double)b1) / fmax(1.0, fabs((double)nb1)),
+                             fabs((double)nb2 - (double)b2) / fmax(1.0, fabs((double)nb2))));
+        a1 = n1;
+        a2 = n2;
+        b1 = nb1;
+        b2 = nb2;
+        if (A.tol > 0.0 && d < A.tol) break;
+    }
+    o1 = log1pf(a1 / rcf) / dx1f;  // back to the logical offset
+    o2 = a2;
+    u[0] = b1;
+    u[1] = b2;
+    dphi = ap;
+}
+
+__global__ void __launch_bounds__(256) push32_kernel(Push32Args A)
+{
+    const GridDev &g = A.g;
+    int64_t n = A.d_count ? *A.d_count : A.n;
+    if (n > A.n) n = A.n;
+    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const unsigned FULL = 0xffffffffu;
+    int lane = threadIdx.x & 31;
+    int ncell = g.nr * g.nth;
+
+    bool live = false;
+    uint32_t tag = DEAD;
+    int i = 0, j = 0, cellk = 0;
+    float o1 = 0, o2 = 0, u[3] = {0, 0, 0};
+    if (p < n) {
+        tag = A.tag[p];
+        if (!(tag & DEAD)) {
+            cellk = A.cell[p];
+            o1 = A.o1[p];
+            o2 = A.o2[p];
+            u[0] = A.u1[p];
+            u[1] = A.u2[p];
+            u[2] = A.u3[p];
+            bool ok = cellk >= 0 && cellk < ncell && o1 >= 0.0f && o1 <= 1.0f && o2 >= 0.0f && o2 <= 1.0f &&
+                      isfinite(u[0]) && isfinite(u[1]) && isfinite(u[2]);
+            if (ok) {
+                live = true;
+                i = cellk % g.nr;
+                j = cellk / g.nr;
+            } else {
+                bool fin = isfinite(o1) && isfinite(o2) && isfinite(u[0]) && isfinite(u[1]) && isfinite(u[2]);
+                set_status(A.status, fin ? GRPIC_ERANGE : GRPIC_ENAN);
+                tag |= DEAD;
+            }
+        }
+    }
+
+    bool dep = false, moved = false;
+    float win[NWIN];
+    int key = -1, ni = i, nj = j;
+    float n1 = o1, n2 = o2;
+    if (live) {
+        int sp = tag & 3u;
+        float dphi = 0.0f;
+        // FP64 island: cells whose inner edge r_i lies below fp64_radius
+        if (i < A.i64)
+            push_one<double>(A, i, j, n1, n2, u, sp, dphi);
+        else
+            push_one<float>(A, i, j, n1, n2, u, sp, dphi);
+        // axis reflection in offset space (theta = 0 is o2 = 0 of row 0,
+        // theta = pi is o2 = 1 of row nth-1)
+        if (j == 0 && n2 < 0.0f) { n2 = -n2; u[1] = -u[1]; }
+        if (j == g.nth - 1 && n2 > 1.0f) { n2 = 2.0f - n2; u[1] = -u[1]; }
+        bool finite = isfinite(n1) && isfinite(n2) && isfinite(u[0]) && isfinite(u[1]) && isfinite(dphi);
+        if (!finite) {
+            set_status(A.status, GRPIC_ENAN);
+            tag |= DEAD;
+        } else {
+            int di = (int)floorf(n1), dj = (int)floorf(n2);
+            if (dj > 0 && j + dj > g.nth - 1) dj = g.nth - 1 - j;  // theta = pi exactly stays in the last row
+            if (di < -1 || di > 1 || dj < -1 || dj > 1) {
+                set_status(A.status, GRPIC_ERANGE);
+                tag |= DEAD;
+            } else {
+                float x1b = n1, x2b = n2;  // end point relative to the start cell
+                // Esirkepov window relative to the start cell: columns i-1..i+2
+                int sp2 = sp;
+                float qw = A.qw[sp2];
+                float S0r[4], S1r[4], S0t[4], S1t[4];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    S0r[k] = W1f(o1 - (float)(k - 1));
+                    S1r[k] = W1f(x1b - (float)(k - 1));
+                    S0t[k] = W1f(o2 - (float)(k - 1));
+                    S1t[k] = W1f(x2b - (float)(k - 1));
+                }
+                float cr = -qw / (2.0f * A.dt);
+                float cp = qw * dphi / A.dt;
+                float Pr = 0.0f;
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    Pr += S1r[k] - S0r[k];
+#pragma unroll
+                    for (int l = 0; l < 4; ++l) win[k * 4 + l] = cr * Pr * (S1t[l] + S0t[l]);
+                }
+                float Pt = 0.0f;
+#pragma unroll
+                for (int l = 0; l < 3; ++l) {
+                    Pt += S1t[l] - S0t[l];
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) win[12 + k * 3 + l] = cr * (S1r[k] + S0r[k]) * Pt;
+                }
+#pragma unroll
+                for (int k = 0; k < 4; ++k)
+#pragma unroll
+                    for (int l = 0; l < 4; ++l)
+                        win[24 + k * 4 + l] = cp * (S1r[k] * S1t[l] * (1.0f / 3.0f) + S1r[k] * S0t[l] * (1.0f / 6.0f) +
+                                                    S0r[k] * S1t[l] * (1.0f / 6.0f) + S0r[k] * S0t[l] * (1.0f / 3.0f));
+                dep = true;
+                moved = true;
+                ni = i + di;
+                nj = j + dj;
+                n1 -= (float)di;
+                n2 -= (float)dj;
+                if (n1 >= 1.0f) n1 = 0x1.fffffep-1f;  // rounding of the re-centring
+                if (n1 < 0.0f) n1 = 0.0f;
+                if (n2 > 1.0f) n2 = 1.0f;
+                if (n2 < 0.0f) n2 = 0.0f;
+                if (ni < 0 || ni >= g.nr) tag |= DEAD;  // left [r_in, r_out)
+                key = (tag & DEAD) ? ncell : nj * g.nr + ni;
+            }
+        }
+    }
+    if (p < n) {
+        if (moved) {
+            A.cell[p] = nj * g.nr + ni;
+            A.o1[p] = n1;
+            A.o2[p] = n2;
+            A.u1[p] = u[0];
+            A.u2[p] = u[1];
+            A.u3[p] = u[2];
+        }
+        if (tag & DEAD) key = ncell;
+        A.tag[p] = tag;
+        A.keys[p] = key;
+    }
+
+    // ---- deposit (warp-uniform start cell -> one reduced set of atomics) ----
+    int wkey = dep ? (j * g.nr + i) : -1;
+    unsigned act = __ballot_sync(FULL, dep);
+    if (act) {
+        int src = __ffs(act) - 1;
+        int ref = __shfl_sync(FULL, wkey, src);
+        bool uniform = __all_sync(FULL, !dep || wkey == ref);
+        if (uniform) {
+            int ri = __shfl_sync(FULL, i, src);
+            int rj = __shfl_sync(FULL, j, src);
+#pragma unroll
+            for (int v = 0; v < NWIN; ++v) {
+                float x = dep ? win[v] : 0.0f;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(FULL, x, o);
+                win[v] = x;
+            }
+            dep = (lane == 0);
+            i = ri;
+            j = rj;
+        }
+        if (dep) {
+#pragma unroll
+            for (int k = 0; k < 3; ++k)
+#pragma unroll
+                for (int l = 0; l < 4; ++l) {
+                    int row = j - 1 + l;
+                    float v = win[k * 4 + l];
+                    if (v != 0.0f && row >= 0 && row <= g.nth) atomicAdd(A.J0 + (size_t)row * A.ld + (i - 1 + k + NG), v);
+                }
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+#pragma unroll
+                for (int l = 0; l < 3; ++l) {
+                    int row = j - 1 + l;
+                    float v = win[12 + k * 3 + l];
+                    if (v != 0.0f && row >= 0 && row <= g.nth - 1)
+                        atomicAdd(A.J1 + (size_t)row * A.ld + (i - 1 + k + NG), v);
+                }
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+#pragma unroll
+                for (int l = 0; l < 4; ++l) {
+                    int row = j - 1 + l;
+                    float v = win[24 + k * 4 + l];
+                    if (v != 0.0f && row >= 0 && row <= g.nth) atomicAdd(A.J2 + (size_t)row * A.ld + (i - 1 + k + NG), v);
+                }
+        }
+    }
+
+    if (A.histogram) {
+        int hk = (p < n) ? key : -1;
+        unsigned peers = __match_any_sync(FULL, hk);
+        if (hk >= 0 && lane == __ffs(peers) - 1) atomicAdd(A.count + hk, __popc(peers));
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_push32(grpic_ctx *ctx, grpic_particles *p, grpic_fields *f, bool histogram, cudaStream_t s)
+{
+    Push32Args A;
+    A.g = ctx->g;
+    A.dt = (float)ctx->prm.dt;
+    A.n_iter = ctx->prm.n_push_iter;
+    A.tol = ctx->prm.push_tol;
+    for (int k = 0; k < 4; ++k) {
+        A.qm[k] = (float)ctx->prm.q_over_m[k];
+        A.qw[k] = (float)ctx->prm.q_weight[k];
+        A.massive[k] = ctx->prm.massive[k];
+    }
+    A.r64 = ctx->prm.fp64_radius;
+    A.i64 = 0;
+    if (A.r64 > 0.0)
+        while (A.i64 < ctx->g.nr && ctx->g.r_in * std::exp(A.i64 * ctx->g.dx1) < A.r64) ++A.i64;
+    A.n = p->n;
+    A.d_count = p->d_count;
+    A.cell = p->cell;
+    A.o1 = (float *)p->x1;
+    A.o2 = (float *)p->x2;
+    A.u1 = (float *)p->u1;
+    A.u2 = (float *)p->u2;
+    A.u3 = (float *)p->u3;
+    A.tag = p->tag;
+    A.D0 = (const float *)f->D[0];
+    A.D1 = (const float *)f->D[1];
+    A.D2 = (const float *)f->D[2];
+    A.B0 = (const float *)f->B[0];
+    A.B1 = (const float *)f->B[1];
+    A.B2 = (const float *)f->B[2];
+    A.J0 = (float *)f->J[0];
+    A.J1 = (float *)f->J[1];
+    A.J2 = (float *)f->J[2];
+    A.ld = f->ld;
+    A.rcol = ctx->rcol;
+    A.keys = ctx->d_keys;
+    A.count = ctx->d_count;
+    A.histogram = histogram ? 1 : 0;
+    A.status = ctx->d_status;
+    if (p->n <= 0) return cudaSuccess;
+    push32_kernel<<<(unsigned)((p->n + 255) / 256), 256, 0, s>>>(A);
+    return cudaGetLastError();
+}
+
 }  // namespace grpic

@@ -215,10 +215,11 @@ __global__ void __launch_bounds__(256) push64_kernel(Push64Args A)
     if (live) {
         // a state outside the domain (or non-finite) would index the fields out
         // of range: refuse it before any gather
-        bool inside = isfinite(r) && isfinite(th) && isfinite(u[0]) && r >= g.r_in && r < g.r_out && th >= 0.0 &&
-                      th <= M_PI;
+        bool inside = isfinite(r) && isfinite(th) && isfinite(u[0]) && isfinite(u[1]) && isfinite(u[2]) &&
+                      r >= g.r_in && r < g.r_out && th >= 0.0 && th <= M_PI;
         if (!inside) {
-            set_status(A.status, (isfinite(r) && isfinite(th)) ? GRPIC_ERANGE : GRPIC_ENAN);
+            bool fin = isfinite(r) && isfinite(th) && isfinite(u[0]) && isfinite(u[1]) && isfinite(u[2]);
+            set_status(A.status, fin ? GRPIC_ERANGE : GRPIC_ENAN);
             tag |= DEAD;
             live = false;
         }

@@ -18,12 +18,13 @@ def configs(nr, nth, a, r_in, r_out, precision=64, **kw):
     return oc, gc
 
 
-def relerr(x, ref, mask=None):
+def relerr(x, ref, mask=None, floor=0.0):
+    """max|x - ref| / max(max|ref|, floor) (max-norm relative error of an array)."""
     x = np.asarray(x, np.float64)
     ref = np.asarray(ref, np.float64)
     if mask is not None:
         x, ref = x[mask], ref[mask]
-    scale = np.max(np.abs(ref))
+    scale = max(np.max(np.abs(ref)), floor)
     if scale == 0:
         return float(np.max(np.abs(x)))
     return float(np.max(np.abs(x - ref)) / scale)
@@ -37,3 +38,28 @@ def flux_form(oc, J):
 
 def logical(oc, r, th):
     return (np.log(r) - math.log(oc.r_in)) / oc.dx1, th / oc.dth
+
+
+def axis_grazers(oc, P, D, B, nsteps, theta_c=1e-3):
+    """Oracle-only pre-run of nsteps full steps: indices into P of the particles
+    whose path comes within theta_c of the polar axis (theta = 0 or pi).
+
+    There gamma^{phi phi} ~ 1/sin^2(theta) makes the push ill-conditioned (the
+    centrifugal barrier is not resolved by dt): a one-ulp difference between
+    two libm implementations grows by orders of magnitude in one step, so two
+    correct FP64 implementations cannot agree to 1e-10 on such paths."""
+    P = P.copy()
+    D = [x.copy() for x in D]
+    B = [x.copy() for x in B]
+    ids = np.arange(P.n)
+    mind = np.minimum(P.th, math.pi - P.th)
+    for _ in range(nsteps):
+        st, J, _ = O.push_deposit(oc, P, D, B)
+        O.field_update(oc, D, B, J)
+        d = np.minimum(P.th, math.pi - P.th)
+        mind[ids] = np.minimum(mind[ids], d)
+        keys = O.cell_keys(oc, P)
+        perm, live = O.counting_sort(keys, oc.nr * oc.nth)
+        P = P.take(perm[:live])
+        ids = ids[perm[:live]]
+    return np.nonzero(mind < theta_c)[0]
