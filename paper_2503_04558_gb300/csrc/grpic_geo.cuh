@@ -23,10 +23,14 @@ struct RhsT {
     T xr, xt, xp, ur, ut;
 };
 
+// FP64: the library's IEEE functions.  FP32 (the FP32 form, whose error
+// budget is 1e-4 against FP64): the hardware approximations (a few ulp).
 __device__ __forceinline__ void sincos_t(double x, double *s, double *c) { sincos(x, s, c); }
-__device__ __forceinline__ void sincos_t(float x, float *s, float *c) { sincosf(x, s, c); }
+__device__ __forceinline__ void sincos_t(float x, float *s, float *c) { __sincosf(x, s, c); }
 __device__ __forceinline__ double sqrt_t(double x) { return sqrt(x); }
-__device__ __forceinline__ float sqrt_t(float x) { return sqrtf(x); }
+__device__ __forceinline__ float sqrt_t(float x) { return x > 0.0f ? x * rsqrtf(x) : 0.0f; }
+__device__ __forceinline__ double rcp_t(double x) { return 1.0 / x; }
+__device__ __forceinline__ float rcp_t(float x) { return __fdividef(1.0f, x); }
 
 // metric + derivatives at (r, theta) given sin/cos of theta
 template <typename T>
@@ -34,13 +38,13 @@ __device__ __forceinline__ void ks_geo_sc(T a, T r, T s, T c, KSGeo<T> &m)
 {
     T a2 = a * a, r2 = r * r;
     T rho2 = r2 + a2 * c * c;
-    T ir = T(1) / rho2;
+    T ir = rcp_t(rho2);
     T ir2 = ir * ir;
     T z = T(2) * r * ir;
-    T iopz = T(1) / (T(1) + z);
+    T iopz = rcp_t(T(1) + z);
     m.alpha = sqrt_t(iopz);
     m.beta = z * iopz;
-    T is2 = T(1) / (s * s);
+    T is2 = rcp_t(s * s);
     m.grr = (a2 + r2) * ir - m.beta;
     m.grp = a * ir;
     m.gtt = ir;
@@ -80,7 +84,7 @@ __device__ __forceinline__ void geo_rhs_m(const KSGeo<M> &m, T eps, T ur, T ut, 
     T grr = (T)m.grr, grp = (T)m.grp, gtt = (T)m.gtt, gpp = (T)m.gpp, alpha = (T)m.alpha;
     T uu = grr * ur * ur + T(2) * grp * ur * up + gtt * ut * ut + gpp * up * up;
     T au0 = sqrt_t(eps + uu);  // alpha u^0
-    T iu0 = alpha / au0;       // 1 / u^0
+    T iu0 = alpha * rcp_t(au0);  // 1 / u^0
     f.xr = (grr * ur + grp * up) * iu0 - (T)m.beta;
     f.xt = gtt * ut * iu0;
     f.xp = (grp * ur + gpp * up) * iu0;

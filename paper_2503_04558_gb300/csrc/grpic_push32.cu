@@ -224,15 +224,20 @@ __device__ __forceinline__ void push_one(const Push32Args &A, int i, int j, floa
         float n1 = d0 + h * (ft.xr + f0.xr), n2 = o2 + h * (ft.xt + f0.xt);
         float nb1 = u[0] + h * (ft.ur + f0.ur), nb2 = u[1] + h * (ft.ut + f0.ut);
         ap = h * (ft.xp + f0.xp);
-        // convergence test of the implicit iteration, in FP64
-        double d = fmax(fmax(fabs((double)n1 - (double)a1) / (double)rcf, fabs((double)n2 - (double)a2)),
-                        fmax(fabs((double)nb1 - (double)b1) / fmax(1.0, fabs((double)nb1)),
-                             fabs((double)nb2 - (double)b2) / fmax(1.0, fabs((double)nb2))));
+        bool done = false;
+        if (A.tol > 0.0) {
+            // convergence test of the implicit iteration, in FP64: change of
+            // the iterate relative to r_i, one theta cell and max(1, |u|)
+            double t = A.tol;
+            done = fabs((double)n1 - (double)a1) < t * (double)rcf && fabs((double)n2 - (double)a2) < t &&
+                   fabs((double)nb1 - (double)b1) < t * fmax(1.0, fabs((double)nb1)) &&
+                   fabs((double)nb2 - (double)b2) < t * fmax(1.0, fabs((double)nb2));
+        }
         a1 = n1;
         a2 = n2;
         b1 = nb1;
         b2 = nb2;
-        if (A.tol > 0.0 && d < A.tol) break;
+        if (done) break;
     }
     o1 = log1pf(a1 / rcf) / dx1f;  // back to the logical offset
     o2 = a2;
