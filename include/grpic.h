@@ -193,6 +193,35 @@ grpic_status grpic_get_areas(grpic_ctx *ctx, double *const out[6], int64_t ld, v
  * word, and return the first device error recorded (GRPIC_OK if none). */
 grpic_status grpic_sync(grpic_ctx *ctx, void *stream);
 
+/* Largest sizes grpic_sort_noalloc accepts (the size of its fixed scratch). */
+#define GRPIC_NOALLOC_MAX_PARTICLES 2097152 /* slots p->n                  */
+#define GRPIC_NOALLOC_MAX_CELLS 262144      /* n_r * n_theta (e.g. 512^2)   */
+
+/* Sort by cell without any device allocation.  The paper has no counterpart:
+ * this entry exists for callers that cannot call cudaMalloc -- code running
+ * while a stream is being captured, hosts whose memory pools own all device
+ * memory, plugin hosts that forbid library allocations.  It computes the same
+ * stable order as grpic_sort (same kernels, same result) but needs no context:
+ * the grid, the precision (64 or 32) and the two particle buffers are given
+ * directly, and the scratch (keys, histogram, offsets, index list) is one
+ * fixed __device__ array of about 20 MB in libgrpic that every GPU loading
+ * the library holds until the process exits.
+ *   - The caller passes inputs and outputs as for grpic_sort: the sorted state
+ *     is written into `scratch` and the two structs' array pointers are
+ *     swapped on return; the live count goes to p->d_count when given.
+ *   - Sizes above GRPIC_NOALLOC_MAX_PARTICLES particles or
+ *     GRPIC_NOALLOC_MAX_CELLS cells return GRPIC_EOVERFLOW before any launch.
+ *   - It calls no cudaMalloc, cudaFree or allocating library routine.  Its
+ *     first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current and sets a kernel
+ *     attribute; make that first call before any stream capture begins.
+ *   - Every call shares the one array, which keeps the last call's contents
+ *     (each call clears what must start at zero).  Calls that overlap on the
+ *     GPU -- on different streams, or from different host threads -- race on
+ *     it and corrupt each other's results: serialize them. */
+grpic_status grpic_sort_noalloc(const grpic_grid *grid, int32_t precision, grpic_particles *p,
+                                grpic_particles *scratch, void *stream);
+
 /* Human-readable description of the last error seen by the context. */
 const char *grpic_last_error(const grpic_ctx *ctx);
 

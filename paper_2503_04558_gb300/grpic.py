@@ -23,7 +23,10 @@ NG = 2
 
 # names the header declares (checked by the CPU test of the boundary)
 EXPORTS = ["grpic_init", "grpic_init_fields", "grpic_push", "grpic_deposit", "grpic_field_update", "grpic_sort",
-           "grpic_step", "grpic_diagnostics", "grpic_get_areas", "grpic_sync", "grpic_last_error", "grpic_destroy"]
+           "grpic_step", "grpic_diagnostics", "grpic_get_areas", "grpic_sync", "grpic_last_error", "grpic_destroy",
+           "grpic_sort_noalloc"]
+NOALLOC_MAX_PARTICLES = 2097152
+NOALLOC_MAX_CELLS = 262144
 
 
 class Grid(C.Structure):
@@ -71,6 +74,7 @@ def load(path: str = LIB_PATH):
         "grpic_diagnostics": [v, p(ParticlesC), p(FieldsC), v, v, v],
         "grpic_get_areas": [v, v * 6, i64, v],
         "grpic_sync": [v, v],
+        "grpic_sort_noalloc": [p(Grid), C.c_int32, p(ParticlesC), p(ParticlesC), v],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
