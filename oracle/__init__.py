@@ -300,3 +300,117 @@ def step(c: Cfg, P: Particles, D, B, do_sort=True):
     if do_sort:
         P = sort(c, P)
     return st, P, J
+
+
+# --------------------------------------------------------------------------
+# batched 1D spark-gap line model (Sec. 4 pair production on radial lines)
+# --------------------------------------------------------------------------
+class Line(C.Structure):
+    _fields_ = [("n", C.c_int), ("a", C.c_double), ("theta", C.c_double), ("r_in", C.c_double),
+                ("r_out", C.c_double), ("dx1", C.c_double), ("dt", C.c_double), ("n_push_iter", C.c_int),
+                ("qm", C.c_double * 4), ("qw", C.c_double * 4), ("massive", C.c_int * 4), ("I0", C.c_double),
+                ("gamma_thr", C.c_double), ("eps_ph", C.c_double), ("tau", C.c_double), ("seed", C.c_uint64)]
+
+
+def _line_sigs(lib_):
+    d, i, l, p, u64 = C.c_double, C.c_int, C.c_long, C.c_void_p, C.c_uint64
+    pl = C.POINTER(Line)
+    sig = {
+        "orc_philox4x64": (None, [p, p, p]),
+        "orc_splitmix64": (u64, [u64]),
+        "orc_child_id": (u64, [u64, C.c_int64, i]),
+        "orc_uniform": (d, [u64, u64, C.c_int64, i]),
+        "orc_line_area": (None, [pl, p]),
+        "orc_line_init_D": (None, [pl, d, p]),
+        "orc_line_step": (i, [pl, C.c_int64, p, l, p, p, p, p, p, p, p, p]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib_, name)
+        fn.restype = res
+        fn.argtypes = args
+
+
+def make_line(n, a, theta, r_in, r_out, dt=None, cfl=0.5, n_push_iter=3, qm=(-1.0, 1.0, 1.0, 0.0),
+              qw=(-1.0, 1.0, 1.0, 0.0), massive=(1, 1, 1, 0), I0=0.0, gamma_thr=100.0, eps_ph=4.0, tau=2.0,
+              seed=0) -> Line:
+    L = Line()
+    L.n, L.a, L.theta, L.r_in, L.r_out = n, a, theta, r_in, r_out
+    L.dx1 = math.log(r_out / r_in) / n
+    L.dt = cfl * r_in * (math.exp(L.dx1) - 1.0) if dt is None else dt
+    L.n_push_iter = n_push_iter
+    for k in range(4):
+        L.qm[k], L.qw[k], L.massive[k] = qm[k], qw[k], massive[k]
+    L.I0, L.gamma_thr, L.eps_ph, L.tau, L.seed = I0, gamma_thr, eps_ph, tau, seed
+    return L
+
+
+def philox4x64(ctr, key):
+    lib_ = lib()
+    _line_sigs(lib_)
+    c = np.ascontiguousarray(ctr, np.uint64)
+    k = np.ascontiguousarray(key, np.uint64)
+    o = np.zeros(4, np.uint64)
+    lib_.orc_philox4x64(_p(c), _p(k), _p(o))
+    return o
+
+
+def child_id(parent, step, k):
+    lib_ = lib()
+    _line_sigs(lib_)
+    return lib_.orc_child_id(int(parent), int(step), int(k))
+
+
+def uniform(seed, pid, step, event):
+    lib_ = lib()
+    _line_sigs(lib_)
+    return lib_.orc_uniform(int(seed), int(pid), int(step), int(event))
+
+
+class LineState:
+    """Particles of one line: logical position x1, covariant u_r, u_phi,
+    tag (species | DEAD) and 64-bit id, with room for `cap` particles."""
+
+    def __init__(self, x1, ur, up, tag, pid, cap):
+        n = len(x1)
+        self.cap = int(cap)
+        self.x1 = np.zeros(self.cap)
+        self.ur = np.zeros(self.cap)
+        self.up = np.zeros(self.cap)
+        self.tag = np.zeros(self.cap, np.uint32)
+        self.id = np.zeros(self.cap, np.uint64)
+        self.x1[:n], self.ur[:n], self.up[:n] = x1, ur, up
+        self.tag[:n], self.id[:n] = tag, pid
+        self.n = n
+
+    def view(self):
+        n = self.n
+        return dict(x1=self.x1[:n], ur=self.ur[:n], up=self.up[:n], tag=self.tag[:n], id=self.id[:n])
+
+
+def line_area(L):
+    lib_ = lib()
+    _line_sigs(lib_)
+    A = np.zeros(L.n)
+    lib_.orc_line_area(C.byref(L), _p(A))
+    return A
+
+
+def line_init_D(L, B0):
+    lib_ = lib()
+    _line_sigs(lib_)
+    D = np.zeros(L.n)
+    lib_.orc_line_init_D(C.byref(L), B0, _p(D))
+    return D
+
+
+def line_step(L, step, S: LineState, D):
+    """One step of the line model in place; returns (status, JA, counts)."""
+    lib_ = lib()
+    _line_sigs(lib_)
+    JA = np.zeros(L.n + 2)
+    counts = np.zeros(2, np.int64)
+    n = C.c_long(S.n)
+    st = lib_.orc_line_step(C.byref(L), step, C.byref(n), S.cap, _p(S.x1), _p(S.ur), _p(S.up), _p(S.tag),
+                            _p(S.id), _p(D), _p(JA), _p(counts))
+    S.n = n.value
+    return st, JA, counts

@@ -1071,3 +1071,239 @@ void orc_divB(const orc_cfg *c, const double *B0r, const double *B1, double *div
             divB[q] = B0r[qp] * g.AB[0][qp] - B0r[q] * g.AB[0][q] + B1[qj] * g.AB[1][qj] - B1[q] * g.AB[1][q];
         }
 }
+
+/* ======================================================================== */
+/* Batched 1D spark gaps (the radiative pair-production prescription of     */
+/* Sec. 4, Eq. optical-depth, on single radial field lines).                 */
+/*                                                                          */
+/* The paper runs its spark gaps in 2D; this 1D line model is the reading   */
+/* used here (listed in the design notes): along a monopole field line at   */
+/* fixed theta_k particles slide radially (theta frozen, u_theta = 0, u_phi */
+/* kept), the electric kick is the covariant gamma_rr D^r part of the Boris */
+/* step, the geodesic step is Eq. geodesic-predictor/-corrector restricted  */
+/* to (r, u_r), the deposit is the 1D Esirkepov prefix sum, and the one     */
+/* field component obeys d(A_r D^r)/dt = I_0 - J^r A_r with an imposed line */
+/* current I_0 (constant along the line, so charge is conserved).           */
+/* Radiation (Sec. 4): a charged particle whose FIDO Lorentz factor         */
+/* Gamma = alpha u^0 reaches gamma_thr emits a photon of FIDO energy eps_ph */
+/* along its momentum and loses that energy; photons follow geodesics with  */
+/* epsilon = 0 and convert with probability 1 - exp(-tau dt) per step into  */
+/* an e-/e+ pair sharing the photon's FIDO energy equally, along its        */
+/* direction (conversion requires energy > 2).                              */
+/* ======================================================================== */
+
+/* Philox4x64-10 (Salmon, Moraes, Dror & Shaw, SC'11): 10 rounds of two     */
+/* 64x64->128 multiplications with the Weyl-sequence key schedule.          */
+static void mulhilo64(uint64_t a, uint64_t b, uint64_t *hi, uint64_t *lo)
+{
+    unsigned __int128 p = (unsigned __int128)a * b;
+    *hi = (uint64_t)(p >> 64);
+    *lo = (uint64_t)p;
+}
+
+void orc_philox4x64(const uint64_t *ctr, const uint64_t *key, uint64_t *out)
+{
+    uint64_t x0 = ctr[0], x1 = ctr[1], x2 = ctr[2], x3 = ctr[3];
+    uint64_t k0 = key[0], k1 = key[1];
+    for (int rnd = 0; rnd < 10; ++rnd) {
+        if (rnd > 0) {
+            k0 += 0x9E3779B97F4A7C15ULL;
+            k1 += 0xBB67AE8584CAA73BULL;
+        }
+        uint64_t h0, l0, h1, l1;
+        mulhilo64(0xD2E7470EE14C6C93ULL, x0, &h0, &l0);
+        mulhilo64(0xCA5A826395121157ULL, x2, &h1, &l1);
+        uint64_t y0 = h1 ^ x1 ^ k0, y1 = l1, y2 = h0 ^ x3 ^ k1, y3 = l0;
+        x0 = y0; x1 = y1; x2 = y2; x3 = y3;
+    }
+    out[0] = x0; out[1] = x1; out[2] = x2; out[3] = x3;
+}
+
+/* splitmix64 finaliser (Steele, Lea & Flood 2014) */
+uint64_t orc_splitmix64(uint64_t x)
+{
+    uint64_t z = x + 0x9E3779B97F4A7C15ULL;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+
+/* identity of the k-th particle created by `parent` at step `step` */
+uint64_t orc_child_id(uint64_t parent, int64_t step, int k)
+{
+    return orc_splitmix64(orc_splitmix64(parent) ^ (((uint64_t)step << 2) | (uint64_t)k));
+}
+
+/* uniform in [0,1) with 53 random bits from counter (id, step, event, 0) */
+double orc_uniform(uint64_t seed, uint64_t id, int64_t step, int event)
+{
+    uint64_t ctr[4] = {id, (uint64_t)step, (uint64_t)event, 0}, key[2] = {seed, 0}, out[4];
+    orc_philox4x64(ctr, key, out);
+    return (double)(out[0] >> 11) * (1.0 / 9007199254740992.0);
+}
+
+typedef struct {
+    int n;                       /* cells along the line                     */
+    double a, theta, r_in, r_out, dx1;
+    double dt;
+    int n_push_iter;
+    double qm[4], qw[4];
+    int massive[4];
+    double I0;                   /* imposed line current (J A units)        */
+    double gamma_thr, eps_ph, tau;
+    uint64_t seed;
+} orc_line;
+
+static double line_r(const orc_line *L, double x) { return L->r_in * exp(x * L->dx1); }
+
+/* A_r of the flux tube at D^r location i+1/2 (per unit theta and phi) */
+void orc_line_area(const orc_line *L, double *A)
+{
+    for (int i = 0; i < L->n; ++i) {
+        orc_metric m;
+        metric_at(L->a, line_r(L, i + 0.5), L->theta, &m);
+        A[i] = m.sqrtg;
+    }
+}
+
+/* D^r on the line from the monopole closed form (App. C) */
+void orc_line_init_D(const orc_line *L, double B0, double *D)
+{
+    for (int i = 0; i < L->n; ++i) {
+        double Dv[3], Bu[3];
+        closed_D(2, L->a, B0, line_r(L, i + 0.5), L->theta, Dv, Bu);
+        D[i] = Dv[0];
+    }
+}
+
+static double line_D_at(const orc_line *L, const double *D, double x)
+{
+    double xi = x - 0.5;
+    int i = (int)floor(xi);
+    double f = xi - i;
+    int i0 = i < 0 ? 0 : (i > L->n - 1 ? L->n - 1 : i);
+    int i1 = i + 1 < 0 ? 0 : (i + 1 > L->n - 1 ? L->n - 1 : i + 1);
+    return (1.0 - f) * D[i0] + f * D[i1];
+}
+
+static double line_gamma(const orc_line *L, double r, double ur, double up, double eps)
+{
+    orc_metric m;
+    metric_at(L->a, r, L->theta, &m);
+    return sqrt(eps + m.gi_rr * ur * ur + 2.0 * m.gi_rp * ur * up + m.gi_pp * up * up);
+}
+
+/* One step of one line.  Arrays hold *np particles (capacity cap): logical
+ * position x1, covariant u_r, u_phi, tag (species | DEAD), id.  D has n
+ * entries, JA (output) n+2 faces (index f+1 for face f = -1..n).  Survivors
+ * keep their order; particles created this step follow in parent order.
+ * counts[0] = photons emitted, counts[1] = photons converted. */
+int orc_line_step(const orc_line *L, int64_t step, long *np, long cap, double *x1, double *ur, double *up,
+                  uint32_t *tag, uint64_t *id, double *D, double *JA, long *counts)
+{
+    int status = ORC_OK;
+    long n0 = *np, nnew = 0;
+    double *nx = malloc(sizeof(double) * (2 * n0 + 2));
+    double *nur = malloc(sizeof(double) * (2 * n0 + 2));
+    double *nup = malloc(sizeof(double) * (2 * n0 + 2));
+    uint32_t *ntag = malloc(sizeof(uint32_t) * (2 * n0 + 2));
+    uint64_t *nid = malloc(sizeof(uint64_t) * (2 * n0 + 2));
+    double *A = malloc(sizeof(double) * L->n);
+    orc_line_area(L, A);
+    memset(JA, 0, sizeof(double) * (L->n + 2));
+    counts[0] = counts[1] = 0;
+    double Pconv = 1.0 - exp(-L->tau * L->dt);
+    for (long p = 0; p < n0; ++p) {
+        if (tag[p] & ORC_DEAD) continue;
+        int sp = tag[p] & 3u;
+        int massive = L->massive[sp];
+        double xa = x1[p];
+        double y[6] = {line_r(L, xa), L->theta, 0.0, ur[p], 0.0, up[p]};
+        if (massive && L->qm[sp] != 0.0) {
+            /* electric part of the Boris step along the line: u_r += (q/m) alpha dt gamma_rr D^r */
+            orc_metric m;
+            metric_at(L->a, y[0], L->theta, &m);
+            y[3] += L->qm[sp] * m.alpha * L->dt * m.g_rr * line_D_at(L, D, xa);
+        }
+        /* geodesic predictor-corrector restricted to (r, u_r) */
+        double eps = massive ? 1.0 : 0.0;
+        double y0[6], f0[6], yt[6], ft[6];
+        memcpy(y0, y, sizeof y0);
+        geo_rhs(L->a, eps, y0, f0);
+        memcpy(yt, y0, sizeof yt);
+        yt[0] = y0[0] + L->dt * f0[0];
+        yt[3] = y0[3] + L->dt * f0[3];
+        for (int it = 0; it < L->n_push_iter; ++it) {
+            geo_rhs(L->a, eps, yt, ft);
+            yt[0] = y0[0] + 0.5 * L->dt * (ft[0] + f0[0]);
+            yt[3] = y0[3] + 0.5 * L->dt * (ft[3] + f0[3]);
+        }
+        if (!isfinite(yt[0]) || !isfinite(yt[3]) || yt[0] <= 0.0) {
+            tag[p] |= ORC_DEAD;
+            status = status ? status : ORC_ENAN;
+            continue;
+        }
+        double xb = log(yt[0] / L->r_in) / L->dx1;
+        int i0 = (int)floor(xa), di = (int)floor(xb) - i0;
+        if (di < -1 || di > 1) {
+            tag[p] |= ORC_DEAD;
+            status = status ? status : ORC_ERANGE;
+            continue;
+        }
+        if (L->qw[sp] != 0.0) {
+            /* 1D Esirkepov: J A(face k+1/2) = -(q/dt) sum_{k'<=k} (S1 - S0)(k') */
+            double acc = 0.0;
+            for (int k = i0 - 1; k <= i0 + 2; ++k) {
+                acc += W1(xb - k) - W1(xa - k);
+                if (k >= -1 && k <= L->n) JA[k + 1] += -L->qw[sp] / L->dt * acc;
+            }
+        }
+        x1[p] = xb;
+        ur[p] = yt[3];
+        double r = yt[0];
+        if (r < L->r_in || r >= L->r_out) { tag[p] |= ORC_DEAD; continue; }
+        if (massive && L->qm[sp] != 0.0) {
+            double G = line_gamma(L, r, ur[p], up[p], 1.0);
+            if (G >= L->gamma_thr) {
+                double pm = sqrt(G * G - 1.0), G2 = G - L->eps_ph, pm2 = sqrt(G2 * G2 - 1.0);
+                double kr = L->eps_ph * ur[p] / pm, kp = L->eps_ph * up[p] / pm;
+                ur[p] *= pm2 / pm;
+                up[p] *= pm2 / pm;
+                nx[nnew] = xb; nur[nnew] = kr; nup[nnew] = kp; ntag[nnew] = 3u;
+                nid[nnew] = orc_child_id(id[p], step, 0);
+                ++nnew;
+                counts[0]++;
+            }
+        } else if (!massive) {
+            double e = line_gamma(L, r, ur[p], up[p], 0.0);
+            double u = orc_uniform(L->seed, id[p], step, 1);
+            if (e > 2.0 && u < Pconv) {
+                double pp = sqrt(0.25 * e * e - 1.0), s = pp / e;
+                tag[p] |= ORC_DEAD;
+                for (int k = 0; k < 2; ++k) {
+                    nx[nnew] = xb; nur[nnew] = s * ur[p]; nup[nnew] = s * up[p]; ntag[nnew] = (uint32_t)k;
+                    nid[nnew] = orc_child_id(id[p], step, 1 + k);
+                    ++nnew;
+                }
+                counts[1]++;
+            }
+        }
+    }
+    /* field: d(A D)/dt = I0 - J A at every D^r location */
+    for (int i = 0; i < L->n; ++i) D[i] += L->dt * (L->I0 - JA[i + 1]) / A[i];
+    /* compaction: survivors in order, then the new particles in parent order */
+    long w = 0;
+    for (long p = 0; p < n0; ++p) {
+        if (tag[p] & ORC_DEAD) continue;
+        x1[w] = x1[p]; ur[w] = ur[p]; up[w] = up[p]; tag[w] = tag[p]; id[w] = id[p];
+        ++w;
+    }
+    for (long k = 0; k < nnew; ++k) {
+        if (w >= cap) { status = status ? status : 6; break; }
+        x1[w] = nx[k]; ur[w] = nur[k]; up[w] = nup[k]; tag[w] = ntag[k]; id[w] = nid[k];
+        ++w;
+    }
+    *np = w;
+    free(nx); free(nur); free(nup); free(ntag); free(nid); free(A);
+    return status;
+}
