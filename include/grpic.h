@@ -193,6 +193,90 @@ grpic_status grpic_get_areas(grpic_ctx *ctx, double *const out[6], int64_t ld, v
  * word, and return the first device error recorded (GRPIC_OK if none). */
 grpic_status grpic_sync(grpic_ctx *ctx, void *stream);
 
+/* ------------------------------------------------------------------------ */
+/* Batched 1D spark gaps: the radiative pair-production prescription of     */
+/* Sec. 4 (threshold photon emission at the FIDO Lorentz factor gamma_thr    */
+/* with FIDO energy eps_ph along the emitter's momentum; photon conversion   */
+/* with probability 1 - exp(-tau dt) per step, Eq. optical-depth, into an   */
+/* e-/e+ pair sharing the photon's FIDO energy) on many independent radial  */
+/* field lines of a monopole Kerr magnetosphere.  Each line k at fixed      */
+/* theta_k has n_cells cells uniform in ln r on [r_in, r_out] and one field */
+/* component D^r at (i+1/2) obeying d(A_r D^r)/dt = I0_k - J^r A_r (A_r =    */
+/* sqrt(gamma) at (r_{i+1/2}, theta_k), I0_k an imposed line current).      */
+/* Particles slide along the line (theta frozen, u_theta = 0, u_phi kept):  */
+/* electric kick q/m alpha dt gamma_rr D^r, geodesic predictor-corrector in */
+/* (r, u_r) (Eqs. geodesic-predictor/-corrector), 1D Esirkepov deposit.      */
+/* Random draws: Philox4x64-10 keyed on (seed, 0) with counter (particle id,*/
+/* step, 1, 0); a uniform is the top 53 bits of the first output word.      */
+/* Children get the id splitmix64(splitmix64(parent) ^ (step << 2 | k)),    */
+/* k = 0 photon, 1 electron, 2 positron.  After each step a line holds its  */
+/* surviving particles in their previous order followed by the particles    */
+/* created in that step in the order of their parents.                      */
+/* FP32 particles and fields; the emission threshold and the conversion     */
+/* decision are taken in FP64.                                              */
+/* ------------------------------------------------------------------------ */
+typedef struct grpic_batch1d_ctx grpic_batch1d_ctx;
+
+typedef struct {
+    int32_t n_lines, n_cells;
+    double a, r_in, r_out, dt;
+    int32_t n_push_iter;
+    double q_over_m[4], q_weight[4];
+    int32_t massive[4];
+    double gamma_thr, eps_ph, tau;
+    double B0;          /* monopole strength of the initial D^r (App. C) */
+    uint64_t seed;      /* Philox key word 0                              */
+    int64_t capacity;   /* particle slots per line in each buffer         */
+} grpic_batch1d_params;
+
+/* Caller-owned device arrays.  Line k's particles occupy slots
+ * [k*capacity, k*capacity + count[k]) of buffer `cur`; the other buffer is
+ * the destination of the next step (the two are swapped every step). */
+typedef struct {
+    double *theta;       /* [n_lines] line inclination theta_k              */
+    double *I0;          /* [n_lines] imposed line current (J A units)      */
+    float *D;            /* [n_lines][n_cells] D^r at i+1/2                 */
+    float *JA;           /* [n_lines][n_cells+2] J^r A_r of the last step at
+                            faces -1..n_cells (output; NULL = not written)  */
+    int32_t *count;      /* [n_lines] particles per line                    */
+    int32_t *cell[2];    /* cell index i along the line                     */
+    float *off[2];       /* offset in [0,1) inside the cell (logical units) */
+    float *ur[2], *up[2];/* covariant u_r, u_phi                            */
+    uint32_t *tag[2];    /* species 0 e-, 1 e+, 3 photon (| bit 31 dead)    */
+    uint64_t *id[2];     /* particle identity (RNG counter)                 */
+    int32_t cur;         /* buffer holding the state; updated by the runs   */
+    unsigned long long *events; /* [2] accumulated emissions, conversions  */
+} grpic_lines;
+
+/* Validate the parameters, build the radius table and the staging scratch
+ * (appended particles of one step, capacity/2 slots per line). */
+grpic_status grpic_batch1d_init(const grpic_batch1d_params *params, grpic_batch1d_ctx **out);
+
+/* A_r along every line and the initial D^r of the monopole (App. C) at
+ * (r_{i+1/2}, theta_k). */
+grpic_status grpic_batch1d_init_fields(grpic_batch1d_ctx *ctx, grpic_lines *lines, void *stream);
+
+/* nsteps steps (global step numbers step0 .. step0+nsteps-1) of every line
+ * in one persistent launch: CTAs take lines from a device queue ordered by
+ * decreasing particle count, keep D^r and J^r A_r of their line in shared
+ * memory and run all nsteps for it.  Capacity overflow drops the excess
+ * appended particles and latches GRPIC_EOVERFLOW (read by
+ * grpic_batch1d_sync). */
+grpic_status grpic_batch1d_run(grpic_batch1d_ctx *ctx, grpic_lines *lines, int nsteps, int64_t step0, void *stream);
+
+/* Autotuner: runs trial_steps real steps (starting at step0) with each
+ * candidate (threads per block, blocks per SM), times them with CUDA events
+ * and keeps the fastest for later runs.  Advances the state by
+ * trial_steps * (number of candidates) steps, returned in *steps_done;
+ * best[0] = threads per block, best[1] = blocks per SM. */
+grpic_status grpic_batch1d_tune(grpic_batch1d_ctx *ctx, grpic_lines *lines, int trial_steps, int64_t step0,
+                                int64_t *steps_done, int32_t best[2], void *stream);
+
+/* Wait for `stream`, return and clear the first latched device error. */
+grpic_status grpic_batch1d_sync(grpic_batch1d_ctx *ctx, void *stream);
+
+void grpic_batch1d_destroy(grpic_batch1d_ctx *ctx);
+
 /* Largest sizes grpic_sort_noalloc accepts (the size of its fixed scratch). */
 #define GRPIC_NOALLOC_MAX_PARTICLES 2097152 /* slots p->n                  */
 #define GRPIC_NOALLOC_MAX_CELLS 262144      /* n_r * n_theta (e.g. 512^2)   */

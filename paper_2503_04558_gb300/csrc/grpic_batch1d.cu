@@ -1,0 +1,683 @@
+// grpic_batch1d.cu -- batched 1D spark gaps in one persistent launch.
+//
+// The pair-production prescription of arXiv:2503.04558 Sec. 4 (Eq.
+// optical-depth) on independent radial lines of a monopole magnetosphere.
+// One CTA owns one line at a time (taken from a device queue ordered by
+// decreasing particle count) and runs every step of the launch for it with
+// the line's D^r, A_r and J^r A_r in shared memory, so fields never travel to
+// HBM between steps; lines are independent, so no CTA ever waits for another.
+// Per step the CTA streams the line's particles in chunks of blockDim: push
+// (electric kick along the line, geodesic predictor-corrector in (r, u_r)),
+// 1D Esirkepov deposit into shared memory, FP64 emission / conversion
+// decisions with Philox4x64-10, then one packed block scan places survivors
+// (in order) in the other buffer and the children (in parent order) in a
+// staging area that is appended after the survivors at the end of the step.
+#include "grpic_geo.cuh"
+
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+namespace grpic {
+namespace {
+
+constexpr int MAX_LINES = 4096;
+
+struct B1Args {
+    int nl, n;
+    double a, r_in, dx1, dt, gthr, eps_ph, Pconv;
+    float af, dx1f, dtf;
+    int n_iter;
+    float qm[4], qw[4];
+    int massive[4];
+    uint64_t seed;
+    int64_t C, Cs;
+    const double *theta, *I0;
+    float *D;
+    const float *Ar;
+    float *JA;
+    const double *rcol;  // r at integer positions 0..n
+    int32_t *count;
+    int32_t *cell[2];
+    float *off[2], *ur[2], *up[2];
+    uint32_t *tag[2];
+    uint64_t *id[2];
+    int32_t *s_cell;
+    float *s_off, *s_ur, *s_up;
+    uint32_t *s_tag;
+    uint64_t *s_id;
+    const int32_t *order;
+    int32_t *queue;
+    int cur, nsteps;
+    int64_t step0;
+    int *status;
+    unsigned long long *events;
+};
+
+// ---- counter-based random numbers ----------------------------------------
+__device__ __forceinline__ void philox4x64_10(uint64_t c[4], uint64_t k0, uint64_t k1)
+{
+    const uint64_t M0 = 0xD2E7470EE14C6C93ULL, M1 = 0xCA5A826395121157ULL;
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r > 0) {
+            k0 += 0x9E3779B97F4A7C15ULL;
+            k1 += 0xBB67AE8584CAA73BULL;
+        }
+        uint64_t lo0 = M0 * c[0], hi0 = __umul64hi(M0, c[0]);
+        uint64_t lo1 = M1 * c[2], hi1 = __umul64hi(M1, c[2]);
+        uint64_t n0 = hi1 ^ c[1] ^ k0, n2 = hi0 ^ c[3] ^ k1;
+        c[0] = n0;
+        c[1] = lo1;
+        c[2] = n2;
+        c[3] = lo0;
+    }
+}
+
+__device__ __forceinline__ double uniform53(uint64_t seed, uint64_t id, int64_t step, int event)
+{
+    uint64_t c[4] = {id, (uint64_t)step, (uint64_t)event, 0ULL};
+    philox4x64_10(c, seed, 0ULL);
+    return (double)(c[0] >> 11) * (1.0 / 9007199254740992.0);
+}
+
+__device__ __forceinline__ uint64_t splitmix64(uint64_t x)
+{
+    uint64_t z = x + 0x9E3779B97F4A7C15ULL;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+
+__device__ __forceinline__ uint64_t child_id(uint64_t parent, int64_t step, int k)
+{
+    return splitmix64(splitmix64(parent) ^ (((uint64_t)step << 2) | (uint64_t)k));
+}
+
+// ---- line geometry in FP64 for the decisions ------------------------------
+// gamma^rr, gamma^rphi, gamma^phiphi at (r, theta) (App. A, Eq. gamma-inverse)
+__device__ __forceinline__ void ginv64(double a, double r, double s, double c, double &grr, double &grp, double &gpp)
+{
+    double rho2 = r * r + a * a * c * c;
+    double ir = 1.0 / rho2;
+    double z = 2.0 * r * ir;
+    grr = (a * a + r * r) * ir - z / (1.0 + z);
+    grp = a * ir;
+    gpp = ir / (s * s);
+}
+
+__device__ __forceinline__ float W1f(float d)
+{
+    d = fabsf(d);
+    return d < 1.0f ? 1.0f - d : 0.0f;
+}
+
+// block-wide exclusive scan of one int per thread; returns the total
+__device__ __forceinline__ int block_scan(int v, int *wsum, int &excl)
+{
+    int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    int x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) wsum[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        int w = lane < nw ? wsum[lane] : 0;
+        int wi = w;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(0xffffffffu, wi, o);
+            if (lane >= o) wi += y;
+        }
+        if (lane < nw) wsum[lane] = wi - w;
+        if (lane == 31) wsum[32] = wi;
+    }
+    __syncthreads();
+    excl = wsum[warp] + x - v;
+    int total = wsum[32];
+    __syncthreads();
+    return total;
+}
+
+struct Kid {
+    int32_t cell;
+    float off, ur, up;
+    uint32_t tag;
+    uint64_t id;
+};
+
+__global__ void b1_kernel(B1Args A)
+{
+    extern __shared__ float smem[];
+    const int n = A.n;
+    float *sD = smem;
+    float *sA = sD + n;
+    float *sJ = sA + n;                      // n + 2 faces (-1..n)
+    int *wsum = (int *)(sJ + n + 2);         // 33 ints
+    int *sv = wsum + 34;                     // [0] line, [1] wptr, [2] sptr, [3] emit, [4] conv, [5] flags
+    const int tid = threadIdx.x, B = blockDim.x;
+
+    for (;;) {
+        if (tid == 0) sv[0] = atomicAdd(A.queue, 1);
+        __syncthreads();
+        int q = sv[0];
+        __syncthreads();
+        if (q >= A.nl) break;
+        const int k = A.order[q];
+        const double th = A.theta[k];
+        double sd, cd;
+        sincos(th, &sd, &cd);
+        const float sf = (float)sd, cf = (float)cd;
+        const float I0 = (float)A.I0[k];
+        for (int i = tid; i < n; i += B) {
+            sD[i] = A.D[(size_t)k * n + i];
+            sA[i] = A.Ar[(size_t)k * n + i];
+        }
+        int cnt = A.count[k];
+        if (cnt > A.C) cnt = (int)A.C;
+        if (cnt < 0) cnt = 0;
+        const size_t base = (size_t)k * A.C, sbase = (size_t)k * A.Cs;
+        for (int st = 0; st < A.nsteps; ++st) {
+            const int64_t step = A.step0 + st;
+            const int src = (A.cur + st) & 1, dst = src ^ 1;
+            for (int i = tid; i < n + 2; i += B) sJ[i] = 0.0f;
+            if (tid == 0) {
+                sv[1] = 0;
+                sv[2] = 0;
+                sv[3] = 0;
+                sv[4] = 0;
+            }
+            __syncthreads();
+            for (int cb = 0; cb < cnt; cb += B) {
+                const int idx = cb + tid;
+                bool alive = false;
+                int napp = 0;
+                Kid kid[2];
+                int32_t ci = 0;
+                float o = 0.f, ur = 0.f, up = 0.f;
+                uint32_t tg = DEAD;
+                uint64_t pid = 0;
+                if (idx < cnt) {
+                    size_t p = base + idx;
+                    ci = A.cell[src][p];
+                    o = A.off[src][p];
+                    ur = A.ur[src][p];
+                    up = A.up[src][p];
+                    tg = A.tag[src][p];
+                    pid = A.id[src][p];
+                }
+                if (idx < cnt && !(tg & DEAD) && ci >= 0 && ci < n) {
+                    const int sp = tg & 3u;
+                    const bool massive = A.massive[sp] != 0, charged = A.qm[sp] != 0.0f;
+                    const float rcf = (float)A.rcol[ci];
+                    const float d0 = rcf * expm1f(o * A.dx1f);  // r - r_i
+                    if (massive && charged) {
+                        // electric part of the Boris step along the line
+                        float xi = o - 0.5f, f = xi;
+                        int is = ci;
+                        if (xi < 0.0f) {
+                            is = ci - 1;
+                            f = xi + 1.0f;
+                        }
+                        int a0 = min(max(is, 0), n - 1), a1 = min(max(is + 1, 0), n - 1);
+                        float Dp = (1.0f - f) * sD[a0] + f * sD[a1];
+                        float r = rcf + d0;
+                        float rho2 = r * r + A.af * A.af * cf * cf;
+                        float opz = 1.0f + 2.0f * r / rho2;
+                        ur += A.qm[sp] * rsqrtf(opz) * A.dtf * opz * Dp;
+                    }
+                    const float eps = massive ? 1.0f : 0.0f;
+                    KSGeo<float> m;
+                    RhsT<float> f0, ft;
+                    ks_geo_sc<float>(A.af, rcf + d0, sf, cf, m);
+                    geo_rhs_m<float, float>(m, eps, ur, 0.0f, up, f0);
+                    float dl = d0 + A.dtf * f0.xr, u1 = ur + A.dtf * f0.ur;
+                    const float h = 0.5f * A.dtf;
+                    for (int it = 0; it < A.n_iter; ++it) {
+                        ks_geo_sc<float>(A.af, rcf + dl, sf, cf, m);
+                        geo_rhs_m<float, float>(m, eps, u1, 0.0f, up, ft);
+                        dl = d0 + h * (ft.xr + f0.xr);
+                        u1 = ur + h * (ft.ur + f0.ur);
+                    }
+                    float on = log1pf(dl / rcf) / A.dx1f;
+                    if (!(isfinite(on) && isfinite(u1) && rcf + dl > 0.0f)) {
+                        set_status(A.status, GRPIC_ENAN);
+                    } else {
+                        int di = (int)floorf(on);
+                        if (di < -1 || di > 1) {
+                            set_status(A.status, GRPIC_ERANGE);
+                        } else {
+                            if (A.qw[sp] != 0.0f) {
+                                // 1D Esirkepov: J A(face f) -= (q/dt) sum_{k'<=f} (S1 - S0)
+                                float acc = 0.0f, cq = -A.qw[sp] / A.dtf;
+#pragma unroll
+                                for (int w = 0; w < 4; ++w) {
+                                    acc += W1f(on - (float)(w - 1)) - W1f(o - (float)(w - 1));
+                                    int face = ci - 1 + w;
+                                    if (acc != 0.0f && face >= -1 && face <= n) atomicAdd(&sJ[face + 1], cq * acc);
+                                }
+                            }
+                            int ni = ci + di;
+                            float no = on - (float)di;
+                            if (no >= 1.0f) no = 0x1.fffffep-1f;
+                            if (no < 0.0f) no = 0.0f;
+                            ur = u1;
+                            if (ni >= 0 && ni < n) {
+                                alive = true;
+                                ci = ni;
+                                o = no;
+                                // FP64 decisions at the new position
+                                if (massive && charged) {
+                                    // FP32 screen, FP64 decision inside the ambiguity band
+                                    float rf = (float)A.rcol[ci] * (1.0f + expm1f(o * A.dx1f));
+                                    float rho2 = rf * rf + A.af * A.af * cf * cf, ir = 1.0f / rho2, z = 2.0f * rf * ir;
+                                    float gr = (A.af * A.af + rf * rf) * ir - z / (1.0f + z), gp = A.af * ir,
+                                          gq = ir / (sf * sf);
+                                    float G2 = 1.0f + gr * ur * ur + 2.0f * gp * ur * up + gq * up * up;
+                                    if (G2 >= (float)(A.gthr * A.gthr) * 0.9999f) {
+                                        double rd = A.rcol[ci] * exp((double)o * A.dx1), grr, grp, gpp;
+                                        ginv64(A.a, rd, sd, cd, grr, grp, gpp);
+                                        double urd = ur, upd = up;
+                                        double G = sqrt(1.0 + grr * urd * urd + 2.0 * grp * urd * upd + gpp * upd * upd);
+                                        if (G >= A.gthr) {
+                                            double pm = sqrt(G * G - 1.0), Gn = G - A.eps_ph;
+                                            double pm2 = sqrt(Gn * Gn - 1.0), sc = pm2 / pm;
+                                            kid[0].cell = ci;
+                                            kid[0].off = o;
+                                            kid[0].ur = (float)(A.eps_ph * urd / pm);
+                                            kid[0].up = (float)(A.eps_ph * upd / pm);
+                                            kid[0].tag = 3u;
+                                            kid[0].id = child_id(pid, step, 0);
+                                            ur = (float)(urd * sc);
+                                            up = (float)(upd * sc);
+                                            napp = 1;
+                                        }
+                                    }
+                                } else if (!massive) {
+                                    double rd = A.rcol[ci] * exp((double)o * A.dx1), grr, grp, gpp;
+                                    ginv64(A.a, rd, sd, cd, grr, grp, gpp);
+                                    double urd = ur, upd = up;
+                                    double e = sqrt(grr * urd * urd + 2.0 * grp * urd * upd + gpp * upd * upd);
+                                    double u = uniform53(A.seed, pid, step, 1);
+                                    if (e > 2.0 && u < A.Pconv) {
+                                        double s = sqrt(0.25 * e * e - 1.0) / e;
+                                        for (int w = 0; w < 2; ++w) {
+                                            kid[w].cell = ci;
+                                            kid[w].off = o;
+                                            kid[w].ur = (float)(s * urd);
+                                            kid[w].up = (float)(s * upd);
+                                            kid[w].tag = (uint32_t)w;
+                                            kid[w].id = child_id(pid, step, 1 + w);
+                                        }
+                                        napp = 2;
+                                        alive = false;
+                                    }
+                                }
+                            }
+                        }
+                    }
+                }
+                // placement: survivors in order, children in parent order
+                int excl;
+                int tot = block_scan((alive ? 1 : 0) | (napp << 16), wsum, excl);
+                int wp = sv[1], sp0 = sv[2];
+                if (alive) {
+                    size_t d = base + wp + (excl & 0xffff);
+                    A.cell[dst][d] = ci;
+                    A.off[dst][d] = o;
+                    A.ur[dst][d] = ur;
+                    A.up[dst][d] = up;
+                    A.tag[dst][d] = tg;
+                    A.id[dst][d] = pid;
+                }
+                int ap = sp0 + (excl >> 16);
+                for (int w = 0; w < napp; ++w) {
+                    if (ap + w < A.Cs) {
+                        size_t d = sbase + ap + w;
+                        A.s_cell[d] = kid[w].cell;
+                        A.s_off[d] = kid[w].off;
+                        A.s_ur[d] = kid[w].ur;
+                        A.s_up[d] = kid[w].up;
+                        A.s_tag[d] = kid[w].tag;
+                        A.s_id[d] = kid[w].id;
+                    }
+                }
+                if (napp == 1) atomicAdd(&sv[3], 1);
+                if (napp == 2) atomicAdd(&sv[4], 1);
+                __syncthreads();
+                if (tid == 0) {
+                    sv[1] = wp + (tot & 0xffff);
+                    sv[2] = sp0 + (tot >> 16);
+                }
+                __syncthreads();
+            }
+            // children after the survivors
+            const int wptr = sv[1], sptr = sv[2];
+            int nap = min(sptr, (int)A.Cs);
+            int room = (int)(A.C - wptr);
+            int ncopy = min(nap, room);
+            if (tid == 0 && ncopy < sptr) set_status(A.status, GRPIC_EOVERFLOW);
+            for (int j = tid; j < ncopy; j += B) {
+                size_t s = sbase + j, d = base + wptr + j;
+                A.cell[dst][d] = A.s_cell[s];
+                A.off[dst][d] = A.s_off[s];
+                A.ur[dst][d] = A.s_ur[s];
+                A.up[dst][d] = A.s_up[s];
+                A.tag[dst][d] = A.s_tag[s];
+                A.id[dst][d] = A.s_id[s];
+            }
+            cnt = wptr + ncopy;
+            // field: d(A D)/dt = I0 - J A
+            for (int i = tid; i < n; i += B) sD[i] += A.dtf * (I0 - sJ[i + 1]) / sA[i];
+            if (A.JA && st == A.nsteps - 1)
+                for (int i = tid; i < n + 2; i += B) A.JA[(size_t)k * (n + 2) + i] = sJ[i];
+            if (tid == 0) {
+                if (sv[3]) atomicAdd(&A.events[0], (unsigned long long)sv[3]);
+                if (sv[4]) atomicAdd(&A.events[1], (unsigned long long)sv[4]);
+            }
+            __syncthreads();
+        }
+        for (int i = tid; i < n; i += B) A.D[(size_t)k * n + i] = sD[i];
+        if (tid == 0) A.count[k] = cnt;
+        __syncthreads();
+    }
+}
+
+// order the lines by decreasing particle count (ties by index) and reset the
+// work queue: one block, bitonic network in shared memory
+__global__ void order_kernel(const int32_t *count, int nl, int32_t *order, int32_t *queue)
+{
+    __shared__ unsigned long long key[MAX_LINES];
+    int N = 1;
+    while (N < nl) N <<= 1;
+    for (int i = threadIdx.x; i < N; i += blockDim.x)
+        key[i] = i < nl ? ((unsigned long long)(0x7fffffffu - (uint32_t)count[i]) << 32) | (uint32_t)i : ~0ULL;
+    __syncthreads();
+    for (int kk = 2; kk <= N; kk <<= 1) {
+        for (int j = kk >> 1; j > 0; j >>= 1) {
+            for (int i = threadIdx.x; i < N; i += blockDim.x) {
+                int l = i ^ j;
+                if (l > i) {
+                    bool up = (i & kk) == 0;
+                    unsigned long long a = key[i], b = key[l];
+                    if ((a > b) == up) {
+                        key[i] = b;
+                        key[l] = a;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+    for (int i = threadIdx.x; i < nl; i += blockDim.x) order[i] = (int32_t)(key[i] & 0xffffffffu);
+    if (threadIdx.x == 0) *queue = 0;
+}
+
+// A_r = sqrt(gamma) at (r_{i+1/2}, theta_k) and the monopole D^r there (App. C)
+__global__ void b1_fields_kernel(int nl, int n, double a, double r_in, double dx1, double B0, const double *theta,
+                                 float *Ar, float *D)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    int k = blockIdx.y;
+    if (i >= n || k >= nl) return;
+    double r = r_in * exp((i + 0.5) * dx1), th = theta[k];
+    double s, c;
+    sincos(th, &s, &c);
+    KS m;
+    ks_point(a, r, th, m);
+    double rho2 = r * r + a * a * c * c, rho4 = rho2 * rho2;
+    double Er = -B0 * 2.0 * a * r * c / rho4;
+    double sgBth = -B0 * 2.0 * a * a * r * s * s * c / rho4;  // sqrt(gamma) B^theta
+    double Eph = -m.beta * sgBth;                             // E_phi - e_{phi r theta} beta B^theta
+    Ar[(size_t)k * n + i] = (float)m.sqrtg;
+    D[(size_t)k * n + i] = (float)((m.gi_rr * Er + m.gi_rp * Eph) / m.alpha);
+}
+
+}  // namespace
+}  // namespace grpic
+
+struct grpic_batch1d_ctx {
+    grpic_batch1d_params p;
+    double *rcol;
+    float *Ar;
+    int32_t *order, *queue;
+    int *status;
+    int32_t *s_cell;
+    float *s_off, *s_ur, *s_up;
+    uint32_t *s_tag;
+    uint64_t *s_id;
+    int64_t Cs;
+    int block, per_sm, sms;
+    size_t smem;
+};
+
+using namespace grpic;
+
+namespace {
+
+B1Args make_args(grpic_batch1d_ctx *c, grpic_lines *L, int nsteps, int64_t step0)
+{
+    B1Args A;
+    memset(&A, 0, sizeof A);
+    const grpic_batch1d_params &p = c->p;
+    A.nl = p.n_lines;
+    A.n = p.n_cells;
+    A.a = p.a;
+    A.af = (float)p.a;
+    A.r_in = p.r_in;
+    A.dx1 = std::log(p.r_out / p.r_in) / p.n_cells;
+    A.dx1f = (float)A.dx1;
+    A.dt = p.dt;
+    A.dtf = (float)p.dt;
+    A.n_iter = p.n_push_iter;
+    for (int s = 0; s < 4; ++s) {
+        A.qm[s] = (float)p.q_over_m[s];
+        A.qw[s] = (float)p.q_weight[s];
+        A.massive[s] = p.massive[s];
+    }
+    A.gthr = p.gamma_thr;
+    A.eps_ph = p.eps_ph;
+    A.Pconv = -std::expm1(-p.tau * p.dt);
+    A.seed = p.seed;
+    A.C = p.capacity;
+    A.Cs = c->Cs;
+    A.theta = L->theta;
+    A.I0 = L->I0;
+    A.D = L->D;
+    A.Ar = c->Ar;
+    A.JA = L->JA;
+    A.rcol = c->rcol;
+    A.count = L->count;
+    for (int b = 0; b < 2; ++b) {
+        A.cell[b] = L->cell[b];
+        A.off[b] = L->off[b];
+        A.ur[b] = L->ur[b];
+        A.up[b] = L->up[b];
+        A.tag[b] = L->tag[b];
+        A.id[b] = L->id[b];
+    }
+    A.s_cell = c->s_cell;
+    A.s_off = c->s_off;
+    A.s_ur = c->s_ur;
+    A.s_up = c->s_up;
+    A.s_tag = c->s_tag;
+    A.s_id = c->s_id;
+    A.order = c->order;
+    A.queue = c->queue;
+    A.cur = L->cur;
+    A.nsteps = nsteps;
+    A.step0 = step0;
+    A.status = c->status;
+    A.events = L->events;
+    return A;
+}
+
+bool lines_ok(const grpic_lines *L)
+{
+    if (!L || !L->theta || !L->I0 || !L->D || !L->count || !L->events || (L->cur != 0 && L->cur != 1)) return false;
+    for (int b = 0; b < 2; ++b)
+        if (!L->cell[b] || !L->off[b] || !L->ur[b] || !L->up[b] || !L->tag[b] || !L->id[b]) return false;
+    return true;
+}
+
+cudaError_t launch_b1(grpic_batch1d_ctx *c, grpic_lines *L, int nsteps, int64_t step0, int block, int per_sm,
+                      cudaStream_t s)
+{
+    order_kernel<<<1, 1024, 0, s>>>(L->count, c->p.n_lines, c->order, c->queue);
+    B1Args A = make_args(c, L, nsteps, step0);
+    b1_kernel<<<c->sms * per_sm, block, c->smem, s>>>(A);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+extern "C" {
+
+grpic_status grpic_batch1d_init(const grpic_batch1d_params *p, grpic_batch1d_ctx **out)
+{
+    if (!out) return GRPIC_EINVAL;
+    *out = nullptr;
+    if (!p || p->n_lines < 1 || p->n_lines > MAX_LINES || p->n_cells < 4 || p->n_cells > 8192 ||
+        !(p->a >= 0.0 && p->a < 1.0) || !(p->r_in > 0.0 && p->r_out > p->r_in) || !(p->dt > 0.0) ||
+        p->n_push_iter < 0 || p->n_push_iter > 64 || p->capacity < 1 || p->capacity > (int64_t)1 << 30 ||
+        !(p->gamma_thr > 1.0) || !(p->eps_ph > 0.0) || !(p->tau >= 0.0) || p->gamma_thr <= p->eps_ph + 1.0)
+        return GRPIC_EINVAL;
+    grpic_batch1d_ctx *c = new (std::nothrow) grpic_batch1d_ctx();
+    if (!c) return GRPIC_ENOMEM;
+    memset((void *)c, 0, sizeof *c);
+    c->p = *p;
+    int n = p->n_cells;
+    c->Cs = p->capacity / 2 > 0 ? p->capacity / 2 : 1;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, dev);
+    c->smem = sizeof(float) * (3 * (size_t)n + 2) + sizeof(int) * 48;
+    size_t ns = (size_t)p->n_lines * c->Cs;
+    cudaError_t e = cudaMalloc(&c->rcol, sizeof(double) * (n + 1));
+    if (e == cudaSuccess) e = cudaMalloc(&c->Ar, sizeof(float) * (size_t)p->n_lines * n);
+    if (e == cudaSuccess) e = cudaMalloc(&c->order, sizeof(int32_t) * p->n_lines);
+    if (e == cudaSuccess) e = cudaMalloc(&c->queue, sizeof(int32_t) * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&c->status, sizeof(int) * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&c->s_cell, sizeof(int32_t) * ns);
+    if (e == cudaSuccess) e = cudaMalloc(&c->s_off, sizeof(float) * ns);
+    if (e == cudaSuccess) e = cudaMalloc(&c->s_ur, sizeof(float) * ns);
+    if (e == cudaSuccess) e = cudaMalloc(&c->s_up, sizeof(float) * ns);
+    if (e == cudaSuccess) e = cudaMalloc(&c->s_tag, sizeof(uint32_t) * ns);
+    if (e == cudaSuccess) e = cudaMalloc(&c->s_id, sizeof(uint64_t) * ns);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(b1_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->smem);
+    if (e != cudaSuccess) {
+        grpic_batch1d_destroy(c);
+        return GRPIC_ENOMEM;
+    }
+    std::vector<double> r(n + 1);
+    double dx1 = std::log(p->r_out / p->r_in) / n;
+    for (int i = 0; i <= n; ++i) r[i] = p->r_in * std::exp(i * dx1);
+    cudaMemcpy(c->rcol, r.data(), sizeof(double) * (n + 1), cudaMemcpyHostToDevice);
+    cudaMemset(c->status, 0, sizeof(int) * 4);
+    // default launch shape until the tuner picks one
+    c->block = 256;
+    c->per_sm = 2;
+    int maxb = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&maxb, b1_kernel, c->block, c->smem);
+    if (maxb < 1) {
+        grpic_batch1d_destroy(c);
+        return GRPIC_EINVAL;
+    }
+    if (c->per_sm > maxb) c->per_sm = maxb;
+    *out = c;
+    return GRPIC_OK;
+}
+
+grpic_status grpic_batch1d_init_fields(grpic_batch1d_ctx *c, grpic_lines *L, void *stream)
+{
+    if (!c || !lines_ok(L)) return GRPIC_EINVAL;
+    const grpic_batch1d_params &p = c->p;
+    dim3 blk(256), grd((p.n_cells + 255) / 256, p.n_lines);
+    b1_fields_kernel<<<grd, blk, 0, (cudaStream_t)stream>>>(p.n_lines, p.n_cells, p.a, p.r_in,
+                                                             std::log(p.r_out / p.r_in) / p.n_cells, p.B0, L->theta,
+                                                             c->Ar, L->D);
+    return cudaGetLastError() == cudaSuccess ? GRPIC_OK : GRPIC_ECUDA;
+}
+
+grpic_status grpic_batch1d_run(grpic_batch1d_ctx *c, grpic_lines *L, int nsteps, int64_t step0, void *stream)
+{
+    if (!c || !lines_ok(L) || nsteps < 0) return GRPIC_EINVAL;
+    if (nsteps == 0) return GRPIC_OK;
+    cudaError_t e = launch_b1(c, L, nsteps, step0, c->block, c->per_sm, (cudaStream_t)stream);
+    if (e != cudaSuccess) return GRPIC_ECUDA;
+    if (nsteps & 1) L->cur ^= 1;
+    return GRPIC_OK;
+}
+
+grpic_status grpic_batch1d_tune(grpic_batch1d_ctx *c, grpic_lines *L, int trial_steps, int64_t step0,
+                                int64_t *steps_done, int32_t best[2], void *stream)
+{
+    if (!c || !lines_ok(L) || trial_steps < 1 || !steps_done || !best) return GRPIC_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int blocks[4] = {128, 256, 512, 1024};
+    const int persm[3] = {1, 2, 4};
+    float best_ms = 1e30f;
+    int bb = c->block, bp = c->per_sm;
+    int64_t done = 0;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    for (int b : blocks) {
+        for (int ps : persm) {
+            int maxb = 0;
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&maxb, b1_kernel, b, c->smem);
+            if (ps > maxb) continue;
+            cudaEventRecord(e0, s);
+            if (launch_b1(c, L, trial_steps, step0 + done, b, ps, s) != cudaSuccess) {
+                cudaEventDestroy(e0);
+                cudaEventDestroy(e1);
+                return GRPIC_ECUDA;
+            }
+            cudaEventRecord(e1, s);
+            cudaEventSynchronize(e1);
+            if (trial_steps & 1) L->cur ^= 1;
+            done += trial_steps;
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (ms < best_ms) {
+                best_ms = ms;
+                bb = b;
+                bp = ps;
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    c->block = bb;
+    c->per_sm = bp;
+    best[0] = bb;
+    best[1] = bp;
+    *steps_done = done;
+    return GRPIC_OK;
+}
+
+grpic_status grpic_batch1d_sync(grpic_batch1d_ctx *c, void *stream)
+{
+    if (!c) return GRPIC_EINVAL;
+    if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) return GRPIC_ECUDA;
+    int st = 0;
+    if (cudaMemcpy(&st, c->status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return GRPIC_ECUDA;
+    if (st) cudaMemset(c->status, 0, sizeof(int));
+    return (grpic_status)st;
+}
+
+void grpic_batch1d_destroy(grpic_batch1d_ctx *c)
+{
+    if (!c) return;
+    void *ptrs[] = {c->rcol, c->Ar, c->order, c->queue, c->status, c->s_cell,
+                    c->s_off, c->s_ur, c->s_up, c->s_tag, c->s_id};
+    for (void *q : ptrs)
+        if (q) cudaFree(q);
+    delete c;
+}
+
+}  // extern "C"

@@ -356,3 +356,198 @@ class Context:
     def sync(self, stream=None) -> int:
         """Wait for the stream and return (and clear) the device status."""
         return self.lib.grpic_sync(self.h, _stream(stream))
+
+
+# ---------------------------------------------------------------------------
+# batched 1D spark gaps
+# ---------------------------------------------------------------------------
+class Batch1DParams(C.Structure):
+    _fields_ = [("n_lines", C.c_int32), ("n_cells", C.c_int32), ("a", C.c_double), ("r_in", C.c_double),
+                ("r_out", C.c_double), ("dt", C.c_double), ("n_push_iter", C.c_int32),
+                ("q_over_m", C.c_double * 4), ("q_weight", C.c_double * 4), ("massive", C.c_int32 * 4),
+                ("gamma_thr", C.c_double), ("eps_ph", C.c_double), ("tau", C.c_double), ("B0", C.c_double),
+                ("seed", C.c_uint64), ("capacity", C.c_int64)]
+
+
+class LinesC(C.Structure):
+    _fields_ = [("theta", C.c_void_p), ("I0", C.c_void_p), ("D", C.c_void_p), ("JA", C.c_void_p),
+                ("count", C.c_void_p), ("cell", C.c_void_p * 2), ("off", C.c_void_p * 2), ("ur", C.c_void_p * 2),
+                ("up", C.c_void_p * 2), ("tag", C.c_void_p * 2), ("id", C.c_void_p * 2), ("cur", C.c_int32),
+                ("events", C.c_void_p)]
+
+
+def _load_b1(lib):
+    v, p = C.c_void_p, C.POINTER
+    for name, args in {"grpic_batch1d_init": [p(Batch1DParams), p(v)],
+                       "grpic_batch1d_init_fields": [v, p(LinesC), v],
+                       "grpic_batch1d_run": [v, p(LinesC), C.c_int, C.c_int64, v],
+                       "grpic_batch1d_tune": [v, p(LinesC), C.c_int, C.c_int64, p(C.c_int64), p(C.c_int32), v],
+                       "grpic_batch1d_sync": [v, v]}.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = C.c_int
+    lib.grpic_batch1d_destroy.argtypes = [v]
+    lib.grpic_batch1d_destroy.restype = None
+
+
+EXPORTS += ["grpic_batch1d_init", "grpic_batch1d_init_fields", "grpic_batch1d_run", "grpic_batch1d_tune",
+            "grpic_batch1d_sync", "grpic_batch1d_destroy"]
+
+
+@dataclass
+class Batch1DConfig:
+    """Batched radial lines (the spark-gap workload): n_lines lines of n_cells
+    cells uniform in ln r on [r_in, r_out]; dt defaults to cfl * dr at r_in."""
+    n_lines: int
+    n_cells: int
+    a: float
+    r_in: float
+    r_out: float
+    capacity: int
+    dt: float | None = None
+    cfl: float = 0.5
+    n_push_iter: int = 3
+    q_over_m: tuple = (-1.0, 1.0, 1.0, 0.0)
+    q_weight: tuple = (-1.0, 1.0, 1.0, 0.0)
+    massive: tuple = (1, 1, 1, 0)
+    gamma_thr: float = 100.0
+    eps_ph: float = 4.0
+    tau: float = 2.0
+    B0: float = 2.0e3
+    seed: int = 0
+
+    def __post_init__(self):
+        self.dx1 = math.log(self.r_out / self.r_in) / self.n_cells
+        if self.dt is None:
+            self.dt = self.cfl * self.r_in * (math.exp(self.dx1) - 1.0)
+
+    def c(self):
+        p = Batch1DParams()
+        p.n_lines, p.n_cells, p.a, p.r_in, p.r_out, p.dt = self.n_lines, self.n_cells, self.a, self.r_in, \
+            self.r_out, self.dt
+        p.n_push_iter = self.n_push_iter
+        for k in range(4):
+            p.q_over_m[k], p.q_weight[k], p.massive[k] = self.q_over_m[k], self.q_weight[k], self.massive[k]
+        p.gamma_thr, p.eps_ph, p.tau, p.B0 = self.gamma_thr, self.eps_ph, self.tau, self.B0
+        p.seed, p.capacity = self.seed, self.capacity
+        return p
+
+
+class Lines:
+    """Device state of all lines (torch tensors) and the C struct view."""
+
+    def __init__(self, cfg: Batch1DConfig, device="cuda"):
+        import torch
+        nl, n, cap = cfg.n_lines, cfg.n_cells, cfg.capacity
+        self.cfg = cfg
+        self.theta = torch.zeros(nl, dtype=torch.float64, device=device)
+        self.I0 = torch.zeros(nl, dtype=torch.float64, device=device)
+        self.D = torch.zeros(nl, n, dtype=torch.float32, device=device)
+        self.JA = torch.zeros(nl, n + 2, dtype=torch.float32, device=device)
+        self.count = torch.zeros(nl, dtype=torch.int32, device=device)
+        self.events = torch.zeros(2, dtype=torch.int64, device=device)
+        self.buf = []
+        for _ in range(2):
+            self.buf.append(dict(cell=torch.zeros(nl, cap, dtype=torch.int32, device=device),
+                                 off=torch.zeros(nl, cap, dtype=torch.float32, device=device),
+                                 ur=torch.zeros(nl, cap, dtype=torch.float32, device=device),
+                                 up=torch.zeros(nl, cap, dtype=torch.float32, device=device),
+                                 tag=torch.zeros(nl, cap, dtype=torch.int32, device=device),
+                                 id=torch.zeros(nl, cap, dtype=torch.int64, device=device)))
+        self._c = LinesC()
+        self._c.cur = 0
+        self._refresh()
+
+    def _refresh(self):
+        c = self._c
+        c.theta, c.I0, c.D, c.JA = (t.data_ptr() for t in (self.theta, self.I0, self.D, self.JA))
+        c.count, c.events = self.count.data_ptr(), self.events.data_ptr()
+        for b in range(2):
+            c.cell[b] = self.buf[b]["cell"].data_ptr()
+            c.off[b] = self.buf[b]["off"].data_ptr()
+            c.ur[b] = self.buf[b]["ur"].data_ptr()
+            c.up[b] = self.buf[b]["up"].data_ptr()
+            c.tag[b] = self.buf[b]["tag"].data_ptr()
+            c.id[b] = self.buf[b]["id"].data_ptr()
+
+    @property
+    def cur(self):
+        return self._c.cur
+
+    def set_line(self, k, cell, off, ur, up, tag, pid):
+        """Write line k's particles into the current buffer (host arrays)."""
+        import torch
+        b = self.buf[self.cur]
+        n = len(cell)
+        if n > self.cfg.capacity:
+            raise ValueError("capacity exceeded")
+        dev = self.D.device
+        b["cell"][k, :n] = torch.as_tensor(np.asarray(cell, np.int32), device=dev)
+        b["off"][k, :n] = torch.as_tensor(np.asarray(off, np.float32), device=dev)
+        b["ur"][k, :n] = torch.as_tensor(np.asarray(ur, np.float32), device=dev)
+        b["up"][k, :n] = torch.as_tensor(np.asarray(up, np.float32), device=dev)
+        b["tag"][k, :n] = torch.as_tensor(np.asarray(tag, np.uint32).view(np.int32), device=dev)
+        b["id"][k, :n] = torch.as_tensor(np.asarray(pid, np.uint64).view(np.int64), device=dev)
+        self.count[k] = n
+
+    def line(self, k):
+        """Line k's particles from the current buffer as numpy arrays."""
+        b = self.buf[self.cur]
+        n = int(self.count[k].item())
+        return dict(cell=b["cell"][k, :n].cpu().numpy(), off=b["off"][k, :n].cpu().numpy(),
+                    ur=b["ur"][k, :n].cpu().numpy(), up=b["up"][k, :n].cpu().numpy(),
+                    tag=b["tag"][k, :n].cpu().numpy().view(np.uint32),
+                    id=b["id"][k, :n].cpu().numpy().view(np.uint64))
+
+
+import numpy as np  # noqa: E402  (used by Lines)
+
+
+class Batch1D:
+    """Owns one grpic_batch1d_ctx."""
+
+    def __init__(self, cfg: Batch1DConfig):
+        import torch
+        torch.cuda.current_device()
+        self.lib = load()
+        _load_b1(self.lib)
+        self.cfg = cfg
+        self._p = cfg.c()
+        h = C.c_void_p()
+        st = self.lib.grpic_batch1d_init(C.byref(self._p), C.byref(h))
+        if st != OK:
+            raise GrpicError(st, "grpic_batch1d_init failed")
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.grpic_batch1d_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def init_fields(self, L: Lines, stream=None):
+        st = self.lib.grpic_batch1d_init_fields(self.h, C.byref(L._c), _stream(stream))
+        if st != OK:
+            raise GrpicError(st, "grpic_batch1d_init_fields")
+
+    def run(self, L: Lines, nsteps, step0, stream=None):
+        st = self.lib.grpic_batch1d_run(self.h, C.byref(L._c), nsteps, step0, _stream(stream))
+        if st != OK:
+            raise GrpicError(st, "grpic_batch1d_run")
+
+    def tune(self, L: Lines, trial_steps, step0, stream=None):
+        done = C.c_int64()
+        best = (C.c_int32 * 2)()
+        st = self.lib.grpic_batch1d_tune(self.h, C.byref(L._c), trial_steps, step0, C.byref(done), best,
+                                         _stream(stream))
+        if st != OK:
+            raise GrpicError(st, "grpic_batch1d_tune")
+        return done.value, (best[0], best[1])
+
+    def sync(self, stream=None):
+        return self.lib.grpic_batch1d_sync(self.h, _stream(stream))
