@@ -245,7 +245,8 @@ typedef struct {
     uint32_t *tag[2];    /* species 0 e-, 1 e+, 3 photon (| bit 31 dead)    */
     uint64_t *id[2];     /* particle identity (RNG counter)                 */
     int32_t cur;         /* buffer holding the state; updated by the runs   */
-    unsigned long long *events; /* [2] accumulated emissions, conversions  */
+    unsigned long long *events; /* [3] accumulated photons emitted, photons
+                                   converted, particle pushes performed     */
 } grpic_lines;
 
 /* Validate the parameters, build the radius table and the staging scratch

@@ -190,6 +190,7 @@ __global__ void b1_kernel(B1Args A)
                 sv[2] = 0;
                 sv[3] = 0;
                 sv[4] = 0;
+                sv[5] = cnt;
             }
             __syncthreads();
             for (int cb = 0; cb < cnt; cb += B) {
@@ -378,6 +379,7 @@ __global__ void b1_kernel(B1Args A)
             if (tid == 0) {
                 if (sv[3]) atomicAdd(&A.events[0], (unsigned long long)sv[3]);
                 if (sv[4]) atomicAdd(&A.events[1], (unsigned long long)sv[4]);
+                atomicAdd(&A.events[2], (unsigned long long)sv[5]);  // particles pushed this step
             }
             __syncthreads();
         }

@@ -445,7 +445,7 @@ class Lines:
         self.D = torch.zeros(nl, n, dtype=torch.float32, device=device)
         self.JA = torch.zeros(nl, n + 2, dtype=torch.float32, device=device)
         self.count = torch.zeros(nl, dtype=torch.int32, device=device)
-        self.events = torch.zeros(2, dtype=torch.int64, device=device)
+        self.events = torch.zeros(3, dtype=torch.int64, device=device)
         self.buf = []
         for _ in range(2):
             self.buf.append(dict(cell=torch.zeros(nl, cap, dtype=torch.int32, device=device),
