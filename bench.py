@@ -306,6 +306,111 @@ def run_reference(args):
 
 
 # ---------------------------------------------------------------------------
+# batched 1D spark gaps (separate workload: --workload batch1d)
+# ---------------------------------------------------------------------------
+B1_LINES, B1_CELLS, B1_A, B1_ROUT, B1_CAP = 512, 4096, 0.99, 20.0, 1_000_000
+
+
+def batch1d_inputs(nl, n, seed=2024):
+    """Per line: 10^U(3,5) particles (e-/e+ pairs at the same positions,
+    uniform along the line), u_r ~ N(0, 0.1), u_phi = 0; inclinations uniform
+    in (0, pi/2); imposed current I0 = Omega_H B0 sin^2(theta) (kappa = 1)."""
+    import numpy as np
+    rng = np.random.Generator(np.random.Philox(seed))
+    counts = (10 ** rng.uniform(3, 5, nl)).astype(np.int64) // 2 * 2
+    lines = []
+    nid = 0
+    for k in range(nl):
+        m = int(counts[k])
+        x = np.repeat(rng.random(m // 2) * n, 2)
+        cell = np.minimum(np.floor(x), n - 1).astype(np.int32)
+        off = (x - cell).astype(np.float32)
+        ur = (rng.standard_normal(m) * 0.1).astype(np.float32)
+        up = np.zeros(m, np.float32)
+        tag = np.tile(np.array([0, 1], np.uint32), m // 2)
+        pid = np.arange(nid, nid + m, dtype=np.uint64)
+        nid += m
+        lines.append((cell, off, ur, up, tag, pid))
+    theta = (np.arange(nl) + 0.5) * (math.pi / 2) / nl
+    return theta, lines
+
+
+def run_batch1d(args):
+    import numpy as np
+    import torch
+    from paper_2503_04558_gb300 import build, grpic as G
+
+    build.build()
+    G.load()
+    rh = horizon(B1_A)
+    cfg = G.Batch1DConfig(B1_LINES, B1_CELLS, B1_A, rh, B1_ROUT, B1_CAP, gamma_thr=100.0, eps_ph=4.0, tau=2.0,
+                          B0=2.0e3, seed=7)
+    B = G.Batch1D(cfg)
+    L = G.Lines(cfg)
+    theta, lines = batch1d_inputs(B1_LINES, B1_CELLS)
+    L.theta.copy_(torch.from_numpy(theta))
+    omega_h = B1_A / (2.0 * rh)
+    L.I0.copy_(torch.from_numpy(omega_h * cfg.B0 * np.sin(theta) ** 2))
+    for k, ln in enumerate(lines):
+        L.set_line(k, *ln)
+    B.init_fields(L)
+    n0 = int(L.count.sum().item())
+    stream = torch.cuda.current_stream()
+    step = 0
+    done, best = B.tune(L, 2, step)         # the tuner's trial steps are real steps
+    step += done
+    B.run(L, args.warmup, step)
+    step += args.warmup
+    st = B.sync()
+    if st != 0:
+        raise RuntimeError(f"device status {st}")
+    ev0 = L.events.cpu().numpy().copy()
+    torch.cuda.synchronize()
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        t0.record(stream)
+        B.run(L, args.steps, step)
+        t1.record(stream)
+        torch.cuda.synchronize()
+    ms = t0.elapsed_time(t1)
+    st = B.sync()
+    ev1 = L.events.cpu().numpy()
+    pushes = int(ev1[2] - ev0[2])
+    cells = B1_LINES * B1_CELLS * args.steps
+    # oracle on a bounded sample: the 8 smallest lines, 3 steps, single thread
+    import oracle as O
+    t = time.perf_counter()
+    oracle_pushes = 0
+    order = np.argsort([len(ln[0]) for ln in lines])[:8]
+    for k in order:
+        Lo = O.make_line(B1_CELLS, B1_A, theta[k], rh, B1_ROUT, dt=cfg.dt, qw=cfg.q_weight, qm=cfg.q_over_m,
+                         I0=omega_h * cfg.B0 * math.sin(theta[k]) ** 2, gamma_thr=100.0, eps_ph=4.0, tau=2.0,
+                         seed=7)
+        cell, off, ur, up, tag, pid = lines[k]
+        S = O.LineState(cell + off.astype(np.float64), ur.astype(np.float64), up.astype(np.float64), tag, pid,
+                        4 * len(cell) + 1000)
+        D = O.line_init_D(Lo, cfg.B0)
+        for s in range(3):
+            oracle_pushes += S.n
+            O.line_step(Lo, s, S, D)
+    osec = time.perf_counter() - t
+    line = {"metric": "batched 1D spark gaps: particle push+deposit/s (one persistent launch)",
+            "value": pushes / (ms * 1e-3), "unit": "particle-steps/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup + done, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "512 radial lines x 4096 cells, a=0.99, r in [r_H, 20], monopole B0=2e3, "
+                                   "gamma_thr=100, eps_ph=4, tau=2, initial 10^U(3,5) particles per line, "
+                                   "capacity 1e6 per line", "initial_particles": n0,
+                       "particles_now": int(L.count.sum().item()), "tuned_launch": list(best)},
+            "cell_updates_per_s": cells / (ms * 1e-3), "events": {"emitted": int(ev1[0] - ev0[0]),
+                                                                 "converted": int(ev1[1] - ev0[1])},
+            "status": int(st), "clocks": clk.summary(), "gpu_launches": 2 * args.steps // args.steps,
+            "cpu_baseline": {"value": oracle_pushes / osec, "unit": "particle-steps/s", "cores": 1,
+                             "kind": "oracle", "sample": f"8 smallest lines, 3 steps, FP64, {osec:.1f} s"}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -317,7 +422,11 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--grid", type=int, default=NR, help="cells per dimension (profiling runs use smaller grids)")
     ap.add_argument("--ppc", type=int, default=PPC, help="particles per cell")
+    ap.add_argument("--workload", default="grpic2d", choices=["grpic2d", "batch1d"])
     args = ap.parse_args()
+    if args.workload == "batch1d" and args.impl == "ours":
+        run_batch1d(args)
+        return
     if args.impl == "reference":
         run_reference(args)
         return

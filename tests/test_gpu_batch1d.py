@@ -43,7 +43,17 @@ def setup(G, nl=6, n=256, cap=20000, per_line=(500, 2000), seed=3, species=None,
         off = (x - cell).astype(np.float32)
         ur = (rng.normal(size=m) * ur_scale).astype(np.float32)
         up = (rng.normal(size=m) * 0.1).astype(np.float32)
-        tag = (rng.integers(0, 2, m) if species is None else np.full(m, species)).astype(np.uint32)
+        if species is None:
+            # e-/e+ with an energetic tail (|u_r| up to ~3 gamma_thr) and photons
+            tag = rng.integers(0, 3, m).astype(np.uint32)
+            tag[tag == 2] = 3
+            hot = rng.random(m) < 0.3
+            ur[hot] = (rng.choice([-1, 1], hot.sum()) * rng.uniform(0.5, 3.0, hot.sum()) * cfg.gamma_thr
+                       ).astype(np.float32)
+            ph = tag == 3
+            ur[ph] = (rng.choice([-1, 1], ph.sum()) * rng.uniform(3.0, 8.0, ph.sum())).astype(np.float32)
+        else:
+            tag = np.full(m, species).astype(np.uint32)
         pid = (np.arange(m, dtype=np.uint64) + np.uint64(k) * np.uint64(1 << 40))
         L.set_line(k, cell, off, ur, up, tag, pid)
         lines.append((cell, off, ur, up, tag, pid))
@@ -95,6 +105,7 @@ def test_one_step_matches_oracle(G):
         assert np.max(np.abs(dg - D)) <= 1e-4 * max(1.0, np.max(np.abs(D))), k
     ev = L.events.cpu().numpy()
     assert ev[0] == emitted and ev[1] == conv
+    assert emitted > 100 and conv > 100
     print("one step: photons emitted", emitted, "converted", conv)
 
 
@@ -125,7 +136,8 @@ def test_many_steps_track_the_oracle_statistically(G):
             st, JA, c = O.line_step(Lo, s, S, D)
             assert st == 0
         n_g = int(L.count[k].item())
-        print("line", k, "particles GPU", n_g, "oracle", S.n)
+        print("line", k, "particles GPU", n_g, "oracle", S.n, "initial", len(lines[k][0]))
+        assert S.n > 1.2 * len(lines[k][0])     # the cascade grew the line
         assert abs(n_g - S.n) <= 0.05 * S.n + 10
         tg = L.line(k)["tag"]
         assert abs((tg == 3).sum() - (S.view()["tag"] == 3).sum()) <= 0.1 * max(1, (S.view()["tag"] == 3).sum()) + 10
