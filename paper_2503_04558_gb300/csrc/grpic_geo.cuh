@@ -16,6 +16,7 @@ struct KSGeo {
     T alpha, beta, grr, grp, gtt, gpp;
     T da_r, da_t, db_r, db_t;
     T dgrr_r, dgrr_t, dgrp_r, dgrp_t, dgtt_r, dgtt_t, dgpp_r, dgpp_t;
+    T rho2, ir, opz;  // rho^2, 1/rho^2, 1 + z (for the lower metric of the Boris step)
 };
 
 template <typename T>
@@ -23,17 +24,44 @@ struct RhsT {
     T xr, xt, xp, ur, ut;
 };
 
-// FP64: the library's IEEE functions.  FP32 (the FP32 form, whose error
-// budget is 1e-4 against FP64): hardware approximations with a relative error
-// of a few ulp for reciprocal and square root; sin/cos keep the accurate
-// sincosf because near the polar axis sin(theta) needs relative accuracy
-// (the fast __sincosf has an absolute error of ~2^-21).
+// FP32 (the FP32 form, whose error budget is 1e-4 against FP64): hardware
+// approximations with a relative error of a few ulp for reciprocal and square
+// root; sin/cos keep the accurate sincosf because near the polar axis
+// sin(theta) needs relative accuracy (the fast __sincosf has an absolute error
+// of ~2^-21).  FP64 (the FP64 island of the FP32 form): reciprocal and square
+// root from an FP32 seed refined by two Newton steps in FP64 (relative error
+// below 2^-52 for the normal range used here), sin/cos from the library.
 __device__ __forceinline__ void sincos_t(double x, double *s, double *c) { sincos(x, s, c); }
 __device__ __forceinline__ void sincos_t(float x, float *s, float *c) { sincosf(x, s, c); }
-__device__ __forceinline__ double sqrt_t(double x) { return sqrt(x); }
-__device__ __forceinline__ float sqrt_t(float x) { return x > 0.0f ? x * rsqrtf(x) : 0.0f; }
-__device__ __forceinline__ double rcp_t(double x) { return 1.0 / x; }
+__device__ __forceinline__ double rcp_t(double x)
+{
+    double y = (double)__frcp_rn((float)x);
+    y = y * (2.0 - x * y);
+    return y * (2.0 - x * y);
+}
 __device__ __forceinline__ float rcp_t(float x) { return __fdividef(1.0f, x); }
+__device__ __forceinline__ double sqrt_t(double x)
+{
+    if (!(x > 0.0)) return 0.0;
+    double y = (double)rsqrtf((float)x);       // 1/sqrt(x), 2^-22
+    y = y * (1.5 - 0.5 * x * y * y);           // 2^-44
+    y = y * (1.5 - 0.5 * x * y * y);           // full precision
+    double s = x * y;
+    return s + 0.5 * y * (x - s * s);          // one correction of the root itself
+}
+__device__ __forceinline__ float sqrt_t(float x) { return x > 0.0f ? x * rsqrtf(x) : 0.0f; }
+
+// sin, cos of (theta0 + d) from sin, cos of theta0 and a short Taylor series
+// of sin d, cos d; for |d| <= 0.05 the truncated terms are below 1e-17.
+template <typename T>
+__device__ __forceinline__ void sincos_shift(T s0, T c0, T d, T &s, T &c)
+{
+    T d2 = d * d;
+    T sd = d * (T(1) - d2 * (T(1) / T(6)) * (T(1) - d2 * (T(1) / T(20)) * (T(1) - d2 * (T(1) / T(42)))));
+    T cd = T(1) - d2 * T(0.5) * (T(1) - d2 * (T(1) / T(12)) * (T(1) - d2 * (T(1) / T(30)) * (T(1) - d2 * (T(1) / T(56)))));
+    s = s0 * cd + c0 * sd;
+    c = c0 * cd - s0 * sd;
+}
 
 // metric + derivatives at (r, theta) given sin/cos of theta
 template <typename T>
@@ -45,6 +73,9 @@ __device__ __forceinline__ void ks_geo_sc(T a, T r, T s, T c, KSGeo<T> &m)
     T ir2 = ir * ir;
     T z = T(2) * r * ir;
     T iopz = rcp_t(T(1) + z);
+    m.rho2 = rho2;
+    m.ir = ir;
+    m.opz = T(1) + z;
     m.alpha = sqrt_t(iopz);
     m.beta = z * iopz;
     T is2 = rcp_t(s * s);

@@ -102,32 +102,6 @@ __device__ __forceinline__ void boris32(const KSPoint<M> &mm, float qm, float dt
     u[2] = um2 + sg * (x0 * s1 - x1 * s0) + h * Dl2;
 }
 
-// right-hand side at r = r_i + dr (dr = r - r_i relative to the cell's inner
-// edge, so the trapezoidal rule acts on r exactly as in Eq. geodesic-corrector)
-// and theta = (j + o2) dtheta; metric in type M.  Returns d(dr)/dt and d(o2)/dt.
-template <typename M>
-__device__ __forceinline__ void rhs_off(const GridDev &g, double rci, int j, float dr, float o2, float eps, float ur,
-                                        float ut, float up, RhsT<float> &f)
-{
-    M r, th;
-    if (sizeof(M) == 8) {
-        r = (M)(rci + (double)dr);
-        th = (M)(((double)j + (double)o2) * g.dth);
-    } else {
-        r = (M)rci + (M)dr;
-        th = (M)(((float)j + o2) * (float)g.dth);
-    }
-    KSGeo<M> m;
-    ks_geo<M>((M)g.a, r, th, m);
-    RhsT<float> fx;
-    geo_rhs_m<M, float>(m, eps, ur, ut, up, fx);
-    f.xr = fx.xr;
-    f.xt = fx.xt * (float)(1.0 / g.dth);
-    f.xp = fx.xp;
-    f.ur = fx.ur;
-    f.ut = fx.ut;
-}
-
 struct St32 {
     int c0, r0, r1;
     float w00, w10, w01, w11, p0, p1;
@@ -179,12 +153,48 @@ __device__ __forceinline__ float W1f(float d)
 
 constexpr int NWIN = 40;
 
+// generalized Boris step in FP32 with the metric of type M at x^n (the lower
+// metric is rebuilt from the quantities the geodesic evaluation keeps)
+template <typename M>
+__device__ __forceinline__ void boris_geo(const KSGeo<M> &m, M a, M r, M s, float qm, float dt, const float D[3],
+                                          const float B[3], float u[3])
+{
+    // gamma_rr = 1+z, gamma_thth = rho^2, gamma_phph = Sigma sin^2 / rho^2,
+    // gamma_rph = -a sin^2 (1+z), sqrt(gamma) = rho^2 sin sqrt(1+z) = rho^2 sin / alpha
+    M r2 = r * r;
+    M s2 = s * s;
+    M Dl = r2 + a * a - M(2) * r;
+    M Sg = (r2 + a * a) * (r2 + a * a) - a * a * Dl * s2;
+    KSPoint<float> mm;
+    mm.alpha = (float)m.alpha;
+    mm.g_rr = (float)m.opz;
+    mm.g_tt = (float)m.rho2;
+    mm.g_pp = (float)(Sg * s2 * m.ir);
+    mm.g_rp = (float)(-a * s2 * m.opz);
+    mm.gi_rr = (float)m.grr;
+    mm.gi_rp = (float)m.grp;
+    mm.gi_tt = (float)m.gtt;
+    mm.gi_pp = (float)m.gpp;
+    mm.sqrtg = (float)(m.rho2 * s / m.alpha);
+    boris32<float>(mm, qm, dt, D, B, u);
+}
+
 template <typename M>
 __device__ __forceinline__ void push_one(const Push32Args &A, int i, int j, float &o1, float &o2, float u[3], int sp,
                                          float &dphi)
 {
     const GridDev &g = A.g;
-    double rci = A.rcol[i + NG];
+    const double rci = A.rcol[i + NG];
+    const float rcf = (float)rci, dx1f = (float)g.dx1;
+    const M am = (M)g.a;
+    const float d0 = rcf * expm1f(o1 * dx1f);  // r - r_i
+    // metric at x^n, shared by the Boris step and the first right-hand side
+    M r0 = (M)rci + (M)d0;
+    M th0 = (sizeof(M) == 8) ? (M)(((double)j + (double)o2) * g.dth) : (M)(((float)j + o2) * (float)g.dth);
+    M s0, c0;
+    sincos_t(th0, &s0, &c0);
+    KSGeo<M> m;
+    ks_geo_sc<M>(am, r0, s0, c0, m);
     if (A.massive[sp] && A.qm[sp] != 0.0f) {
         St32 Sh0, S0h, S00, Shh;
         stencil32(g, i, j, o1, o2, true, false, 1.0f, Sh0);
@@ -199,28 +209,28 @@ __device__ __forceinline__ void push_one(const Push32Args &A, int i, int j, floa
         Bv[2] = gather32(A.B2, A.ld, Shh);
         S0h.p0 = S0h.p1 = 1.0f;
         Bv[0] = gather32(A.B0, A.ld, S0h);
-        KSPoint<M> mm;
-        M r, th;
-        if (sizeof(M) == 8) {
-            r = (M)(rci + (double)((float)rci * expm1f(o1 * (float)g.dx1)));
-            th = (M)(((double)j + (double)o2) * g.dth);
-        } else {
-            r = (M)rci * (M)(1.0f + expm1f(o1 * (float)g.dx1));
-            th = (M)(((float)j + o2) * (float)g.dth);
-        }
-        ks_point_t<M>((M)g.a, r, th, mm);
-        boris32<M>(mm, A.qm[sp], A.dt, Dv, Bv, u);
+        boris_geo<M>(m, am, r0, s0, A.qm[sp], A.dt, Dv, Bv, u);
     }
-    float eps = A.massive[sp] ? 1.0f : 0.0f;
-    float dt = A.dt, h = 0.5f * dt;
-    float rcf = (float)rci, dx1f = (float)g.dx1;
-    float d0 = rcf * expm1f(o1 * dx1f);  // r - r_i
+    const float eps = A.massive[sp] ? 1.0f : 0.0f;
+    const float dt = A.dt, h = 0.5f * dt;
+    const float idth = (float)(1.0 / g.dth);
     RhsT<float> f0, ft;
-    rhs_off<M>(g, rci, j, d0, o2, eps, u[0], u[1], u[2], f0);
+    geo_rhs_m<M, float>(m, eps, u[0], u[1], u[2], f0);
+    f0.xt *= idth;
     float a1 = d0 + dt * f0.xr, a2 = o2 + dt * f0.xt, ap = dt * f0.xp;
     float b1 = u[0] + dt * f0.ur, b2 = u[1] + dt * f0.ut;
     for (int it = 0; it < A.n_iter; ++it) {
-        rhs_off<M>(g, rci, j, a1, a2, eps, b1, b2, u[2], ft);
+        // metric at the iterate: theta = theta^n + (a2 - o2) dtheta
+        M dth_it = (sizeof(M) == 8) ? (M)(((double)a2 - (double)o2) * g.dth) : (M)((a2 - o2) * (float)g.dth);
+        M s, c;
+        if (fabs((double)dth_it) <= 0.05)
+            sincos_shift<M>(s0, c0, dth_it, s, c);
+        else
+            sincos_t(th0 + dth_it, &s, &c);
+        KSGeo<M> mi;
+        ks_geo_sc<M>(am, (M)rci + (M)a1, s, c, mi);
+        geo_rhs_m<M, float>(mi, eps, b1, b2, u[2], ft);
+        ft.xt *= idth;
         float n1 = d0 + h * (ft.xr + f0.xr), n2 = o2 + h * (ft.xt + f0.xt);
         float nb1 = u[0] + h * (ft.ur + f0.ur), nb2 = u[1] + h * (ft.ut + f0.ut);
         ap = h * (ft.xp + f0.xp);
