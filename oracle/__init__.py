@@ -79,6 +79,7 @@ def lib():
             "orc_rho": (None, [pc, l, p, p, p, p]),
             "orc_divD": (None, [pc, p, p, p]),
             "orc_divB": (None, [pc, p, p, p]),
+            "orc_horizon_flux": (d, [pc, p, p, p, p, p, p, i]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(_lib, name)
@@ -414,3 +415,30 @@ def line_step(L, step, S: LineState, D):
                             _p(S.id), _p(D), _p(JA), _p(counts))
     S.n = n.value
     return st, JA, counts
+
+
+# --------------------------------------------------------------------------
+# differentiable form: objective and its finite-difference gradient
+# --------------------------------------------------------------------------
+def horizon_index(c: Cfg, a_nominal: float) -> int:
+    """Vertex ring nearest the horizon of the nominal spin (the grid stays
+    fixed when the spin is varied)."""
+    return int(round(math.log(horizon(a_nominal) / c.r_in) / c.dx1))
+
+
+def horizon_flux(c: Cfg, D, B, iH: int) -> float:
+    return lib().orc_horizon_flux(C.byref(c), *[_p(x) for x in list(D) + list(B)], iH)
+
+
+def flux_run(c: Cfg, P: Particles, D, B, nsteps: int, iH: int) -> float:
+    """Time-averaged horizon flux over nsteps steps (push + deposit, field
+    update; no sort, which only permutes particles): L = (1/N) sum_n flux(F^{n+1})."""
+    P = P.copy()
+    D = [x.copy() for x in D]
+    B = [x.copy() for x in B]
+    L = 0.0
+    for _ in range(nsteps):
+        st, J, _ = push_deposit(c, P, D, B)
+        field_update(c, D, B, J)
+        L += horizon_flux(c, D, B, iH)
+    return L / nsteps

@@ -1307,3 +1307,31 @@ int orc_line_step(const orc_line *L, int64_t step, long *np, long cap, double *x
     free(nx); free(nur); free(nup); free(ntag); free(nid); free(A);
     return status;
 }
+
+/* ======================================================================== */
+/* Objective of the differentiable form: the radial Poynting flux through   */
+/* the vertex ring i_H nearest the horizon, sum over theta cells of         */
+/* (E_theta H_phi - E_phi H_theta) dtheta (dphi = 1), with E_i, H_i the      */
+/* auxiliary fields of Eq. E-H-B-D (App. B forms) and every factor brought  */
+/* to (i_H, j+1/2) by the two- or four-point averages of the Yee layout.    */
+/* ======================================================================== */
+double orc_horizon_flux(const orc_cfg *c, double *D0, double *D1, double *D2, double *B0r, double *B1, double *B2,
+                        int iH)
+{
+    orc_geom g = *geom_get(c);
+    double *D[3] = {D0, D1, D2}, *B[3] = {B0r, B1, B2};
+    double *E[3], *H[3];
+    for (int k = 0; k < 3; ++k) { E[k] = malloc(g.n * sizeof(double)); H[k] = malloc(g.n * sizeof(double)); }
+    aux_fields(&g, D, B, E, H);
+    double L = 0.0;
+    for (int j = 0; j < c->nth; ++j) {
+        double Eth = E[1][IDX(c, iH, j)];
+        double Hph = 0.5 * (H[2][IDX(c, iH - 1, j)] + H[2][IDX(c, iH, j)]);
+        double Eph = 0.5 * (E[2][IDX(c, iH, j)] + E[2][IDX(c, iH, j + 1)]);
+        double Hth = 0.25 * (H[1][IDX(c, iH - 1, j)] + H[1][IDX(c, iH, j)] + H[1][IDX(c, iH - 1, j + 1)] +
+                             H[1][IDX(c, iH, j + 1)]);
+        L += (Eth * Hph - Eph * Hth) * c->dth;
+    }
+    for (int k = 0; k < 3; ++k) { free(E[k]); free(H[k]); }
+    return L;
+}
