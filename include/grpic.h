@@ -194,6 +194,64 @@ grpic_status grpic_get_areas(grpic_ctx *ctx, double *const out[6], int64_t ld, v
 grpic_status grpic_sync(grpic_ctx *ctx, void *stream);
 
 /* ------------------------------------------------------------------------ */
+/* Differentiable form (FP64 contexts only).  The objective is the time-     */
+/* averaged radial Poynting flux of the 3+1 fields (S = E x H, Sec. 2.1's    */
+/* auxiliary E_i, H_i of App. B) through the ring of cell faces at column    */
+/* i_H (the paper defines no objective; this is the reading used here):      */
+/*   flux(F) = sum_j (E_theta H_phi - E_phi H_theta)(r_{i_H}, theta_{j+1/2})  */
+/*             dtheta,   with H_phi, E_phi, H_theta averaged onto that point  */
+/*             from their staggered locations (2, 2 and 4 points),            */
+/*   L = (1/N) sum_{n=0}^{N-1} flux(F^{n+1}),                                  */
+/* where one step is grpic_push (fields n, deposit into J) followed by       */
+/* grpic_field_update (no sort: it only permutes the particles).             */
+/* ------------------------------------------------------------------------ */
+
+/* flux(F) of the fields in f (D, B; J unused) into *out (host double).
+ * 1 <= i_horizon <= n_r - 1.  Synchronises `stream`. */
+grpic_status grpic_horizon_flux(grpic_ctx *ctx, const grpic_fields *f, int i_horizon, double *out, void *stream);
+
+/* Transpose of one field update (Eqs. fld-predictor, fld-corrector with the
+ * boundary copies and the outer damping; n_field_iter >= 1): given the
+ * adjoint lam_in->D/B of the fields after the update, writes the adjoint of
+ * the fields before it into lam_out->D/B and the adjoint of the integrated
+ * currents J A into lam_out->J.  All arrays (n_theta+1) x ld device doubles,
+ * lam_in->ld == lam_out->ld; lam_in is not modified.  Allocates and frees
+ * its scratch (24 arrays); synchronises `stream`. */
+grpic_status grpic_adjoint_field_step(grpic_ctx *ctx, const grpic_fields *lam_in, grpic_fields *lam_out,
+                                      void *stream);
+
+/* Forward run of nsteps steps from (p0, f0) and the reverse sweep of its
+ * hand-written adjoint: particles by the transposed deposit, axis reflection,
+ * the transposed geodesic step (see trapezoid_ift), the Boris Jacobian and
+ * the transposed interpolation; fields by the transposed stage sequence.  The forward
+ * states are recomputed from checkpoints taken every checkpoint_every steps
+ * (memory: ceil(nsteps/checkpoint_every) + checkpoint_every + 2 copies of
+ * the particle and field state).
+ *   p0:  n live or dead particles (FP64 SoA r, theta, u_r, u_theta, u_phi,
+ *        tag); not modified.  p0->d_count is ignored (p0->n is used).
+ *   f0:  the fields at step 0 (D, B; f0->J unused); not modified.
+ *   L_out: host double, the objective L.
+ *   grad_p[5]: device arrays of n doubles: dL/d(r, theta, u_r, u_theta,
+ *        u_phi) of every particle at step 0 (0 for dead ones).
+ *   grad_f[6]: NULL or device arrays (n_theta+1) x f0->ld for dL/dD^r,
+ *        dL/dD^theta, dL/dD^phi, dL/dB^r, dL/dB^theta, dL/dB^phi at step 0,
+ *        entry by entry (guard columns included); a NULL entry is skipped.
+ * trapezoid_ift selects the particle Jacobian of the geodesic step:
+ *   0  the transpose of the predictor and the n_push_iter correctors exactly
+ *      as the push runs them (the gradient of the computed trajectory);
+ *   1  the implicit-function theorem at the converged trapezoid, one 5x5
+ *      transposed solve per particle: the gradient of the trapezoidal rule
+ *      itself, equal to 0 up to the iteration's residual (near the polar
+ *      axis, where dt/2 |dF/dy| approaches 1, three correctors do not
+ *      converge and the two differ).
+ * n_push_iter must not exceed 16 (the adjoint keeps the iterates).
+ * A particle the forward refuses (ERANGE, ENAN) contributes no gradient and
+ * its status is returned after the sweep.  Synchronises `stream`. */
+grpic_status grpic_adjoint_grad(grpic_ctx *ctx, const grpic_particles *p0, const grpic_fields *f0, int nsteps,
+                                int checkpoint_every, int i_horizon, int trapezoid_ift, double *L_out,
+                                double *const grad_p[5], double *const grad_f[6], void *stream);
+
+/* ------------------------------------------------------------------------ */
 /* Batched 1D spark gaps: the radiative pair-production prescription of     */
 /* Sec. 4 (threshold photon emission at the FIDO Lorentz factor gamma_thr    */
 /* with FIDO energy eps_ph along the emitter's momentum; photon conversion   */

@@ -1,0 +1,1179 @@
+// grpic_adjoint.cu -- the differentiable form: a hand-written adjoint of the
+// FP64 time step (push + deposit + field update, arXiv:2503.04558 Sec. 2) for
+// the time-averaged radial Poynting flux through the horizon ring,
+//   L = (1/N) sum_n sum_j (E_th H_ph - E_ph H_th)(i_H, j+1/2) dtheta,
+// with respect to the initial particle state and the initial fields.
+//
+// Reverse sweep per step n (state S_n = particles, F_n = D, B):
+//   * seed   lambda_F^{n+1} += dL/dF^{n+1}  (through the auxiliary fields);
+//   * fields the field update is linear in (F^n, J): its transpose runs the
+//            predictor-corrector stages backwards with the transposed circulation
+//            and auxiliary-field stencils (scatter with atomics), the boundary
+//            copies transposed into their source cells;
+//   * particles for every particle: the transpose of the deposit (derivatives of
+//            the piecewise-linear CIC weights), the axis reflection, the geodesic
+//            trapezoid by the implicit-function theorem at the converged iterate
+//            (I - dt/2 dF/dy)^T w = lambda (a 5x5 solve), the Boris step and the
+//            interpolation (scatter of lambda_E into lambda_F).  Local Jacobians
+//            come from forward-mode dual numbers through the same metric code.
+// Recompute checkpoints every `checkpoint_every` steps bound the memory.
+#include "grpic_geo.cuh"
+
+#include <cstring>
+#include <new>
+#include <vector>
+
+namespace grpic {
+
+// ---- forward-mode dual numbers ---------------------------------------------
+template <int N>
+struct DN {
+    double v;
+    double d[N];
+    __device__ DN() {}
+    __device__ DN(double x) : v(x)
+    {
+#pragma unroll
+        for (int k = 0; k < N; ++k) d[k] = 0.0;
+    }
+};
+template <int N>
+__device__ __forceinline__ DN<N> operator+(const DN<N> &a, const DN<N> &b)
+{
+    DN<N> r;
+    r.v = a.v + b.v;
+#pragma unroll
+    for (int k = 0; k < N; ++k) r.d[k] = a.d[k] + b.d[k];
+    return r;
+}
+template <int N>
+__device__ __forceinline__ DN<N> operator-(const DN<N> &a, const DN<N> &b)
+{
+    DN<N> r;
+    r.v = a.v - b.v;
+#pragma unroll
+    for (int k = 0; k < N; ++k) r.d[k] = a.d[k] - b.d[k];
+    return r;
+}
+template <int N>
+__device__ __forceinline__ DN<N> operator-(const DN<N> &a)
+{
+    DN<N> r;
+    r.v = -a.v;
+#pragma unroll
+    for (int k = 0; k < N; ++k) r.d[k] = -a.d[k];
+    return r;
+}
+template <int N>
+__device__ __forceinline__ DN<N> operator*(const DN<N> &a, const DN<N> &b)
+{
+    DN<N> r;
+    r.v = a.v * b.v;
+#pragma unroll
+    for (int k = 0; k < N; ++k) r.d[k] = a.d[k] * b.v + a.v * b.d[k];
+    return r;
+}
+template <int N>
+__device__ __forceinline__ DN<N> operator/(const DN<N> &a, const DN<N> &b)
+{
+    DN<N> r;
+    double ib = 1.0 / b.v;
+    r.v = a.v * ib;
+#pragma unroll
+    for (int k = 0; k < N; ++k) r.d[k] = (a.d[k] - r.v * b.d[k]) * ib;
+    return r;
+}
+template <int N>
+__device__ __forceinline__ DN<N> rcp_t(const DN<N> &a)
+{
+    DN<N> r;
+    r.v = 1.0 / a.v;
+#pragma unroll
+    for (int k = 0; k < N; ++k) r.d[k] = -a.d[k] * r.v * r.v;
+    return r;
+}
+template <int N>
+__device__ __forceinline__ DN<N> sqrt_t(const DN<N> &a)
+{
+    DN<N> r;
+    r.v = sqrt(a.v);
+    double h = a.v > 0.0 ? 0.5 / r.v : 0.0;
+#pragma unroll
+    for (int k = 0; k < N; ++k) r.d[k] = a.d[k] * h;
+    return r;
+}
+template <int N>
+__device__ __forceinline__ void sincos_t(const DN<N> &a, DN<N> *s, DN<N> *c)
+{
+    double sv, cv;
+    sincos(a.v, &sv, &cv);
+    s->v = sv;
+    c->v = cv;
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+        s->d[k] = cv * a.d[k];
+        c->d[k] = -sv * a.d[k];
+    }
+}
+
+namespace {
+
+// ---- the particle's local maps ---------------------------------------------
+// right-hand side of Eq. particle-eom (no Lorentz force) at y = (r, th, ur, ut, up)
+template <typename T>
+__device__ __forceinline__ void rhs_y(double a, double eps, const T y[5], T f[6])
+{
+    T s, c;
+    sincos_t(y[1], &s, &c);
+    KSGeo<T> m;
+    ks_geo_sc<T>(T(a), y[0], s, c, m);
+    RhsT<T> o;
+    geo_rhs_m<T, T>(m, T(eps), y[2], y[3], y[4], o);
+    f[0] = o.xr;
+    f[1] = o.xt;
+    f[2] = o.xp;
+    f[3] = o.ur;
+    f[4] = o.ut;
+    f[5] = T(0.0);
+}
+
+// F = (X^r, X^th, U_r, U_th, U_ph) and X^ph at y, with dF/dy and dX^ph/dy
+__device__ void rhs_jac(double a, double eps, const double y[5], double F[5], double J[5][5], double &Fp,
+                        double dFp[5])
+{
+    DN<5> yd[5], f[6];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+        yd[k] = DN<5>(y[k]);
+        yd[k].d[k] = 1.0;
+    }
+    rhs_y<DN<5>>(a, eps, yd, f);
+    const int map[5] = {0, 1, 3, 4, 5};
+    for (int r = 0; r < 5; ++r) {
+        F[r] = f[map[r]].v;
+        for (int k = 0; k < 5; ++k) J[r][k] = f[map[r]].d[k];
+    }
+    Fp = f[2].v;
+    for (int k = 0; k < 5; ++k) dFp[k] = f[2].d[k];
+}
+
+// generalized Boris step (Eqs. boris-plus-minus, u0bar, boris-scheme) on
+// z = (r, th, u_r, u_th, u_ph, D^r, D^th, D^ph, B^r, B^th, B^ph) -> u'
+template <typename T>
+__device__ __forceinline__ void boris_z(double a, double qm, double dt, const T z[11], T out[3])
+{
+    T s, c;
+    sincos_t(z[1], &s, &c);
+    T r = z[0];
+    T a2 = T(a * a);
+    T s2 = s * s;
+    T rho2 = r * r + a2 * c * c;
+    T ir = rcp_t(rho2);
+    T zz = T(2.0) * r * ir;
+    T opz = T(1.0) + zz;
+    T alpha = sqrt_t(rcp_t(opz));
+    T Dl = r * r + a2 - T(2.0) * r;
+    T Sg = (r * r + a2) * (r * r + a2) - a2 * Dl * s2;
+    T g_rr = opz, g_tt = rho2, g_pp = Sg * s2 * ir, g_rp = -T(a) * s2 * opz;
+    T i_rr = (a2 + r * r) * ir - zz * rcp_t(opz), i_rp = T(a) * ir, i_tt = ir, i_pp = ir * rcp_t(s2);
+    T sg = rho2 * s * sqrt_t(opz);
+    T Dl0 = g_rr * z[5] + g_rp * z[7], Dl1 = g_tt * z[6], Dl2 = g_rp * z[5] + g_pp * z[7];
+    T h = T(0.5 * qm * dt) * alpha;
+    T um0 = z[2] + h * Dl0, um1 = z[3] + h * Dl1, um2 = z[4] + h * Dl2;
+    T v0 = i_rr * um0 + i_rp * um2, v1 = i_tt * um1, v2 = i_rp * um0 + i_pp * um2;
+    T u0b = sqrt_t(T(1.0) + um0 * v0 + um1 * v1 + um2 * v2) / alpha;
+    T kt = T(0.5 * qm * dt) / u0b;
+    T t0 = kt * z[8], t1 = kt * z[9], t2 = kt * z[10];
+    T tt = t0 * (g_rr * t0 + g_rp * t2) + t1 * (g_tt * t1) + t2 * (g_rp * t0 + g_pp * t2);
+    T ks = T(2.0) / (T(1.0) + tt);
+    T s0 = ks * t0, s1 = ks * t1, s2b = ks * t2;
+    T w0 = um0 + sg * (v1 * t2 - v2 * t1);
+    T w1 = um1 + sg * (v2 * t0 - v0 * t2);
+    T w2 = um2 + sg * (v0 * t1 - v1 * t0);
+    T x0 = i_rr * w0 + i_rp * w2, x1 = i_tt * w1, x2 = i_rp * w0 + i_pp * w2;
+    out[0] = um0 + sg * (x1 * s2b - x2 * s1) + h * Dl0;
+    out[1] = um1 + sg * (x2 * s0 - x0 * s2b) + h * Dl1;
+    out[2] = um2 + sg * (x0 * s1 - x1 * s0) + h * Dl2;
+}
+
+// small dense solve M x = b (n = 5), Gaussian elimination with partial pivoting
+__device__ void solve5(double M[5][5], double b[5])
+{
+    for (int c = 0; c < 5; ++c) {
+        int p = c;
+        for (int r = c + 1; r < 5; ++r)
+            if (fabs(M[r][c]) > fabs(M[p][c])) p = r;
+        if (p != c) {
+            for (int k = 0; k < 5; ++k) {
+                double t = M[c][k];
+                M[c][k] = M[p][k];
+                M[p][k] = t;
+            }
+            double t = b[c];
+            b[c] = b[p];
+            b[p] = t;
+        }
+        double iv = 1.0 / M[c][c];
+        for (int r = c + 1; r < 5; ++r) {
+            double f = M[r][c] * iv;
+            for (int k = c; k < 5; ++k) M[r][k] -= f * M[c][k];
+            b[r] -= f * b[c];
+        }
+    }
+    for (int c = 4; c >= 0; --c) {
+        double s = b[c];
+        for (int k = c + 1; k < 5; ++k) s -= M[c][k] * b[k];
+        b[c] = s / M[c][c];
+    }
+}
+
+__device__ __forceinline__ double W1(double d)
+{
+    d = fabs(d);
+    return d < 1.0 ? 1.0 - d : 0.0;
+}
+__device__ __forceinline__ double dW1(double d) { return fabs(d) < 1.0 ? (d > 0.0 ? -1.0 : (d < 0.0 ? 1.0 : 0.0)) : 0.0; }
+
+__device__ __forceinline__ int jcell(const GridDev &g, double x2)
+{
+    int j = (int)floor(x2);
+    return j > g.nth - 1 ? g.nth - 1 : j;
+}
+
+// staggered bilinear stencil with axis mirroring (as in the push)
+struct St {
+    int c0, r0, r1;
+    double f, gg, p0, p1;
+};
+__device__ __forceinline__ void stencil(const GridDev &g, double x1, double x2, bool half_r, bool half_t, double par,
+                                        St &S)
+{
+    double xi = half_r ? x1 - 0.5 : x1;
+    double fi = floor(xi);
+    S.f = xi - fi;
+    S.c0 = (int)fi + NG;
+    S.p0 = S.p1 = 1.0;
+    if (half_t) {
+        double eta = x2 - 0.5, fj = floor(eta);
+        int j = (int)fj;
+        S.gg = eta - fj;
+        S.r0 = j;
+        S.r1 = j + 1;
+        if (S.r0 < 0) { S.r0 = -1 - S.r0; S.p0 = par; }
+        if (S.r1 > g.nth - 1) { S.r1 = 2 * g.nth - 1 - S.r1; S.p1 = par; }
+    } else {
+        int j = (int)floor(x2);
+        if (j > g.nth - 1) j = g.nth - 1;
+        S.gg = x2 - j;
+        S.r0 = j;
+        S.r1 = j + 1;
+    }
+}
+// value and d/dx1, d/dx2 (logical) of the interpolant
+__device__ __forceinline__ void gather_d(const double *F, int64_t ld, const St &S, double &v, double &d1, double &d2)
+{
+    double a00 = S.p0 * F[(size_t)S.r0 * ld + S.c0], a10 = S.p0 * F[(size_t)S.r0 * ld + S.c0 + 1];
+    double a01 = S.p1 * F[(size_t)S.r1 * ld + S.c0], a11 = S.p1 * F[(size_t)S.r1 * ld + S.c0 + 1];
+    double f = S.f, g = S.gg;
+    v = (1 - f) * (1 - g) * a00 + f * (1 - g) * a10 + (1 - f) * g * a01 + f * g * a11;
+    d1 = (1 - g) * (a10 - a00) + g * (a11 - a01);
+    d2 = (1 - f) * (a01 - a00) + f * (a11 - a10);
+}
+__device__ __forceinline__ void scatter_w(double *L, int64_t ld, const St &S, double lam)
+{
+    double f = S.f, g = S.gg;
+    atomicAdd(L + (size_t)S.r0 * ld + S.c0, S.p0 * (1 - f) * (1 - g) * lam);
+    atomicAdd(L + (size_t)S.r0 * ld + S.c0 + 1, S.p0 * f * (1 - g) * lam);
+    atomicAdd(L + (size_t)S.r1 * ld + S.c0, S.p1 * (1 - f) * g * lam);
+    atomicAdd(L + (size_t)S.r1 * ld + S.c0 + 1, S.p1 * f * g * lam);
+}
+
+constexpr int MAX_ITER = 16;  // correctors the adjoint keeps iterates for
+
+struct PAdjArgs {
+    GridDev g;
+    double dt;
+    int n_iter;
+    int ift;                  // 1: implicit-function theorem at the converged trapezoid
+    double qm[4], qw[4];
+    int massive[4];
+    int64_t n;
+    const double *x[5];       // state n: r, th, ur, ut, up
+    const uint32_t *tag0;     // tags at n
+    const uint32_t *tag1;     // tags at n+1
+    const double *F[6];       // fields at n
+    const double *lamJ[3];    // adjoint of J A
+    const double *lam1[5];    // adjoint of state n+1
+    double *lam0[5];          // adjoint of state n (output)
+    double *lamF[6];          // adjoint of fields at n (accumulated)
+    int64_t ld;
+};
+
+__global__ void __launch_bounds__(128) particle_adjoint(PAdjArgs A)
+{
+    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= A.n) return;
+    const GridDev &g = A.g;
+    double out[5] = {0, 0, 0, 0, 0};
+    uint32_t t0 = A.tag0[p];
+    if (t0 & DEAD) {
+        for (int k = 0; k < 5; ++k) A.lam0[k][p] = 0.0;
+        return;
+    }
+    const int sp = t0 & 3u;
+    const bool massive = A.massive[sp] != 0, charged = massive && A.qm[sp] != 0.0;
+    double r = A.x[0][p], th = A.x[1][p];
+    double u[3] = {A.x[2][p], A.x[3][p], A.x[4][p]};
+    // a state the push refused (outside the domain, non-finite) moved nothing
+    bool inside = isfinite(r) && isfinite(th) && isfinite(u[0]) && isfinite(u[1]) && isfinite(u[2]) &&
+                  r >= g.r_in && r < g.r_out && th >= 0.0 && th <= M_PI;
+    if (!inside) {
+        for (int k = 0; k < 5; ++k) A.lam0[k][p] = 0.0;
+        return;
+    }
+    double x1a = (log(r) - g.ln_rin) / g.dx1, x2a = th / g.dth;
+    if (x1a >= (double)g.nr) x1a = nextafter((double)g.nr, 0.0);  // as in the push
+    if (x1a < 0.0) x1a = 0.0;
+    const double dt = A.dt, eps = massive ? 1.0 : 0.0;
+
+    // forward recomputation with local derivatives
+    St S[6];
+    double E[6], dE1[6], dE2[6];
+    double JB[3][11];
+    double up[3] = {u[0], u[1], u[2]};
+    if (charged) {
+        stencil(g, x1a, x2a, true, false, 1.0, S[0]);   // D^r
+        stencil(g, x1a, x2a, false, true, -1.0, S[1]);  // D^th (odd across the axis)
+        stencil(g, x1a, x2a, false, false, 1.0, S[2]);  // D^ph
+        stencil(g, x1a, x2a, false, true, 1.0, S[3]);   // B^r
+        stencil(g, x1a, x2a, true, false, 1.0, S[4]);   // B^th
+        stencil(g, x1a, x2a, true, true, 1.0, S[5]);    // B^ph
+        for (int c = 0; c < 6; ++c) gather_d(A.F[c], A.ld, S[c], E[c], dE1[c], dE2[c]);
+        DN<11> z[11], o[3];
+        double zv[11] = {r, th, u[0], u[1], u[2], E[0], E[1], E[2], E[3], E[4], E[5]};
+        for (int k = 0; k < 11; ++k) {
+            z[k] = DN<11>(zv[k]);
+            z[k].d[k] = 1.0;
+        }
+        boris_z<DN<11>>(g.a, A.qm[sp], dt, z, o);
+        for (int i = 0; i < 3; ++i) {
+            up[i] = o[i].v;
+            for (int k = 0; k < 11; ++k) JB[i][k] = o[i].d[k];
+        }
+    }
+    double y0[5] = {r, th, up[0], up[1], up[2]};
+    double F0[5], J0[5][5], Fp0, dFp0[5];
+    rhs_jac(g.a, eps, y0, F0, J0, Fp0, dFp0);
+    // the predictor-corrector itself (as in the push)
+    // predictor and correctors exactly as the push runs them; the iterates
+    // at which the corrector right-hand sides are evaluated are kept
+    const int N = A.n_iter;
+    double yit[MAX_ITER][5];
+    double y1[5], yt[5];
+    for (int k = 0; k < 5; ++k) yt[k] = y0[k] + dt * F0[k];
+    double dphi = dt * Fp0;
+    for (int it = 0; it < N; ++it) {
+        for (int k = 0; k < 5; ++k) yit[it][k] = yt[k];
+        double ft[6];
+        rhs_y<double>(g.a, eps, yt, ft);
+        const double Ft[5] = {ft[0], ft[1], ft[3], ft[4], 0.0};
+        for (int k = 0; k < 5; ++k) yt[k] = y0[k] + 0.5 * dt * (Ft[k] + F0[k]);
+        dphi = 0.5 * dt * (ft[2] + Fp0);
+    }
+    for (int k = 0; k < 5; ++k) y1[k] = yt[k];
+    double refl = 1.0;
+    double th1 = y1[1];
+    if (th1 < 0.0) { th1 = -th1; refl = -1.0; }
+    else if (th1 > M_PI) { th1 = 2.0 * M_PI - th1; refl = -1.0; }
+    double x1b = (log(y1[0]) - g.ln_rin) / g.dx1, x2b = th1 / g.dth;
+    int i0 = (int)floor(x1a), j0 = jcell(g, x2a);
+    int di = (int)floor(x1b) - i0, dj = jcell(g, x2b) - j0;
+    bool moved_ok = di >= -1 && di <= 1 && dj >= -1 && dj <= 1 && isfinite(x1b) && isfinite(x2b);
+    if (!moved_ok) {
+        for (int k = 0; k < 5; ++k) A.lam0[k][p] = 0.0;
+        return;
+    }
+
+    // ---- adjoint -------------------------------------------------------
+    double l1[5] = {0, 0, 0, 0, 0};
+    if (!(A.tag1[p] & DEAD))
+        for (int k = 0; k < 5; ++k) l1[k] = A.lam1[k][p];
+    double ldphi = 0.0, lx1a = 0.0, lx2a = 0.0, lx1b = 0.0, lx2b = 0.0;
+    double qw = A.qw[sp];
+    if (qw != 0.0) {
+        // transpose of the Esirkepov window (same algebra as the push)
+        double S0r[4], S1r[4], S0t[4], S1t[4], dS0r[4], dS1r[4], dS0t[4], dS1t[4];
+        for (int k = 0; k < 4; ++k) {
+            double cr_ = i0 - 1 + k, ct = j0 - 1 + k;
+            S0r[k] = W1(x1a - cr_); dS0r[k] = dW1(x1a - cr_);
+            S1r[k] = W1(x1b - cr_); dS1r[k] = dW1(x1b - cr_);
+            S0t[k] = W1(x2a - ct); dS0t[k] = dW1(x2a - ct);
+            S1t[k] = W1(x2b - ct); dS1t[k] = dW1(x2b - ct);
+        }
+        double cr = -qw / (2.0 * dt), cq = qw / dt, cp = cq * dphi;
+        double Pr = 0.0, dPr1 = 0.0, dPr0 = 0.0;
+        for (int k = 0; k < 3; ++k) {
+            Pr += S1r[k] - S0r[k];
+            dPr1 += dS1r[k];
+            dPr0 += dS0r[k];
+            for (int l = 0; l < 4; ++l) {
+                int row = j0 - 1 + l;
+                if (row < 0 || row > g.nth) continue;
+                double L = A.lamJ[0][(size_t)row * A.ld + (i0 - 1 + k + NG)];
+                lx1b += L * cr * dPr1 * (S1t[l] + S0t[l]);
+                lx1a += -L * cr * dPr0 * (S1t[l] + S0t[l]);
+                lx2b += L * cr * Pr * dS1t[l];
+                lx2a += L * cr * Pr * dS0t[l];
+            }
+        }
+        double Pt = 0.0, dPt1 = 0.0, dPt0 = 0.0;
+        for (int l = 0; l < 3; ++l) {
+            Pt += S1t[l] - S0t[l];
+            dPt1 += dS1t[l];
+            dPt0 += dS0t[l];
+            int row = j0 - 1 + l;
+            if (row < 0 || row > g.nth - 1) continue;
+            for (int k = 0; k < 4; ++k) {
+                double L = A.lamJ[1][(size_t)row * A.ld + (i0 - 1 + k + NG)];
+                lx1b += L * cr * dS1r[k] * Pt;
+                lx1a += L * cr * dS0r[k] * Pt;
+                lx2b += L * cr * (S1r[k] + S0r[k]) * dPt1;
+                lx2a += -L * cr * (S1r[k] + S0r[k]) * dPt0;
+            }
+        }
+        for (int k = 0; k < 4; ++k)
+            for (int l = 0; l < 4; ++l) {
+                int row = j0 - 1 + l;
+                if (row < 0 || row > g.nth) continue;
+                double L = A.lamJ[2][(size_t)row * A.ld + (i0 - 1 + k + NG)];
+                double w = S1r[k] * S1t[l] / 3.0 + S1r[k] * S0t[l] / 6.0 + S0r[k] * S1t[l] / 6.0 + S0r[k] * S0t[l] / 3.0;
+                ldphi += L * cq * w;
+                lx1b += L * cp * dS1r[k] * (S1t[l] / 3.0 + S0t[l] / 6.0);
+                lx1a += L * cp * dS0r[k] * (S1t[l] / 6.0 + S0t[l] / 3.0);
+                lx2b += L * cp * (S1r[k] / 3.0 + S0r[k] / 6.0) * dS1t[l];
+                lx2a += L * cp * (S1r[k] / 6.0 + S0r[k] / 3.0) * dS0t[l];
+            }
+    }
+    // end point: logical -> (r, theta) after reflection, then the reflection
+    l1[0] += lx1b / (y1[0] * g.dx1);
+    l1[1] += lx2b / g.dth;
+    l1[1] *= refl;
+    l1[3] *= refl;
+    const double hh = 0.5 * dt;
+    double l0[5];
+    if (A.ift) {
+        // the converged trapezoid y1 = y0 + dt/2 (F(y1) + F(y0)), dphi = dt/2
+        // (X^ph(y1) + X^ph(y0)), by the implicit-function theorem:
+        // (I - dt/2 dF/dy(y1))^T w = lambda_1, lambda_0 = (I + dt/2 dF/dy(y0))^T w
+        double F1[5], J1[5][5], Fp1, dFp1[5];
+        rhs_jac(g.a, eps, y1, F1, J1, Fp1, dFp1);
+        for (int k = 0; k < 5; ++k) l1[k] += hh * ldphi * dFp1[k];
+        double M[5][5];
+        for (int a = 0; a < 5; ++a)
+            for (int b = 0; b < 5; ++b) M[a][b] = (a == b ? 1.0 : 0.0) - hh * J1[b][a];  // transposed
+        double w[5] = {l1[0], l1[1], l1[2], l1[3], l1[4]};
+        solve5(M, w);
+        for (int k = 0; k < 5; ++k) {
+            double s = w[k];
+            for (int a = 0; a < 5; ++a) s += hh * J0[a][k] * w[a];
+            l0[k] = s + hh * ldphi * dFp0[k];
+        }
+    } else {
+        // transpose of the iteration the push runs: y~_0 = y0 + dt F(y0),
+        // y~_{k+1} = y0 + dt/2 (F(y~_k) + F(y0)), dphi = dt/2 (X^ph(y~_{N-1}) + X^ph(y0))
+        double gk[5] = {l1[0], l1[1], l1[2], l1[3], l1[4]};
+        double lF0[5] = {0, 0, 0, 0, 0}, ly0[5] = {0, 0, 0, 0, 0}, lFp0 = 0.0;
+        if (N == 0) {
+            lFp0 += dt * ldphi;
+        } else {
+            for (int it = N - 1; it >= 0; --it) {
+                for (int k = 0; k < 5; ++k) {
+                    ly0[k] += gk[k];
+                    lF0[k] += hh * gk[k];
+                }
+                double ap = (it == N - 1) ? hh * ldphi : 0.0;
+                lFp0 += ap;
+                double Fk[5], Jk[5][5], Fpk, dFpk[5];
+                rhs_jac(g.a, eps, yit[it], Fk, Jk, Fpk, dFpk);
+                double gn[5];
+                for (int b = 0; b < 5; ++b) {
+                    double s = ap * dFpk[b];
+                    for (int a = 0; a < 5; ++a) s += Jk[a][b] * hh * gk[a];
+                    gn[b] = s;
+                }
+                for (int k = 0; k < 5; ++k) gk[k] = gn[k];
+            }
+        }
+        for (int k = 0; k < 5; ++k) {
+            ly0[k] += gk[k];
+            lF0[k] += dt * gk[k];
+        }
+        for (int k = 0; k < 5; ++k) {
+            double s = ly0[k] + lFp0 * dFp0[k];
+            for (int a = 0; a < 5; ++a) s += J0[a][k] * lF0[a];
+            l0[k] = s;
+        }
+    }
+    // start point: deposit's start-weight derivatives
+    l0[0] += lx1a / (r * g.dx1);
+    l0[1] += lx2a / g.dth;
+    // Boris: y0 = (r, th, u'(r, th, u, E))
+    out[0] = l0[0];
+    out[1] = l0[1];
+    if (charged) {
+        double lE[6] = {0, 0, 0, 0, 0, 0};
+        for (int i = 0; i < 3; ++i) {
+            double li = l0[2 + i];
+            out[0] += JB[i][0] * li;
+            out[1] += JB[i][1] * li;
+            for (int k = 0; k < 3; ++k) out[2 + k] += JB[i][2 + k] * li;
+            for (int c = 0; c < 6; ++c) lE[c] += JB[i][5 + c] * li;
+        }
+        double lx1 = 0.0, lx2 = 0.0;
+        for (int c = 0; c < 6; ++c) {
+            scatter_w(A.lamF[c], A.ld, S[c], lE[c]);
+            lx1 += lE[c] * dE1[c];
+            lx2 += lE[c] * dE2[c];
+        }
+        out[0] += lx1 / (r * g.dx1);
+        out[1] += lx2 / g.dth;
+    } else {
+        for (int k = 0; k < 3; ++k) out[2 + k] = l0[2 + k];
+    }
+    for (int k = 0; k < 5; ++k) A.lam0[k][p] = out[k];
+}
+
+// ---- field update transpose -------------------------------------------------
+struct FAdj {
+    int nr, nth;
+    int64_t ld, ldt;
+    size_t slab;
+    const double *tab, *col1d;
+};
+
+__device__ __forceinline__ double tb(const FAdj &A, int slot, int i, int j)
+{
+    return A.tab[slot * A.slab + (size_t)j * A.ldt + (i + NG)];
+}
+
+// lamC (6 arrays at physical points) -> aux adjoints lamA[0..5] = H_r, H_th,
+// H_ph, E_r, E_th, E_ph (transpose of the circulations, Eqs. D-update, B-update)
+__global__ void circ_T(FAdj A, const double *const *lamC, double *const *lamA, double dth)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    int j = blockIdx.y * blockDim.y + threadIdx.y;
+    if (i > A.nr || j > A.nth) return;
+    const int nr = A.nr, nth = A.nth;
+    size_t q = (size_t)j * A.ld + (i + NG);
+    auto at = [&](double *L, int ii, int jj, double v) { atomicAdd(L + (size_t)jj * A.ld + (ii + NG), v); };
+    double drd = A.col1d[1 * A.ldt + i + NG], drp = A.col1d[0 * A.ldt + i + NG];
+    if (i <= nr - 1) {
+        double gv = lamC[0][q] * tb(A, T_INV_ADR, i, j);
+        if (j < nth) at(lamA[2], i, j, gv);
+        if (j > 0) at(lamA[2], i, j - 1, -gv);
+    }
+    if (j < nth) {
+        double gv = lamC[1][q] * tb(A, T_INV_ADT, i, j);
+        at(lamA[2], i - 1, j, gv);
+        at(lamA[2], i, j, -gv);
+        double gb = lamC[3][q] * tb(A, T_INV_ABR, i, j);
+        at(lamA[5], i, j + 1, -gb);
+        at(lamA[5], i, j, gb);
+    }
+    if (j > 0 && j < nth) {
+        double gv = lamC[2][q] * tb(A, T_INV_ADP, i, j);
+        at(lamA[1], i, j, gv * dth);
+        at(lamA[1], i - 1, j, -gv * dth);
+        at(lamA[0], i, j - 1, gv * drd);
+        at(lamA[0], i, j, -gv * drd);
+        if (i <= nr - 1) {
+            double gb = lamC[4][q] * tb(A, T_INV_ABT, i, j);
+            at(lamA[5], i, j, -gb);
+            at(lamA[5], i + 1, j, gb);
+        }
+    }
+    if (i <= nr - 1 && j < nth) {
+        double gb = lamC[5][q] * tb(A, T_INV_ABP, i, j);
+        at(lamA[4], i + 1, j, -gb * dth);
+        at(lamA[4], i, j, gb * dth);
+        at(lamA[3], i, j, -gb * drp);
+        at(lamA[3], i, j + 1, gb * drp);
+    }
+}
+
+// aux adjoints -> field adjoints (transpose of Eqs. auxH, auxE); one thread per
+// storage column/row, scatter with atomics
+__global__ void aux_T(FAdj A, const double *const *lamA, double *const *lamX)
+{
+    int col = blockIdx.x * blockDim.x + threadIdx.x;
+    int j = blockIdx.y * blockDim.y + threadIdx.y;
+    if (col < 1 || col > (int)A.ldt - 2 || j > A.nth) return;
+    int i = col - NG;
+    size_t q = (size_t)j * A.ld + col;
+    auto at = [&](double *L, int ii, int jj, double v) {
+        if (v != 0.0) atomicAdd(L + (size_t)jj * A.ld + (ii + NG), v);
+    };
+    double h;
+    // fields: 0 D^r, 1 D^th, 2 D^ph, 3 B^r, 4 B^th, 5 B^ph
+    if (j < A.nth) {
+        h = lamA[0][q];  // H_r
+        if (h != 0.0) {
+            at(lamX[3], i, j, tb(A, T_AGRR_BR, i, j) * h);
+            at(lamX[5], i, j, 0.5 * tb(A, T_AGRP_BP, i, j) * h);
+            at(lamX[5], i - 1, j, 0.5 * tb(A, T_AGRP_BP, i - 1, j) * h);
+        }
+        h = lamA[2][q];  // H_ph
+        if (h != 0.0) {
+            at(lamX[5], i, j, tb(A, T_AGPP_BP, i, j) * h);
+            at(lamX[3], i, j, 0.5 * tb(A, T_AGRP_BR, i, j) * h);
+            at(lamX[3], i + 1, j, 0.5 * tb(A, T_AGRP_BR, i + 1, j) * h);
+            at(lamX[1], i, j, -0.5 * tb(A, T_SGB_DT, i, j) * h);
+            at(lamX[1], i + 1, j, -0.5 * tb(A, T_SGB_DT, i + 1, j) * h);
+        }
+        h = lamA[4][q];  // E_th
+        if (h != 0.0) {
+            at(lamX[1], i, j, tb(A, T_AGTT_DT, i, j) * h);
+            at(lamX[5], i, j, -0.5 * tb(A, T_SGB_BP, i, j) * h);
+            at(lamX[5], i - 1, j, -0.5 * tb(A, T_SGB_BP, i - 1, j) * h);
+        }
+    }
+    h = lamA[1][q];  // H_th
+    if (h != 0.0) {
+        at(lamX[4], i, j, tb(A, T_AGTT_BT, i, j) * h);
+        at(lamX[2], i, j, 0.5 * tb(A, T_SGB_DP, i, j) * h);
+        at(lamX[2], i + 1, j, 0.5 * tb(A, T_SGB_DP, i + 1, j) * h);
+    }
+    h = lamA[3][q];  // E_r
+    if (h != 0.0) {
+        at(lamX[0], i, j, tb(A, T_AGRR_DR, i, j) * h);
+        at(lamX[2], i, j, 0.5 * tb(A, T_AGRP_DP, i, j) * h);
+        at(lamX[2], i + 1, j, 0.5 * tb(A, T_AGRP_DP, i + 1, j) * h);
+    }
+    h = lamA[5][q];  // E_ph
+    if (h != 0.0) {
+        at(lamX[2], i, j, tb(A, T_AGPP_DP, i, j) * h);
+        at(lamX[0], i, j, 0.5 * tb(A, T_AGRP_DR, i, j) * h);
+        at(lamX[0], i - 1, j, 0.5 * tb(A, T_AGRP_DR, i - 1, j) * h);
+        at(lamX[4], i, j, 0.5 * tb(A, T_SGB_BT, i, j) * h);
+        at(lamX[4], i - 1, j, 0.5 * tb(A, T_SGB_BT, i - 1, j) * h);
+    }
+}
+
+__device__ __forceinline__ bool phys(int comp, int i, int j, int nr, int nth)
+{
+    bool half_r = (comp == 0 || comp == 4 || comp == 5), half_t = (comp == 1 || comp == 3 || comp == 5);
+    if (i < 0 || i > (half_r ? nr - 1 : nr)) return false;
+    if (j > (half_t ? nth - 1 : nth)) return false;
+    return true;
+}
+
+// transpose of the boundary projection P of one stage (with damping when
+// damp != 0): mu[phys] = damp * (lam[phys] + lam of the guard copies of it);
+// axis D^ph, B^th rows and non-physical entries get 0
+__global__ void proj_T(FAdj A, const double *const *lam, double *const *mu, int damp)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    int j = blockIdx.y * blockDim.y + threadIdx.y;
+    if (i > A.nr || j > A.nth) return;
+    for (int comp = 0; comp < 6; ++comp) {
+        size_t row = (size_t)j * A.ld;
+        double v = 0.0;
+        if (phys(comp, i, j, A.nr, A.nth) && !((comp == 2 || comp == 4) && (j == 0 || j == A.nth))) {
+            bool half_r = (comp == 0 || comp == 4 || comp == 5);
+            int last = half_r ? A.nr - 1 : A.nr;
+            v = lam[comp][row + i + NG];
+            if (i == 0) v += lam[comp][row + 0] + lam[comp][row + 1];
+            if (i == last)
+                for (int c = last + 1 + NG; c < A.nr + 2 * NG; ++c) v += lam[comp][row + c];
+            if (damp) v *= A.col1d[(half_r ? 3 : 2) * A.ldt + i + NG];
+        }
+        mu[comp][row + i + NG] = v;
+        if (i == 0) { mu[comp][row + 0] = 0.0; mu[comp][row + 1] = 0.0; }
+        if (i == A.nr)
+            for (int c = A.nr + 1 + NG; c < A.nr + 2 * NG; ++c) mu[comp][row + c] = 0.0;
+    }
+}
+
+// entries a field update never writes (rows past the last half-theta row,
+// columns past the last guard) keep their value: the identity
+__global__ void passthru(FAdj A, const double *const *lamIn, double *const *lamOut)
+{
+    int c = blockIdx.x * blockDim.x + threadIdx.x;
+    int j = blockIdx.y * blockDim.y + threadIdx.y;
+    if (c >= A.ld || j > A.nth) return;
+    size_t q = (size_t)j * A.ld + c;
+    for (int comp = 0; comp < 6; ++comp) {
+        bool half_t = (comp == 1 || comp == 3 || comp == 5);
+        bool written = c < A.nr + 2 * NG && j <= (half_t ? A.nth - 1 : A.nth);
+        if (!written) lamOut[comp][q] += lamIn[comp][q];
+    }
+}
+
+// y[k] += s * x[k] over n elements of 6 arrays
+__global__ void axpy6(double *const *y, const double *const *x, double s, size_t n)
+{
+    size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n) return;
+    for (int k = 0; k < 6; ++k) y[k][e] += s * x[k][e];
+}
+
+// lamJ[k] (J A adjoint) += s * invA^D_k * mu_D[k] at physical D points
+__global__ void jadj(FAdj A, const double *const *mu, double *const *lamJ, double s)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    int j = blockIdx.y * blockDim.y + threadIdx.y;
+    if (i > A.nr || j > A.nth) return;
+    const int inv[3] = {T_INV_ADR, T_INV_ADT, T_INV_ADP};
+    for (int k = 0; k < 3; ++k)
+        if (phys(k, i, j, A.nr, A.nth)) {
+            size_t q = (size_t)j * A.ld + i + NG;
+            lamJ[k][q] += s * tb(A, inv[k], i, j) * mu[k][q];
+        }
+}
+
+// ---- objective ------------------------------------------------------------
+__device__ __forceinline__ double fx(const double *F, int64_t ld, int i, int j) { return F[(size_t)j * ld + i + NG]; }
+
+// auxiliary fields needed at the ring (same formulas as the field update)
+struct Ring {
+    double Eth, Hph, Eph, Hth;
+};
+__device__ Ring ring_vals(FAdj A, const double *const *F, int iH, int j)
+{
+    auto Hph = [&](int i, int jj) {
+        return tb(A, T_AGPP_BP, i, jj) * fx(F[5], A.ld, i, jj) +
+               0.5 * (tb(A, T_AGRP_BR, i, jj) * fx(F[3], A.ld, i, jj) + tb(A, T_AGRP_BR, i + 1, jj) * fx(F[3], A.ld, i + 1, jj)) -
+               0.5 * (tb(A, T_SGB_DT, i, jj) * fx(F[1], A.ld, i, jj) + tb(A, T_SGB_DT, i + 1, jj) * fx(F[1], A.ld, i + 1, jj));
+    };
+    auto Hth = [&](int i, int jj) {
+        return tb(A, T_AGTT_BT, i, jj) * fx(F[4], A.ld, i, jj) +
+               0.5 * (tb(A, T_SGB_DP, i, jj) * fx(F[2], A.ld, i, jj) + tb(A, T_SGB_DP, i + 1, jj) * fx(F[2], A.ld, i + 1, jj));
+    };
+    auto Eth = [&](int i, int jj) {
+        return tb(A, T_AGTT_DT, i, jj) * fx(F[1], A.ld, i, jj) -
+               0.5 * (tb(A, T_SGB_BP, i, jj) * fx(F[5], A.ld, i, jj) + tb(A, T_SGB_BP, i - 1, jj) * fx(F[5], A.ld, i - 1, jj));
+    };
+    auto Eph = [&](int i, int jj) {
+        return tb(A, T_AGPP_DP, i, jj) * fx(F[2], A.ld, i, jj) +
+               0.5 * (tb(A, T_AGRP_DR, i, jj) * fx(F[0], A.ld, i, jj) + tb(A, T_AGRP_DR, i - 1, jj) * fx(F[0], A.ld, i - 1, jj)) +
+               0.5 * (tb(A, T_SGB_BT, i, jj) * fx(F[4], A.ld, i, jj) + tb(A, T_SGB_BT, i - 1, jj) * fx(F[4], A.ld, i - 1, jj));
+    };
+    Ring R;
+    R.Eth = Eth(iH, j);
+    R.Hph = 0.5 * (Hph(iH - 1, j) + Hph(iH, j));
+    R.Eph = 0.5 * (Eph(iH, j) + Eph(iH, j + 1));
+    R.Hth = 0.25 * (Hth(iH - 1, j) + Hth(iH, j) + Hth(iH - 1, j + 1) + Hth(iH, j + 1));
+    return R;
+}
+
+// flux at the ring (one block reduction) accumulated into *out with weight w
+__global__ void flux_kernel(FAdj A, const double *const *F, int iH, double dth, double w, double *out)
+{
+    __shared__ double red[256];
+    double s = 0.0;
+    for (int j = threadIdx.x; j < A.nth; j += blockDim.x) {
+        Ring R = ring_vals(A, F, iH, j);
+        s += (R.Eth * R.Hph - R.Eph * R.Hth) * dth;
+    }
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out += w * red[0];
+}
+
+// seed: aux adjoints of w * flux (then aux_T maps them to the fields)
+__global__ void flux_seed(FAdj A, const double *const *F, int iH, double dth, double w, double *const *lamA)
+{
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= A.nth) return;
+    Ring R = ring_vals(A, F, iH, j);
+    double c = w * dth;
+    auto at = [&](int comp, int i, int jj, double v) { atomicAdd(lamA[comp] + (size_t)jj * A.ld + i + NG, v); };
+    // aux order: 0 H_r, 1 H_th, 2 H_ph, 3 E_r, 4 E_th, 5 E_ph
+    at(4, iH, j, c * R.Hph);
+    at(2, iH - 1, j, 0.5 * c * R.Eth);
+    at(2, iH, j, 0.5 * c * R.Eth);
+    at(5, iH, j, -0.5 * c * R.Hth);
+    at(5, iH, j + 1, -0.5 * c * R.Hth);
+    for (int di = -1; di <= 0; ++di)
+        for (int dj = 0; dj <= 1; ++dj) at(1, iH + di, j + dj, -0.25 * c * R.Eph);
+}
+
+}  // namespace
+}  // namespace grpic
+
+using namespace grpic;
+
+namespace {
+
+struct Bufs {
+    size_t fn;      // elements of one field array
+    int64_t np;     // particles
+};
+
+// device pointer arrays for kernels taking "double *const *" (6 entries)
+struct PtrSet {
+    double **d;  // device array of 6 (or 3) pointers
+};
+
+cudaError_t upload_ptrs(double *const *h, int n, double ***d, cudaStream_t s)
+{
+    cudaError_t e = cudaMalloc(d, sizeof(double *) * n);
+    if (e != cudaSuccess) return e;
+    return cudaMemcpyAsync(*d, h, sizeof(double *) * n, cudaMemcpyHostToDevice, s);
+}
+
+}  // namespace
+
+extern "C" grpic_status grpic_horizon_flux(grpic_ctx *ctx, const grpic_fields *f, int i_horizon, double *out,
+                                           void *stream)
+{
+    if (!ctx || !f || !out || ctx->prm.precision != 64 || f->ld < ctx->g.nr + 2 * NG || i_horizon < 1 ||
+        i_horizon > ctx->g.nr - 1)
+        return GRPIC_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    double *hp[6];
+    for (int k = 0; k < 3; ++k) {
+        hp[k] = (double *)f->D[k];
+        hp[3 + k] = (double *)f->B[k];
+    }
+    double **dp = nullptr;
+    if (upload_ptrs(hp, 6, &dp, s) != cudaSuccess) return GRPIC_ENOMEM;
+    FAdj A{ctx->g.nr, ctx->g.nth, f->ld, ctx->g.ld_tab, ctx->slab, ctx->tab, ctx->col1d};
+    cudaMemsetAsync(out, 0, sizeof(double), s);
+    flux_kernel<<<1, 256, 0, s>>>(A, dp, i_horizon, ctx->g.dth, 1.0, out);
+    cudaError_t e = cudaGetLastError();
+    cudaStreamSynchronize(s);
+    cudaFree(dp);
+    return e == cudaSuccess ? GRPIC_OK : GRPIC_ECUDA;
+}
+
+// Transpose of one field update: lam (adjoint of F^{n+1}, in f_lam->D/B) ->
+// adjoint of F^n (out->D/B) and of the integrated currents J A (out->J).
+static grpic_status field_adjoint(grpic_ctx *ctx, double **lamIn, double **lamOut, double **lamJ, double **work,
+                                  int64_t ld, cudaStream_t s, double ***dptrs)
+{
+    // work: mu[6], lamCn[6], lamPrev[6], aux[6]  (24 arrays); dptrs: device copies
+    const int N = ctx->prm.n_field_iter;
+    const double dt = ctx->prm.dt, bs = ctx->prm.beta_field, as = 1.0 - bs;
+    size_t fn = (size_t)(ctx->g.nth + 1) * ld;
+    FAdj A{ctx->g.nr, ctx->g.nth, ld, ctx->g.ld_tab, ctx->slab, ctx->tab, ctx->col1d};
+    dim3 blk(64, 4), grd((ctx->g.nr + 1 + 63) / 64, (ctx->g.nth + 1 + 3) / 4);
+    dim3 gfull((ctx->g.ld_tab + 63) / 64, (ctx->g.nth + 1 + 3) / 4);
+    unsigned nb = (unsigned)((fn + 255) / 256);
+    double **d_in = dptrs[0], **d_out = dptrs[1], **d_J = dptrs[2], **d_mu = dptrs[3], **d_lcn = dptrs[4],
+           **d_prev = dptrs[5], **d_aux = dptrs[6], **d_cur = dptrs[7];
+    double **mu = work, **lcn = work + 6, **prev = work + 12, **aux = work + 18;
+    for (int k = 0; k < 6; ++k) {
+        cudaMemsetAsync(lamOut[k], 0, fn * sizeof(double), s);
+        cudaMemsetAsync(lcn[k], 0, fn * sizeof(double), s);
+        cudaMemsetAsync(mu[k], 0, fn * sizeof(double), s);
+    }
+    for (int k = 0; k < 3; ++k) cudaMemsetAsync(lamJ[k], 0, fn * sizeof(double), s);
+    dim3 gld((unsigned)((ld + 63) / 64), (ctx->g.nth + 1 + 3) / 4);
+    passthru<<<gld, blk, 0, s>>>(A, d_in, d_out);
+    // current adjoint of the stage output: starts at lamIn
+    cudaMemcpyAsync(d_cur, d_in, sizeof(double *) * 6, cudaMemcpyDeviceToDevice, s);
+    for (int k = N; k >= 0; --k) {
+        // mu = P_k^T lam_k (damping in the last stage)
+        proj_T<<<grd, blk, 0, s>>>(A, d_cur, d_mu, (k == N && N > 0) ? 1 : 0);
+        // lam X^n (physical part) += mu; lam Cn += dt * (k==0 ? 1 : alpha) * mu; lam J -= dt * invA * mu
+        axpy6<<<nb, 256, 0, s>>>(d_out, d_mu, 1.0, fn);
+        axpy6<<<nb, 256, 0, s>>>(d_lcn, d_mu, dt * (k == 0 ? 1.0 : as), fn);
+        jadj<<<grd, blk, 0, s>>>(A, d_mu, d_J, -dt);
+        if (k > 0) {
+            // lam of the previous iterate = C^T (dt beta mu)
+            for (int c = 0; c < 6; ++c) {
+                cudaMemsetAsync(aux[c], 0, fn * sizeof(double), s);
+                cudaMemsetAsync(prev[c], 0, fn * sizeof(double), s);
+            }
+            // scale mu by dt*beta in place
+            axpy6<<<nb, 256, 0, s>>>(d_mu, d_mu, dt * bs - 1.0, fn);
+            circ_T<<<grd, blk, 0, s>>>(A, d_mu, d_aux, ctx->g.dth);
+            aux_T<<<gfull, blk, 0, s>>>(A, d_aux, d_prev);
+            cudaMemcpyAsync(d_cur, d_prev, sizeof(double *) * 6, cudaMemcpyDeviceToDevice, s);
+        }
+    }
+    // lam X^n += C^T lam Cn
+    for (int c = 0; c < 6; ++c) cudaMemsetAsync(aux[c], 0, fn * sizeof(double), s);
+    circ_T<<<grd, blk, 0, s>>>(A, d_lcn, d_aux, ctx->g.dth);
+    aux_T<<<gfull, blk, 0, s>>>(A, d_aux, d_out);
+    (void)lamIn;
+    return cudaGetLastError() == cudaSuccess ? GRPIC_OK : GRPIC_ECUDA;
+}
+
+extern "C" grpic_status grpic_adjoint_field_step(grpic_ctx *ctx, const grpic_fields *lam_in, grpic_fields *lam_out,
+                                                 void *stream)
+{
+    if (!ctx || !lam_in || !lam_out || ctx->prm.precision != 64 || lam_in->ld != lam_out->ld ||
+        lam_in->ld < ctx->g.nr + 2 * NG || ctx->prm.n_field_iter < 1)
+        return GRPIC_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    int64_t ld = lam_in->ld;
+    size_t fn = (size_t)(ctx->g.nth + 1) * ld;
+    std::vector<double *> work(24, nullptr);
+    for (auto &w : work)
+        if (cudaMalloc(&w, fn * sizeof(double)) != cudaSuccess) return GRPIC_ENOMEM;
+    double *in[6], *out[6], *J[3];
+    for (int k = 0; k < 3; ++k) {
+        in[k] = (double *)lam_in->D[k];
+        in[3 + k] = (double *)lam_in->B[k];
+        out[k] = (double *)lam_out->D[k];
+        out[3 + k] = (double *)lam_out->B[k];
+        J[k] = (double *)lam_out->J[k];
+    }
+    double **dp[8];
+    double *cur_dummy[6] = {0};
+    bool ok = upload_ptrs(in, 6, &dp[0], s) == cudaSuccess && upload_ptrs(out, 6, &dp[1], s) == cudaSuccess &&
+              upload_ptrs(J, 3, &dp[2], s) == cudaSuccess && upload_ptrs(&work[0], 6, &dp[3], s) == cudaSuccess &&
+              upload_ptrs(&work[6], 6, &dp[4], s) == cudaSuccess && upload_ptrs(&work[12], 6, &dp[5], s) == cudaSuccess &&
+              upload_ptrs(&work[18], 6, &dp[6], s) == cudaSuccess && upload_ptrs(cur_dummy, 6, &dp[7], s) == cudaSuccess;
+    grpic_status st = ok ? field_adjoint(ctx, in, out, J, work.data(), ld, s, dp) : GRPIC_ENOMEM;
+    cudaStreamSynchronize(s);
+    for (int k = 0; k < 8; ++k)
+        if (ok) cudaFree(dp[k]);
+    for (auto w : work) cudaFree(w);
+    return st;
+}
+
+// ---------------------------------------------------------------------------
+// full gradient: forward with checkpoints, reverse sweep
+// ---------------------------------------------------------------------------
+extern "C" grpic_status grpic_adjoint_grad(grpic_ctx *ctx, const grpic_particles *p0, const grpic_fields *f0,
+                                           int nsteps, int checkpoint_every, int i_horizon, int trapezoid_ift,
+                                           double *L_out, double *const grad_p[5], double *const grad_f[6],
+                                           void *stream)
+{
+    if (!ctx || !p0 || !f0 || !L_out || ctx->prm.precision != 64 || nsteps < 1 || checkpoint_every < 1 ||
+        i_horizon < 1 || i_horizon > ctx->g.nr - 1 || ctx->prm.n_field_iter < 1 || f0->ld < ctx->g.nr + 2 * NG ||
+        p0->n < 0 || p0->n > INT32_MAX || (!grad_p && grad_f) || ctx->prm.n_push_iter > MAX_ITER)
+        return GRPIC_EINVAL;
+    const bool want = grad_p != nullptr;  // NULL: the objective alone
+    if (want)
+        for (int k = 0; k < 5; ++k)
+            if (!grad_p[k]) return GRPIC_EINVAL;
+    if (p0->n > 0 && (!p0->x1 || !p0->x2 || !p0->u1 || !p0->u2 || !p0->u3 || !p0->tag)) return GRPIC_EINVAL;
+    for (int k = 0; k < 3; ++k)
+        if (!f0->D[k] || !f0->B[k]) return GRPIC_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t ld = f0->ld, np = p0->n;
+    const size_t fn = (size_t)(ctx->g.nth + 1) * ld;
+    const int ck = checkpoint_every;
+    const int nseg = (nsteps + ck - 1) / ck;
+    std::vector<void *> allocs;
+    auto dalloc = [&](size_t bytes) -> void * {
+        void *q = nullptr;
+        if (cudaMalloc(&q, bytes > 0 ? bytes : 8) != cudaSuccess) return nullptr;
+        allocs.push_back(q);
+        return q;
+    };
+    auto cleanup = [&]() {
+        cudaStreamSynchronize(s);
+        for (void *q : allocs) cudaFree(q);
+    };
+    // states: checkpoints (nseg) and the current segment's states (ck + 1)
+    struct State {
+        double *F[6];
+        double *x[5];
+        uint32_t *tag;
+    };
+    auto new_state = [&](State &S) -> bool {
+        for (int k = 0; k < 6; ++k)
+            if (!(S.F[k] = (double *)dalloc(fn * sizeof(double)))) return false;
+        for (int k = 0; k < 5; ++k)
+            if (!(S.x[k] = (double *)dalloc(np * sizeof(double)))) return false;
+        return (S.tag = (uint32_t *)dalloc(np * sizeof(uint32_t))) != nullptr;
+    };
+    std::vector<State> cks(want ? nseg : 0), seg(want ? ck + 1 : 0);
+    bool ok = true;
+    for (auto &S : cks) ok = ok && new_state(S);
+    for (auto &S : seg) ok = ok && new_state(S);
+    // working particles / fields for the forward runs
+    State W;
+    ok = ok && new_state(W);
+    double *Jw[3];
+    for (int k = 0; k < 3; ++k) ok = ok && (Jw[k] = (double *)dalloc(fn * sizeof(double)));
+    int64_t *cnt = (int64_t *)dalloc(sizeof(int64_t));
+    double *Ldev = (double *)dalloc(sizeof(double));
+    // adjoint arrays
+    double *lamF[6], *lamF2[6], *lamJ[3], *lamP[5], *lamP2[5], *aux[6];
+    for (int k = 0; k < 6; ++k) {
+        ok = ok && (lamF[k] = (double *)dalloc(fn * sizeof(double)));
+        ok = ok && (lamF2[k] = (double *)dalloc(fn * sizeof(double)));
+        ok = ok && (aux[k] = (double *)dalloc(fn * sizeof(double)));
+    }
+    for (int k = 0; k < 3; ++k) ok = ok && (lamJ[k] = (double *)dalloc(fn * sizeof(double)));
+    for (int k = 0; k < 5; ++k) {
+        ok = ok && (lamP[k] = (double *)dalloc(np * sizeof(double)));
+        ok = ok && (lamP2[k] = (double *)dalloc(np * sizeof(double)));
+    }
+    std::vector<double *> work(want ? 24 : 0, nullptr);
+    for (auto &w : work) ok = ok && (w = (double *)dalloc(fn * sizeof(double)));
+    if (!ok) {
+        cleanup();
+        return GRPIC_ENOMEM;
+    }
+    auto copy_state = [&](State &dst, const State &src) {
+        for (int k = 0; k < 6; ++k) cudaMemcpyAsync(dst.F[k], src.F[k], fn * sizeof(double), cudaMemcpyDeviceToDevice, s);
+        for (int k = 0; k < 5; ++k) cudaMemcpyAsync(dst.x[k], src.x[k], np * sizeof(double), cudaMemcpyDeviceToDevice, s);
+        cudaMemcpyAsync(dst.tag, src.tag, np * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s);
+    };
+    // initial state -> W
+    for (int k = 0; k < 3; ++k) {
+        cudaMemcpyAsync(W.F[k], f0->D[k], fn * sizeof(double), cudaMemcpyDeviceToDevice, s);
+        cudaMemcpyAsync(W.F[3 + k], f0->B[k], fn * sizeof(double), cudaMemcpyDeviceToDevice, s);
+    }
+    void *px[5] = {p0->x1, p0->x2, p0->u1, p0->u2, p0->u3};
+    for (int k = 0; k < 5; ++k) cudaMemcpyAsync(W.x[k], px[k], np * sizeof(double), cudaMemcpyDeviceToDevice, s);
+    cudaMemcpyAsync(W.tag, p0->tag, np * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s);
+    cudaMemcpyAsync(cnt, &np, sizeof(int64_t), cudaMemcpyHostToDevice, s);
+    cudaMemsetAsync(Ldev, 0, sizeof(double), s);
+
+    grpic_fields FW;
+    for (int k = 0; k < 3; ++k) {
+        FW.D[k] = W.F[k];
+        FW.B[k] = W.F[3 + k];
+        FW.J[k] = Jw[k];
+    }
+    FW.ld = ld;
+    grpic_particles PW;
+    memset(&PW, 0, sizeof PW);
+    PW.n = np;
+    PW.capacity = np;
+    PW.d_count = nullptr;
+    PW.x1 = W.x[0];
+    PW.x2 = W.x[1];
+    PW.u1 = W.x[2];
+    PW.u2 = W.x[3];
+    PW.u3 = W.x[4];
+    PW.tag = W.tag;
+    double *Wf[6];
+    for (int k = 0; k < 6; ++k) Wf[k] = W.F[k];
+    double **dWf = nullptr, **dLamF = nullptr, **dLamF2 = nullptr, **dAux = nullptr, **dSegF = nullptr;
+    ok = upload_ptrs(Wf, 6, &dWf, s) == cudaSuccess && upload_ptrs(lamF, 6, &dLamF, s) == cudaSuccess &&
+         upload_ptrs(lamF2, 6, &dLamF2, s) == cudaSuccess && upload_ptrs(aux, 6, &dAux, s) == cudaSuccess &&
+         cudaMalloc(&dSegF, sizeof(double *) * 6) == cudaSuccess;
+    if (ok) {
+        allocs.push_back(dWf);
+        allocs.push_back(dLamF);
+        allocs.push_back(dLamF2);
+        allocs.push_back(dAux);
+        allocs.push_back(dSegF);
+    } else {
+        cleanup();
+        return GRPIC_ENOMEM;
+    }
+    FAdj A{ctx->g.nr, ctx->g.nth, ld, ctx->g.ld_tab, ctx->slab, ctx->tab, ctx->col1d};
+    const double wL = 1.0 / nsteps, dth = ctx->g.dth;
+    grpic_status st = GRPIC_OK;
+    auto fwd_step = [&]() -> grpic_status {
+        for (int k = 0; k < 3; ++k) cudaMemsetAsync(Jw[k], 0, fn * sizeof(double), s);
+        if (launch_push64(ctx, &PW, &FW, false, s) != cudaSuccess) return GRPIC_ECUDA;
+        grpic_status r = GRPIC_OK;
+        if (launch_field64(ctx, &FW, s) != cudaSuccess) r = GRPIC_ECUDA;
+        return r;
+    };
+    // ---- forward with checkpoints --------------------------------------
+    if (ensure_field_scratch_ext(ctx, ld) != GRPIC_OK || ensure_particle_scratch_ext(ctx, np) != GRPIC_OK) {
+        cleanup();
+        return GRPIC_ENOMEM;
+    }
+    for (int n = 0; n < nsteps && st == GRPIC_OK; ++n) {
+        if (want && n % ck == 0) copy_state(cks[n / ck], W);
+        st = fwd_step();
+        flux_kernel<<<1, 256, 0, s>>>(A, dWf, i_horizon, dth, wL, Ldev);
+    }
+    cudaMemcpyAsync(L_out, Ldev, sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (!want) {
+        int hst = 0;
+        cudaMemcpyAsync(&hst, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost, s);
+        cudaMemsetAsync(ctx->d_status, 0, sizeof(int), s);
+        ctx->keys_valid = 0;
+        cleanup();
+        if (cudaGetLastError() != cudaSuccess && st == GRPIC_OK) st = GRPIC_ECUDA;
+        if (st == GRPIC_OK && hst != 0) st = (grpic_status)hst;
+        return st;
+    }
+    // ---- reverse sweep -----------------------------------------------------
+    for (int k = 0; k < 6; ++k) cudaMemsetAsync(lamF[k], 0, fn * sizeof(double), s);
+    for (int k = 0; k < 5; ++k) cudaMemsetAsync(lamP[k], 0, np * sizeof(double), s);
+    double **dptrs[8];
+    double *Jl[3] = {lamJ[0], lamJ[1], lamJ[2]};
+    double *cur_dummy[6] = {0};
+    ok = upload_ptrs(lamF, 6, &dptrs[0], s) == cudaSuccess && upload_ptrs(lamF2, 6, &dptrs[1], s) == cudaSuccess &&
+         upload_ptrs(Jl, 3, &dptrs[2], s) == cudaSuccess && upload_ptrs(&work[0], 6, &dptrs[3], s) == cudaSuccess &&
+         upload_ptrs(&work[6], 6, &dptrs[4], s) == cudaSuccess && upload_ptrs(&work[12], 6, &dptrs[5], s) == cudaSuccess &&
+         upload_ptrs(&work[18], 6, &dptrs[6], s) == cudaSuccess && upload_ptrs(cur_dummy, 6, &dptrs[7], s) == cudaSuccess;
+    if (!ok) {
+        cleanup();
+        return GRPIC_ENOMEM;
+    }
+    for (int k = 0; k < 8; ++k) allocs.push_back(dptrs[k]);
+    dim3 gfull((ctx->g.ld_tab + 63) / 64, (ctx->g.nth + 1 + 3) / 4), blk(64, 4);
+    for (int sgi = nseg - 1; sgi >= 0 && st == GRPIC_OK; --sgi) {
+        int n0 = sgi * ck, len = std::min(ck, nsteps - n0);
+        // recompute the segment's states
+        copy_state(W, cks[sgi]);
+        copy_state(seg[0], W);
+        for (int m = 0; m < len && st == GRPIC_OK; ++m) {
+            st = fwd_step();
+            copy_state(seg[m + 1], W);
+        }
+        for (int m = len - 1; m >= 0 && st == GRPIC_OK; --m) {
+            // seed: lamF (adjoint of F^{n+1}) += wL dflux/dF^{n+1}
+            for (int k = 0; k < 6; ++k) cudaMemsetAsync(aux[k], 0, fn * sizeof(double), s);
+            cudaMemcpyAsync(dSegF, seg[m + 1].F, sizeof(double *) * 6, cudaMemcpyHostToDevice, s);
+            flux_seed<<<(ctx->g.nth + 127) / 128, 128, 0, s>>>(A, dSegF, i_horizon, dth, wL, dAux);
+            aux_T<<<gfull, blk, 0, s>>>(A, dAux, dLamF);
+            // fields: lamF -> lamF2 (adjoint of F^n through the field update), lamJ
+            st = field_adjoint(ctx, lamF, lamF2, lamJ, work.data(), ld, s, dptrs);
+            if (st != GRPIC_OK) break;
+            // particles
+            PAdjArgs P;
+            P.g = ctx->g;
+            P.dt = ctx->prm.dt;
+            P.n_iter = ctx->prm.n_push_iter;
+            P.ift = trapezoid_ift ? 1 : 0;
+            for (int k = 0; k < 4; ++k) {
+                P.qm[k] = ctx->prm.q_over_m[k];
+                P.qw[k] = ctx->prm.q_weight[k];
+                P.massive[k] = ctx->prm.massive[k];
+            }
+            P.n = np;
+            for (int k = 0; k < 5; ++k) {
+                P.x[k] = seg[m].x[k];
+                P.lam1[k] = lamP[k];
+                P.lam0[k] = lamP2[k];
+            }
+            P.tag0 = seg[m].tag;
+            P.tag1 = seg[m + 1].tag;
+            for (int k = 0; k < 6; ++k) {
+                P.F[k] = seg[m].F[k];
+                P.lamF[k] = lamF2[k];
+            }
+            for (int k = 0; k < 3; ++k) P.lamJ[k] = lamJ[k];
+            P.ld = ld;
+            if (np > 0) particle_adjoint<<<(unsigned)((np + 127) / 128), 128, 0, s>>>(P);
+            if (cudaGetLastError() != cudaSuccess) st = GRPIC_ECUDA;
+            for (int k = 0; k < 5; ++k) std::swap(lamP[k], lamP2[k]);
+            // lamF <- lamF2
+            for (int k = 0; k < 6; ++k) cudaMemcpyAsync(lamF[k], lamF2[k], fn * sizeof(double), cudaMemcpyDeviceToDevice, s);
+        }
+    }
+    for (int k = 0; k < 5; ++k) cudaMemcpyAsync(grad_p[k], lamP[k], np * sizeof(double), cudaMemcpyDeviceToDevice, s);
+    if (grad_f)
+        for (int k = 0; k < 6; ++k)
+            if (grad_f[k]) cudaMemcpyAsync(grad_f[k], lamF[k], fn * sizeof(double), cudaMemcpyDeviceToDevice, s);
+    // a particle the forward refused (range, non-finite) is reported like the step does
+    int hst = 0;
+    cudaMemcpyAsync(&hst, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost, s);
+    cudaMemsetAsync(ctx->d_status, 0, sizeof(int), s);
+    ctx->keys_valid = 0;
+    cleanup();
+    if (cudaGetLastError() != cudaSuccess && st == GRPIC_OK) st = GRPIC_ECUDA;
+    if (st == GRPIC_OK && hst != 0) st = (grpic_status)hst;
+    return st;
+}

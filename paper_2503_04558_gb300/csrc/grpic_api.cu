@@ -168,6 +168,10 @@ grpic_status field_impl(grpic_ctx *ctx, grpic_fields *f, cudaStream_t s)
 
 }  // namespace
 
+// scratch for the adjoint translation unit (same buffers as the step's)
+grpic_status grpic::ensure_field_scratch_ext(grpic_ctx *ctx, int64_t ld) { return ensure_field_scratch(ctx, ld); }
+grpic_status grpic::ensure_particle_scratch_ext(grpic_ctx *ctx, int64_t n) { return ensure_particle_scratch(ctx, n); }
+
 extern "C" {
 
 grpic_status grpic_init(grpic_metric metric, double spin, const grpic_grid *grid, const grpic_params *prm,

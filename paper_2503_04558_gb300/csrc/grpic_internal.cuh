@@ -146,6 +146,8 @@ cudaError_t launch_field32(grpic_ctx *ctx, grpic_fields *f, cudaStream_t s);
 cudaError_t launch_keys(grpic_ctx *ctx, const grpic_particles *p, cudaStream_t s);
 cudaError_t sort_setup();
 cudaError_t launch_sort(grpic_ctx *ctx, grpic_particles *p, grpic_particles *scratch, cudaStream_t s);
+grpic_status ensure_field_scratch_ext(grpic_ctx *ctx, int64_t ld);
+grpic_status ensure_particle_scratch_ext(grpic_ctx *ctx, int64_t n);
 cudaError_t launch_diag(grpic_ctx *ctx, const grpic_particles *p, const grpic_fields *f, void *rho, void *divD,
                         cudaStream_t s);
 }  // namespace grpic

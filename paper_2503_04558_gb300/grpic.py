@@ -551,3 +551,139 @@ class Batch1D:
 
     def sync(self, stream=None):
         return self.lib.grpic_batch1d_sync(self.h, _stream(stream))
+
+
+# ---------------------------------------------------------------------------
+# differentiable form: horizon Poynting flux and its adjoint (FP64 contexts)
+# ---------------------------------------------------------------------------
+EXPORTS += ["grpic_horizon_flux", "grpic_adjoint_field_step", "grpic_adjoint_grad"]
+
+
+def _load_adj(lib):
+    v, p = C.c_void_p, C.POINTER
+    for name, args in {"grpic_horizon_flux": [v, p(FieldsC), C.c_int, p(C.c_double), v],
+                       "grpic_adjoint_field_step": [v, p(FieldsC), p(FieldsC), v],
+                       "grpic_adjoint_grad": [v, p(ParticlesC), p(FieldsC), C.c_int, C.c_int, C.c_int,
+                                              C.c_int, p(C.c_double), v, v, v]}.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = C.c_int
+
+
+def horizon_index(cfg: Config, a_nominal: float | None = None) -> int:
+    """Column nearest the outer horizon of spin a_nominal (default cfg.a)."""
+    a = cfg.a if a_nominal is None else a_nominal
+    return int(round(math.log(horizon(a) / cfg.r_in) / cfg.dx1))
+
+
+def _fields_of(D, B, ld, J=None):
+    f = FieldsC()
+    for k in range(3):
+        f.D[k] = D[k].data_ptr()
+        f.B[k] = B[k].data_ptr()
+        f.J[k] = J[k].data_ptr() if J is not None else 0
+    f.ld = ld
+    return f
+
+
+def horizon_flux(gctx: Context, F: Fields, i_horizon: int, stream=None) -> float:
+    """flux(F) = sum_j (E_th H_ph - E_ph H_th)(r_iH, theta_{j+1/2}) dtheta."""
+    _load_adj(gctx.lib)
+    out = C.c_double()
+    fc = F.c()
+    gctx._check(gctx.lib.grpic_horizon_flux(gctx.h, C.byref(fc), int(i_horizon), C.byref(out), _stream(stream)),
+                "grpic_horizon_flux")
+    return out.value
+
+
+def adjoint_field_step(gctx: Context, lam: Fields, stream=None) -> Fields:
+    """Transpose of one field update: returns a Fields holding the adjoint of
+    the fields before the update (D, B) and of the integrated currents (J)."""
+    _load_adj(gctx.lib)
+    out = Fields(gctx.cfg, device=lam.D[0].device, ld=lam.ld)
+    fi, fo = lam.c(), out.c()
+    gctx._check(gctx.lib.grpic_adjoint_field_step(gctx.h, C.byref(fi), C.byref(fo), _stream(stream)),
+                "grpic_adjoint_field_step")
+    return out
+
+
+def adjoint_grad(gctx: Context, x, tag, D, B, nsteps: int, i_horizon: int, checkpoint_every: int = 20,
+                 want_grad: bool = True, ift: bool = False, stream=None):
+    """Objective L of nsteps steps from particles x = (r, theta, u_r, u_theta,
+    u_phi) (five float64 device tensors of n), tag (int32 tensor of n) and
+    fields D, B (three (n_theta+1, ld) float64 tensors each).  Returns L and,
+    if want_grad, the gradients (five tensors like x, six like D + B).
+    ift=True differentiates the converged geodesic trapezoid (implicit-function
+    theorem) instead of the correctors the push runs."""
+    import torch
+    _load_adj(gctx.lib)
+    n = int(x[0].numel())
+    ld = int(D[0].shape[1])
+    xs = [t.contiguous() for t in x]
+    pc = ParticlesC()
+    pc.n, pc.capacity, pc.d_count = n, max(n, 1), 0
+    pc.x1, pc.x2, pc.u1, pc.u2, pc.u3 = (t.data_ptr() for t in xs)
+    pc.tag = tag.data_ptr()
+    pc.cell = 0
+    Dc = [t.contiguous() for t in D]
+    Bc = [t.contiguous() for t in B]
+    fc = _fields_of(Dc, Bc, ld)
+    L = C.c_double()
+    gp = gf = None
+    if want_grad:
+        gp = [torch.empty_like(t) for t in xs]
+        gf = [torch.empty_like(t) for t in Dc + Bc]
+        arr_p = (C.c_void_p * 5)(*[t.data_ptr() for t in gp])
+        arr_f = (C.c_void_p * 6)(*[t.data_ptr() for t in gf])
+    else:
+        arr_p = arr_f = None
+    st = gctx.lib.grpic_adjoint_grad(gctx.h, C.byref(pc), C.byref(fc), int(nsteps), int(checkpoint_every),
+                                     int(i_horizon), 1 if ift else 0, C.byref(L), arr_p, arr_f, _stream(stream))
+    gctx._check(st, "grpic_adjoint_grad")
+    return L.value, gp, gf
+
+
+def _autograd_fn():
+    import torch
+
+    class HorizonFluxFn(torch.autograd.Function):
+        """L = horizon flux objective; inputs: the five particle state
+        tensors and the six field tensors at step 0.  The gradient comes from
+        the hand-written adjoint (grpic_adjoint_grad), evaluated in the
+        forward pass when any input needs it."""
+
+        @staticmethod
+        def forward(fctx, gctx, tag, nsteps, i_horizon, checkpoint_every, ift, *xs):
+            need = any(fctx.needs_input_grad[6:])
+            L, gp, gf = adjoint_grad(gctx, list(xs[:5]), tag, list(xs[5:8]), list(xs[8:11]), nsteps, i_horizon,
+                                     checkpoint_every, want_grad=need, ift=ift)
+            if need:
+                fctx.save_for_backward(*(gp + gf))
+            return torch.tensor(L, dtype=torch.float64, device=xs[0].device)
+
+        @staticmethod
+        def backward(fctx, gL):
+            g = fctx.saved_tensors
+            return (None,) * 6 + tuple(gL * t for t in g)
+
+    return HorizonFluxFn
+
+
+_HFN = None
+
+
+def horizon_flux_objective(gctx: Context, x, tag, D, B, nsteps: int, i_horizon: int, checkpoint_every: int = 20,
+                           ift: bool = False):
+    """Differentiable L(x, D, B) (torch scalar); backward() fills .grad of the
+    inputs that require it through the adjoint."""
+    global _HFN
+    if _HFN is None:
+        _HFN = _autograd_fn()
+    return _HFN.apply(gctx, tag, int(nsteps), int(i_horizon), int(checkpoint_every), bool(ift), *x, *D, *B)
+
+
+def spin_gradient_fd(make, h: float = 1e-6) -> float:
+    """dL/da by a central difference: make(a_offset) must build the context
+    and the inputs at spin a + a_offset on the grid of the nominal spin and
+    return L.  (The adjoint does not differentiate the metric tables.)"""
+    return (make(h) - make(-h)) / (2.0 * h)
