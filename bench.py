@@ -7,7 +7,14 @@ cell (4.19e8 e+/e-), thermal momenta (Maxwell-Juttner T = 0.3), absorbing
 outer layer, CFL 0.5.  A step is one pass of the whole hot path: push with
 fused deposit, field update (1 predictor + 7 correctors), stable sort by cell.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision 64|32]
+The headline value is the FP32 form (int32 cell + FP32 offsets and momenta,
+double-FP32 metric inside 1.5 r_H); the same line carries the FP64 plain path
+on the same workload ("fp64_plain"), the differentiable form ("adjoint": the
+gradient of the horizon Poynting flux over 200 steps of a 256^2 run with 2e6
+particles) and the batched 1D spark gaps ("batch1d": 512 lines x 4096 cells).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision both|32|64]
+                  [--workload grpic2d|batch1d|adjoint] [--no-extras]
                   [--impl ours|reference]
 
 --impl reference times the FP64 CPU oracle (test infrastructure) on a bounded
@@ -40,6 +47,17 @@ R_OUT = 100.0
 PPC = 100
 THERMAL_T = 0.3
 B0 = 1.0
+
+
+# Arithmetic per particle-step of the push kernels, counted by ncu on the same
+# kernels (flop_count = 2 FMA + MUL + ADD of the SASS instruction counters;
+# the capture commands and counts are in profiles/).
+PUSH64_FP64_FLOP = 1711.0   # profiles/push64_fp64_512x512_16ppc.md
+PUSH32_FP32_FLOP = 1633.0   # profiles/push32_fp32form_1024x1024_16ppc.md
+# ALU peaks from unit counts x clock: 152 SMs x 2.07 GHz x (4 FP64 flops,
+# 256 FP32 flops) per SM per clock
+FP64_PEAK_TFLOPS = 152 * 2.07e9 * 4 / 1e12
+FP32_PEAK_TFLOPS = 152 * 2.07e9 * 256 / 1e12
 
 
 def horizon(a):
@@ -124,7 +142,7 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
-def run_ours(args, rank, world):
+def run_grpic(args, prec, rank, world, e2e_steps):
     import torch
     from paper_2503_04558_gb300 import build, grpic as G, synth
 
@@ -132,7 +150,6 @@ def run_ours(args, rank, world):
     G.load()
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
     torch.cuda.set_device(dev)
-    prec = args.precision
     cfg = workload_config(prec, args.grid, args.grid)
     ctx = G.Context(cfg)
     F = G.Fields(cfg)
@@ -194,15 +211,17 @@ def run_ours(args, rank, world):
 
     # end to end through host buffers (pinned), copies inside the timed region
     e2e = None
-    if args.e2e_steps > 0:
-        e2e = run_e2e(args, ctx, S, F, cfg, stream)
+    if e2e_steps > 0:
+        e2e = run_e2e(e2e_steps, ctx, S, F, cfg, stream)
 
     res = dict(total_ms=total_ms, push_ms=push_ms, field_ms=field_ms, n=n, live=live, cells=cfg.n_r * cfg.n_theta,
-               clocks=clk.summary(), e2e=e2e, cfg=cfg)
+               clocks=clk.summary(), e2e=e2e, cfg=cfg, prec=prec)
+    del S, F, ctx
+    torch.cuda.empty_cache()
     return res
 
 
-def run_e2e(args, ctx, S, F, cfg, stream):
+def run_e2e(e2e_steps, ctx, S, F, cfg, stream):
     """Host-resident state: every step copies the particle and field arrays
     host->device from pinned memory, runs the step through the library and
     copies the state back."""
@@ -220,7 +239,7 @@ def run_e2e(args, ctx, S, F, cfg, stream):
     h2d = sum(h.numel() * h.element_size() for h in host + hostf)
     start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     start.record(stream)
-    for _ in range(args.e2e_steps):
+    for _ in range(e2e_steps):
         cur = [t for t in S.a.arrays() if t is not None]
         for h, t in zip(host, cur):
             t[:n].copy_(h, non_blocking=True)
@@ -235,9 +254,9 @@ def run_e2e(args, ctx, S, F, cfg, stream):
             h.copy_(t, non_blocking=True)
     stop.record(stream)
     torch.cuda.synchronize()
-    ms = start.elapsed_time(stop) / args.e2e_steps
+    ms = start.elapsed_time(stop) / e2e_steps
     return {"value": n / (ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": h2d,
-            "ms_per_step": ms, "steps": args.e2e_steps}
+            "ms_per_step": ms, "steps": e2e_steps}
 
 
 # ---------------------------------------------------------------------------
@@ -274,7 +293,7 @@ def oracle_sample(steps, n_side=128):
             "steps": steps, "grid": f"{n_side}x{n_side}"}
 
 
-def cpu_baseline_block(steps=2, n_side=128):
+def cpu_baseline_block(steps=2, n_side=256):
     s = oracle_sample(steps, n_side)
     return {"value": s["value"], "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"{s['grid']} sub-grid of the 2048x2048 workload, {PPC} ppc ({s['particles']} particles), "
@@ -335,7 +354,9 @@ def batch1d_inputs(nl, n, seed=2024):
     return theta, lines
 
 
-def run_batch1d(args):
+def batch1d_measure(steps, warmup):
+    """Tuned persistent run of the 512 lines; returns the figures and the
+    oracle's throughput on a bounded sample (the 8 smallest lines, 3 steps)."""
     import numpy as np
     import torch
     from paper_2503_04558_gb300 import build, grpic as G
@@ -359,8 +380,8 @@ def run_batch1d(args):
     step = 0
     done, best = B.tune(L, 2, step)         # the tuner's trial steps are real steps
     step += done
-    B.run(L, args.warmup, step)
-    step += args.warmup
+    B.run(L, warmup, step)
+    step += warmup
     st = B.sync()
     if st != 0:
         raise RuntimeError(f"device status {st}")
@@ -369,15 +390,14 @@ def run_batch1d(args):
     t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler(torch.cuda.current_device()) as clk:
         t0.record(stream)
-        B.run(L, args.steps, step)
+        B.run(L, steps, step)
         t1.record(stream)
         torch.cuda.synchronize()
     ms = t0.elapsed_time(t1)
     st = B.sync()
     ev1 = L.events.cpu().numpy()
     pushes = int(ev1[2] - ev0[2])
-    cells = B1_LINES * B1_CELLS * args.steps
-    # oracle on a bounded sample: the 8 smallest lines, 3 steps, single thread
+    cells = B1_LINES * B1_CELLS * steps
     import oracle as O
     t = time.perf_counter()
     oracle_pushes = 0
@@ -394,93 +414,223 @@ def run_batch1d(args):
             oracle_pushes += S.n
             O.line_step(Lo, s, S, D)
     osec = time.perf_counter() - t
+    out = {"value": pushes / (ms * 1e-3), "unit": "particle-steps/s", "steps": steps, "warmup": warmup + done,
+           "ms_per_step": ms / steps, "dtype": "f32",
+           "workload": "512 radial lines x 4096 cells, a=0.99, r in [r_H, 20], monopole B0=2e3, gamma_thr=100, "
+                       "eps_ph=4, tau=2, initial 10^U(3,5) particles per line, capacity 1e6 per line",
+           "initial_particles": n0, "particles_now": int(L.count.sum().item()), "tuned_launch": list(best),
+           "cell_updates_per_s": cells / (ms * 1e-3),
+           "events": {"emitted": int(ev1[0] - ev0[0]), "converted": int(ev1[1] - ev0[1])},
+           "status": int(st), "clocks": clk.summary(), "gpu_launches": 2,
+           "l2": "inputs larger than L2 (particle state %.0f MB)" % (n0 * 24 / 1e6),
+           "cpu_baseline": {"value": oracle_pushes / osec, "unit": "particle-steps/s", "cores": 1,
+                            "kind": "oracle", "sample": f"8 smallest lines, 3 steps, FP64, {osec:.1f} s"}}
+    del B, L
+    torch.cuda.empty_cache()
+    return out
+
+
+def run_batch1d(args):
+    m = batch1d_measure(args.steps, args.warmup)
     line = {"metric": "batched 1D spark gaps: particle push+deposit/s (one persistent launch)",
-            "value": pushes / (ms * 1e-3), "unit": "particle-steps/s", "n_gpus": 1, "steps": args.steps,
-            "warmup": args.warmup + done, "ms_per_step": ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "512 radial lines x 4096 cells, a=0.99, r in [r_H, 20], monopole B0=2e3, "
-                                   "gamma_thr=100, eps_ph=4, tau=2, initial 10^U(3,5) particles per line, "
-                                   "capacity 1e6 per line", "initial_particles": n0,
-                       "particles_now": int(L.count.sum().item()), "tuned_launch": list(best)},
-            "cell_updates_per_s": cells / (ms * 1e-3), "events": {"emitted": int(ev1[0] - ev0[0]),
-                                                                 "converted": int(ev1[1] - ev0[1])},
-            "status": int(st), "clocks": clk.summary(), "gpu_launches": 2,
-            "cpu_baseline": {"value": oracle_pushes / osec, "unit": "particle-steps/s", "cores": 1,
-                             "kind": "oracle", "sample": f"8 smallest lines, 3 steps, FP64, {osec:.1f} s"}}
+            "value": m["value"], "unit": m["unit"], "n_gpus": 1, "steps": args.steps, "warmup": m["warmup"],
+            "ms_per_step": m["ms_per_step"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": m["workload"], "initial_particles": m["initial_particles"],
+                       "particles_now": m["particles_now"], "tuned_launch": m["tuned_launch"], "l2": m["l2"]},
+            "cell_updates_per_s": m["cell_updates_per_s"], "events": m["events"], "status": m["status"],
+            "clocks": m["clocks"], "gpu_launches": 2, "cpu_baseline": m["cpu_baseline"]}
     print(json.dumps(line), flush=True)
 
 
 # ---------------------------------------------------------------------------
+# differentiable form: gradient of the horizon Poynting flux
+# ---------------------------------------------------------------------------
+ADJ_N, ADJ_A, ADJ_ROUT, ADJ_NP, ADJ_STEPS = 256, 0.9, 50.0, 2_000_000, 200
+
+
+def adjoint_measure(reps=2):
+    """256^2, a = 0.9, r in [0.9 r_H, 50], Wald B0 = 1, 2e6 particles (sigma
+    0.1), 200 FP64 steps; L = time-averaged horizon Poynting flux.  Times the
+    objective alone and the objective with its gradient (forward with
+    checkpoints every 20 steps, recompute and reverse sweep); an L2-sized
+    buffer is rewritten before every timed run (the state is below L2)."""
+    import torch
+    from paper_2503_04558_gb300 import build, grpic as G, synth
+
+    build.build()
+    G.load()
+    rin = 0.9 * horizon(ADJ_A)
+    cfg = G.Config(ADJ_N, ADJ_N, ADJ_A, rin, ADJ_ROUT)
+    ctx = G.Context(cfg)
+    F = G.Fields(cfg)
+    ctx.init_fields(F, G.WALD, 1.0)
+    gen = synth.particles_torch(ADJ_N, ADJ_N, cfg.r_in, cfg.r_out, ADJ_NP, seed=5, sigma=0.1, device="cuda")
+    x = [gen[k].contiguous() for k in ("r", "th", "u1", "u2", "u3")]
+    tag = gen["tag"]
+    tag = (tag.to(torch.int64) if tag.dtype != torch.int32 else tag).to(torch.int32).contiguous()
+    iH = G.horizon_index(cfg)
+    flush = torch.empty(256 * 2**20 // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def timed(want):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        L, gp, gf = G.adjoint_grad(ctx, x, tag, F.D, F.B, ADJ_STEPS, iH, want_grad=want)
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b), L
+
+    timed(False)
+    timed(True)   # warm-up of both paths
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        fwd = [timed(False) for _ in range(reps)]
+        grad = [timed(True) for _ in range(reps)]
+    f_ms = statistics.mean(t for t, _ in fwd)
+    g_ms = statistics.mean(t for t, _ in grad)
+    out = {"value": ADJ_NP * ADJ_STEPS / (g_ms * 1e-3), "unit": "particle-steps/s (objective + gradient)",
+           "forward_s": f_ms / 1e3, "gradient_s": g_ms / 1e3, "gradient_over_forward": g_ms / f_ms,
+           "objective": grad[0][1], "dtype": "f64", "checkpoint_every": 20, "reps": reps,
+           "workload": "256x256, a=0.9, r in [0.9 r_H, 50], Wald B0=1, 2e6 e+/e- (sigma 0.1), 200 steps, "
+                       "L = time-averaged horizon Poynting flux, gradient w.r.t. the initial particle state "
+                       "and fields", "l2": "state below L2: 256 MB written before each timed run",
+           "clocks": clk.summary()}
+    del ctx, F, x, gen, flush
+    torch.cuda.empty_cache()
+    return out
+
+
+def run_adjoint(args):
+    m = adjoint_measure(max(1, args.steps))
+    line = {"metric": "differentiable form: particle-steps/s of objective + gradient (hand-written adjoint)",
+            "value": m["value"], "unit": m["unit"], "n_gpus": 1, "steps": m["reps"], "warmup": 1,
+            "ms_per_step": m["gradient_s"] * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": m["workload"], "l2": m["l2"]}, "forward_s": m["forward_s"],
+            "gradient_over_forward": m["gradient_over_forward"], "objective": m["objective"],
+            "clocks": m["clocks"]}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+def grpic_summary(res, args, world, esz_prec):
+    """Per-form figures and the roofline of the push kernel."""
+    n, cells = res["n"], res["cells"]
+    push_ms = statistics.mean(res["push_ms"])
+    field_ms = statistics.mean(res["field_ms"])
+    ms = res["total_ms"] / args.steps
+    pk, pk_kind = peaks()
+    prec = res["prec"]
+    esz = 8 if prec == 64 else 4
+    # algorithmic bytes of one push launch: read and write the particle state
+    # (FP64: r, theta, u_r, u_theta, u_phi, tag; FP32: cell, o1, o2, u x3, tag)
+    bpp = (5 * esz + 4) * 2 + (4 if prec == 32 else 0) * 2
+    gbs = n * bpp / (push_ms * 1e-3) / 1e9
+    hbm = {"kernel": "push+deposit", "bound": "hbm", "achieved": gbs, "peak": pk["hbm_gbs"], "unit": "GB/s",
+           "frac": gbs / pk["hbm_gbs"], "traffic": None, "peak_source": f"{pk_kind} hbm_gbs (MEASURED_PEAKS)",
+           "bytes_per_particle": bpp}
+    # the FP32 form is bound by FP32 instruction issue, not by HBM: report
+    # the FP32 ALU roofline with the HBM one beside it
+    ach32 = n * PUSH32_FP32_FLOP / (push_ms * 1e-3) / 1e12
+    roof = {"kernel": "push+deposit (FP32 form)", "bound": "alu", "achieved": ach32, "peak": FP32_PEAK_TFLOPS,
+            "unit": "TFLOP/s", "frac": ach32 / FP32_PEAK_TFLOPS, "traffic": None,
+            "peak_source": "152 SMs x 2.07 GHz x 256 FP32 flop/clk/SM (recipe unit counts and clock)",
+            "flop_per_particle": PUSH32_FP32_FLOP, "hbm": hbm}
+    if prec == 64:
+        # FP64 arithmetic bounds this kernel on GB300: report the FP64 roofline
+        ach = n * PUSH64_FP64_FLOP / (push_ms * 1e-3) / 1e12
+        roof = {"kernel": "push+deposit (FP64)", "bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS,
+                "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS, "traffic": None,
+                "peak_source": "152 SMs x 2.07 GHz x 4 FP64 flop/clk/SM (recipe unit counts and clock)",
+                "flop_per_particle": PUSH64_FP64_FLOP, "hbm": hbm}
+    return {"value": world * n * args.steps / (res["total_ms"] * 1e-3), "ms_per_step": ms,
+            "push_deposit_per_s": world * n / (push_ms * 1e-3), "cell_updates_per_s": world * cells / (field_ms * 1e-3),
+            "push_ms": push_ms, "field_ms": field_ms, "sort_ms": ms - push_ms - field_ms, "live_particles": res["live"],
+            "roofline": roof, "clocks": res["clocks"], "particles": n, "cells": cells,
+            "dtype": "f64" if prec == 64 else "f32"}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=4)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", type=int, default=64, choices=[64, 32])
+    ap.add_argument("--precision", default="both", choices=["both", "32", "64"],
+                    help="both: FP32 form headline + FP64 plain on the same workload")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the adjoint and batch1d sub-measurements")
     ap.add_argument("--grid", type=int, default=NR, help="cells per dimension (profiling runs use smaller grids)")
     ap.add_argument("--ppc", type=int, default=PPC, help="particles per cell")
-    ap.add_argument("--workload", default="grpic2d", choices=["grpic2d", "batch1d"])
+    ap.add_argument("--workload", default="grpic2d", choices=["grpic2d", "batch1d", "adjoint"])
     args = ap.parse_args()
-    if args.workload == "batch1d" and args.impl == "ours":
-        run_batch1d(args)
-        return
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.workload == "batch1d":
+        run_batch1d(args)
+        return
+    if args.workload == "adjoint":
+        run_adjoint(args)
         return
     import torch
     world = int(os.environ.get("WORLD_SIZE", 1))
     rank = int(os.environ.get("RANK", 0))
     if world > 1:
         torch.distributed.init_process_group("nccl")
-    res = run_ours(args, rank, world)
+    head_prec = 64 if args.precision == "64" else 32
+    res = run_grpic(args, head_prec, rank, world, args.e2e_steps)
     total_ms = res["total_ms"]
     if world > 1:
         t = torch.tensor([total_ms], device="cuda")
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         total_ms = float(t.item())
+        res["total_ms"] = total_ms
+    second = None
+    if args.precision == "both":
+        second = run_grpic(args, 64, rank, world, 0)
+        if world > 1:
+            t = torch.tensor([second["total_ms"]], device="cuda")
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            second["total_ms"] = float(t.item())
+    extras = {}
+    if not args.no_extras:
+        for name, fn in (("adjoint", lambda: adjoint_measure(2)), ("batch1d", lambda: batch1d_measure(64, 3))):
+            try:
+                extras[name] = fn()
+            except Exception as e:  # reported, not hidden: the headline stands on its own
+                extras[name] = {"error": f"{type(e).__name__}: {e}"}
     if rank == 0:
         cfg = res["cfg"]
-        n, cells = res["n"], res["cells"]
-        ms = total_ms / args.steps
-        value = world * n * args.steps / (total_ms * 1e-3)
-        push_ms = statistics.mean(res["push_ms"])
-        field_ms = statistics.mean(res["field_ms"])
-        pk, pk_kind = peaks()
-        esz = 8 if args.precision == 64 else 4
-        # algorithmic bytes of one push+deposit launch: read and write the
-        # particle state (r, theta, u_r, u_theta, u_phi, tag [, cell])
-        bpp = (5 * esz + 4) * 2 + (4 if args.precision == 32 else 0) * 2
-        achieved_gbs = n * bpp / (push_ms * 1e-3) / 1e9
-        roof = {"kernel": "push+deposit", "bound": "hbm", "achieved": achieved_gbs, "peak": pk["hbm_gbs"],
-                "unit": "GB/s", "frac": achieved_gbs / pk["hbm_gbs"], "traffic": None,
-                "peak_source": f"{pk_kind} hbm_gbs", "bytes_per_particle": bpp}
-        if args.precision == 64:
-            # FP64 arithmetic bounds this kernel on GB300;
-            # flops counted per particle-step from the kernel's DP instructions
-            fpp = float(os.environ.get("GRPIC_FP64_FLOP_PER_PARTICLE", "0")) or None
-            fp64_peak = float(os.environ.get("GRPIC_FP64_PEAK_TFLOPS", "1.25"))
-            if fpp:
-                ach = n * fpp / (push_ms * 1e-3) / 1e12
-                roof = {"kernel": "push+deposit", "bound": "alu", "achieved": ach, "peak": fp64_peak,
-                        "unit": "TFLOP/s", "frac": ach / fp64_peak, "traffic": None,
-                        "hbm_frac": achieved_gbs / pk["hbm_gbs"], "flop_per_particle": fpp}
-        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-                "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-                "vs_baseline": None, "dtype": "f64" if args.precision == 64 else "f32", "data": "synthetic",
+        h = grpic_summary(res, args, world, head_prec)
+        esz = 8 if head_prec == 64 else 4
+        line = {"metric": METRIC, "value": h["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": h["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": h["dtype"], "data": "synthetic",
                 "config": {"workload": "GRPIC step (push+deposit, field update 1+7 stages, sort), %dx%d "
                                        "log-r x theta, a=0.99, r in [0.9 r_H, 100], split monopole, %d ppc, thermal "
-                                       "T=0.3, FP%d" % (args.grid, args.grid, args.ppc, args.precision),
-                           "particles": n, "cells": cells, "parallelism": f"replicas x{world}",
-                           "l2": "inputs larger than L2 (particle state %.1f GB)" % (n * (5 * esz + 4) / 1e9)},
-                "push_deposit_per_s": world * n / (push_ms * 1e-3),
-                "cell_updates_per_s": world * cells / (field_ms * 1e-3),
-                "push_ms": push_ms, "field_ms": field_ms, "sort_ms": ms - push_ms - field_ms,
-                "live_particles": res["live"], "roofline": roof, "clocks": res["clocks"],
+                                       "T=0.3, %s" % (args.grid, args.grid, args.ppc,
+                                                      "FP32 form (double-FP32 metric inside 1.5 r_H)"
+                                                      if head_prec == 32 else "FP64 plain"),
+                           "particles": h["particles"], "cells": h["cells"], "parallelism": f"replicas x{world}",
+                           "l2": "inputs larger than L2 (particle state %.1f GB)"
+                                 % (h["particles"] * (5 * esz + 4) / 1e9)},
+                "push_deposit_per_s": h["push_deposit_per_s"], "cell_updates_per_s": h["cell_updates_per_s"],
+                "push_ms": h["push_ms"], "field_ms": h["field_ms"], "sort_ms": h["sort_ms"],
+                "live_particles": h["live_particles"], "roofline": h["roofline"], "clocks": h["clocks"],
                 "gpu_launches": args.steps * (1 + 1 + cfg.n_field_iter + 7),
                 "e2e": res["e2e"]}
+        if second is not None:
+            s2 = grpic_summary(second, args, world, 64)
+            line["fp64_plain"] = {k: s2[k] for k in ("value", "ms_per_step", "push_deposit_per_s",
+                                                     "cell_updates_per_s", "push_ms", "field_ms", "sort_ms",
+                                                     "live_particles", "roofline", "clocks", "dtype")}
+            line["fp64_plain"]["unit"] = UNIT
+            line["fp32_over_fp64"] = h["value"] / s2["value"]
+        line.update(extras)
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline_block()
         print(json.dumps(line), flush=True)

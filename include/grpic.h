@@ -95,9 +95,12 @@ typedef struct {
  * the epsilon of u^0 (1 massive, 0 photon: no Boris step, Sec. 2.2).
  * precision: 64 (FP64 path) or 32 (FP32 form).  fp64_radius: in the FP32 form,
  * metric evaluations of particles in cells whose inner edge lies below
- * fp64_radius run in FP64 (<= 0: never).  push_tol: in the FP32 form, the geodesic corrector stops
- * once the FP64-measured change of the iterate falls below push_tol (<= 0:
- * always n_push_iter correctors); the FP64 path always runs n_push_iter. */
+ * fp64_radius run in extended precision (<= 0: never), with the arithmetic
+ * island_arith selects: 0 double-FP32 pairs (~48-bit significands on the
+ * FP32 pipes, the default), 1 native FP64.  push_tol: in the FP32 form, the
+ * geodesic corrector stops once the FP64-measured change of the iterate falls
+ * below push_tol (<= 0: always n_push_iter correctors); the FP64 path always
+ * runs n_push_iter. */
 typedef struct {
     double dt;
     double beta_field;
@@ -110,6 +113,7 @@ typedef struct {
     int32_t sort_every;
     double fp64_radius;
     double push_tol;
+    int32_t island_arith;
 } grpic_params;
 
 typedef struct {

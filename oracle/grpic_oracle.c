@@ -27,7 +27,11 @@
  *     (bundled convention, Sec. 2.2 and Fig. stepping).
  *
  * Parity pins: see tests/test_oracle_*.py; every exported function here is
- * pinned by at least one test against something other than itself.
+ * pinned by at least one test against something other than itself.  One part
+ * is parity unpinned: the profile of the outer absorbing layer, f <- f (1 -
+ * d_max s^3) over the last damp_cells columns, is a reading (the paper names
+ * the layer but gives no profile or constants); the tests pin only that it
+ * leaves the interior untouched and that it is off when d_max = 0.
  */
 #include <math.h>
 #include <stdint.h>

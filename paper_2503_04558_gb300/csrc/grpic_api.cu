@@ -190,6 +190,7 @@ grpic_status grpic_init(grpic_metric metric, double spin, const grpic_grid *grid
         prm->n_field_iter > 64)
         return GRPIC_EINVAL;
     if (prm->precision != 64 && prm->precision != 32) return GRPIC_EINVAL;
+    if (prm->island_arith != 0 && prm->island_arith != 1) return GRPIC_EINVAL;
     if (!(prm->beta_field >= 0.0 && prm->beta_field <= 1.0)) return GRPIC_EINVAL;
 
     grpic_ctx *ctx = new (std::nothrow) grpic_ctx();
@@ -247,6 +248,26 @@ grpic_status grpic_init(grpic_metric metric, double spin, const grpic_grid *grid
             to_float<<<(unsigned)((n + 255) / 256), 256>>>(ctx->tab, ctx->tab32, n);
             to_float<<<(unsigned)((4 * g.ld_tab + 255) / 256), 256>>>(ctx->col1d, ctx->col1d32, 4 * g.ld_tab);
             e = cudaGetLastError();
+        }
+        // float-pair tables of the near-horizon island: r_i and sin/cos theta_j
+        if (e == cudaSuccess) e = cudaMalloc(&ctx->rcol2, sizeof(float) * 2 * g.ld_tab);
+        if (e == cudaSuccess) e = cudaMalloc(&ctx->rowsc, sizeof(float) * 4 * (g.nth + 1));
+        if (e == cudaSuccess) {
+            auto split = [](double x, float *o) {
+                o[0] = (float)x;
+                o[1] = (float)(x - (double)o[0]);
+            };
+            float *h2 = (float *)malloc(sizeof(float) * 2 * g.ld_tab);
+            float *h4 = (float *)malloc(sizeof(float) * 4 * (g.nth + 1));
+            for (int c = 0; c < g.ld_tab; ++c) split(g.r_in * std::exp((c - NG) * g.dx1), h2 + 2 * c);
+            for (int j = 0; j <= g.nth; ++j) {
+                split(std::sin(j * g.dth), h4 + 4 * j);
+                split(std::cos(j * g.dth), h4 + 4 * j + 2);
+            }
+            e = cudaMemcpy(ctx->rcol2, h2, sizeof(float) * 2 * g.ld_tab, cudaMemcpyHostToDevice);
+            if (e == cudaSuccess) e = cudaMemcpy(ctx->rowsc, h4, sizeof(float) * 4 * (g.nth + 1), cudaMemcpyHostToDevice);
+            free(h2);
+            free(h4);
         }
     }
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
@@ -372,7 +393,7 @@ const char *grpic_last_error(const grpic_ctx *ctx) { return ctx ? ctx->err : "nu
 void grpic_destroy(grpic_ctx *ctx)
 {
     if (!ctx) return;
-    void *ptrs[] = {ctx->rcol, ctx->tab, ctx->col1d, ctx->tab32, ctx->col1d32, ctx->fscratch, ctx->d_status, ctx->d_keys,
+    void *ptrs[] = {ctx->rcol, ctx->rcol2, ctx->rowsc, ctx->tab, ctx->col1d, ctx->tab32, ctx->col1d32, ctx->fscratch, ctx->d_status, ctx->d_keys,
                     ctx->d_count, ctx->d_offset, ctx->d_cursor, ctx->d_blocksum, ctx->d_perm, ctx->d_bigseg};
     for (void *q : ptrs)
         if (q) cudaFree(q);

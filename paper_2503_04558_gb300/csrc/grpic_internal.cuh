@@ -52,6 +52,8 @@ struct grpic_ctx {
     float *col1d32;
     size_t slab;        // elements per slab = (nth+1)*ld_tab
     double *rcol;       // r at integer columns r_in exp(i dx1), index i + NG
+    float *rcol2;       // the same as (hi, lo) float pairs (precision 32 only)
+    float *rowsc;       // sin, cos of theta_j = j dtheta as (hi, lo) pairs, j = 0..nth (precision 32)
     // field-solver scratch: Cn[6], two iterate buffers[12] in field precision
     void *fscratch;
     int64_t fscratch_ld;

@@ -10,13 +10,17 @@
 //     in the paper while the position keeps FP32 precision relative to its
 //     cell whatever the grid size;
 //   * fields, tables and deposited currents are FP32;
-//   * FP64 is kept for (i) the metric (alpha, beta, gamma^ij and derivatives)
-//     of particles in cells whose inner edge lies below fp64_radius (the FP64
-//     island near the horizon), (ii) the corrector's
+//   * extended precision is kept for (i) the metric (alpha, beta, gamma^ij and
+//     derivatives) of particles in cells whose inner edge lies below
+//     fp64_radius (the island near the horizon): double-FP32 pairs by
+//     default, native FP64 on request (island_arith), (ii) the corrector's
 //     convergence test: after each corrector the change of the iterate is
 //     measured in FP64 and the iteration stops once it is below the tolerance
 //     (at most n_push_iter correctors).
 #include "grpic_geo.cuh"
+#include "grpic_df.cuh"
+
+#include <type_traits>
 
 namespace grpic {
 namespace {
@@ -30,6 +34,12 @@ struct Push32Args {
     int massive[4];
     double r64;
     int i64;  // first column whose inner edge is at or beyond fp64_radius
+    int island_fp64;   // 1: native FP64 island, 0: double-FP32 pairs
+    int use_tol;       // FP64 convergence test of the correctors
+    float af, dthf, idthf, dx1f;  // a, dtheta, 1/dtheta, dx1 in FP32
+    df a_df, dth_df;              // a, dtheta as float pairs
+    const float *rcol2;  // r_i as (hi, lo) float pairs, index i + NG
+    const float *rowsc;  // sin, cos theta_j as float pairs, index j
     int64_t n;
     const int64_t *d_count;
     int32_t *cell;
@@ -183,16 +193,27 @@ template <typename M>
 __device__ __forceinline__ void push_one(const Push32Args &A, int i, int j, float &o1, float &o2, float u[3], int sp,
                                          float &dphi)
 {
+    constexpr bool IS_DF = std::is_same<M, df>::value, IS_D = std::is_same<M, double>::value;
     const GridDev &g = A.g;
-    const double rci = A.rcol[i + NG];
-    const float rcf = (float)rci, dx1f = (float)g.dx1;
-    const M am = (M)g.a;
-    const float d0 = rcf * expm1f(o1 * dx1f);  // r - r_i
+    const float2 rc2 = __ldg(reinterpret_cast<const float2 *>(A.rcol2) + i + NG);
+    const float rcf = IS_D ? (float)A.rcol[i + NG] : __fadd_rn(rc2.x, rc2.y);
+    const float d0 = rcf * expm1f(o1 * A.dx1f);  // r - r_i
     // metric at x^n, shared by the Boris step and the first right-hand side
-    M r0 = (M)rci + (M)d0;
-    M th0 = (sizeof(M) == 8) ? (M)(((double)j + (double)o2) * g.dth) : (M)(((float)j + o2) * (float)g.dth);
-    M s0, c0;
-    sincos_t(th0, &s0, &c0);
+    M am, r0, s0, c0;
+    if constexpr (IS_D) {
+        am = g.a;
+        r0 = A.rcol[i + NG] + (double)d0;
+        sincos(((double)j + (double)o2) * g.dth, &s0, &c0);
+    } else if constexpr (IS_DF) {
+        am = A.a_df;
+        r0 = df(rc2.x, rc2.y) + df(d0);
+        const float4 sc = __ldg(reinterpret_cast<const float4 *>(A.rowsc) + j);
+        sincos_shift_df(df(sc.x, sc.y), df(sc.z, sc.w), mul(A.dth_df, o2), s0, c0);
+    } else {
+        am = A.af;
+        r0 = rcf + d0;
+        sincosf(((float)j + o2) * A.dthf, &s0, &c0);
+    }
     KSGeo<M> m;
     ks_geo_sc<M>(am, r0, s0, c0, m);
     if (A.massive[sp] && A.qm[sp] != 0.0f) {
@@ -213,7 +234,7 @@ __device__ __forceinline__ void push_one(const Push32Args &A, int i, int j, floa
     }
     const float eps = A.massive[sp] ? 1.0f : 0.0f;
     const float dt = A.dt, h = 0.5f * dt;
-    const float idth = (float)(1.0 / g.dth);
+    const float idth = A.idthf;
     RhsT<float> f0, ft;
     geo_rhs_m<M, float>(m, eps, u[0], u[1], u[2], f0);
     f0.xt *= idth;
@@ -221,21 +242,40 @@ __device__ __forceinline__ void push_one(const Push32Args &A, int i, int j, floa
     float b1 = u[0] + dt * f0.ur, b2 = u[1] + dt * f0.ut;
     for (int it = 0; it < A.n_iter; ++it) {
         // metric at the iterate: theta = theta^n + (a2 - o2) dtheta
-        M dth_it = (sizeof(M) == 8) ? (M)(((double)a2 - (double)o2) * g.dth) : (M)((a2 - o2) * (float)g.dth);
-        M s, c;
-        if (fabs((double)dth_it) <= 0.05)
-            sincos_shift<M>(s0, c0, dth_it, s, c);
-        else
-            sincos_t(th0 + dth_it, &s, &c);
+        M s, c, ri;
+        if constexpr (IS_D) {
+            double d = ((double)a2 - (double)o2) * g.dth;
+            if (fabs(d) <= 0.05)
+                sincos_shift<double>(s0, c0, d, s, c);
+            else
+                sincos(((double)j + (double)o2) * g.dth + d, &s, &c);
+            ri = A.rcol[i + NG] + (double)a1;
+        } else if constexpr (IS_DF) {
+            df d = two_sum(a2, -o2) * A.dth_df;
+            if (fabs_hi(d) <= 0.1f) {
+                sincos_shift_df(s0, c0, d, s, c);
+            } else {
+                df th = df(j) * A.dth_df + mul(A.dth_df, o2) + d;
+                sincos_t(th, &s, &c);
+            }
+            ri = df(rc2.x, rc2.y) + df(a1);
+        } else {
+            float d = (a2 - o2) * A.dthf;
+            if (fabsf(d) <= 0.05f)
+                sincos_shift<float>(s0, c0, d, s, c);
+            else
+                sincosf(((float)j + o2) * A.dthf + d, &s, &c);
+            ri = rcf + a1;
+        }
         KSGeo<M> mi;
-        ks_geo_sc<M>(am, (M)rci + (M)a1, s, c, mi);
+        ks_geo_sc<M>(am, ri, s, c, mi);
         geo_rhs_m<M, float>(mi, eps, b1, b2, u[2], ft);
         ft.xt *= idth;
         float n1 = d0 + h * (ft.xr + f0.xr), n2 = o2 + h * (ft.xt + f0.xt);
         float nb1 = u[0] + h * (ft.ur + f0.ur), nb2 = u[1] + h * (ft.ut + f0.ut);
         ap = h * (ft.xp + f0.xp);
         bool done = false;
-        if (A.tol > 0.0) {
+        if (A.use_tol) {
             // convergence test of the implicit iteration, in FP64: change of
             // the iterate relative to r_i, one theta cell and max(1, |u|)
             double t = A.tol;
@@ -249,7 +289,7 @@ __device__ __forceinline__ void push_one(const Push32Args &A, int i, int j, floa
         b2 = nb2;
         if (done) break;
     }
-    o1 = log1pf(a1 / rcf) / dx1f;  // back to the logical offset
+    o1 = log1pf(a1 / rcf) / A.dx1f;  // back to the logical offset
     o2 = a2;
     u[0] = b1;
     u[1] = b2;
@@ -301,10 +341,12 @@ __global__ void __launch_bounds__(256) push32_kernel(Push32Args A)
         int sp = tag & 3u;
         float dphi = 0.0f;
         // FP64 island: cells whose inner edge r_i lies below fp64_radius
-        if (i < A.i64)
+        if (i >= A.i64)
+            push_one<float>(A, i, j, n1, n2, u, sp, dphi);
+        else if (A.island_fp64)
             push_one<double>(A, i, j, n1, n2, u, sp, dphi);
         else
-            push_one<float>(A, i, j, n1, n2, u, sp, dphi);
+            push_one<df>(A, i, j, n1, n2, u, sp, dphi);
         // axis reflection in offset space (theta = 0 is o2 = 0 of row 0,
         // theta = pi is o2 = 1 of row nth-1)
         if (j == 0 && n2 < 0.0f) { n2 = -n2; u[1] = -u[1]; }
@@ -455,6 +497,16 @@ cudaError_t launch_push32(grpic_ctx *ctx, grpic_particles *p, grpic_fields *f, b
         A.massive[k] = ctx->prm.massive[k];
     }
     A.r64 = ctx->prm.fp64_radius;
+    A.island_fp64 = ctx->prm.island_arith == 1 ? 1 : 0;
+    A.use_tol = ctx->prm.push_tol > 0.0 ? 1 : 0;
+    A.af = (float)ctx->g.a;
+    A.dthf = (float)ctx->g.dth;
+    A.idthf = (float)(1.0 / ctx->g.dth);
+    A.dx1f = (float)ctx->g.dx1;
+    A.a_df = df_const(ctx->g.a);
+    A.dth_df = df_const(ctx->g.dth);
+    A.rcol2 = ctx->rcol2;
+    A.rowsc = ctx->rowsc;
     A.i64 = 0;
     if (A.r64 > 0.0)
         while (A.i64 < ctx->g.nr && ctx->g.r_in * std::exp(A.i64 * ctx->g.dx1) < A.r64) ++A.i64;

@@ -230,3 +230,36 @@ def test_fp32_convergence_tolerance(G):
     for k in ("x1", "x2", "u1", "u2", "u3"):
         a, b = out[0][k].astype(np.float64), out[1][k].astype(np.float64)
         assert np.max(np.abs(a - b)) <= 1e-5 * max(1.0, np.max(np.abs(a))), k
+
+
+def test_fp32_island_arithmetic(G):
+    """The near-horizon island evaluates the metric in double-FP32 pairs by
+    default and in native FP64 on request: both give the FP64 oracle's step to
+    FP32 accuracy for the particles inside 1.5 r_H."""
+    res = {}
+    for island in (0, 1):
+        oc, gc = cfg32(32, qw=(-0.01, 0.01, 0.01, 0.0))
+        gc.island_arith = island
+        ctx = G.Context(gc)
+        F = G.Fields(gc)
+        ctx.init_fields(F, O.WALD, 2.0)
+        D, B = O.init_fields(oc, O.WALD, 2.0)
+        P = make_particles(oc, 20000, seed=4, sigma=0.5)
+        th0, r0 = P.th.copy(), P.r.copy()
+        S = load32(G, gc, oc, P)
+        ctx.push(S, F)
+        assert ctx.sync() == 0
+        O.push_deposit(oc, P, D, B)
+        h = S.host()
+        sel = ((P.tag & O.DEAD) == 0) & (np.minimum(th0, math.pi - th0) > 0.05) & (r0 < 1.4 * RH)
+        x1g, x2g = logical_from_fp32(oc, h)
+        x1o = (np.log(P.r) - math.log(oc.r_in)) / oc.dx1
+        x2o = P.th / oc.dth
+        err = max(np.abs(x1g - x1o)[sel].max(), np.abs(x2g - x2o)[sel].max())
+        uerr = max(relerr(h[k][sel], ref[sel]) for k, ref in (("u1", P.u1), ("u2", P.u2), ("u3", P.u3)))
+        print(f"island_arith={island}: {sel.sum()} island particles, position error {err:.2e} cells, "
+              f"momentum error {uerr:.2e}")
+        assert sel.sum() > 1000
+        assert err < 2e-5 and uerr < 2e-5
+        res[island] = (x1g[sel], x2g[sel])
+    assert np.abs(res[0][0] - res[1][0]).max() < 2e-5 and np.abs(res[0][1] - res[1][1]).max() < 2e-5

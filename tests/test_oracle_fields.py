@@ -168,3 +168,31 @@ def test_boundary_conditions_after_update():
     for X in D + B:
         for g in range(c.ng):
             np.testing.assert_array_equal(X[:, g], X[:, c.ng])
+
+
+def test_damping_layer_leaves_the_interior_and_only_scales_the_outer_columns():
+    """The outer absorbing layer (a reading: the paper gives no profile) acts
+    only on the last damp_cells columns, once per step, as a factor in
+    [1 - d_max, 1] that does not increase outwards; elsewhere one update is
+    bit-identical to the undamped one."""
+    a = 0.9
+    out = {}
+    for damp in (0.0, 0.1):
+        c = O.make_cfg(32, 24, a, 0.9 * O.horizon(a), 20.0, damp_max=damp)
+        D, B = O.init_fields(c, O.WALD, 1.0)
+        rng = np.random.default_rng(4)
+        J = [rng.normal(size=O.field_shape(c)) * 0.01 for _ in range(3)]
+        O.field_update(c, D, B, J)
+        out[damp] = (c, D + B)
+    c, und = out[0.0]
+    _, dam = out[0.1]
+    first = c.nr - c.damp_cells
+    for k, (x, y) in enumerate(zip(dam, und)):
+        cols_in = slice(0, c.ng + first - 1)
+        assert np.array_equal(x[:, cols_in], y[:, cols_in]), k
+        ratio = np.divide(x[:, c.ng + first:c.ng + c.nr], y[:, c.ng + first:c.ng + c.nr],
+                          out=np.ones_like(x[:, c.ng + first:c.ng + c.nr]),
+                          where=np.abs(y[:, c.ng + first:c.ng + c.nr]) > 1e-12)
+        assert ratio.min() >= 1.0 - 0.1 - 1e-12 and ratio.max() <= 1.0 + 1e-12, k
+        prof = np.median(ratio, axis=0)
+        assert np.all(np.diff(prof) <= 1e-12), k
