@@ -210,12 +210,25 @@ def run_grpic(args, prec, rank, world, e2e_steps):
     live = S.live()
 
     # end to end through host buffers (pinned), copies inside the timed region
+    # the same steps replayed from the library's CUDA graph of two steps
+    ctx.step_graph(S, F, 2)  # capture
+    torch.cuda.synchronize()
+    g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    g0.record(stream)
+    ctx.step_graph(S, F, 2 * max(1, args.steps // 2))
+    g1.record(stream)
+    torch.cuda.synchronize()
+    graph_ms = g0.elapsed_time(g1) / (2 * max(1, args.steps // 2))
+    st = ctx.sync()
+    if st != 0:
+        raise RuntimeError(f"device status {st} in the graph replay")
+
     e2e = None
     if e2e_steps > 0:
         e2e = run_e2e(e2e_steps, ctx, S, F, cfg, stream)
 
     res = dict(total_ms=total_ms, push_ms=push_ms, field_ms=field_ms, n=n, live=live, cells=cfg.n_r * cfg.n_theta,
-               clocks=clk.summary(), e2e=e2e, cfg=cfg, prec=prec)
+               clocks=clk.summary(), e2e=e2e, cfg=cfg, prec=prec, graph_ms=graph_ms)
     del S, F, ctx
     torch.cuda.empty_cache()
     return res
@@ -548,6 +561,7 @@ def grpic_summary(res, args, world, esz_prec):
     return {"value": world * n * args.steps / (res["total_ms"] * 1e-3), "ms_per_step": ms,
             "push_deposit_per_s": world * n / (push_ms * 1e-3), "cell_updates_per_s": world * cells / (field_ms * 1e-3),
             "push_ms": push_ms, "field_ms": field_ms, "sort_ms": ms - push_ms - field_ms, "live_particles": res["live"],
+            "graph_ms_per_step": res["graph_ms"],
             "roofline": roof, "clocks": res["clocks"], "particles": n, "cells": cells,
             "dtype": "f64" if prec == 64 else "f32"}
 
@@ -620,12 +634,13 @@ def main():
                                  % (h["particles"] * (5 * esz + 4) / 1e9)},
                 "push_deposit_per_s": h["push_deposit_per_s"], "cell_updates_per_s": h["cell_updates_per_s"],
                 "push_ms": h["push_ms"], "field_ms": h["field_ms"], "sort_ms": h["sort_ms"],
-                "live_particles": h["live_particles"], "roofline": h["roofline"], "clocks": h["clocks"],
+                "live_particles": h["live_particles"], "graph_ms_per_step": h["graph_ms_per_step"],
+                "roofline": h["roofline"], "clocks": h["clocks"],
                 "gpu_launches": args.steps * (1 + 1 + cfg.n_field_iter + 7),
                 "e2e": res["e2e"]}
         if second is not None:
             s2 = grpic_summary(second, args, world, 64)
-            line["fp64_plain"] = {k: s2[k] for k in ("value", "ms_per_step", "push_deposit_per_s",
+            line["fp64_plain"] = {k: s2[k] for k in ("value", "ms_per_step", "graph_ms_per_step", "push_deposit_per_s",
                                                      "cell_updates_per_s", "push_ms", "field_ms", "sort_ms",
                                                      "live_particles", "roofline", "clocks", "dtype")}
             line["fp64_plain"]["unit"] = UNIT

@@ -182,6 +182,17 @@ grpic_status grpic_sort(grpic_ctx *ctx, grpic_particles *p, grpic_particles *scr
 grpic_status grpic_step(grpic_ctx *ctx, grpic_particles *p, grpic_particles *scratch, grpic_fields *f, int nsteps,
                         void *stream);
 
+/* The same steps as grpic_step (sort_every must be 1) replayed from a CUDA
+ * graph of two steps (push, field update, sort, twice), captured on the first
+ * call for these buffers and again whenever a buffer pointer or size changes.
+ * When *p is not the output of the last sort one eager step runs first, so
+ * that both captured sorts are neighbour sorts; an odd remainder also runs
+ * eagerly.  The capture runs on a private stream and synchronizes the device
+ * once; replays are enqueued on `stream`.  p and scratch are swapped as in
+ * grpic_step. */
+grpic_status grpic_step_graph(grpic_ctx *ctx, grpic_particles *p, grpic_particles *scratch, grpic_fields *f,
+                              int nsteps, void *stream);
+
 /* Diagnostics at vertices: rho = sum q w S / dV (cloud in cell) into rho[]
  * and the discrete div D of Eq. J-integral-eqn's integral form into divD[];
  * both (n_theta+1) x ld arrays of the field precision (device). */

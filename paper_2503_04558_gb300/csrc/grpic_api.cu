@@ -127,9 +127,14 @@ grpic_status sort_impl(grpic_ctx *ctx, grpic_particles *p, grpic_particles *q, c
         cudaError_t e = launch_keys(ctx, p, s);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "keys");
     }
-    cudaError_t e = launch_sort(ctx, p, q, s);
+    // the neighbour sort needs the particles to be the last sort's output
+    // with exactly one push since (the device re-checks the rest)
+    bool neighbour = p->n > 0 && p->tag && ctx->sorted_tag == p->tag && ctx->pushes_since_sort == 1 &&
+                     ctx->keys_valid && ctx->keys_tag == p->tag;
+    cudaError_t e = launch_sort_step(ctx, p, q, neighbour, s);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "sort");
     ctx->keys_valid = 0;
+    std::swap(ctx->d_offset, ctx->d_offset_prev);  // segments of the new order
     // the sorted state now lives in q's arrays: swap the array pointers
     std::swap(p->x1, q->x1);
     std::swap(p->x2, q->x2);
@@ -138,6 +143,8 @@ grpic_status sort_impl(grpic_ctx *ctx, grpic_particles *p, grpic_particles *q, c
     std::swap(p->u3, q->u3);
     std::swap(p->tag, q->tag);
     std::swap(p->cell, q->cell);
+    ctx->sorted_tag = p->tag;
+    ctx->pushes_since_sort = 0;
     return GRPIC_OK;
 }
 
@@ -154,6 +161,7 @@ grpic_status push_impl(grpic_ctx *ctx, grpic_particles *p, grpic_fields *f, bool
     if (e != cudaSuccess) return cuda_fail(ctx, e, "push");
     ctx->keys_valid = histogram ? 1 : 0;
     ctx->keys_tag = p->tag;
+    ctx->pushes_since_sort = (p->tag == ctx->sorted_tag) ? ctx->pushes_since_sort + 1 : 2;
     return GRPIC_OK;
 }
 
@@ -222,6 +230,10 @@ grpic_status grpic_init(grpic_metric metric, double spin, const grpic_grid *grid
     if (e == cudaSuccess) e = cudaMalloc(&ctx->d_cursor, sizeof(int32_t) * (ncell + 3));
     if (e == cudaSuccess) e = cudaMalloc(&ctx->d_blocksum, sizeof(int32_t) * 8192);
     if (e == cudaSuccess) e = cudaMalloc(&ctx->d_bigseg, sizeof(int32_t) * (ncell + 1));
+    if (e == cudaSuccess) e = cudaMalloc(&ctx->d_offset_prev, sizeof(int32_t) * (ncell + 3));
+    if (e == cudaSuccess) e = cudaMalloc(&ctx->d_cnt9, sizeof(int32_t) * 9 * ncell);
+    if (e == cudaSuccess) e = cudaMalloc(&ctx->d_base9, sizeof(int32_t) * 9 * ncell);
+    if (e == cudaSuccess) e = cudaMalloc(&ctx->d_sortflag, sizeof(int32_t));
     if (e == cudaSuccess) {
         e = cudaMalloc(&ctx->rcol, sizeof(double) * g.ld_tab);
         if (e == cudaSuccess) {
@@ -236,6 +248,7 @@ grpic_status grpic_init(grpic_metric metric, double spin, const grpic_grid *grid
         return GRPIC_ENOMEM;
     }
     cudaMemset(ctx->d_status, 0, 64);
+    cudaMemset(ctx->d_offset_prev, 0, sizeof(int32_t) * (ncell + 3));  // no segments before the first sort
     // q*w per species next to the status word (read by the diagnostics)
     cudaMemcpy((char *)ctx->d_status + 16, prm->q_weight, 4 * sizeof(double), cudaMemcpyHostToDevice);
     e = launch_tables(ctx, 0);
@@ -344,6 +357,72 @@ grpic_status grpic_step(grpic_ctx *ctx, grpic_particles *p, grpic_particles *scr
     return GRPIC_OK;
 }
 
+grpic_status grpic_step_graph(grpic_ctx *ctx, grpic_particles *p, grpic_particles *scratch, grpic_fields *f,
+                              int nsteps, void *stream)
+{
+    if (!ctx) return GRPIC_EINVAL;
+    if (nsteps < 0 || ctx->prm.sort_every != 1 || !particles_ok(ctx, p) || !fields_ok(ctx, f) ||
+        !particles_ok(ctx, scratch) || scratch->capacity < p->n)
+        return fail(ctx, GRPIC_EINVAL, "grpic_step_graph: bad arguments (sort_every must be 1)");
+    int done = 0;
+    grpic_status st = GRPIC_OK;
+    // start from a sort's output so that both captured sorts are neighbour sorts
+    if (nsteps > 0 && !(ctx->sorted_tag == p->tag && ctx->pushes_since_sort == 0)) {
+        st = grpic_step(ctx, p, scratch, f, 1, stream);
+        if (st) return st;
+        done = 1;
+    }
+    const int pairs = (nsteps - done) / 2;
+    if (pairs > 0) {
+        const void *key[24] = {p->x1, p->x2, p->u1, p->u2, p->u3, p->tag, p->cell, p->d_count,
+                               scratch->x1, scratch->x2, scratch->u1, scratch->u2, scratch->u3, scratch->tag,
+                               scratch->cell, f->D[0], f->D[1], f->D[2], f->B[0], f->B[1], f->B[2], f->J[0], f->J[1],
+                               f->J[2]};
+        bool same = ctx->graph_exec && memcmp(key, ctx->graph_key, sizeof key) == 0 &&
+                    ctx->keys_cap >= p->n && ctx->fscratch_ld == f->ld;
+        if (!same) {
+            if (ctx->graph_exec) cudaGraphExecDestroy(ctx->graph_exec);
+            ctx->graph_exec = nullptr;
+            cudaError_t e = cudaSuccess;
+            if (!ctx->cap_stream) e = cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking);
+            if (e != cudaSuccess) return cuda_fail(ctx, e, "graph stream");
+            // everything the two steps allocate, allocated before the capture
+            st = ensure_particle_scratch(ctx, p->n);
+            if (!st) st = ensure_field_scratch(ctx, f->ld);
+            if (st) return st;
+            cudaDeviceSynchronize();
+            const int64_t sc = ctx->step_count;
+            e = cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal);
+            if (e != cudaSuccess) return cuda_fail(ctx, e, "graph capture");
+            st = grpic_step(ctx, p, scratch, f, 2, ctx->cap_stream);
+            cudaGraph_t g = nullptr;
+            e = cudaStreamEndCapture(ctx->cap_stream, &g);
+            ctx->step_count = sc;
+            if (st || e != cudaSuccess) {
+                if (g) cudaGraphDestroy(g);
+                return st ? st : cuda_fail(ctx, e, "graph capture");
+            }
+            e = cudaGraphInstantiate(&ctx->graph_exec, g, 0);
+            cudaGraphDestroy(g);
+            if (e != cudaSuccess) {
+                ctx->graph_exec = nullptr;
+                return cuda_fail(ctx, e, "graph instantiate");
+            }
+            memcpy(ctx->graph_key, key, sizeof key);
+            // the capture left the host bookkeeping of two steps (pointers back
+            // in place, the last sort's output current): the same after a replay
+        }
+        for (int k = 0; k < pairs; ++k) {
+            cudaError_t e = cudaGraphLaunch(ctx->graph_exec, S(stream));
+            if (e != cudaSuccess) return cuda_fail(ctx, e, "graph launch");
+            ctx->step_count += 2;
+        }
+        done += 2 * pairs;
+    }
+    if (done < nsteps) st = grpic_step(ctx, p, scratch, f, nsteps - done, stream);
+    return st;
+}
+
 grpic_status grpic_diagnostics(grpic_ctx *ctx, const grpic_particles *p, const grpic_fields *f, void *rho, void *divD,
                                void *stream)
 {
@@ -393,7 +472,9 @@ const char *grpic_last_error(const grpic_ctx *ctx) { return ctx ? ctx->err : "nu
 void grpic_destroy(grpic_ctx *ctx)
 {
     if (!ctx) return;
-    void *ptrs[] = {ctx->rcol, ctx->rcol2, ctx->rowsc, ctx->tab, ctx->col1d, ctx->tab32, ctx->col1d32, ctx->fscratch, ctx->d_status, ctx->d_keys,
+    if (ctx->graph_exec) cudaGraphExecDestroy(ctx->graph_exec);
+    if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
+    void *ptrs[] = {ctx->d_offset_prev, ctx->d_cnt9, ctx->d_base9, ctx->d_sortflag, ctx->rcol, ctx->rcol2, ctx->rowsc, ctx->tab, ctx->col1d, ctx->tab32, ctx->col1d32, ctx->fscratch, ctx->d_status, ctx->d_keys,
                     ctx->d_count, ctx->d_offset, ctx->d_cursor, ctx->d_blocksum, ctx->d_perm, ctx->d_bigseg};
     for (void *q : ptrs)
         if (q) cudaFree(q);

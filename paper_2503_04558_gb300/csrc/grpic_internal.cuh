@@ -67,10 +67,20 @@ struct grpic_ctx {
     int32_t *d_blocksum;  // scan partials
     int32_t *d_perm;      // new slot -> old slot
     int32_t *d_bigseg;    // list of oversized segments
+    int32_t *d_offset_prev;  // segment offsets of the last sort's output (ncell+3)
+    int32_t *d_cnt9;      // per old cell, particles moving in each of 9 directions (9 x ncell)
+    int32_t *d_base9;     // per old cell and direction, the first destination slot (9 x ncell)
+    int32_t *d_sortflag;  // 0: neighbour sort applies, 1: general counting sort
+    const uint32_t *sorted_tag;  // tag array the last sort wrote
+    int64_t pushes_since_sort;
     int64_t perm_cap;
     int keys_valid;       // keys/histogram of the current order are valid
     const uint32_t *keys_tag;  // tag array of the particles those keys belong to
     int64_t step_count;
+    // CUDA graph of two steps (grpic_step_graph) and the buffers it was captured on
+    cudaStream_t cap_stream;
+    cudaGraphExec_t graph_exec;
+    const void *graph_key[24];
     char err[256];
 };
 
@@ -148,6 +158,8 @@ cudaError_t launch_field32(grpic_ctx *ctx, grpic_fields *f, cudaStream_t s);
 cudaError_t launch_keys(grpic_ctx *ctx, const grpic_particles *p, cudaStream_t s);
 cudaError_t sort_setup();
 cudaError_t launch_sort(grpic_ctx *ctx, grpic_particles *p, grpic_particles *scratch, cudaStream_t s);
+cudaError_t launch_sort_step(grpic_ctx *ctx, grpic_particles *p, grpic_particles *scratch, bool neighbour,
+                             cudaStream_t s);
 grpic_status ensure_field_scratch_ext(grpic_ctx *ctx, int64_t ld);
 grpic_status ensure_particle_scratch_ext(grpic_ctx *ctx, int64_t n);
 cudaError_t launch_diag(grpic_ctx *ctx, const grpic_particles *p, const grpic_fields *f, void *rho, void *divD,

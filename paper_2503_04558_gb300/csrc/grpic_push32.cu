@@ -19,6 +19,7 @@
 //     (at most n_push_iter correctors).
 #include "grpic_geo.cuh"
 #include "grpic_df.cuh"
+#include "grpic_window.cuh"
 
 #include <type_traits>
 
@@ -161,8 +162,6 @@ __device__ __forceinline__ float W1f(float d)
     return d < 1.0f ? 1.0f - d : 0.0f;
 }
 
-constexpr int NWIN = 40;
-
 // generalized Boris step in FP32 with the metric of type M at x^n (the lower
 // metric is rebuilt from the quantities the geodesic evaluation keeps)
 template <typename M>
@@ -296,7 +295,12 @@ __device__ __forceinline__ void push_one(const Push32Args &A, int i, int j, floa
     dphi = ap;
 }
 
-__global__ void __launch_bounds__(256) push32_kernel(Push32Args A)
+// resident 256-thread blocks per SM the register allocation is sized for
+#ifndef GRPIC_PUSH32_MINB
+#define GRPIC_PUSH32_MINB 2
+#endif
+
+__global__ void __launch_bounds__(256, GRPIC_PUSH32_MINB) push32_kernel(Push32Args A)
 {
     const GridDev &g = A.g;
     int64_t n = A.d_count ? *A.d_count : A.n;
@@ -425,7 +429,7 @@ __global__ void __launch_bounds__(256) push32_kernel(Push32Args A)
         A.keys[p] = key;
     }
 
-    // ---- deposit (warp-uniform start cell -> one reduced set of atomics) ----
+    // ---- deposit (warp-uniform start cell -> reduce-scatter over the lanes) --
     int wkey = dep ? (j * g.nr + i) : -1;
     unsigned act = __ballot_sync(FULL, dep);
     if (act) {
@@ -435,43 +439,18 @@ __global__ void __launch_bounds__(256) push32_kernel(Push32Args A)
         if (uniform) {
             int ri = __shfl_sync(FULL, i, src);
             int rj = __shfl_sync(FULL, j, src);
+            if (!dep) {
 #pragma unroll
-            for (int v = 0; v < NWIN; ++v) {
-                float x = dep ? win[v] : 0.0f;
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(FULL, x, o);
-                win[v] = x;
+                for (int v = 0; v < NWIN; ++v) win[v] = 0.0f;
             }
-            dep = (lane == 0);
-            i = ri;
-            j = rj;
-        }
-        if (dep) {
+            float tot[2];
+            int idx[2];
+            window_reduce_scatter<float>(win, lane, tot, idx);
+            window_add<float>(idx[0], tot[0], ri, rj, g.nth, NG, A.ld, A.J0, A.J1, A.J2);
+            window_add<float>(idx[1], tot[1], ri, rj, g.nth, NG, A.ld, A.J0, A.J1, A.J2);
+        } else if (dep) {
 #pragma unroll
-            for (int k = 0; k < 3; ++k)
-#pragma unroll
-                for (int l = 0; l < 4; ++l) {
-                    int row = j - 1 + l;
-                    float v = win[k * 4 + l];
-                    if (v != 0.0f && row >= 0 && row <= g.nth) atomicAdd(A.J0 + (size_t)row * A.ld + (i - 1 + k + NG), v);
-                }
-#pragma unroll
-            for (int k = 0; k < 4; ++k)
-#pragma unroll
-                for (int l = 0; l < 3; ++l) {
-                    int row = j - 1 + l;
-                    float v = win[12 + k * 3 + l];
-                    if (v != 0.0f && row >= 0 && row <= g.nth - 1)
-                        atomicAdd(A.J1 + (size_t)row * A.ld + (i - 1 + k + NG), v);
-                }
-#pragma unroll
-            for (int k = 0; k < 4; ++k)
-#pragma unroll
-                for (int l = 0; l < 4; ++l) {
-                    int row = j - 1 + l;
-                    float v = win[24 + k * 4 + l];
-                    if (v != 0.0f && row >= 0 && row <= g.nth) atomicAdd(A.J2 + (size_t)row * A.ld + (i - 1 + k + NG), v);
-                }
+            for (int v = 0; v < NWIN; ++v) window_add<float>(v, win[v], i, j, g.nth, NG, A.ld, A.J0, A.J1, A.J2);
         }
     }
 

@@ -16,11 +16,12 @@
 //      factor per dimension:  J^r A_r(k+1/2, l) = -qw/(2dt) P_r(k) (S1_t + S0_t)(l)
 //      with P_r(k) = sum_{k'<=k} (S1_r - S0_r)(k'), and likewise for theta.
 //      A warp whose particles all start in one cell (the usual case after the
-//      sort) reduces its 4x4-window contributions with shuffles and issues one
-//      set of FP64 atomics; otherwise each lane issues its own;
+//      sort) reduce-scatters its 4x4-window contributions over the lanes and
+//      each lane adds at most two totals; otherwise each lane adds its own;
 //   6. cell key of x^{n+1} (dead -> n_cells) and a warp-aggregated histogram
 //      for the sort.
 #include "grpic_internal.cuh"
+#include "grpic_window.cuh"
 
 namespace grpic {
 namespace {
@@ -182,8 +183,6 @@ __device__ __forceinline__ int jcell(const GridDev &g, double x2)
     return j > g.nth - 1 ? g.nth - 1 : j;
 }
 
-constexpr int NWIN = 40;  // 12 J^r A_r + 12 J^theta A_theta + 16 J^phi dV
-
 __global__ void __launch_bounds__(256) push64_kernel(Push64Args A)
 {
     const GridDev &g = A.g;
@@ -318,7 +317,10 @@ __global__ void __launch_bounds__(256) push64_kernel(Push64Args A)
                 u[0] = urt;
                 u[1] = utt;
                 if (rt < g.r_in || rt >= g.r_out) tag |= DEAD;
-                key = (tag & DEAD) ? ncell : (jcell(g, x2b) * g.nr + (int)floor(x1b));
+                // the column the next push will start from (it clamps x1 into [0, nr))
+                int ib = (int)floor(x1b);
+                ib = ib < 0 ? 0 : (ib > g.nr - 1 ? g.nr - 1 : ib);
+                key = (tag & DEAD) ? ncell : (jcell(g, x2b) * g.nr + ib);
             }
         }
     }
@@ -335,58 +337,28 @@ __global__ void __launch_bounds__(256) push64_kernel(Push64Args A)
         A.keys[p] = key;
     }
 
-    // ---- deposit: warp-uniform start cell -> shuffle reduction -------------
+    // ---- deposit: warp-uniform start cell -> reduce-scatter over the lanes ---
     int wkey = dep ? (j0 * g.nr + i0) : -1;
     unsigned act = __ballot_sync(FULL, dep);
     if (act) {
-        int ref = __shfl_sync(FULL, wkey, __ffs(act) - 1);
+        int src = __ffs(act) - 1;
+        int ref = __shfl_sync(FULL, wkey, src);
         bool uniform = __all_sync(FULL, !dep || wkey == ref);
         if (uniform) {
-            int ri0 = __shfl_sync(FULL, i0, __ffs(act) - 1);
-            int rj0 = __shfl_sync(FULL, j0, __ffs(act) - 1);
+            int ri0 = __shfl_sync(FULL, i0, src);
+            int rj0 = __shfl_sync(FULL, j0, src);
+            if (!dep) {
 #pragma unroll
-            for (int v = 0; v < NWIN; ++v) {
-                double x = dep ? win[v] : 0.0;
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(FULL, x, o);
-                win[v] = x;
+                for (int v = 0; v < NWIN; ++v) win[v] = 0.0;
             }
-            if (lane == 0) {
-                i0 = ri0;
-                j0 = rj0;
-                dep = true;
-            } else {
-                dep = false;
-            }
-        }
-        if (dep) {
+            double tot[2];
+            int idx[2];
+            window_reduce_scatter<double>(win, lane, tot, idx);
+            window_add<double>(idx[0], tot[0], ri0, rj0, g.nth, NG, A.ld, A.J0, A.J1, A.J2);
+            window_add<double>(idx[1], tot[1], ri0, rj0, g.nth, NG, A.ld, A.J0, A.J1, A.J2);
+        } else if (dep) {
 #pragma unroll
-            for (int k = 0; k < 3; ++k)
-#pragma unroll
-                for (int l = 0; l < 4; ++l) {
-                    int row = j0 - 1 + l;
-                    double v = win[k * 4 + l];
-                    if (v != 0.0 && row >= 0 && row <= g.nth)
-                        atomicAdd(A.J0 + (size_t)row * A.ld + (i0 - 1 + k + NG), v);
-                }
-#pragma unroll
-            for (int k = 0; k < 4; ++k)
-#pragma unroll
-                for (int l = 0; l < 3; ++l) {
-                    int row = j0 - 1 + l;
-                    double v = win[12 + k * 3 + l];
-                    if (v != 0.0 && row >= 0 && row <= g.nth - 1)
-                        atomicAdd(A.J1 + (size_t)row * A.ld + (i0 - 1 + k + NG), v);
-                }
-#pragma unroll
-            for (int k = 0; k < 4; ++k)
-#pragma unroll
-                for (int l = 0; l < 4; ++l) {
-                    int row = j0 - 1 + l;
-                    double v = win[24 + k * 4 + l];
-                    if (v != 0.0 && row >= 0 && row <= g.nth)
-                        atomicAdd(A.J2 + (size_t)row * A.ld + (i0 - 1 + k + NG), v);
-                }
+            for (int v = 0; v < NWIN; ++v) window_add<double>(v, win[v], i0, j0, g.nth, NG, A.ld, A.J0, A.J1, A.J2);
         }
     }
 

@@ -15,8 +15,25 @@
 //      i.e. stability;
 //   5. gather of every particle array through the index list into the second
 //      buffer; slots past the live count are marked dead.
+//
+// Neighbour sort (the step's sort when the particles are the output of the
+// previous sort and one push moved them): a particle of old cell s lands in
+// one of its 9 neighbours k = s + dj*n_r + di (di, dj in -1..1) or dies.  The
+// stable order of cell k is then its sources in increasing cell order, each
+// source's particles in slot order, so
+//   6. count, per old cell, the particles going in each direction;
+//   7. destination counts = sums over the 9 sources; exclusive scan;
+//   8. each particle goes straight to offset[k] + (particles of lower sources
+//      into k) + (its rank among its cell's particles in that direction),
+//      moving its data once, with no atomics and no fix-up.
+// The count pass checks the precondition (every key a neighbour of its
+// segment, live count = the previous sort's) and raises a device flag when
+// it fails; the general kernels then run instead.  Every kernel of both paths
+// reads the flag and strides over its work with a fixed grid, so the path
+// not taken costs one flag read per block.
 #include "grpic_internal.cuh"
 
+#include <algorithm>
 #include <climits>
 
 namespace grpic {
@@ -132,23 +149,31 @@ __global__ void keys_kernel(GridDev g, int64_t nmax, const int64_t *d_count, con
     if (key >= 0 && (threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(count + key, __popc(peers));
 }
 
+// general path kernels skip their work when flag is set and 0 (the neighbour
+// sort applied); flag == nullptr always runs
+__device__ __forceinline__ bool general_off(const int32_t *flag) { return flag && *flag == 0; }
+
 __global__ void scatter_kernel(int64_t nmax, const int64_t *d_count, const int32_t *keys, const int32_t *offset,
-                               int32_t *cursor, int32_t *perm, int ncell)
+                               int32_t *cursor, int32_t *perm, int ncell, const int32_t *flag)
 {
+    if (general_off(flag)) return;
     int64_t n = d_count ? *d_count : nmax;
     if (n > nmax) n = nmax;
-    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    int key = (p < n) ? keys[p] : -1;
-    if (key == ncell) key = -1;  // dead particles are dropped
-    unsigned peers = __match_any_sync(0xffffffffu, key);
-    int lane = threadIdx.x & 31;
-    int leader = __ffs(peers) - 1;
-    int base = 0;
-    if (key >= 0 && lane == leader) base = atomicAdd(cursor + key, __popc(peers));
-    base = __shfl_sync(0xffffffffu, base, leader);
-    if (key >= 0) {
-        int rank = __popc(peers & ((1u << lane) - 1u));
-        perm[offset[key] + base + rank] = (int32_t)p;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t end = (n + 31) & ~(int64_t)31;  // whole warps take part in the match
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < end; p += stride) {
+        int key = (p < n) ? keys[p] : -1;
+        if (key == ncell) key = -1;  // dead particles are dropped
+        unsigned peers = __match_any_sync(0xffffffffu, key);
+        int lane = threadIdx.x & 31;
+        int leader = __ffs(peers) - 1;
+        int base = 0;
+        if (key >= 0 && lane == leader) base = atomicAdd(cursor + key, __popc(peers));
+        base = __shfl_sync(0xffffffffu, base, leader);
+        if (key >= 0) {
+            int rank = __popc(peers & ((1u << lane) - 1u));
+            perm[offset[key] + base + rank] = (int32_t)p;
+        }
     }
 }
 
@@ -200,42 +225,45 @@ __device__ void smem_sort_warp(int *s, int m)
 }
 
 __global__ void __launch_bounds__(SEG_WARPS * 32) segfix_kernel(const int32_t *offset, int32_t *perm, int ncell,
-                                                                 int32_t *bigseg, int32_t *nbig, int32_t *status)
+                                                                 int32_t *bigseg, int32_t *nbig, const int32_t *flag)
 {
+    if (general_off(flag)) return;
     __shared__ int sh[SEG_WARPS][SEG_WARP_MAX];
     int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    int64_t cellk = (int64_t)blockIdx.x * SEG_WARPS + warp;
-    if (cellk >= ncell) return;
-    int start = offset[cellk];
-    int m = offset[cellk + 1] - start;
-    if (m <= 1) return;
-    int32_t *seg = perm + start;
-    // already in order?  (the usual case for cells nobody entered)
-    bool ok = true;
-    for (int i = lane; i + 1 < m; i += 32) ok &= seg[i] <= seg[i + 1];
-    if (__all_sync(0xffffffffu, ok)) return;
-    if (m <= 32) {
-        int v = lane < m ? seg[lane] : INT_MAX;
-        v = warp_sort32(v);
-        if (lane < m) seg[lane] = v;
-    } else if (m <= SEG_WARP_MAX) {
-        int *s = sh[warp];
-        for (int i = lane; i < m; i += 32) s[i] = seg[i];
-        __syncwarp();
-        smem_sort_warp(s, m);
-        for (int i = lane; i < m; i += 32) seg[i] = s[i];
-    } else if (lane == 0) {
-        int k = atomicAdd(nbig, 1);
-        bigseg[k] = (int32_t)cellk;
+    for (int64_t cellk = (int64_t)blockIdx.x * SEG_WARPS + warp; cellk < ncell;
+         cellk += (int64_t)gridDim.x * SEG_WARPS) {
+        int start = offset[cellk];
+        int m = offset[cellk + 1] - start;
+        if (m <= 1) continue;
+        int32_t *seg = perm + start;
+        // already in order?  (the usual case for cells nobody entered)
+        bool ok = true;
+        for (int i = lane; i + 1 < m; i += 32) ok &= seg[i] <= seg[i + 1];
+        if (__all_sync(0xffffffffu, ok)) continue;
+        if (m <= 32) {
+            int v = lane < m ? seg[lane] : INT_MAX;
+            v = warp_sort32(v);
+            if (lane < m) seg[lane] = v;
+        } else if (m <= SEG_WARP_MAX) {
+            int *s = sh[warp];
+            for (int i = lane; i < m; i += 32) s[i] = seg[i];
+            __syncwarp();
+            smem_sort_warp(s, m);
+            for (int i = lane; i < m; i += 32) seg[i] = s[i];
+            __syncwarp();
+        } else if (lane == 0) {
+            int k = atomicAdd(nbig, 1);
+            bigseg[k] = (int32_t)cellk;
+        }
     }
-    (void)status;
 }
 
 // one block per oversized segment: bitonic network in shared memory when it
 // fits, in global memory otherwise
 __global__ void __launch_bounds__(1024) bigseg_kernel(const int32_t *offset, int32_t *perm, const int32_t *bigseg,
-                                                      const int32_t *nbig)
+                                                      const int32_t *nbig, const int32_t *flag)
 {
+    if (general_off(flag)) return;
     extern __shared__ int sm[];
     for (int e = blockIdx.x; e < *nbig; e += gridDim.x) {
     int cellk = bigseg[e];
@@ -290,20 +318,201 @@ struct GatherArgs {
 };
 
 template <typename T>
-__global__ void gather_kernel(GatherArgs A, int nfields)
+__global__ void gather_kernel(GatherArgs A, int nfields, const int32_t *flag)
 {
-    int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (general_off(flag)) return;
     int64_t live = *A.live;
-    if (s == 0 && A.count_out) *A.count_out = live;
-    if (s >= A.nmax) return;
-    if (s < live) {
-        int32_t src = A.perm[s];
-        for (int k = 0; k < nfields; ++k) ((T *)A.dst[k])[s] = ((const T *)A.src[k])[src];
-        A.tag_dst[s] = A.tag_src[src];
-        if (A.cell_dst) A.cell_dst[s] = A.cell_src[src];
-    } else {
-        A.tag_dst[s] = DEAD;
+    int64_t s0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s0 == 0 && A.count_out) *A.count_out = live;
+    for (int64_t s = s0; s < A.nmax; s += (int64_t)gridDim.x * blockDim.x) {
+        if (s < live) {
+            int32_t src = A.perm[s];
+            for (int k = 0; k < nfields; ++k) ((T *)A.dst[k])[s] = ((const T *)A.src[k])[src];
+            A.tag_dst[s] = A.tag_src[src];
+            if (A.cell_dst) A.cell_dst[s] = A.cell_src[src];
+        } else {
+            A.tag_dst[s] = DEAD;
+        }
     }
+}
+
+// ---------------------------------------------------------------------------
+// neighbour sort
+// ---------------------------------------------------------------------------
+// direction d = (dj+1)*3 + (di+1); cnt9 is stored direction-major (d*ncell + s)
+
+// direction of key k from old cell s (column si): -1 if k is not one of the 9
+// neighbours.  |k - s| <= n_r + 1 for a neighbour, and with n_r >= 3 the row
+// step follows from the sign of k - s without a division.
+__device__ __forceinline__ int dir_of(int k, int s, int si, int nr)
+{
+    int delta = k - s;
+    int dj = (delta > 1) - (delta < -1);
+    int di = delta - dj * nr;
+    if (di < -1 || di > 1 || si + di < 0 || si + di >= nr) return -1;
+    return (dj + 1) * 3 + (di + 1);
+}
+
+// step 6: per old cell s (segment [off[s], off[s+1]) of the previous sort's
+// output), the particles moving in each direction; dead keys are dropped.
+// Raises *flag if a key is not a neighbour or the live count changed.
+__global__ void __launch_bounds__(256) count9_kernel(const int32_t *off, const int32_t *keys, int nr, int ncell,
+                                                     const int64_t *d_count, int64_t nmax, int32_t *cnt9,
+                                                     int32_t *flag)
+{
+    __shared__ int cnt_sh[8][16];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    int *cnt = cnt_sh[wib];
+    if (wid == 0 && lane == 0) {
+        int64_t n = d_count ? *d_count : nmax;
+        if (n != (int64_t)off[ncell] || n > nmax) atomicExch(flag, 1);
+    }
+    for (int64_t s = wid; s < ncell; s += nw) {
+        const int start = off[s], end = off[s + 1];
+        const int si = (int)(s % nr);
+        if (lane < 9) cnt[lane] = 0;
+        __syncwarp();
+        bool bad = false;
+        for (int b = start; b < end; b += 32) {
+            int p = b + lane;
+            int cls = -1;
+            if (p < end) {
+                int k = keys[p];
+                if (k >= 0 && k < ncell) {
+                    cls = dir_of(k, (int)s, si, nr);
+                    bad |= cls < 0;
+                } else {
+                    bad |= k != ncell;
+                }
+            }
+            unsigned peers = __match_any_sync(0xffffffffu, cls);
+            if (cls >= 0 && lane == __ffs(peers) - 1) cnt[cls] += __popc(peers);
+            __syncwarp();
+        }
+        if (lane < 9) cnt9[(int64_t)lane * ncell + s] = cnt[lane];
+        if (__any_sync(0xffffffffu, bad) && lane == 0) atomicExch(flag, 1);
+        __syncwarp();
+    }
+}
+
+__device__ __forceinline__ int dir_di(int d) { return d % 3 - 1; }
+__device__ __forceinline__ int dir_dj(int d) { return d / 3 - 1; }
+
+// particles of direction d' arriving in cell (ik, jk), 0 if the source cell
+// (ik - di', jk - dj') lies outside the grid
+__device__ __forceinline__ int arrivals(const int32_t *cnt9, int nr, int nth, int64_t ncell, int ik, int jk, int d)
+{
+    int is = ik - dir_di(d), js = jk - dir_dj(d);
+    if (is < 0 || is >= nr || js < 0 || js >= nth) return 0;
+    return cnt9[(int64_t)d * ncell + (int64_t)js * nr + is];
+}
+
+// step 7: destination counts into count[] (count[ncell] = 0: the dead are dropped)
+__global__ void dest_count_kernel(const int32_t *cnt9, int nr, int nth, int32_t *count, const int32_t *flag)
+{
+    if (*flag) return;
+    const int64_t ncell = (int64_t)nr * nth;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k <= ncell;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        int c = 0;
+        if (k < ncell) {
+            int ik = (int)(k % nr), jk = (int)(k / nr);
+#pragma unroll
+            for (int d = 0; d < 9; ++d) c += arrivals(cnt9, nr, nth, ncell, ik, jk, d);
+        }
+        count[k] = c;
+    }
+}
+
+// first destination slot of old cell s's direction-d particles:
+// offset[k] + arrivals into k from the sources below s in cell order (the
+// directions d' > d), k = s moved by d
+__global__ void base9_kernel(const int32_t *cnt9, int32_t *base9, const int32_t *off_new, int nr, int nth,
+                             const int32_t *flag)
+{
+    if (*flag) return;
+    const int64_t ncell = (int64_t)nr * nth;
+    for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < ncell; s += (int64_t)gridDim.x * blockDim.x) {
+        const int si = (int)(s % nr), sj = (int)(s / nr);
+        int base[9];
+#pragma unroll
+        for (int d = 0; d < 9; ++d) {
+            int ik = si + dir_di(d), jk = sj + dir_dj(d);
+            int v = 0;
+            if (ik >= 0 && ik < nr && jk >= 0 && jk < nth) {
+                v = off_new[(int64_t)jk * nr + ik];
+#pragma unroll
+                for (int d2 = d + 1; d2 < 9; ++d2) v += arrivals(cnt9, nr, nth, ncell, ik, jk, d2);
+            }
+            base[d] = v;
+        }
+#pragma unroll
+        for (int d = 0; d < 9; ++d) base9[(int64_t)d * ncell + s] = base[d];
+    }
+}
+
+struct NbrArgs {
+    int nr, nth;
+    int64_t nmax;
+    const int32_t *off_old, *off_new, *base9, *keys, *flag;
+    const void *src[5];
+    void *dst[5];
+    const uint32_t *tag_src;
+    uint32_t *tag_dst;
+    int32_t *cell_dst;  // FP32 form: the new cell key
+    int64_t *count_out;
+};
+
+// step 8: stable placement, one warp per old cell; the particle data moves once
+template <typename T>
+__global__ void __launch_bounds__(256) neighbour_scatter_kernel(NbrArgs A)
+{
+    if (*A.flag) return;
+    __shared__ int run_sh[8][16];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    int *run = run_sh[wib];
+    const int64_t ncell = (int64_t)A.nr * A.nth;
+    const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t s = wid; s < ncell; s += nw) {
+        const int start = A.off_old[s], end = A.off_old[s + 1];
+        if (start == end) continue;
+        const int si = (int)(s % A.nr);
+        if (lane < 9) run[lane] = A.base9[(int64_t)lane * ncell + s];
+        __syncwarp();
+        for (int b = start; b < end; b += 32) {
+            int p = b + lane;
+            int cls = -1, k = 0;
+            T v[5];
+            uint32_t tg = 0;
+            if (p < end) {
+                k = A.keys[p];
+#pragma unroll
+                for (int f = 0; f < 5; ++f) v[f] = ((const T *)A.src[f])[p];
+                tg = A.tag_src[p];
+                if (k >= 0 && k < ncell) cls = dir_of(k, (int)s, si, A.nr);
+            }
+            unsigned peers = __match_any_sync(0xffffffffu, cls);
+            int dst = 0;
+            if (cls >= 0) dst = run[cls] + __popc(peers & ((1u << lane) - 1u));
+            __syncwarp();
+            if (cls >= 0 && lane == __ffs(peers) - 1) run[cls] += __popc(peers);
+            __syncwarp();
+            if (cls >= 0) {
+#pragma unroll
+                for (int f = 0; f < 5; ++f) ((T *)A.dst[f])[dst] = v[f];
+                A.tag_dst[dst] = tg;
+                if (A.cell_dst) A.cell_dst[dst] = k;
+            }
+        }
+    }
+    // slots past the new live count are dead; the live count goes back to the set
+    const int64_t live = A.off_new[ncell];
+    const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t0 == 0 && A.count_out) *A.count_out = live;
+    for (int64_t q = live + t0; q < A.nmax; q += (int64_t)gridDim.x * blockDim.x) A.tag_dst[q] = DEAD;
 }
 
 }  // namespace
@@ -343,13 +552,14 @@ cudaError_t launch_sort(grpic_ctx *ctx, grpic_particles *p, grpic_particles *q, 
     if (p->n > 0) {
         unsigned blocks = (unsigned)((p->n + 255) / 256);
         scatter_kernel<<<blocks, 256, 0, s>>>(p->n, p->d_count, ctx->d_keys, ctx->d_offset, ctx->d_cursor, ctx->d_perm,
-                                              ncell);
+                                              ncell, nullptr);
     }
     segfix_kernel<<<(ncell + SEG_WARPS - 1) / SEG_WARPS, SEG_WARPS * 32, 0, s>>>(ctx->d_offset, ctx->d_perm, ncell,
-                                                                                 ctx->d_bigseg, nbig, ctx->d_status);
+                                                                                 ctx->d_bigseg, nbig, nullptr);
     // oversized segments (rare): the list length is only known on the device,
     // so a fixed grid strides over it and returns at once when it is empty
-    bigseg_kernel<<<64, 1024, SEG_BLOCK_MAX * sizeof(int), s>>>(ctx->d_offset, ctx->d_perm, ctx->d_bigseg, nbig);
+    bigseg_kernel<<<64, 1024, SEG_BLOCK_MAX * sizeof(int), s>>>(ctx->d_offset, ctx->d_perm, ctx->d_bigseg, nbig,
+                                                                nullptr);
     GatherArgs A;
     A.nmax = p->n;
     A.live = ctx->d_offset + ncell;
@@ -371,9 +581,101 @@ cudaError_t launch_sort(grpic_ctx *ctx, grpic_particles *p, grpic_particles *q, 
     if (p->n > 0) {
         unsigned blocks = (unsigned)((p->n + 255) / 256);
         if (ctx->prm.precision == 64)
-            gather_kernel<double><<<blocks, 256, 0, s>>>(A, nf);
+            gather_kernel<double><<<blocks, 256, 0, s>>>(A, nf, nullptr);
         else
-            gather_kernel<float><<<blocks, 256, 0, s>>>(A, nf);
+            gather_kernel<float><<<blocks, 256, 0, s>>>(A, nf, nullptr);
+    }
+    return cudaGetLastError();
+}
+
+// The step's sort.  neighbour: the host's view allows the neighbour sort (the
+// particles are the last sort's output and one push ran since); the device
+// confirms it in the count pass.  Offsets of the result are left in
+// ctx->d_offset (the previous ones are read from ctx->d_offset_prev).
+cudaError_t launch_sort_step(grpic_ctx *ctx, grpic_particles *p, grpic_particles *q, bool neighbour, cudaStream_t s)
+{
+    const int ncell = ctx->g.nr * ctx->g.nth;
+    const int64_t nscan = (int64_t)ncell + 1;
+    const int nb = (int)((nscan + SCAN_TILE - 1) / SCAN_TILE);
+    int dev_sms = 152;
+    cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, ctx->device);
+    const unsigned grid = (unsigned)dev_sms * 8;  // fixed grids, strided work
+    int32_t *flag = ctx->d_sortflag;
+    if (neighbour && ctx->g.nr >= 3) {
+        cudaMemsetAsync(flag, 0, sizeof(int32_t), s);
+        count9_kernel<<<grid, 256, 0, s>>>(ctx->d_offset_prev, ctx->d_keys, ctx->g.nr, ncell, p->d_count, p->n,
+                                           ctx->d_cnt9, flag);
+        dest_count_kernel<<<grid, 256, 0, s>>>(ctx->d_cnt9, ctx->g.nr, ctx->g.nth, ctx->d_count, flag);
+    } else {
+        cudaMemsetAsync(flag, 0xff, sizeof(int32_t), s);  // nonzero: general path
+    }
+    // d_count holds the destination counts (neighbour path) or the push's
+    // histogram (general path); one scan serves both
+    scan_tiles<<<nb, SCAN_T, 0, s>>>(ctx->d_count, ctx->d_offset, ctx->d_blocksum, nscan);
+    scan_sums<<<1, SCAN_T, 0, s>>>(ctx->d_blocksum, nb, ctx->d_offset + nscan);
+    add_back<<<(unsigned)((nscan + 255) / 256), 256, 0, s>>>(ctx->d_offset, ctx->d_blocksum, nscan);
+    if (neighbour && ctx->g.nr >= 3 && p->n > 0) {
+        base9_kernel<<<grid, 256, 0, s>>>(ctx->d_cnt9, ctx->d_base9, ctx->d_offset, ctx->g.nr, ctx->g.nth, flag);
+        NbrArgs A;
+        A.nr = ctx->g.nr;
+        A.nth = ctx->g.nth;
+        A.nmax = p->n;
+        A.off_old = ctx->d_offset_prev;
+        A.off_new = ctx->d_offset;
+        A.base9 = ctx->d_base9;
+        A.keys = ctx->d_keys;
+        A.flag = flag;
+        void *sp[5] = {p->x1, p->x2, p->u1, p->u2, p->u3};
+        void *dp[5] = {q->x1, q->x2, q->u1, q->u2, q->u3};
+        for (int k = 0; k < 5; ++k) {
+            A.src[k] = sp[k];
+            A.dst[k] = dp[k];
+        }
+        A.tag_src = p->tag;
+        A.tag_dst = q->tag;
+        A.cell_dst = (ctx->prm.precision == 32) ? q->cell : nullptr;
+        A.count_out = p->d_count;
+        if (ctx->prm.precision == 64)
+            neighbour_scatter_kernel<double><<<grid, 256, 0, s>>>(A);
+        else
+            neighbour_scatter_kernel<float><<<grid, 256, 0, s>>>(A);
+    }
+    // general path (skipped on the device when the neighbour sort applied)
+    cudaMemsetAsync(ctx->d_cursor, 0, sizeof(int32_t) * nscan, s);
+    int32_t *nbig = ctx->d_cursor + nscan;
+    cudaMemsetAsync(nbig, 0, sizeof(int32_t), s);
+    // general path grids: enough blocks for memory parallelism, few enough
+    // that skipping them costs little
+    const int64_t gmax = (int64_t)dev_sms * 64;
+    const unsigned gp = (unsigned)std::max<int64_t>(1, std::min<int64_t>((p->n + 255) / 256, gmax));
+    const unsigned gs = (unsigned)std::max<int64_t>(1, std::min<int64_t>((ncell + SEG_WARPS - 1) / SEG_WARPS, gmax));
+    if (p->n > 0)
+        scatter_kernel<<<gp, 256, 0, s>>>(p->n, p->d_count, ctx->d_keys, ctx->d_offset, ctx->d_cursor, ctx->d_perm,
+                                          ncell, flag);
+    segfix_kernel<<<gs, SEG_WARPS * 32, 0, s>>>(ctx->d_offset, ctx->d_perm, ncell, ctx->d_bigseg, nbig, flag);
+    bigseg_kernel<<<64, 1024, SEG_BLOCK_MAX * sizeof(int), s>>>(ctx->d_offset, ctx->d_perm, ctx->d_bigseg, nbig, flag);
+    GatherArgs G;
+    G.nmax = p->n;
+    G.live = ctx->d_offset + ncell;
+    G.perm = ctx->d_perm;
+    G.tag_src = p->tag;
+    G.tag_dst = q->tag;
+    G.count_out = p->d_count;
+    void *sp[5] = {p->x1, p->x2, p->u1, p->u2, p->u3};
+    void *dp[5] = {q->x1, q->x2, q->u1, q->u2, q->u3};
+    for (int k = 0; k < 5; ++k) {
+        G.src[k] = sp[k];
+        G.dst[k] = dp[k];
+    }
+    G.src[5] = nullptr;
+    G.dst[5] = nullptr;
+    G.cell_src = (ctx->prm.precision == 32) ? p->cell : nullptr;
+    G.cell_dst = (ctx->prm.precision == 32) ? q->cell : nullptr;
+    if (p->n > 0) {
+        if (ctx->prm.precision == 64)
+            gather_kernel<double><<<gp, 256, 0, s>>>(G, 5, flag);
+        else
+            gather_kernel<float><<<gp, 256, 0, s>>>(G, 5, flag);
     }
     return cudaGetLastError();
 }

@@ -23,7 +23,7 @@ NG = 2
 
 # names the header declares (checked by the CPU test of the boundary)
 EXPORTS = ["grpic_init", "grpic_init_fields", "grpic_push", "grpic_deposit", "grpic_field_update", "grpic_sort",
-           "grpic_step", "grpic_diagnostics", "grpic_get_areas", "grpic_sync", "grpic_last_error", "grpic_destroy",
+           "grpic_step", "grpic_step_graph", "grpic_diagnostics", "grpic_get_areas", "grpic_sync", "grpic_last_error", "grpic_destroy",
            "grpic_sort_noalloc"]
 NOALLOC_MAX_PARTICLES = 2097152
 NOALLOC_MAX_CELLS = 262144
@@ -71,6 +71,7 @@ def load(path: str = LIB_PATH):
         "grpic_field_update": [v, p(FieldsC), v],
         "grpic_sort": [v, p(ParticlesC), p(ParticlesC), v],
         "grpic_step": [v, p(ParticlesC), p(ParticlesC), p(FieldsC), i, v],
+        "grpic_step_graph": [v, p(ParticlesC), p(ParticlesC), p(FieldsC), i, v],
         "grpic_diagnostics": [v, p(ParticlesC), p(FieldsC), v, v, v],
         "grpic_get_areas": [v, v * 6, i64, v],
         "grpic_sync": [v, v],
@@ -332,6 +333,15 @@ class Context:
         fc = F.c()
         self._check(self.lib.grpic_step(self.h, C.byref(P._sc), C.byref(P._ss), C.byref(fc), nsteps,
                                         _stream(stream)), "grpic_step")
+        P.sync_ptrs()
+
+    def step_graph(self, P: ParticleSet, F: Fields, nsteps=1, stream=None):
+        """grpic_step replayed from a captured CUDA graph of two steps."""
+        P._sc.n = P.n
+        P._ss.n = P.n
+        fc = F.c()
+        self._check(self.lib.grpic_step_graph(self.h, C.byref(P._sc), C.byref(P._ss), C.byref(fc), nsteps,
+                                              _stream(stream)), "grpic_step_graph")
         P.sync_ptrs()
 
     def diagnostics(self, P: ParticleSet | None, F: Fields, stream=None):

@@ -124,6 +124,42 @@ def test_sort_is_bit_exact(G):
         assert np.array_equal(h[k], ref), k
 
 
+@pytest.mark.parametrize("extra", [0, 10])
+def test_step_sort_after_replacing_particles(G, extra):
+    """The step's sort moves particles straight to their place when they are
+    the previous sort's output moved by one push (neighbour sort).  Particles
+    replaced in the same buffers in between (same or different count) must make
+    the device fall back to the general counting sort: the result is still the
+    oracle's stable sort of the pushed particles."""
+    oc, gc = configs(24, 20, A09, 0.9 * RH, 20.0)
+    ctx, F = gpu_fields(G, gc, O.WALD, 1.0)
+    D, B = O.init_fields(oc, O.WALD, 1.0)
+    P = make_particles(oc, 6000, seed=12)
+    S = load_set(G, gc, P)
+    ctx.step(S, F, 1)
+    st, P1, J = O.step(oc, P, D, B)
+    assert st == 0 and ctx.sync() == 0
+    live = S.live()
+    assert live == P1.n
+    Q = make_particles(oc, 8000, seed=13)
+    rng = np.random.default_rng(3)
+    Q = Q.take(rng.permutation(Q.n)[:live + extra])
+    S.load(Q.r, Q.th, Q.u1, Q.u2, Q.u3, Q.tag)
+    ctx.push(S, F)
+    ctx.sort(S)
+    assert ctx.sync() == 0
+    st, J, _ = O.push_deposit(oc, Q, D, B)
+    Qs = O.sort(oc, Q)
+    h = S.host()
+    assert S.live() == Qs.n
+    assert np.array_equal(h["tag"], Qs.tag)
+    x1g, x2g = logical(oc, h["x1"], h["x2"])
+    x1o, x2o = logical(oc, Qs.r, Qs.th)
+    assert np.array_equal(np.floor(x2g) * oc.nr + np.floor(x1g), np.floor(x2o) * oc.nr + np.floor(x1o))
+    for k, ref in zip(("x1", "x2", "u1", "u2", "u3"), (Qs.r, Qs.th, Qs.u1, Qs.u2, Qs.u3)):
+        assert relerr(h[k], ref) < 1e-12, k
+
+
 def charge_residual(G, ctx, S, F, rho0_div0, oc):
     rho, div = ctx.diagnostics(S, F)
     res = host(div) - host(rho) - rho0_div0
@@ -333,3 +369,29 @@ def test_photons_follow_geodesics_without_deposit(G):
         assert relerr(h[k], ref) < 1e-12, k
     for k in range(3):
         assert np.all(host(F.J[k]) == 0)
+
+
+def test_step_graph_matches_eager_steps(G):
+    """grpic_step_graph (one eager step to reach a sorted state, then a CUDA
+    graph of two steps captured once and replayed) gives the eager steps'
+    state: same order, tags and values up to the deposit's atomic ordering."""
+    oc, gc = configs(48, 40, A09, 0.9 * RH, 20.0)
+    out = []
+    for graph in (False, True):
+        ctx, F = gpu_fields(G, gc, O.WALD, 1.0)
+        P = make_particles(oc, 30000, seed=21)
+        S = load_set(G, gc, P)
+        if graph:
+            ctx.step_graph(S, F, 7)
+            ctx.step_graph(S, F, 4)
+        else:
+            ctx.step(S, F, 11)
+        assert ctx.sync() == 0
+        out.append((S.host(), [host(t) for t in F.D + F.B], S.live()))
+    (h0, f0, n0), (h1, f1, n1) = out
+    assert n0 == n1
+    assert np.array_equal(h0["tag"], h1["tag"])
+    for k in ("x1", "x2", "u1", "u2", "u3"):
+        assert relerr(h1[k], h0[k]) < 1e-12, k
+    for a, b in zip(f1, f0):
+        assert relerr(a, b) < 1e-12
