@@ -98,9 +98,11 @@ typedef struct {
  * fp64_radius run in extended precision (<= 0: never), with the arithmetic
  * island_arith selects: 0 double-FP32 pairs (~48-bit significands on the
  * FP32 pipes, the default), 1 native FP64.  push_tol: in the FP32 form, the
- * geodesic corrector stops once the FP64-measured change of the iterate falls
- * below push_tol (<= 0: always n_push_iter correctors); the FP64 path always
- * runs n_push_iter. */
+ * geodesic corrector stops once the change of the iterate (relative to r_i,
+ * in theta cells, relative to max(1, |u|)) falls below push_tol (<= 0: always
+ * n_push_iter correctors).  The change is exact: two floats within a factor 2
+ * subtract exactly (Sterbenz's lemma), so the test takes the FP64 decision
+ * for converging iterates.  The FP64 path always runs n_push_iter. */
 typedef struct {
     double dt;
     double beta_field;
@@ -337,6 +339,13 @@ grpic_status grpic_batch1d_init_fields(grpic_batch1d_ctx *ctx, grpic_lines *line
  * appended particles and latches GRPIC_EOVERFLOW (read by
  * grpic_batch1d_sync). */
 grpic_status grpic_batch1d_run(grpic_batch1d_ctx *ctx, grpic_lines *lines, int nsteps, int64_t step0, void *stream);
+
+/* The same run as grpic_batch1d_run from a CUDA graph (the line-order
+ * kernel, then the persistent kernel), built on the first call for these
+ * line buffers and launch shape; later calls only update the persistent
+ * kernel's arguments (steps, first step, current buffer) in the graph. */
+grpic_status grpic_batch1d_run_graph(grpic_batch1d_ctx *ctx, grpic_lines *lines, int nsteps, int64_t step0,
+                                     void *stream);
 
 /* Autotuner: runs trial_steps real steps (starting at step0) with each
  * candidate (threads per block, blocks per SM), times them with CUDA events

@@ -12,10 +12,13 @@
 //            copies transposed into their source cells;
 //   * particles for every particle: the transpose of the deposit (derivatives of
 //            the piecewise-linear CIC weights), the axis reflection, the geodesic
-//            trapezoid by the implicit-function theorem at the converged iterate
-//            (I - dt/2 dF/dy)^T w = lambda (a 5x5 solve), the Boris step and the
-//            interpolation (scatter of lambda_E into lambda_F).  Local Jacobians
-//            come from forward-mode dual numbers through the same metric code.
+//            step (the predictor and correctors as run, transposed one by one,
+//            or the implicit-function theorem at the converged trapezoid,
+//            (I - dt/2 dF/dy)^T w = lambda, a 5x5 solve), the Boris step and the
+//            interpolation (scatter of lambda_E into lambda_F).  Vector-Jacobian
+//            products of the right-hand side are a hand-written reverse pass;
+//            the metric's derivatives and the other local Jacobians come from
+//            forward-mode dual numbers through the same metric code.
 // Recompute checkpoints every `checkpoint_every` steps bound the memory.
 #include "grpic_geo.cuh"
 
@@ -157,6 +160,81 @@ __device__ void rhs_jac(double a, double eps, const double y[5], double F[5], do
     for (int k = 0; k < 5; ++k) dFp[k] = f[2].d[k];
 }
 
+// w^T dF/dy + wp dX^ph/dy at y = (r, th, u_r, u_th, u_ph) for F = (X^r, X^th,
+// U_r, U_th, 0): the reverse pass of the right-hand side of Eq. particle-eom
+// written out by hand, with the metric quantities and their r and theta
+// derivatives from two-slot dual numbers (their second derivatives of the
+// metric come out of the same evaluation).
+__device__ void rhs_vjp(double a, double eps, const double y[5], const double w[5], double wp, double out[5])
+{
+    DN<2> r(y[0]), th(y[1]);
+    r.d[0] = 1.0;
+    th.d[1] = 1.0;
+    DN<2> s, c;
+    sincos_t(th, &s, &c);
+    KSGeo<DN<2>> m;
+    ks_geo_sc<DN<2>>(DN<2>(a), r, s, c, m);
+    const double ur = y[2], ut = y[3], up = y[4];
+    const double grr = m.grr.v, grp = m.grp.v, gtt = m.gtt.v, gpp = m.gpp.v, alpha = m.alpha.v;
+    // forward values
+    const double uu = grr * ur * ur + 2.0 * grp * ur * up + gtt * ut * ut + gpp * up * up;
+    const double au0 = sqrt(eps + uu);
+    const double iu0 = alpha / au0;
+    const double h = 0.5 * iu0;
+    const double Qr = ur * ur * m.dgrr_r.v + 2.0 * ur * up * m.dgrp_r.v + ut * ut * m.dgtt_r.v + up * up * m.dgpp_r.v;
+    const double Qt = ur * ur * m.dgrr_t.v + 2.0 * ur * up * m.dgrp_t.v + ut * ut * m.dgtt_t.v + up * up * m.dgpp_t.v;
+    const double Lxr = w[0], Lxt = w[1], Lur = w[2], Lut = w[3], Lxp = wp;
+    // U_r = -au0 da_r + ur db_r - h Qr,  U_th likewise
+    const double Lh = -Lur * Qr - Lut * Qt;
+    const double LQr = -Lur * h, LQt = -Lut * h;
+    double Lau0 = -Lur * m.da_r.v - Lut * m.da_t.v;
+    const double Lda_r = -Lur * au0, Lda_t = -Lut * au0, Ldb_r = Lur * ur, Ldb_t = Lut * ur;
+    double L_ur = Lur * m.db_r.v + Lut * m.db_t.v;
+    double L_ut = 0.0, L_up = 0.0;
+    L_ur += LQr * (2.0 * ur * m.dgrr_r.v + 2.0 * up * m.dgrp_r.v) + LQt * (2.0 * ur * m.dgrr_t.v + 2.0 * up * m.dgrp_t.v);
+    L_up += LQr * (2.0 * ur * m.dgrp_r.v + 2.0 * up * m.dgpp_r.v) + LQt * (2.0 * ur * m.dgrp_t.v + 2.0 * up * m.dgpp_t.v);
+    L_ut += LQr * (2.0 * ut * m.dgtt_r.v) + LQt * (2.0 * ut * m.dgtt_t.v);
+    const double Ldgrr_r = LQr * ur * ur, Ldgrp_r = LQr * 2.0 * ur * up, Ldgtt_r = LQr * ut * ut,
+                 Ldgpp_r = LQr * up * up;
+    const double Ldgrr_t = LQt * ur * ur, Ldgrp_t = LQt * 2.0 * ur * up, Ldgtt_t = LQt * ut * ut,
+                 Ldgpp_t = LQt * up * up;
+    // X^r = (grr ur + grp up) iu0 - beta, X^th = gtt ut iu0, X^ph = (grp ur + gpp up) iu0
+    double Liu0 = 0.5 * Lh + Lxr * (grr * ur + grp * up) + Lxt * gtt * ut + Lxp * (grp * ur + gpp * up);
+    const double Lbeta = -Lxr;
+    double Lgrr = Lxr * ur * iu0, Lgrp = (Lxr * up + Lxp * ur) * iu0, Lgtt = Lxt * ut * iu0, Lgpp = Lxp * up * iu0;
+    L_ur += (Lxr * grr + Lxp * grp) * iu0;
+    L_up += (Lxr * grp + Lxp * gpp) * iu0;
+    L_ut += Lxt * gtt * iu0;
+    // iu0 = alpha / au0, au0 = sqrt(eps + uu)
+    const double Lalpha = Liu0 / au0;
+    Lau0 -= Liu0 * alpha / (au0 * au0);
+    const double Luu = Lau0 / (2.0 * au0);
+    Lgrr += Luu * ur * ur;
+    Lgrp += Luu * 2.0 * ur * up;
+    Lgtt += Luu * ut * ut;
+    Lgpp += Luu * up * up;
+    L_ur += Luu * (2.0 * grr * ur + 2.0 * grp * up);
+    L_ut += Luu * 2.0 * gtt * ut;
+    L_up += Luu * (2.0 * grp * ur + 2.0 * gpp * up);
+    // metric quantities -> r, theta
+    const DN<2> *q[18] = {&m.grr, &m.grp, &m.gtt, &m.gpp, &m.alpha, &m.beta, &m.da_r, &m.da_t, &m.db_r,
+                          &m.db_t, &m.dgrr_r, &m.dgrr_t, &m.dgrp_r, &m.dgrp_t, &m.dgtt_r, &m.dgtt_t, &m.dgpp_r,
+                          &m.dgpp_t};
+    const double Lq[18] = {Lgrr, Lgrp, Lgtt, Lgpp, Lalpha, Lbeta, Lda_r, Lda_t, Ldb_r,
+                           Ldb_t, Ldgrr_r, Ldgrr_t, Ldgrp_r, Ldgrp_t, Ldgtt_r, Ldgtt_t, Ldgpp_r, Ldgpp_t};
+    double Lr = 0.0, Lth = 0.0;
+#pragma unroll
+    for (int k = 0; k < 18; ++k) {
+        Lr += Lq[k] * q[k]->d[0];
+        Lth += Lq[k] * q[k]->d[1];
+    }
+    out[0] = Lr;
+    out[1] = Lth;
+    out[2] = L_ur;
+    out[3] = L_ut;
+    out[4] = L_up;
+}
+
 // generalized Boris step (Eqs. boris-plus-minus, u0bar, boris-scheme) on
 // z = (r, th, u_r, u_th, u_ph, D^r, D^th, D^ph, B^r, B^th, B^ph) -> u'
 template <typename T>
@@ -194,6 +272,133 @@ __device__ __forceinline__ void boris_z(double a, double qm, double dt, const T 
     out[0] = um0 + sg * (x1 * s2b - x2 * s1) + h * Dl0;
     out[1] = um1 + sg * (x2 * s0 - x0 * s2b) + h * Dl1;
     out[2] = um2 + sg * (x0 * s1 - x1 * s0) + h * Dl2;
+}
+
+// lo^T d(u')/dz for the Boris step above, z = (r, th, u_r, u_th, u_ph, D^r,
+// D^th, D^ph, B^r, B^th, B^ph): its reverse pass written out by hand, the
+// metric's r and theta derivatives from two-slot dual numbers
+__device__ void boris_vjp(double a, double qm, double dt, const double z[11], const double lo[3], double out[11])
+{
+    DN<2> r(z[0]), th(z[1]);
+    r.d[0] = 1.0;
+    th.d[1] = 1.0;
+    DN<2> s, c;
+    sincos_t(th, &s, &c);
+    const DN<2> a2 = DN<2>(a * a), s2 = s * s;
+    const DN<2> rho2 = r * r + a2 * c * c;
+    const DN<2> ir = rcp_t(rho2);
+    const DN<2> zz = DN<2>(2.0) * r * ir;
+    const DN<2> opz = DN<2>(1.0) + zz;
+    const DN<2> alphaD = sqrt_t(rcp_t(opz));
+    const DN<2> Dl_ = r * r + a2 - DN<2>(2.0) * r;
+    const DN<2> Sg = (r * r + a2) * (r * r + a2) - a2 * Dl_ * s2;
+    // metric quantities q[] = g_rr, g_rp, g_tt, g_pp, i_rr, i_rp, i_tt, i_pp, sqrt(gamma), alpha
+    DN<2> q[10];
+    q[0] = opz;
+    q[1] = -DN<2>(a) * s2 * opz;
+    q[2] = rho2;
+    q[3] = Sg * s2 * ir;
+    q[4] = (a2 + r * r) * ir - zz * rcp_t(opz);
+    q[5] = DN<2>(a) * ir;
+    q[6] = ir;
+    q[7] = ir * rcp_t(s2);
+    q[8] = rho2 * s * sqrt_t(opz);
+    q[9] = alphaD;
+    const double grr = q[0].v, grp = q[1].v, gtt = q[2].v, gpp = q[3].v;
+    const double irr = q[4].v, irp = q[5].v, itt = q[6].v, ipp = q[7].v, sg = q[8].v, alpha = q[9].v;
+    const double u[3] = {z[2], z[3], z[4]}, D[3] = {z[5], z[6], z[7]}, B[3] = {z[8], z[9], z[10]};
+    const double c1 = 0.5 * qm * dt;
+    // forward values
+    const double Dl[3] = {grr * D[0] + grp * D[2], gtt * D[1], grp * D[0] + gpp * D[2]};
+    const double h = c1 * alpha;
+    const double um[3] = {u[0] + h * Dl[0], u[1] + h * Dl[1], u[2] + h * Dl[2]};
+    const double v[3] = {irr * um[0] + irp * um[2], itt * um[1], irp * um[0] + ipp * um[2]};
+    const double S = 1.0 + um[0] * v[0] + um[1] * v[1] + um[2] * v[2];
+    const double rS = sqrt(S);
+    const double u0b = rS / alpha;
+    const double kt = c1 / u0b;
+    const double t[3] = {kt * B[0], kt * B[1], kt * B[2]};
+    const double Gt[3] = {grr * t[0] + grp * t[2], gtt * t[1], grp * t[0] + gpp * t[2]};
+    const double tt = t[0] * Gt[0] + t[1] * Gt[1] + t[2] * Gt[2];
+    const double ks = 2.0 / (1.0 + tt);
+    const double sv[3] = {ks * t[0], ks * t[1], ks * t[2]};
+    const double vt[3] = {v[1] * t[2] - v[2] * t[1], v[2] * t[0] - v[0] * t[2], v[0] * t[1] - v[1] * t[0]};
+    const double w[3] = {um[0] + sg * vt[0], um[1] + sg * vt[1], um[2] + sg * vt[2]};
+    const double x[3] = {irr * w[0] + irp * w[2], itt * w[1], irp * w[0] + ipp * w[2]};
+    const double C[3] = {x[1] * sv[2] - x[2] * sv[1], x[2] * sv[0] - x[0] * sv[2], x[0] * sv[1] - x[1] * sv[0]};
+    // reverse: out_i = um_i + sg C_i + h Dl_i
+    double Lum[3] = {lo[0], lo[1], lo[2]};
+    double Lh = lo[0] * Dl[0] + lo[1] * Dl[1] + lo[2] * Dl[2];
+    double LDl[3] = {lo[0] * h, lo[1] * h, lo[2] * h};
+    double Lq[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+    Lq[8] += lo[0] * C[0] + lo[1] * C[1] + lo[2] * C[2];
+    const double LC[3] = {lo[0] * sg, lo[1] * sg, lo[2] * sg};
+    // C = x cross s
+    double Lx[3] = {sv[1] * LC[2] - sv[2] * LC[1], sv[2] * LC[0] - sv[0] * LC[2], sv[0] * LC[1] - sv[1] * LC[0]};
+    double Ls[3] = {LC[1] * x[2] - LC[2] * x[1], LC[2] * x[0] - LC[0] * x[2], LC[0] * x[1] - LC[1] * x[0]};
+    // x = Ginv w
+    double Lw[3] = {irr * Lx[0] + irp * Lx[2], itt * Lx[1], irp * Lx[0] + ipp * Lx[2]};
+    Lq[4] += Lx[0] * w[0];
+    Lq[5] += Lx[0] * w[2] + Lx[2] * w[0];
+    Lq[6] += Lx[1] * w[1];
+    Lq[7] += Lx[2] * w[2];
+    // w = um + sg (v cross t)
+    for (int i = 0; i < 3; ++i) Lum[i] += Lw[i];
+    Lq[8] += Lw[0] * vt[0] + Lw[1] * vt[1] + Lw[2] * vt[2];
+    const double LD_[3] = {Lw[0] * sg, Lw[1] * sg, Lw[2] * sg};
+    double Lv[3] = {t[1] * LD_[2] - t[2] * LD_[1], t[2] * LD_[0] - t[0] * LD_[2], t[0] * LD_[1] - t[1] * LD_[0]};
+    double Lt[3] = {LD_[1] * v[2] - LD_[2] * v[1], LD_[2] * v[0] - LD_[0] * v[2], LD_[0] * v[1] - LD_[1] * v[0]};
+    // s = ks t, ks = 2 / (1 + tt), tt = t^T G t
+    const double Lks = Ls[0] * t[0] + Ls[1] * t[1] + Ls[2] * t[2];
+    for (int i = 0; i < 3; ++i) Lt[i] += ks * Ls[i];
+    const double Ltt = -Lks * 2.0 / ((1.0 + tt) * (1.0 + tt));
+    for (int i = 0; i < 3; ++i) Lt[i] += 2.0 * Ltt * Gt[i];
+    Lq[0] += Ltt * t[0] * t[0];
+    Lq[1] += Ltt * 2.0 * t[0] * t[2];
+    Lq[2] += Ltt * t[1] * t[1];
+    Lq[3] += Ltt * t[2] * t[2];
+    // t = kt B, kt = c1 / u0b, u0b = sqrt(S) / alpha
+    const double Lkt = Lt[0] * B[0] + Lt[1] * B[1] + Lt[2] * B[2];
+    const double LB[3] = {kt * Lt[0], kt * Lt[1], kt * Lt[2]};
+    const double Lu0b = -Lkt * c1 / (u0b * u0b);
+    const double LS = Lu0b / (2.0 * rS * alpha);
+    Lq[9] -= Lu0b * rS / (alpha * alpha);
+    // S = 1 + um . v, v = Ginv um
+    for (int i = 0; i < 3; ++i) {
+        Lum[i] += LS * v[i];
+        Lv[i] += LS * um[i];
+    }
+    Lum[0] += irr * Lv[0] + irp * Lv[2];
+    Lum[1] += itt * Lv[1];
+    Lum[2] += irp * Lv[0] + ipp * Lv[2];
+    Lq[4] += Lv[0] * um[0];
+    Lq[5] += Lv[0] * um[2] + Lv[2] * um[0];
+    Lq[6] += Lv[1] * um[1];
+    Lq[7] += Lv[2] * um[2];
+    // um = u + h Dl, h = c1 alpha, Dl = G D
+    for (int i = 0; i < 3; ++i) {
+        Lh += Lum[i] * Dl[i];
+        LDl[i] += h * Lum[i];
+    }
+    Lq[9] += c1 * Lh;
+    const double LDv[3] = {grr * LDl[0] + grp * LDl[2], gtt * LDl[1], grp * LDl[0] + gpp * LDl[2]};
+    Lq[0] += LDl[0] * D[0];
+    Lq[1] += LDl[0] * D[2] + LDl[2] * D[0];
+    Lq[2] += LDl[1] * D[1];
+    Lq[3] += LDl[2] * D[2];
+    double Lr = 0.0, Lth = 0.0;
+#pragma unroll
+    for (int k = 0; k < 10; ++k) {
+        Lr += Lq[k] * q[k].d[0];
+        Lth += Lq[k] * q[k].d[1];
+    }
+    out[0] = Lr;
+    out[1] = Lth;
+    for (int i = 0; i < 3; ++i) {
+        out[2 + i] = Lum[i];
+        out[5 + i] = LDv[i];
+        out[8 + i] = LB[i];
+    }
 }
 
 // small dense solve M x = b (n = 5), Gaussian elimination with partial pivoting
@@ -339,7 +544,6 @@ __global__ void __launch_bounds__(128) particle_adjoint(PAdjArgs A)
     // forward recomputation with local derivatives
     St S[6];
     double E[6], dE1[6], dE2[6];
-    double JB[3][11];
     double up[3] = {u[0], u[1], u[2]};
     if (charged) {
         stencil(g, x1a, x2a, true, false, 1.0, S[0]);   // D^r
@@ -349,21 +553,21 @@ __global__ void __launch_bounds__(128) particle_adjoint(PAdjArgs A)
         stencil(g, x1a, x2a, true, false, 1.0, S[4]);   // B^th
         stencil(g, x1a, x2a, true, true, 1.0, S[5]);    // B^ph
         for (int c = 0; c < 6; ++c) gather_d(A.F[c], A.ld, S[c], E[c], dE1[c], dE2[c]);
-        DN<11> z[11], o[3];
         double zv[11] = {r, th, u[0], u[1], u[2], E[0], E[1], E[2], E[3], E[4], E[5]};
-        for (int k = 0; k < 11; ++k) {
-            z[k] = DN<11>(zv[k]);
-            z[k].d[k] = 1.0;
-        }
-        boris_z<DN<11>>(g.a, A.qm[sp], dt, z, o);
-        for (int i = 0; i < 3; ++i) {
-            up[i] = o[i].v;
-            for (int k = 0; k < 11; ++k) JB[i][k] = o[i].d[k];
-        }
+        boris_z<double>(g.a, A.qm[sp], dt, zv, up);
     }
     double y0[5] = {r, th, up[0], up[1], up[2]};
-    double F0[5], J0[5][5], Fp0, dFp0[5];
-    rhs_jac(g.a, eps, y0, F0, J0, Fp0, dFp0);
+    double F0[5], Fp0;
+    {
+        double f0[6];
+        rhs_y<double>(g.a, eps, y0, f0);
+        F0[0] = f0[0];
+        F0[1] = f0[1];
+        F0[2] = f0[3];
+        F0[3] = f0[4];
+        F0[4] = 0.0;
+        Fp0 = f0[2];
+    }
     // the predictor-corrector itself (as in the push)
     // predictor and correctors exactly as the push runs them; the iterates
     // at which the corrector right-hand sides are evaluated are kept
@@ -473,11 +677,10 @@ __global__ void __launch_bounds__(128) particle_adjoint(PAdjArgs A)
             for (int b = 0; b < 5; ++b) M[a][b] = (a == b ? 1.0 : 0.0) - hh * J1[b][a];  // transposed
         double w[5] = {l1[0], l1[1], l1[2], l1[3], l1[4]};
         solve5(M, w);
-        for (int k = 0; k < 5; ++k) {
-            double s = w[k];
-            for (int a = 0; a < 5; ++a) s += hh * J0[a][k] * w[a];
-            l0[k] = s + hh * ldphi * dFp0[k];
-        }
+        double hw[5], v0[5];
+        for (int k = 0; k < 5; ++k) hw[k] = hh * w[k];
+        rhs_vjp(g.a, eps, y0, hw, hh * ldphi, v0);
+        for (int k = 0; k < 5; ++k) l0[k] = w[k] + v0[k];
     } else {
         // transpose of the iteration the push runs: y~_0 = y0 + dt F(y0),
         // y~_{k+1} = y0 + dt/2 (F(y~_k) + F(y0)), dphi = dt/2 (X^ph(y~_{N-1}) + X^ph(y0))
@@ -493,14 +696,9 @@ __global__ void __launch_bounds__(128) particle_adjoint(PAdjArgs A)
                 }
                 double ap = (it == N - 1) ? hh * ldphi : 0.0;
                 lFp0 += ap;
-                double Fk[5], Jk[5][5], Fpk, dFpk[5];
-                rhs_jac(g.a, eps, yit[it], Fk, Jk, Fpk, dFpk);
-                double gn[5];
-                for (int b = 0; b < 5; ++b) {
-                    double s = ap * dFpk[b];
-                    for (int a = 0; a < 5; ++a) s += Jk[a][b] * hh * gk[a];
-                    gn[b] = s;
-                }
+                double hg[5], gn[5];
+                for (int k = 0; k < 5; ++k) hg[k] = hh * gk[k];
+                rhs_vjp(g.a, eps, yit[it], hg, ap, gn);
                 for (int k = 0; k < 5; ++k) gk[k] = gn[k];
             }
         }
@@ -508,11 +706,9 @@ __global__ void __launch_bounds__(128) particle_adjoint(PAdjArgs A)
             ly0[k] += gk[k];
             lF0[k] += dt * gk[k];
         }
-        for (int k = 0; k < 5; ++k) {
-            double s = ly0[k] + lFp0 * dFp0[k];
-            for (int a = 0; a < 5; ++a) s += J0[a][k] * lF0[a];
-            l0[k] = s;
-        }
+        double v0[5];
+        rhs_vjp(g.a, eps, y0, lF0, lFp0, v0);
+        for (int k = 0; k < 5; ++k) l0[k] = ly0[k] + v0[k];
     }
     // start point: deposit's start-weight derivatives
     l0[0] += lx1a / (r * g.dx1);
@@ -521,14 +717,14 @@ __global__ void __launch_bounds__(128) particle_adjoint(PAdjArgs A)
     out[0] = l0[0];
     out[1] = l0[1];
     if (charged) {
-        double lE[6] = {0, 0, 0, 0, 0, 0};
-        for (int i = 0; i < 3; ++i) {
-            double li = l0[2 + i];
-            out[0] += JB[i][0] * li;
-            out[1] += JB[i][1] * li;
-            for (int k = 0; k < 3; ++k) out[2 + k] += JB[i][2 + k] * li;
-            for (int c = 0; c < 6; ++c) lE[c] += JB[i][5 + c] * li;
-        }
+        double zv[11] = {r, th, u[0], u[1], u[2], E[0], E[1], E[2], E[3], E[4], E[5]};
+        double lb[11];
+        boris_vjp(g.a, A.qm[sp], dt, zv, l0 + 2, lb);
+        out[0] += lb[0];
+        out[1] += lb[1];
+        for (int k = 0; k < 3; ++k) out[2 + k] = lb[2 + k];
+        double lE[6];
+        for (int c = 0; c < 6; ++c) lE[c] = lb[5 + c];
         double lx1 = 0.0, lx2 = 0.0;
         for (int c = 0; c < 6; ++c) {
             scatter_w(A.lamF[c], A.ld, S[c], lE[c]);
@@ -1092,6 +1288,7 @@ extern "C" grpic_status grpic_adjoint_grad(grpic_ctx *ctx, const grpic_particles
         cudaMemcpyAsync(&hst, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost, s);
         cudaMemsetAsync(ctx->d_status, 0, sizeof(int), s);
         ctx->keys_valid = 0;
+        ctx->hist_valid = 0;
         cleanup();
         if (cudaGetLastError() != cudaSuccess && st == GRPIC_OK) st = GRPIC_ECUDA;
         if (st == GRPIC_OK && hst != 0) st = (grpic_status)hst;
@@ -1172,6 +1369,7 @@ extern "C" grpic_status grpic_adjoint_grad(grpic_ctx *ctx, const grpic_particles
     cudaMemcpyAsync(&hst, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost, s);
     cudaMemsetAsync(ctx->d_status, 0, sizeof(int), s);
     ctx->keys_valid = 0;
+    ctx->hist_valid = 0;
     cleanup();
     if (cudaGetLastError() != cudaSuccess && st == GRPIC_OK) st = GRPIC_ECUDA;
     if (st == GRPIC_OK && hst != 0) st = (grpic_status)hst;

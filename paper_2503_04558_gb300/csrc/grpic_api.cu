@@ -126,14 +126,23 @@ grpic_status sort_impl(grpic_ctx *ctx, grpic_particles *p, grpic_particles *q, c
         cudaMemsetAsync(ctx->d_count, 0, sizeof(int32_t) * (ncell + 1), s);
         cudaError_t e = launch_keys(ctx, p, s);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "keys");
+        ctx->keys_valid = 1;
+        ctx->hist_valid = 1;
+        ctx->keys_tag = p->tag;
     }
     // the neighbour sort needs the particles to be the last sort's output
     // with exactly one push since (the device re-checks the rest)
-    bool neighbour = p->n > 0 && p->tag && ctx->sorted_tag == p->tag && ctx->pushes_since_sort == 1 &&
-                     ctx->keys_valid && ctx->keys_tag == p->tag;
-    cudaError_t e = launch_sort_step(ctx, p, q, neighbour, s);
+    bool neighbour = p->n > 0 && p->tag && ctx->sorted_tag == p->tag && ctx->pushes_since_sort == 1;
+    if (!neighbour && !ctx->hist_valid) {
+        cudaMemsetAsync(ctx->d_count, 0, sizeof(int32_t) * (ncell + 1), s);
+        cudaError_t e = launch_hist(ctx, p, s);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "histogram");
+        ctx->hist_valid = 1;
+    }
+    cudaError_t e = launch_sort_step(ctx, p, q, neighbour, !ctx->hist_valid, s);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "sort");
     ctx->keys_valid = 0;
+    ctx->hist_valid = 0;
     std::swap(ctx->d_offset, ctx->d_offset_prev);  // segments of the new order
     // the sorted state now lives in q's arrays: swap the array pointers
     std::swap(p->x1, q->x1);
@@ -148,9 +157,13 @@ grpic_status sort_impl(grpic_ctx *ctx, grpic_particles *p, grpic_particles *q, c
     return GRPIC_OK;
 }
 
-grpic_status push_impl(grpic_ctx *ctx, grpic_particles *p, grpic_fields *f, bool histogram, cudaStream_t s)
+grpic_status push_impl(grpic_ctx *ctx, grpic_particles *p, grpic_fields *f, bool for_sort, cudaStream_t s)
 {
     int64_t ncell = (int64_t)ctx->g.nr * ctx->g.nth;
+    // the histogram serves the general sort only: a sort that will be a
+    // neighbour sort rebuilds it from the keys if the device falls back
+    const bool neighbour_next = p->n > 0 && p->tag && p->tag == ctx->sorted_tag && ctx->pushes_since_sort == 0;
+    const bool histogram = for_sort && !neighbour_next;
     grpic_status st = ensure_particle_scratch(ctx, p->n);
     if (st) return st;
     size_t bytes = (size_t)(ctx->g.nth + 1) * f->ld * fsize(ctx);
@@ -159,7 +172,8 @@ grpic_status push_impl(grpic_ctx *ctx, grpic_particles *p, grpic_fields *f, bool
     cudaError_t e = (ctx->prm.precision == 64) ? launch_push64(ctx, p, f, histogram, s)
                                                 : launch_push32(ctx, p, f, histogram, s);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "push");
-    ctx->keys_valid = histogram ? 1 : 0;
+    ctx->keys_valid = 1;  // the push writes every slot's key
+    ctx->hist_valid = histogram ? 1 : 0;
     ctx->keys_tag = p->tag;
     ctx->pushes_since_sort = (p->tag == ctx->sorted_tag) ? ctx->pushes_since_sort + 1 : 2;
     return GRPIC_OK;

@@ -455,6 +455,12 @@ struct grpic_batch1d_ctx {
     int64_t Cs;
     int block, per_sm, sms;
     size_t smem;
+    // CUDA graph of one run (line order + persistent kernel) and what it was built for
+    cudaGraph_t graph;
+    cudaGraphExec_t gexec;
+    cudaGraphNode_t g_b1;
+    const void *gkey[20];
+    int gshape[2];
 };
 
 using namespace grpic;
@@ -662,6 +668,63 @@ grpic_status grpic_batch1d_tune(grpic_batch1d_ctx *c, grpic_lines *L, int trial_
     return GRPIC_OK;
 }
 
+grpic_status grpic_batch1d_run_graph(grpic_batch1d_ctx *c, grpic_lines *L, int nsteps, int64_t step0, void *stream)
+{
+    if (!c || !lines_ok(L) || nsteps < 0) return GRPIC_EINVAL;
+    if (nsteps == 0) return GRPIC_OK;
+    const void *key[20] = {L->theta, L->I0, L->D, L->JA, L->count, L->events, L->cell[0], L->cell[1], L->off[0],
+                           L->off[1], L->ur[0], L->ur[1], L->up[0], L->up[1], L->tag[0], L->tag[1], L->id[0],
+                           L->id[1], nullptr, nullptr};
+    B1Args A = make_args(c, L, nsteps, step0);
+    cudaKernelNodeParams pb;
+    memset(&pb, 0, sizeof pb);
+    void *bargs[] = {&A};
+    pb.func = (void *)b1_kernel;
+    pb.gridDim = dim3((unsigned)(c->sms * c->per_sm));
+    pb.blockDim = dim3((unsigned)c->block);
+    pb.sharedMemBytes = (unsigned)c->smem;
+    pb.kernelParams = bargs;
+    cudaError_t e = cudaSuccess;
+    bool same = c->gexec && memcmp(key, c->gkey, sizeof key) == 0 && c->gshape[0] == c->block &&
+                c->gshape[1] == c->per_sm;
+    if (same) {
+        // only the run's arguments (steps, first step, current buffer) change
+        e = cudaGraphExecKernelNodeSetParams(c->gexec, c->g_b1, &pb);
+    } else {
+        if (c->gexec) cudaGraphExecDestroy(c->gexec);
+        if (c->graph) cudaGraphDestroy(c->graph);
+        c->gexec = nullptr;
+        c->graph = nullptr;
+        e = cudaGraphCreate(&c->graph, 0);
+        cudaGraphNode_t n_order = nullptr;
+        int32_t *cnt = L->count, *ord = c->order, *que = c->queue;
+        int nl = c->p.n_lines;
+        void *oargs[] = {&cnt, &nl, &ord, &que};
+        cudaKernelNodeParams po;
+        memset(&po, 0, sizeof po);
+        po.func = (void *)order_kernel;
+        po.gridDim = dim3(1);
+        po.blockDim = dim3(1024);
+        po.kernelParams = oargs;
+        if (e == cudaSuccess) e = cudaGraphAddKernelNode(&n_order, c->graph, nullptr, 0, &po);
+        if (e == cudaSuccess) e = cudaGraphAddKernelNode(&c->g_b1, c->graph, &n_order, 1, &pb);
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&c->gexec, c->graph, 0);
+        if (e != cudaSuccess) {
+            if (c->graph) cudaGraphDestroy(c->graph);
+            c->graph = nullptr;
+            c->gexec = nullptr;
+            return GRPIC_ECUDA;
+        }
+        memcpy(c->gkey, key, sizeof key);
+        c->gshape[0] = c->block;
+        c->gshape[1] = c->per_sm;
+    }
+    if (e == cudaSuccess) e = cudaGraphLaunch(c->gexec, (cudaStream_t)stream);
+    if (e != cudaSuccess) return GRPIC_ECUDA;
+    if (nsteps & 1) L->cur ^= 1;
+    return GRPIC_OK;
+}
+
 grpic_status grpic_batch1d_sync(grpic_batch1d_ctx *c, void *stream)
 {
     if (!c) return GRPIC_EINVAL;
@@ -675,6 +738,8 @@ grpic_status grpic_batch1d_sync(grpic_batch1d_ctx *c, void *stream)
 void grpic_batch1d_destroy(grpic_batch1d_ctx *c)
 {
     if (!c) return;
+    if (c->gexec) cudaGraphExecDestroy(c->gexec);
+    if (c->graph) cudaGraphDestroy(c->graph);
     void *ptrs[] = {c->rcol, c->Ar, c->order, c->queue, c->status, c->s_cell,
                     c->s_off, c->s_ur, c->s_up, c->s_tag, c->s_id};
     for (void *q : ptrs)

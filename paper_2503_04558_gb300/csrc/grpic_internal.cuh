@@ -74,7 +74,8 @@ struct grpic_ctx {
     const uint32_t *sorted_tag;  // tag array the last sort wrote
     int64_t pushes_since_sort;
     int64_t perm_cap;
-    int keys_valid;       // keys/histogram of the current order are valid
+    int keys_valid;       // keys of the current order are valid
+    int hist_valid;       // and so is their histogram (d_count)
     const uint32_t *keys_tag;  // tag array of the particles those keys belong to
     int64_t step_count;
     // CUDA graph of two steps (grpic_step_graph) and the buffers it was captured on
@@ -159,7 +160,8 @@ cudaError_t launch_keys(grpic_ctx *ctx, const grpic_particles *p, cudaStream_t s
 cudaError_t sort_setup();
 cudaError_t launch_sort(grpic_ctx *ctx, grpic_particles *p, grpic_particles *scratch, cudaStream_t s);
 cudaError_t launch_sort_step(grpic_ctx *ctx, grpic_particles *p, grpic_particles *scratch, bool neighbour,
-                             cudaStream_t s);
+                             bool hist_on_fallback, cudaStream_t s);
+cudaError_t launch_hist(grpic_ctx *ctx, const grpic_particles *p, cudaStream_t s);
 grpic_status ensure_field_scratch_ext(grpic_ctx *ctx, int64_t ld);
 grpic_status ensure_particle_scratch_ext(grpic_ctx *ctx, int64_t n);
 cudaError_t launch_diag(grpic_ctx *ctx, const grpic_particles *p, const grpic_fields *f, void *rho, void *divD,

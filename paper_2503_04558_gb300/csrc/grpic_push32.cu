@@ -15,8 +15,8 @@
 //     fp64_radius (the island near the horizon): double-FP32 pairs by
 //     default, native FP64 on request (island_arith), (ii) the corrector's
 //     convergence test: after each corrector the change of the iterate is
-//     measured in FP64 and the iteration stops once it is below the tolerance
-//     (at most n_push_iter correctors).
+//     measured (exactly, see below) and the iteration stops once it is below
+//     the tolerance (at most n_push_iter correctors).
 #include "grpic_geo.cuh"
 #include "grpic_df.cuh"
 #include "grpic_window.cuh"
@@ -30,13 +30,13 @@ struct Push32Args {
     GridDev g;
     float dt;
     int n_iter;
-    double tol;
+    float tolf;
     float qm[4], qw[4];
     int massive[4];
     double r64;
     int i64;  // first column whose inner edge is at or beyond fp64_radius
     int island_fp64;   // 1: native FP64 island, 0: double-FP32 pairs
-    int use_tol;       // FP64 convergence test of the correctors
+    int use_tol;       // convergence test of the correctors
     float af, dthf, idthf, dx1f;  // a, dtheta, 1/dtheta, dx1 in FP32
     df a_df, dth_df;              // a, dtheta as float pairs
     const float *rcol2;  // r_i as (hi, lo) float pairs, index i + NG
@@ -156,12 +156,6 @@ __device__ __forceinline__ float gather32(const float *__restrict__ F, int64_t l
     return S.p0 * (S.w00 * __ldg(a) + S.w10 * __ldg(a + 1)) + S.p1 * (S.w01 * __ldg(b) + S.w11 * __ldg(b + 1));
 }
 
-__device__ __forceinline__ float W1f(float d)
-{
-    d = fabsf(d);
-    return d < 1.0f ? 1.0f - d : 0.0f;
-}
-
 // generalized Boris step in FP32 with the metric of type M at x^n (the lower
 // metric is rebuilt from the quantities the geodesic evaluation keeps)
 template <typename M>
@@ -275,12 +269,15 @@ __device__ __forceinline__ void push_one(const Push32Args &A, int i, int j, floa
         ap = h * (ft.xp + f0.xp);
         bool done = false;
         if (A.use_tol) {
-            // convergence test of the implicit iteration, in FP64: change of
-            // the iterate relative to r_i, one theta cell and max(1, |u|)
-            double t = A.tol;
-            done = fabs((double)n1 - (double)a1) < t * (double)rcf && fabs((double)n2 - (double)a2) < t &&
-                   fabs((double)nb1 - (double)b1) < t * fmax(1.0, fabs((double)nb1)) &&
-                   fabs((double)nb2 - (double)b2) < t * fmax(1.0, fabs((double)nb2));
+            // convergence test of the implicit iteration: change of the
+            // iterate relative to r_i, one theta cell and max(1, |u|).  The
+            // difference of two floats within a factor 2 of each other is
+            // exact in FP32 (Sterbenz's lemma), so for converging iterates
+            // these differences are the FP64 ones; only the thresholds are
+            // rounded to FP32.
+            const float t = A.tolf;
+            done = fabsf(n1 - a1) < t * rcf && fabsf(n2 - a2) < t &&
+                   fabsf(nb1 - b1) < t * fmaxf(1.0f, fabsf(nb1)) && fabsf(nb2 - b2) < t * fmaxf(1.0f, fabsf(nb2));
         }
         a1 = n1;
         a2 = n2;
@@ -297,7 +294,7 @@ __device__ __forceinline__ void push_one(const Push32Args &A, int i, int j, floa
 
 // resident 256-thread blocks per SM the register allocation is sized for
 #ifndef GRPIC_PUSH32_MINB
-#define GRPIC_PUSH32_MINB 2
+#define GRPIC_PUSH32_MINB 4
 #endif
 
 __global__ void __launch_bounds__(256, GRPIC_PUSH32_MINB) push32_kernel(Push32Args A)
@@ -338,7 +335,7 @@ __global__ void __launch_bounds__(256, GRPIC_PUSH32_MINB) push32_kernel(Push32Ar
     }
 
     bool dep = false, moved = false;
-    float win[NWIN];
+    float wa1 = 0, wa2 = 0, wb1 = 0, wb2 = 0, wq = 0, wphi = 0;  // window inputs (kept for regrouping)
     int key = -1, ni = i, nj = j;
     float n1 = o1, n2 = o2;
     if (live) {
@@ -366,40 +363,14 @@ __global__ void __launch_bounds__(256, GRPIC_PUSH32_MINB) push32_kernel(Push32Ar
                 set_status(A.status, GRPIC_ERANGE);
                 tag |= DEAD;
             } else {
-                float x1b = n1, x2b = n2;  // end point relative to the start cell
-                // Esirkepov window relative to the start cell: columns i-1..i+2
-                int sp2 = sp;
-                float qw = A.qw[sp2];
-                float S0r[4], S1r[4], S0t[4], S1t[4];
-#pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    S0r[k] = W1f(o1 - (float)(k - 1));
-                    S1r[k] = W1f(x1b - (float)(k - 1));
-                    S0t[k] = W1f(o2 - (float)(k - 1));
-                    S1t[k] = W1f(x2b - (float)(k - 1));
-                }
-                float cr = -qw / (2.0f * A.dt);
-                float cp = qw * dphi / A.dt;
-                float Pr = 0.0f;
-#pragma unroll
-                for (int k = 0; k < 3; ++k) {
-                    Pr += S1r[k] - S0r[k];
-#pragma unroll
-                    for (int l = 0; l < 4; ++l) win[k * 4 + l] = cr * Pr * (S1t[l] + S0t[l]);
-                }
-                float Pt = 0.0f;
-#pragma unroll
-                for (int l = 0; l < 3; ++l) {
-                    Pt += S1t[l] - S0t[l];
-#pragma unroll
-                    for (int k = 0; k < 4; ++k) win[12 + k * 3 + l] = cr * (S1r[k] + S0r[k]) * Pt;
-                }
-#pragma unroll
-                for (int k = 0; k < 4; ++k)
-#pragma unroll
-                    for (int l = 0; l < 4; ++l)
-                        win[24 + k * 4 + l] = cp * (S1r[k] * S1t[l] * (1.0f / 3.0f) + S1r[k] * S0t[l] * (1.0f / 6.0f) +
-                                                    S0r[k] * S1t[l] * (1.0f / 6.0f) + S0r[k] * S0t[l] * (1.0f / 3.0f));
+                // inputs of the Esirkepov window (columns i-1..i+2, rows j-1..j+2);
+                // the end point (n1, n2) is relative to the start cell
+                wq = A.qw[sp];
+                wa1 = o1;
+                wa2 = o2;
+                wb1 = n1;
+                wb2 = n2;
+                wphi = dphi;
                 dep = true;
                 moved = true;
                 ni = i + di;
@@ -429,30 +400,9 @@ __global__ void __launch_bounds__(256, GRPIC_PUSH32_MINB) push32_kernel(Push32Ar
         A.keys[p] = key;
     }
 
-    // ---- deposit (warp-uniform start cell -> reduce-scatter over the lanes) --
-    int wkey = dep ? (j * g.nr + i) : -1;
-    unsigned act = __ballot_sync(FULL, dep);
-    if (act) {
-        int src = __ffs(act) - 1;
-        int ref = __shfl_sync(FULL, wkey, src);
-        bool uniform = __all_sync(FULL, !dep || wkey == ref);
-        if (uniform) {
-            int ri = __shfl_sync(FULL, i, src);
-            int rj = __shfl_sync(FULL, j, src);
-            if (!dep) {
-#pragma unroll
-                for (int v = 0; v < NWIN; ++v) win[v] = 0.0f;
-            }
-            float tot[2];
-            int idx[2];
-            window_reduce_scatter<float>(win, lane, tot, idx);
-            window_add<float>(idx[0], tot[0], ri, rj, g.nth, NG, A.ld, A.J0, A.J1, A.J2);
-            window_add<float>(idx[1], tot[1], ri, rj, g.nth, NG, A.ld, A.J0, A.J1, A.J2);
-        } else if (dep) {
-#pragma unroll
-            for (int v = 0; v < NWIN; ++v) window_add<float>(v, win[v], i, j, g.nth, NG, A.ld, A.J0, A.J1, A.J2);
-        }
-    }
+    // ---- deposit: lanes grouped by start cell, each group reduce-scattered --
+    deposit_warp<float, 3>(dep, i, j, g.nr, wa1, wa2, wb1, wb2, wq, wphi, A.dt, lane, g.nth, NG, A.ld, A.J0, A.J1,
+                        A.J2);
 
     if (A.histogram) {
         int hk = (p < n) ? key : -1;
@@ -469,7 +419,7 @@ cudaError_t launch_push32(grpic_ctx *ctx, grpic_particles *p, grpic_fields *f, b
     A.g = ctx->g;
     A.dt = (float)ctx->prm.dt;
     A.n_iter = ctx->prm.n_push_iter;
-    A.tol = ctx->prm.push_tol;
+    A.tolf = (float)ctx->prm.push_tol;
     for (int k = 0; k < 4; ++k) {
         A.qm[k] = (float)ctx->prm.q_over_m[k];
         A.qw[k] = (float)ctx->prm.q_weight[k];

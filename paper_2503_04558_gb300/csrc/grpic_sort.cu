@@ -134,10 +134,14 @@ __global__ void keys_kernel(GridDev g, int64_t nmax, const int64_t *d_count, con
         if (!(tag[p] & DEAD)) {
             if (FP64) {
                 double r = ((const double *)x1)[p], th = ((const double *)x2)[p];
-                int i = (int)floor((log(r) - g.ln_rin) / g.dx1);
-                int j = (int)floor(th / g.dth);
-                if (j > g.nth - 1) j = g.nth - 1;
-                if (i >= 0 && i < g.nr && j >= 0) key = j * g.nr + i;
+                if (r >= g.r_in && r < g.r_out && th >= 0.0 && th <= M_PI) {
+                    // the cell the push would start from (x1 clamped into [0, nr))
+                    int i = (int)floor((log(r) - g.ln_rin) / g.dx1);
+                    i = i < 0 ? 0 : (i > g.nr - 1 ? g.nr - 1 : i);
+                    int j = (int)floor(th / g.dth);
+                    if (j > g.nth - 1) j = g.nth - 1;
+                    key = j * g.nr + i;
+                }
             } else {
                 int c = cell[p];
                 if (c >= 0 && c < ncell) key = c;
@@ -336,6 +340,30 @@ __global__ void gather_kernel(GatherArgs A, int nfields, const int32_t *flag)
     }
 }
 
+// histogram of existing keys (dead key included), for the general path
+__global__ void hist_zero_kernel(int32_t *count, int64_t n, const int32_t *flag)
+{
+    if (general_off(flag)) return;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        count[i] = 0;
+}
+
+__global__ void hist_kernel(int64_t nmax, const int64_t *d_count, const int32_t *keys, int32_t *count, int ncell,
+                            const int32_t *flag)
+{
+    if (general_off(flag)) return;
+    int64_t n = d_count ? *d_count : nmax;
+    if (n > nmax) n = nmax;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t end = (n + 31) & ~(int64_t)31;
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < end; p += stride) {
+        int key = (p < n) ? keys[p] : -1;
+        if (key > ncell) key = -1;
+        unsigned peers = __match_any_sync(0xffffffffu, key);
+        if (key >= 0 && (threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(count + key, __popc(peers));
+    }
+}
+
 // ---------------------------------------------------------------------------
 // neighbour sort
 // ---------------------------------------------------------------------------
@@ -482,18 +510,37 @@ __global__ void __launch_bounds__(256) neighbour_scatter_kernel(NbrArgs A)
         const int si = (int)(s % A.nr);
         if (lane < 9) run[lane] = A.base9[(int64_t)lane * ncell + s];
         __syncwarp();
+        // software pipeline: the next 32 particles are loaded while the
+        // current ones are placed (two chunks of loads in flight per warp)
+        int kn = ncell;
+        T vn[5];
+        uint32_t tn = 0;
+        {
+            int p = start + lane;
+            if (p < end) {
+                kn = A.keys[p];
+#pragma unroll
+                for (int f = 0; f < 5; ++f) vn[f] = ((const T *)A.src[f])[p];
+                tn = A.tag_src[p];
+            }
+        }
         for (int b = start; b < end; b += 32) {
             int p = b + lane;
-            int cls = -1, k = 0;
+            int k = kn;
             T v[5];
-            uint32_t tg = 0;
-            if (p < end) {
-                k = A.keys[p];
 #pragma unroll
-                for (int f = 0; f < 5; ++f) v[f] = ((const T *)A.src[f])[p];
-                tg = A.tag_src[p];
-                if (k >= 0 && k < ncell) cls = dir_of(k, (int)s, si, A.nr);
+            for (int f = 0; f < 5; ++f) v[f] = vn[f];
+            uint32_t tg = tn;
+            int q = p + 32;
+            kn = ncell;
+            if (q < end) {
+                kn = A.keys[q];
+#pragma unroll
+                for (int f = 0; f < 5; ++f) vn[f] = ((const T *)A.src[f])[q];
+                tn = A.tag_src[q];
             }
+            int cls = -1;
+            if (p < end && k >= 0 && k < ncell) cls = dir_of(k, (int)s, si, A.nr);
             unsigned peers = __match_any_sync(0xffffffffu, cls);
             int dst = 0;
             if (cls >= 0) dst = run[cls] + __popc(peers & ((1u << lane) - 1u));
@@ -592,7 +639,18 @@ cudaError_t launch_sort(grpic_ctx *ctx, grpic_particles *p, grpic_particles *q, 
 // particles are the last sort's output and one push ran since); the device
 // confirms it in the count pass.  Offsets of the result are left in
 // ctx->d_offset (the previous ones are read from ctx->d_offset_prev).
-cudaError_t launch_sort_step(grpic_ctx *ctx, grpic_particles *p, grpic_particles *q, bool neighbour, cudaStream_t s)
+cudaError_t launch_hist(grpic_ctx *ctx, const grpic_particles *p, cudaStream_t s)
+{
+    if (p->n <= 0) return cudaSuccess;
+    int dev_sms = 152;
+    cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, ctx->device);
+    const unsigned g = (unsigned)std::max<int64_t>(1, std::min<int64_t>((p->n + 255) / 256, (int64_t)dev_sms * 64));
+    hist_kernel<<<g, 256, 0, s>>>(p->n, p->d_count, ctx->d_keys, ctx->d_count, ctx->g.nr * ctx->g.nth, nullptr);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sort_step(grpic_ctx *ctx, grpic_particles *p, grpic_particles *q, bool neighbour,
+                             bool hist_on_fallback, cudaStream_t s)
 {
     const int ncell = ctx->g.nr * ctx->g.nth;
     const int64_t nscan = (int64_t)ncell + 1;
@@ -606,6 +664,11 @@ cudaError_t launch_sort_step(grpic_ctx *ctx, grpic_particles *p, grpic_particles
         count9_kernel<<<grid, 256, 0, s>>>(ctx->d_offset_prev, ctx->d_keys, ctx->g.nr, ncell, p->d_count, p->n,
                                            ctx->d_cnt9, flag);
         dest_count_kernel<<<grid, 256, 0, s>>>(ctx->d_cnt9, ctx->g.nr, ctx->g.nth, ctx->d_count, flag);
+        if (hist_on_fallback) {
+            // the push skipped the histogram: rebuild it if the device fell back
+            hist_zero_kernel<<<grid, 256, 0, s>>>(ctx->d_count, nscan, flag);
+            hist_kernel<<<grid, 256, 0, s>>>(p->n, p->d_count, ctx->d_keys, ctx->d_count, ncell, flag);
+        }
     } else {
         cudaMemsetAsync(flag, 0xff, sizeof(int32_t), s);  // nonzero: general path
     }

@@ -103,4 +103,98 @@ __device__ __forceinline__ void window_add(int v, T val, int i0, int j0, int nth
     atomicAdd(dst + (size_t)row * ld + (i0 - 1 + k + ng), val);
 }
 
+// The 40 window values of one particle moving from (a1, a2) to (b1, b2), in
+// cell units relative to the lower corner of its start cell (a in [0, 1],
+// b in [-1, 2]); dphi its phi advance.  With CIC weights the prefix sums of
+// Eq. esirkepov-decomp factor per dimension:
+//   J^r A_r (k, l)     = -qw/(2dt) P_r(k) (S1_t + S0_t)(l),  P_r(k) = sum_{k'<=k} (S1_r - S0_r)(k')
+//   J^th A_th (k, l)   = -qw/(2dt) (S1_r + S0_r)(k) P_t(l)
+//   J^ph dV (k, l)     = qw dphi/dt (S1r S1t/3 + S1r S0t/6 + S0r S1t/6 + S0r S0t/3)(k, l)
+// (Eq. j-phi-deposit), k, l = 0..3 standing for columns/rows -1..2.
+template <typename T>
+__device__ __forceinline__ T cic_weight(T d)
+{
+    d = d < T(0) ? -d : d;
+    return d < T(1) ? T(1) - d : T(0);
+}
+
+template <typename T>
+__device__ __forceinline__ void esirkepov_window(T a1, T a2, T b1, T b2, T qw, T dphi, T dt, T win[NWIN])
+{
+    T S0r[4], S1r[4], S0t[4], S1t[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        S0r[k] = cic_weight<T>(a1 - T(k - 1));
+        S1r[k] = cic_weight<T>(b1 - T(k - 1));
+        S0t[k] = cic_weight<T>(a2 - T(k - 1));
+        S1t[k] = cic_weight<T>(b2 - T(k - 1));
+    }
+    const T cr = -qw / (T(2) * dt);
+    const T cp = qw * dphi / dt;
+    T Pr = T(0);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        Pr += S1r[k] - S0r[k];
+#pragma unroll
+        for (int l = 0; l < 4; ++l) win[k * 4 + l] = cr * Pr * (S1t[l] + S0t[l]);
+    }
+    T Pt = T(0);
+#pragma unroll
+    for (int l = 0; l < 3; ++l) {
+        Pt += S1t[l] - S0t[l];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) win[12 + k * 3 + l] = cr * (S1r[k] + S0r[k]) * Pt;
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+#pragma unroll
+        for (int l = 0; l < 4; ++l)
+            win[24 + k * 4 + l] = cp * (S1r[k] * S1t[l] * (T(1) / T(3)) + S1r[k] * S0t[l] * (T(1) / T(6)) +
+                                        S0r[k] * S1t[l] * (T(1) / T(6)) + S0r[k] * S0t[l] * (T(1) / T(3)));
+}
+
+// Deposit of a warp's windows: the lanes are grouped by start cell and each
+// group (up to MAXG of them; the usual warp after the sort has one or two)
+// builds its windows and reduce-scatters them in turn, so every lane
+// computes its window once and the 40 values live only here; lanes of the
+// remaining groups add their own entries.  All 32 lanes must call.  (The
+// FP64 push keeps its own deposit: on the FP64-bound kernel this grouping
+// measured slower than reducing only warps with a single start cell.)
+template <typename T, int MAXG>
+__device__ __forceinline__ void deposit_warp(bool dep, int i0, int j0, int nr, T a1, T a2, T b1, T b2, T qw, T dphi,
+                                             T dt, int lane, int nth, int ng, int64_t ld, T *J0, T *J1, T *J2)
+{
+    const unsigned FULL = 0xffffffffu;
+    const int wk = dep ? j0 * nr + i0 : -1;
+    bool pending = dep;
+#pragma unroll 1
+    for (int pass = 0; pass < MAXG; ++pass) {
+        const unsigned todo = __ballot_sync(FULL, pending);
+        if (!todo) return;
+        const int leader = __ffs(todo) - 1;
+        const int gk = __shfl_sync(FULL, wk, leader);
+        const int gi = __shfl_sync(FULL, i0, leader), gj = __shfl_sync(FULL, j0, leader);
+        const bool in = pending && wk == gk;
+        T win[NWIN];
+        if (in) {
+            esirkepov_window<T>(a1, a2, b1, b2, qw, dphi, dt, win);
+        } else {
+#pragma unroll
+            for (int v = 0; v < NWIN; ++v) win[v] = T(0);
+        }
+        T tot[2];
+        int idx[2];
+        window_reduce_scatter<T>(win, lane, tot, idx);
+        window_add<T>(idx[0], tot[0], gi, gj, nth, ng, ld, J0, J1, J2);
+        window_add<T>(idx[1], tot[1], gi, gj, nth, ng, ld, J0, J1, J2);
+        pending = pending && !in;
+    }
+    if (pending) {
+        T win[NWIN];
+        esirkepov_window<T>(a1, a2, b1, b2, qw, dphi, dt, win);
+#pragma unroll
+        for (int v = 0; v < NWIN; ++v) window_add<T>(v, win[v], i0, j0, nth, ng, ld, J0, J1, J2);
+    }
+}
+
 }  // namespace grpic

@@ -393,6 +393,7 @@ def _load_b1(lib):
     for name, args in {"grpic_batch1d_init": [p(Batch1DParams), p(v)],
                        "grpic_batch1d_init_fields": [v, p(LinesC), v],
                        "grpic_batch1d_run": [v, p(LinesC), C.c_int, C.c_int64, v],
+                       "grpic_batch1d_run_graph": [v, p(LinesC), C.c_int, C.c_int64, v],
                        "grpic_batch1d_tune": [v, p(LinesC), C.c_int, C.c_int64, p(C.c_int64), p(C.c_int32), v],
                        "grpic_batch1d_sync": [v, v]}.items():
         fn = getattr(lib, name)
@@ -402,7 +403,8 @@ def _load_b1(lib):
     lib.grpic_batch1d_destroy.restype = None
 
 
-EXPORTS += ["grpic_batch1d_init", "grpic_batch1d_init_fields", "grpic_batch1d_run", "grpic_batch1d_tune",
+EXPORTS += ["grpic_batch1d_init", "grpic_batch1d_init_fields", "grpic_batch1d_run", "grpic_batch1d_run_graph",
+            "grpic_batch1d_tune",
             "grpic_batch1d_sync", "grpic_batch1d_destroy"]
 
 
@@ -551,6 +553,11 @@ class Batch1D:
         st = self.lib.grpic_batch1d_run(self.h, C.byref(L._c), nsteps, step0, _stream(stream))
         if st != OK:
             raise GrpicError(st, "grpic_batch1d_run")
+
+    def run_graph(self, L: Lines, nsteps, step0, stream=None):
+        st = self.lib.grpic_batch1d_run_graph(self.h, C.byref(L._c), nsteps, step0, _stream(stream))
+        if st != OK:
+            raise GrpicError(st, "grpic_batch1d_run_graph")
 
     def tune(self, L: Lines, trial_steps, step0, stream=None):
         done = C.c_int64()

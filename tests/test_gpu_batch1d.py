@@ -157,3 +157,25 @@ def test_tuner_picks_a_launch_shape_and_advances(G):
     assert B.sync() == 0
     assert best[0] in (128, 256, 512, 1024) and best[1] in (1, 2, 4)
     assert done >= 2 and done % 2 == 0
+
+
+def test_graph_runs_match_direct_runs(G):
+    """grpic_batch1d_run_graph (graph built on the first call, the persistent
+    kernel's arguments updated on later ones) gives the lines of
+    grpic_batch1d_run bit for bit, emissions and conversions included."""
+    out = []
+    for graph in (False, True):
+        cfg, B, L, lines, thetas = setup(G, nl=6, seed=11)
+        run = B.run_graph if graph else B.run
+        run(L, 3, 0)
+        run(L, 2, 3)
+        run(L, 4, 5)
+        assert B.sync() == 0
+        out.append(([L.line(k) for k in range(6)], L.D.cpu().numpy().copy(), L.events.cpu().numpy().copy()))
+    (l0, d0, e0), (l1, d1, e1) = out
+    assert e0[0] > 0 and e0[1] > 0          # the runs emitted and converted photons
+    assert np.array_equal(e0, e1)
+    assert np.array_equal(d0.view(np.uint32), d1.view(np.uint32))
+    for a, b in zip(l0, l1):
+        for k in a:
+            assert np.array_equal(a[k], b[k]), k

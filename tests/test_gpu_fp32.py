@@ -1,5 +1,6 @@
-"""The FP32 form (int32 cell + FP32 offsets, FP32 fields and currents, FP64
-metric within 1.5 r_H and FP64 convergence test) against the FP64 oracle on
+"""The FP32 form (int32 cell + FP32 offsets, FP32 fields and currents,
+double-FP32 metric within 1.5 r_H, exact convergence test with tolerance
+1e-6 at most 3 correctors) against the FP64 oracle on
 the same seeded inputs.  Each test states the error it measures; the bar for
 fields is 1e-4 relative (max norm per array)."""
 import math
@@ -59,6 +60,7 @@ def host(t):
 def cfg32(n, **kw):
     oc, gc = configs(n, n, A09, 0.9 * RH, 50.0 if n >= 64 else 20.0, precision=32, **kw)
     gc.fp64_radius = 1.5 * RH
+    gc.push_tol = 1e-6      # the FP32 form as benchmarked: early exit from the correctors
     return oc, gc
 
 
@@ -213,8 +215,8 @@ def test_fp32_config1_charge_conservation(run20):
 
 
 def test_fp32_convergence_tolerance(G):
-    """With push_tol > 0 the FP64 convergence test stops the corrector early;
-    the result stays within FP32 precision of the fixed-count push."""
+    """With push_tol > 0 the convergence test stops the corrector early; the
+    result stays within FP32 precision of the fixed-count push."""
     oc, gc = cfg32(32)
     out = []
     for tol in (0.0, 1e-6):
