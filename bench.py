@@ -52,7 +52,7 @@ B0 = 1.0
 # Arithmetic per particle-step of the push kernels, counted by ncu on the same
 # kernels (flop_count = 2 FMA + MUL + ADD of the SASS instruction counters;
 # the capture commands and counts are in profiles/).
-PUSH64_FP64_FLOP = 1711.0   # profiles/push64_fp64_512x512_16ppc.md
+PUSH64_FP64_FLOP = 1734.0   # profiles/push64_fp64_512x512_64ppc.md
 PUSH32_FP32_FLOP = 1344.0   # profiles/push32_fp32form_1024x1024_64ppc.md
 # ALU peaks from unit counts x clock: 152 SMs x 2.07 GHz x (4 FP64 flops,
 # 256 FP32 flops) per SM per clock
@@ -478,7 +478,7 @@ def run_batch1d(args):
 ADJ_N, ADJ_A, ADJ_ROUT, ADJ_NP, ADJ_STEPS = 256, 0.9, 50.0, 2_000_000, 200
 
 
-def adjoint_measure(reps=2):
+def adjoint_measure(reps=2, n_particles=None, nsteps=None):
     """256^2, a = 0.9, r in [0.9 r_H, 50], Wald B0 = 1, 2e6 particles (sigma
     0.1), 200 FP64 steps; L = time-averaged horizon Poynting flux.  Times the
     objective alone and the objective with its gradient (forward with
@@ -489,12 +489,14 @@ def adjoint_measure(reps=2):
 
     build.build()
     G.load()
+    n_particles = n_particles or ADJ_NP
+    nsteps = nsteps or ADJ_STEPS
     rin = 0.9 * horizon(ADJ_A)
     cfg = G.Config(ADJ_N, ADJ_N, ADJ_A, rin, ADJ_ROUT)
     ctx = G.Context(cfg)
     F = G.Fields(cfg)
     ctx.init_fields(F, G.WALD, 1.0)
-    gen = synth.particles_torch(ADJ_N, ADJ_N, cfg.r_in, cfg.r_out, ADJ_NP, seed=5, sigma=0.1, device="cuda")
+    gen = synth.particles_torch(ADJ_N, ADJ_N, cfg.r_in, cfg.r_out, n_particles, seed=5, sigma=0.1, device="cuda")
     x = [gen[k].contiguous() for k in ("r", "th", "u1", "u2", "u3")]
     tag = gen["tag"]
     tag = (tag.to(torch.int64) if tag.dtype != torch.int32 else tag).to(torch.int32).contiguous()
@@ -507,7 +509,7 @@ def adjoint_measure(reps=2):
         torch.cuda.synchronize()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
-        L, gp, gf = G.adjoint_grad(ctx, x, tag, F.D, F.B, ADJ_STEPS, iH, want_grad=want)
+        L, gp, gf = G.adjoint_grad(ctx, x, tag, F.D, F.B, nsteps, iH, want_grad=want)
         b.record(stream)
         torch.cuda.synchronize()
         return a.elapsed_time(b), L
@@ -519,12 +521,12 @@ def adjoint_measure(reps=2):
         grad = [timed(True) for _ in range(reps)]
     f_ms = statistics.mean(t for t, _ in fwd)
     g_ms = statistics.mean(t for t, _ in grad)
-    out = {"value": ADJ_NP * ADJ_STEPS / (g_ms * 1e-3), "unit": "particle-steps/s (objective + gradient)",
+    out = {"value": n_particles * nsteps / (g_ms * 1e-3), "unit": "particle-steps/s (objective + gradient)",
            "forward_s": f_ms / 1e3, "gradient_s": g_ms / 1e3, "gradient_over_forward": g_ms / f_ms,
            "objective": grad[0][1], "dtype": "f64", "checkpoint_every": 20, "reps": reps,
-           "workload": "256x256, a=0.9, r in [0.9 r_H, 50], Wald B0=1, 2e6 e+/e- (sigma 0.1), 200 steps, "
+           "workload": "256x256, a=0.9, r in [0.9 r_H, 50], Wald B0=1, %.0e e+/e- (sigma 0.1), %d steps, "
                        "L = time-averaged horizon Poynting flux, gradient w.r.t. the initial particle state "
-                       "and fields", "l2": "state below L2: 256 MB written before each timed run",
+                       "and fields" % (n_particles, nsteps), "l2": "state below L2: 256 MB written before each timed run",
            "clocks": clk.summary()}
     del ctx, F, x, gen, flush
     torch.cuda.empty_cache()
@@ -532,7 +534,7 @@ def adjoint_measure(reps=2):
 
 
 def run_adjoint(args):
-    m = adjoint_measure(max(1, args.steps))
+    m = adjoint_measure(max(1, args.steps), args.adj_particles, args.adj_steps)
     line = {"metric": "differentiable form: particle-steps/s of objective + gradient (hand-written adjoint)",
             "value": m["value"], "unit": m["unit"], "n_gpus": 1, "steps": m["reps"], "warmup": 1,
             "ms_per_step": m["gradient_s"] * 1e3, "higher_is_better": True, "scaling": "weak",
@@ -544,6 +546,25 @@ def run_adjoint(args):
 
 
 # ---------------------------------------------------------------------------
+def max_over_ranks(x, world):
+    """The slowest rank's time (the job's time): all_reduce(MAX) over the
+    process group (on the device for NCCL, on the host for gloo)."""
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(particles_per_rank, steps, world, total_ms):
+    """Whole-job particle-steps/s: every rank pushes its own replica of the
+    workload (weak scaling), the job takes the slowest rank's time."""
+    return world * particles_per_rank * steps / (total_ms * 1e-3)
+
+
 def grpic_summary(res, args, world, esz_prec):
     """Per-form figures and the roofline of the push kernel."""
     n, cells = res["n"], res["cells"]
@@ -574,7 +595,7 @@ def grpic_summary(res, args, world, esz_prec):
                 "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS, "traffic": None,
                 "peak_source": "152 SMs x 2.07 GHz x 4 FP64 flop/clk/SM (recipe unit counts and clock)",
                 "flop_per_particle": PUSH64_FP64_FLOP, "hbm": hbm}
-    return {"value": world * n * args.steps / (res["total_ms"] * 1e-3), "ms_per_step": ms,
+    return {"value": job_value(n, args.steps, world, res["total_ms"]), "ms_per_step": ms,
             "push_deposit_per_s": world * n / (push_ms * 1e-3), "cell_updates_per_s": world * cells / (field_ms * 1e-3),
             "push_ms": push_ms, "field_ms": field_ms, "sort_ms": ms - push_ms - field_ms, "live_particles": res["live"],
             "graph_ms_per_step": res["graph_ms"], "particle_statuses": res["statuses"],
@@ -596,6 +617,8 @@ def main():
     ap.add_argument("--grid", type=int, default=NR, help="cells per dimension (profiling runs use smaller grids)")
     ap.add_argument("--ppc", type=int, default=PPC, help="particles per cell")
     ap.add_argument("--workload", default="grpic2d", choices=["grpic2d", "batch1d", "adjoint"])
+    ap.add_argument("--adj-particles", type=int, default=None, help="adjoint workload size (profiling runs)")
+    ap.add_argument("--adj-steps", type=int, default=None, help="adjoint steps (profiling runs)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
@@ -613,19 +636,11 @@ def main():
         torch.distributed.init_process_group("nccl")
     head_prec = 64 if args.precision == "64" else 32
     res = run_grpic(args, head_prec, rank, world, args.e2e_steps)
-    total_ms = res["total_ms"]
-    if world > 1:
-        t = torch.tensor([total_ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
-        res["total_ms"] = total_ms
+    res["total_ms"] = max_over_ranks(res["total_ms"], world)
     second = None
     if args.precision == "both":
         second = run_grpic(args, 64, rank, world, 0)
-        if world > 1:
-            t = torch.tensor([second["total_ms"]], device="cuda")
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            second["total_ms"] = float(t.item())
+        second["total_ms"] = max_over_ranks(second["total_ms"], world)
     extras = {}
     if not args.no_extras:
         for name, fn in (("adjoint", lambda: adjoint_measure(2)), ("batch1d", lambda: batch1d_measure(200, 600))):

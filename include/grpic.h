@@ -201,6 +201,19 @@ grpic_status grpic_step_graph(grpic_ctx *ctx, grpic_particles *p, grpic_particle
 grpic_status grpic_diagnostics(grpic_ctx *ctx, const grpic_particles *p, const grpic_fields *f, void *rho, void *divD,
                                void *stream);
 
+/* Running charge-conservation check of Sec. 3.4 (the FP32 form's FP64
+ * check): rho of the particles (cloud in cell, accumulated in FP64 whatever
+ * the precision) and div D (Eq. J-integral-eqn, formed in FP64 from the
+ * stored D) at the vertices; out[0] = max |div D - rho - base| and out[1] =
+ * max |rho| over the interior vertices (columns 1 .. n_r - damp_cells - 1, all
+ * rows: the guard copies and the damping layer change div D by design), as
+ * host doubles.  base: NULL or a device (n_theta+1) x ld FP64 array of an
+ * earlier call's div D - rho (so that out[0] measures the change since);
+ * state: NULL or such an array to receive this call's div D - rho.  p may be
+ * NULL (no particles).  Synchronizes `stream`. */
+grpic_status grpic_charge_check(grpic_ctx *ctx, const grpic_particles *p, const grpic_fields *f, const double *base,
+                                double *state, double out[2], void *stream);
+
 /* Copy the face areas of Eq. area-element (A^D_r, A^D_theta, A^D_phi = dV,
  * A^B_r, A^B_theta, A^B_phi) into six caller device arrays of
  * (n_theta+1) x ld doubles. */

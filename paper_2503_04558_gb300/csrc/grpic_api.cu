@@ -447,6 +447,31 @@ grpic_status grpic_diagnostics(grpic_ctx *ctx, const grpic_particles *p, const g
     return e == cudaSuccess ? GRPIC_OK : cuda_fail(ctx, e, "diagnostics");
 }
 
+grpic_status grpic_charge_check(grpic_ctx *ctx, const grpic_particles *p, const grpic_fields *f, const double *base,
+                                double *state, double out[2], void *stream)
+{
+    if (!ctx) return GRPIC_EINVAL;
+    if (!fields_ok(ctx, f) || !out || (p && !particles_ok(ctx, p)))
+        return fail(ctx, GRPIC_EINVAL, "grpic_charge_check: bad arguments");
+    const size_t n = (size_t)(ctx->g.nth + 1) * f->ld;
+    double *rho = nullptr, *divD = nullptr;
+    unsigned long long *dout = nullptr;
+    cudaError_t e = cudaMalloc(&rho, n * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&divD, n * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&dout, 2 * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = launch_charge_check(ctx, p, f, rho, divD, base, state, dout, S(stream));
+    unsigned long long h[2] = {0, 0};
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h, dout, sizeof h, cudaMemcpyDeviceToHost, S(stream));
+    if (e == cudaSuccess) e = cudaStreamSynchronize(S(stream));
+    cudaFree(rho);
+    cudaFree(divD);
+    cudaFree(dout);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "charge check");
+    memcpy(&out[0], &h[0], sizeof(double));
+    memcpy(&out[1], &h[1], sizeof(double));
+    return GRPIC_OK;
+}
+
 grpic_status grpic_get_areas(grpic_ctx *ctx, double *const out[6], int64_t ld, void *stream)
 {
     if (!ctx) return GRPIC_EINVAL;

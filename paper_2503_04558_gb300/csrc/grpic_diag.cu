@@ -29,9 +29,12 @@ __device__ __forceinline__ void logical(const GridDev &g, const void *x1, const 
     }
 }
 
-template <typename T>
+// T: the particle and field precision of the context; A: the type rho and
+// div D are accumulated and stored in (T for the diagnostics, double for the
+// charge check)
+template <typename T, typename A = T>
 __global__ void rho_particles(GridDev g, int64_t nmax, const int64_t *d_count, const void *x1, const void *x2,
-                              const int32_t *cell, const uint32_t *tag, const double *qw, T *rho, int64_t ld)
+                              const int32_t *cell, const uint32_t *tag, const double *qw, A *rho, int64_t ld)
 {
     int64_t n = d_count ? *d_count : nmax;
     if (n > nmax) n = nmax;
@@ -44,16 +47,16 @@ __global__ void rho_particles(GridDev g, int64_t nmax, const int64_t *d_count, c
     if (!(a >= -1.0 && a < g.nr + 1.0 && b >= 0.0 && b <= (double)g.nth)) return;  // outside the arrays
     int i = (int)floor(a), j = jcl(g, b);
     double f = a - i, h = b - j, q = qw[t & 3u];
-    T *r0 = rho + (size_t)j * ld + i + NG;
-    T *r1 = r0 + ld;
-    atomicAdd(r0, (T)(q * (1 - f) * (1 - h)));
-    atomicAdd(r0 + 1, (T)(q * f * (1 - h)));
-    atomicAdd(r1, (T)(q * (1 - f) * h));
-    atomicAdd(r1 + 1, (T)(q * f * h));
+    A *r0 = rho + (size_t)j * ld + i + NG;
+    A *r1 = r0 + ld;
+    atomicAdd(r0, (A)(q * (1 - f) * (1 - h)));
+    atomicAdd(r0 + 1, (A)(q * f * (1 - h)));
+    atomicAdd(r1, (A)(q * (1 - f) * h));
+    atomicAdd(r1 + 1, (A)(q * f * h));
 }
 
-template <typename T>
-__global__ void vertex_diag(GridDev g, const double *tab, size_t slab, const T *D0, const T *D1, T *rho, T *divD,
+template <typename T, typename A = T>
+__global__ void vertex_diag(GridDev g, const double *tab, size_t slab, const T *D0, const T *D1, A *rho, A *divD,
                             int64_t ld)
 {
     int col = blockIdx.x * blockDim.x + threadIdx.x;
@@ -61,15 +64,48 @@ __global__ void vertex_diag(GridDev g, const double *tab, size_t slab, const T *
     if (col >= g.ld_tab || j > g.nth) return;
     size_t q = (size_t)j * ld + col, qt = (size_t)j * g.ld_tab + col;
     double idv = tab[T_INV_ADP * slab + qt];
-    if (rho) rho[q] = (T)((double)rho[q] * idv);
+    if (rho) rho[q] = (A)((double)rho[q] * idv);
     if (col == 0) {
-        divD[q] = (T)0;
+        divD[q] = (A)0;
         return;
     }
     double flux = (double)D0[q] * tab[T_ADR * slab + qt] - (double)D0[q - 1] * tab[T_ADR * slab + qt - 1];
     if (j < g.nth) flux += (double)D1[q] * tab[T_ADT * slab + qt];
     if (j > 0) flux -= (double)D1[q - ld] * tab[T_ADT * slab + qt - g.ld_tab];
-    divD[q] = (T)(flux * idv);
+    divD[q] = (A)(flux * idv);
+}
+
+// max |div D - rho - base| and max |rho| over the interior vertices
+// (columns 1..imax, all rows) into out[0], out[1] as the bit patterns of
+// non-negative doubles (ordered like the integers); state = div D - rho
+__global__ void charge_check_kernel(int imax, int nth, const double *rho, const double *divD, const double *base,
+                                    double *state, int64_t ld, unsigned long long *out)
+{
+    __shared__ double sr[256], sq[256];
+    double mres = 0.0, mrho = 0.0;
+    const int64_t n = (int64_t)imax * (nth + 1);
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+        int i = 1 + (int)(e % imax), j = (int)(e / imax);
+        size_t q = (size_t)j * ld + i + NG;
+        double d = divD[q] - rho[q];
+        if (state) state[q] = d;
+        mres = fmax(mres, fabs(d - (base ? base[q] : 0.0)));
+        mrho = fmax(mrho, fabs(rho[q]));
+    }
+    sr[threadIdx.x] = mres;
+    sq[threadIdx.x] = mrho;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) {
+            sr[threadIdx.x] = fmax(sr[threadIdx.x], sr[threadIdx.x + o]);
+            sq[threadIdx.x] = fmax(sq[threadIdx.x], sq[threadIdx.x + o]);
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        atomicMax(out, (unsigned long long)__double_as_longlong(sr[0]));
+        atomicMax(out + 1, (unsigned long long)__double_as_longlong(sq[0]));
+    }
 }
 
 // deposit of given moves (FP64 state layout), same window algebra as the push
@@ -161,7 +197,35 @@ cudaError_t diag_t(grpic_ctx *ctx, const grpic_particles *p, const grpic_fields 
     return cudaGetLastError();
 }
 
+template <typename T>
+cudaError_t check_t(grpic_ctx *ctx, const grpic_particles *p, const grpic_fields *f, double *rho, double *divD,
+                    const double *base, double *state, unsigned long long *out, const double *d_qw, cudaStream_t s)
+{
+    size_t bytes = (size_t)(ctx->g.nth + 1) * f->ld * sizeof(double);
+    cudaMemsetAsync(rho, 0, bytes, s);
+    cudaMemsetAsync(out, 0, 2 * sizeof(unsigned long long), s);
+    if (p && p->n > 0)
+        rho_particles<T, double><<<(unsigned)((p->n + 255) / 256), 256, 0, s>>>(
+            ctx->g, p->n, p->d_count, p->x1, p->x2, p->cell, p->tag, d_qw, rho, f->ld);
+    dim3 blk(32, 4), grd((ctx->g.ld_tab + 31) / 32, (ctx->g.nth + 1 + 3) / 4);
+    vertex_diag<T, double><<<grd, blk, 0, s>>>(ctx->g, ctx->tab, ctx->slab, (const T *)f->D[0], (const T *)f->D[1],
+                                               rho, divD, f->ld);
+    int imax = ctx->g.nr - ctx->grid.damp_cells - 1;
+    if (imax > ctx->g.nr - 1) imax = ctx->g.nr - 1;
+    if (imax >= 1)
+        charge_check_kernel<<<256, 256, 0, s>>>(imax, ctx->g.nth, rho, divD, base, state, f->ld, out);
+    return cudaGetLastError();
+}
+
 }  // namespace
+
+cudaError_t launch_charge_check(grpic_ctx *ctx, const grpic_particles *p, const grpic_fields *f, double *rho,
+                                double *divD, const double *base, double *state, unsigned long long *out, cudaStream_t s)
+{
+    const double *d_qw = (const double *)(ctx->d_status + 4);
+    if (ctx->prm.precision == 64) return check_t<double>(ctx, p, f, rho, divD, base, state, out, d_qw, s);
+    return check_t<float>(ctx, p, f, rho, divD, base, state, out, d_qw, s);
+}
 
 // q*w per species lives in a tiny device array owned by the context's scratch
 cudaError_t launch_diag(grpic_ctx *ctx, const grpic_particles *p, const grpic_fields *f, void *rho, void *divD,

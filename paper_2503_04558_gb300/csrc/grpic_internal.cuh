@@ -166,4 +166,7 @@ grpic_status ensure_field_scratch_ext(grpic_ctx *ctx, int64_t ld);
 grpic_status ensure_particle_scratch_ext(grpic_ctx *ctx, int64_t n);
 cudaError_t launch_diag(grpic_ctx *ctx, const grpic_particles *p, const grpic_fields *f, void *rho, void *divD,
                         cudaStream_t s);
+cudaError_t launch_charge_check(grpic_ctx *ctx, const grpic_particles *p, const grpic_fields *f, double *rho,
+                                double *divD, const double *base, double *state, unsigned long long *out,
+                                cudaStream_t s);
 }  // namespace grpic

@@ -504,11 +504,24 @@ __global__ void __launch_bounds__(256) neighbour_scatter_kernel(NbrArgs A)
     const int64_t ncell = (int64_t)A.nr * A.nth;
     const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    // the next cell's segment bounds and first slots are fetched one cell ahead
+    int nstart = 0, nend = 0, nbase = 0;
+    if (wid < ncell) {
+        nstart = A.off_old[wid];
+        nend = A.off_old[wid + 1];
+        if (lane < 9) nbase = A.base9[(int64_t)lane * ncell + wid];
+    }
     for (int64_t s = wid; s < ncell; s += nw) {
-        const int start = A.off_old[s], end = A.off_old[s + 1];
+        const int start = nstart, end = nend, base = nbase;
+        const int64_t sn = s + nw;
+        if (sn < ncell) {
+            nstart = A.off_old[sn];
+            nend = A.off_old[sn + 1];
+            if (lane < 9) nbase = A.base9[(int64_t)lane * ncell + sn];
+        }
         if (start == end) continue;
         const int si = (int)(s % A.nr);
-        if (lane < 9) run[lane] = A.base9[(int64_t)lane * ncell + s];
+        if (lane < 9) run[lane] = base;
         __syncwarp();
         // software pipeline: the next 32 particles are loaded while the
         // current ones are placed (two chunks of loads in flight per warp)

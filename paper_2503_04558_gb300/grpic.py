@@ -23,7 +23,7 @@ NG = 2
 
 # names the header declares (checked by the CPU test of the boundary)
 EXPORTS = ["grpic_init", "grpic_init_fields", "grpic_push", "grpic_deposit", "grpic_field_update", "grpic_sort",
-           "grpic_step", "grpic_step_graph", "grpic_diagnostics", "grpic_get_areas", "grpic_sync", "grpic_last_error", "grpic_destroy",
+           "grpic_step", "grpic_step_graph", "grpic_diagnostics", "grpic_charge_check", "grpic_get_areas", "grpic_sync", "grpic_last_error", "grpic_destroy",
            "grpic_sort_noalloc"]
 NOALLOC_MAX_PARTICLES = 2097152
 NOALLOC_MAX_CELLS = 262144
@@ -73,6 +73,7 @@ def load(path: str = LIB_PATH):
         "grpic_step": [v, p(ParticlesC), p(ParticlesC), p(FieldsC), i, v],
         "grpic_step_graph": [v, p(ParticlesC), p(ParticlesC), p(FieldsC), i, v],
         "grpic_diagnostics": [v, p(ParticlesC), p(FieldsC), v, v, v],
+        "grpic_charge_check": [v, p(ParticlesC), p(FieldsC), v, v, p(d), v],
         "grpic_get_areas": [v, v * 6, i64, v],
         "grpic_sync": [v, v],
         "grpic_sort_noalloc": [p(Grid), C.c_int32, p(ParticlesC), p(ParticlesC), v],
@@ -356,6 +357,20 @@ class Context:
         self._check(self.lib.grpic_diagnostics(self.h, C.byref(P._sc) if P is not None else None, C.byref(fc),
                                                _ptr(rho), _ptr(div), _stream(stream)), "grpic_diagnostics")
         return rho, div
+
+    def charge_check(self, P: ParticleSet | None, F: Fields, base=None, want_state=False, stream=None):
+        """(max |div D - rho - base|, max |rho|) over the interior vertices in
+        FP64, and this call's div D - rho (an FP64 tensor) if want_state."""
+        import torch
+        state = torch.zeros((self.cfg.n_theta + 1, F.ld), dtype=torch.float64, device=F.D[0].device) \
+            if want_state else None
+        if P is not None:
+            P._sc.n = P.n
+        out = (C.c_double * 2)()
+        fc = F.c()
+        self._check(self.lib.grpic_charge_check(self.h, C.byref(P._sc) if P is not None else None, C.byref(fc),
+                                                _ptr(base), _ptr(state), out, _stream(stream)), "grpic_charge_check")
+        return out[0], out[1], state
 
     def areas(self, stream=None):
         import torch

@@ -174,6 +174,7 @@ def run20(G):
     S = load32(G, gc, oc, P)
     rho0, div0 = ctx.diagnostics(S, F)
     base = host(div0) - host(rho0)
+    _, _, state0 = ctx.charge_check(S, F, want_state=True)   # the FP64 running check
     worst = 0.0
     for _ in range(20):
         ctx.step(S, F, 1)
@@ -184,7 +185,8 @@ def run20(G):
         sl = (slice(0, oc.nth + 1), slice(oc.ng + 1, oc.ng + last + 1))
         worst = max(worst, np.max(np.abs(res[sl])) / np.max(np.abs(host(rho)[sl])))
     assert ctx.sync() == 0
-    return dict(oc=oc, F=F, S=S, P=P, D=D, B=B, charge=worst)
+    chk = ctx.charge_check(S, F, base=state0)
+    return dict(oc=oc, F=F, S=S, P=P, D=D, B=B, charge=worst, check=chk[:2])
 
 
 def test_fp32_config1_field_error(run20):
@@ -212,6 +214,15 @@ def test_fp32_config1_particle_error(run20):
 def test_fp32_config1_charge_conservation(run20):
     print("FP32 form charge residual / max|rho|:", run20["charge"])
     assert run20["charge"] < 1e-4
+
+
+def test_fp32_running_charge_check_in_fp64(run20):
+    """grpic_charge_check (rho accumulated and div D formed in FP64 from the
+    FP32 state, max over the interior vertices): after 20 steps the change of
+    div D - rho since step 0 stays at the FP32 deposit's rounding."""
+    res, rmax = run20["check"]
+    print("FP32 form FP64 charge check: max|d(div D - rho)| / max|rho| =", res / rmax)
+    assert rmax > 0 and res / rmax < 1e-4
 
 
 def test_fp32_convergence_tolerance(G):

@@ -185,6 +185,7 @@ def config1(G):
     S = load_set(G, gc, P)
     rho0, div0 = ctx.diagnostics(S, F)
     base = host(div0) - host(rho0)
+    _, _, state0 = ctx.charge_check(S, F, want_state=True)
     worst = 0.0
     mind = np.inf
     for step in range(20):
@@ -195,7 +196,13 @@ def config1(G):
         res, rmax = charge_residual(G, ctx, S, F, base, oc)
         worst = max(worst, res / rmax)
     assert ctx.sync() == 0
-    return dict(oc=oc, ctx=ctx, F=F, S=S, P=P, D=D, B=B, charge=worst, ngraze=len(graze), mind=mind)
+    chk = ctx.charge_check(S, F, base=state0)
+    rho, div = ctx.diagnostics(S, F)
+    last = oc.nr - oc.damp_cells - 1
+    sl = (slice(0, oc.nth + 1), slice(oc.ng + 1, oc.ng + last + 1))
+    host_check = (float(np.max(np.abs((host(div) - host(rho) - base)[sl]))), float(np.max(np.abs(host(rho)[sl]))))
+    return dict(oc=oc, ctx=ctx, F=F, S=S, P=P, D=D, B=B, charge=worst, ngraze=len(graze), mind=mind,
+                check=chk[:2], host_check=host_check)
 
 
 def test_config1_axis_grazers_are_few(config1):
@@ -232,6 +239,16 @@ def test_config1_particles_after_20_steps(config1):
 
 def test_config1_charge_conservation(config1):
     assert config1["charge"] < 1e-12, config1["charge"]
+
+
+def test_config1_running_charge_check(config1):
+    """grpic_charge_check reduces max|div D - rho - base| and max|rho| over the
+    interior vertices on the device; on the FP64 path it reproduces the
+    host-side reduction of the diagnostics arrays."""
+    (res, rmax), (hres, hmax) = config1["check"], config1["host_check"]
+    assert rmax == pytest.approx(hmax, rel=1e-12)
+    assert res / rmax < 1e-12
+    assert abs(res - hres) <= 1e-12 * rmax
 
 
 def test_config1_full_input_conserves_charge(G):
