@@ -274,12 +274,24 @@ grpic_status grpic_adjoint_field_step(grpic_ctx *ctx, const grpic_fields *lam_in
  *      itself, equal to 0 up to the iteration's residual (near the polar
  *      axis, where dt/2 |dF/dy| approaches 1, three correctors do not
  *      converge and the two differ).
+ *   dL_da: NULL or a host double: the derivative of L with respect to the
+ *        spin a at fixed step-0 state (p0, f0), fixed grid (r_in, r_out,
+ *        n_r, n_theta), dt and i_horizon.  It collects the metric of every
+ *        push (Boris and geodesic right-hand sides, exactly: a third dual
+ *        slot in their hand-written reverse passes), the tables of every
+ *        field update and of the objective (face-area inverses and metric
+ *        products of App. B) contracted with the stage adjoints, the tables'
+ *        a-derivatives taken by a central difference h = 1e-5 of the
+ *        quadratures.  Initial fields that depend on a (the Wald solution)
+ *        add sum grad_f . dF0/da, which the caller forms.  Requires grad_p;
+ *        costs per step one field update more and (n_field_iter + 1) * 6 + 3
+ *        field arrays of memory per checkpoint segment.
  * n_push_iter must not exceed 16 (the adjoint keeps the iterates).
  * A particle the forward refuses (ERANGE, ENAN) contributes no gradient and
  * its status is returned after the sweep.  Synchronises `stream`. */
 grpic_status grpic_adjoint_grad(grpic_ctx *ctx, const grpic_particles *p0, const grpic_fields *f0, int nsteps,
                                 int checkpoint_every, int i_horizon, int trapezoid_ift, double *L_out,
-                                double *const grad_p[5], double *const grad_f[6], void *stream);
+                                double *const grad_p[5], double *const grad_f[6], double *dL_da, void *stream);
 
 /* ------------------------------------------------------------------------ */
 /* Batched 1D spark gaps: the radiative pair-production prescription of     */

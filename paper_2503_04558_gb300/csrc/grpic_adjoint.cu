@@ -165,15 +165,20 @@ __device__ void rhs_jac(double a, double eps, const double y[5], double F[5], do
 // written out by hand, with the metric quantities and their r and theta
 // derivatives from two-slot dual numbers (their second derivatives of the
 // metric come out of the same evaluation).
-__device__ void rhs_vjp(double a, double eps, const double y[5], const double w[5], double wp, double out[5])
+// ND = 2: slots d/dr, d/dtheta; ND = 3 adds d/da (the spin gradient), whose
+// contraction with the adjoint is added to *out_a
+template <int ND>
+__device__ void rhs_vjp(double a, double eps, const double y[5], const double w[5], double wp, double out[5],
+                        double *out_a = nullptr)
 {
-    DN<2> r(y[0]), th(y[1]);
+    DN<ND> r(y[0]), th(y[1]), aD(a);
     r.d[0] = 1.0;
     th.d[1] = 1.0;
-    DN<2> s, c;
+    if constexpr (ND > 2) aD.d[2] = 1.0;
+    DN<ND> s, c;
     sincos_t(th, &s, &c);
-    KSGeo<DN<2>> m;
-    ks_geo_sc<DN<2>>(DN<2>(a), r, s, c, m);
+    KSGeo<DN<ND>> m;
+    ks_geo_sc<DN<ND>>(aD, r, s, c, m);
     const double ur = y[2], ut = y[3], up = y[4];
     const double grr = m.grr.v, grp = m.grp.v, gtt = m.gtt.v, gpp = m.gpp.v, alpha = m.alpha.v;
     // forward values
@@ -217,7 +222,7 @@ __device__ void rhs_vjp(double a, double eps, const double y[5], const double w[
     L_ut += Luu * 2.0 * gtt * ut;
     L_up += Luu * (2.0 * grp * ur + 2.0 * gpp * up);
     // metric quantities -> r, theta
-    const DN<2> *q[18] = {&m.grr, &m.grp, &m.gtt, &m.gpp, &m.alpha, &m.beta, &m.da_r, &m.da_t, &m.db_r,
+    const DN<ND> *q[18] = {&m.grr, &m.grp, &m.gtt, &m.gpp, &m.alpha, &m.beta, &m.da_r, &m.da_t, &m.db_r,
                           &m.db_t, &m.dgrr_r, &m.dgrr_t, &m.dgrp_r, &m.dgrp_t, &m.dgtt_r, &m.dgtt_t, &m.dgpp_r,
                           &m.dgpp_t};
     const double Lq[18] = {Lgrr, Lgrp, Lgtt, Lgpp, Lalpha, Lbeta, Lda_r, Lda_t, Ldb_r,
@@ -227,6 +232,12 @@ __device__ void rhs_vjp(double a, double eps, const double y[5], const double w[
     for (int k = 0; k < 18; ++k) {
         Lr += Lq[k] * q[k]->d[0];
         Lth += Lq[k] * q[k]->d[1];
+    }
+    if constexpr (ND > 2) {
+        double La = 0.0;
+#pragma unroll
+        for (int k = 0; k < 18; ++k) La += Lq[k] * q[k]->d[2];
+        *out_a += La;
     }
     out[0] = Lr;
     out[1] = Lth;
@@ -277,29 +288,33 @@ __device__ __forceinline__ void boris_z(double a, double qm, double dt, const T 
 // lo^T d(u')/dz for the Boris step above, z = (r, th, u_r, u_th, u_ph, D^r,
 // D^th, D^ph, B^r, B^th, B^ph): its reverse pass written out by hand, the
 // metric's r and theta derivatives from two-slot dual numbers
-__device__ void boris_vjp(double a, double qm, double dt, const double z[11], const double lo[3], double out[11])
+template <int ND>
+__device__ void boris_vjp(double a, double qm, double dt, const double z[11], const double lo[3], double out[11],
+                          double *out_a = nullptr)
 {
-    DN<2> r(z[0]), th(z[1]);
+    // slots: d/dr, d/dtheta (and d/da when ND = 3)
+    DN<ND> r(z[0]), th(z[1]), aD(a);
     r.d[0] = 1.0;
     th.d[1] = 1.0;
-    DN<2> s, c;
+    if constexpr (ND > 2) aD.d[2] = 1.0;
+    DN<ND> s, c;
     sincos_t(th, &s, &c);
-    const DN<2> a2 = DN<2>(a * a), s2 = s * s;
-    const DN<2> rho2 = r * r + a2 * c * c;
-    const DN<2> ir = rcp_t(rho2);
-    const DN<2> zz = DN<2>(2.0) * r * ir;
-    const DN<2> opz = DN<2>(1.0) + zz;
-    const DN<2> alphaD = sqrt_t(rcp_t(opz));
-    const DN<2> Dl_ = r * r + a2 - DN<2>(2.0) * r;
-    const DN<2> Sg = (r * r + a2) * (r * r + a2) - a2 * Dl_ * s2;
+    const DN<ND> a2 = aD * aD, s2 = s * s;
+    const DN<ND> rho2 = r * r + a2 * c * c;
+    const DN<ND> ir = rcp_t(rho2);
+    const DN<ND> zz = DN<ND>(2.0) * r * ir;
+    const DN<ND> opz = DN<ND>(1.0) + zz;
+    const DN<ND> alphaD = sqrt_t(rcp_t(opz));
+    const DN<ND> Dl_ = r * r + a2 - DN<ND>(2.0) * r;
+    const DN<ND> Sg = (r * r + a2) * (r * r + a2) - a2 * Dl_ * s2;
     // metric quantities q[] = g_rr, g_rp, g_tt, g_pp, i_rr, i_rp, i_tt, i_pp, sqrt(gamma), alpha
-    DN<2> q[10];
+    DN<ND> q[10];
     q[0] = opz;
-    q[1] = -DN<2>(a) * s2 * opz;
+    q[1] = -aD * s2 * opz;
     q[2] = rho2;
     q[3] = Sg * s2 * ir;
     q[4] = (a2 + r * r) * ir - zz * rcp_t(opz);
-    q[5] = DN<2>(a) * ir;
+    q[5] = aD * ir;
     q[6] = ir;
     q[7] = ir * rcp_t(s2);
     q[8] = rho2 * s * sqrt_t(opz);
@@ -391,6 +406,12 @@ __device__ void boris_vjp(double a, double qm, double dt, const double z[11], co
     for (int k = 0; k < 10; ++k) {
         Lr += Lq[k] * q[k].d[0];
         Lth += Lq[k] * q[k].d[1];
+    }
+    if constexpr (ND > 2) {
+        double La = 0.0;
+#pragma unroll
+        for (int k = 0; k < 10; ++k) La += Lq[k] * q[k].d[2];
+        *out_a += La;
     }
     out[0] = Lr;
     out[1] = Lth;
@@ -511,16 +532,20 @@ struct PAdjArgs {
     const double *lam1[5];    // adjoint of state n+1
     double *lam0[5];          // adjoint of state n (output)
     double *lamF[6];          // adjoint of fields at n (accumulated)
+    double *La;               // per particle: its part of dL/da (may be null)
     int64_t ld;
 };
 
+template <bool SPIN>
 __global__ void __launch_bounds__(128) particle_adjoint(PAdjArgs A)
 {
+    constexpr int ND = SPIN ? 3 : 2;
     int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= A.n) return;
     const GridDev &g = A.g;
     double out[5] = {0, 0, 0, 0, 0};
     uint32_t t0 = A.tag0[p];
+    if (SPIN) A.La[p] = 0.0;
     if (t0 & DEAD) {
         for (int k = 0; k < 5; ++k) A.lam0[k][p] = 0.0;
         return;
@@ -665,6 +690,8 @@ __global__ void __launch_bounds__(128) particle_adjoint(PAdjArgs A)
     l1[3] *= refl;
     const double hh = 0.5 * dt;
     double l0[5];
+    double la = 0.0;                       // dL/da through the metric of this push
+    double *pla = &la;
     if (A.ift) {
         // the converged trapezoid y1 = y0 + dt/2 (F(y1) + F(y0)), dphi = dt/2
         // (X^ph(y1) + X^ph(y0)), by the implicit-function theorem:
@@ -679,7 +706,12 @@ __global__ void __launch_bounds__(128) particle_adjoint(PAdjArgs A)
         solve5(M, w);
         double hw[5], v0[5];
         for (int k = 0; k < 5; ++k) hw[k] = hh * w[k];
-        rhs_vjp(g.a, eps, y0, hw, hh * ldphi, v0);
+        if constexpr (SPIN) {
+            // the a-dependence of F(y1): w . dt/2 dF/da(y1) + dt/2 ldphi dX^ph/da(y1)
+            double unused[5];
+            rhs_vjp<ND>(g.a, eps, y1, hw, hh * ldphi, unused, pla);
+        }
+        rhs_vjp<ND>(g.a, eps, y0, hw, hh * ldphi, v0, pla);
         for (int k = 0; k < 5; ++k) l0[k] = w[k] + v0[k];
     } else {
         // transpose of the iteration the push runs: y~_0 = y0 + dt F(y0),
@@ -698,7 +730,7 @@ __global__ void __launch_bounds__(128) particle_adjoint(PAdjArgs A)
                 lFp0 += ap;
                 double hg[5], gn[5];
                 for (int k = 0; k < 5; ++k) hg[k] = hh * gk[k];
-                rhs_vjp(g.a, eps, yit[it], hg, ap, gn);
+                rhs_vjp<ND>(g.a, eps, yit[it], hg, ap, gn, pla);
                 for (int k = 0; k < 5; ++k) gk[k] = gn[k];
             }
         }
@@ -707,7 +739,7 @@ __global__ void __launch_bounds__(128) particle_adjoint(PAdjArgs A)
             lF0[k] += dt * gk[k];
         }
         double v0[5];
-        rhs_vjp(g.a, eps, y0, lF0, lFp0, v0);
+        rhs_vjp<ND>(g.a, eps, y0, lF0, lFp0, v0, pla);
         for (int k = 0; k < 5; ++k) l0[k] = ly0[k] + v0[k];
     }
     // start point: deposit's start-weight derivatives
@@ -719,7 +751,7 @@ __global__ void __launch_bounds__(128) particle_adjoint(PAdjArgs A)
     if (charged) {
         double zv[11] = {r, th, u[0], u[1], u[2], E[0], E[1], E[2], E[3], E[4], E[5]};
         double lb[11];
-        boris_vjp(g.a, A.qm[sp], dt, zv, l0 + 2, lb);
+        boris_vjp<ND>(g.a, A.qm[sp], dt, zv, l0 + 2, lb, pla);
         out[0] += lb[0];
         out[1] += lb[1];
         for (int k = 0; k < 3; ++k) out[2 + k] = lb[2 + k];
@@ -737,6 +769,7 @@ __global__ void __launch_bounds__(128) particle_adjoint(PAdjArgs A)
         for (int k = 0; k < 3; ++k) out[2 + k] = l0[2 + k];
     }
     for (int k = 0; k < 5; ++k) A.lam0[k][p] = out[k];
+    if (SPIN) A.La[p] = la;
 }
 
 // ---- field update transpose -------------------------------------------------
@@ -998,6 +1031,162 @@ __global__ void flux_seed(FAdj A, const double *const *F, int iH, double dth, do
         for (int dj = 0; dj <= 1; ++dj) at(1, iH + di, j + dj, -0.25 * c * R.Eph);
 }
 
+// ---- spin derivative of the field update and of the objective -------------
+// At fixed fields the update and the flux depend on the spin only through
+// the static tables (face-area inverses, metric products of the auxiliary
+// fields); dtab holds their a-derivatives.  A value and its a-derivative:
+struct VD {
+    double v, d;
+};
+__device__ __forceinline__ VD operator+(VD x, VD y) { return {x.v + y.v, x.d + y.d}; }
+__device__ __forceinline__ VD operator-(VD x, VD y) { return {x.v - y.v, x.d - y.d}; }
+__device__ __forceinline__ VD operator*(double c, VD x) { return {c * x.v, c * x.d}; }
+
+// auxiliary fields of App. B (the field update's formulas) with their
+// a-derivatives at fixed X
+struct DAux {
+    FAdj A;
+    const double *dtab;
+    const double *const *X;
+    __device__ VD p(int slot, int comp, int i, int j) const
+    {
+        size_t q = slot * A.slab + (size_t)j * A.ldt + (i + NG);
+        double x = X[comp][(size_t)j * A.ld + (i + NG)];
+        return {A.tab[q] * x, dtab[q] * x};
+    }
+    __device__ VD t(int slot, int i, int j) const
+    {
+        size_t q = slot * A.slab + (size_t)j * A.ldt + (i + NG);
+        return {A.tab[q], dtab[q]};
+    }
+    __device__ VD Hr(int i, int j) const
+    {
+        return p(T_AGRR_BR, 3, i, j) + 0.5 * (p(T_AGRP_BP, 5, i, j) + p(T_AGRP_BP, 5, i - 1, j));
+    }
+    __device__ VD Hth(int i, int j) const
+    {
+        return p(T_AGTT_BT, 4, i, j) + 0.5 * (p(T_SGB_DP, 2, i, j) + p(T_SGB_DP, 2, i + 1, j));
+    }
+    __device__ VD Hph(int i, int j) const
+    {
+        return p(T_AGPP_BP, 5, i, j) + 0.5 * (p(T_AGRP_BR, 3, i, j) + p(T_AGRP_BR, 3, i + 1, j)) -
+               0.5 * (p(T_SGB_DT, 1, i, j) + p(T_SGB_DT, 1, i + 1, j));
+    }
+    __device__ VD Er(int i, int j) const
+    {
+        return p(T_AGRR_DR, 0, i, j) + 0.5 * (p(T_AGRP_DP, 2, i, j) + p(T_AGRP_DP, 2, i + 1, j));
+    }
+    __device__ VD Eth(int i, int j) const
+    {
+        return p(T_AGTT_DT, 1, i, j) - 0.5 * (p(T_SGB_BP, 5, i, j) + p(T_SGB_BP, 5, i - 1, j));
+    }
+    __device__ VD Eph(int i, int j) const
+    {
+        return p(T_AGPP_DP, 2, i, j) + 0.5 * (p(T_AGRP_DR, 0, i, j) + p(T_AGRP_DR, 0, i - 1, j)) +
+               0.5 * (p(T_SGB_BT, 4, i, j) + p(T_SGB_BT, 4, i - 1, j));
+    }
+};
+
+// block sum of v added to *out (blockDim.x * blockDim.y = 256)
+__device__ __forceinline__ void block_add(double v, double *out)
+{
+    __shared__ double red[256];
+    const int t = threadIdx.y * blockDim.x + threadIdx.x;
+    red[t] = v;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if (t < o) red[t] += red[t + o];
+        __syncthreads();
+    }
+    if (t == 0 && red[0] != 0.0) atomicAdd(out, red[0]);
+}
+
+// *out += sum over points of w . dC/da (X): C the circulation of one stage
+// (Eqs. D-update, B-update divided by the face areas), w adjoint-shaped
+__global__ void __launch_bounds__(256) dcirc_dot(FAdj A, const double *dtab, const double *const *X,
+                                                 const double *const *w, double dth, double *out)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    int j = blockIdx.y * blockDim.y + threadIdx.y;
+    double acc = 0.0;
+    if (i <= A.nr && j <= A.nth) {
+        DAux X_{A, dtab, X};
+        const int nr = A.nr, nth = A.nth;
+        const size_t q = (size_t)j * A.ld + (i + NG);
+        const double drd = A.col1d[1 * A.ldt + i + NG], drp = A.col1d[0 * A.ldt + i + NG];
+        auto term = [&](int comp, int inv_slot, VD circ) {
+            VD inv = X_.t(inv_slot, i, j);
+            return w[comp][q] * (circ.d * inv.v + circ.v * inv.d);
+        };
+        if (i <= nr - 1) {
+            VD hp = (j < nth) ? X_.Hph(i, j) : VD{0.0, 0.0};
+            VD hm = (j > 0) ? X_.Hph(i, j - 1) : VD{0.0, 0.0};
+            acc += term(0, T_INV_ADR, hp - hm);
+        }
+        if (j < nth) {
+            acc += term(1, T_INV_ADT, X_.Hph(i - 1, j) - X_.Hph(i, j));
+            acc += term(3, T_INV_ABR, -1.0 * (X_.Eph(i, j + 1) - X_.Eph(i, j)));
+        }
+        if (j > 0 && j < nth) {
+            acc += term(2, T_INV_ADP, dth * (X_.Hth(i, j) - X_.Hth(i - 1, j)) + drd * (X_.Hr(i, j - 1) - X_.Hr(i, j)));
+            if (i <= nr - 1) acc += term(4, T_INV_ABT, -1.0 * (X_.Eph(i, j) - X_.Eph(i + 1, j)));
+        }
+        if (i <= nr - 1 && j < nth)
+            acc += term(5, T_INV_ABP,
+                        -1.0 * (dth * (X_.Eth(i + 1, j) - X_.Eth(i, j)) + drp * (X_.Er(i, j) - X_.Er(i, j + 1))));
+    }
+    block_add(acc, out);
+}
+
+// *out += sj * sum over the D points a stage writes of w . d(invA)/da J A
+// (the current term of Eq. fld-predictor / fld-corrector)
+__global__ void __launch_bounds__(256) jinv_dot(FAdj A, const double *dtab, const double *const *w,
+                                                const double *const *J, double sj, double *out)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    int j = blockIdx.y * blockDim.y + threadIdx.y;
+    double acc = 0.0;
+    if (i <= A.nr && j <= A.nth) {
+        const size_t q = (size_t)j * A.ld + (i + NG), qt = (size_t)j * A.ldt + (i + NG);
+        if (i <= A.nr - 1) acc += w[0][q] * dtab[T_INV_ADR * A.slab + qt] * J[0][q];
+        if (j < A.nth) acc += w[1][q] * dtab[T_INV_ADT * A.slab + qt] * J[1][q];
+        if (j > 0 && j < A.nth) acc += w[2][q] * dtab[T_INV_ADP * A.slab + qt] * J[2][q];
+    }
+    block_add(sj * acc, out);
+}
+
+// *out += w * d(flux)/da at fixed fields F (the ring values of the objective)
+__global__ void __launch_bounds__(256) flux_da(FAdj A, const double *dtab, const double *const *F, int iH, double dth,
+                                               double w, double *out)
+{
+    double acc = 0.0;
+    int j = blockIdx.x * 256 + threadIdx.x;
+    if (j < A.nth) {
+        DAux X_{A, dtab, F};
+        VD Eth = X_.Eth(iH, j);
+        VD Hph = 0.5 * (X_.Hph(iH - 1, j) + X_.Hph(iH, j));
+        VD Eph = 0.5 * (X_.Eph(iH, j) + X_.Eph(iH, j + 1));
+        VD Hth = 0.25 * (X_.Hth(iH - 1, j) + X_.Hth(iH, j) + X_.Hth(iH - 1, j + 1) + X_.Hth(iH, j + 1));
+        acc = w * dth * (Eth.d * Hph.v + Eth.v * Hph.d - Eph.d * Hth.v - Eph.v * Hth.d);
+    }
+    block_add(acc, out);
+}
+
+// dtab = (tab(a + h) - tab(a - h)) / (2h)
+__global__ void central_diff(const double *tp, const double *tm, double inv2h, size_t n, double *d)
+{
+    size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e < n) d[e] = (tp[e] - tm[e]) * inv2h;
+}
+
+// *out += sum of x[0..n)
+__global__ void __launch_bounds__(256) sum_into(const double *x, int64_t n, double *out)
+{
+    double acc = 0.0;
+    for (int64_t e = (int64_t)blockIdx.x * 256 + threadIdx.x; e < n; e += (int64_t)gridDim.x * 256) acc += x[e];
+    block_add(acc, out);
+}
+
 }  // namespace
 }  // namespace grpic
 
@@ -1047,10 +1236,25 @@ extern "C" grpic_status grpic_horizon_flux(grpic_ctx *ctx, const grpic_fields *f
     return e == cudaSuccess ? GRPIC_OK : GRPIC_ECUDA;
 }
 
+// What the spin derivative of one field update needs: the derivative
+// tables, the update's input fields Xn, its currents J and every stage's
+// output Y[k] (device pointer arrays), and the scalar it accumulates into.
+struct SpinField {
+    const double *dtab;
+    double **Xn;   // 6
+    double **J;    // 3
+    double **Y;    // (n_field_iter + 1) * 6
+    double *La;
+};
+
 // Transpose of one field update: lam (adjoint of F^{n+1}, in f_lam->D/B) ->
 // adjoint of F^n (out->D/B) and of the integrated currents J A (out->J).
+// With sp, also adds the update's a-derivative contracted with the stage
+// adjoints to sp->La: every stage's pre-projection value
+//   dt (c_k C(Xn) + beta_s C(Y_{k-1})) - dt invA J   (c_0 = 1, c_k = alpha_s)
+// depends on a through the tables of C and invA.
 static grpic_status field_adjoint(grpic_ctx *ctx, double **lamIn, double **lamOut, double **lamJ, double **work,
-                                  int64_t ld, cudaStream_t s, double ***dptrs)
+                                  int64_t ld, cudaStream_t s, double ***dptrs, const SpinField *sp = nullptr)
 {
     // work: mu[6], lamCn[6], lamPrev[6], aux[6]  (24 arrays); dptrs: device copies
     const int N = ctx->prm.n_field_iter;
@@ -1080,6 +1284,8 @@ static grpic_status field_adjoint(grpic_ctx *ctx, double **lamIn, double **lamOu
         axpy6<<<nb, 256, 0, s>>>(d_out, d_mu, 1.0, fn);
         axpy6<<<nb, 256, 0, s>>>(d_lcn, d_mu, dt * (k == 0 ? 1.0 : as), fn);
         jadj<<<grd, blk, 0, s>>>(A, d_mu, d_J, -dt);
+        if (sp)  // the current term: -dt mu_k . d(invA)/da J
+            jinv_dot<<<grd, blk, 0, s>>>(A, sp->dtab, d_mu, sp->J, -dt, sp->La);
         if (k > 0) {
             // lam of the previous iterate = C^T (dt beta mu)
             for (int c = 0; c < 6; ++c) {
@@ -1088,11 +1294,15 @@ static grpic_status field_adjoint(grpic_ctx *ctx, double **lamIn, double **lamOu
             }
             // scale mu by dt*beta in place
             axpy6<<<nb, 256, 0, s>>>(d_mu, d_mu, dt * bs - 1.0, fn);
+            if (sp)  // dt beta_s mu_k . dC/da (Y_{k-1})
+                dcirc_dot<<<grd, blk, 0, s>>>(A, sp->dtab, sp->Y + (k - 1) * 6, d_mu, ctx->g.dth, sp->La);
             circ_T<<<grd, blk, 0, s>>>(A, d_mu, d_aux, ctx->g.dth);
             aux_T<<<gfull, blk, 0, s>>>(A, d_aux, d_prev);
             cudaMemcpyAsync(d_cur, d_prev, sizeof(double *) * 6, cudaMemcpyDeviceToDevice, s);
         }
     }
+    // (sum_k dt c_k mu_k) . dC/da (X^n)
+    if (sp) dcirc_dot<<<grd, blk, 0, s>>>(A, sp->dtab, sp->Xn, d_lcn, ctx->g.dth, sp->La);
     // lam X^n += C^T lam Cn
     for (int c = 0; c < 6; ++c) cudaMemsetAsync(aux[c], 0, fn * sizeof(double), s);
     circ_T<<<grd, blk, 0, s>>>(A, d_lcn, d_aux, ctx->g.dth);
@@ -1141,11 +1351,11 @@ extern "C" grpic_status grpic_adjoint_field_step(grpic_ctx *ctx, const grpic_fie
 extern "C" grpic_status grpic_adjoint_grad(grpic_ctx *ctx, const grpic_particles *p0, const grpic_fields *f0,
                                            int nsteps, int checkpoint_every, int i_horizon, int trapezoid_ift,
                                            double *L_out, double *const grad_p[5], double *const grad_f[6],
-                                           void *stream)
+                                           double *dL_da, void *stream)
 {
     if (!ctx || !p0 || !f0 || !L_out || ctx->prm.precision != 64 || nsteps < 1 || checkpoint_every < 1 ||
         i_horizon < 1 || i_horizon > ctx->g.nr - 1 || ctx->prm.n_field_iter < 1 || f0->ld < ctx->g.nr + 2 * NG ||
-        p0->n < 0 || p0->n > INT32_MAX || (!grad_p && grad_f) || ctx->prm.n_push_iter > MAX_ITER)
+        p0->n < 0 || p0->n > INT32_MAX || (!grad_p && (grad_f || dL_da)) || ctx->prm.n_push_iter > MAX_ITER)
         return GRPIC_EINVAL;
     const bool want = grad_p != nullptr;  // NULL: the objective alone
     if (want)
@@ -1208,9 +1418,37 @@ extern "C" grpic_status grpic_adjoint_grad(grpic_ctx *ctx, const grpic_particles
     }
     std::vector<double *> work(want ? 24 : 0, nullptr);
     for (auto &w : work) ok = ok && (w = (double *)dalloc(fn * sizeof(double)));
+    // spin derivative: derivative tables, per-particle parts, the segment's
+    // currents and one update's stage outputs
+    const bool spin = dL_da != nullptr;
+    const int NF = ctx->prm.n_field_iter;
+    const size_t ntab = ctx->slab * T_COUNT;
+    double *dtab = nullptr, *Ladev = nullptr, *Lap = nullptr;
+    std::vector<double *> segJ(spin ? 3 * ck : 0, nullptr), Ystage(spin ? 6 * (NF + 1) : 0, nullptr);
+    if (spin) {
+        ok = ok && (dtab = (double *)dalloc(ntab * sizeof(double)));
+        ok = ok && (Ladev = (double *)dalloc(sizeof(double)));
+        ok = ok && (Lap = (double *)dalloc(np * sizeof(double)));
+        for (auto &q : segJ) ok = ok && (q = (double *)dalloc(fn * sizeof(double)));
+        for (auto &q : Ystage) ok = ok && (q = (double *)dalloc(fn * sizeof(double)));
+    }
     if (!ok) {
         cleanup();
         return GRPIC_ENOMEM;
+    }
+    if (spin) {
+        // a-derivatives of the tables by central differences, h = 1e-5 (the
+        // quadratures are smooth in a: truncation ~h^2, rounding ~1e-16/h)
+        const double h = 1e-5;
+        double *tp = (double *)dalloc(ntab * sizeof(double)), *tm = (double *)dalloc(ntab * sizeof(double));
+        double *c1 = (double *)dalloc(4 * ctx->g.ld_tab * sizeof(double));
+        if (!tp || !tm || !c1 || launch_tables_at(ctx, ctx->g.a + h, tp, c1, s) != cudaSuccess ||
+            launch_tables_at(ctx, ctx->g.a - h, tm, c1, s) != cudaSuccess) {
+            cleanup();
+            return GRPIC_ENOMEM;
+        }
+        central_diff<<<(unsigned)((ntab + 255) / 256), 256, 0, s>>>(tp, tm, 0.5 / h, ntab, dtab);
+        cudaMemsetAsync(Ladev, 0, sizeof(double), s);
     }
     auto copy_state = [&](State &dst, const State &src) {
         for (int k = 0; k < 6; ++k) cudaMemcpyAsync(dst.F[k], src.F[k], fn * sizeof(double), cudaMemcpyDeviceToDevice, s);
@@ -1281,6 +1519,8 @@ extern "C" grpic_status grpic_adjoint_grad(grpic_ctx *ctx, const grpic_particles
         if (want && n % ck == 0) copy_state(cks[n / ck], W);
         st = fwd_step();
         flux_kernel<<<1, 256, 0, s>>>(A, dWf, i_horizon, dth, wL, Ldev);
+        if (spin)  // the objective's own tables at F^{n+1}
+            flux_da<<<(ctx->g.nth + 255) / 256, 256, 0, s>>>(A, dtab, dWf, i_horizon, dth, wL, Ladev);
     }
     cudaMemcpyAsync(L_out, Ldev, sizeof(double), cudaMemcpyDeviceToHost, s);
     if (!want) {
@@ -1309,6 +1549,19 @@ extern "C" grpic_status grpic_adjoint_grad(grpic_ctx *ctx, const grpic_particles
         return GRPIC_ENOMEM;
     }
     for (int k = 0; k < 8; ++k) allocs.push_back(dptrs[k]);
+    SpinField spf{dtab, nullptr, nullptr, nullptr, Ladev};
+    if (spin) {
+        ok = upload_ptrs(Ystage.data(), 6 * (NF + 1), &spf.Y, s) == cudaSuccess;
+        if (ok) allocs.push_back(spf.Y);
+        ok = ok && cudaMalloc(&spf.Xn, sizeof(double *) * 6) == cudaSuccess;
+        if (ok) allocs.push_back(spf.Xn);
+        ok = ok && cudaMalloc(&spf.J, sizeof(double *) * 3) == cudaSuccess;
+        if (ok) allocs.push_back(spf.J);
+        if (!ok) {
+            cleanup();
+            return GRPIC_ENOMEM;
+        }
+    }
     dim3 gfull((ctx->g.ld_tab + 63) / 64, (ctx->g.nth + 1 + 3) / 4), blk(64, 4);
     for (int sgi = nseg - 1; sgi >= 0 && st == GRPIC_OK; --sgi) {
         int n0 = sgi * ck, len = std::min(ck, nsteps - n0);
@@ -1318,6 +1571,9 @@ extern "C" grpic_status grpic_adjoint_grad(grpic_ctx *ctx, const grpic_particles
         for (int m = 0; m < len && st == GRPIC_OK; ++m) {
             st = fwd_step();
             copy_state(seg[m + 1], W);
+            if (spin)
+                for (int k = 0; k < 3; ++k)
+                    cudaMemcpyAsync(segJ[3 * m + k], Jw[k], fn * sizeof(double), cudaMemcpyDeviceToDevice, s);
         }
         for (int m = len - 1; m >= 0 && st == GRPIC_OK; --m) {
             // seed: lamF (adjoint of F^{n+1}) += wL dflux/dF^{n+1}
@@ -1326,7 +1582,16 @@ extern "C" grpic_status grpic_adjoint_grad(grpic_ctx *ctx, const grpic_particles
             flux_seed<<<(ctx->g.nth + 127) / 128, 128, 0, s>>>(A, dSegF, i_horizon, dth, wL, dAux);
             aux_T<<<gfull, blk, 0, s>>>(A, dAux, dLamF);
             // fields: lamF -> lamF2 (adjoint of F^n through the field update), lamJ
-            st = field_adjoint(ctx, lamF, lamF2, lamJ, work.data(), ld, s, dptrs);
+            if (spin) {
+                // the update of step m again, every stage kept
+                if (launch_field64_stages(ctx, seg[m].F, &segJ[3 * m], Ystage.data(), ld, s) != cudaSuccess) {
+                    st = GRPIC_ECUDA;
+                    break;
+                }
+                cudaMemcpyAsync(spf.Xn, seg[m].F, sizeof(double *) * 6, cudaMemcpyHostToDevice, s);
+                cudaMemcpyAsync(spf.J, &segJ[3 * m], sizeof(double *) * 3, cudaMemcpyHostToDevice, s);
+            }
+            st = field_adjoint(ctx, lamF, lamF2, lamJ, work.data(), ld, s, dptrs, spin ? &spf : nullptr);
             if (st != GRPIC_OK) break;
             // particles
             PAdjArgs P;
@@ -1353,7 +1618,13 @@ extern "C" grpic_status grpic_adjoint_grad(grpic_ctx *ctx, const grpic_particles
             }
             for (int k = 0; k < 3; ++k) P.lamJ[k] = lamJ[k];
             P.ld = ld;
-            if (np > 0) particle_adjoint<<<(unsigned)((np + 127) / 128), 128, 0, s>>>(P);
+            P.La = spin ? Lap : nullptr;
+            if (np > 0 && spin) particle_adjoint<true><<<(unsigned)((np + 127) / 128), 128, 0, s>>>(P);
+            if (np > 0 && !spin) particle_adjoint<false><<<(unsigned)((np + 127) / 128), 128, 0, s>>>(P);
+            if (spin && np > 0) {
+                unsigned nb = (unsigned)std::min<int64_t>((np + 255) / 256, 4 * 152);
+                sum_into<<<nb, 256, 0, s>>>(Lap, np, Ladev);
+            }
             if (cudaGetLastError() != cudaSuccess) st = GRPIC_ECUDA;
             for (int k = 0; k < 5; ++k) std::swap(lamP[k], lamP2[k]);
             // lamF <- lamF2
@@ -1364,6 +1635,7 @@ extern "C" grpic_status grpic_adjoint_grad(grpic_ctx *ctx, const grpic_particles
     if (grad_f)
         for (int k = 0; k < 6; ++k)
             if (grad_f[k]) cudaMemcpyAsync(grad_f[k], lamF[k], fn * sizeof(double), cudaMemcpyDeviceToDevice, s);
+    if (spin) cudaMemcpyAsync(dL_da, Ladev, sizeof(double), cudaMemcpyDeviceToHost, s);
     // a particle the forward refused (range, non-finite) is reported like the step does
     int hst = 0;
     cudaMemcpyAsync(&hst, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost, s);

@@ -244,6 +244,43 @@ cudaError_t run_field(grpic_ctx *ctx, grpic_fields *f, const T *tab, const T *co
 
 }  // namespace
 
+// The FP64 field update from Xn with currents J, every stage's output kept:
+// Y[k][0..5] for k = 0 (predictor) .. N (the last corrector, damped) -- the
+// iterates the adjoint needs to differentiate the update w.r.t. its tables.
+// Xn is not modified; Y buffers are (nth+1) x ld each.
+cudaError_t launch_field64_stages(grpic_ctx *ctx, double *const Xn[6], double *const J[3], double *const *Y,
+                                  int64_t ld, cudaStream_t s)
+{
+    FieldArgs<double> A;
+    A.nr = ctx->g.nr;
+    A.nth = ctx->g.nth;
+    A.ld = ld;
+    A.ldt = ctx->g.ld_tab;
+    A.slab = ctx->slab;
+    A.dt = ctx->prm.dt;
+    A.bs = ctx->prm.beta_field;
+    A.as = 1.0 - ctx->prm.beta_field;
+    A.dth = ctx->g.dth;
+    A.tab = ctx->tab;
+    A.col1d = ctx->col1d;
+    for (int k = 0; k < 3; ++k) A.J[k] = J[k];
+    for (int k = 0; k < 6; ++k) {
+        A.Xn[k] = Xn[k];
+        A.Cn[k] = fslot<double>(ctx, k, ld);
+    }
+    dim3 blk(64, 4), grd((A.nr + 1 + 63) / 64, (A.nth + 1 + 3) / 4);
+    const int N = ctx->prm.n_field_iter;
+    for (int st = 0; st <= N; ++st) {
+        for (int k = 0; k < 6; ++k) {
+            A.Xc[k] = st == 0 ? Xn[k] : Y[(st - 1) * 6 + k];
+            A.Xo[k] = Y[st * 6 + k];
+        }
+        A.mode = st == 0 ? 0 : (st == N ? 2 : 1);
+        field_stage_kernel<double><<<grd, blk, 0, s>>>(A);
+    }
+    return cudaGetLastError();
+}
+
 cudaError_t launch_field64(grpic_ctx *ctx, grpic_fields *f, cudaStream_t s)
 {
     return run_field<double>(ctx, f, ctx->tab, ctx->col1d, s);

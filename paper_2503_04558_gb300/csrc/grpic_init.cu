@@ -287,6 +287,18 @@ cudaError_t launch_tables(grpic_ctx *ctx, cudaStream_t s)
     return cudaGetLastError();
 }
 
+// the tables of spin a (grid unchanged) into caller buffers: the spin
+// gradient differences them at a +- h
+cudaError_t launch_tables_at(grpic_ctx *ctx, double a, double *tab, double *col1d, cudaStream_t s)
+{
+    GridDev g = ctx->g;
+    g.a = a;
+    dim3 blk(32, 4), grd((ctx->g.ld_tab + 31) / 32, (ctx->g.nth + 1 + 3) / 4);
+    tables_kernel<<<grd, blk, 0, s>>>(g, make_gl(ctx), tab, ctx->slab, col1d, ctx->grid.damp_cells,
+                                      ctx->grid.damp_max);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_init_fields(grpic_ctx *ctx, int kind, double B0, const grpic_fields *f, cudaStream_t s)
 {
     dim3 blk(32, 4), grd((ctx->g.ld_tab + 31) / 32, (ctx->g.nth + 1 + 3) / 4);

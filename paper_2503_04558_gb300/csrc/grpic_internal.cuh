@@ -155,7 +155,10 @@ cudaError_t launch_push32(grpic_ctx *ctx, grpic_particles *p, grpic_fields *f, b
 cudaError_t launch_deposit(grpic_ctx *ctx, const grpic_particles *b, const grpic_particles *a, const void *dphi,
                            grpic_fields *f, cudaStream_t s);
 cudaError_t launch_field64(grpic_ctx *ctx, grpic_fields *f, cudaStream_t s);
+cudaError_t launch_field64_stages(grpic_ctx *ctx, double *const Xn[6], double *const J[3], double *const *Y, int64_t ld,
+                                  cudaStream_t s);
 cudaError_t launch_field32(grpic_ctx *ctx, grpic_fields *f, cudaStream_t s);
+cudaError_t launch_tables_at(grpic_ctx *ctx, double a, double *tab, double *col1d, cudaStream_t s);
 cudaError_t launch_keys(grpic_ctx *ctx, const grpic_particles *p, cudaStream_t s);
 cudaError_t sort_setup();
 cudaError_t launch_sort(grpic_ctx *ctx, grpic_particles *p, grpic_particles *scratch, cudaStream_t s);

@@ -598,7 +598,7 @@ def _load_adj(lib):
     for name, args in {"grpic_horizon_flux": [v, p(FieldsC), C.c_int, p(C.c_double), v],
                        "grpic_adjoint_field_step": [v, p(FieldsC), p(FieldsC), v],
                        "grpic_adjoint_grad": [v, p(ParticlesC), p(FieldsC), C.c_int, C.c_int, C.c_int,
-                                              C.c_int, p(C.c_double), v, v, v]}.items():
+                                              C.c_int, p(C.c_double), v, v, v, v]}.items():
         fn = getattr(lib, name)
         fn.argtypes = args
         fn.restype = C.c_int
@@ -642,13 +642,15 @@ def adjoint_field_step(gctx: Context, lam: Fields, stream=None) -> Fields:
 
 
 def adjoint_grad(gctx: Context, x, tag, D, B, nsteps: int, i_horizon: int, checkpoint_every: int = 20,
-                 want_grad: bool = True, ift: bool = False, stream=None):
+                 want_grad: bool = True, ift: bool = False, want_spin: bool = False, stream=None):
     """Objective L of nsteps steps from particles x = (r, theta, u_r, u_theta,
     u_phi) (five float64 device tensors of n), tag (int32 tensor of n) and
     fields D, B (three (n_theta+1, ld) float64 tensors each).  Returns L and,
     if want_grad, the gradients (five tensors like x, six like D + B).
     ift=True differentiates the converged geodesic trapezoid (implicit-function
-    theorem) instead of the correctors the push runs."""
+    theorem) instead of the correctors the push runs.  want_spin=True (needs
+    want_grad) appends dL/da at fixed step-0 particles and fields (grid, dt
+    and i_horizon fixed) as a fourth result."""
     import torch
     _load_adj(gctx.lib)
     n = int(x[0].numel())
@@ -671,10 +673,39 @@ def adjoint_grad(gctx: Context, x, tag, D, B, nsteps: int, i_horizon: int, check
         arr_f = (C.c_void_p * 6)(*[t.data_ptr() for t in gf])
     else:
         arr_p = arr_f = None
+    if want_spin and not want_grad:
+        raise ValueError("want_spin needs want_grad")
+    La = C.c_double()
     st = gctx.lib.grpic_adjoint_grad(gctx.h, C.byref(pc), C.byref(fc), int(nsteps), int(checkpoint_every),
-                                     int(i_horizon), 1 if ift else 0, C.byref(L), arr_p, arr_f, _stream(stream))
+                                     int(i_horizon), 1 if ift else 0, C.byref(L), arr_p, arr_f,
+                                     C.byref(La) if want_spin else None, _stream(stream))
     gctx._check(st, "grpic_adjoint_grad")
+    if want_spin:
+        return L.value, gp, gf, La.value
     return L.value, gp, gf
+
+
+def spin_gradient(cfg: Config, x, tag, kind: int, B0: float, nsteps: int, i_horizon: int,
+                  checkpoint_every: int = 20, h: float = 1e-5):
+    """dL/da for a run that starts from the closed-form fields `kind`, B0 of
+    spin a = cfg.a (grid, dt and i_horizon held at cfg's): the adjoint's
+    part at fixed step-0 state plus grad_F0 . dF0/da, the initial fields'
+    a-derivative taken by a central difference (h) of their closed forms.
+    Returns (L, dL/da)."""
+    import dataclasses
+    ctx = Context(cfg)
+    F = Fields(cfg)
+    ctx.init_fields(F, kind, B0)
+    L, _, gf, La = adjoint_grad(ctx, x, tag, F.D, F.B, nsteps, i_horizon, checkpoint_every, want_spin=True)
+    dF = []
+    for da in (h, -h):
+        c = dataclasses.replace(cfg, a=cfg.a + da)
+        cx = Context(c)
+        Fa = Fields(c)
+        cx.init_fields(Fa, kind, B0)
+        dF.append([t.clone() for t in Fa.D + Fa.B])
+        del cx
+    return L, La + sum(float((g * (p - m)).sum()) for g, p, m in zip(gf, dF[0], dF[1])) / (2.0 * h)
 
 
 def _autograd_fn():
@@ -719,5 +750,5 @@ def horizon_flux_objective(gctx: Context, x, tag, D, B, nsteps: int, i_horizon: 
 def spin_gradient_fd(make, h: float = 1e-6) -> float:
     """dL/da by a central difference: make(a_offset) must build the context
     and the inputs at spin a + a_offset on the grid of the nominal spin and
-    return L.  (The adjoint does not differentiate the metric tables.)"""
+    return L (the check of spin_gradient)."""
     return (make(h) - make(-h)) / (2.0 * h)

@@ -8,6 +8,9 @@ the C ABI (grpic_adjoint_field_step, grpic_adjoint_grad, grpic_horizon_flux).
   * directional derivatives of L (random directions in the initial momenta,
     positions and fields, and the Wald strength B0) match central finite
     differences of the GPU forward and of the oracle's FP64 objective;
+  * dL/da (the spin) matches central differences of L in a with the grid, dt
+    and i_H held, both at fixed initial fields (the adjoint's own part) and
+    with the Wald fields of each spin (its part plus grad_F0 . dF0/da);
   * the gradient does not depend on the checkpoint interval;
   * the torch.autograd.Function hands the same gradients to .grad.
 
@@ -18,6 +21,7 @@ iteration converges (away from the polar axis, many correctors).  Central
 differences of the particle terms see the kinks of the piecewise-linear CIC
 weights when a perturbed path crosses a cell boundary or centre, which bounds
 the agreement with them to ~1e-6 relative here."""
+import dataclasses
 import math
 
 import numpy as np
@@ -178,6 +182,48 @@ def test_gradient_matches_finite_differences(G, case, which, h):
     assert abs(pred - fo) <= 2e-6 * abs(fo)
 
 
+def test_spin_gradient_matches_finite_differences(G, case):
+    h = 1e-6
+    oc, gc = case["oc"], case["gc"]
+    L, gp, gf, La = G.adjoint_grad(case["ctx"], case["x"], case["tag"], case["F"].D, case["F"].B, NSTEPS,
+                                   case["iH"], want_spin=True)
+    assert L == pytest.approx(case["L"], rel=1e-13)
+    for a, b in zip(gp + gf, case["gp"] + case["gf"]):
+        assert relerr(host(a), host(b)) < 1e-12
+
+    def gpu_at(da, fixed_fields):
+        c = dataclasses.replace(gc, a=A09 + da)
+        ctx = G.Context(c)
+        F = case["F"] if fixed_fields else G.Fields(c)
+        if not fixed_fields:
+            ctx.init_fields(F, O.WALD, 1.0)
+        return G.adjoint_grad(ctx, case["x"], case["tag"], F.D, F.B, NSTEPS, case["iH"], want_grad=False)[0]
+
+    def oracle_at(da, fixed_fields):
+        o = O.make_cfg(oc.nr, oc.nth, A09 + da, oc.r_in, oc.r_out, dt=oc.dt, damp_cells=oc.damp_cells)
+        D, B = (case["D"], case["B"]) if fixed_fields else O.init_fields(o, O.WALD, 1.0)
+        return O.flux_run(o, case["P"], D, B, NSTEPS, case["iH"])
+
+    # the adjoint's own part: metric of the pushes, tables of the updates and the flux
+    fd = (gpu_at(h, True) - gpu_at(-h, True)) / (2 * h)
+    fo = (oracle_at(h, True) - oracle_at(-h, True)) / (2 * h)
+    print(f"dL/da at fixed F0: adjoint {La:.12e} gpu-fd {fd:.12e} oracle-fd {fo:.12e}")
+    assert abs(La - fd) <= 2e-6 * abs(fd)
+    assert abs(La - fo) <= 2e-6 * abs(fo)
+    # with the initial Wald fields of each spin
+    L2, dLda = G.spin_gradient(gc, case["x"], case["tag"], O.WALD, 1.0, NSTEPS, case["iH"])
+    assert L2 == pytest.approx(case["L"], rel=1e-13)
+    fd = G.spin_gradient_fd(lambda da: gpu_at(da, False), h)
+    fo = (oracle_at(h, False) - oracle_at(-h, False)) / (2 * h)
+    print(f"dL/da: adjoint {dLda:.12e} gpu-fd {fd:.12e} oracle-fd {fo:.12e}")
+    assert abs(dLda - fd) <= 2e-6 * abs(fd)
+    assert abs(dLda - fo) <= 2e-6 * abs(fo)
+    # checkpointing leaves it unchanged
+    La7 = G.adjoint_grad(case["ctx"], case["x"], case["tag"], case["F"].D, case["F"].B, NSTEPS, case["iH"],
+                         checkpoint_every=7, want_spin=True)[3]
+    assert La7 == pytest.approx(La, rel=1e-10)
+
+
 def test_gradient_independent_of_checkpoint_interval(G, case):
     for ck in (1, 7):
         L, gp, gf = G.adjoint_grad(case["ctx"], case["x"], case["tag"], case["F"].D, case["F"].B, NSTEPS,
@@ -221,9 +267,10 @@ def test_ift_mode_matches_the_converged_iteration(G):
     iH = O.horizon_index(oc, A09)
     x = [dev(a) for a in (P.r, P.th, P.u1, P.u2, P.u3)]
     tag = dev(P.tag.view(np.int32))
-    L0, g0, f0 = G.adjoint_grad(ctx, x, tag, F.D, F.B, 10, iH)
-    L1, g1, f1 = G.adjoint_grad(ctx, x, tag, F.D, F.B, 10, iH, ift=True)
+    L0, g0, f0, a0 = G.adjoint_grad(ctx, x, tag, F.D, F.B, 10, iH, want_spin=True)
+    L1, g1, f1, a1 = G.adjoint_grad(ctx, x, tag, F.D, F.B, 10, iH, ift=True, want_spin=True)
     assert L1 == pytest.approx(L0, rel=1e-13)   # the deposit's atomics may order sums differently
+    assert a1 == pytest.approx(a0, rel=1e-8)
     errs = [relerr(host(a), host(b)) for a, b in zip(g1 + f1, g0 + f0)]
     print("ift vs unrolled:", " ".join(f"{e:.1e}" for e in errs))
     assert max(errs) < 1e-8
