@@ -23,9 +23,12 @@
 // source's particles in slot order, so
 //   6. count, per old cell, the particles going in each direction;
 //   7. destination counts = sums over the 9 sources; exclusive scan;
-//   8. each particle goes straight to offset[k] + (particles of lower sources
-//      into k) + (its rank among its cell's particles in that direction),
-//      moving its data once, with no atomics and no fix-up.
+//   8. each particle's slot index goes straight to offset[k] + (particles of
+//      lower sources into k) + (its rank among its cell's particles in that
+//      direction), with no atomics and no fix-up;
+// and step 5's gather moves the data, as for the general path.  Placing only
+// the indices keeps the per-cell bookkeeping off the particle data: the
+// gather's reads are nearly sequential runs and its writes sequential.
 // The count pass checks the precondition (every key a neighbour of its
 // segment, live count = the previous sort's) and raises a device flag when
 // it fails; the general kernels then run instead.  Every kernel of both paths
@@ -321,21 +324,49 @@ struct GatherArgs {
     int64_t *count_out;
 };
 
+// q[s] = p[perm[s]] for the live slots, DEAD tags past them.  Each thread
+// moves four slots per round (their permutation entries first, then all
+// their loads) so that enough loads are in flight to cover the latency.
 template <typename T>
-__global__ void gather_kernel(GatherArgs A, int nfields, const int32_t *flag)
+__global__ void __launch_bounds__(256) gather_kernel(GatherArgs A, int nfields, const int32_t *flag)
 {
     if (general_off(flag)) return;
-    int64_t live = *A.live;
-    int64_t s0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t live = *A.live;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t s0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (s0 == 0 && A.count_out) *A.count_out = live;
-    for (int64_t s = s0; s < A.nmax; s += (int64_t)gridDim.x * blockDim.x) {
-        if (s < live) {
-            int32_t src = A.perm[s];
-            for (int k = 0; k < nfields; ++k) ((T *)A.dst[k])[s] = ((const T *)A.src[k])[src];
-            A.tag_dst[s] = A.tag_src[src];
-            if (A.cell_dst) A.cell_dst[s] = A.cell_src[src];
-        } else {
-            A.tag_dst[s] = DEAD;
+    for (int64_t base = s0; base < A.nmax; base += 4 * stride) {
+        int32_t src[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int64_t s = base + u * stride;
+            src[u] = s < live ? A.perm[s] : -1;
+        }
+        T v[4][5];
+        uint32_t tg[4];
+        int32_t cl[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            if (src[u] < 0) continue;
+#pragma unroll
+            for (int k = 0; k < 5; ++k)
+                if (k < nfields) v[u][k] = ((const T *)A.src[k])[src[u]];
+            tg[u] = A.tag_src[src[u]];
+            if (A.cell_dst) cl[u] = A.cell_src[src[u]];
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int64_t s = base + u * stride;
+            if (s >= A.nmax) break;
+            if (src[u] < 0) {
+                A.tag_dst[s] = DEAD;
+                continue;
+            }
+#pragma unroll
+            for (int k = 0; k < 5; ++k)
+                if (k < nfields) ((T *)A.dst[k])[s] = v[u][k];
+            A.tag_dst[s] = tg[u];
+            if (A.cell_dst) A.cell_dst[s] = cl[u];
         }
     }
 }
@@ -381,14 +412,52 @@ __device__ __forceinline__ int dir_of(int k, int s, int si, int nr)
     return (dj + 1) * 3 + (di + 1);
 }
 
+// The neighbour-sort passes walk the old cells in tasks of TASK_CELLS
+// consecutive cells per warp: the task's particles [off[s0], off[s0 + m]) are
+// one contiguous stream of 32-particle chunks (no pipeline restart at each
+// cell), and a particle's old cell is found among the task's segment starts,
+// which the lanes hold (lane l: off[s0 + l]).
+constexpr int TASK_CELLS = 32;
+
+// index (0 .. m-1) of the task cell whose segment holds slot b + lane: the
+// number of segment starts off[s0 + l], 1 <= l < m, at or before it (empty
+// segments share their start with the next one, so each counts).  A chunk
+// rarely holds a segment start, so the starts inside it are visited one by
+// one.  All 32 lanes call with the same b.
+__device__ __forceinline__ int task_cell(int b, int lane, int o, int m)
+{
+    const unsigned FULL = 0xffffffffu;
+    const bool own = lane >= 1 && lane < m;
+    int c = __popc(__ballot_sync(FULL, own && o <= b));
+    unsigned inside = __ballot_sync(FULL, own && o > b && o - b < 32);
+    const int p = b + lane;
+    while (inside) {
+        const int l = __ffs(inside) - 1;
+        inside &= inside - 1;
+        c += p >= __shfl_sync(FULL, o, l);
+    }
+    return c;
+}
+
+// column of cell s0 + c given the column s0i of s0
+__device__ __forceinline__ int task_col(int s0i, int c, int nr)
+{
+    int si = s0i + c;
+    while (si >= nr) si -= nr;
+    return si;
+}
+
 // step 6: per old cell s (segment [off[s], off[s+1]) of the previous sort's
 // output), the particles moving in each direction; dead keys are dropped.
-// Raises *flag if a key is not a neighbour or the live count changed.
+// Raises *flag if a key is not a neighbour or the live count changed.  Keys
+// are loaded four chunks at a time (a short loop body needs the loads in
+// flight to cover the memory latency).
 __global__ void __launch_bounds__(256) count9_kernel(const int32_t *off, const int32_t *keys, int nr, int ncell,
                                                      const int64_t *d_count, int64_t nmax, int32_t *cnt9,
                                                      int32_t *flag)
 {
-    __shared__ int cnt_sh[8][16];
+    __shared__ int cnt_sh[8][TASK_CELLS * 9];
+    const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -397,30 +466,49 @@ __global__ void __launch_bounds__(256) count9_kernel(const int32_t *off, const i
         int64_t n = d_count ? *d_count : nmax;
         if (n != (int64_t)off[ncell] || n > nmax) atomicExch(flag, 1);
     }
-    for (int64_t s = wid; s < ncell; s += nw) {
-        const int start = off[s], end = off[s + 1];
-        const int si = (int)(s % nr);
-        if (lane < 9) cnt[lane] = 0;
+    const int64_t ntask = ((int64_t)ncell + TASK_CELLS - 1) / TASK_CELLS;
+    for (int64_t t = wid; t < ntask; t += nw) {
+        const int64_t s0 = t * TASK_CELLS;
+        const int m = (int)((int64_t)ncell - s0 < TASK_CELLS ? (int64_t)ncell - s0 : TASK_CELLS);
+        const int o = off[s0 + (lane < m ? lane : m)];
+        const int end = off[s0 + m];
+        const int beg = __shfl_sync(FULL, o, 0);
+        const int s0i = (int)(s0 % nr);
+        for (int e = lane; e < TASK_CELLS * 9; e += 32) cnt[e] = 0;
         __syncwarp();
         bool bad = false;
-        for (int b = start; b < end; b += 32) {
-            int p = b + lane;
-            int cls = -1;
-            if (p < end) {
-                int k = keys[p];
-                if (k >= 0 && k < ncell) {
-                    cls = dir_of(k, (int)s, si, nr);
-                    bad |= cls < 0;
-                } else {
-                    bad |= k != ncell;
-                }
+        for (int b = beg; b < end; b += 4 * 32) {
+            int kk[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int p = b + u * 32 + lane;
+                kk[u] = p < end ? keys[p] : -2;
             }
-            unsigned peers = __match_any_sync(0xffffffffu, cls);
-            if (cls >= 0 && lane == __ffs(peers) - 1) cnt[cls] += __popc(peers);
-            __syncwarp();
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int p = b + u * 32 + lane;
+                if (b + u * 32 >= end) break;  // warp-uniform
+                const int c = task_cell(b + u * 32, lane, o, m);
+                int key2 = -1;
+                if (p < end) {
+                    const int k = kk[u];
+                    if (k >= 0 && k < ncell) {
+                        const int cls = dir_of(k, (int)(s0 + c), task_col(s0i, c, nr), nr);
+                        bad |= cls < 0;
+                        if (cls >= 0) key2 = c * 9 + cls;
+                    } else {
+                        bad |= k != ncell;
+                    }
+                }
+                const unsigned peers = __match_any_sync(FULL, key2);
+                if (key2 >= 0 && lane == __ffs(peers) - 1) cnt[key2] += __popc(peers);
+                __syncwarp();
+            }
         }
-        if (lane < 9) cnt9[(int64_t)lane * ncell + s] = cnt[lane];
-        if (__any_sync(0xffffffffu, bad) && lane == 0) atomicExch(flag, 1);
+        if (lane < m)
+#pragma unroll
+            for (int d = 0; d < 9; ++d) cnt9[(int64_t)d * ncell + s0 + lane] = cnt[lane * 9 + d];
+        if (__any_sync(FULL, bad) && lane == 0) atomicExch(flag, 1);
         __syncwarp();
     }
 }
@@ -481,98 +569,67 @@ __global__ void base9_kernel(const int32_t *cnt9, int32_t *base9, const int32_t 
     }
 }
 
-struct NbrArgs {
-    int nr, nth;
-    int64_t nmax;
-    const int32_t *off_old, *off_new, *base9, *keys, *flag;
-    const void *src[5];
-    void *dst[5];
-    const uint32_t *tag_src;
-    uint32_t *tag_dst;
-    int32_t *cell_dst;  // FP32 form: the new cell key
-    int64_t *count_out;
-};
 
-// step 8: stable placement, one warp per old cell; the particle data moves once
-template <typename T>
-__global__ void __launch_bounds__(256) neighbour_scatter_kernel(NbrArgs A)
+// step 8: stable placement of the indices: perm[dst] = src, the gather then
+// moves the particle data (one pass with coalesced reads of nearly
+// sequential runs).  A warp streams the keys of TASK_CELLS consecutive old
+// cells; each particle takes the first free slot of its (old cell,
+// direction) run (run counters in shared memory, started at base9), equal
+// (cell, direction) lanes of a chunk taking consecutive slots in lane order.
+__global__ void __launch_bounds__(256) neighbour_perm_kernel(const int32_t *off_old, const int32_t *base9,
+                                                             const int32_t *keys, int nr, int nth, int64_t nmax,
+                                                             int32_t *perm, const int32_t *flag)
 {
-    if (*A.flag) return;
-    __shared__ int run_sh[8][16];
+    if (*flag) return;
+    __shared__ int run_sh[8][TASK_CELLS * 9];
+    const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     int *run = run_sh[wib];
-    const int64_t ncell = (int64_t)A.nr * A.nth;
+    const int64_t ncell = (int64_t)nr * nth;
     const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    // the next cell's segment bounds and first slots are fetched one cell ahead
-    int nstart = 0, nend = 0, nbase = 0;
-    if (wid < ncell) {
-        nstart = A.off_old[wid];
-        nend = A.off_old[wid + 1];
-        if (lane < 9) nbase = A.base9[(int64_t)lane * ncell + wid];
-    }
-    for (int64_t s = wid; s < ncell; s += nw) {
-        const int start = nstart, end = nend, base = nbase;
-        const int64_t sn = s + nw;
-        if (sn < ncell) {
-            nstart = A.off_old[sn];
-            nend = A.off_old[sn + 1];
-            if (lane < 9) nbase = A.base9[(int64_t)lane * ncell + sn];
-        }
-        if (start == end) continue;
-        const int si = (int)(s % A.nr);
-        if (lane < 9) run[lane] = base;
+    const int64_t ntask = (ncell + TASK_CELLS - 1) / TASK_CELLS;
+    for (int64_t t = wid; t < ntask; t += nw) {
+        const int64_t s0 = t * TASK_CELLS;
+        const int m = (int)(ncell - s0 < TASK_CELLS ? ncell - s0 : TASK_CELLS);
+        const int o = off_old[s0 + (lane < m ? lane : m)];
+        const int end = off_old[s0 + m];
+        const int beg = __shfl_sync(FULL, o, 0);
+        if (beg >= end) continue;  // warp-uniform
+        if (lane < m)
+#pragma unroll
+            for (int d = 0; d < 9; ++d) run[lane * 9 + d] = base9[(int64_t)d * ncell + s0 + lane];
+        const int s0i = (int)(s0 % nr);
         __syncwarp();
-        // software pipeline: the next 32 particles are loaded while the
-        // current ones are placed (two chunks of loads in flight per warp)
-        int kn = ncell;
-        T vn[5];
-        uint32_t tn = 0;
-        {
-            int p = start + lane;
-            if (p < end) {
-                kn = A.keys[p];
+        for (int b = beg; b < end; b += 4 * 32) {
+            int kk[4];
 #pragma unroll
-                for (int f = 0; f < 5; ++f) vn[f] = ((const T *)A.src[f])[p];
-                tn = A.tag_src[p];
+            for (int u = 0; u < 4; ++u) {
+                const int p = b + u * 32 + lane;
+                kk[u] = p < end ? keys[p] : -2;
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                if (b + u * 32 >= end) break;  // warp-uniform
+                const int p = b + u * 32 + lane;
+                const int c = task_cell(b + u * 32, lane, o, m);
+                const int k = kk[u];
+                int key2 = -1;
+                if (p < end && k >= 0 && k < ncell) {
+                    const int cls = dir_of(k, (int)(s0 + c), task_col(s0i, c, nr), nr);
+                    if (cls >= 0) key2 = c * 9 + cls;
+                }
+                const unsigned peers = __match_any_sync(FULL, key2);
+                int dst = 0;
+                if (key2 >= 0) dst = run[key2] + __popc(peers & ((1u << lane) - 1u));
+                __syncwarp();
+                if (key2 >= 0 && lane == __ffs(peers) - 1) run[key2] += __popc(peers);
+                __syncwarp();
+                if (key2 >= 0 && dst >= 0 && dst < nmax) perm[dst] = p;
             }
         }
-        for (int b = start; b < end; b += 32) {
-            int p = b + lane;
-            int k = kn;
-            T v[5];
-#pragma unroll
-            for (int f = 0; f < 5; ++f) v[f] = vn[f];
-            uint32_t tg = tn;
-            int q = p + 32;
-            kn = ncell;
-            if (q < end) {
-                kn = A.keys[q];
-#pragma unroll
-                for (int f = 0; f < 5; ++f) vn[f] = ((const T *)A.src[f])[q];
-                tn = A.tag_src[q];
-            }
-            int cls = -1;
-            if (p < end && k >= 0 && k < ncell) cls = dir_of(k, (int)s, si, A.nr);
-            unsigned peers = __match_any_sync(0xffffffffu, cls);
-            int dst = 0;
-            if (cls >= 0) dst = run[cls] + __popc(peers & ((1u << lane) - 1u));
-            __syncwarp();
-            if (cls >= 0 && lane == __ffs(peers) - 1) run[cls] += __popc(peers);
-            __syncwarp();
-            if (cls >= 0) {
-#pragma unroll
-                for (int f = 0; f < 5; ++f) ((T *)A.dst[f])[dst] = v[f];
-                A.tag_dst[dst] = tg;
-                if (A.cell_dst) A.cell_dst[dst] = k;
-            }
-        }
+        __syncwarp();
     }
-    // slots past the new live count are dead; the live count goes back to the set
-    const int64_t live = A.off_new[ncell];
-    const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t0 == 0 && A.count_out) *A.count_out = live;
-    for (int64_t q = live + t0; q < A.nmax; q += (int64_t)gridDim.x * blockDim.x) A.tag_dst[q] = DEAD;
 }
 
 }  // namespace
@@ -692,31 +749,10 @@ cudaError_t launch_sort_step(grpic_ctx *ctx, grpic_particles *p, grpic_particles
     add_back<<<(unsigned)((nscan + 255) / 256), 256, 0, s>>>(ctx->d_offset, ctx->d_blocksum, nscan);
     if (neighbour && ctx->g.nr >= 3 && p->n > 0) {
         base9_kernel<<<grid, 256, 0, s>>>(ctx->d_cnt9, ctx->d_base9, ctx->d_offset, ctx->g.nr, ctx->g.nth, flag);
-        NbrArgs A;
-        A.nr = ctx->g.nr;
-        A.nth = ctx->g.nth;
-        A.nmax = p->n;
-        A.off_old = ctx->d_offset_prev;
-        A.off_new = ctx->d_offset;
-        A.base9 = ctx->d_base9;
-        A.keys = ctx->d_keys;
-        A.flag = flag;
-        void *sp[5] = {p->x1, p->x2, p->u1, p->u2, p->u3};
-        void *dp[5] = {q->x1, q->x2, q->u1, q->u2, q->u3};
-        for (int k = 0; k < 5; ++k) {
-            A.src[k] = sp[k];
-            A.dst[k] = dp[k];
-        }
-        A.tag_src = p->tag;
-        A.tag_dst = q->tag;
-        A.cell_dst = (ctx->prm.precision == 32) ? q->cell : nullptr;
-        A.count_out = p->d_count;
-        if (ctx->prm.precision == 64)
-            neighbour_scatter_kernel<double><<<grid, 256, 0, s>>>(A);
-        else
-            neighbour_scatter_kernel<float><<<grid, 256, 0, s>>>(A);
+        neighbour_perm_kernel<<<grid, 256, 0, s>>>(ctx->d_offset_prev, ctx->d_base9, ctx->d_keys, ctx->g.nr,
+                                                   ctx->g.nth, p->n, ctx->d_perm, flag);
     }
-    // general path (skipped on the device when the neighbour sort applied)
+    // general path to the permutation (skipped on the device when the neighbour sort applied)
     cudaMemsetAsync(ctx->d_cursor, 0, sizeof(int32_t) * nscan, s);
     int32_t *nbig = ctx->d_cursor + nscan;
     cudaMemsetAsync(nbig, 0, sizeof(int32_t), s);
@@ -747,11 +783,12 @@ cudaError_t launch_sort_step(grpic_ctx *ctx, grpic_particles *p, grpic_particles
     G.dst[5] = nullptr;
     G.cell_src = (ctx->prm.precision == 32) ? p->cell : nullptr;
     G.cell_dst = (ctx->prm.precision == 32) ? q->cell : nullptr;
+    // both paths leave the permutation in d_perm: one gather moves the data
     if (p->n > 0) {
         if (ctx->prm.precision == 64)
-            gather_kernel<double><<<gp, 256, 0, s>>>(G, 5, flag);
+            gather_kernel<double><<<gp, 256, 0, s>>>(G, 5, nullptr);
         else
-            gather_kernel<float><<<gp, 256, 0, s>>>(G, 5, flag);
+            gather_kernel<float><<<gp, 256, 0, s>>>(G, 5, nullptr);
     }
     return cudaGetLastError();
 }

@@ -110,7 +110,9 @@ __device__ __forceinline__ void window_add(int v, T val, int i0, int j0, int nth
 //   J^r A_r (k, l)     = -qw/(2dt) P_r(k) (S1_t + S0_t)(l),  P_r(k) = sum_{k'<=k} (S1_r - S0_r)(k')
 //   J^th A_th (k, l)   = -qw/(2dt) (S1_r + S0_r)(k) P_t(l)
 //   J^ph dV (k, l)     = qw dphi/dt (S1r S1t/3 + S1r S0t/6 + S0r S1t/6 + S0r S0t/3)(k, l)
-// (Eq. j-phi-deposit), k, l = 0..3 standing for columns/rows -1..2.
+// (Eq. j-phi-deposit), k, l = 0..3 standing for columns/rows -1..2.  The
+// start point lies in its cell, so its weights are (0, 1 - a, a, 0) and
+// only the end point's four weights per dimension need evaluating.
 template <typename T>
 __device__ __forceinline__ T cic_weight(T d)
 {
@@ -121,12 +123,11 @@ __device__ __forceinline__ T cic_weight(T d)
 template <typename T>
 __device__ __forceinline__ void esirkepov_window(T a1, T a2, T b1, T b2, T qw, T dphi, T dt, T win[NWIN])
 {
-    T S0r[4], S1r[4], S0t[4], S1t[4];
+    const T S0r[4] = {T(0), T(1) - a1, a1, T(0)}, S0t[4] = {T(0), T(1) - a2, a2, T(0)};
+    T S1r[4], S1t[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-        S0r[k] = cic_weight<T>(a1 - T(k - 1));
         S1r[k] = cic_weight<T>(b1 - T(k - 1));
-        S0t[k] = cic_weight<T>(a2 - T(k - 1));
         S1t[k] = cic_weight<T>(b2 - T(k - 1));
     }
     const T cr = -qw / (T(2) * dt);
@@ -135,22 +136,29 @@ __device__ __forceinline__ void esirkepov_window(T a1, T a2, T b1, T b2, T qw, T
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
         Pr += S1r[k] - S0r[k];
+        const T c = cr * Pr;
 #pragma unroll
-        for (int l = 0; l < 4; ++l) win[k * 4 + l] = cr * Pr * (S1t[l] + S0t[l]);
+        for (int l = 0; l < 4; ++l) win[k * 4 + l] = c * (S1t[l] + S0t[l]);
     }
     T Pt = T(0);
 #pragma unroll
     for (int l = 0; l < 3; ++l) {
         Pt += S1t[l] - S0t[l];
+        const T c = cr * Pt;
 #pragma unroll
-        for (int k = 0; k < 4; ++k) win[12 + k * 3 + l] = cr * (S1r[k] + S0r[k]) * Pt;
+        for (int k = 0; k < 4; ++k) win[12 + k * 3 + l] = c * (S1r[k] + S0r[k]);
+    }
+    // J^phi = S1r (x) cp (S1t/3 + S0t/6) + S0r (x) cp (S1t/6 + S0t/3)
+    T cU[4], cV[4];
+#pragma unroll
+    for (int l = 0; l < 4; ++l) {
+        cU[l] = cp * (S1t[l] * (T(1) / T(3)) + S0t[l] * (T(1) / T(6)));
+        cV[l] = cp * (S1t[l] * (T(1) / T(6)) + S0t[l] * (T(1) / T(3)));
     }
 #pragma unroll
     for (int k = 0; k < 4; ++k)
 #pragma unroll
-        for (int l = 0; l < 4; ++l)
-            win[24 + k * 4 + l] = cp * (S1r[k] * S1t[l] * (T(1) / T(3)) + S1r[k] * S0t[l] * (T(1) / T(6)) +
-                                        S0r[k] * S1t[l] * (T(1) / T(6)) + S0r[k] * S0t[l] * (T(1) / T(3)));
+        for (int l = 0; l < 4; ++l) win[24 + k * 4 + l] = S1r[k] * cU[l] + S0r[k] * cV[l];
 }
 
 // Deposit of a warp's windows: the lanes are grouped by start cell and each
