@@ -223,6 +223,17 @@ grpic_status grpic_get_areas(grpic_ctx *ctx, double *const out[6], int64_t ld, v
  * word, and return the first device error recorded (GRPIC_OK if none). */
 grpic_status grpic_sync(grpic_ctx *ctx, void *stream);
 
+/* Phase timing of grpic_step: with enable != 0, every step of grpic_step
+ * records CUDA events on its stream around the push (fused deposit), the
+ * field update and the sort; enable = 0 stops it (grpic_step_graph's
+ * captured steps are never timed).  grpic_get_timing waits for the recorded
+ * events and writes out[0..2] = the summed milliseconds of push, field update
+ * and sort over the steps since the last read or enable, and *nsteps their
+ * number, then starts a new sum.  Events are created as needed (not inside a
+ * capture). */
+grpic_status grpic_set_timing(grpic_ctx *ctx, int enable);
+grpic_status grpic_get_timing(grpic_ctx *ctx, double out[3], int64_t *nsteps);
+
 /* ------------------------------------------------------------------------ */
 /* Differentiable form (FP64 contexts only).  The objective is the time-     */
 /* averaged radial Poynting flux of the 3+1 fields (S = E x H, Sec. 2.1's    */

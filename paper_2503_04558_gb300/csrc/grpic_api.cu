@@ -117,7 +117,10 @@ grpic_status ensure_particle_scratch(grpic_ctx *ctx, int64_t n)
     return GRPIC_OK;
 }
 
-grpic_status sort_impl(grpic_ctx *ctx, grpic_particles *p, grpic_particles *q, cudaStream_t s)
+// materialize = false (inside grpic_step, a push follows): the order is left
+// in ctx->d_perm and the next push reads the particles through it
+grpic_status sort_impl(grpic_ctx *ctx, grpic_particles *p, grpic_particles *q, cudaStream_t s,
+                       bool materialize = true)
 {
     int64_t ncell = (int64_t)ctx->g.nr * ctx->g.nth;
     grpic_status st = ensure_particle_scratch(ctx, p->n);
@@ -139,11 +142,16 @@ grpic_status sort_impl(grpic_ctx *ctx, grpic_particles *p, grpic_particles *q, c
         if (e != cudaSuccess) return cuda_fail(ctx, e, "histogram");
         ctx->hist_valid = 1;
     }
-    cudaError_t e = launch_sort_step(ctx, p, q, neighbour, !ctx->hist_valid, s);
+    cudaError_t e = launch_sort_step(ctx, p, q, neighbour, !ctx->hist_valid, materialize, s);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "sort");
     ctx->keys_valid = 0;
     ctx->hist_valid = 0;
     std::swap(ctx->d_offset, ctx->d_offset_prev);  // segments of the new order
+    if (!materialize) {
+        ctx->pending_perm = 1;
+        ctx->pending_tag = p->tag;
+        return GRPIC_OK;
+    }
     // the sorted state now lives in q's arrays: swap the array pointers
     std::swap(p->x1, q->x1);
     std::swap(p->x2, q->x2);
@@ -157,9 +165,40 @@ grpic_status sort_impl(grpic_ctx *ctx, grpic_particles *p, grpic_particles *q, c
     return GRPIC_OK;
 }
 
-grpic_status push_impl(grpic_ctx *ctx, grpic_particles *p, grpic_fields *f, bool for_sort, cudaStream_t s)
+grpic_status push_impl(grpic_ctx *ctx, grpic_particles *p, grpic_fields *f, bool for_sort, cudaStream_t s,
+                       grpic_particles *scratch = nullptr)
 {
     int64_t ncell = (int64_t)ctx->g.nr * ctx->g.nth;
+    if (ctx->pending_perm) {
+        // the last sort left its order in d_perm: read p through it and write
+        // the pushed particles, in that order, into scratch's arrays
+        if (!scratch || p->tag != ctx->pending_tag) return fail(ctx, GRPIC_EINVAL, "push: a sort's order is pending");
+        ctx->pending_perm = 0;
+        size_t bytes = (size_t)(ctx->g.nth + 1) * f->ld * fsize(ctx);
+        for (int k = 0; k < 3; ++k) cudaMemsetAsync(f->J[k], 0, bytes, s);
+        grpic_particles out = *scratch;
+        out.n = p->n;
+        out.d_count = p->d_count;
+        const int32_t *live = ctx->d_offset_prev + ncell;
+        cudaError_t e = (ctx->prm.precision == 64)
+                            ? launch_push64(ctx, p, &out, ctx->d_perm, live, f, false, s)
+                            : launch_push32(ctx, p, &out, ctx->d_perm, live, f, false, s);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "push");
+        std::swap(p->x1, scratch->x1);
+        std::swap(p->x2, scratch->x2);
+        std::swap(p->u1, scratch->u1);
+        std::swap(p->u2, scratch->u2);
+        std::swap(p->u3, scratch->u3);
+        std::swap(p->tag, scratch->tag);
+        std::swap(p->cell, scratch->cell);
+        // p now holds the sorted order pushed once: the next sort is a neighbour sort
+        ctx->sorted_tag = p->tag;
+        ctx->pushes_since_sort = 1;
+        ctx->keys_valid = 1;
+        ctx->hist_valid = 0;
+        ctx->keys_tag = p->tag;
+        return GRPIC_OK;
+    }
     // the histogram serves the general sort only: a sort that will be a
     // neighbour sort rebuilds it from the keys if the device falls back
     const bool neighbour_next = p->n > 0 && p->tag && p->tag == ctx->sorted_tag && ctx->pushes_since_sort == 0;
@@ -169,8 +208,8 @@ grpic_status push_impl(grpic_ctx *ctx, grpic_particles *p, grpic_fields *f, bool
     size_t bytes = (size_t)(ctx->g.nth + 1) * f->ld * fsize(ctx);
     for (int k = 0; k < 3; ++k) cudaMemsetAsync(f->J[k], 0, bytes, s);
     if (histogram) cudaMemsetAsync(ctx->d_count, 0, sizeof(int32_t) * (ncell + 1), s);
-    cudaError_t e = (ctx->prm.precision == 64) ? launch_push64(ctx, p, f, histogram, s)
-                                                : launch_push32(ctx, p, f, histogram, s);
+    cudaError_t e = (ctx->prm.precision == 64) ? launch_push64(ctx, p, p, nullptr, nullptr, f, histogram, s)
+                                                : launch_push32(ctx, p, p, nullptr, nullptr, f, histogram, s);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "push");
     ctx->keys_valid = 1;  // the push writes every slot's key
     ctx->hist_valid = histogram ? 1 : 0;
@@ -348,6 +387,53 @@ grpic_status grpic_sort(grpic_ctx *ctx, grpic_particles *p, grpic_particles *scr
     return sort_impl(ctx, p, scratch, S(stream));
 }
 
+// one step: push (through a pending permutation if the last sort left one),
+// field update, and the sort when due; materialize = false leaves the sort's
+// order pending for the next step's push
+static cudaEvent_t *timing_slot(grpic_ctx *ctx)
+{
+    if (!ctx->timing) return nullptr;
+    if (!ctx->tevents) ctx->tevents = new std::vector<cudaEvent_t>();
+    std::vector<cudaEvent_t> &v = *ctx->tevents;
+    const size_t need = 4 * (size_t)(ctx->tsteps + 1);
+    while (v.size() < need) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+        v.push_back(e);
+    }
+    return &v[4 * (size_t)ctx->tsteps];
+}
+
+static grpic_status step_one(grpic_ctx *ctx, grpic_particles *p, grpic_particles *scratch, grpic_fields *f,
+                             bool materialize, cudaStream_t s, bool timed = true)
+{
+    const int every = ctx->prm.sort_every;
+    const bool sort_now = every > 0 && ((ctx->step_count + 1) % every == 0);
+    cudaEvent_t *ev = timed ? timing_slot(ctx) : nullptr;
+    if (ev) cudaEventRecord(ev[0], s);
+    grpic_status st = push_impl(ctx, p, f, sort_now, s, scratch);
+    if (ev) cudaEventRecord(ev[1], s);
+    if (!st) st = field_impl(ctx, f, s);
+    if (ev) cudaEventRecord(ev[2], s);
+    if (!st && sort_now) st = sort_impl(ctx, p, scratch, s, materialize);
+    if (ev) {
+        cudaEventRecord(ev[3], s);
+        ctx->tsteps++;
+    }
+    if (!st) ctx->step_count++;
+    return st;
+}
+
+// a failed call leaves the particle data valid but unsorted
+static grpic_status drop_pending(grpic_ctx *ctx, grpic_status st)
+{
+    if (st && ctx->pending_perm) {
+        ctx->pending_perm = 0;
+        ctx->sorted_tag = nullptr;
+    }
+    return st;
+}
+
 grpic_status grpic_step(grpic_ctx *ctx, grpic_particles *p, grpic_particles *scratch, grpic_fields *f, int nsteps,
                         void *stream)
 {
@@ -356,21 +442,17 @@ grpic_status grpic_step(grpic_ctx *ctx, grpic_particles *p, grpic_particles *scr
     if (nsteps < 0 || !particles_ok(ctx, p) || !fields_ok(ctx, f) ||
         (every > 0 && (!particles_ok(ctx, scratch) || scratch->capacity < p->n)))
         return fail(ctx, GRPIC_EINVAL, "grpic_step: bad arguments");
-    for (int k = 0; k < nsteps; ++k) {
-        bool sort_now = every > 0 && ((ctx->step_count + 1) % every == 0);
-        grpic_status st = push_impl(ctx, p, f, sort_now, S(stream));
-        if (st) return st;
-        st = field_impl(ctx, f, S(stream));
-        if (st) return st;
-        if (sort_now) {
-            st = sort_impl(ctx, p, scratch, S(stream));
-            if (st) return st;
-        }
-        ctx->step_count++;
-    }
-    return GRPIC_OK;
+    grpic_status st = GRPIC_OK;
+    // a sort followed by this call's next push leaves only its order (the
+    // push reads through it); the call's last sort moves the data
+    for (int k = 0; k < nsteps && !st; ++k) st = step_one(ctx, p, scratch, f, k == nsteps - 1, S(stream));
+    return drop_pending(ctx, st);
 }
 
+// Steps 2 .. nsteps-1 of a run run as replays of a captured graph of two
+// steps whose sorts leave their order pending (each push reads through the
+// previous sort's permutation into the other buffer, so two steps bring the
+// buffers back): the data moves once per call, in the last step's sort.
 grpic_status grpic_step_graph(grpic_ctx *ctx, grpic_particles *p, grpic_particles *scratch, grpic_fields *f,
                               int nsteps, void *stream)
 {
@@ -378,63 +460,76 @@ grpic_status grpic_step_graph(grpic_ctx *ctx, grpic_particles *p, grpic_particle
     if (nsteps < 0 || ctx->prm.sort_every != 1 || !particles_ok(ctx, p) || !fields_ok(ctx, f) ||
         !particles_ok(ctx, scratch) || scratch->capacity < p->n)
         return fail(ctx, GRPIC_EINVAL, "grpic_step_graph: bad arguments (sort_every must be 1)");
-    int done = 0;
+    if (nsteps < 4) return grpic_step(ctx, p, scratch, f, nsteps, stream);
     grpic_status st = GRPIC_OK;
-    // start from a sort's output so that both captured sorts are neighbour sorts
-    if (nsteps > 0 && !(ctx->sorted_tag == p->tag && ctx->pushes_since_sort == 0)) {
-        st = grpic_step(ctx, p, scratch, f, 1, stream);
-        if (st) return st;
-        done = 1;
+    int done = 0;
+    // head: a plain step if the particles are not a sort's output, then one
+    // step that leaves its sort pending
+    if (!(ctx->sorted_tag == p->tag && ctx->pushes_since_sort == 0)) {
+        st = step_one(ctx, p, scratch, f, true, S(stream));
+        done++;
     }
-    const int pairs = (nsteps - done) / 2;
-    if (pairs > 0) {
+    if (!st) {
+        st = step_one(ctx, p, scratch, f, false, S(stream));
+        done++;
+    }
+    const int steady = nsteps - done - 1;  // the last step materializes
+    const int pairs = steady / 2;
+    if (!st && pairs > 0) {
         const void *key[24] = {p->x1, p->x2, p->u1, p->u2, p->u3, p->tag, p->cell, p->d_count,
                                scratch->x1, scratch->x2, scratch->u1, scratch->u2, scratch->u3, scratch->tag,
                                scratch->cell, f->D[0], f->D[1], f->D[2], f->B[0], f->B[1], f->B[2], f->J[0], f->J[1],
                                f->J[2]};
         bool same = ctx->graph_exec && memcmp(key, ctx->graph_key, sizeof key) == 0 &&
-                    ctx->keys_cap >= p->n && ctx->fscratch_ld == f->ld;
+                    ctx->keys_cap >= p->n && ctx->fscratch_ld == f->ld && ctx->graph_offset == ctx->d_offset;
         if (!same) {
             if (ctx->graph_exec) cudaGraphExecDestroy(ctx->graph_exec);
             ctx->graph_exec = nullptr;
             cudaError_t e = cudaSuccess;
             if (!ctx->cap_stream) e = cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking);
-            if (e != cudaSuccess) return cuda_fail(ctx, e, "graph stream");
-            // everything the two steps allocate, allocated before the capture
+            if (e != cudaSuccess) return drop_pending(ctx, cuda_fail(ctx, e, "graph stream"));
+            // everything the two steps allocate is allocated already (the head
+            // steps ran); the capture must wait for them
             st = ensure_particle_scratch(ctx, p->n);
             if (!st) st = ensure_field_scratch(ctx, f->ld);
-            if (st) return st;
-            cudaDeviceSynchronize();
+            if (st) return drop_pending(ctx, st);
+            cudaStreamSynchronize(S(stream));
             const int64_t sc = ctx->step_count;
             e = cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal);
-            if (e != cudaSuccess) return cuda_fail(ctx, e, "graph capture");
-            st = grpic_step(ctx, p, scratch, f, 2, ctx->cap_stream);
+            if (e != cudaSuccess) return drop_pending(ctx, cuda_fail(ctx, e, "graph capture"));
+            st = step_one(ctx, p, scratch, f, false, ctx->cap_stream, false);
+            if (!st) st = step_one(ctx, p, scratch, f, false, ctx->cap_stream, false);
             cudaGraph_t g = nullptr;
             e = cudaStreamEndCapture(ctx->cap_stream, &g);
             ctx->step_count = sc;
             if (st || e != cudaSuccess) {
                 if (g) cudaGraphDestroy(g);
-                return st ? st : cuda_fail(ctx, e, "graph capture");
+                return drop_pending(ctx, st ? st : cuda_fail(ctx, e, "graph capture"));
             }
             e = cudaGraphInstantiate(&ctx->graph_exec, g, 0);
             cudaGraphDestroy(g);
             if (e != cudaSuccess) {
                 ctx->graph_exec = nullptr;
-                return cuda_fail(ctx, e, "graph instantiate");
+                return drop_pending(ctx, cuda_fail(ctx, e, "graph instantiate"));
             }
             memcpy(ctx->graph_key, key, sizeof key);
-            // the capture left the host bookkeeping of two steps (pointers back
-            // in place, the last sort's output current): the same after a replay
+            ctx->graph_offset = ctx->d_offset;
+            // the capture left the host bookkeeping of two steps: pointers, the
+            // offsets' double buffer and the pending order as before them,
+            // which is also the state after each replay
         }
         for (int k = 0; k < pairs; ++k) {
             cudaError_t e = cudaGraphLaunch(ctx->graph_exec, S(stream));
-            if (e != cudaSuccess) return cuda_fail(ctx, e, "graph launch");
+            if (e != cudaSuccess) return drop_pending(ctx, cuda_fail(ctx, e, "graph launch"));
             ctx->step_count += 2;
         }
         done += 2 * pairs;
     }
-    if (done < nsteps) st = grpic_step(ctx, p, scratch, f, nsteps - done, stream);
-    return st;
+    while (!st && done < nsteps) {
+        st = step_one(ctx, p, scratch, f, done == nsteps - 1, S(stream));
+        done++;
+    }
+    return drop_pending(ctx, st);
 }
 
 grpic_status grpic_diagnostics(grpic_ctx *ctx, const grpic_particles *p, const grpic_fields *f, void *rho, void *divD,
@@ -508,9 +603,40 @@ grpic_status grpic_sync(grpic_ctx *ctx, void *stream)
 
 const char *grpic_last_error(const grpic_ctx *ctx) { return ctx ? ctx->err : "null context"; }
 
+grpic_status grpic_set_timing(grpic_ctx *ctx, int enable)
+{
+    if (!ctx) return GRPIC_EINVAL;
+    ctx->timing = enable ? 1 : 0;
+    ctx->tsteps = 0;
+    return GRPIC_OK;
+}
+
+grpic_status grpic_get_timing(grpic_ctx *ctx, double out[3], int64_t *nsteps)
+{
+    if (!ctx || !out || !nsteps) return GRPIC_EINVAL;
+    out[0] = out[1] = out[2] = 0.0;
+    *nsteps = ctx->tsteps;
+    for (int64_t k = 0; k < ctx->tsteps; ++k) {
+        cudaEvent_t *ev = &(*ctx->tevents)[4 * (size_t)k];
+        if (cudaEventSynchronize(ev[3]) != cudaSuccess) return cuda_fail(ctx, cudaGetLastError(), "timing");
+        for (int ph = 0; ph < 3; ++ph) {
+            float ms = 0.0f;
+            if (cudaEventElapsedTime(&ms, ev[ph], ev[ph + 1]) != cudaSuccess)
+                return cuda_fail(ctx, cudaGetLastError(), "timing");
+            out[ph] += ms;
+        }
+    }
+    ctx->tsteps = 0;
+    return GRPIC_OK;
+}
+
 void grpic_destroy(grpic_ctx *ctx)
 {
     if (!ctx) return;
+    if (ctx->tevents) {
+        for (cudaEvent_t e : *ctx->tevents) cudaEventDestroy(e);
+        delete ctx->tevents;
+    }
     if (ctx->graph_exec) cudaGraphExecDestroy(ctx->graph_exec);
     if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
     void *ptrs[] = {ctx->d_offset_prev, ctx->d_cnt9, ctx->d_base9, ctx->d_sortflag, ctx->rcol, ctx->rcol2, ctx->rowsc, ctx->tab, ctx->col1d, ctx->tab32, ctx->col1d32, ctx->fscratch, ctx->d_status, ctx->d_keys,

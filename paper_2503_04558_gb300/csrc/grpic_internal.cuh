@@ -7,6 +7,8 @@
 // sqrt(1+z) (from sqrt(-g) = rho^2 sin(theta) = alpha sqrt(gamma)).
 #pragma once
 
+#include <vector>
+
 #include <cmath>
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -73,6 +75,10 @@ struct grpic_ctx {
     int32_t *d_sortflag;  // 0: neighbour sort applies, 1: general counting sort
     const uint32_t *sorted_tag;  // tag array the last sort wrote
     int64_t pushes_since_sort;
+    // a sort inside grpic_step that left its order in d_perm for the next
+    // push to read through (the data in the tag array pending_tag unmoved)
+    int pending_perm;
+    const uint32_t *pending_tag;
     int64_t perm_cap;
     int keys_valid;       // keys of the current order are valid
     int hist_valid;       // and so is their histogram (d_count)
@@ -82,6 +88,12 @@ struct grpic_ctx {
     cudaStream_t cap_stream;
     cudaGraphExec_t graph_exec;
     const void *graph_key[24];
+    int32_t *graph_offset;     // d_offset when the graph was captured (its double buffer's phase)
+    // phase timing of grpic_step: 4 events per timed step (before the push,
+    // after it, after the field update, after the sort)
+    int timing;
+    std::vector<cudaEvent_t> *tevents;
+    int64_t tsteps;
     char err[256];
 };
 
@@ -150,8 +162,13 @@ __device__ inline void set_status(int *st, int code) { atomicCAS(st, 0, code); }
 namespace grpic {
 cudaError_t launch_tables(grpic_ctx *ctx, cudaStream_t s);
 cudaError_t launch_init_fields(grpic_ctx *ctx, int kind, double B0, const grpic_fields *f, cudaStream_t s);
-cudaError_t launch_push64(grpic_ctx *ctx, grpic_particles *p, grpic_fields *f, bool histogram, cudaStream_t s);
-cudaError_t launch_push32(grpic_ctx *ctx, grpic_particles *p, grpic_fields *f, bool histogram, cudaStream_t s);
+// push (fused with the deposit) of the particles of `in` into `p`: in place
+// when perm is null (in == p), else slot k of p takes the particle of slot
+// perm[k] of in for k < *live (the last sort's permutation, data not moved)
+cudaError_t launch_push64(grpic_ctx *ctx, const grpic_particles *in, grpic_particles *p, const int32_t *perm,
+                          const int32_t *live, grpic_fields *f, bool histogram, cudaStream_t s);
+cudaError_t launch_push32(grpic_ctx *ctx, const grpic_particles *in, grpic_particles *p, const int32_t *perm,
+                          const int32_t *live, grpic_fields *f, bool histogram, cudaStream_t s);
 cudaError_t launch_deposit(grpic_ctx *ctx, const grpic_particles *b, const grpic_particles *a, const void *dphi,
                            grpic_fields *f, cudaStream_t s);
 cudaError_t launch_field64(grpic_ctx *ctx, grpic_fields *f, cudaStream_t s);
@@ -162,8 +179,10 @@ cudaError_t launch_tables_at(grpic_ctx *ctx, double a, double *tab, double *col1
 cudaError_t launch_keys(grpic_ctx *ctx, const grpic_particles *p, cudaStream_t s);
 cudaError_t sort_setup();
 cudaError_t launch_sort(grpic_ctx *ctx, grpic_particles *p, grpic_particles *scratch, cudaStream_t s);
+// the step's sort; materialize = false leaves the order in ctx->d_perm
+// (destination slot -> source slot) and the particle data where it is
 cudaError_t launch_sort_step(grpic_ctx *ctx, grpic_particles *p, grpic_particles *scratch, bool neighbour,
-                             bool hist_on_fallback, cudaStream_t s);
+                             bool hist_on_fallback, bool materialize, cudaStream_t s);
 cudaError_t launch_hist(grpic_ctx *ctx, const grpic_particles *p, cudaStream_t s);
 grpic_status ensure_field_scratch_ext(grpic_ctx *ctx, int64_t ld);
 grpic_status ensure_particle_scratch_ext(grpic_ctx *ctx, int64_t n);

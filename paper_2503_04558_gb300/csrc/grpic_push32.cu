@@ -46,6 +46,15 @@ struct Push32Args {
     int32_t *cell;
     float *o1, *o2, *u1, *u2, *u3;
     uint32_t *tag;
+    // read through a permutation: slot p's particle comes from slot perm[p]
+    // of the input arrays (the last sort's order, its data not yet moved);
+    // live slots = *live, whose count goes to *count_out.  perm == nullptr:
+    // the input arrays are the output arrays (in place).
+    const int32_t *perm, *live;
+    int64_t *count_out;
+    const int32_t *in_cell;
+    const float *in_o1, *in_o2, *in_u1, *in_u2, *in_u3;
+    const uint32_t *in_tag;
     const float *D0, *D1, *D2, *B0, *B1, *B2;
     float *J0, *J1, *J2;
     int64_t ld;
@@ -300,26 +309,29 @@ __device__ __forceinline__ void push_one(const Push32Args &A, int i, int j, floa
 __global__ void __launch_bounds__(256, GRPIC_PUSH32_MINB) push32_kernel(Push32Args A)
 {
     const GridDev &g = A.g;
-    int64_t n = A.d_count ? *A.d_count : A.n;
+    const bool permuted = A.perm != nullptr;
+    int64_t n = permuted ? (int64_t)*A.live : (A.d_count ? *A.d_count : A.n);
     if (n > A.n) n = A.n;
     int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const unsigned FULL = 0xffffffffu;
     int lane = threadIdx.x & 31;
     int ncell = g.nr * g.nth;
+    if (permuted && p == 0 && A.count_out) *A.count_out = n;
 
     bool live = false;
     uint32_t tag = DEAD;
     int i = 0, j = 0, cellk = 0;
     float o1 = 0, o2 = 0, u[3] = {0, 0, 0};
     if (p < n) {
-        tag = A.tag[p];
+        const int64_t src = permuted ? (int64_t)A.perm[p] : p;
+        tag = A.in_tag[src];
         if (!(tag & DEAD)) {
-            cellk = A.cell[p];
-            o1 = A.o1[p];
-            o2 = A.o2[p];
-            u[0] = A.u1[p];
-            u[1] = A.u2[p];
-            u[2] = A.u3[p];
+            cellk = A.in_cell[src];
+            o1 = A.in_o1[src];
+            o2 = A.in_o2[src];
+            u[0] = A.in_u1[src];
+            u[1] = A.in_u2[src];
+            u[2] = A.in_u3[src];
             bool ok = cellk >= 0 && cellk < ncell && o1 >= 0.0f && o1 <= 1.0f && o2 >= 0.0f && o2 <= 1.0f &&
                       isfinite(u[0]) && isfinite(u[1]) && isfinite(u[2]);
             if (ok) {
@@ -387,7 +399,7 @@ __global__ void __launch_bounds__(256, GRPIC_PUSH32_MINB) push32_kernel(Push32Ar
         }
     }
     if (p < n) {
-        if (moved) {
+        if (moved || permuted) {
             A.cell[p] = nj * g.nr + ni;
             A.o1[p] = n1;
             A.o2[p] = n2;
@@ -398,6 +410,8 @@ __global__ void __launch_bounds__(256, GRPIC_PUSH32_MINB) push32_kernel(Push32Ar
         if (tag & DEAD) key = ncell;
         A.tag[p] = tag;
         A.keys[p] = key;
+    } else if (permuted && p < A.n) {
+        A.tag[p] = DEAD;  // past the live slots of the permuted order
     }
 
     // ---- deposit: lanes grouped by start cell, each group reduce-scattered --
@@ -413,7 +427,8 @@ __global__ void __launch_bounds__(256, GRPIC_PUSH32_MINB) push32_kernel(Push32Ar
 
 }  // namespace
 
-cudaError_t launch_push32(grpic_ctx *ctx, grpic_particles *p, grpic_fields *f, bool histogram, cudaStream_t s)
+cudaError_t launch_push32(grpic_ctx *ctx, const grpic_particles *in, grpic_particles *p, const int32_t *perm,
+                          const int32_t *live, grpic_fields *f, bool histogram, cudaStream_t s)
 {
     Push32Args A;
     A.g = ctx->g;
@@ -448,6 +463,16 @@ cudaError_t launch_push32(grpic_ctx *ctx, grpic_particles *p, grpic_fields *f, b
     A.u2 = (float *)p->u2;
     A.u3 = (float *)p->u3;
     A.tag = p->tag;
+    A.perm = perm;
+    A.live = live;
+    A.count_out = perm ? p->d_count : nullptr;
+    A.in_cell = in->cell;
+    A.in_o1 = (const float *)in->x1;
+    A.in_o2 = (const float *)in->x2;
+    A.in_u1 = (const float *)in->u1;
+    A.in_u2 = (const float *)in->u2;
+    A.in_u3 = (const float *)in->u3;
+    A.in_tag = in->tag;
     A.D0 = (const float *)f->D[0];
     A.D1 = (const float *)f->D[1];
     A.D2 = (const float *)f->D[2];

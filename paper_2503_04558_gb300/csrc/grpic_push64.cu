@@ -36,6 +36,12 @@ struct Push64Args {
     const int64_t *d_count;
     double *r, *th, *u1, *u2, *u3;
     uint32_t *tag;
+    // read through a permutation (see the FP32 push): slot p's particle comes
+    // from slot perm[p] of the input arrays; perm == nullptr: in place
+    const int32_t *perm, *live;
+    int64_t *count_out;
+    const double *in_r, *in_th, *in_u1, *in_u2, *in_u3;
+    const uint32_t *in_tag;
     const double *D0, *D1, *D2, *B0, *B1, *B2;
     double *J0, *J1, *J2;
     int64_t ld;
@@ -186,25 +192,28 @@ __device__ __forceinline__ int jcell(const GridDev &g, double x2)
 __global__ void __launch_bounds__(256) push64_kernel(Push64Args A)
 {
     const GridDev &g = A.g;
-    int64_t n = A.d_count ? *A.d_count : A.n;
+    const bool permuted = A.perm != nullptr;
+    int64_t n = permuted ? (int64_t)*A.live : (A.d_count ? *A.d_count : A.n);
     if (n > A.n) n = A.n;
     int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const unsigned FULL = 0xffffffffu;
     int lane = threadIdx.x & 31;
     int ncell = g.nr * g.nth;
+    if (permuted && p == 0 && A.count_out) *A.count_out = n;
 
     bool live = false;
     uint32_t tag = DEAD;
     double r = 0, th = 0, u[3] = {0, 0, 0};
     if (p < n) {
-        tag = A.tag[p];
+        const int64_t src = permuted ? (int64_t)A.perm[p] : p;
+        tag = A.in_tag[src];
         if (!(tag & DEAD)) {
             live = true;
-            r = A.r[p];
-            th = A.th[p];
-            u[0] = A.u1[p];
-            u[1] = A.u2[p];
-            u[2] = A.u3[p];
+            r = A.in_r[src];
+            th = A.in_th[src];
+            u[0] = A.in_u1[src];
+            u[1] = A.in_u2[src];
+            u[2] = A.in_u3[src];
         }
     }
 
@@ -325,7 +334,7 @@ __global__ void __launch_bounds__(256) push64_kernel(Push64Args A)
         }
     }
     if (p < n) {
-        if (dep) {
+        if (dep || permuted) {
             A.r[p] = r;
             A.th[p] = th;
             A.u1[p] = u[0];
@@ -335,6 +344,8 @@ __global__ void __launch_bounds__(256) push64_kernel(Push64Args A)
         if (tag & DEAD) key = ncell;
         A.tag[p] = tag;
         A.keys[p] = key;
+    } else if (permuted && p < A.n) {
+        A.tag[p] = DEAD;  // past the live slots of the permuted order
     }
 
     // ---- deposit: warp-uniform start cell -> reduce-scatter over the lanes ---
@@ -372,7 +383,8 @@ __global__ void __launch_bounds__(256) push64_kernel(Push64Args A)
 
 }  // namespace
 
-cudaError_t launch_push64(grpic_ctx *ctx, grpic_particles *p, grpic_fields *f, bool histogram, cudaStream_t s)
+cudaError_t launch_push64(grpic_ctx *ctx, const grpic_particles *in, grpic_particles *p, const int32_t *perm,
+                          const int32_t *live, grpic_fields *f, bool histogram, cudaStream_t s)
 {
     Push64Args A;
     A.g = ctx->g;
@@ -391,6 +403,15 @@ cudaError_t launch_push64(grpic_ctx *ctx, grpic_particles *p, grpic_fields *f, b
     A.u2 = (double *)p->u2;
     A.u3 = (double *)p->u3;
     A.tag = p->tag;
+    A.perm = perm;
+    A.live = live;
+    A.count_out = perm ? p->d_count : nullptr;
+    A.in_r = (const double *)in->x1;
+    A.in_th = (const double *)in->x2;
+    A.in_u1 = (const double *)in->u1;
+    A.in_u2 = (const double *)in->u2;
+    A.in_u3 = (const double *)in->u3;
+    A.in_tag = in->tag;
     A.D0 = (const double *)f->D[0];
     A.D1 = (const double *)f->D[1];
     A.D2 = (const double *)f->D[2];

@@ -720,7 +720,7 @@ cudaError_t launch_hist(grpic_ctx *ctx, const grpic_particles *p, cudaStream_t s
 }
 
 cudaError_t launch_sort_step(grpic_ctx *ctx, grpic_particles *p, grpic_particles *q, bool neighbour,
-                             bool hist_on_fallback, cudaStream_t s)
+                             bool hist_on_fallback, bool materialize, cudaStream_t s)
 {
     const int ncell = ctx->g.nr * ctx->g.nth;
     const int64_t nscan = (int64_t)ncell + 1;
@@ -784,7 +784,8 @@ cudaError_t launch_sort_step(grpic_ctx *ctx, grpic_particles *p, grpic_particles
     G.cell_src = (ctx->prm.precision == 32) ? p->cell : nullptr;
     G.cell_dst = (ctx->prm.precision == 32) ? q->cell : nullptr;
     // both paths leave the permutation in d_perm: one gather moves the data
-    if (p->n > 0) {
+    // (or the next push reads through it)
+    if (p->n > 0 && materialize) {
         if (ctx->prm.precision == 64)
             gather_kernel<double><<<gp, 256, 0, s>>>(G, 5, nullptr);
         else

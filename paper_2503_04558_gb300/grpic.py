@@ -24,7 +24,7 @@ NG = 2
 # names the header declares (checked by the CPU test of the boundary)
 EXPORTS = ["grpic_init", "grpic_init_fields", "grpic_push", "grpic_deposit", "grpic_field_update", "grpic_sort",
            "grpic_step", "grpic_step_graph", "grpic_diagnostics", "grpic_charge_check", "grpic_get_areas", "grpic_sync", "grpic_last_error", "grpic_destroy",
-           "grpic_sort_noalloc"]
+           "grpic_sort_noalloc", "grpic_set_timing", "grpic_get_timing"]
 NOALLOC_MAX_PARTICLES = 2097152
 NOALLOC_MAX_CELLS = 262144
 
@@ -77,6 +77,8 @@ def load(path: str = LIB_PATH):
         "grpic_get_areas": [v, v * 6, i64, v],
         "grpic_sync": [v, v],
         "grpic_sort_noalloc": [p(Grid), C.c_int32, p(ParticlesC), p(ParticlesC), v],
+        "grpic_set_timing": [v, i],
+        "grpic_get_timing": [v, p(d), p(i64)],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -336,8 +338,21 @@ class Context:
                                         _stream(stream)), "grpic_step")
         P.sync_ptrs()
 
+    def set_timing(self, enable: bool):
+        """Record per-phase CUDA events in every step of grpic_step."""
+        self._check(self.lib.grpic_set_timing(self.h, 1 if enable else 0), "grpic_set_timing")
+
+    def get_timing(self):
+        """(push ms, field update ms, sort ms) summed over the timed steps
+        since the last read, and their number; waits for the events."""
+        out = (C.c_double * 3)()
+        n = C.c_int64()
+        self._check(self.lib.grpic_get_timing(self.h, out, C.byref(n)), "grpic_get_timing")
+        return out[0], out[1], out[2], n.value
+
     def step_graph(self, P: ParticleSet, F: Fields, nsteps=1, stream=None):
-        """grpic_step replayed from a captured CUDA graph of two steps."""
+        """grpic_step with steps 2 .. nsteps-1 replayed from a captured CUDA
+        graph of two steps (nsteps >= 4; fewer run as grpic_step)."""
         P._sc.n = P.n
         P._ss.n = P.n
         fc = F.c()

@@ -412,3 +412,36 @@ def test_step_graph_matches_eager_steps(G):
         assert relerr(h1[k], h0[k]) < 1e-12, k
     for a, b in zip(f1, f0):
         assert relerr(a, b) < 1e-12
+
+
+def test_deferred_order_matches_separate_calls(G):
+    """Inside one grpic_step call each sort but the last leaves only its
+    order, and the next push reads the particles through it into the other
+    buffer.  The result equals steps run as separate push, field update and
+    sort calls (each sort moving the data): same order and tags, values up to
+    the deposit's atomic ordering; the phase timing sees every step."""
+    oc, gc = configs(40, 32, A09, 0.9 * RH, 20.0)
+    out = []
+    for deferred in (False, True):
+        ctx, F = gpu_fields(G, gc, O.WALD, 1.0)
+        P = make_particles(oc, 20000, seed=31)
+        S = load_set(G, gc, P)
+        if deferred:
+            ctx.set_timing(True)
+            ctx.step(S, F, 6)
+            tp, tf, ts, nt = ctx.get_timing()
+            assert nt == 6 and tp > 0 and tf > 0 and ts > 0
+        else:
+            for _ in range(6):
+                ctx.push(S, F)
+                ctx.field_update(F)
+                ctx.sort(S)
+        assert ctx.sync() == 0
+        out.append((S.host(), [host(t) for t in F.D + F.B], S.live()))
+    (h0, f0, n0), (h1, f1, n1) = out
+    assert n0 == n1
+    assert np.array_equal(h0["tag"], h1["tag"])
+    for k in ("x1", "x2", "u1", "u2", "u3"):
+        assert relerr(h1[k], h0[k]) < 1e-12, k
+    for a, b in zip(f1, f0):
+        assert relerr(a, b) < 1e-12
