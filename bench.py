@@ -53,11 +53,18 @@ B0 = 1.0
 # kernels (flop_count = 2 FMA + MUL + ADD of the SASS instruction counters;
 # the capture commands and counts are in profiles/).
 PUSH64_FP64_FLOP = 1734.0   # profiles/push64_fp64_512x512_64ppc.md
-PUSH32_FP32_FLOP = 1344.0   # profiles/push32_fp32form_1024x1024_64ppc.md
+PUSH32_FP32_FLOP = 1248.0   # profiles/push32_fp32form_1024x1024_64ppc.md
+# the same capture: instructions issued per particle (warp instructions x 32)
+# and DRAM bytes per particle (read + write), scaled to a launch by the
+# number of particles
+PUSH32_INST = 2145.0
+PUSH32_DRAM_B = 68.3
 # ALU peaks from unit counts x clock: 152 SMs x 2.07 GHz x (4 FP64 flops,
-# 256 FP32 flops) per SM per clock
+# 256 FP32 flops) per SM per clock; instruction issue: 4 schedulers x 1 warp
+# instruction per SM per clock
 FP64_PEAK_TFLOPS = 152 * 2.07e9 * 4 / 1e12
 FP32_PEAK_TFLOPS = 152 * 2.07e9 * 256 / 1e12
+ISSUE_PEAK_GWARP = 152 * 2.07e9 * 4 / 1e9
 
 
 def horizon(a):
@@ -609,10 +616,17 @@ def grpic_summary(res, args, world, esz_prec):
     # the FP32 form is bound by FP32 instruction issue, not by HBM: report
     # the FP32 ALU roofline with the HBM one beside it
     ach32 = n * PUSH32_FP32_FLOP / (push_ms * 1e-3) / 1e12
+    issue = n * PUSH32_INST / 32 / (push_ms * 1e-3) / 1e9
+    if prec == 32:
+        hbm["traffic"] = n * PUSH32_DRAM_B
+        hbm["traffic_source"] = "ncu dram bytes per particle at 1024^2 x 64 ppc, x particles"
     roof = {"kernel": "push+deposit (FP32 form)", "bound": "alu", "achieved": ach32, "peak": FP32_PEAK_TFLOPS,
-            "unit": "TFLOP/s", "frac": ach32 / FP32_PEAK_TFLOPS, "traffic": None,
+            "unit": "TFLOP/s", "frac": ach32 / FP32_PEAK_TFLOPS, "traffic": n * PUSH32_DRAM_B,
             "peak_source": "152 SMs x 2.07 GHz x 256 FP32 flop/clk/SM (recipe unit counts and clock)",
-            "flop_per_particle": PUSH32_FP32_FLOP, "hbm": hbm}
+            "flop_per_particle": PUSH32_FP32_FLOP, "hbm": hbm,
+            "issue": {"achieved": issue, "peak": ISSUE_PEAK_GWARP, "unit": "G warp-instructions/s",
+                      "frac": issue / ISSUE_PEAK_GWARP, "inst_per_particle": PUSH32_INST,
+                      "peak_source": "152 SMs x 4 schedulers x 2.07 GHz"}}
     if prec == 64:
         # FP64 arithmetic bounds this kernel on GB300: report the FP64 roofline
         ach = n * PUSH64_FP64_FLOP / (push_ms * 1e-3) / 1e12
@@ -701,8 +715,9 @@ def main():
                 "roofline": h["roofline"], "clocks": h["clocks"],
                 # per step: push, 1 + n_field_iter field stages, 12 sort kernels
                 # (count, destinations, histogram pair, 3 scan, bases, placement and
-                # the general path's 3, which return at once); one gather per call
-                "gpu_launches": args.steps * (1 + 1 + cfg.n_field_iter + 12) + 1,
+                # the general path's 3, which return at once) -- the count only
+                # in the first step, later pushes count -- and one gather per call
+                "gpu_launches": args.steps * (1 + 1 + cfg.n_field_iter + 12) - (args.steps - 1) + 1,
                 "e2e": res["e2e"]}
         if second is not None:
             s2 = grpic_summary(second, args, world, 64)

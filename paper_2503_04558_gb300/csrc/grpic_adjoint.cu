@@ -1505,7 +1505,7 @@ extern "C" grpic_status grpic_adjoint_grad(grpic_ctx *ctx, const grpic_particles
     grpic_status st = GRPIC_OK;
     auto fwd_step = [&]() -> grpic_status {
         for (int k = 0; k < 3; ++k) cudaMemsetAsync(Jw[k], 0, fn * sizeof(double), s);
-        if (launch_push64(ctx, &PW, &PW, nullptr, nullptr, &FW, false, s) != cudaSuccess) return GRPIC_ECUDA;
+        if (launch_push64(ctx, &PW, &PW, nullptr, nullptr, nullptr, &FW, false, s) != cudaSuccess) return GRPIC_ECUDA;
         grpic_status r = GRPIC_OK;
         if (launch_field64(ctx, &FW, s) != cudaSuccess) r = GRPIC_ECUDA;
         return r;

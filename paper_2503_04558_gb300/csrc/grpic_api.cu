@@ -142,7 +142,9 @@ grpic_status sort_impl(grpic_ctx *ctx, grpic_particles *p, grpic_particles *q, c
         if (e != cudaSuccess) return cuda_fail(ctx, e, "histogram");
         ctx->hist_valid = 1;
     }
-    cudaError_t e = launch_sort_step(ctx, p, q, neighbour, !ctx->hist_valid, materialize, s);
+    const bool counts_ready = neighbour && ctx->counts_ready;
+    ctx->counts_ready = 0;
+    cudaError_t e = launch_sort_step(ctx, p, q, neighbour, !ctx->hist_valid, materialize, counts_ready, s);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "sort");
     ctx->keys_valid = 0;
     ctx->hist_valid = 0;
@@ -180,10 +182,13 @@ grpic_status push_impl(grpic_ctx *ctx, grpic_particles *p, grpic_fields *f, bool
         out.n = p->n;
         out.d_count = p->d_count;
         const int32_t *live = ctx->d_offset_prev + ncell;
+        // the counts of the next neighbour sort come from this push
+        cudaMemsetAsync(ctx->d_cnt9, 0, sizeof(int32_t) * 9 * (size_t)ncell, s);
         cudaError_t e = (ctx->prm.precision == 64)
-                            ? launch_push64(ctx, p, &out, ctx->d_perm, live, f, false, s)
-                            : launch_push32(ctx, p, &out, ctx->d_perm, live, f, false, s);
+                            ? launch_push64(ctx, p, &out, ctx->d_perm, live, ctx->d_cnt9, f, false, s)
+                            : launch_push32(ctx, p, &out, ctx->d_perm, live, ctx->d_cnt9, f, false, s);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "push");
+        ctx->counts_ready = 1;
         std::swap(p->x1, scratch->x1);
         std::swap(p->x2, scratch->x2);
         std::swap(p->u1, scratch->u1);
@@ -208,8 +213,9 @@ grpic_status push_impl(grpic_ctx *ctx, grpic_particles *p, grpic_fields *f, bool
     size_t bytes = (size_t)(ctx->g.nth + 1) * f->ld * fsize(ctx);
     for (int k = 0; k < 3; ++k) cudaMemsetAsync(f->J[k], 0, bytes, s);
     if (histogram) cudaMemsetAsync(ctx->d_count, 0, sizeof(int32_t) * (ncell + 1), s);
-    cudaError_t e = (ctx->prm.precision == 64) ? launch_push64(ctx, p, p, nullptr, nullptr, f, histogram, s)
-                                                : launch_push32(ctx, p, p, nullptr, nullptr, f, histogram, s);
+    ctx->counts_ready = 0;
+    cudaError_t e = (ctx->prm.precision == 64) ? launch_push64(ctx, p, p, nullptr, nullptr, nullptr, f, histogram, s)
+                                                : launch_push32(ctx, p, p, nullptr, nullptr, nullptr, f, histogram, s);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "push");
     ctx->keys_valid = 1;  // the push writes every slot's key
     ctx->hist_valid = histogram ? 1 : 0;

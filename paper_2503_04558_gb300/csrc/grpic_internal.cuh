@@ -79,6 +79,7 @@ struct grpic_ctx {
     // push to read through (the data in the tag array pending_tag unmoved)
     int pending_perm;
     const uint32_t *pending_tag;
+    int counts_ready;  // the last (permuted) push filled d_cnt9 for the next sort
     int64_t perm_cap;
     int keys_valid;       // keys of the current order are valid
     int hist_valid;       // and so is their histogram (d_count)
@@ -165,10 +166,12 @@ cudaError_t launch_init_fields(grpic_ctx *ctx, int kind, double B0, const grpic_
 // push (fused with the deposit) of the particles of `in` into `p`: in place
 // when perm is null (in == p), else slot k of p takes the particle of slot
 // perm[k] of in for k < *live (the last sort's permutation, data not moved)
+// and, when cnt9 is given (zeroed), the push also counts per start cell and
+// direction for the next neighbour sort
 cudaError_t launch_push64(grpic_ctx *ctx, const grpic_particles *in, grpic_particles *p, const int32_t *perm,
-                          const int32_t *live, grpic_fields *f, bool histogram, cudaStream_t s);
+                          const int32_t *live, int32_t *cnt9, grpic_fields *f, bool histogram, cudaStream_t s);
 cudaError_t launch_push32(grpic_ctx *ctx, const grpic_particles *in, grpic_particles *p, const int32_t *perm,
-                          const int32_t *live, grpic_fields *f, bool histogram, cudaStream_t s);
+                          const int32_t *live, int32_t *cnt9, grpic_fields *f, bool histogram, cudaStream_t s);
 cudaError_t launch_deposit(grpic_ctx *ctx, const grpic_particles *b, const grpic_particles *a, const void *dphi,
                            grpic_fields *f, cudaStream_t s);
 cudaError_t launch_field64(grpic_ctx *ctx, grpic_fields *f, cudaStream_t s);
@@ -181,8 +184,9 @@ cudaError_t sort_setup();
 cudaError_t launch_sort(grpic_ctx *ctx, grpic_particles *p, grpic_particles *scratch, cudaStream_t s);
 // the step's sort; materialize = false leaves the order in ctx->d_perm
 // (destination slot -> source slot) and the particle data where it is
+// counts_ready: the push already filled d_cnt9 (neighbour path only)
 cudaError_t launch_sort_step(grpic_ctx *ctx, grpic_particles *p, grpic_particles *scratch, bool neighbour,
-                             bool hist_on_fallback, bool materialize, cudaStream_t s);
+                             bool hist_on_fallback, bool materialize, bool counts_ready, cudaStream_t s);
 cudaError_t launch_hist(grpic_ctx *ctx, const grpic_particles *p, cudaStream_t s);
 grpic_status ensure_field_scratch_ext(grpic_ctx *ctx, int64_t ld);
 grpic_status ensure_particle_scratch_ext(grpic_ctx *ctx, int64_t n);

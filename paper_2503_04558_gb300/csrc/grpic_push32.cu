@@ -52,6 +52,10 @@ struct Push32Args {
     // the input arrays are the output arrays (in place).
     const int32_t *perm, *live;
     int64_t *count_out;
+    // with perm: the particles of each old cell going in each direction
+    // (direction-major, d * n_cells + cell; zeroed by the caller), the counts
+    // of the next neighbour sort
+    int32_t *cnt9;
     const int32_t *in_cell;
     const float *in_o1, *in_o2, *in_u1, *in_u2, *in_u3;
     const uint32_t *in_tag;
@@ -414,21 +418,32 @@ __global__ void __launch_bounds__(256, GRPIC_PUSH32_MINB) push32_kernel(Push32Ar
         A.tag[p] = DEAD;  // past the live slots of the permuted order
     }
 
-    // ---- deposit: lanes grouped by start cell, each group reduce-scattered --
-    deposit_warp<float, 3>(dep, i, j, g.nr, wa1, wa2, wb1, wb2, wq, wphi, A.dt, lane, g.nth, NG, A.ld, A.J0, A.J1,
-                        A.J2);
+    if (A.cnt9) {
+        // old cell = start cell (the slot's segment of the permuted order);
+        // lanes match on cell * 9 + direction (32-bit: the cells of one warp
+        // lie far closer together than 2^32 / 9)
+        const bool counted = p < n && moved && !(tag & DEAD);
+        const int dir = (nj - j + 1) * 3 + (ni - i + 1);
+        const unsigned mk = counted ? (unsigned)cellk * 9u + (unsigned)dir : 0xffffffffu;
+        const unsigned peers = __match_any_sync(FULL, mk);
+        if (counted && lane == __ffs(peers) - 1) atomicAdd(A.cnt9 + (int64_t)dir * ncell + cellk, (int)__popc(peers));
+    }
 
     if (A.histogram) {
         int hk = (p < n) ? key : -1;
         unsigned peers = __match_any_sync(FULL, hk);
         if (hk >= 0 && lane == __ffs(peers) - 1) atomicAdd(A.count + hk, __popc(peers));
     }
+
+    // ---- deposit: lanes grouped by start cell, each group reduce-scattered --
+    deposit_warp<float, 3>(dep, i, j, g.nr, wa1, wa2, wb1, wb2, wq, wphi, A.dt, lane, g.nth, NG, A.ld, A.J0, A.J1,
+                        A.J2);
 }
 
 }  // namespace
 
 cudaError_t launch_push32(grpic_ctx *ctx, const grpic_particles *in, grpic_particles *p, const int32_t *perm,
-                          const int32_t *live, grpic_fields *f, bool histogram, cudaStream_t s)
+                          const int32_t *live, int32_t *cnt9, grpic_fields *f, bool histogram, cudaStream_t s)
 {
     Push32Args A;
     A.g = ctx->g;
@@ -466,6 +481,7 @@ cudaError_t launch_push32(grpic_ctx *ctx, const grpic_particles *in, grpic_parti
     A.perm = perm;
     A.live = live;
     A.count_out = perm ? p->d_count : nullptr;
+    A.cnt9 = perm ? cnt9 : nullptr;
     A.in_cell = in->cell;
     A.in_o1 = (const float *)in->x1;
     A.in_o2 = (const float *)in->x2;

@@ -40,6 +40,7 @@ struct Push64Args {
     // from slot perm[p] of the input arrays; perm == nullptr: in place
     const int32_t *perm, *live;
     int64_t *count_out;
+    int32_t *cnt9;  // with perm: counts of the next neighbour sort (see the FP32 push)
     const double *in_r, *in_th, *in_u1, *in_u2, *in_u3;
     const uint32_t *in_tag;
     const double *D0, *D1, *D2, *B0, *B1, *B2;
@@ -379,12 +380,26 @@ __global__ void __launch_bounds__(256) push64_kernel(Push64Args A)
         unsigned peers = __match_any_sync(FULL, hk);
         if (hk >= 0 && lane == __ffs(peers) - 1) atomicAdd(A.count + hk, __popc(peers));
     }
+    if (A.cnt9) {
+        // old cell = start cell (i0, j0); the key is the new cell; lanes match
+        // on cell * 9 + direction (32-bit: see the FP32 push)
+        const bool counted = p < n && dep && key >= 0 && key < ncell;
+        int dir = 0, c0 = 0;
+        if (counted) {
+            const int ki = key % g.nr, kj = key / g.nr;
+            dir = (kj - j0 + 1) * 3 + (ki - i0 + 1);
+            c0 = j0 * g.nr + i0;
+        }
+        const unsigned mk = counted ? (unsigned)c0 * 9u + (unsigned)dir : 0xffffffffu;
+        const unsigned peers = __match_any_sync(FULL, mk);
+        if (counted && lane == __ffs(peers) - 1) atomicAdd(A.cnt9 + (int64_t)dir * ncell + c0, (int)__popc(peers));
+    }
 }
 
 }  // namespace
 
 cudaError_t launch_push64(grpic_ctx *ctx, const grpic_particles *in, grpic_particles *p, const int32_t *perm,
-                          const int32_t *live, grpic_fields *f, bool histogram, cudaStream_t s)
+                          const int32_t *live, int32_t *cnt9, grpic_fields *f, bool histogram, cudaStream_t s)
 {
     Push64Args A;
     A.g = ctx->g;
@@ -406,6 +421,7 @@ cudaError_t launch_push64(grpic_ctx *ctx, const grpic_particles *in, grpic_parti
     A.perm = perm;
     A.live = live;
     A.count_out = perm ? p->d_count : nullptr;
+    A.cnt9 = perm ? cnt9 : nullptr;
     A.in_r = (const double *)in->x1;
     A.in_th = (const double *)in->x2;
     A.in_u1 = (const double *)in->u1;

@@ -720,7 +720,7 @@ cudaError_t launch_hist(grpic_ctx *ctx, const grpic_particles *p, cudaStream_t s
 }
 
 cudaError_t launch_sort_step(grpic_ctx *ctx, grpic_particles *p, grpic_particles *q, bool neighbour,
-                             bool hist_on_fallback, bool materialize, cudaStream_t s)
+                             bool hist_on_fallback, bool materialize, bool counts_ready, cudaStream_t s)
 {
     const int ncell = ctx->g.nr * ctx->g.nth;
     const int64_t nscan = (int64_t)ncell + 1;
@@ -731,8 +731,11 @@ cudaError_t launch_sort_step(grpic_ctx *ctx, grpic_particles *p, grpic_particles
     int32_t *flag = ctx->d_sortflag;
     if (neighbour && ctx->g.nr >= 3) {
         cudaMemsetAsync(flag, 0, sizeof(int32_t), s);
-        count9_kernel<<<grid, 256, 0, s>>>(ctx->d_offset_prev, ctx->d_keys, ctx->g.nr, ncell, p->d_count, p->n,
-                                           ctx->d_cnt9, flag);
+        // (a push that read through the last sort's permutation counted
+        // already: its slots are that sort's segments by construction)
+        if (!counts_ready)
+            count9_kernel<<<grid, 256, 0, s>>>(ctx->d_offset_prev, ctx->d_keys, ctx->g.nr, ncell, p->d_count, p->n,
+                                               ctx->d_cnt9, flag);
         dest_count_kernel<<<grid, 256, 0, s>>>(ctx->d_cnt9, ctx->g.nr, ctx->g.nth, ctx->d_count, flag);
         if (hist_on_fallback) {
             // the push skipped the histogram: rebuild it if the device fell back
