@@ -102,7 +102,11 @@ typedef struct {
  * in theta cells, relative to max(1, |u|)) falls below push_tol (<= 0: always
  * n_push_iter correctors).  The change is exact: two floats within a factor 2
  * subtract exactly (Sterbenz's lemma), so the test takes the FP64 decision
- * for converging iterates.  The FP64 path always runs n_push_iter. */
+ * for converging iterates.  The FP64 path always runs n_push_iter.
+ * pusher: the momentum update of charged particles (Sec. 2.2): 0 the
+ * generalized Boris step (Eqs. boris-plus-minus .. boris-scheme, the
+ * default), 1 Vay's update in the FIDO frame (the paper's alternative; the
+ * differentiable form supports 0 only). */
 typedef struct {
     double dt;
     double beta_field;
@@ -116,6 +120,7 @@ typedef struct {
     double fp64_radius;
     double push_tol;
     int32_t island_arith;
+    int32_t pusher;
 } grpic_params;
 
 typedef struct {

@@ -47,7 +47,8 @@ class Cfg(C.Structure):
                 ("dt", C.c_double), ("beta_s", C.c_double),
                 ("n_fld_iter", C.c_int), ("n_push_iter", C.c_int),
                 ("damp_cells", C.c_int), ("damp_max", C.c_double),
-                ("qm", C.c_double * 4), ("qw", C.c_double * 4), ("massive", C.c_int * 4)]
+                ("qm", C.c_double * 4), ("qw", C.c_double * 4), ("massive", C.c_int * 4),
+                ("pusher", C.c_int)]
 
 
 _lib = None
@@ -69,6 +70,7 @@ def lib():
             "orc_circulations": (None, [pc] + [p] * 12),
             "orc_geodesic_rhs": (None, [d, d, p, p]),
             "orc_boris": (None, [d, d, d, d, d, p, p, p]),
+            "orc_vay": (None, [d, d, d, d, d, p, p, p]),
             "orc_push_values": (None, [d, d, i, d, i, p, p, p]),
             "orc_push_analytic": (i, [i, d, d, d, i, d, i, p, l, l, p]),
             "orc_interp": (None, [pc, p, p, p, p, p, p, d, d, p]),
@@ -103,7 +105,7 @@ def horizon(a: float) -> float:
 
 def make_cfg(nr, nth, a, r_in, r_out, dt=None, cfl=0.5, beta_s=0.53, n_fld_iter=7, n_push_iter=3,
              damp_cells=None, damp_max=0.1, qm=(-1.0, 1.0, 1.0, 0.0), qw=(-1e-3, 1e-3, 1e-3, 0.0),
-             massive=(1, 1, 1, 0)) -> Cfg:
+             massive=(1, 1, 1, 0), pusher=0) -> Cfg:
     """Grid uniform in ln r and theta; dt from the CFL reading
     dt = cfl * min(dr, r dtheta) at r_in when not given."""
     c = Cfg()
@@ -122,6 +124,7 @@ def make_cfg(nr, nth, a, r_in, r_out, dt=None, cfl=0.5, beta_s=0.53, n_fld_iter=
     c.damp_max = damp_max
     for k in range(4):
         c.qm[k], c.qw[k], c.massive[k] = qm[k], qw[k], massive[k]
+    c.pusher = pusher
     return c
 
 
@@ -193,6 +196,13 @@ def geodesic_rhs(a, eps, y):
 def boris(a, r, th, qm, dt, Dv, Bv, u):
     u = np.array(u, dtype=np.float64)
     lib().orc_boris(a, r, th, qm, dt, _p(np.asarray(Dv, np.float64)), _p(np.asarray(Bv, np.float64)), _p(u))
+    return u
+
+
+def vay(a, r, th, qm, dt, Dv, Bv, u):
+    """Vay's momentum update in the FIDO frame over dt (fields D, B contravariant)."""
+    u = np.array(u, dtype=np.float64)
+    lib().orc_vay(a, r, th, qm, dt, _p(np.asarray(Dv, np.float64)), _p(np.asarray(Bv, np.float64)), _p(u))
     return u
 
 

@@ -62,6 +62,8 @@ typedef struct {
     double qm[4];      /* q/m per species                                    */
     double qw[4];      /* deposited macro charge q*w per species             */
     int massive[4];    /* epsilon in u^0 (1 massive, 0 photon)               */
+    int pusher;        /* momentum update: 0 generalized Boris, 1 Vay in the  */
+                       /* FIDO frame (Sec. 2.2)                              */
 } orc_cfg;
 
 /* ------------------------------------------------------------------------ */
@@ -769,16 +771,92 @@ void orc_boris(double a, double r, double th, double qm, double dt, const double
     boris(&m, qm, dt, Dv, Bv, u);
 }
 
-/* Boris (skipped for photons or q = 0) then the geodesic predictor (Eq.
- * geodesic-predictor) and n_iter trapezoidal correctors (Eq.
- * geodesic-corrector), each re-evaluated at the latest iterate. y[2] = phi. */
+/* The alternative momentum update of Sec. 2.2: transform to the FIDO frame
+ * and apply Vay's update there (Vay 2008, Phys. Plasmas 15, 056701).
+ *
+ * FIDO frame: the orthonormal spatial triad e_(a) of the normal observer,
+ *   e_(r)   = (1, 0, -g_rp/g_pp) / sqrt(g_rr - g_rp^2/g_pp),
+ *   e_(th)  = (0, 1/sqrt(g_thth), 0),
+ *   e_(ph)  = (0, 0, 1/sqrt(g_pp))            (contravariant components),
+ * right-handed like (r, theta, phi).  A covector u_i has frame components
+ * u_a = e^i_(a) u_i, a vector V^j has V_a = e^i_(a) gamma_ij V^j, and back
+ * u_i = sum_a gamma_ij e^j_(a) u_a.  There the Lorentz force of Eq. Lorentz
+ * is the flat one, with the FIDO's fields E = D and B and its proper time
+ * d tau = alpha dt:  du/dtau = (q/m)(E + u x B / Gamma), Gamma = sqrt(1 + u.u).
+ *
+ * Vay's step over dtau, fields at n:
+ *   u'     = u + (q/m) dtau (E + (u / Gamma) x B / 2)
+ *   tau    = (q/m) dtau B / 2,   u* = u'.tau,   sigma = 1 + u'.u' - tau.tau
+ *   Gamma1 = sqrt((sigma + sqrt(sigma^2 + 4 (tau.tau + u*^2))) / 2)
+ *   t      = tau / Gamma1,        s = 1 / (1 + t.t)
+ *   u1     = s (u' + (u'.t) t + u' x t).                                      */
+static void vay_fido(const orc_metric *m, double qm, double dt, const double Dv[3], const double Bv[3], double u[3])
+{
+    double E[3][3] = {{0}};  /* E[a] = e^i_(a) (contravariant components) */
+    double nr = sqrt(m->g_rr - m->g_rp * m->g_rp / m->g_pp);
+    E[0][0] = 1.0 / nr;
+    E[0][2] = -m->g_rp / m->g_pp / nr;
+    E[1][1] = 1.0 / sqrt(m->g_thth);
+    E[2][2] = 1.0 / sqrt(m->g_pp);
+    double Dl[3], Bl[3];
+    lower(m, Dv, Dl);
+    lower(m, Bv, Bl);
+    double uf[3], Ef[3], Bf[3];
+    for (int a = 0; a < 3; ++a) {
+        uf[a] = Ef[a] = Bf[a] = 0.0;
+        for (int i = 0; i < 3; ++i) {
+            uf[a] += E[a][i] * u[i];
+            Ef[a] += E[a][i] * Dl[i];
+            Bf[a] += E[a][i] * Bl[i];
+        }
+    }
+    double dtau = m->alpha * dt;
+    double G = sqrt(1.0 + uf[0] * uf[0] + uf[1] * uf[1] + uf[2] * uf[2]);
+    double vxB[3] = {(uf[1] * Bf[2] - uf[2] * Bf[1]) / G, (uf[2] * Bf[0] - uf[0] * Bf[2]) / G,
+                     (uf[0] * Bf[1] - uf[1] * Bf[0]) / G};
+    double up[3], tau[3];
+    for (int a = 0; a < 3; ++a) {
+        up[a] = uf[a] + qm * dtau * (Ef[a] + 0.5 * vxB[a]);
+        tau[a] = 0.5 * qm * dtau * Bf[a];
+    }
+    double us = up[0] * tau[0] + up[1] * tau[1] + up[2] * tau[2];
+    double tt = tau[0] * tau[0] + tau[1] * tau[1] + tau[2] * tau[2];
+    double sigma = 1.0 + up[0] * up[0] + up[1] * up[1] + up[2] * up[2] - tt;
+    double G1 = sqrt(0.5 * (sigma + sqrt(sigma * sigma + 4.0 * (tt + us * us))));
+    double t[3] = {tau[0] / G1, tau[1] / G1, tau[2] / G1};
+    double s = 1.0 / (1.0 + (t[0] * t[0] + t[1] * t[1] + t[2] * t[2]));
+    double ut = up[0] * t[0] + up[1] * t[1] + up[2] * t[2];
+    double u1[3] = {s * (up[0] + ut * t[0] + (up[1] * t[2] - up[2] * t[1])),
+                    s * (up[1] + ut * t[1] + (up[2] * t[0] - up[0] * t[2])),
+                    s * (up[2] + ut * t[2] + (up[0] * t[1] - up[1] * t[0]))};
+    /* back to the coordinate covector: u_i = gamma_ij e^j_(a) u1_a */
+    double w[3] = {0, 0, 0};
+    for (int a = 0; a < 3; ++a)
+        for (int j = 0; j < 3; ++j) w[j] += E[a][j] * u1[a];
+    lower(m, w, u);
+}
+
+void orc_vay(double a, double r, double th, double qm, double dt, const double *Dv, const double *Bv, double *u)
+{
+    orc_metric m;
+    metric_at(a, r, th, &m);
+    vay_fido(&m, qm, dt, Dv, Bv, u);
+}
+
+/* Momentum update (generalized Boris, or Vay in the FIDO frame; skipped for
+ * photons or q = 0) then the geodesic predictor (Eq. geodesic-predictor) and
+ * n_iter trapezoidal correctors (Eq. geodesic-corrector), each re-evaluated
+ * at the latest iterate. y[2] = phi. */
 static void push_core(double a, double qm, int massive, double dt, int n_iter,
-                      const double Dv[3], const double Bv[3], double y[6])
+                      const double Dv[3], const double Bv[3], double y[6], int pusher)
 {
     if (massive && qm != 0.0) {
         orc_metric m;
         metric_at(a, y[0], y[1], &m);
-        boris(&m, qm, dt, Dv, Bv, &y[3]);
+        if (pusher == 1)
+            vay_fido(&m, qm, dt, Dv, Bv, &y[3]);
+        else
+            boris(&m, qm, dt, Dv, Bv, &y[3]);
     }
     double eps = massive ? 1.0 : 0.0;
     double y0[6], f0[6], yt[6], ft[6];
@@ -795,7 +873,7 @@ static void push_core(double a, double qm, int massive, double dt, int n_iter,
 /* one push with given field values (for pins of the pusher) */
 void orc_push_values(double a, double qm, int massive, double dt, int n_iter, const double *Dv, const double *Bv, double *y)
 {
-    push_core(a, qm, massive, dt, n_iter, Dv, Bv, y);
+    push_core(a, qm, massive, dt, n_iter, Dv, Bv, y, 0);
 }
 
 /* nsteps pushes with fields from the closed-form solution evaluated at x^n
@@ -808,7 +886,7 @@ int orc_push_analytic(int kind, double B0, double a, double qm, int massive, dou
     for (long s = 0; s < nsteps; ++s) {
         double Dv[3] = {0, 0, 0}, Bv[3] = {0, 0, 0};
         if (B0 != 0.0) closed_D(kind, a, B0, y[0], y[1], Dv, Bv);
-        push_core(a, qm, massive, dt, n_iter, Dv, Bv, y);
+        push_core(a, qm, massive, dt, n_iter, Dv, Bv, y, 0);
         if (every > 0 && (s + 1) % every == 0) {
             memcpy(traj + 6 * ns, y, 6 * sizeof(double));
             ++ns;
@@ -964,7 +1042,7 @@ int orc_push_deposit(const orc_cfg *c, long np, double *pr, double *pth, double 
         double x1a = (log(y[0]) - lnrin) / c->dx1, x2a = y[1] / c->dth;
         double Dv[3], Bv[3];
         interp_fields(c, D, B, x1a, x2a, Dv, Bv);
-        push_core(c->a, c->qm[sp], c->massive[sp], c->dt, c->n_push_iter, Dv, Bv, y);
+        push_core(c->a, c->qm[sp], c->massive[sp], c->dt, c->n_push_iter, Dv, Bv, y, c->pusher);
         /* axis reflection */
         if (y[1] < 0.0) { y[1] = -y[1]; y[4] = -y[4]; }
         if (y[1] > M_PI) { y[1] = 2.0 * M_PI - y[1]; y[4] = -y[4]; }

@@ -20,6 +20,7 @@
 #include "grpic_geo.cuh"
 #include "grpic_df.cuh"
 #include "grpic_window.cuh"
+#include "grpic_vay.cuh"
 
 #include <type_traits>
 
@@ -66,6 +67,7 @@ struct Push32Args {
     int32_t *keys;
     int32_t *count;
     int histogram;
+    int pusher;  // 0 generalized Boris, 1 Vay in the FIDO frame
     int *status;
 };
 
@@ -173,7 +175,7 @@ __device__ __forceinline__ float gather32(const float *__restrict__ F, int64_t l
 // metric is rebuilt from the quantities the geodesic evaluation keeps)
 template <typename M>
 __device__ __forceinline__ void boris_geo(const KSGeo<M> &m, M a, M r, M s, float qm, float dt, const float D[3],
-                                          const float B[3], float u[3])
+                                          const float B[3], float u[3], int pusher)
 {
     // gamma_rr = 1+z, gamma_thth = rho^2, gamma_phph = Sigma sin^2 / rho^2,
     // gamma_rph = -a sin^2 (1+z), sqrt(gamma) = rho^2 sin sqrt(1+z) = rho^2 sin / alpha
@@ -192,7 +194,13 @@ __device__ __forceinline__ void boris_geo(const KSGeo<M> &m, M a, M r, M s, floa
     mm.gi_tt = (float)m.gtt;
     mm.gi_pp = (float)m.gpp;
     mm.sqrtg = (float)(m.rho2 * s / m.alpha);
-    boris32<float>(mm, qm, dt, D, B, u);
+    if (pusher) {
+        const VayMetric<float> vm{mm.alpha, mm.g_rr, mm.g_rp, mm.g_tt, mm.g_pp, mm.gi_rr, mm.gi_rp, mm.gi_tt,
+                                  mm.gi_pp, mm.sqrtg};
+        vay_step<float>(vm, qm, dt, D, B, u);
+    } else {
+        boris32<float>(mm, qm, dt, D, B, u);
+    }
 }
 
 template <typename M>
@@ -236,7 +244,7 @@ __device__ __forceinline__ void push_one(const Push32Args &A, int i, int j, floa
         Bv[2] = gather32(A.B2, A.ld, Shh);
         S0h.p0 = S0h.p1 = 1.0f;
         Bv[0] = gather32(A.B0, A.ld, S0h);
-        boris_geo<M>(m, am, r0, s0, A.qm[sp], A.dt, Dv, Bv, u);
+        boris_geo<M>(m, am, r0, s0, A.qm[sp], A.dt, Dv, Bv, u, A.pusher);
     }
     const float eps = A.massive[sp] ? 1.0f : 0.0f;
     const float dt = A.dt, h = 0.5f * dt;
@@ -503,6 +511,7 @@ cudaError_t launch_push32(grpic_ctx *ctx, const grpic_particles *in, grpic_parti
     A.keys = ctx->d_keys;
     A.count = ctx->d_count;
     A.histogram = histogram ? 1 : 0;
+    A.pusher = ctx->prm.pusher;
     A.status = ctx->d_status;
     if (p->n <= 0) return cudaSuccess;
     push32_kernel<<<(unsigned)((p->n + 255) / 256), 256, 0, s>>>(A);

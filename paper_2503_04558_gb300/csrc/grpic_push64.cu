@@ -22,6 +22,7 @@
 //      for the sort.
 #include "grpic_internal.cuh"
 #include "grpic_window.cuh"
+#include "grpic_vay.cuh"
 
 namespace grpic {
 namespace {
@@ -49,6 +50,7 @@ struct Push64Args {
     int32_t *keys;
     int32_t *count;
     int histogram;
+    int pusher;  // 0 generalized Boris, 1 Vay in the FIDO frame
     int *status;
 };
 
@@ -127,6 +129,16 @@ __device__ __forceinline__ void boris(double a, double r, double th, double qm, 
     u[0] = um0 + sg * (x1 * s2 - x2 * s1) + h * Dl0;
     u[1] = um1 + sg * (x2 * s0 - x0 * s2) + h * Dl1;
     u[2] = um2 + sg * (x0 * s1 - x1 * s0) + h * Dl2;
+}
+
+// Vay's update in the FIDO frame with the metric at (r, theta)
+__device__ __forceinline__ void vay(double a, double r, double th, double qm, double dt, const double D[3],
+                                    const double B[3], double u[3])
+{
+    KS k;
+    ks_point(a, r, th, k);
+    VayMetric<double> m{k.alpha, k.g_rr, k.g_rp, k.g_tt, k.g_pp, k.gi_rr, k.gi_rp, k.gi_tt, k.gi_pp, k.sqrtg};
+    vay_step<double>(m, qm, dt, D, B, u);
 }
 
 // bilinear weights on a lattice staggered by (sr, st) cells
@@ -252,7 +264,10 @@ __global__ void __launch_bounds__(256) push64_kernel(Push64Args A)
             Bv[2] = gather(A.B2, A.ld, Shh);
             S0h.p0 = S0h.p1 = 1.0;  // B^r is even across the axis
             Bv[0] = gather(A.B0, A.ld, S0h);
-            boris(g.a, r, th, A.qm[sp], A.dt, Dv, Bv, u);
+            if (A.pusher)
+                vay(g.a, r, th, A.qm[sp], A.dt, Dv, Bv, u);
+            else
+                boris(g.a, r, th, A.qm[sp], A.dt, Dv, Bv, u);
         }
         // geodesic predictor-corrector (Sec. 2.2)
         double eps = A.massive[sp] ? 1.0 : 0.0;
@@ -441,6 +456,7 @@ cudaError_t launch_push64(grpic_ctx *ctx, const grpic_particles *in, grpic_parti
     A.keys = ctx->d_keys;
     A.count = ctx->d_count;
     A.histogram = histogram ? 1 : 0;
+    A.pusher = ctx->prm.pusher;
     A.status = ctx->d_status;
     if (p->n <= 0) return cudaSuccess;
     int64_t blocks = (p->n + 255) / 256;

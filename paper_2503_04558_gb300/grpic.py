@@ -38,7 +38,8 @@ class Params(C.Structure):
     _fields_ = [("dt", C.c_double), ("beta_field", C.c_double), ("n_field_iter", C.c_int32),
                 ("n_push_iter", C.c_int32), ("q_over_m", C.c_double * 4), ("q_weight", C.c_double * 4),
                 ("massive", C.c_int32 * 4), ("precision", C.c_int32), ("sort_every", C.c_int32),
-                ("fp64_radius", C.c_double), ("push_tol", C.c_double), ("island_arith", C.c_int32)]
+                ("fp64_radius", C.c_double), ("push_tol", C.c_double), ("island_arith", C.c_int32),
+                ("pusher", C.c_int32)]
 
 
 class ParticlesC(C.Structure):
@@ -127,6 +128,7 @@ class Config:
     fp64_radius: float = 0.0
     push_tol: float = 0.0
     island_arith: int = 0     # 0 double-FP32 pairs, 1 native FP64
+    pusher: int = 0           # 0 generalized Boris, 1 Vay in the FIDO frame
 
     def __post_init__(self):
         self.dx1 = math.log(self.r_out / self.r_in) / self.n_r
@@ -150,6 +152,7 @@ class Config:
         p.precision, p.sort_every, p.fp64_radius = self.precision, self.sort_every, self.fp64_radius
         p.push_tol = self.push_tol
         p.island_arith = self.island_arith
+        p.pusher = self.pusher
         return p
 
 

@@ -94,8 +94,9 @@ def test_fp32_field_update_error(G):
     assert max(errs) < 1e-5, errs
 
 
-def test_fp32_push_one_step_error(G):
-    oc, gc = cfg32(32, qw=(-0.01, 0.01, 0.01, 0.0))
+@pytest.mark.parametrize("pusher", [0, 1])
+def test_fp32_push_one_step_error(G, pusher):
+    oc, gc = cfg32(32, qw=(-0.01, 0.01, 0.01, 0.0), pusher=pusher)
     ctx = G.Context(gc)
     F = G.Fields(gc)
     ctx.init_fields(F, O.WALD, 2.0)

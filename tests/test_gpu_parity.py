@@ -87,8 +87,12 @@ def load_set(G, gc, P):
     return S
 
 
-def test_push_deposit_matches_oracle(G):
-    oc, gc = configs(32, 32, A09, 0.9 * RH, 20.0, qw=(-0.01, 0.01, 0.01, 0.0))
+@pytest.mark.parametrize("pusher", [0, 1])
+def test_push_deposit_matches_oracle(G, pusher):
+    """One push + deposit; pusher 0 the generalized Boris step, 1 Vay's update
+    in the FIDO frame (the oracle transforms with an explicit triad, the GPU
+    path uses the metric's dot and cross products)."""
+    oc, gc = configs(32, 32, A09, 0.9 * RH, 20.0, qw=(-0.01, 0.01, 0.01, 0.0), pusher=pusher)
     ctx, F = gpu_fields(G, gc, O.WALD, 2.0)
     D, B = O.init_fields(oc, O.WALD, 2.0)
     P = make_particles(oc, 20000, seed=3, sigma=0.5)
@@ -364,6 +368,8 @@ def test_invalid_arguments_are_rejected(G):
         GG.Context(GG.Config(16, 15, 0.9, 1.3, 20.0))     # odd n_theta
     with pytest.raises(GG.GrpicError):
         GG.Context(GG.Config(16, 16, 1.0, 1.3, 20.0))     # a = 1
+    with pytest.raises(GG.GrpicError):
+        GG.Context(GG.Config(16, 16, 0.9, 1.3, 20.0, pusher=2))   # no such pusher
     oc, gc = configs(16, 16, A09, 0.9 * RH, 20.0)
     ctx = GG.Context(gc)
     S = GG.ParticleSet(gc, 8)
@@ -445,3 +451,28 @@ def test_deferred_order_matches_separate_calls(G):
         assert relerr(h1[k], h0[k]) < 1e-12, k
     for a, b in zip(f1, f0):
         assert relerr(a, b) < 1e-12
+
+
+def test_vay_pusher_steps_match_oracle(G):
+    """Ten full steps with Vay's update in the FIDO frame (48 x 40, Wald
+    B0 = 2, 2e4 particles, sigma = 0.5) against the oracle: fields and
+    particles to 1e-10, the axis-grazing paths left out as in config 1."""
+    oc, gc = configs(48, 40, A09, 0.9 * RH, 20.0, qw=(-0.01, 0.01, 0.01, 0.0), pusher=1)
+    ctx, F = gpu_fields(G, gc, O.WALD, 2.0)
+    D, B = O.init_fields(oc, O.WALD, 2.0)
+    P = make_particles(oc, 20000, seed=17, sigma=0.5)
+    graze = axis_grazers(oc, P, D, B, 10)
+    P = P.take(np.setdiff1d(np.arange(P.n), graze))
+    S = load_set(G, gc, P)
+    ctx.step(S, F, 10)
+    assert ctx.sync() == 0
+    for _ in range(10):
+        st, P, J = O.step(oc, P, D, B)
+        assert st == 0
+    for k in range(3):
+        assert relerr(host(F.D[k]), D[k]) < TOL, ("D", k)
+        assert relerr(host(F.B[k]), B[k]) < TOL, ("B", k)
+    h = S.host()
+    assert np.array_equal(h["tag"], P.tag)
+    for k, ref in zip(("x1", "x2", "u1", "u2", "u3"), (P.r, P.th, P.u1, P.u2, P.u3)):
+        assert relerr(h[k], ref) < TOL, k

@@ -5,7 +5,10 @@ the closed-form fields it is driven by in the charged-orbit checks (App. C).
 Independent references: Hamilton's equations with the textbook Kerr metric
 (tests/kerr_indep.py), the conserved energy, angular momentum and Carter
 constant of Kerr geodesics, the printed Table 1 initial data (tests/golden),
-and the implicit equation the Boris scheme solves (Eq. boris-step)."""
+the implicit equation the Boris scheme solves (Eq. boris-step), and for the
+alternative Vay update in the FIDO frame the implicit equation of Vay's
+scheme, its drift property and energy conservation in a pure magnetic
+field."""
 import math
 import os
 
@@ -137,6 +140,103 @@ def test_boris_rotation_preserves_norm_without_electric_field(seed):
     _, _, _, gi = K.three_plus_one(a, r, th)
     n0, n1 = u @ gi @ u, up @ gi @ up
     assert abs(n1 - n0) < 1e-13 * n0
+
+
+# ---------------------------------------------------------------------------
+# the alternative momentum update: Vay's step in the FIDO frame (Sec. 2.2)
+# ---------------------------------------------------------------------------
+def _vay_residual(a, r, th, qm, dt, Dv, Bv, u):
+    """Residual of Vay's implicit equation over the FIDO proper time alpha dt,
+    u1 - u = (q/m) alpha dt (E + (u/Gamma + u1/Gamma1)/2 x B), in coordinate
+    components with the independent 3+1 metric: E_i = gamma_ij D^j, the
+    cross product e_ijk V^j B^k of the raised velocity, Gamma = sqrt(1 +
+    gamma^ij u_i u_j)."""
+    alpha, beta, gam, gi = K.three_plus_one(a, r, th)
+    sqrtg = math.sqrt(np.linalg.det(gam))
+    u = np.asarray(u, np.float64)
+    u1 = O.vay(a, r, th, qm, dt, Dv, Bv, u)
+    G0 = math.sqrt(1 + u @ gi @ u)
+    G1 = math.sqrt(1 + u1 @ gi @ u1)
+    v = gi @ (u / G0 + u1 / G1) / 2
+    B = np.asarray(Bv)
+    cross = sqrtg * np.array([v[1] * B[2] - v[2] * B[1], v[2] * B[0] - v[0] * B[2], v[0] * B[1] - v[1] * B[0]])
+    res = u1 - u - qm * alpha * dt * (gam @ np.asarray(Dv) + cross)
+    return res, u1, gi
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_vay_solves_its_implicit_equation(seed):
+    rng = np.random.default_rng(300 + seed)
+    a = rng.uniform(0, 0.999)
+    r = rng.uniform(1.2, 30)
+    th = rng.uniform(0.1, 3.0)
+    Dv = rng.normal(size=3) * [1, 1 / r, 1 / r]
+    Bv = rng.normal(size=3) * [3, 3 / r, 3 / r]
+    u = rng.normal(size=3) * [2, 2 * r, 2 * r]
+    res, u1, _ = _vay_residual(a, r, th, rng.choice([-1.0, 1.0]), 0.05, Dv, Bv, u)
+    assert np.max(np.abs(res)) < 1e-12 * max(1.0, np.max(np.abs(u1)))
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_vay_preserves_norm_without_electric_field(seed):
+    rng = np.random.default_rng(400 + seed)
+    a, r, th = 0.9, rng.uniform(1.5, 10), rng.uniform(0.2, 2.9)
+    Bv = rng.normal(size=3) * [10, 10 / r, 10 / r]
+    u = rng.normal(size=3) * [1, r, r]
+    u1 = O.vay(a, r, th, 1.0, 0.1, [0, 0, 0], Bv, u)
+    _, _, _, gi = K.three_plus_one(a, r, th)
+    n0, n1 = u @ gi @ u, u1 @ gi @ u1
+    assert abs(n1 - n0) < 1e-12 * n0
+
+
+def test_vay_pure_electric_kick_is_exact():
+    a, r, th = 0.7, 3.3, 1.1
+    alpha, _, gam, _ = K.three_plus_one(a, r, th)
+    Dv = np.array([0.4, -0.07, 0.02])
+    u = np.array([0.3, -1.2, 2.5])
+    u1 = O.vay(a, r, th, -1.0, 0.2, Dv, [0, 0, 0], u)
+    np.testing.assert_allclose(u1, u - alpha * 0.2 * (gam @ Dv), rtol=1e-14, atol=1e-14)
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_vay_leaves_the_drift_momentum_unchanged(seed):
+    """Vay's defining property: a particle whose velocity cancels the
+    electric field (E + v x B = 0, any Lorentz factor) is not accelerated.
+    The field D is built from u and B with the independent metric."""
+    rng = np.random.default_rng(500 + seed)
+    a, r, th = rng.uniform(0, 0.99), rng.uniform(1.5, 20), rng.uniform(0.3, 2.8)
+    _, _, gam, gi = K.three_plus_one(a, r, th)
+    sqrtg = math.sqrt(np.linalg.det(gam))
+    Bv = rng.normal(size=3) * [5, 5 / r, 5 / r]
+    # a momentum perpendicular to B (frame dot product u_i B^i = 0), Gamma ~ 10^2
+    u = rng.normal(size=3) * [1, r, r]
+    u = u - (u @ Bv) / (Bv @ gam @ Bv) * (gam @ Bv)
+    u *= 100.0 / math.sqrt(u @ gi @ u)
+    G = math.sqrt(1 + u @ gi @ u)
+    v = gi @ u / G
+    vxB = sqrtg * np.array([v[1] * Bv[2] - v[2] * Bv[1], v[2] * Bv[0] - v[0] * Bv[2], v[0] * Bv[1] - v[1] * Bv[0]])
+    Dv = -gi @ vxB   # E_i = gamma_ij D^j = -(v x B)_i
+    u1 = O.vay(a, r, th, 1.0, 0.05, Dv, Bv, u)
+    dv = np.max(np.abs(u1 - u))
+    assert dv < 1e-11 * np.max(np.abs(u))
+    # the generalized Boris step does not keep it (it averages u^- and u^+
+    # with the Lorentz factor of u^-)
+    db = np.max(np.abs(O.boris(a, r, th, 1.0, 0.05, Dv, Bv, u) - u))
+    assert db > 1e2 * max(dv, 1e-16 * np.max(np.abs(u)))
+
+
+def test_vay_and_boris_differ_at_third_order():
+    """Both steps are second-order accurate for the same force, so one step
+    of each differs by O(dt^3)."""
+    rng = np.random.default_rng(7)
+    a, r, th = 0.9, 4.0, 1.0
+    Dv = rng.normal(size=3) * [1, 0.25, 0.25]
+    Bv = rng.normal(size=3) * [3, 0.75, 0.75]
+    u = rng.normal(size=3) * [1, 4, 4]
+    diffs = []
+    for dt in (0.04, 0.02, 0.01):
+        diffs.append(np.max(np.abs(O.vay(a, r, th, 1.0, dt, Dv, Bv, u) - O.boris(a, r, th, 1.0, dt, Dv, Bv, u))))
+    assert 6.0 < diffs[0] / diffs[1] < 10.0 and 6.0 < diffs[1] / diffs[2] < 10.0, diffs
 
 
 # ---------------------------------------------------------------------------
