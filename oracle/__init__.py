@@ -48,7 +48,7 @@ class Cfg(C.Structure):
                 ("n_fld_iter", C.c_int), ("n_push_iter", C.c_int),
                 ("damp_cells", C.c_int), ("damp_max", C.c_double),
                 ("qm", C.c_double * 4), ("qw", C.c_double * 4), ("massive", C.c_int * 4),
-                ("pusher", C.c_int)]
+                ("pusher", C.c_int), ("shape", C.c_int)]
 
 
 _lib = None
@@ -71,6 +71,7 @@ def lib():
             "orc_geodesic_rhs": (None, [d, d, p, p]),
             "orc_boris": (None, [d, d, d, d, d, p, p, p]),
             "orc_vay": (None, [d, d, d, d, d, p, p, p]),
+            "orc_w3": (d, [d]),
             "orc_push_values": (None, [d, d, i, d, i, p, p, p]),
             "orc_push_analytic": (i, [i, d, d, d, i, d, i, p, l, l, p]),
             "orc_interp": (None, [pc, p, p, p, p, p, p, d, d, p]),
@@ -105,7 +106,7 @@ def horizon(a: float) -> float:
 
 def make_cfg(nr, nth, a, r_in, r_out, dt=None, cfl=0.5, beta_s=0.53, n_fld_iter=7, n_push_iter=3,
              damp_cells=None, damp_max=0.1, qm=(-1.0, 1.0, 1.0, 0.0), qw=(-1e-3, 1e-3, 1e-3, 0.0),
-             massive=(1, 1, 1, 0), pusher=0) -> Cfg:
+             massive=(1, 1, 1, 0), pusher=0, shape=1) -> Cfg:
     """Grid uniform in ln r and theta; dt from the CFL reading
     dt = cfl * min(dr, r dtheta) at r_in when not given."""
     c = Cfg()
@@ -125,6 +126,7 @@ def make_cfg(nr, nth, a, r_in, r_out, dt=None, cfl=0.5, beta_s=0.53, n_fld_iter=
     for k in range(4):
         c.qm[k], c.qw[k], c.massive[k] = qm[k], qw[k], massive[k]
     c.pusher = pusher
+    c.shape = shape
     return c
 
 
@@ -197,6 +199,11 @@ def boris(a, r, th, qm, dt, Dv, Bv, u):
     u = np.array(u, dtype=np.float64)
     lib().orc_boris(a, r, th, qm, dt, _p(np.asarray(Dv, np.float64)), _p(np.asarray(Bv, np.float64)), _p(u))
     return u
+
+
+def w3(x) -> float:
+    """The cubic B-spline weight of the third-order shape."""
+    return lib().orc_w3(float(x))
 
 
 def vay(a, r, th, qm, dt, Dv, Bv, u):

@@ -64,6 +64,8 @@ typedef struct {
     int massive[4];    /* epsilon in u^0 (1 massive, 0 photon)               */
     int pusher;        /* momentum update: 0 generalized Boris, 1 Vay in the  */
                        /* FIDO frame (Sec. 2.2)                              */
+    int shape;         /* particle shape (Sec. 2.3): 1 cloud in cell, 3 the  */
+                       /* third-order (cubic B-) spline                      */
 } orc_cfg;
 
 /* ------------------------------------------------------------------------ */
@@ -945,11 +947,124 @@ static void interp_fields(const orc_cfg *c, double *const D[3], double *const B[
     Bv[2] = interp(c, B[2], x1, x2, 0.5, 1, 1.0);
 }
 
+/* ------------------------------------------------------------------------ */
+/* Third-order spline shape (Sec. 2.3's configuration option): the cubic    */
+/* B-spline in logical units, the convolution of four unit boxes,           */
+/*   W3(x) = 2/3 - x^2 + |x|^3/2        for |x| < 1,                         */
+/*         = (2 - |x|)^3 / 6            for 1 <= |x| < 2,   0 beyond,        */
+/* and S = W3(x1 - i) W3(x2 - j) on each lattice.  Rows past the polar axis */
+/* are the mirror rows of the relabelling (r, -theta, phi + pi) of the same */
+/* point: theta components change sign, r and phi components do not.       */
+/* ------------------------------------------------------------------------ */
+static double W3(double d)
+{
+    d = fabs(d);
+    if (d < 1.0) return 2.0 / 3.0 - d * d + 0.5 * d * d * d;
+    if (d < 2.0) { double e = 2.0 - d; return e * e * e / 6.0; }
+    return 0.0;
+}
+
+/* mirror of row j and its parity: integer (vertex) rows theta_j = j dth,
+ * half rows theta_{j+1/2} */
+double orc_w3(double d) { return W3(d); }
+
+static int mirror_row(const orc_cfg *c, int j, int half_t, int *flip)
+{
+    *flip = 0;
+    int top = half_t ? c->nth - 1 : c->nth;
+    if (j < 0) { *flip = 1; return half_t ? -1 - j : -j; }
+    if (j > top) { *flip = 1; return half_t ? 2 * c->nth - 1 - j : 2 * c->nth - j; }
+    return j;
+}
+
+static double interp3(const orc_cfg *c, const double *F, double x1, double x2, double sr, int half_t, double par)
+{
+    double xi = x1 - sr, eta = x2 - (half_t ? 0.5 : 0.0);
+    int i = (int)floor(xi), j = (int)floor(eta);
+    double v = 0.0;
+    for (int a = -1; a <= 2; ++a) {
+        double wr = W3(xi - (i + a));
+        for (int b = -1; b <= 2; ++b) {
+            int flip, jj = mirror_row(c, j + b, half_t, &flip);
+            v += wr * W3(eta - (j + b)) * (flip ? par : 1.0) * F[IDX(c, i + a, jj)];
+        }
+    }
+    return v;
+}
+
+static void interp_fields3(const orc_cfg *c, double *const D[3], double *const B[3], double x1, double x2,
+                           double Dv[3], double Bv[3])
+{
+    Dv[0] = interp3(c, D[0], x1, x2, 0.5, 0, 1.0);
+    Dv[1] = interp3(c, D[1], x1, x2, 0.0, 1, -1.0);
+    Dv[2] = interp3(c, D[2], x1, x2, 0.0, 0, 1.0);
+    Bv[0] = interp3(c, B[0], x1, x2, 0.0, 1, 1.0);
+    Bv[1] = interp3(c, B[1], x1, x2, 0.5, 0, -1.0);
+    Bv[2] = interp3(c, B[2], x1, x2, 0.5, 1, 1.0);
+}
+
 void orc_interp(const orc_cfg *c, double *D0, double *D1, double *D2, double *B0r, double *B1, double *B2,
                 double x1, double x2, double *out6)
 {
     double *D[3] = {D0, D1, D2}, *B[3] = {B0r, B1, B2};
-    interp_fields(c, D, B, x1, x2, out6, out6 + 3);
+    if (c->shape == 3)
+        interp_fields3(c, D, B, x1, x2, out6, out6 + 3);
+    else
+        interp_fields(c, D, B, x1, x2, out6, out6 + 3);
+}
+
+/* Eq. esirkepov-decomp and j-phi-deposit with the cubic shape: the window
+ * spans the 5 x 5 vertices (b1 .. b1+4, b2 .. b2+4) around both positions
+ * (b = the lower of the two cells, minus 1); W_r, W_theta from the four shape
+ * products, prefix sums along r (J^r A at faces b1+A+1/2) and theta.  Entries
+ * past the polar axis are added to their mirror entries (J^r A, J^phi even,
+ * J^theta A odd; the axis rows are their own mirrors); columns past the
+ * storage (a particle leaving through r_out) are dropped. */
+static void fold_add(const orc_cfg *c, double *F, int i, int j, int half_t, double odd, double v)
+{
+    if (v == 0.0 || i < -c->ng || i > c->nr + c->ng - 1) return;
+    int flip, jj = mirror_row(c, j, half_t, &flip);
+    F[IDX(c, i, jj)] += flip ? odd * v : v;
+}
+
+static void deposit_one3(const orc_cfg *c, const double *dV, double *JrA, double *JtA, double *Jph,
+                         double qw, double r0x, double t0x, double r1x, double t1x, double dphi)
+{
+    int fr0 = (int)floor(r0x), fr1 = (int)floor(r1x);
+    int b1 = (fr0 < fr1 ? fr0 : fr1) - 1;
+    int j0 = (int)floor(t0x), j1 = (int)floor(t1x);
+    int b2 = (j0 < j1 ? j0 : j1) - 1;
+    double Wr[5][5], Wt[5][5];
+    for (int A = 0; A < 5; ++A)
+        for (int Bb = 0; Bb < 5; ++Bb) {
+            int k = b1 + A, l = b2 + Bb;
+            double S00 = W3(r0x - k) * W3(t0x - l);
+            double S11 = W3(r1x - k) * W3(t1x - l);
+            double S10 = W3(r1x - k) * W3(t0x - l);
+            double S01 = W3(r0x - k) * W3(t1x - l);
+            Wr[A][Bb] = S11 - S01 + S10 - S00;
+            Wt[A][Bb] = S11 - S10 + S01 - S00;
+            double sbar = S11 / 3.0 + S10 / 6.0 + S01 / 6.0 + S00 / 3.0;
+            if (sbar != 0.0) {
+                int flip, ll = mirror_row(c, l, 0, &flip);
+                if (k >= -c->ng && k <= c->nr + c->ng - 1)
+                    Jph[IDX(c, k, ll)] += qw * (dphi / c->dt) * sbar / dV[IDX(c, k, ll)];
+            }
+        }
+    for (int Bb = 0; Bb < 5; ++Bb) {
+        double acc = 0.0;
+        for (int A = 0; A < 4; ++A) {
+            acc += Wr[A][Bb];
+            fold_add(c, JrA, b1 + A, b2 + Bb, 0, 1.0, -qw / (2.0 * c->dt) * acc);
+        }
+    }
+    for (int A = 0; A < 5; ++A) {
+        double acc = 0.0;
+        for (int Bb = 0; Bb < 4; ++Bb) {
+            acc += Wt[A][Bb];
+            fold_add(c, JtA, b1 + A, b2 + Bb, 1, -1.0, -qw / (2.0 * c->dt) * acc);
+        }
+    }
 }
 
 /* ------------------------------------------------------------------------ */
@@ -1013,7 +1128,10 @@ void orc_deposit_one(const orc_cfg *c, double *JrA, double *JtA, double *Jph, do
                      double r0x, double t0x, double r1x, double t1x, double dphi)
 {
     orc_geom g = *geom_get(c); /* shallow copy of the cached tables */
-    deposit_one(c, g.AD[2], JrA, JtA, Jph, qw, r0x, t0x, r1x, t1x, dphi);
+    if (c->shape == 3)
+        deposit_one3(c, g.AD[2], JrA, JtA, Jph, qw, r0x, t0x, r1x, t1x, dphi);
+    else
+        deposit_one(c, g.AD[2], JrA, JtA, Jph, qw, r0x, t0x, r1x, t1x, dphi);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -1041,7 +1159,10 @@ int orc_push_deposit(const orc_cfg *c, long np, double *pr, double *pth, double 
         double y[6] = {pr[p], pth[p], 0.0, pu1[p], pu2[p], pu3[p]};
         double x1a = (log(y[0]) - lnrin) / c->dx1, x2a = y[1] / c->dth;
         double Dv[3], Bv[3];
-        interp_fields(c, D, B, x1a, x2a, Dv, Bv);
+        if (c->shape == 3)
+            interp_fields3(c, D, B, x1a, x2a, Dv, Bv);
+        else
+            interp_fields(c, D, B, x1a, x2a, Dv, Bv);
         push_core(c->a, c->qm[sp], c->massive[sp], c->dt, c->n_push_iter, Dv, Bv, y, c->pusher);
         /* axis reflection */
         if (y[1] < 0.0) { y[1] = -y[1]; y[4] = -y[4]; }
@@ -1057,7 +1178,10 @@ int orc_push_deposit(const orc_cfg *c, long np, double *pr, double *pth, double 
             if (dphi_out) dphi_out[p] = 0.0;
             continue;
         }
-        deposit_one(c, g.AD[2], J0, J1, J2, c->qw[sp], x1a, x2a, x1b, x2b, y[2]);
+        if (c->shape == 3)
+            deposit_one3(c, g.AD[2], J0, J1, J2, c->qw[sp], x1a, x2a, x1b, x2b, y[2]);
+        else
+            deposit_one(c, g.AD[2], J0, J1, J2, c->qw[sp], x1a, x2a, x1b, x2b, y[2]);
         pr[p] = y[0]; pth[p] = y[1]; pu1[p] = y[3]; pu2[p] = y[4]; pu3[p] = y[5];
         if (dphi_out) dphi_out[p] = y[2];
         if (y[0] < c->r_in || y[0] >= c->r_out) tag[p] |= ORC_DEAD;
@@ -1119,6 +1243,18 @@ void orc_rho(const orc_cfg *c, long np, const double *pr, const double *pth, con
     for (long p = 0; p < np; ++p) {
         if (tag[p] & ORC_DEAD) continue;
         double x1 = (log(pr[p]) - lnrin) / c->dx1, x2 = pth[p] / c->dth;
+        if (c->shape == 3) {
+            int i = (int)floor(x1), j = (int)floor(x2);
+            for (int A = -1; A <= 2; ++A)
+                for (int Bb = -1; Bb <= 2; ++Bb) {
+                    int k = i + A, l = j + Bb, flip;
+                    if (k < -c->ng || k > c->nr + c->ng - 1) continue;
+                    int ll = mirror_row(c, l, 0, &flip);
+                    double S = W3(x1 - k) * W3(x2 - l);
+                    rho[IDX(c, k, ll)] += c->qw[tag[p] & 3u] * S / g.AD[2][IDX(c, k, ll)];
+                }
+            continue;
+        }
         int i = (int)floor(x1), j = jcell(c, x2);
         for (int A = 0; A < 2; ++A)
             for (int Bb = 0; Bb < 2; ++Bb) {

@@ -5,7 +5,9 @@ interpolation, its full time step (continuity of Sec. 3.4) and its sort.
 Independent references: the discrete continuity equation written out with a
 cloud-in-cell shape of the test's own, the total current moments of a moving
 charge, exactness of bilinear interpolation on linear data, the stable
-argsort of numpy."""
+argsort of numpy; for the third-order (cubic B-) spline shape its moments and
+knot smoothness, the same continuity with the test's own folded cubic
+density, and linear reproduction."""
 import math
 
 import numpy as np
@@ -111,11 +113,15 @@ def test_interpolation_reproduces_linear_fields_and_axis_parity():
 
 
 def _charge_residual(c, D0, P0, D1, P1):
-    """max over interior vertices of |(div D - rho)^1 - (div D - rho)^0|."""
+    """max over interior vertices of |(div D - rho)^1 - (div D - rho)^0|.
+    Interior: from column 1 (the cubic shape: 2, since a particle absorbed
+    just inside r_in still covers vertex 1 with its cloud) to the damping
+    layer."""
     r0 = O.divD(c, D0) - O.rho(c, P0)
     r1 = O.divD(c, D1) - O.rho(c, P1)
     last = c.nr - c.damp_cells - 1
-    sl = (slice(0, c.nth + 1), slice(c.ng + 1, c.ng + last + 1))
+    first = 2 if c.shape == 3 else 1
+    sl = (slice(0, c.nth + 1), slice(c.ng + first, c.ng + last + 1))
     return np.max(np.abs(r1 - r0)[sl]), np.max(np.abs(O.rho(c, P1)[sl]))
 
 
@@ -140,6 +146,120 @@ def test_full_steps_conserve_charge_to_round_off():
         worst = max(worst, res / rmax)
     assert worst < 1e-12, worst
     assert P.n < 3000   # the inner-boundary particle left the domain
+
+
+# ---------------------------------------------------------------------------
+# third-order spline shape (the configuration option of Sec. 2.3)
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("x", [0.0, 0.37, 0.5, 0.93, -1.2, 2.71])
+def test_cubic_spline_weights_are_the_cubic_b_spline(x):
+    """Partition of unity, first moment x and second moment x^2 + 1/3 (the
+    variance of four unit boxes convolved) over the 4 nonzero weights, support
+    |d| < 2, and C^2 joins at the knots 1 and 2."""
+    ks = np.arange(math.floor(x) - 3, math.floor(x) + 5)
+    w = np.array([O.w3(x - k) for k in ks])
+    assert np.all(w >= 0) and np.count_nonzero(w) <= 4
+    assert w.sum() == pytest.approx(1.0, abs=1e-15)
+    assert (ks * w).sum() == pytest.approx(x, abs=1e-14)
+    assert (ks * ks * w).sum() == pytest.approx(x * x + 1.0 / 3.0, abs=1e-13)
+    for knot in (1.0, 2.0):
+        h = 1e-5
+        d1 = [(O.w3(knot + s * h + h) - O.w3(knot + s * h - h)) / (2 * h) for s in (-2, 2)]
+        d2 = [(O.w3(knot + s * h + h) - 2 * O.w3(knot + s * h) + O.w3(knot + s * h - h)) / h ** 2 for s in (-2, 2)]
+        # one-sided values 4h apart: the first derivatives differ by about
+        # 4h times the second, the second derivatives by 4h times the third
+        assert abs(d1[0] - d1[1]) < 10 * h and abs(d2[0] - d2[1]) < 1e-3
+    assert O.w3(2.0) == 0.0 and O.w3(2.5) == 0.0
+
+
+def cubic_density(c, x1, x2, q):
+    """q * S_kl at every vertex with the cubic shape, rows past the polar axis
+    added to their mirror rows (theta -> -theta, 2 pi - theta)."""
+    out = np.zeros(O.field_shape(c))
+    i, j = int(math.floor(x1)), int(math.floor(x2))
+    for k in range(i - 1, i + 3):
+        if k < -c.ng or k > c.nr + c.ng - 1:
+            continue
+        for l in range(j - 1, j + 3):
+            m = -l if l < 0 else (2 * c.nth - l if l > c.nth else l)
+            out[m, k + c.ng] += q * O.w3(x1 - k) * O.w3(x2 - l)
+    return out
+
+
+CUBIC_MOVES = MOVES[:6] + [((4.4, 0.6), (4.1, 0.1)), ((5.2, 1.4), (5.9, 0.6)), ((6.0, 11.3), (6.6, 11.98)),
+                           ((3.1, 10.2), (3.7, 11.1)), ((2.5, 0.0), (2.5, 0.7))]
+
+
+@pytest.mark.parametrize("p0,p1", CUBIC_MOVES)
+def test_cubic_single_particle_continuity_is_exact(p0, p1):
+    """With the cubic shape, near the polar axis included (ghost rows folded:
+    J^r A even, J^theta A odd), q (S^{n+1} - S^n) = -dt div(J A) at every
+    vertex."""
+    c = cfg(shape=3)
+    qw = 0.37
+    JrA, JtA, Jph = O.deposit_one(c, qw, p0[0], p0[1], p1[0], p1[1], 0.0)
+    drho = cubic_density(c, *p1, qw) - cubic_density(c, *p0, qw)
+    div = divergence_of_flux(c, JrA, JtA)
+    np.testing.assert_allclose(drho, -c.dt * div, rtol=0, atol=2e-15)
+    assert np.all(Jph == 0)
+
+
+def test_cubic_static_particle_radial_motion_and_moments():
+    c = cfg(shape=3)
+    JrA, JtA, Jph = O.deposit_one(c, 1.0, 4.3, 5.6, 4.3, 5.6, 0.0)
+    assert np.all(JrA == 0) and np.all(JtA == 0) and np.all(Jph == 0)
+    JrA, JtA, Jph = O.deposit_one(c, 1.0, 4.3, 5.6, 4.9, 5.6, 0.0)
+    assert np.all(JtA == 0)
+    AD, _ = O.areas(c)
+    x0, x1, dphi, q = (4.3, 5.6), (4.8, 5.45), 0.013, -2.0
+    JrA, JtA, Jph = O.deposit_one(c, q, *x0, *x1, dphi)
+    assert JrA.sum() == pytest.approx(q * (x1[0] - x0[0]) / c.dt, rel=1e-12)
+    assert JtA.sum() == pytest.approx(q * (x1[1] - x0[1]) / c.dt, rel=1e-12)
+    assert (Jph * AD[2]).sum() == pytest.approx(q * dphi / c.dt, rel=1e-12)
+
+
+def test_cubic_interpolation_reproduces_linear_fields():
+    """The cubic B-spline reproduces linear data exactly (first moment), on
+    every staggered lattice, away from the axis and the radial ends."""
+    c = cfg(shape=3)
+    stag = [(0.5, 0.0), (0.0, 0.5), (0.0, 0.0), (0.0, 0.5), (0.5, 0.0), (0.5, 0.5)]
+    coef = [(0.3, 1.1, -0.7), (-2.0, 0.4, 0.9), (1.5, -0.3, 0.2), (0.1, 0.2, 0.3), (-0.6, 0.8, -1.2), (2.2, 0.5, 0.5)]
+    F = []
+    for (sr, st), (a0, a1, a2) in zip(stag, coef):
+        col = np.arange(c.ld) - c.ng + sr
+        row = np.arange(c.nth + 1) + st
+        F.append(a0 + a1 * col[None, :] + a2 * row[:, None])
+    for x1, x2 in [(3.3, 4.6), (2.1, 7.2), (8.9, 2.3), (5.5, 5.5)]:
+        v = O.interp(c, F[:3], F[3:], x1, x2)
+        ref = [a0 + a1 * x1 + a2 * x2 for (a0, a1, a2) in coef]
+        np.testing.assert_allclose(v, ref, rtol=0, atol=1e-13)
+    # next to the axis the mirror rows carry the parities: a constant theta
+    # component averages to less than the constant, the others keep it
+    G = [np.ones(O.field_shape(c)) for _ in range(6)]
+    v = O.interp(c, G[:3], G[3:], 4.2, 0.6)
+    for k in (0, 2, 3, 5):
+        assert v[k] == pytest.approx(1.0, abs=1e-14)
+    assert v[1] < 1.0 and v[4] < 1.0
+
+
+def test_cubic_full_steps_conserve_charge_to_round_off():
+    """Sec. 3.4's continuity with the cubic shape: push, deposit (folded at
+    the axis), field update and sort keep div D - rho to round-off."""
+    c = cfg(n=24, qw=(-0.05, 0.05, 0.05, 0.0), shape=3)
+    D, B = O.init_fields(c, O.WALD, 1.0)
+    arrs = synth.particles(c.nr, c.nth, c.r_in, c.r_out, 3000, seed=9, sigma=0.6)
+    P = O.Particles(*arrs)
+    P.th[0], P.u2[0] = 0.3 * c.dth, -3.0 * P.r[0]
+    P.th[1], P.u2[1] = math.pi - 0.4 * c.dth, 3.0 * P.r[1]
+    D0 = [x.copy() for x in D]
+    P0 = P.copy()
+    worst = 0.0
+    for _ in range(6):
+        st, P, J = O.step(c, P, D, B)
+        assert st == 0
+        res, rmax = _charge_residual(c, D0, P0, D, P)
+        worst = max(worst, res / rmax)
+    assert worst < 1e-12, worst
 
 
 def test_sort_matches_stable_argsort():
