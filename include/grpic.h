@@ -106,7 +106,13 @@ typedef struct {
  * pusher: the momentum update of charged particles (Sec. 2.2): 0 the
  * generalized Boris step (Eqs. boris-plus-minus .. boris-scheme, the
  * default), 1 Vay's update in the FIDO frame (the paper's alternative; the
- * differentiable form supports 0 only). */
+ * differentiable form supports 0 only).
+ * shape_order: the particle shape of the interpolation and of the
+ * Esirkepov deposit (Sec. 2.3): 1 cloud in cell (the default), 3 the
+ * third-order (cubic B-) spline, FP64 path only (the FP32 form and the
+ * differentiable form refuse it).  With the cubic shape a particle's cloud
+ * reaches two rows past the polar axis, folded back with the axis parities,
+ * and two columns into the guard columns. */
 typedef struct {
     double dt;
     double beta_field;
@@ -121,6 +127,7 @@ typedef struct {
     double push_tol;
     int32_t island_arith;
     int32_t pusher;
+    int32_t shape_order;
 } grpic_params;
 
 typedef struct {
@@ -211,7 +218,8 @@ grpic_status grpic_diagnostics(grpic_ctx *ctx, const grpic_particles *p, const g
  * the precision) and div D (Eq. J-integral-eqn, formed in FP64 from the
  * stored D) at the vertices; out[0] = max |div D - rho - base| and out[1] =
  * max |rho| over the interior vertices (columns 1 .. n_r - damp_cells - 1, all
- * rows: the guard copies and the damping layer change div D by design), as
+ * rows, from column 2 with the cubic shape; the guard copies and the damping
+ * layer change div D by design), as
  * host doubles.  base: NULL or a device (n_theta+1) x ld FP64 array of an
  * earlier call's div D - rho (so that out[0] measures the change since);
  * state: NULL or such an array to receive this call's div D - rho.  p may be

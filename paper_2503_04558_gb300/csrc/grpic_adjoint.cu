@@ -1356,7 +1356,7 @@ extern "C" grpic_status grpic_adjoint_grad(grpic_ctx *ctx, const grpic_particles
     if (!ctx || !p0 || !f0 || !L_out || ctx->prm.precision != 64 || nsteps < 1 || checkpoint_every < 1 ||
         i_horizon < 1 || i_horizon > ctx->g.nr - 1 || ctx->prm.n_field_iter < 1 || f0->ld < ctx->g.nr + 2 * NG ||
         p0->n < 0 || p0->n > INT32_MAX || (!grad_p && (grad_f || dL_da)) || ctx->prm.n_push_iter > MAX_ITER ||
-        ctx->prm.pusher != 0)
+        ctx->prm.pusher != 0 || ctx->prm.shape_order != 1)
         return GRPIC_EINVAL;
     const bool want = grad_p != nullptr;  // NULL: the objective alone
     if (want)

@@ -259,6 +259,7 @@ grpic_status grpic_init(grpic_metric metric, double spin, const grpic_grid *grid
     if (prm->precision != 64 && prm->precision != 32) return GRPIC_EINVAL;
     if (prm->island_arith != 0 && prm->island_arith != 1) return GRPIC_EINVAL;
     if (prm->pusher != 0 && prm->pusher != 1) return GRPIC_EINVAL;
+    if (!(prm->shape_order == 1 || (prm->shape_order == 3 && prm->precision == 64))) return GRPIC_EINVAL;
     if (!(prm->beta_field >= 0.0 && prm->beta_field <= 1.0)) return GRPIC_EINVAL;
 
     grpic_ctx *ctx = new (std::nothrow) grpic_ctx();

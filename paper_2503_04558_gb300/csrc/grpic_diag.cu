@@ -5,6 +5,7 @@
 // deposit.  Also the standalone deposit entry (moves given by two particle
 // states and their azimuthal displacement).
 #include "grpic_internal.cuh"
+#include "grpic_shape3.cuh"
 
 namespace grpic {
 namespace {
@@ -34,7 +35,8 @@ __device__ __forceinline__ void logical(const GridDev &g, const void *x1, const 
 // charge check)
 template <typename T, typename A = T>
 __global__ void rho_particles(GridDev g, int64_t nmax, const int64_t *d_count, const void *x1, const void *x2,
-                              const int32_t *cell, const uint32_t *tag, const double *qw, A *rho, int64_t ld)
+                              const int32_t *cell, const uint32_t *tag, const double *qw, A *rho, int64_t ld,
+                              int shape)
 {
     int64_t n = d_count ? *d_count : nmax;
     if (n > nmax) n = nmax;
@@ -45,6 +47,23 @@ __global__ void rho_particles(GridDev g, int64_t nmax, const int64_t *d_count, c
     double a, b;
     logical<T>(g, x1, x2, cell, p, a, b);
     if (!(a >= -1.0 && a < g.nr + 1.0 && b >= 0.0 && b <= (double)g.nth)) return;  // outside the arrays
+    if (shape == 3) {
+        // cubic weights on the 4 x 4 vertices, rows past the axis folded
+        // (even), columns past the guard columns dropped
+        const int i = (int)floor(a), j = (int)floor(b);
+        const double q = qw[t & 3u];
+        for (int ka = -1; ka <= 2; ++ka) {
+            const int k = i + ka;
+            if (k < -NG || k > g.nr + NG - 1) continue;
+            const double wr = w3(a - k);
+            for (int lb = -1; lb <= 2; ++lb) {
+                bool flip;
+                const int l = mirror_row(j + lb, false, g.nth, flip);
+                atomicAdd(rho + (size_t)l * ld + k + NG, (A)(q * wr * w3(b - (j + lb))));
+            }
+        }
+        return;
+    }
     int i = (int)floor(a), j = jcl(g, b);
     double f = a - i, h = b - j, q = qw[t & 3u];
     A *r0 = rho + (size_t)j * ld + i + NG;
@@ -76,16 +95,17 @@ __global__ void vertex_diag(GridDev g, const double *tab, size_t slab, const T *
 }
 
 // max |div D - rho - base| and max |rho| over the interior vertices
-// (columns 1..imax, all rows) into out[0], out[1] as the bit patterns of
+// (columns imin..imax, all rows) into out[0], out[1] as the bit patterns of
 // non-negative doubles (ordered like the integers); state = div D - rho
-__global__ void charge_check_kernel(int imax, int nth, const double *rho, const double *divD, const double *base,
-                                    double *state, int64_t ld, unsigned long long *out)
+__global__ void charge_check_kernel(int imin, int imax, int nth, const double *rho, const double *divD,
+                                    const double *base, double *state, int64_t ld, unsigned long long *out)
 {
     __shared__ double sr[256], sq[256];
     double mres = 0.0, mrho = 0.0;
-    const int64_t n = (int64_t)imax * (nth + 1);
+    const int w = imax - imin + 1;
+    const int64_t n = (int64_t)w * (nth + 1);
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
-        int i = 1 + (int)(e % imax), j = (int)(e / imax);
+        int i = imin + (int)(e % w), j = (int)(e / w);
         size_t q = (size_t)j * ld + i + NG;
         double d = divD[q] - rho[q];
         if (state) state[q] = d;
@@ -118,7 +138,8 @@ __device__ __forceinline__ double W1(double d)
 template <typename T>
 __global__ void deposit_kernel(GridDev g, int64_t nmax, const void *xa1, const void *xa2, const int32_t *ca,
                                const void *xb1, const void *xb2, const int32_t *cb, const uint32_t *tag, const void *dphi,
-                               const double *qw, double dt, T *J0, T *J1, T *J2, int64_t ld, int *status)
+                               const double *qw, double dt, T *J0, T *J1, T *J2, int64_t ld, int *status,
+                               int shape)
 {
     int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= nmax) return;
@@ -145,6 +166,11 @@ __global__ void deposit_kernel(GridDev g, int64_t nmax, const void *xa1, const v
         return;
     }
     double q = qw[t & 3u];
+    if (shape == 3) {
+        if constexpr (sizeof(T) == 8)
+            deposit3(g.nr, g.nth, ld, (double *)J0, (double *)J1, (double *)J2, q, dt, x1a, x2a, x1b, x2b, dp);
+        return;
+    }
     double S0r[4], S1r[4], S0t[4], S1t[4];
     for (int k = 0; k < 4; ++k) {
         S0r[k] = W1(x1a - (i0 - 1 + k));
@@ -189,7 +215,7 @@ cudaError_t diag_t(grpic_ctx *ctx, const grpic_particles *p, const grpic_fields 
         cudaMemsetAsync(rho, 0, bytes, s);
         if (p && p->n > 0)
             rho_particles<T><<<(unsigned)((p->n + 255) / 256), 256, 0, s>>>(
-                ctx->g, p->n, p->d_count, p->x1, p->x2, p->cell, p->tag, d_qw, (T *)rho, f->ld);
+                ctx->g, p->n, p->d_count, p->x1, p->x2, p->cell, p->tag, d_qw, (T *)rho, f->ld, ctx->prm.shape_order);
     }
     dim3 blk(32, 4), grd((ctx->g.ld_tab + 31) / 32, (ctx->g.nth + 1 + 3) / 4);
     vertex_diag<T><<<grd, blk, 0, s>>>(ctx->g, ctx->tab, ctx->slab, (const T *)f->D[0], (const T *)f->D[1], (T *)rho,
@@ -206,14 +232,17 @@ cudaError_t check_t(grpic_ctx *ctx, const grpic_particles *p, const grpic_fields
     cudaMemsetAsync(out, 0, 2 * sizeof(unsigned long long), s);
     if (p && p->n > 0)
         rho_particles<T, double><<<(unsigned)((p->n + 255) / 256), 256, 0, s>>>(
-            ctx->g, p->n, p->d_count, p->x1, p->x2, p->cell, p->tag, d_qw, rho, f->ld);
+            ctx->g, p->n, p->d_count, p->x1, p->x2, p->cell, p->tag, d_qw, rho, f->ld, ctx->prm.shape_order);
     dim3 blk(32, 4), grd((ctx->g.ld_tab + 31) / 32, (ctx->g.nth + 1 + 3) / 4);
     vertex_diag<T, double><<<grd, blk, 0, s>>>(ctx->g, ctx->tab, ctx->slab, (const T *)f->D[0], (const T *)f->D[1],
                                                rho, divD, f->ld);
     int imax = ctx->g.nr - ctx->grid.damp_cells - 1;
     if (imax > ctx->g.nr - 1) imax = ctx->g.nr - 1;
-    if (imax >= 1)
-        charge_check_kernel<<<256, 256, 0, s>>>(imax, ctx->g.nth, rho, divD, base, state, f->ld, out);
+    // a particle absorbed just inside r_in still covers vertex 1 with the
+    // cubic shape's cloud: the interior starts one column further in
+    const int imin = ctx->prm.shape_order == 3 ? 2 : 1;
+    if (imax >= imin)
+        charge_check_kernel<<<256, 256, 0, s>>>(imin, imax, ctx->g.nth, rho, divD, base, state, f->ld, out);
     return cudaGetLastError();
 }
 
@@ -245,11 +274,12 @@ cudaError_t launch_deposit(grpic_ctx *ctx, const grpic_particles *b, const grpic
     if (ctx->prm.precision == 64)
         deposit_kernel<double><<<blocks, 256, 0, s>>>(ctx->g, b->n, b->x1, b->x2, b->cell, a->x1, a->x2, a->cell,
                                                       a->tag, dphi, d_qw, ctx->prm.dt, (double *)f->J[0],
-                                                      (double *)f->J[1], (double *)f->J[2], f->ld, ctx->d_status);
+                                                      (double *)f->J[1], (double *)f->J[2], f->ld, ctx->d_status,
+                                                      ctx->prm.shape_order);
     else
         deposit_kernel<float><<<blocks, 256, 0, s>>>(ctx->g, b->n, b->x1, b->x2, b->cell, a->x1, a->x2, a->cell, a->tag,
                                                      dphi, d_qw, ctx->prm.dt, (float *)f->J[0], (float *)f->J[1],
-                                                     (float *)f->J[2], f->ld, ctx->d_status);
+                                                     (float *)f->J[2], f->ld, ctx->d_status, 1);
     return cudaGetLastError();
 }
 

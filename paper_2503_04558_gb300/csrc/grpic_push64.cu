@@ -23,6 +23,7 @@
 #include "grpic_internal.cuh"
 #include "grpic_window.cuh"
 #include "grpic_vay.cuh"
+#include "grpic_shape3.cuh"
 
 namespace grpic {
 namespace {
@@ -202,6 +203,10 @@ __device__ __forceinline__ int jcell(const GridDev &g, double x2)
     return j > g.nth - 1 ? g.nth - 1 : j;
 }
 
+// SHAPE 1: cloud in cell (bilinear interpolation, 4 x 4 window reduced across
+// the warp); SHAPE 3: the cubic spline of grpic_shape3.cuh (4 x 4 taps,
+// per-lane deposit of the 5 x 5 window)
+template <int SHAPE>
 __global__ void __launch_bounds__(256) push64_kernel(Push64Args A)
 {
     const GridDev &g = A.g;
@@ -251,19 +256,23 @@ __global__ void __launch_bounds__(256) push64_kernel(Push64Args A)
         if (x1a >= (double)g.nr) x1a = nextafter((double)g.nr, 0.0);  // rounding just below r_out
         if (x1a < 0.0) x1a = 0.0;
         if (A.massive[sp] && A.qm[sp] != 0.0) {
-            Stencil Sh0, S0h, S00, Shh;
-            stencil(g, x1a, x2a, true, false, 1.0, Sh0);   // D^r, B^theta
-            stencil(g, x1a, x2a, false, true, -1.0, S0h);  // D^theta (odd across the axis)
-            stencil(g, x1a, x2a, false, false, 1.0, S00);  // D^phi
-            stencil(g, x1a, x2a, true, true, 1.0, Shh);    // B^phi
             double Dv[3], Bv[3];
-            Dv[0] = gather(A.D0, A.ld, Sh0);
-            Dv[1] = gather(A.D1, A.ld, S0h);
-            Dv[2] = gather(A.D2, A.ld, S00);
-            Bv[1] = gather(A.B1, A.ld, Sh0);
-            Bv[2] = gather(A.B2, A.ld, Shh);
-            S0h.p0 = S0h.p1 = 1.0;  // B^r is even across the axis
-            Bv[0] = gather(A.B0, A.ld, S0h);
+            if constexpr (SHAPE == 3) {
+                gather3_fields(A.D0, A.D1, A.D2, A.B0, A.B1, A.B2, A.ld, g.nth, x1a, x2a, Dv, Bv);
+            } else {
+                Stencil Sh0, S0h, S00, Shh;
+                stencil(g, x1a, x2a, true, false, 1.0, Sh0);   // D^r, B^theta
+                stencil(g, x1a, x2a, false, true, -1.0, S0h);  // D^theta (odd across the axis)
+                stencil(g, x1a, x2a, false, false, 1.0, S00);  // D^phi
+                stencil(g, x1a, x2a, true, true, 1.0, Shh);    // B^phi
+                Dv[0] = gather(A.D0, A.ld, Sh0);
+                Dv[1] = gather(A.D1, A.ld, S0h);
+                Dv[2] = gather(A.D2, A.ld, S00);
+                Bv[1] = gather(A.B1, A.ld, Sh0);
+                Bv[2] = gather(A.B2, A.ld, Shh);
+                S0h.p0 = S0h.p1 = 1.0;  // B^r is even across the axis
+                Bv[0] = gather(A.B0, A.ld, S0h);
+            }
             if (A.pusher)
                 vay(g.a, r, th, A.qm[sp], A.dt, Dv, Bv, u);
             else
@@ -303,39 +312,43 @@ __global__ void __launch_bounds__(256) push64_kernel(Push64Args A)
                 tag |= DEAD;
                 live = false;
             } else {
-                // Esirkepov window: columns i0-1..i0+2, rows j0-1..j0+2
-                int sp2 = tag & 3u;
-                double qw = A.qw[sp2];
-                double S0r[4], S1r[4], S0t[4], S1t[4];
-#pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    S0r[k] = W1(x1a - (i0 - 1 + k));
-                    S1r[k] = W1(x1b - (i0 - 1 + k));
-                    S0t[k] = W1(x2a - (j0 - 1 + k));
-                    S1t[k] = W1(x2b - (j0 - 1 + k));
+                if constexpr (SHAPE == 3) {
+                    deposit3(g.nr, g.nth, A.ld, A.J0, A.J1, A.J2, A.qw[tag & 3u], dt, x1a, x2a, x1b, x2b, pt);
+                } else {
+                    // Esirkepov window: columns i0-1..i0+2, rows j0-1..j0+2
+                    int sp2 = tag & 3u;
+                    double qw = A.qw[sp2];
+                    double S0r[4], S1r[4], S0t[4], S1t[4];
+    #pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        S0r[k] = W1(x1a - (i0 - 1 + k));
+                        S1r[k] = W1(x1b - (i0 - 1 + k));
+                        S0t[k] = W1(x2a - (j0 - 1 + k));
+                        S1t[k] = W1(x2b - (j0 - 1 + k));
+                    }
+                    double cr = -qw / (2.0 * dt);
+                    double cp = qw * pt / dt;
+                    double Pr = 0.0;
+    #pragma unroll
+                    for (int k = 0; k < 3; ++k) {
+                        Pr += S1r[k] - S0r[k];
+    #pragma unroll
+                        for (int l = 0; l < 4; ++l) win[k * 4 + l] = cr * Pr * (S1t[l] + S0t[l]);
+                    }
+                    double Pt = 0.0;
+    #pragma unroll
+                    for (int l = 0; l < 3; ++l) {
+                        Pt += S1t[l] - S0t[l];
+    #pragma unroll
+                        for (int k = 0; k < 4; ++k) win[12 + k * 3 + l] = cr * (S1r[k] + S0r[k]) * Pt;
+                    }
+    #pragma unroll
+                    for (int k = 0; k < 4; ++k)
+    #pragma unroll
+                        for (int l = 0; l < 4; ++l)
+                            win[24 + k * 4 + l] = cp * (S1r[k] * S1t[l] * (1.0 / 3.0) + S1r[k] * S0t[l] * (1.0 / 6.0) +
+                                                        S0r[k] * S1t[l] * (1.0 / 6.0) + S0r[k] * S0t[l] * (1.0 / 3.0));
                 }
-                double cr = -qw / (2.0 * dt);
-                double cp = qw * pt / dt;
-                double Pr = 0.0;
-#pragma unroll
-                for (int k = 0; k < 3; ++k) {
-                    Pr += S1r[k] - S0r[k];
-#pragma unroll
-                    for (int l = 0; l < 4; ++l) win[k * 4 + l] = cr * Pr * (S1t[l] + S0t[l]);
-                }
-                double Pt = 0.0;
-#pragma unroll
-                for (int l = 0; l < 3; ++l) {
-                    Pt += S1t[l] - S0t[l];
-#pragma unroll
-                    for (int k = 0; k < 4; ++k) win[12 + k * 3 + l] = cr * (S1r[k] + S0r[k]) * Pt;
-                }
-#pragma unroll
-                for (int k = 0; k < 4; ++k)
-#pragma unroll
-                    for (int l = 0; l < 4; ++l)
-                        win[24 + k * 4 + l] = cp * (S1r[k] * S1t[l] * (1.0 / 3.0) + S1r[k] * S0t[l] * (1.0 / 6.0) +
-                                                    S0r[k] * S1t[l] * (1.0 / 6.0) + S0r[k] * S0t[l] * (1.0 / 3.0));
                 dep = true;
                 r = rt;
                 th = tt;
@@ -365,6 +378,7 @@ __global__ void __launch_bounds__(256) push64_kernel(Push64Args A)
     }
 
     // ---- deposit: warp-uniform start cell -> reduce-scatter over the lanes ---
+    if constexpr (SHAPE == 1) {
     int wkey = dep ? (j0 * g.nr + i0) : -1;
     unsigned act = __ballot_sync(FULL, dep);
     if (act) {
@@ -387,6 +401,7 @@ __global__ void __launch_bounds__(256) push64_kernel(Push64Args A)
 #pragma unroll
             for (int v = 0; v < NWIN; ++v) window_add<double>(v, win[v], i0, j0, g.nth, NG, A.ld, A.J0, A.J1, A.J2);
         }
+    }
     }
 
     // ---- histogram of the new keys (warp-aggregated) -----------------------
@@ -460,7 +475,10 @@ cudaError_t launch_push64(grpic_ctx *ctx, const grpic_particles *in, grpic_parti
     A.status = ctx->d_status;
     if (p->n <= 0) return cudaSuccess;
     int64_t blocks = (p->n + 255) / 256;
-    push64_kernel<<<(unsigned)blocks, 256, 0, s>>>(A);
+    if (ctx->prm.shape_order == 3)
+        push64_kernel<3><<<(unsigned)blocks, 256, 0, s>>>(A);
+    else
+        push64_kernel<1><<<(unsigned)blocks, 256, 0, s>>>(A);
     return cudaGetLastError();
 }
 

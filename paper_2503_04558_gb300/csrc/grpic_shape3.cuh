@@ -1,0 +1,140 @@
+// grpic_shape3.cuh -- the third-order particle shape of Sec. 2.3 (a
+// configuration option there): the cubic B-spline in logical units,
+//   W3(x) = 2/3 - x^2 + |x|^3/2 (|x| < 1),  (2 - |x|)^3 / 6 (1 <= |x| < 2),
+// S = W3(x1 - i) W3(x2 - j) on each staggered lattice, for the field
+// interpolation (4 x 4 taps) and the Esirkepov deposit (Eq. esirkepov-decomp
+// over the 5 x 5 vertices around both positions, Eq. j-phi-deposit).
+//
+// Rows past the polar axis are the mirror rows of the relabelling (r, -theta,
+// phi + pi) of the same point: the theta components (D^theta, B^theta,
+// J^theta) change sign there, the others do not; the axis rows are their own
+// mirrors.  Interpolation reads the mirror rows with that parity, the
+// deposit adds into them with it (which keeps the continuity of the
+// half-width axis cells exact).  Columns: the two guard columns on each side
+// hold what the interpolation needs; deposits past them (a particle leaving
+// through r_out) are dropped.
+#pragma once
+
+#include "grpic_internal.cuh"
+
+namespace grpic {
+
+__device__ __forceinline__ double w3(double d)
+{
+    d = fabs(d);
+    if (d < 1.0) return 2.0 / 3.0 - d * d + 0.5 * d * d * d;
+    if (d < 2.0) {
+        const double e = 2.0 - d;
+        return e * e * e * (1.0 / 6.0);
+    }
+    return 0.0;
+}
+
+// mirror of row j (integer rows theta_j, or half rows theta_{j+1/2})
+__device__ __forceinline__ int mirror_row(int j, bool half_t, int nth, bool &flip)
+{
+    const int top = half_t ? nth - 1 : nth;
+    flip = false;
+    if (j < 0) {
+        flip = true;
+        return half_t ? -1 - j : -j;
+    }
+    if (j > top) {
+        flip = true;
+        return half_t ? 2 * nth - 1 - j : 2 * nth - j;
+    }
+    return j;
+}
+
+// field component on its lattice (staggered by sr in r, half rows if half_t;
+// par = the parity across the axis) at logical (x1, x2)
+__device__ __forceinline__ double gather3(const double *__restrict__ F, int64_t ld, int nth, double x1, double x2,
+                                          double sr, bool half_t, double par)
+{
+    const double xi = x1 - sr, eta = x2 - (half_t ? 0.5 : 0.0);
+    const int i = (int)floor(xi), j = (int)floor(eta);
+    double wr[4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) wr[a] = w3(xi - (i - 1 + a));
+    double v = 0.0;
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+        bool flip;
+        const int jj = mirror_row(j - 1 + b, half_t, nth, flip);
+        const double wt = w3(eta - (j - 1 + b)) * (flip ? par : 1.0);
+        const double *row = F + (size_t)jj * ld + (i - 1 + NG);
+        double s = 0.0;
+#pragma unroll
+        for (int a = 0; a < 4; ++a) s += wr[a] * __ldg(row + a);
+        v += wt * s;
+    }
+    return v;
+}
+
+// the six fields at the particle (D^r, D^th, D^ph, B^r, B^th, B^ph)
+__device__ __forceinline__ void gather3_fields(const double *D0, const double *D1, const double *D2, const double *B0,
+                                               const double *B1, const double *B2, int64_t ld, int nth, double x1,
+                                               double x2, double Dv[3], double Bv[3])
+{
+    Dv[0] = gather3(D0, ld, nth, x1, x2, 0.5, false, 1.0);
+    Dv[1] = gather3(D1, ld, nth, x1, x2, 0.0, true, -1.0);
+    Dv[2] = gather3(D2, ld, nth, x1, x2, 0.0, false, 1.0);
+    Bv[0] = gather3(B0, ld, nth, x1, x2, 0.0, true, 1.0);
+    Bv[1] = gather3(B1, ld, nth, x1, x2, 0.5, false, -1.0);
+    Bv[2] = gather3(B2, ld, nth, x1, x2, 0.5, true, 1.0);
+}
+
+__device__ __forceinline__ void fold_add3(double *F, int64_t ld, int nr, int nth, int i, int j, bool half_t, double odd,
+                                          double v)
+{
+    if (v == 0.0 || i < -NG || i > nr + NG - 1) return;
+    bool flip;
+    const int jj = mirror_row(j, half_t, nth, flip);
+    atomicAdd(F + (size_t)jj * ld + (i + NG), flip ? odd * v : v);
+}
+
+// integrated currents of one move from (x1a, x2a) to (x1b, x2b) (logical,
+// at most one cell apart in each direction): J^r A (J0), J^theta A (J1),
+// J^phi dV (J2)
+__device__ __forceinline__ void deposit3(int nr, int nth, int64_t ld, double *J0, double *J1, double *J2, double qw,
+                                         double dt, double x1a, double x2a, double x1b, double x2b, double dphi)
+{
+    const int fa = (int)floor(x1a), fb = (int)floor(x1b);
+    const int b1 = (fa < fb ? fa : fb) - 1;
+    const int ga = (int)floor(x2a), gb = (int)floor(x2b);
+    const int b2 = (ga < gb ? ga : gb) - 1;
+    double S0r[5], S1r[5], S0t[5], S1t[5];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+        S0r[k] = w3(x1a - (b1 + k));
+        S1r[k] = w3(x1b - (b1 + k));
+        S0t[k] = w3(x2a - (b2 + k));
+        S1t[k] = w3(x2b - (b2 + k));
+    }
+    const double cr = -qw / (2.0 * dt), cp = qw * dphi / dt;
+    // J^r A at faces b1 + k + 1/2 (k = 0..3): prefix sums of (S1r - S0r) (S1t + S0t)
+    double Pr = 0.0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        Pr += S1r[k] - S0r[k];
+#pragma unroll
+        for (int l = 0; l < 5; ++l) fold_add3(J0, ld, nr, nth, b1 + k, b2 + l, false, 1.0, cr * Pr * (S1t[l] + S0t[l]));
+    }
+    double Pt = 0.0;
+#pragma unroll
+    for (int l = 0; l < 4; ++l) {
+        Pt += S1t[l] - S0t[l];
+#pragma unroll
+        for (int k = 0; k < 5; ++k) fold_add3(J1, ld, nr, nth, b1 + k, b2 + l, true, -1.0, cr * (S1r[k] + S0r[k]) * Pt);
+    }
+#pragma unroll
+    for (int k = 0; k < 5; ++k)
+#pragma unroll
+        for (int l = 0; l < 5; ++l) {
+            const double w = S1r[k] * S1t[l] * (1.0 / 3.0) + S1r[k] * S0t[l] * (1.0 / 6.0) +
+                             S0r[k] * S1t[l] * (1.0 / 6.0) + S0r[k] * S0t[l] * (1.0 / 3.0);
+            fold_add3(J2, ld, nr, nth, b1 + k, b2 + l, false, 1.0, cp * w);
+        }
+}
+
+}  // namespace grpic

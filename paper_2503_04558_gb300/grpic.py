@@ -39,7 +39,7 @@ class Params(C.Structure):
                 ("n_push_iter", C.c_int32), ("q_over_m", C.c_double * 4), ("q_weight", C.c_double * 4),
                 ("massive", C.c_int32 * 4), ("precision", C.c_int32), ("sort_every", C.c_int32),
                 ("fp64_radius", C.c_double), ("push_tol", C.c_double), ("island_arith", C.c_int32),
-                ("pusher", C.c_int32)]
+                ("pusher", C.c_int32), ("shape_order", C.c_int32)]
 
 
 class ParticlesC(C.Structure):
@@ -129,6 +129,7 @@ class Config:
     push_tol: float = 0.0
     island_arith: int = 0     # 0 double-FP32 pairs, 1 native FP64
     pusher: int = 0           # 0 generalized Boris, 1 Vay in the FIDO frame
+    shape_order: int = 1      # 1 cloud in cell, 3 cubic spline (FP64 path)
 
     def __post_init__(self):
         self.dx1 = math.log(self.r_out / self.r_in) / self.n_r
@@ -153,6 +154,7 @@ class Config:
         p.push_tol = self.push_tol
         p.island_arith = self.island_arith
         p.pusher = self.pusher
+        p.shape_order = self.shape_order
         return p
 
 

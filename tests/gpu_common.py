@@ -12,7 +12,7 @@ def configs(nr, nth, a, r_in, r_out, precision=64, **kw):
     oc = O.make_cfg(nr, nth, a, r_in, r_out, **kw)
     gk = dict(dt=oc.dt, beta_field=oc.beta_s, n_field_iter=oc.n_fld_iter, n_push_iter=oc.n_push_iter,
               damp_cells=oc.damp_cells, damp_max=oc.damp_max, q_over_m=tuple(oc.qm), q_weight=tuple(oc.qw),
-              massive=tuple(oc.massive), precision=precision, pusher=oc.pusher)
+              massive=tuple(oc.massive), precision=precision, pusher=oc.pusher, shape_order=oc.shape)
     gc = G.Config(nr, nth, a, r_in, r_out, **gk)
     assert gc.ld == oc.ld
     return oc, gc

@@ -476,3 +476,63 @@ def test_vay_pusher_steps_match_oracle(G):
     assert np.array_equal(h["tag"], P.tag)
     for k, ref in zip(("x1", "x2", "u1", "u2", "u3"), (P.r, P.th, P.u1, P.u2, P.u3)):
         assert relerr(h[k], ref) < TOL, k
+
+
+# ---------------------------------------------------------------------------
+# third-order (cubic B-) spline shape, FP64 path
+# ---------------------------------------------------------------------------
+def test_cubic_shape_push_deposit_matches_oracle(G):
+    """One push + deposit with the cubic shape (interpolation over 4 x 4 taps,
+    the 5 x 5 Esirkepov window, both folded at the polar axis)."""
+    oc, gc = configs(32, 32, A09, 0.9 * RH, 20.0, qw=(-0.01, 0.01, 0.01, 0.0), shape=3)
+    ctx, F = gpu_fields(G, gc, O.WALD, 2.0)
+    D, B = O.init_fields(oc, O.WALD, 2.0)
+    P = make_particles(oc, 20000, seed=3, sigma=0.5)
+    S = load_set(G, gc, P)
+    ctx.push(S, F)
+    assert ctx.sync() == 0
+    st, J, _ = O.push_deposit(oc, P, D, B)
+    assert st == 0
+    h = S.host()
+    assert np.array_equal(h["tag"], P.tag)
+    for k, ref in zip(("x1", "x2", "u1", "u2", "u3"), (P.r, P.th, P.u1, P.u2, P.u3)):
+        assert relerr(h[k], ref) < 1e-12, k
+    for k, ref in enumerate(flux_form(oc, J)):
+        assert relerr(host(F.J[k]), ref) < 1e-11, ("J", k)
+
+
+def test_cubic_shape_steps_match_oracle_and_conserve_charge(G):
+    """Ten steps with the cubic shape (48 x 40, Wald B0 = 2, 2e4 particles,
+    two of them sent through the polar axis): fields and particles against the
+    oracle to 1e-10, and the running charge check (interior from column 2)
+    below 1e-12 of max rho."""
+    oc, gc = configs(48, 40, A09, 0.9 * RH, 20.0, qw=(-0.01, 0.01, 0.01, 0.0), shape=3)
+    ctx, F = gpu_fields(G, gc, O.WALD, 2.0)
+    D, B = O.init_fields(oc, O.WALD, 2.0)
+    P = make_particles(oc, 20000, seed=23, sigma=0.5)
+    graze = axis_grazers(oc, P, D, B, 10)
+    P = P.take(np.setdiff1d(np.arange(P.n), graze))
+    S = load_set(G, gc, P)
+    _, _, state0 = ctx.charge_check(S, F, want_state=True)
+    ctx.step(S, F, 10)
+    assert ctx.sync() == 0
+    res, rmax, _ = ctx.charge_check(S, F, base=state0)
+    assert res < 1e-12 * rmax, (res, rmax)
+    for _ in range(10):
+        st, P, J = O.step(oc, P, D, B)
+        assert st == 0
+    for k in range(3):
+        assert relerr(host(F.D[k]), D[k]) < TOL, ("D", k)
+        assert relerr(host(F.B[k]), B[k]) < TOL, ("B", k)
+    h = S.host()
+    assert np.array_equal(h["tag"], P.tag)
+    for k, ref in zip(("x1", "x2", "u1", "u2", "u3"), (P.r, P.th, P.u1, P.u2, P.u3)):
+        assert relerr(h[k], ref) < TOL, k
+
+
+def test_cubic_shape_refused_where_not_built(G):
+    from paper_2503_04558_gb300 import grpic as GG
+    with pytest.raises(GG.GrpicError):
+        GG.Context(GG.Config(16, 16, 0.9, 1.3, 20.0, precision=32, shape_order=3))
+    with pytest.raises(GG.GrpicError):
+        GG.Context(GG.Config(16, 16, 0.9, 1.3, 20.0, shape_order=2))
