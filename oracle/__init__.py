@@ -48,7 +48,9 @@ class Cfg(C.Structure):
                 ("n_fld_iter", C.c_int), ("n_push_iter", C.c_int),
                 ("damp_cells", C.c_int), ("damp_max", C.c_double),
                 ("qm", C.c_double * 4), ("qw", C.c_double * 4), ("massive", C.c_int * 4),
-                ("pusher", C.c_int), ("shape", C.c_int)]
+                ("pusher", C.c_int), ("shape", C.c_int), ("radiation", C.c_int), ("injection", C.c_int),
+                ("gamma_thr", C.c_double), ("eps_ph", C.c_double), ("tau", C.c_double),
+                ("sigma_thr", C.c_double), ("eps_db", C.c_double), ("seed", C.c_uint64)]
 
 
 _lib = None
@@ -79,6 +81,8 @@ def lib():
             "orc_push_deposit": (i, [pc, l, p, p, p, p, p, p, p, p, p, p, p, p, p, p, p, p]),
             "orc_cell_keys": (None, [pc, l, p, p, p, p]),
             "orc_counting_sort": (l, [l, l, p, p]),
+            "orc_radiate": (i, [pc, C.c_int64, p, l, p, p, p, p, p, p, p]),
+            "orc_inject": (i, [pc, C.c_int64, p, l, p, p, p, p, p, p, p, p, p, p, p, p, p]),
             "orc_rho": (None, [pc, l, p, p, p, p]),
             "orc_divD": (None, [pc, p, p, p]),
             "orc_divB": (None, [pc, p, p, p]),
@@ -106,7 +110,8 @@ def horizon(a: float) -> float:
 
 def make_cfg(nr, nth, a, r_in, r_out, dt=None, cfl=0.5, beta_s=0.53, n_fld_iter=7, n_push_iter=3,
              damp_cells=None, damp_max=0.1, qm=(-1.0, 1.0, 1.0, 0.0), qw=(-1e-3, 1e-3, 1e-3, 0.0),
-             massive=(1, 1, 1, 0), pusher=0, shape=1) -> Cfg:
+             massive=(1, 1, 1, 0), pusher=0, shape=1, radiation=0, injection=0, gamma_thr=100.0, eps_ph=4.0,
+             tau=2.0, sigma_thr=10.0, eps_db=1e-3, seed=0) -> Cfg:
     """Grid uniform in ln r and theta; dt from the CFL reading
     dt = cfl * min(dr, r dtheta) at r_in when not given."""
     c = Cfg()
@@ -127,6 +132,9 @@ def make_cfg(nr, nth, a, r_in, r_out, dt=None, cfl=0.5, beta_s=0.53, n_fld_iter=
         c.qm[k], c.qw[k], c.massive[k] = qm[k], qw[k], massive[k]
     c.pusher = pusher
     c.shape = shape
+    c.radiation, c.injection = radiation, injection
+    c.gamma_thr, c.eps_ph, c.tau = gamma_thr, eps_ph, tau
+    c.sigma_thr, c.eps_db, c.seed = sigma_thr, eps_db, seed
     return c
 
 
@@ -310,11 +318,53 @@ def divB(c: Cfg, B):
     return out
 
 
-def step(c: Cfg, P: Particles, D, B, do_sort=True):
+def _grow(P: Particles, extra: int) -> Particles:
+    pad = lambda a, fill: np.concatenate([a, np.full(extra, fill, a.dtype)])
+    return Particles(pad(P.r, 1.0), pad(P.th, 1.0), pad(P.u1, 0.0), pad(P.u2, 0.0), pad(P.u3, 0.0),
+                     pad(P.tag, DEAD))
+
+
+def radiate(c: Cfg, P: Particles, step: int):
+    """Emission and conversion after a push (slot order); children appended.
+    Returns (status, P with the children, (emitted, converted))."""
+    n = P.n
+    Q = _grow(P, 2 * n + 2)
+    np_ = C.c_long(n)
+    counts = (C.c_long * 2)()
+    st = lib().orc_radiate(C.byref(c), step, C.byref(np_), Q.n, _p(Q.r), _p(Q.th), _p(Q.u1), _p(Q.u2), _p(Q.u3),
+                           _p(Q.tag), counts)
+    return st, Q.take(np.arange(np_.value)), (counts[0], counts[1])
+
+
+def inject(c: Cfg, P: Particles, D, B, step: int):
+    """Pair injection after the field update (cell order); pairs appended.
+    Returns (status, P with the pairs, number of cells that injected)."""
+    extra = 2 * c.nr * c.nth
+    Q = _grow(P, extra)
+    np_ = C.c_long(P.n)
+    cnt = C.c_long(0)
+    st = lib().orc_inject(C.byref(c), step, C.byref(np_), Q.n, _p(Q.r), _p(Q.th), _p(Q.u1), _p(Q.u2), _p(Q.u3),
+                          _p(Q.tag), *[_p(x) for x in list(D) + list(B)], C.byref(cnt))
+    return st, Q.take(np.arange(np_.value)), cnt.value
+
+
+def step(c: Cfg, P: Particles, D, B, do_sort=True, step=0, events=None):
     """One time step in the paper's order (Fig. stepping): push + deposit from
-    fields n, field update n -> n+1 with J^{n+1/2}, then the sort by cell."""
+    fields n (then emission and conversion if c.radiation), field update
+    n -> n+1 with J^{n+1/2} (then injection if c.injection), then the sort by
+    cell.  `step` keys the random numbers; events (a list) receives
+    (emitted, converted, injecting cells)."""
     st, J, dphi = push_deposit(c, P, D, B)
+    ev = [0, 0, 0]
+    if c.radiation:
+        s2, P, (ev[0], ev[1]) = radiate(c, P, step)
+        st = st or s2
     field_update(c, D, B, J)
+    if c.injection:
+        s3, P, ev[2] = inject(c, P, D, B, step)
+        st = st or s3
+    if events is not None:
+        events.append(tuple(ev))
     if do_sort:
         P = sort(c, P)
     return st, P, J

@@ -66,6 +66,12 @@ typedef struct {
                        /* FIDO frame (Sec. 2.2)                              */
     int shape;         /* particle shape (Sec. 2.3): 1 cloud in cell, 3 the  */
                        /* third-order (cubic B-) spline                      */
+    int radiation;     /* 2D photon emission and pair conversion (Sec. 4)    */
+    int injection;     /* pair injection of the plasma-filled Wald run       */
+    double gamma_thr, eps_ph, tau;   /* emission threshold, photon energy,   */
+                                     /* conversion opacity                   */
+    double sigma_thr, eps_db;        /* injection thresholds                 */
+    uint64_t seed;                   /* Philox key                           */
 } orc_cfg;
 
 /* ------------------------------------------------------------------------ */
@@ -1552,4 +1558,132 @@ double orc_horizon_flux(const orc_cfg *c, double *D0, double *D1, double *D2, do
     }
     for (int k = 0; k < 3; ++k) { free(E[k]); free(H[k]); }
     return L;
+}
+
+
+/* ======================================================================== */
+/* 2D radiation and injection (Sec. 4's prescription on the 2D grid, and   */
+/* the pair injection of Sec. 3.4's plasma-filled Wald run).                */
+/*                                                                          */
+/* After the push + deposit, in slot order:                                 */
+/*  - a charged massive particle with FIDO Lorentz factor                   */
+/*    Gamma = sqrt(1 + gamma^ij u_i u_j) >= gamma_thr (and Gamma - eps_ph   */
+/*    >= 1) emits a photon of FIDO energy eps_ph along its momentum and     */
+/*    loses that energy: u -> u sqrt((Gamma-eps)^2-1)/sqrt(Gamma^2-1); the  */
+/*    photon starts at the emitter with k_i = eps_ph u_i / |u|;             */
+/*  - a photon (massless species) with FIDO energy e = |k| > 2 converts     */
+/*    with probability 1 - exp(-tau dt): U = uniform(seed, slot, step, 1)   */
+/*    < P; it dies and an e- and an e+ start at its position, each with     */
+/*    u = s k, s = sqrt((e/2)^2 - 1)/e (FIDO energy e/2 along k).           */
+/* Children are appended after all slots, in parent order (photon: one      */
+/* child; conversion: e-, then e+).                                         */
+/*                                                                          */
+/* After the field update, per cell in cell order (c = j nr + i):           */
+/*  sigma = B^2 / n with B^2 = gamma_ij B^i B^j and D.B = gamma_ij D^i B^j  */
+/*  at the cell centre (x1, x2) = (i + 1/2, j + 1/2) (fields of the shape  */
+/*  in use), n = (charged live particles in the cell) |qw_0| / V_cell      */
+/*  (V_cell = A^B_phi of the cell, no fewer than one particle); where       */
+/*  sigma > sigma_thr and |D.B| / B^2 > eps_db an e- and an e+ are          */
+/*  injected at rest in the FIDO frame (u_i = 0) at x = (i + U1, j + U2),  */
+/*  U1 = uniform(seed, c, step, 2), U2 = uniform(seed, c, step, 3), appended */
+/*  in cell order.                                                          */
+/* ======================================================================== */
+static double fido_norm2(const orc_metric *m, double u1, double u2, double u3)
+{
+    return m->gi_rr * u1 * u1 + 2.0 * m->gi_rp * u1 * u3 + m->gi_thth * u2 * u2 + m->gi_pp * u3 * u3;
+}
+
+int orc_radiate(const orc_cfg *c, int64_t step, long *np, long cap, double *r, double *th, double *u1, double *u2,
+                double *u3, uint32_t *tag, long counts[2])
+{
+    int status = ORC_OK;
+    long n0 = *np, w = n0;
+    double P = 1.0 - exp(-c->tau * c->dt);
+    counts[0] = counts[1] = 0;
+    for (long p = 0; p < n0; ++p) {
+        if (tag[p] & ORC_DEAD) continue;
+        int sp = tag[p] & 3u;
+        orc_metric m;
+        metric_at(c->a, r[p], th[p], &m);
+        double uu = fido_norm2(&m, u1[p], u2[p], u3[p]);
+        if (c->massive[sp] && c->qm[sp] != 0.0) {
+            double G = sqrt(1.0 + uu);
+            if (G >= c->gamma_thr && G - c->eps_ph >= 1.0) {
+                double pm = sqrt(uu), G2 = G - c->eps_ph, f = sqrt(G2 * G2 - 1.0) / pm, k = c->eps_ph / pm;
+                double k1 = k * u1[p], k2 = k * u2[p], k3 = k * u3[p];
+                u1[p] *= f; u2[p] *= f; u3[p] *= f;
+                counts[0]++;
+                if (w >= cap) { status = 6; continue; }
+                r[w] = r[p]; th[w] = th[p]; u1[w] = k1; u2[w] = k2; u3[w] = k3; tag[w] = 3u;
+                ++w;
+            }
+        } else if (!c->massive[sp]) {
+            double e = sqrt(uu);
+            if (e > 2.0 && orc_uniform(c->seed, (uint64_t)p, step, 1) < P) {
+                double s = sqrt(0.25 * e * e - 1.0) / e;
+                tag[p] |= ORC_DEAD;
+                counts[1]++;
+                for (int k = 0; k < 2; ++k) {
+                    if (w >= cap) { status = 6; break; }
+                    r[w] = r[p]; th[w] = th[p]; u1[w] = s * u1[p]; u2[w] = s * u2[p]; u3[w] = s * u3[p];
+                    tag[w] = (uint32_t)k;
+                    ++w;
+                }
+            }
+        }
+    }
+    *np = w;
+    return status;
+}
+
+int orc_inject(const orc_cfg *c, int64_t step, long *np, long cap, double *r, double *th, double *u1, double *u2,
+               double *u3, uint32_t *tag, double *D0, double *D1, double *D2, double *B0r, double *B1, double *B2,
+               long *count)
+{
+    orc_geom g = *geom_get(c);
+    double *D[3] = {D0, D1, D2}, *B[3] = {B0r, B1, B2};
+    long ncell = (long)c->nr * c->nth, n0 = *np, w = n0;
+    long *nq = calloc(ncell, sizeof(long));
+    double lnrin = log(c->r_in);
+    for (long p = 0; p < n0; ++p) {
+        if (tag[p] & ORC_DEAD) continue;
+        int sp = tag[p] & 3u;
+        if (!(c->massive[sp] && c->qm[sp] != 0.0)) continue;
+        double x1 = (log(r[p]) - lnrin) / c->dx1, x2 = th[p] / c->dth;
+        int i = (int)floor(x1), j = jcell(c, x2);
+        if (i < 0 || i >= c->nr || j < 0) continue;
+        nq[(long)j * c->nr + i]++;
+    }
+    int status = ORC_OK;
+    *count = 0;
+    double w0 = fabs(c->qw[0]);
+    for (long cc = 0; cc < ncell; ++cc) {
+        int i = (int)(cc % c->nr), j = (int)(cc / c->nr);
+        double x1 = i + 0.5, x2 = j + 0.5;
+        double Dv[3], Bv[3];
+        if (c->shape == 3)
+            interp_fields3(c, D, B, x1, x2, Dv, Bv);
+        else
+            interp_fields(c, D, B, x1, x2, Dv, Bv);
+        orc_metric m;
+        metric_at(c->a, c->r_in * exp(x1 * c->dx1), x2 * c->dth, &m);
+        double Bl[3];
+        lower(&m, Bv, Bl);
+        double B2 = Bl[0] * Bv[0] + Bl[1] * Bv[1] + Bl[2] * Bv[2];
+        double DB = Bl[0] * Dv[0] + Bl[1] * Dv[1] + Bl[2] * Dv[2];
+        double V = g.AB[2][IDX(c, i, j)];
+        double n = (nq[cc] > 0 ? (double)nq[cc] : 1.0) * w0 / V;
+        if (!(B2 > 0.0) || !(B2 / n > c->sigma_thr) || !(fabs(DB) / B2 > c->eps_db)) continue;
+        double U1 = orc_uniform(c->seed, (uint64_t)cc, step, 2), U2 = orc_uniform(c->seed, (uint64_t)cc, step, 3);
+        double rr = c->r_in * exp((i + U1) * c->dx1), tt = (j + U2) * c->dth;
+        for (int k = 0; k < 2; ++k) {
+            if (w >= cap) { status = 6; break; }
+            r[w] = rr; th[w] = tt; u1[w] = 0.0; u2[w] = 0.0; u3[w] = 0.0; tag[w] = (uint32_t)k;
+            ++w;
+        }
+        (*count)++;
+    }
+    free(nq);
+    *np = w;
+    return status;
 }
