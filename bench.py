@@ -596,6 +596,51 @@ def job_value(particles_per_rank, steps, world, total_ms):
     return world * particles_per_rank * steps / (total_ms * 1e-3)
 
 
+def pairs_2d_measure(n=1024, ppc=16, steps=3):
+    """The 2D pair cascade on the FP64 path: the plasma-filled Wald setting
+    (a = 0.99, rotating Wald B0 = 500, injection where sigma > 10 and
+    |D.B|/B^2 > 1e-3) with photon emission at gamma_thr = 100 (eps_ph = 4)
+    and conversion (tau = 2); one warm-up step, `steps` timed steps of
+    grpic_step."""
+    import torch
+    from paper_2503_04558_gb300 import grpic as G, synth
+    a = 0.99
+    rin = 0.9 * horizon(a)
+    cfg = G.Config(n, n, a, rin, R_OUT, q_weight=(-1e-3, 1e-3, 1e-3, 0.0), radiation=1, injection=1,
+                   gamma_thr=100.0, eps_ph=4.0, tau=2.0, sigma_thr=10.0, eps_db=1e-3, seed=1)
+    ctx = G.Context(cfg)
+    F = G.Fields(cfg)
+    ctx.init_fields(F, G.WALD, 500.0)
+    n0 = n * n * ppc
+    gen = synth.particles_torch(n, n, rin, R_OUT, n0, seed=77, sigma=0.1, device="cuda")
+    S = G.ParticleSet(cfg, 3 * n0)
+    S.load(gen["r"], gen["th"], gen["u1"], gen["u2"], gen["u3"], gen["tag"])
+    del gen
+    ctx.step(S, F, 1)
+    st = ctx.sync()
+    live0 = S.live()
+    torch.cuda.synchronize()
+    ctx.set_timing(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    ctx.step(S, F, steps)
+    e1.record()
+    torch.cuda.synchronize()
+    tp, tf, ts, tn = ctx.get_timing()
+    ctx.set_timing(False)
+    st = st or ctx.sync()
+    ms = e0.elapsed_time(e1) / steps
+    live1 = S.live()
+    out = {"what": "FP64 2D step with photon emission, pair conversion and pair injection", "grid": f"{n}x{n}",
+           "particles_start": live0, "particles_end": live1, "steps": steps, "warmup": 1, "ms_per_step": ms,
+           "value": 0.5 * (live0 + live1) / (ms * 1e-3), "unit": "particle-steps/s",
+           "phases": {"push_and_appends_ms": tp / tn, "field_and_injection_ms": tf / tn, "sort_ms": ts / tn},
+           "status": ["OK", "EINVAL", "ENOMEM", "ECUDA", "ERANGE", "ENAN", "EOVERFLOW"][st] if st < 7 else st}
+    del S, F, ctx
+    torch.cuda.empty_cache()
+    return out
+
+
 def grpic_summary(res, args, world, esz_prec):
     """Per-form figures and the roofline of the push kernel."""
     n, cells = res["n"], res["cells"]
@@ -717,6 +762,10 @@ def main():
                                      "particle_statuses": rc["statuses"]}
         except Exception as e:
             extras["cubic_shape"] = {"error": f"{type(e).__name__}: {e}"}
+        try:
+            extras["pairs_2d"] = pairs_2d_measure()
+        except Exception as e:
+            extras["pairs_2d"] = {"error": f"{type(e).__name__}: {e}"}
     if not args.no_extras:
         for name, fn in (("adjoint", lambda: adjoint_measure(2)), ("batch1d", lambda: batch1d_measure(200, 600))):
             try:

@@ -112,7 +112,23 @@ typedef struct {
  * third-order (cubic B-) spline, FP64 path only (the FP32 form and the
  * differentiable form refuse it).  With the cubic shape a particle's cloud
  * reaches two rows past the polar axis, folded back with the axis parities,
- * and two columns into the guard columns. */
+ * and two columns into the guard columns.
+ * radiation (FP64 path, Sec. 4 on the 2D grid): after its push a charged
+ * particle (species 0, 1, 2 with q != 0) whose FIDO Lorentz factor reaches
+ * gamma_thr emits a photon (species 3) of FIDO energy eps_ph along its
+ * momentum and keeps the rest; a photon of FIDO energy e > 2 converts with
+ * probability 1 - exp(-tau dt) into an e- (species 0) and an e+ (species 1)
+ * of FIDO energy e/2 each along its momentum.  injection (FP64 path, the
+ * plasma-filled Wald run): after the field update every cell whose
+ * magnetisation B^2 / n exceeds sigma_thr and whose |D.B| / B^2 exceeds
+ * eps_db gets an e-/e+ pair at rest in the FIDO frame at a random point
+ * (n: charged particles in the cell, at least one, times |q_weight[0]| over
+ * the cell's volume).  Random numbers: Philox4x64-10 keyed on (seed, 0),
+ * counter (slot or cell, step, event, 0).  New particles are appended after
+ * the live slots in parent (cell) order, before the sort; with radiation or
+ * injection grpic_step and grpic_step_graph treat the whole capacity as the
+ * slot range (p->n is set to p->capacity; the device count holds the live
+ * particles) and report GRPIC_EOVERFLOW when it fills. */
 typedef struct {
     double dt;
     double beta_field;
@@ -128,6 +144,11 @@ typedef struct {
     int32_t island_arith;
     int32_t pusher;
     int32_t shape_order;
+    int32_t radiation;
+    int32_t injection;
+    double gamma_thr, eps_ph, tau;
+    double sigma_thr, eps_db;
+    uint64_t seed;
 } grpic_params;
 
 typedef struct {

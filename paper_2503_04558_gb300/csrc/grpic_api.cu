@@ -260,6 +260,11 @@ grpic_status grpic_init(grpic_metric metric, double spin, const grpic_grid *grid
     if (prm->island_arith != 0 && prm->island_arith != 1) return GRPIC_EINVAL;
     if (prm->pusher != 0 && prm->pusher != 1) return GRPIC_EINVAL;
     if (!(prm->shape_order == 1 || (prm->shape_order == 3 && prm->precision == 64))) return GRPIC_EINVAL;
+    if ((prm->radiation != 0 && prm->radiation != 1) || (prm->injection != 0 && prm->injection != 1) ||
+        ((prm->radiation || prm->injection) && prm->precision != 64))
+        return GRPIC_EINVAL;
+    if (prm->radiation && !(prm->eps_ph > 0.0 && prm->gamma_thr >= 1.0 && prm->tau >= 0.0)) return GRPIC_EINVAL;
+    if (prm->injection && !(prm->sigma_thr >= 0.0 && prm->eps_db >= 0.0)) return GRPIC_EINVAL;
     if (!(prm->beta_field >= 0.0 && prm->beta_field <= 1.0)) return GRPIC_EINVAL;
 
     grpic_ctx *ctx = new (std::nothrow) grpic_ctx();
@@ -314,6 +319,12 @@ grpic_status grpic_init(grpic_metric metric, double spin, const grpic_grid *grid
     cudaMemcpy((char *)ctx->d_status + 16, prm->q_weight, 4 * sizeof(double), cudaMemcpyHostToDevice);
     e = launch_tables(ctx, 0);
     if (e == cudaSuccess) e = sort_setup();
+    if (e == cudaSuccess && (prm->radiation || prm->injection)) {
+        e = cudaMalloc(&ctx->d_spqm, 4 * sizeof(double));
+        if (e == cudaSuccess) e = cudaMalloc(&ctx->d_spmassive, 4 * sizeof(int));
+        if (e == cudaSuccess) e = cudaMemcpy(ctx->d_spqm, prm->q_over_m, 4 * sizeof(double), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(ctx->d_spmassive, prm->massive, 4 * sizeof(int), cudaMemcpyHostToDevice);
+    }
     if (e == cudaSuccess && prm->precision == 32) {
         e = cudaMalloc(&ctx->tab32, sizeof(float) * ctx->slab * T_COUNT);
         if (e == cudaSuccess) e = cudaMalloc(&ctx->col1d32, sizeof(float) * 4 * g.ld_tab);
@@ -442,6 +453,39 @@ static grpic_status drop_pending(grpic_ctx *ctx, grpic_status st)
     return st;
 }
 
+// one step with 2D radiation and/or injection: push (with the emission and
+// conversion decisions), the children appended, field update, injection,
+// and a general sort that moves the data (the appends break the neighbour
+// sort's precondition)
+static grpic_status step_one_rad(grpic_ctx *ctx, grpic_particles *p, grpic_particles *scratch, grpic_fields *f,
+                                 cudaStream_t s)
+{
+    cudaEvent_t *ev = timing_slot(ctx);
+    if (ev) cudaEventRecord(ev[0], s);
+    grpic_status st = push_impl(ctx, p, f, false, s);
+    cudaError_t e = cudaSuccess;
+    if (!st && ctx->prm.radiation) e = launch_append_children(ctx, p, s);
+    if (e != cudaSuccess) st = cuda_fail(ctx, e, "radiation");
+    if (ev) cudaEventRecord(ev[1], s);
+    if (!st) st = field_impl(ctx, f, s);
+    if (!st && ctx->prm.injection) {
+        e = launch_injection(ctx, p, f, s);
+        if (e != cudaSuccess) st = cuda_fail(ctx, e, "injection");
+    }
+    if (ev) cudaEventRecord(ev[2], s);
+    if (!st) {
+        ctx->hist_valid = 0;        // the appended slots carry keys, the histogram is rebuilt
+        ctx->sorted_tag = nullptr;  // general path
+        st = sort_impl(ctx, p, scratch, s, true);
+    }
+    if (ev) {
+        cudaEventRecord(ev[3], s);
+        ctx->tsteps++;
+    }
+    if (!st) ctx->step_count++;
+    return st;
+}
+
 grpic_status grpic_step(grpic_ctx *ctx, grpic_particles *p, grpic_particles *scratch, grpic_fields *f, int nsteps,
                         void *stream)
 {
@@ -450,6 +494,18 @@ grpic_status grpic_step(grpic_ctx *ctx, grpic_particles *p, grpic_particles *scr
     if (nsteps < 0 || !particles_ok(ctx, p) || !fields_ok(ctx, f) ||
         (every > 0 && (!particles_ok(ctx, scratch) || scratch->capacity < p->n)))
         return fail(ctx, GRPIC_EINVAL, "grpic_step: bad arguments");
+    if (ctx->prm.radiation || ctx->prm.injection) {
+        // new particles: the whole capacity is the slot range, the device
+        // count the live particles; every step sorts
+        if (every != 1 || scratch->capacity < p->capacity)
+            return fail(ctx, GRPIC_EINVAL, "grpic_step: radiation and injection need sort_every 1 and equal buffers");
+        p->n = p->capacity;
+        scratch->n = scratch->capacity;
+        grpic_status st = ensure_particle_scratch(ctx, p->capacity);
+        if (!st && ensure_rad_scratch(ctx, p->capacity) != cudaSuccess) st = fail(ctx, GRPIC_ENOMEM, "radiation scratch");
+        for (int k = 0; k < nsteps && !st; ++k) st = step_one_rad(ctx, p, scratch, f, S(stream));
+        return st;
+    }
     grpic_status st = GRPIC_OK;
     // a sort followed by this call's next push leaves only its order (the
     // push reads through it); the call's last sort moves the data
@@ -468,7 +524,7 @@ grpic_status grpic_step_graph(grpic_ctx *ctx, grpic_particles *p, grpic_particle
     if (nsteps < 0 || ctx->prm.sort_every != 1 || !particles_ok(ctx, p) || !fields_ok(ctx, f) ||
         !particles_ok(ctx, scratch) || scratch->capacity < p->n)
         return fail(ctx, GRPIC_EINVAL, "grpic_step_graph: bad arguments (sort_every must be 1)");
-    if (nsteps < 4) return grpic_step(ctx, p, scratch, f, nsteps, stream);
+    if (nsteps < 4 || ctx->prm.radiation || ctx->prm.injection) return grpic_step(ctx, p, scratch, f, nsteps, stream);
     grpic_status st = GRPIC_OK;
     int done = 0;
     // head: a plain step if the particles are not a sort's output, then one
@@ -647,7 +703,7 @@ void grpic_destroy(grpic_ctx *ctx)
     }
     if (ctx->graph_exec) cudaGraphExecDestroy(ctx->graph_exec);
     if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
-    void *ptrs[] = {ctx->d_offset_prev, ctx->d_cnt9, ctx->d_base9, ctx->d_sortflag, ctx->rcol, ctx->rcol2, ctx->rowsc, ctx->tab, ctx->col1d, ctx->tab32, ctx->col1d32, ctx->fscratch, ctx->d_status, ctx->d_keys,
+    void *ptrs[] = {ctx->d_spawn, ctx->d_rad, ctx->d_spqm, ctx->d_spmassive, ctx->d_offset_prev, ctx->d_cnt9, ctx->d_base9, ctx->d_sortflag, ctx->rcol, ctx->rcol2, ctx->rowsc, ctx->tab, ctx->col1d, ctx->tab32, ctx->col1d32, ctx->fscratch, ctx->d_status, ctx->d_keys,
                     ctx->d_count, ctx->d_offset, ctx->d_cursor, ctx->d_blocksum, ctx->d_perm, ctx->d_bigseg};
     for (void *q : ptrs)
         if (q) cudaFree(q);

@@ -80,6 +80,13 @@ struct grpic_ctx {
     int pending_perm;
     const uint32_t *pending_tag;
     int counts_ready;  // the last (permuted) push filled d_cnt9 for the next sort
+    // 2D radiation and injection: per-slot spawn counts, block sums/offsets,
+    // charged particles and injection flags per cell; q/m and massive per
+    // species on the device
+    int32_t *d_spawn, *d_rad;
+    int64_t rad_cap;
+    double *d_spqm;
+    int *d_spmassive;
     int64_t perm_cap;
     int keys_valid;       // keys of the current order are valid
     int hist_valid;       // and so is their histogram (d_count)
@@ -179,6 +186,10 @@ cudaError_t launch_field64_stages(grpic_ctx *ctx, double *const Xn[6], double *c
                                   cudaStream_t s);
 cudaError_t launch_field32(grpic_ctx *ctx, grpic_fields *f, cudaStream_t s);
 cudaError_t launch_tables_at(grpic_ctx *ctx, double a, double *tab, double *col1d, cudaStream_t s);
+cudaError_t launch_scan_i32(const int32_t *in, int32_t *out, int32_t *bsum, int64_t n, cudaStream_t s);
+cudaError_t ensure_rad_scratch(grpic_ctx *ctx, int64_t cap);
+cudaError_t launch_append_children(grpic_ctx *ctx, grpic_particles *p, cudaStream_t s);
+cudaError_t launch_injection(grpic_ctx *ctx, grpic_particles *p, const grpic_fields *f, cudaStream_t s);
 cudaError_t launch_keys(grpic_ctx *ctx, const grpic_particles *p, cudaStream_t s);
 cudaError_t sort_setup();
 cudaError_t launch_sort(grpic_ctx *ctx, grpic_particles *p, grpic_particles *scratch, cudaStream_t s);

@@ -24,6 +24,7 @@
 #include "grpic_window.cuh"
 #include "grpic_vay.cuh"
 #include "grpic_shape3.cuh"
+#include "grpic_philox.cuh"
 
 namespace grpic {
 namespace {
@@ -52,6 +53,13 @@ struct Push64Args {
     int32_t *count;
     int histogram;
     int pusher;  // 0 generalized Boris, 1 Vay in the FIDO frame
+    // 2D radiation: emission / conversion decisions per slot into spawn
+    // (0, 1 photon, 2 pair), see grpic_rad.cu
+    int radiation;
+    double gamma_thr, eps_ph, pconv;
+    uint64_t seed;
+    int64_t step;
+    int32_t *spawn;
     int *status;
 };
 
@@ -236,6 +244,7 @@ __global__ void __launch_bounds__(256) push64_kernel(Push64Args A)
     }
 
     bool dep = false;
+    int spawn = 0;
     double win[NWIN];
     int i0 = 0, j0 = 0, key = -1;
     if (live) {
@@ -359,9 +368,34 @@ __global__ void __launch_bounds__(256) push64_kernel(Push64Args A)
                 int ib = (int)floor(x1b);
                 ib = ib < 0 ? 0 : (ib > g.nr - 1 ? g.nr - 1 : ib);
                 key = (tag & DEAD) ? ncell : (jcell(g, x2b) * g.nr + ib);
+                if (A.radiation && !(tag & DEAD)) {
+                    // at the new position: emission by a charged particle above
+                    // gamma_thr, conversion of a photon above 2 m c^2
+                    KS m;
+                    ks_point(g.a, r, th, m);
+                    const double uu = m.gi_rr * u[0] * u[0] + 2.0 * m.gi_rp * u[0] * u[2] + m.gi_tt * u[1] * u[1] +
+                                      m.gi_pp * u[2] * u[2];
+                    if (A.massive[sp] && A.qm[sp] != 0.0) {
+                        const double G = sqrt(1.0 + uu), G2 = G - A.eps_ph;
+                        if (G >= A.gamma_thr && G2 >= 1.0) {
+                            const double f = sqrt(G2 * G2 - 1.0) / sqrt(uu);
+                            u[0] *= f;
+                            u[1] *= f;
+                            u[2] *= f;
+                            spawn = 1;
+                        }
+                    } else if (!A.massive[sp]) {
+                        if (sqrt(uu) > 2.0 && uniform53(A.seed, (uint64_t)p, A.step, 1) < A.pconv) {
+                            spawn = 2;
+                            tag |= DEAD;
+                            key = ncell;
+                        }
+                    }
+                }
             }
         }
     }
+    if (A.spawn && p < n) A.spawn[p] = spawn;
     if (p < n) {
         if (dep || permuted) {
             A.r[p] = r;
@@ -472,6 +506,13 @@ cudaError_t launch_push64(grpic_ctx *ctx, const grpic_particles *in, grpic_parti
     A.count = ctx->d_count;
     A.histogram = histogram ? 1 : 0;
     A.pusher = ctx->prm.pusher;
+    A.radiation = ctx->prm.radiation;
+    A.gamma_thr = ctx->prm.gamma_thr;
+    A.eps_ph = ctx->prm.eps_ph;
+    A.pconv = 1.0 - std::exp(-ctx->prm.tau * ctx->prm.dt);
+    A.seed = ctx->prm.seed;
+    A.step = ctx->step_count;
+    A.spawn = ctx->prm.radiation ? ctx->d_spawn : nullptr;
     A.status = ctx->d_status;
     if (p->n <= 0) return cudaSuccess;
     int64_t blocks = (p->n + 255) / 256;

@@ -634,6 +634,19 @@ __global__ void __launch_bounds__(256) neighbour_perm_kernel(const int32_t *off_
 
 }  // namespace
 
+// exclusive scan of n int32 values into out[0..n) and their total into
+// out[n]; bsum: SCAN_TILE scratch entries (n <= SCAN_TILE^2)
+cudaError_t launch_scan_i32(const int32_t *in, int32_t *out, int32_t *bsum, int64_t n, cudaStream_t s)
+{
+    const int64_t nb = (n + SCAN_TILE - 1) / SCAN_TILE;
+    if (nb > SCAN_TILE) return cudaErrorInvalidValue;
+    if (n <= 0) return cudaMemsetAsync(out, 0, sizeof(int32_t), s);
+    scan_tiles<<<(unsigned)nb, SCAN_T, 0, s>>>(in, out, bsum, n);
+    scan_sums<<<1, SCAN_T, 0, s>>>(bsum, (int)nb, out + n);
+    add_back<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(out, bsum, n);
+    return cudaGetLastError();
+}
+
 cudaError_t sort_setup()
 {
     return cudaFuncSetAttribute(bigseg_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,

@@ -39,7 +39,9 @@ class Params(C.Structure):
                 ("n_push_iter", C.c_int32), ("q_over_m", C.c_double * 4), ("q_weight", C.c_double * 4),
                 ("massive", C.c_int32 * 4), ("precision", C.c_int32), ("sort_every", C.c_int32),
                 ("fp64_radius", C.c_double), ("push_tol", C.c_double), ("island_arith", C.c_int32),
-                ("pusher", C.c_int32), ("shape_order", C.c_int32)]
+                ("pusher", C.c_int32), ("shape_order", C.c_int32), ("radiation", C.c_int32),
+                ("injection", C.c_int32), ("gamma_thr", C.c_double), ("eps_ph", C.c_double), ("tau", C.c_double),
+                ("sigma_thr", C.c_double), ("eps_db", C.c_double), ("seed", C.c_uint64)]
 
 
 class ParticlesC(C.Structure):
@@ -130,6 +132,14 @@ class Config:
     island_arith: int = 0     # 0 double-FP32 pairs, 1 native FP64
     pusher: int = 0           # 0 generalized Boris, 1 Vay in the FIDO frame
     shape_order: int = 1      # 1 cloud in cell, 3 cubic spline (FP64 path)
+    radiation: int = 0        # 2D photon emission and pair conversion (FP64 path)
+    injection: int = 0        # pair injection where sigma > sigma_thr and |D.B|/B^2 > eps_db
+    gamma_thr: float = 100.0
+    eps_ph: float = 4.0
+    tau: float = 2.0
+    sigma_thr: float = 10.0
+    eps_db: float = 1e-3
+    seed: int = 0
 
     def __post_init__(self):
         self.dx1 = math.log(self.r_out / self.r_in) / self.n_r
@@ -155,6 +165,9 @@ class Config:
         p.island_arith = self.island_arith
         p.pusher = self.pusher
         p.shape_order = self.shape_order
+        p.radiation, p.injection = self.radiation, self.injection
+        p.gamma_thr, p.eps_ph, p.tau = self.gamma_thr, self.eps_ph, self.tau
+        p.sigma_thr, p.eps_db, p.seed = self.sigma_thr, self.eps_db, self.seed
         return p
 
 
@@ -342,6 +355,7 @@ class Context:
         self._check(self.lib.grpic_step(self.h, C.byref(P._sc), C.byref(P._ss), C.byref(fc), nsteps,
                                         _stream(stream)), "grpic_step")
         P.sync_ptrs()
+        P.n = P._sc.n   # radiation or injection: the whole capacity is the slot range
 
     def set_timing(self, enable: bool):
         """Record per-phase CUDA events in every step of grpic_step."""
