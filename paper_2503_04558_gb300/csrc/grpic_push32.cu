@@ -444,8 +444,8 @@ __global__ void __launch_bounds__(256, GRPIC_PUSH32_MINB) push32_kernel(Push32Ar
     }
 
     // ---- deposit: lanes grouped by start cell, each group reduce-scattered --
-    deposit_warp<float, 3>(dep, i, j, g.nr, wa1, wa2, wb1, wb2, wq, wphi, A.dt, lane, g.nth, NG, A.ld, A.J0, A.J1,
-                        A.J2);
+    deposit_warp_split<float, 3>(dep, i, j, g.nr, wa1, wa2, wb1, wb2, wq, wphi, A.dt, lane, g.nth, NG, A.ld, A.J0,
+                                 A.J1, A.J2);
 }
 
 }  // namespace

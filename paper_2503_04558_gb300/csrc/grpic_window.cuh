@@ -205,4 +205,149 @@ __device__ __forceinline__ void deposit_warp(bool dep, int i0, int j0, int nr, T
     }
 }
 
+// The same deposit split by support.  A particle that stays in its start
+// cell touches 8 window entries only (J^r A at face 1, rows 1-2; J^theta A at
+// columns 1-2, face 1; J^phi dV at columns 1-2, rows 1-2): every lane adds its
+// values at those 8 "core" entries into a warp reduction (grouped by start
+// cell as above, 9 shuffles instead of 45), and a lane whose end point left
+// the start cell (di, dj = floor(b) in -1..1 not both 0) adds its other
+// nonzero entries directly: the extra column ex = 0 or 3 (face ef = 0 or 2)
+// of an r move and the extra row of a theta move, 5 entries for a move along
+// one axis, 13 for a diagonal one.  The entries and values are those of
+// esirkepov_window; lanes that stay execute the extra part predicated off.
+template <typename T>
+__device__ __forceinline__ void reduce8(T v[8], int lane, T &tot, int &idx)
+{
+    const unsigned FULL = 0xffffffffu;
+    int base = 0;
+#pragma unroll
+    for (int st = 0, half = 4, m = 16; st < 3; ++st, half >>= 1, m >>= 1) {
+        const bool hi = lane & m;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            if (k < half) {
+                T keep = hi ? v[k + half] : v[k];
+                T send = hi ? v[k] : v[k + half];
+                v[k] = keep + __shfl_xor_sync(FULL, send, m);
+            }
+        }
+        base += hi ? half : 0;
+    }
+    v[0] += __shfl_xor_sync(FULL, v[0], 2);
+    v[0] += __shfl_xor_sync(FULL, v[0], 1);
+    tot = v[0];
+    idx = (lane & 3) == 0 ? base : -1;  // one lane of each quad adds
+}
+
+template <typename T, int MAXG>
+__device__ __forceinline__ void deposit_warp_split(bool dep, int i0, int j0, int nr, T a1, T a2, T b1, T b2, T qw,
+                                                   T dphi, T dt, int lane, int nth, int ng, int64_t ld, T *J0, T *J1,
+                                                   T *J2)
+{
+    const unsigned FULL = 0xffffffffu;
+    // per-dimension weights (k, l = 0..3 stand for columns / rows -1..2)
+    T S1r[4], S1t[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        S1r[k] = cic_weight<T>(b1 - T(k - 1));
+        S1t[k] = cic_weight<T>(b2 - T(k - 1));
+    }
+    const T S0r1 = T(1) - a1, S0r2 = a1, S0t1 = T(1) - a2, S0t2 = a2;
+    const T cr = -qw / (T(2) * dt), cp = qw * dphi / dt;
+    // prefix sums: Pr(k) = sum_{k' <= k} (S1r - S0r)(k'), Pt likewise
+    const T Pr0 = S1r[0], Pr1 = Pr0 + S1r[1] - S0r1, Pr2 = Pr1 + S1r[2] - S0r2;
+    const T Pt0 = S1t[0], Pt1 = Pt0 + S1t[1] - S0t1, Pt2 = Pt1 + S1t[2] - S0t2;
+    const T S0t[4] = {T(0), S0t1, S0t2, T(0)}, S0r[4] = {T(0), S0r1, S0r2, T(0)};
+    T cU[4], cV[4];
+#pragma unroll
+    for (int l = 0; l < 4; ++l) {
+        cU[l] = cp * (S1t[l] * (T(1) / T(3)) + S0t[l] * (T(1) / T(6)));
+        cV[l] = cp * (S1t[l] * (T(1) / T(6)) + S0t[l] * (T(1) / T(3)));
+    }
+    // ---- the 8 core entries, reduced per start-cell group
+    const int wk = dep ? j0 * nr + i0 : -1;
+    bool pending = dep;
+#pragma unroll 1
+    for (int pass = 0; pass < MAXG; ++pass) {
+        const unsigned todo = __ballot_sync(FULL, pending);
+        if (!todo) break;
+        const int leader = __ffs(todo) - 1;
+        const int gk = __shfl_sync(FULL, wk, leader);
+        const int gi = __shfl_sync(FULL, i0, leader), gj = __shfl_sync(FULL, j0, leader);
+        const bool in = pending && wk == gk;
+        T v[8];
+        if (in) {
+            const T c1 = cr * Pr1;
+            v[0] = c1 * (S1t[1] + S0t1);  // J^r A (face 1, row 1)
+            v[1] = c1 * (S1t[2] + S0t2);  // J^r A (face 1, row 2)
+            const T c2 = cr * Pt1;
+            v[2] = c2 * (S1r[1] + S0r1);  // J^th A (column 1, face 1)
+            v[3] = c2 * (S1r[2] + S0r2);  // J^th A (column 2, face 1)
+            v[4] = S1r[1] * cU[1] + S0r1 * cV[1];  // J^ph (1, 1)
+            v[5] = S1r[1] * cU[2] + S0r1 * cV[2];  // J^ph (1, 2)
+            v[6] = S1r[2] * cU[1] + S0r2 * cV[1];  // J^ph (2, 1)
+            v[7] = S1r[2] * cU[2] + S0r2 * cV[2];  // J^ph (2, 2)
+        } else {
+#pragma unroll
+            for (int k = 0; k < 8; ++k) v[k] = T(0);
+        }
+        T tot;
+        int idx;
+        reduce8<T>(v, lane, tot, idx);
+        if (idx >= 0 && tot != T(0)) {
+            // core entry idx -> window index of esirkepov_window: 5, 6 (J^r A),
+            // 16, 19 (J^th A), 29, 30, 33, 34 (J^ph)
+            const int wi = idx < 2 ? 5 + idx : (idx < 4 ? 16 + 3 * (idx - 2) : (idx < 6 ? 25 + idx : 27 + idx));
+            window_add<T>(wi, tot, gi, gj, nth, ng, ld, J0, J1, J2);
+        }
+        pending = pending && !in;
+    }
+    if (pending) {
+        // lanes of start cells beyond MAXG groups: their core entries directly
+        const T c1 = cr * Pr1, c2 = cr * Pt1;
+        window_add<T>(1 * 4 + 1, c1 * (S1t[1] + S0t1), i0, j0, nth, ng, ld, J0, J1, J2);
+        window_add<T>(1 * 4 + 2, c1 * (S1t[2] + S0t2), i0, j0, nth, ng, ld, J0, J1, J2);
+        window_add<T>(12 + 1 * 3 + 1, c2 * (S1r[1] + S0r1), i0, j0, nth, ng, ld, J0, J1, J2);
+        window_add<T>(12 + 2 * 3 + 1, c2 * (S1r[2] + S0r2), i0, j0, nth, ng, ld, J0, J1, J2);
+        window_add<T>(24 + 1 * 4 + 1, S1r[1] * cU[1] + S0r1 * cV[1], i0, j0, nth, ng, ld, J0, J1, J2);
+        window_add<T>(24 + 1 * 4 + 2, S1r[1] * cU[2] + S0r1 * cV[2], i0, j0, nth, ng, ld, J0, J1, J2);
+        window_add<T>(24 + 2 * 4 + 1, S1r[2] * cU[1] + S0r2 * cV[1], i0, j0, nth, ng, ld, J0, J1, J2);
+        window_add<T>(24 + 2 * 4 + 2, S1r[2] * cU[2] + S0r2 * cV[2], i0, j0, nth, ng, ld, J0, J1, J2);
+    }
+    // ---- the entries outside the core, lanes that left the start cell
+    const int di = dep ? (int)floor(b1) : 0, dj = dep ? (int)floor(b2) : 0;
+    if (!__any_sync(FULL, di != 0 || dj != 0)) return;
+    const int ex = di > 0 ? 3 : 0, ef = di > 0 ? 2 : 0;  // extra column / face (valid if di != 0)
+    const int ey = dj > 0 ? 3 : 0, eg = dj > 0 ? 2 : 0;  // extra row / theta face (valid if dj != 0)
+    const T Prx = ef == 2 ? Pr2 : Pr0, Ptx = eg == 2 ? Pt2 : Pt0;
+    const T S1rx = S1r[ex], S1tx = S1t[ey];
+    if (di != 0) {
+        // J^r A at the extra face, rows 1, 2 (and the extra row)
+        window_add<T>(ef * 4 + 1, cr * Prx * (S1t[1] + S0t1), i0, j0, nth, ng, ld, J0, J1, J2);
+        window_add<T>(ef * 4 + 2, cr * Prx * (S1t[2] + S0t2), i0, j0, nth, ng, ld, J0, J1, J2);
+        // J^th A at the extra column, face 1; J^ph at the extra column, rows 1, 2
+        window_add<T>(12 + ex * 3 + 1, cr * S1rx * Pt1, i0, j0, nth, ng, ld, J0, J1, J2);
+        window_add<T>(24 + ex * 4 + 1, S1rx * cU[1], i0, j0, nth, ng, ld, J0, J1, J2);
+        window_add<T>(24 + ex * 4 + 2, S1rx * cU[2], i0, j0, nth, ng, ld, J0, J1, J2);
+    }
+    if (dj != 0) {
+        // J^th A at the extra theta face, columns 1, 2; J^r A at face 1, the
+        // extra row; J^ph at columns 1, 2, the extra row
+        window_add<T>(12 + 1 * 3 + eg, cr * (S1r[1] + S0r1) * Ptx, i0, j0, nth, ng, ld, J0, J1, J2);
+        window_add<T>(12 + 2 * 3 + eg, cr * (S1r[2] + S0r2) * Ptx, i0, j0, nth, ng, ld, J0, J1, J2);
+        window_add<T>(1 * 4 + ey, cr * Pr1 * S1tx, i0, j0, nth, ng, ld, J0, J1, J2);
+        window_add<T>(24 + 1 * 4 + ey, S1r[1] * cp * S1tx * (T(1) / T(3)) + S0r1 * cp * S1tx * (T(1) / T(6)), i0, j0,
+                      nth, ng, ld, J0, J1, J2);
+        window_add<T>(24 + 2 * 4 + ey, S1r[2] * cp * S1tx * (T(1) / T(3)) + S0r2 * cp * S1tx * (T(1) / T(6)), i0, j0,
+                      nth, ng, ld, J0, J1, J2);
+    }
+    if (di != 0 && dj != 0) {
+        // the corner: J^r A (extra face, extra row), J^th A (extra column,
+        // extra theta face), J^ph (extra column, extra row)
+        window_add<T>(ef * 4 + ey, cr * Prx * S1tx, i0, j0, nth, ng, ld, J0, J1, J2);
+        window_add<T>(12 + ex * 3 + eg, cr * S1rx * Ptx, i0, j0, nth, ng, ld, J0, J1, J2);
+        window_add<T>(24 + ex * 4 + ey, S1rx * cp * S1tx * (T(1) / T(3)), i0, j0, nth, ng, ld, J0, J1, J2);
+    }
+}
+
 }  // namespace grpic
