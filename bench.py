@@ -53,12 +53,12 @@ B0 = 1.0
 # kernels (flop_count = 2 FMA + MUL + ADD of the SASS instruction counters;
 # the capture commands and counts are in profiles/).
 PUSH64_FP64_FLOP = 1734.0   # profiles/push64_fp64_512x512_64ppc.md
-PUSH32_FP32_FLOP = 1248.0   # profiles/push32_fp32form_1024x1024_64ppc.md
+PUSH32_FP32_FLOP = 1136.0   # profiles/push32_fp32form_1024x1024_64ppc.md
 # the same capture: instructions issued per particle (warp instructions x 32)
 # and DRAM bytes per particle (read + write), scaled to a launch by the
 # number of particles
-PUSH32_INST = 2145.0
-PUSH32_DRAM_B = 68.3
+PUSH32_INST = 1942.0
+PUSH32_DRAM_B = 70.0
 # ALU peaks from unit counts x clock: 152 SMs x 2.07 GHz x (4 FP64 flops,
 # 256 FP32 flops) per SM per clock; instruction issue: 4 schedulers x 1 warp
 # instruction per SM per clock

@@ -214,7 +214,7 @@ __device__ __forceinline__ int jcell(const GridDev &g, double x2)
 // SHAPE 1: cloud in cell (bilinear interpolation, 4 x 4 window reduced across
 // the warp); SHAPE 3: the cubic spline of grpic_shape3.cuh (4 x 4 taps,
 // per-lane deposit of the 5 x 5 window)
-template <int SHAPE>
+template <int SHAPE, bool RAD>
 __global__ void __launch_bounds__(256) push64_kernel(Push64Args A)
 {
     const GridDev &g = A.g;
@@ -368,7 +368,7 @@ __global__ void __launch_bounds__(256) push64_kernel(Push64Args A)
                 int ib = (int)floor(x1b);
                 ib = ib < 0 ? 0 : (ib > g.nr - 1 ? g.nr - 1 : ib);
                 key = (tag & DEAD) ? ncell : (jcell(g, x2b) * g.nr + ib);
-                if (A.radiation && !(tag & DEAD)) {
+                if (RAD && !(tag & DEAD)) {
                     // at the new position: emission by a charged particle above
                     // gamma_thr, conversion of a photon above 2 m c^2
                     KS m;
@@ -395,7 +395,7 @@ __global__ void __launch_bounds__(256) push64_kernel(Push64Args A)
             }
         }
     }
-    if (A.spawn && p < n) A.spawn[p] = spawn;
+    if (RAD && p < n) A.spawn[p] = spawn;
     if (p < n) {
         if (dep || permuted) {
             A.r[p] = r;
@@ -516,10 +516,18 @@ cudaError_t launch_push64(grpic_ctx *ctx, const grpic_particles *in, grpic_parti
     A.status = ctx->d_status;
     if (p->n <= 0) return cudaSuccess;
     int64_t blocks = (p->n + 255) / 256;
-    if (ctx->prm.shape_order == 3)
-        push64_kernel<3><<<(unsigned)blocks, 256, 0, s>>>(A);
-    else
-        push64_kernel<1><<<(unsigned)blocks, 256, 0, s>>>(A);
+    const bool rad = ctx->prm.radiation != 0;
+    if (ctx->prm.shape_order == 3) {
+        if (rad)
+            push64_kernel<3, true><<<(unsigned)blocks, 256, 0, s>>>(A);
+        else
+            push64_kernel<3, false><<<(unsigned)blocks, 256, 0, s>>>(A);
+    } else {
+        if (rad)
+            push64_kernel<1, true><<<(unsigned)blocks, 256, 0, s>>>(A);
+        else
+            push64_kernel<1, false><<<(unsigned)blocks, 256, 0, s>>>(A);
+    }
     return cudaGetLastError();
 }
 
