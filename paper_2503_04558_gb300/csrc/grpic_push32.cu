@@ -224,9 +224,12 @@ __device__ __forceinline__ void push_one(const Push32Args &A, int i, int j, floa
         const float4 sc = __ldg(reinterpret_cast<const float4 *>(A.rowsc) + j);
         sincos_shift_df(df(sc.x, sc.y), df(sc.z, sc.w), mul(A.dth_df, o2), s0, c0);
     } else {
+        // sin, cos of theta_j (row table) shifted by o2 dtheta (|shift| <= one
+        // cell: the series of sincos_shift is exact to FP32 rounding there)
         am = A.af;
         r0 = rcf + d0;
-        sincosf(((float)j + o2) * A.dthf, &s0, &c0);
+        const float4 sc = __ldg(reinterpret_cast<const float4 *>(A.rowsc) + j);
+        sincos_shift<float>(sc.x, sc.z, o2 * A.dthf, s0, c0);
     }
     KSGeo<M> m;
     ks_geo_sc<M>(am, r0, s0, c0, m);

@@ -239,6 +239,15 @@ __device__ __forceinline__ void reduce8(T v[8], int lane, T &tot, int &idx)
     idx = (lane & 3) == 0 ? base : -1;  // one lane of each quad adds
 }
 
+// add v at window column k, row l of one current array (rows 0..rmax exist)
+template <typename T>
+__device__ __forceinline__ void add_at(T *J, int rmax, int i0, int j0, int k, int l, int ng, int64_t ld, T v)
+{
+    const int row = j0 - 1 + l;
+    if (v == T(0) || row < 0 || row > rmax) return;
+    atomicAdd(J + (size_t)row * ld + (i0 - 1 + k + ng), v);
+}
+
 template <typename T, int MAXG>
 __device__ __forceinline__ void deposit_warp_split(bool dep, int i0, int j0, int nr, T a1, T a2, T b1, T b2, T qw,
                                                    T dphi, T dt, int lane, int nth, int ng, int64_t ld, T *J0, T *J1,
@@ -294,25 +303,27 @@ __device__ __forceinline__ void deposit_warp_split(bool dep, int i0, int j0, int
         T tot;
         int idx;
         reduce8<T>(v, lane, tot, idx);
-        if (idx >= 0 && tot != T(0)) {
-            // core entry idx -> window index of esirkepov_window: 5, 6 (J^r A),
-            // 16, 19 (J^th A), 29, 30, 33, 34 (J^ph)
-            const int wi = idx < 2 ? 5 + idx : (idx < 4 ? 16 + 3 * (idx - 2) : (idx < 6 ? 25 + idx : 27 + idx));
-            window_add<T>(wi, tot, gi, gj, nth, ng, ld, J0, J1, J2);
+        if (idx >= 0) {
+            // core entry idx: 0, 1 J^r A (face 1, rows 1, 2); 2, 3 J^th A
+            // (columns 1, 2, face 1); 4..7 J^ph (columns 1, 2 x rows 1, 2)
+            T *J = idx < 2 ? J0 : (idx < 4 ? J1 : J2);
+            const int k = idx < 2 ? 1 : (idx < 4 ? idx - 1 : 1 + ((idx - 4) >> 1));
+            const int l = idx < 2 ? 1 + idx : (idx < 4 ? 1 : 1 + ((idx - 4) & 1));
+            add_at<T>(J, idx < 4 && idx >= 2 ? nth - 1 : nth, gi, gj, k, l, ng, ld, tot);
         }
         pending = pending && !in;
     }
     if (pending) {
         // lanes of start cells beyond MAXG groups: their core entries directly
         const T c1 = cr * Pr1, c2 = cr * Pt1;
-        window_add<T>(1 * 4 + 1, c1 * (S1t[1] + S0t1), i0, j0, nth, ng, ld, J0, J1, J2);
-        window_add<T>(1 * 4 + 2, c1 * (S1t[2] + S0t2), i0, j0, nth, ng, ld, J0, J1, J2);
-        window_add<T>(12 + 1 * 3 + 1, c2 * (S1r[1] + S0r1), i0, j0, nth, ng, ld, J0, J1, J2);
-        window_add<T>(12 + 2 * 3 + 1, c2 * (S1r[2] + S0r2), i0, j0, nth, ng, ld, J0, J1, J2);
-        window_add<T>(24 + 1 * 4 + 1, S1r[1] * cU[1] + S0r1 * cV[1], i0, j0, nth, ng, ld, J0, J1, J2);
-        window_add<T>(24 + 1 * 4 + 2, S1r[1] * cU[2] + S0r1 * cV[2], i0, j0, nth, ng, ld, J0, J1, J2);
-        window_add<T>(24 + 2 * 4 + 1, S1r[2] * cU[1] + S0r2 * cV[1], i0, j0, nth, ng, ld, J0, J1, J2);
-        window_add<T>(24 + 2 * 4 + 2, S1r[2] * cU[2] + S0r2 * cV[2], i0, j0, nth, ng, ld, J0, J1, J2);
+        add_at<T>(J0, nth, i0, j0, 1, 1, ng, ld, c1 * (S1t[1] + S0t1));
+        add_at<T>(J0, nth, i0, j0, 1, 2, ng, ld, c1 * (S1t[2] + S0t2));
+        add_at<T>(J1, nth - 1, i0, j0, 1, 1, ng, ld, c2 * (S1r[1] + S0r1));
+        add_at<T>(J1, nth - 1, i0, j0, 2, 1, ng, ld, c2 * (S1r[2] + S0r2));
+        add_at<T>(J2, nth, i0, j0, 1, 1, ng, ld, S1r[1] * cU[1] + S0r1 * cV[1]);
+        add_at<T>(J2, nth, i0, j0, 1, 2, ng, ld, S1r[1] * cU[2] + S0r1 * cV[2]);
+        add_at<T>(J2, nth, i0, j0, 2, 1, ng, ld, S1r[2] * cU[1] + S0r2 * cV[1]);
+        add_at<T>(J2, nth, i0, j0, 2, 2, ng, ld, S1r[2] * cU[2] + S0r2 * cV[2]);
     }
     // ---- the entries outside the core, lanes that left the start cell
     const int di = dep ? (int)floor(b1) : 0, dj = dep ? (int)floor(b2) : 0;
@@ -322,31 +333,30 @@ __device__ __forceinline__ void deposit_warp_split(bool dep, int i0, int j0, int
     const T Prx = ef == 2 ? Pr2 : Pr0, Ptx = eg == 2 ? Pt2 : Pt0;
     const T S1rx = S1r[ex], S1tx = S1t[ey];
     if (di != 0) {
-        // J^r A at the extra face, rows 1, 2 (and the extra row)
-        window_add<T>(ef * 4 + 1, cr * Prx * (S1t[1] + S0t1), i0, j0, nth, ng, ld, J0, J1, J2);
-        window_add<T>(ef * 4 + 2, cr * Prx * (S1t[2] + S0t2), i0, j0, nth, ng, ld, J0, J1, J2);
-        // J^th A at the extra column, face 1; J^ph at the extra column, rows 1, 2
-        window_add<T>(12 + ex * 3 + 1, cr * S1rx * Pt1, i0, j0, nth, ng, ld, J0, J1, J2);
-        window_add<T>(24 + ex * 4 + 1, S1rx * cU[1], i0, j0, nth, ng, ld, J0, J1, J2);
-        window_add<T>(24 + ex * 4 + 2, S1rx * cU[2], i0, j0, nth, ng, ld, J0, J1, J2);
+        // J^r A at the extra face, rows 1, 2; J^th A at the extra column,
+        // face 1; J^ph at the extra column, rows 1, 2
+        add_at<T>(J0, nth, i0, j0, ef, 1, ng, ld, cr * Prx * (S1t[1] + S0t1));
+        add_at<T>(J0, nth, i0, j0, ef, 2, ng, ld, cr * Prx * (S1t[2] + S0t2));
+        add_at<T>(J1, nth - 1, i0, j0, ex, 1, ng, ld, cr * S1rx * Pt1);
+        add_at<T>(J2, nth, i0, j0, ex, 1, ng, ld, S1rx * cU[1]);
+        add_at<T>(J2, nth, i0, j0, ex, 2, ng, ld, S1rx * cU[2]);
     }
     if (dj != 0) {
         // J^th A at the extra theta face, columns 1, 2; J^r A at face 1, the
         // extra row; J^ph at columns 1, 2, the extra row
-        window_add<T>(12 + 1 * 3 + eg, cr * (S1r[1] + S0r1) * Ptx, i0, j0, nth, ng, ld, J0, J1, J2);
-        window_add<T>(12 + 2 * 3 + eg, cr * (S1r[2] + S0r2) * Ptx, i0, j0, nth, ng, ld, J0, J1, J2);
-        window_add<T>(1 * 4 + ey, cr * Pr1 * S1tx, i0, j0, nth, ng, ld, J0, J1, J2);
-        window_add<T>(24 + 1 * 4 + ey, S1r[1] * cp * S1tx * (T(1) / T(3)) + S0r1 * cp * S1tx * (T(1) / T(6)), i0, j0,
-                      nth, ng, ld, J0, J1, J2);
-        window_add<T>(24 + 2 * 4 + ey, S1r[2] * cp * S1tx * (T(1) / T(3)) + S0r2 * cp * S1tx * (T(1) / T(6)), i0, j0,
-                      nth, ng, ld, J0, J1, J2);
+        const T u3 = cp * S1tx * (T(1) / T(3)), u6 = cp * S1tx * (T(1) / T(6));
+        add_at<T>(J1, nth - 1, i0, j0, 1, eg, ng, ld, cr * (S1r[1] + S0r1) * Ptx);
+        add_at<T>(J1, nth - 1, i0, j0, 2, eg, ng, ld, cr * (S1r[2] + S0r2) * Ptx);
+        add_at<T>(J0, nth, i0, j0, 1, ey, ng, ld, cr * Pr1 * S1tx);
+        add_at<T>(J2, nth, i0, j0, 1, ey, ng, ld, S1r[1] * u3 + S0r1 * u6);
+        add_at<T>(J2, nth, i0, j0, 2, ey, ng, ld, S1r[2] * u3 + S0r2 * u6);
     }
     if (di != 0 && dj != 0) {
         // the corner: J^r A (extra face, extra row), J^th A (extra column,
         // extra theta face), J^ph (extra column, extra row)
-        window_add<T>(ef * 4 + ey, cr * Prx * S1tx, i0, j0, nth, ng, ld, J0, J1, J2);
-        window_add<T>(12 + ex * 3 + eg, cr * S1rx * Ptx, i0, j0, nth, ng, ld, J0, J1, J2);
-        window_add<T>(24 + ex * 4 + ey, S1rx * cp * S1tx * (T(1) / T(3)), i0, j0, nth, ng, ld, J0, J1, J2);
+        add_at<T>(J0, nth, i0, j0, ef, ey, ng, ld, cr * Prx * S1tx);
+        add_at<T>(J1, nth - 1, i0, j0, ex, eg, ng, ld, cr * S1rx * Ptx);
+        add_at<T>(J2, nth, i0, j0, ex, ey, ng, ld, S1rx * cp * S1tx * (T(1) / T(3)));
     }
 }
 
