@@ -199,11 +199,6 @@ __device__ __forceinline__ double gather(const double *__restrict__ F, int64_t l
     return S.p0 * (S.w00 * __ldg(a) + S.w10 * __ldg(a + 1)) + S.p1 * (S.w01 * __ldg(b) + S.w11 * __ldg(b + 1));
 }
 
-__device__ __forceinline__ double W1(double d)
-{
-    d = fabs(d);
-    return d < 1.0 ? 1.0 - d : 0.0;
-}
 
 __device__ __forceinline__ int jcell(const GridDev &g, double x2)
 {
@@ -245,7 +240,7 @@ __global__ void __launch_bounds__(256) push64_kernel(Push64Args A)
 
     bool dep = false;
     int spawn = 0;
-    double win[NWIN];
+    double wa1 = 0.0, wa2 = 0.0, wb1 = 0.0, wb2 = 0.0, wq = 0.0, wphi = 0.0;  // window inputs (CIC)
     int i0 = 0, j0 = 0, key = -1;
     if (live) {
         // a state outside the domain (or non-finite) would index the fields out
@@ -324,39 +319,14 @@ __global__ void __launch_bounds__(256) push64_kernel(Push64Args A)
                 if constexpr (SHAPE == 3) {
                     deposit3(g.nr, g.nth, A.ld, A.J0, A.J1, A.J2, A.qw[tag & 3u], dt, x1a, x2a, x1b, x2b, pt);
                 } else {
-                    // Esirkepov window: columns i0-1..i0+2, rows j0-1..j0+2
-                    int sp2 = tag & 3u;
-                    double qw = A.qw[sp2];
-                    double S0r[4], S1r[4], S0t[4], S1t[4];
-    #pragma unroll
-                    for (int k = 0; k < 4; ++k) {
-                        S0r[k] = W1(x1a - (i0 - 1 + k));
-                        S1r[k] = W1(x1b - (i0 - 1 + k));
-                        S0t[k] = W1(x2a - (j0 - 1 + k));
-                        S1t[k] = W1(x2b - (j0 - 1 + k));
-                    }
-                    double cr = -qw / (2.0 * dt);
-                    double cp = qw * pt / dt;
-                    double Pr = 0.0;
-    #pragma unroll
-                    for (int k = 0; k < 3; ++k) {
-                        Pr += S1r[k] - S0r[k];
-    #pragma unroll
-                        for (int l = 0; l < 4; ++l) win[k * 4 + l] = cr * Pr * (S1t[l] + S0t[l]);
-                    }
-                    double Pt = 0.0;
-    #pragma unroll
-                    for (int l = 0; l < 3; ++l) {
-                        Pt += S1t[l] - S0t[l];
-    #pragma unroll
-                        for (int k = 0; k < 4; ++k) win[12 + k * 3 + l] = cr * (S1r[k] + S0r[k]) * Pt;
-                    }
-    #pragma unroll
-                    for (int k = 0; k < 4; ++k)
-    #pragma unroll
-                        for (int l = 0; l < 4; ++l)
-                            win[24 + k * 4 + l] = cp * (S1r[k] * S1t[l] * (1.0 / 3.0) + S1r[k] * S0t[l] * (1.0 / 6.0) +
-                                                        S0r[k] * S1t[l] * (1.0 / 6.0) + S0r[k] * S0t[l] * (1.0 / 3.0));
+                    // inputs of the split window deposit, relative to the
+                    // start cell (i0, j0): the start in [0, 1], the end in [-1, 2]
+                    wq = A.qw[tag & 3u];
+                    wa1 = x1a - i0;
+                    wa2 = x2a - j0;
+                    wb1 = x1b - i0;
+                    wb2 = x2b - j0;
+                    wphi = pt;
                 }
                 dep = true;
                 r = rt;
@@ -411,32 +381,11 @@ __global__ void __launch_bounds__(256) push64_kernel(Push64Args A)
         A.tag[p] = DEAD;  // past the live slots of the permuted order
     }
 
-    // ---- deposit: warp-uniform start cell -> reduce-scatter over the lanes ---
-    if constexpr (SHAPE == 1) {
-    int wkey = dep ? (j0 * g.nr + i0) : -1;
-    unsigned act = __ballot_sync(FULL, dep);
-    if (act) {
-        int src = __ffs(act) - 1;
-        int ref = __shfl_sync(FULL, wkey, src);
-        bool uniform = __all_sync(FULL, !dep || wkey == ref);
-        if (uniform) {
-            int ri0 = __shfl_sync(FULL, i0, src);
-            int rj0 = __shfl_sync(FULL, j0, src);
-            if (!dep) {
-#pragma unroll
-                for (int v = 0; v < NWIN; ++v) win[v] = 0.0;
-            }
-            double tot[2];
-            int idx[2];
-            window_reduce_scatter<double>(win, lane, tot, idx);
-            window_add<double>(idx[0], tot[0], ri0, rj0, g.nth, NG, A.ld, A.J0, A.J1, A.J2);
-            window_add<double>(idx[1], tot[1], ri0, rj0, g.nth, NG, A.ld, A.J0, A.J1, A.J2);
-        } else if (dep) {
-#pragma unroll
-            for (int v = 0; v < NWIN; ++v) window_add<double>(v, win[v], i0, j0, g.nth, NG, A.ld, A.J0, A.J1, A.J2);
-        }
-    }
-    }
+    // ---- deposit (CIC): the core entries reduced across the warp by start
+    // cell, the entries of lanes that left their cell added directly
+    if constexpr (SHAPE == 1)
+        deposit_warp_split<double, 3>(dep, i0, j0, g.nr, wa1, wa2, wb1, wb2, wq, wphi, A.dt, lane, g.nth, NG, A.ld,
+                                      A.J0, A.J1, A.J2);
 
     // ---- histogram of the new keys (warp-aggregated) -----------------------
     if (A.histogram) {
