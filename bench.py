@@ -52,7 +52,8 @@ B0 = 1.0
 # Arithmetic per particle-step of the push kernels, counted by ncu on the same
 # kernels (flop_count = 2 FMA + MUL + ADD of the SASS instruction counters;
 # the capture commands and counts are in profiles/).
-PUSH64_FP64_FLOP = 1734.0   # profiles/push64_fp64_512x512_64ppc.md
+PUSH64_FP64_FLOP = 1528.0   # profiles/push64_fp64_512x512_64ppc.md
+PUSH64_DRAM_B = 95.9        # the same capture: DRAM bytes per particle (read + write)
 PUSH32_FP32_FLOP = 1136.0   # profiles/push32_fp32form_1024x1024_64ppc.md
 # the same capture: instructions issued per particle (warp instructions x 32)
 # and DRAM bytes per particle (read + write), scaled to a launch by the
@@ -666,6 +667,9 @@ def grpic_summary(res, args, world, esz_prec):
     if prec == 32:
         hbm["traffic"] = n * PUSH32_DRAM_B
         hbm["traffic_source"] = "ncu dram bytes per particle at 1024^2 x 64 ppc, x particles"
+    else:
+        hbm["traffic"] = n * PUSH64_DRAM_B
+        hbm["traffic_source"] = "ncu dram bytes per particle at 512^2 x 64 ppc, x particles"
     roof = {"kernel": "push+deposit (FP32 form)", "bound": "alu", "achieved": ach32, "peak": FP32_PEAK_TFLOPS,
             "unit": "TFLOP/s", "frac": ach32 / FP32_PEAK_TFLOPS, "traffic": n * PUSH32_DRAM_B,
             "peak_source": "152 SMs x 2.07 GHz x 256 FP32 flop/clk/SM (recipe unit counts and clock)",
@@ -677,7 +681,7 @@ def grpic_summary(res, args, world, esz_prec):
         # FP64 arithmetic bounds this kernel on GB300: report the FP64 roofline
         ach = n * PUSH64_FP64_FLOP / (push_ms * 1e-3) / 1e12
         roof = {"kernel": "push+deposit (FP64)", "bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS,
-                "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS, "traffic": None,
+                "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS, "traffic": n * PUSH64_DRAM_B,
                 "peak_source": "152 SMs x 2.07 GHz x 4 FP64 flop/clk/SM (recipe unit counts and clock)",
                 "flop_per_particle": PUSH64_FP64_FLOP, "hbm": hbm}
     return {"value": job_value(n, args.steps, world, res["total_ms"]), "ms_per_step": ms,
