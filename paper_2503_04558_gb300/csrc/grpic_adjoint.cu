@@ -19,7 +19,10 @@
 //            products of the right-hand side are a hand-written reverse pass;
 //            the metric's derivatives and the other local Jacobians come from
 //            forward-mode dual numbers through the same metric code.
-// Recompute checkpoints every `checkpoint_every` steps bound the memory.
+// Recompute checkpoints every `checkpoint_every` steps bound the memory; the
+// segment's recompute runs the FP64 push in its recording form, so the
+// particle adjoint reads the Boris output and the corrector iterates (with
+// sin, cos of theta) instead of running the push again.
 #include "grpic_geo.cuh"
 
 #include <cstring>
@@ -80,7 +83,7 @@ template <int N>
 __device__ __forceinline__ DN<N> operator/(const DN<N> &a, const DN<N> &b)
 {
     DN<N> r;
-    double ib = 1.0 / b.v;
+    double ib = rcp_t(b.v);
     r.v = a.v * ib;
 #pragma unroll
     for (int k = 0; k < N; ++k) r.d[k] = (a.d[k] - r.v * b.d[k]) * ib;
@@ -90,7 +93,7 @@ template <int N>
 __device__ __forceinline__ DN<N> rcp_t(const DN<N> &a)
 {
     DN<N> r;
-    r.v = 1.0 / a.v;
+    r.v = rcp_t(a.v);
 #pragma unroll
     for (int k = 0; k < N; ++k) r.d[k] = -a.d[k] * r.v * r.v;
     return r;
@@ -99,8 +102,8 @@ template <int N>
 __device__ __forceinline__ DN<N> sqrt_t(const DN<N> &a)
 {
     DN<N> r;
-    r.v = sqrt(a.v);
-    double h = a.v > 0.0 ? 0.5 / r.v : 0.0;
+    r.v = sqrt_t(a.v);
+    double h = a.v > 0.0 ? 0.5 * rcp_t(r.v) : 0.0;
 #pragma unroll
     for (int k = 0; k < N; ++k) r.d[k] = a.d[k] * h;
     return r;
@@ -167,24 +170,25 @@ __device__ void rhs_jac(double a, double eps, const double y[5], double F[5], do
 // metric come out of the same evaluation).
 // ND = 2: slots d/dr, d/dtheta; ND = 3 adds d/da (the spin gradient), whose
 // contraction with the adjoint is added to *out_a
+// sv, cv: sin and cos of y[1]
 template <int ND>
-__device__ void rhs_vjp(double a, double eps, const double y[5], const double w[5], double wp, double out[5],
-                        double *out_a = nullptr)
+__device__ void rhs_vjp(double a, double eps, const double y[5], double sv, double cv, const double w[5], double wp,
+                        double out[5], double *out_a = nullptr)
 {
-    DN<ND> r(y[0]), th(y[1]), aD(a);
+    DN<ND> r(y[0]), aD(a), s(sv), c(cv);
     r.d[0] = 1.0;
-    th.d[1] = 1.0;
+    s.d[1] = cv;
+    c.d[1] = -sv;
     if constexpr (ND > 2) aD.d[2] = 1.0;
-    DN<ND> s, c;
-    sincos_t(th, &s, &c);
     KSGeo<DN<ND>> m;
     ks_geo_sc<DN<ND>>(aD, r, s, c, m);
     const double ur = y[2], ut = y[3], up = y[4];
     const double grr = m.grr.v, grp = m.grp.v, gtt = m.gtt.v, gpp = m.gpp.v, alpha = m.alpha.v;
     // forward values
     const double uu = grr * ur * ur + 2.0 * grp * ur * up + gtt * ut * ut + gpp * up * up;
-    const double au0 = sqrt(eps + uu);
-    const double iu0 = alpha / au0;
+    const double au0 = sqrt_t(eps + uu);
+    const double iau = rcp_t(au0);
+    const double iu0 = alpha * iau;
     const double h = 0.5 * iu0;
     const double Qr = ur * ur * m.dgrr_r.v + 2.0 * ur * up * m.dgrp_r.v + ut * ut * m.dgtt_r.v + up * up * m.dgpp_r.v;
     const double Qt = ur * ur * m.dgrr_t.v + 2.0 * ur * up * m.dgrp_t.v + ut * ut * m.dgtt_t.v + up * up * m.dgpp_t.v;
@@ -211,9 +215,9 @@ __device__ void rhs_vjp(double a, double eps, const double y[5], const double w[
     L_up += (Lxr * grp + Lxp * gpp) * iu0;
     L_ut += Lxt * gtt * iu0;
     // iu0 = alpha / au0, au0 = sqrt(eps + uu)
-    const double Lalpha = Liu0 / au0;
-    Lau0 -= Liu0 * alpha / (au0 * au0);
-    const double Luu = Lau0 / (2.0 * au0);
+    const double Lalpha = Liu0 * iau;
+    Lau0 -= Liu0 * alpha * iau * iau;
+    const double Luu = 0.5 * Lau0 * iau;
     Lgrr += Luu * ur * ur;
     Lgrp += Luu * 2.0 * ur * up;
     Lgtt += Luu * ut * ut;
@@ -246,59 +250,20 @@ __device__ void rhs_vjp(double a, double eps, const double y[5], const double w[
     out[4] = L_up;
 }
 
-// generalized Boris step (Eqs. boris-plus-minus, u0bar, boris-scheme) on
-// z = (r, th, u_r, u_th, u_ph, D^r, D^th, D^ph, B^r, B^th, B^ph) -> u'
-template <typename T>
-__device__ __forceinline__ void boris_z(double a, double qm, double dt, const T z[11], T out[3])
-{
-    T s, c;
-    sincos_t(z[1], &s, &c);
-    T r = z[0];
-    T a2 = T(a * a);
-    T s2 = s * s;
-    T rho2 = r * r + a2 * c * c;
-    T ir = rcp_t(rho2);
-    T zz = T(2.0) * r * ir;
-    T opz = T(1.0) + zz;
-    T alpha = sqrt_t(rcp_t(opz));
-    T Dl = r * r + a2 - T(2.0) * r;
-    T Sg = (r * r + a2) * (r * r + a2) - a2 * Dl * s2;
-    T g_rr = opz, g_tt = rho2, g_pp = Sg * s2 * ir, g_rp = -T(a) * s2 * opz;
-    T i_rr = (a2 + r * r) * ir - zz * rcp_t(opz), i_rp = T(a) * ir, i_tt = ir, i_pp = ir * rcp_t(s2);
-    T sg = rho2 * s * sqrt_t(opz);
-    T Dl0 = g_rr * z[5] + g_rp * z[7], Dl1 = g_tt * z[6], Dl2 = g_rp * z[5] + g_pp * z[7];
-    T h = T(0.5 * qm * dt) * alpha;
-    T um0 = z[2] + h * Dl0, um1 = z[3] + h * Dl1, um2 = z[4] + h * Dl2;
-    T v0 = i_rr * um0 + i_rp * um2, v1 = i_tt * um1, v2 = i_rp * um0 + i_pp * um2;
-    T u0b = sqrt_t(T(1.0) + um0 * v0 + um1 * v1 + um2 * v2) / alpha;
-    T kt = T(0.5 * qm * dt) / u0b;
-    T t0 = kt * z[8], t1 = kt * z[9], t2 = kt * z[10];
-    T tt = t0 * (g_rr * t0 + g_rp * t2) + t1 * (g_tt * t1) + t2 * (g_rp * t0 + g_pp * t2);
-    T ks = T(2.0) / (T(1.0) + tt);
-    T s0 = ks * t0, s1 = ks * t1, s2b = ks * t2;
-    T w0 = um0 + sg * (v1 * t2 - v2 * t1);
-    T w1 = um1 + sg * (v2 * t0 - v0 * t2);
-    T w2 = um2 + sg * (v0 * t1 - v1 * t0);
-    T x0 = i_rr * w0 + i_rp * w2, x1 = i_tt * w1, x2 = i_rp * w0 + i_pp * w2;
-    out[0] = um0 + sg * (x1 * s2b - x2 * s1) + h * Dl0;
-    out[1] = um1 + sg * (x2 * s0 - x0 * s2b) + h * Dl1;
-    out[2] = um2 + sg * (x0 * s1 - x1 * s0) + h * Dl2;
-}
-
-// lo^T d(u')/dz for the Boris step above, z = (r, th, u_r, u_th, u_ph, D^r,
-// D^th, D^ph, B^r, B^th, B^ph): its reverse pass written out by hand, the
-// metric's r and theta derivatives from two-slot dual numbers
+// lo^T d(u')/dz for the generalized Boris step (Eqs. boris-plus-minus, u0bar,
+// boris-scheme) u' = u'(z), z = (r, th, u_r, u_th, u_ph, D^r, D^th, D^ph, B^r,
+// B^th, B^ph): its reverse pass written out by hand, the metric's r and theta
+// derivatives from two-slot dual numbers; sn, cs = sin, cos of theta
 template <int ND>
-__device__ void boris_vjp(double a, double qm, double dt, const double z[11], const double lo[3], double out[11],
-                          double *out_a = nullptr)
+__device__ void boris_vjp(double a, double qm, double dt, const double z[11], double sn, double cs, const double lo[3],
+                          double out[11], double *out_a = nullptr)
 {
     // slots: d/dr, d/dtheta (and d/da when ND = 3)
-    DN<ND> r(z[0]), th(z[1]), aD(a);
+    DN<ND> r(z[0]), aD(a), s(sn), c(cs);
     r.d[0] = 1.0;
-    th.d[1] = 1.0;
+    s.d[1] = cs;
+    c.d[1] = -sn;
     if constexpr (ND > 2) aD.d[2] = 1.0;
-    DN<ND> s, c;
-    sincos_t(th, &s, &c);
     const DN<ND> a2 = aD * aD, s2 = s * s;
     const DN<ND> rho2 = r * r + a2 * c * c;
     const DN<ND> ir = rcp_t(rho2);
@@ -329,13 +294,16 @@ __device__ void boris_vjp(double a, double qm, double dt, const double z[11], co
     const double um[3] = {u[0] + h * Dl[0], u[1] + h * Dl[1], u[2] + h * Dl[2]};
     const double v[3] = {irr * um[0] + irp * um[2], itt * um[1], irp * um[0] + ipp * um[2]};
     const double S = 1.0 + um[0] * v[0] + um[1] * v[1] + um[2] * v[2];
-    const double rS = sqrt(S);
-    const double u0b = rS / alpha;
-    const double kt = c1 / u0b;
+    const double rS = sqrt_t(S);
+    const double ialpha = rcp_t(alpha), irS = rcp_t(rS);
+    const double u0b = rS * ialpha;
+    const double iu0b = alpha * irS;
+    const double kt = c1 * iu0b;
     const double t[3] = {kt * B[0], kt * B[1], kt * B[2]};
     const double Gt[3] = {grr * t[0] + grp * t[2], gtt * t[1], grp * t[0] + gpp * t[2]};
     const double tt = t[0] * Gt[0] + t[1] * Gt[1] + t[2] * Gt[2];
-    const double ks = 2.0 / (1.0 + tt);
+    const double i1tt = rcp_t(1.0 + tt);
+    const double ks = 2.0 * i1tt;
     const double sv[3] = {ks * t[0], ks * t[1], ks * t[2]};
     const double vt[3] = {v[1] * t[2] - v[2] * t[1], v[2] * t[0] - v[0] * t[2], v[0] * t[1] - v[1] * t[0]};
     const double w[3] = {um[0] + sg * vt[0], um[1] + sg * vt[1], um[2] + sg * vt[2]};
@@ -366,7 +334,7 @@ __device__ void boris_vjp(double a, double qm, double dt, const double z[11], co
     // s = ks t, ks = 2 / (1 + tt), tt = t^T G t
     const double Lks = Ls[0] * t[0] + Ls[1] * t[1] + Ls[2] * t[2];
     for (int i = 0; i < 3; ++i) Lt[i] += ks * Ls[i];
-    const double Ltt = -Lks * 2.0 / ((1.0 + tt) * (1.0 + tt));
+    const double Ltt = -Lks * 2.0 * i1tt * i1tt;
     for (int i = 0; i < 3; ++i) Lt[i] += 2.0 * Ltt * Gt[i];
     Lq[0] += Ltt * t[0] * t[0];
     Lq[1] += Ltt * 2.0 * t[0] * t[2];
@@ -375,9 +343,9 @@ __device__ void boris_vjp(double a, double qm, double dt, const double z[11], co
     // t = kt B, kt = c1 / u0b, u0b = sqrt(S) / alpha
     const double Lkt = Lt[0] * B[0] + Lt[1] * B[1] + Lt[2] * B[2];
     const double LB[3] = {kt * Lt[0], kt * Lt[1], kt * Lt[2]};
-    const double Lu0b = -Lkt * c1 / (u0b * u0b);
-    const double LS = Lu0b / (2.0 * rS * alpha);
-    Lq[9] -= Lu0b * rS / (alpha * alpha);
+    const double Lu0b = -Lkt * c1 * iu0b * iu0b;
+    const double LS = 0.5 * Lu0b * irS * ialpha;
+    Lq[9] -= Lu0b * rS * ialpha * ialpha;
     // S = 1 + um . v, v = Ginv um
     for (int i = 0; i < 3; ++i) {
         Lum[i] += LS * v[i];
@@ -514,7 +482,7 @@ __device__ __forceinline__ void scatter_w(double *L, int64_t ld, const St &S, do
     atomicAdd(L + (size_t)S.r1 * ld + S.c0 + 1, S.p1 * f * g * lam);
 }
 
-constexpr int MAX_ITER = 16;  // correctors the adjoint keeps iterates for
+constexpr int MAX_ITER = 16;  // correctors the adjoint accepts
 
 struct PAdjArgs {
     GridDev g;
@@ -528,6 +496,8 @@ struct PAdjArgs {
     const uint32_t *tag0;     // tags at n
     const uint32_t *tag1;     // tags at n+1
     const double *F[6];       // fields at n
+    const double *tape;       // the forward push's record of step n (layout in grpic_internal.cuh)
+    int64_t tape_ld;
     const double *lamJ[3];    // adjoint of J A
     const double *lam1[5];    // adjoint of state n+1
     double *lam0[5];          // adjoint of state n (output)
@@ -565,51 +535,15 @@ __global__ void __launch_bounds__(128) particle_adjoint(PAdjArgs A)
     if (x1a >= (double)g.nr) x1a = nextafter((double)g.nr, 0.0);  // as in the push
     if (x1a < 0.0) x1a = 0.0;
     const double dt = A.dt, eps = massive ? 1.0 : 0.0;
-
-    // forward recomputation with local derivatives
-    St S[6];
-    double E[6], dE1[6], dE2[6];
-    double up[3] = {u[0], u[1], u[2]};
-    if (charged) {
-        stencil(g, x1a, x2a, true, false, 1.0, S[0]);   // D^r
-        stencil(g, x1a, x2a, false, true, -1.0, S[1]);  // D^th (odd across the axis)
-        stencil(g, x1a, x2a, false, false, 1.0, S[2]);  // D^ph
-        stencil(g, x1a, x2a, false, true, 1.0, S[3]);   // B^r
-        stencil(g, x1a, x2a, true, false, 1.0, S[4]);   // B^th
-        stencil(g, x1a, x2a, true, true, 1.0, S[5]);    // B^ph
-        for (int c = 0; c < 6; ++c) gather_d(A.F[c], A.ld, S[c], E[c], dE1[c], dE2[c]);
-        double zv[11] = {r, th, u[0], u[1], u[2], E[0], E[1], E[2], E[3], E[4], E[5]};
-        boris_z<double>(g.a, A.qm[sp], dt, zv, up);
-    }
-    double y0[5] = {r, th, up[0], up[1], up[2]};
-    double F0[5], Fp0;
-    {
-        double f0[6];
-        rhs_y<double>(g.a, eps, y0, f0);
-        F0[0] = f0[0];
-        F0[1] = f0[1];
-        F0[2] = f0[3];
-        F0[3] = f0[4];
-        F0[4] = 0.0;
-        Fp0 = f0[2];
-    }
-    // the predictor-corrector itself (as in the push)
-    // predictor and correctors exactly as the push runs them; the iterates
-    // at which the corrector right-hand sides are evaluated are kept
-    const int N = A.n_iter;
-    double yit[MAX_ITER][5];
-    double y1[5], yt[5];
-    for (int k = 0; k < 5; ++k) yt[k] = y0[k] + dt * F0[k];
-    double dphi = dt * Fp0;
-    for (int it = 0; it < N; ++it) {
-        for (int k = 0; k < 5; ++k) yit[it][k] = yt[k];
-        double ft[6];
-        rhs_y<double>(g.a, eps, yt, ft);
-        const double Ft[5] = {ft[0], ft[1], ft[3], ft[4], 0.0};
-        for (int k = 0; k < 5; ++k) yt[k] = y0[k] + 0.5 * dt * (Ft[k] + F0[k]);
-        dphi = 0.5 * dt * (ft[2] + Fp0);
-    }
-    for (int k = 0; k < 5; ++k) y1[k] = yt[k];
+    // the forward push's record: u' after the Boris step, the corrector
+    // iterates, x^{n+1} before the reflection
+    const double *T = A.tape + p;
+    const int64_t tl = A.tape_ld;
+    const int N = A.n_iter, te = tape_end(N);
+    const double y0[5] = {r, th, T[(TAPE_U + 0) * tl], T[(TAPE_U + 1) * tl], T[(TAPE_U + 2) * tl]};
+    const double s0 = T[TAPE_SC0 * tl], c0 = T[(TAPE_SC0 + 1) * tl];
+    const double y1[5] = {T[te * tl], T[(te + 1) * tl], T[(te + 2) * tl], T[(te + 3) * tl], y0[4]};
+    const double dphi = T[(te + 4) * tl];
     double refl = 1.0;
     double th1 = y1[1];
     if (th1 < 0.0) { th1 = -th1; refl = -1.0; }
@@ -617,7 +551,9 @@ __global__ void __launch_bounds__(128) particle_adjoint(PAdjArgs A)
     double x1b = (log(y1[0]) - g.ln_rin) / g.dx1, x2b = th1 / g.dth;
     int i0 = (int)floor(x1a), j0 = jcell(g, x2a);
     int di = (int)floor(x1b) - i0, dj = jcell(g, x2b) - j0;
-    bool moved_ok = di >= -1 && di <= 1 && dj >= -1 && dj <= 1 && isfinite(x1b) && isfinite(x2b);
+    // the push's own checks: a finite end point, at most one cell away
+    bool moved_ok = di >= -1 && di <= 1 && dj >= -1 && dj <= 1 && isfinite(x1b) && isfinite(x2b) &&
+                    isfinite(y1[2]) && isfinite(y1[3]) && isfinite(dphi);
     if (!moved_ok) {
         for (int k = 0; k < 5; ++k) A.lam0[k][p] = 0.0;
         return;
@@ -630,7 +566,11 @@ __global__ void __launch_bounds__(128) particle_adjoint(PAdjArgs A)
     double ldphi = 0.0, lx1a = 0.0, lx2a = 0.0, lx1b = 0.0, lx2b = 0.0;
     double qw = A.qw[sp];
     if (qw != 0.0) {
-        // transpose of the Esirkepov window (same algebra as the push)
+        // transpose of the Esirkepov window (same algebra as the push), each
+        // current's window contracted with its adjoint one row or column at a
+        // time: J^r A_r(k+1/2, l) = cr P_r(k) (S1_t + S0_t)(l), J^th A_th
+        // likewise, J^phi dV(k, l) = cq dphi (S1_r A_t + S0_r B_t)(k, l) with
+        // A_t = S1_t / 3 + S0_t / 6, B_t = S1_t / 6 + S0_t / 3
         double S0r[4], S1r[4], S0t[4], S1t[4], dS0r[4], dS1r[4], dS0t[4], dS1t[4];
         for (int k = 0; k < 4; ++k) {
             double cr_ = i0 - 1 + k, ct = j0 - 1 + k;
@@ -639,21 +579,26 @@ __global__ void __launch_bounds__(128) particle_adjoint(PAdjArgs A)
             S0t[k] = W1(x2a - ct); dS0t[k] = dW1(x2a - ct);
             S1t[k] = W1(x2b - ct); dS1t[k] = dW1(x2b - ct);
         }
-        double cr = -qw / (2.0 * dt), cq = qw / dt, cp = cq * dphi;
+        const double cr = -qw / (2.0 * dt), cq = qw / dt, cp = cq * dphi;
+        const double c3 = 1.0 / 3.0, c6 = 1.0 / 6.0;
         double Pr = 0.0, dPr1 = 0.0, dPr0 = 0.0;
         for (int k = 0; k < 3; ++k) {
             Pr += S1r[k] - S0r[k];
             dPr1 += dS1r[k];
             dPr0 += dS0r[k];
+            double U = 0.0, V = 0.0, W = 0.0;
             for (int l = 0; l < 4; ++l) {
                 int row = j0 - 1 + l;
                 if (row < 0 || row > g.nth) continue;
                 double L = A.lamJ[0][(size_t)row * A.ld + (i0 - 1 + k + NG)];
-                lx1b += L * cr * dPr1 * (S1t[l] + S0t[l]);
-                lx1a += -L * cr * dPr0 * (S1t[l] + S0t[l]);
-                lx2b += L * cr * Pr * dS1t[l];
-                lx2a += L * cr * Pr * dS0t[l];
+                U += L * (S1t[l] + S0t[l]);
+                V += L * dS1t[l];
+                W += L * dS0t[l];
             }
+            lx1b += cr * dPr1 * U;
+            lx1a -= cr * dPr0 * U;
+            lx2b += cr * Pr * V;
+            lx2a += cr * Pr * W;
         }
         double Pt = 0.0, dPt1 = 0.0, dPt0 = 0.0;
         for (int l = 0; l < 3; ++l) {
@@ -662,26 +607,43 @@ __global__ void __launch_bounds__(128) particle_adjoint(PAdjArgs A)
             dPt0 += dS0t[l];
             int row = j0 - 1 + l;
             if (row < 0 || row > g.nth - 1) continue;
+            double U = 0.0, V = 0.0, W = 0.0;
             for (int k = 0; k < 4; ++k) {
                 double L = A.lamJ[1][(size_t)row * A.ld + (i0 - 1 + k + NG)];
-                lx1b += L * cr * dS1r[k] * Pt;
-                lx1a += L * cr * dS0r[k] * Pt;
-                lx2b += L * cr * (S1r[k] + S0r[k]) * dPt1;
-                lx2a += -L * cr * (S1r[k] + S0r[k]) * dPt0;
+                U += L * (S1r[k] + S0r[k]);
+                V += L * dS1r[k];
+                W += L * dS0r[k];
             }
+            lx1b += cr * Pt * V;
+            lx1a += cr * Pt * W;
+            lx2b += cr * dPt1 * U;
+            lx2a -= cr * dPt0 * U;
         }
-        for (int k = 0; k < 4; ++k)
+        double At[4], Bt[4], LC[4] = {0, 0, 0, 0}, LD[4] = {0, 0, 0, 0};
+        for (int l = 0; l < 4; ++l) {
+            At[l] = c3 * S1t[l] + c6 * S0t[l];
+            Bt[l] = c6 * S1t[l] + c3 * S0t[l];
+        }
+        for (int k = 0; k < 4; ++k) {
+            const double Ck = c3 * S1r[k] + c6 * S0r[k], Dk = c6 * S1r[k] + c3 * S0r[k];
+            double LA = 0.0, LB = 0.0;
             for (int l = 0; l < 4; ++l) {
                 int row = j0 - 1 + l;
                 if (row < 0 || row > g.nth) continue;
                 double L = A.lamJ[2][(size_t)row * A.ld + (i0 - 1 + k + NG)];
-                double w = S1r[k] * S1t[l] / 3.0 + S1r[k] * S0t[l] / 6.0 + S0r[k] * S1t[l] / 6.0 + S0r[k] * S0t[l] / 3.0;
-                ldphi += L * cq * w;
-                lx1b += L * cp * dS1r[k] * (S1t[l] / 3.0 + S0t[l] / 6.0);
-                lx1a += L * cp * dS0r[k] * (S1t[l] / 6.0 + S0t[l] / 3.0);
-                lx2b += L * cp * (S1r[k] / 3.0 + S0r[k] / 6.0) * dS1t[l];
-                lx2a += L * cp * (S1r[k] / 6.0 + S0r[k] / 3.0) * dS0t[l];
+                LA += L * At[l];
+                LB += L * Bt[l];
+                LC[l] += L * Ck;
+                LD[l] += L * Dk;
             }
+            ldphi += cq * (S1r[k] * LA + S0r[k] * LB);
+            lx1b += cp * dS1r[k] * LA;
+            lx1a += cp * dS0r[k] * LB;
+        }
+        for (int l = 0; l < 4; ++l) {
+            lx2b += cp * dS1t[l] * LC[l];
+            lx2a += cp * dS0t[l] * LD[l];
+        }
     }
     // end point: logical -> (r, theta) after reflection, then the reflection
     l1[0] += lx1b / (y1[0] * g.dx1);
@@ -708,10 +670,11 @@ __global__ void __launch_bounds__(128) particle_adjoint(PAdjArgs A)
         for (int k = 0; k < 5; ++k) hw[k] = hh * w[k];
         if constexpr (SPIN) {
             // the a-dependence of F(y1): w . dt/2 dF/da(y1) + dt/2 ldphi dX^ph/da(y1)
-            double unused[5];
-            rhs_vjp<ND>(g.a, eps, y1, hw, hh * ldphi, unused, pla);
+            double unused[5], s1, c1;
+            sincos(y1[1], &s1, &c1);
+            rhs_vjp<ND>(g.a, eps, y1, s1, c1, hw, hh * ldphi, unused, pla);
         }
-        rhs_vjp<ND>(g.a, eps, y0, hw, hh * ldphi, v0, pla);
+        rhs_vjp<ND>(g.a, eps, y0, s0, c0, hw, hh * ldphi, v0, pla);
         for (int k = 0; k < 5; ++k) l0[k] = w[k] + v0[k];
     } else {
         // transpose of the iteration the push runs: y~_0 = y0 + dt F(y0),
@@ -730,7 +693,9 @@ __global__ void __launch_bounds__(128) particle_adjoint(PAdjArgs A)
                 lFp0 += ap;
                 double hg[5], gn[5];
                 for (int k = 0; k < 5; ++k) hg[k] = hh * gk[k];
-                rhs_vjp<ND>(g.a, eps, yit[it], hg, ap, gn, pla);
+                const double *q = T + (int64_t)(TAPE_IT + 6 * it) * tl;
+                const double yi[5] = {q[0], q[tl], q[2 * tl], q[3 * tl], y0[4]};
+                rhs_vjp<ND>(g.a, eps, yi, q[4 * tl], q[5 * tl], hg, ap, gn, pla);
                 for (int k = 0; k < 5; ++k) gk[k] = gn[k];
             }
         }
@@ -739,7 +704,7 @@ __global__ void __launch_bounds__(128) particle_adjoint(PAdjArgs A)
             lF0[k] += dt * gk[k];
         }
         double v0[5];
-        rhs_vjp<ND>(g.a, eps, y0, lF0, lFp0, v0, pla);
+        rhs_vjp<ND>(g.a, eps, y0, s0, c0, lF0, lFp0, v0, pla);
         for (int k = 0; k < 5; ++k) l0[k] = ly0[k] + v0[k];
     }
     // start point: deposit's start-weight derivatives
@@ -749,9 +714,19 @@ __global__ void __launch_bounds__(128) particle_adjoint(PAdjArgs A)
     out[0] = l0[0];
     out[1] = l0[1];
     if (charged) {
+        // fields at x^n and their logical derivatives
+        St S[6];
+        double E[6], dE1[6], dE2[6];
+        stencil(g, x1a, x2a, true, false, 1.0, S[0]);   // D^r
+        stencil(g, x1a, x2a, false, true, -1.0, S[1]);  // D^th (odd across the axis)
+        stencil(g, x1a, x2a, false, false, 1.0, S[2]);  // D^ph
+        stencil(g, x1a, x2a, false, true, 1.0, S[3]);   // B^r
+        stencil(g, x1a, x2a, true, false, 1.0, S[4]);   // B^th
+        stencil(g, x1a, x2a, true, true, 1.0, S[5]);    // B^ph
+        for (int c = 0; c < 6; ++c) gather_d(A.F[c], A.ld, S[c], E[c], dE1[c], dE2[c]);
         double zv[11] = {r, th, u[0], u[1], u[2], E[0], E[1], E[2], E[3], E[4], E[5]};
         double lb[11];
-        boris_vjp<ND>(g.a, A.qm[sp], dt, zv, l0 + 2, lb, pla);
+        boris_vjp<ND>(g.a, A.qm[sp], dt, zv, s0, c0, l0 + 2, lb, pla);
         out[0] += lb[0];
         out[1] += lb[1];
         for (int k = 0; k < 3; ++k) out[2 + k] = lb[2 + k];
@@ -1356,7 +1331,7 @@ extern "C" grpic_status grpic_adjoint_grad(grpic_ctx *ctx, const grpic_particles
     if (!ctx || !p0 || !f0 || !L_out || ctx->prm.precision != 64 || nsteps < 1 || checkpoint_every < 1 ||
         i_horizon < 1 || i_horizon > ctx->g.nr - 1 || ctx->prm.n_field_iter < 1 || f0->ld < ctx->g.nr + 2 * NG ||
         p0->n < 0 || p0->n > INT32_MAX || (!grad_p && (grad_f || dL_da)) || ctx->prm.n_push_iter > MAX_ITER ||
-        ctx->prm.pusher != 0 || ctx->prm.shape_order != 1)
+        ctx->prm.pusher != 0 || ctx->prm.shape_order != 1 || ctx->prm.radiation != 0 || ctx->prm.injection != 0)
         return GRPIC_EINVAL;
     const bool want = grad_p != nullptr;  // NULL: the objective alone
     if (want)
@@ -1417,6 +1392,10 @@ extern "C" grpic_status grpic_adjoint_grad(grpic_ctx *ctx, const grpic_particles
         ok = ok && (lamP[k] = (double *)dalloc(np * sizeof(double)));
         ok = ok && (lamP2[k] = (double *)dalloc(np * sizeof(double)));
     }
+    // the forward push's record of every step of the current segment
+    const int TW = tape_width(ctx->prm.n_push_iter);
+    double *tape = want ? (double *)dalloc((size_t)ck * TW * (size_t)np * sizeof(double)) : nullptr;
+    ok = ok && (!want || tape);
     std::vector<double *> work(want ? 24 : 0, nullptr);
     for (auto &w : work) ok = ok && (w = (double *)dalloc(fn * sizeof(double)));
     // spin derivative: derivative tables, per-particle parts, the segment's
@@ -1504,9 +1483,12 @@ extern "C" grpic_status grpic_adjoint_grad(grpic_ctx *ctx, const grpic_particles
     FAdj A{ctx->g.nr, ctx->g.nth, ld, ctx->g.ld_tab, ctx->slab, ctx->tab, ctx->col1d};
     const double wL = 1.0 / nsteps, dth = ctx->g.dth;
     grpic_status st = GRPIC_OK;
-    auto fwd_step = [&]() -> grpic_status {
+    // one forward step; with a tape slice, the push also records itself there
+    auto fwd_step = [&](double *tp) -> grpic_status {
         for (int k = 0; k < 3; ++k) cudaMemsetAsync(Jw[k], 0, fn * sizeof(double), s);
-        if (launch_push64(ctx, &PW, &PW, nullptr, nullptr, nullptr, &FW, false, s) != cudaSuccess) return GRPIC_ECUDA;
+        cudaError_t e = tp ? launch_push64_tape(ctx, &PW, &FW, tp, np, s)
+                           : launch_push64(ctx, &PW, &PW, nullptr, nullptr, nullptr, &FW, false, s);
+        if (e != cudaSuccess) return GRPIC_ECUDA;
         grpic_status r = GRPIC_OK;
         if (launch_field64(ctx, &FW, s) != cudaSuccess) r = GRPIC_ECUDA;
         return r;
@@ -1518,7 +1500,7 @@ extern "C" grpic_status grpic_adjoint_grad(grpic_ctx *ctx, const grpic_particles
     }
     for (int n = 0; n < nsteps && st == GRPIC_OK; ++n) {
         if (want && n % ck == 0) copy_state(cks[n / ck], W);
-        st = fwd_step();
+        st = fwd_step(nullptr);
         flux_kernel<<<1, 256, 0, s>>>(A, dWf, i_horizon, dth, wL, Ldev);
         if (spin)  // the objective's own tables at F^{n+1}
             flux_da<<<(ctx->g.nth + 255) / 256, 256, 0, s>>>(A, dtab, dWf, i_horizon, dth, wL, Ladev);
@@ -1570,7 +1552,7 @@ extern "C" grpic_status grpic_adjoint_grad(grpic_ctx *ctx, const grpic_particles
         copy_state(W, cks[sgi]);
         copy_state(seg[0], W);
         for (int m = 0; m < len && st == GRPIC_OK; ++m) {
-            st = fwd_step();
+            st = fwd_step(tape + (size_t)m * TW * (size_t)np);
             copy_state(seg[m + 1], W);
             if (spin)
                 for (int k = 0; k < 3; ++k)
@@ -1611,6 +1593,8 @@ extern "C" grpic_status grpic_adjoint_grad(grpic_ctx *ctx, const grpic_particles
                 P.lam1[k] = lamP[k];
                 P.lam0[k] = lamP2[k];
             }
+            P.tape = tape + (size_t)m * TW * (size_t)np;
+            P.tape_ld = np;
             P.tag0 = seg[m].tag;
             P.tag1 = seg[m + 1].tag;
             for (int k = 0; k < 6; ++k) {

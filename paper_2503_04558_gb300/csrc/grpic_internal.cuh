@@ -164,6 +164,19 @@ __host__ __device__ inline double r_of(const GridDev &g, double x1) { return g.r
 
 __device__ inline void set_status(int *st, int code) { atomicCAS(st, 0, code); }
 
+// Record of one FP64 push kept for the adjoint (structure of arrays: entry k
+// of particle p at tape[k * tape_ld + p]):
+//   TAPE_U + 0..2    u' after the Boris step (u itself for an uncharged particle)
+//   TAPE_SC0 + 0..1  sin, cos of theta^n
+//   TAPE_IT + 6 it   the point of corrector `it`'s right-hand side (it < n_iter):
+//                    r, theta, u_r, u_theta, sin theta, cos theta
+//   tape_end(n)      x^{n+1} before the axis reflection: r, theta, u_r, u_theta,
+//                    then delta phi
+// Written for every particle the push moved or refused after the geodesic step.
+constexpr int TAPE_U = 0, TAPE_SC0 = 3, TAPE_IT = 5;
+__host__ __device__ constexpr int tape_end(int n_iter) { return TAPE_IT + 6 * n_iter; }
+__host__ __device__ constexpr int tape_width(int n_iter) { return tape_end(n_iter) + 5; }
+
 }  // namespace grpic
 
 // entry points implemented in the kernel translation units (host side)
@@ -177,6 +190,10 @@ cudaError_t launch_init_fields(grpic_ctx *ctx, int kind, double B0, const grpic_
 // direction for the next neighbour sort
 cudaError_t launch_push64(grpic_ctx *ctx, const grpic_particles *in, grpic_particles *p, const int32_t *perm,
                           const int32_t *live, int32_t *cnt9, grpic_fields *f, bool histogram, cudaStream_t s);
+// the FP64 push in place, writing the adjoint's record of every particle
+// (layout above, tape_ld >= p->n)
+cudaError_t launch_push64_tape(grpic_ctx *ctx, grpic_particles *p, grpic_fields *f, double *tape, int64_t tape_ld,
+                               cudaStream_t s);
 cudaError_t launch_push32(grpic_ctx *ctx, const grpic_particles *in, grpic_particles *p, const int32_t *perm,
                           const int32_t *live, int32_t *cnt9, grpic_fields *f, bool histogram, cudaStream_t s);
 cudaError_t launch_deposit(grpic_ctx *ctx, const grpic_particles *b, const grpic_particles *a, const void *dphi,

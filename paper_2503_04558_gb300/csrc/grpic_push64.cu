@@ -61,6 +61,8 @@ struct Push64Args {
     int64_t step;
     int32_t *spawn;
     int *status;
+    double *tape;  // the adjoint's record of the push (TAPE instantiation only)
+    int64_t tape_ld;
 };
 
 struct Rhs {
@@ -69,11 +71,9 @@ struct Rhs {
 
 // Right-hand sides of Eq. particle-eom without F_i, with the analytic
 // Kerr-Schild derivatives of alpha, beta^r and gamma^{jk}.
-__device__ __forceinline__ void geo_rhs(double a, double eps, double r, double th, double ur, double ut, double up,
-                                        Rhs &f)
+__device__ __forceinline__ void geo_rhs_sc(double a, double eps, double r, double s, double c, double ur, double ut,
+                                           double up, Rhs &f)
 {
-    double s, c;
-    sincos(th, &s, &c);
     double a2 = a * a, r2 = r * r;
     double rho2 = r2 + a2 * c * c;
     double ir = 1.0 / rho2;
@@ -107,6 +107,13 @@ __device__ __forceinline__ void geo_rhs(double a, double eps, double r, double t
     double h = 0.5 * iu0;
     f.ur = -au0 * da_r + ur * db_r - h * (ur * ur * dgrr_r + 2.0 * ur * up * dgrp_r + ut * ut * dgtt_r + up * up * dgpp_r);
     f.ut = -au0 * da_t + ur * db_t - h * (ur * ur * dgrr_t + 2.0 * ur * up * dgrp_t + ut * ut * dgtt_t + up * up * dgpp_t);
+}
+__device__ __forceinline__ void geo_rhs(double a, double eps, double r, double th, double ur, double ut, double up,
+                                        Rhs &f)
+{
+    double s, c;
+    sincos(th, &s, &c);
+    geo_rhs_sc(a, eps, r, s, c, ur, ut, up, f);
 }
 
 // Generalized Boris step over dt at the particle (u covariant, D, B contravariant)
@@ -208,8 +215,9 @@ __device__ __forceinline__ int jcell(const GridDev &g, double x2)
 
 // SHAPE 1: cloud in cell (bilinear interpolation, 4 x 4 window reduced across
 // the warp); SHAPE 3: the cubic spline of grpic_shape3.cuh (4 x 4 taps,
-// per-lane deposit of the 5 x 5 window)
-template <int SHAPE, bool RAD>
+// per-lane deposit of the 5 x 5 window).  TAPE: also write the adjoint's
+// record of the push (CIC, no radiation)
+template <int SHAPE, bool RAD, bool TAPE>
 __global__ void __launch_bounds__(256) push64_kernel(Push64Args A)
 {
     const GridDev &g = A.g;
@@ -285,18 +293,52 @@ __global__ void __launch_bounds__(256) push64_kernel(Push64Args A)
         // geodesic predictor-corrector (Sec. 2.2)
         double eps = A.massive[sp] ? 1.0 : 0.0;
         Rhs f0, ft;
-        geo_rhs(g.a, eps, r, th, u[0], u[1], u[2], f0);
+        double *tape = TAPE ? A.tape + p : nullptr;
+        const int64_t tl = A.tape_ld;
+        if constexpr (TAPE) {
+            double s0, c0;
+            sincos(th, &s0, &c0);
+            tape[(TAPE_U + 0) * tl] = u[0];
+            tape[(TAPE_U + 1) * tl] = u[1];
+            tape[(TAPE_U + 2) * tl] = u[2];
+            tape[TAPE_SC0 * tl] = s0;
+            tape[(TAPE_SC0 + 1) * tl] = c0;
+            geo_rhs_sc(g.a, eps, r, s0, c0, u[0], u[1], u[2], f0);
+        } else {
+            geo_rhs(g.a, eps, r, th, u[0], u[1], u[2], f0);
+        }
         double dt = A.dt;
         double rt = r + dt * f0.xr, tt = th + dt * f0.xt, pt = dt * f0.xp;
         double urt = u[0] + dt * f0.ur, utt = u[1] + dt * f0.ut;
         for (int it = 0; it < A.n_iter; ++it) {
-            geo_rhs(g.a, eps, rt, tt, urt, utt, u[2], ft);
+            if constexpr (TAPE) {
+                double st, ct;
+                sincos(tt, &st, &ct);
+                double *q = tape + (int64_t)(TAPE_IT + 6 * it) * tl;
+                q[0] = rt;
+                q[tl] = tt;
+                q[2 * tl] = urt;
+                q[3 * tl] = utt;
+                q[4 * tl] = st;
+                q[5 * tl] = ct;
+                geo_rhs_sc(g.a, eps, rt, st, ct, urt, utt, u[2], ft);
+            } else {
+                geo_rhs(g.a, eps, rt, tt, urt, utt, u[2], ft);
+            }
             double h = 0.5 * dt;
             rt = r + h * (ft.xr + f0.xr);
             tt = th + h * (ft.xt + f0.xt);
             pt = h * (ft.xp + f0.xp);
             urt = u[0] + h * (ft.ur + f0.ur);
             utt = u[1] + h * (ft.ut + f0.ut);
+        }
+        if constexpr (TAPE) {
+            double *q = tape + (int64_t)tape_end(A.n_iter) * tl;
+            q[0] = rt;
+            q[tl] = tt;
+            q[2 * tl] = urt;
+            q[3 * tl] = utt;
+            q[4 * tl] = pt;
         }
         // axis reflection
         if (tt < 0.0) { tt = -tt; utt = -utt; }
@@ -411,8 +453,8 @@ __global__ void __launch_bounds__(256) push64_kernel(Push64Args A)
 
 }  // namespace
 
-cudaError_t launch_push64(grpic_ctx *ctx, const grpic_particles *in, grpic_particles *p, const int32_t *perm,
-                          const int32_t *live, int32_t *cnt9, grpic_fields *f, bool histogram, cudaStream_t s)
+static Push64Args push64_args(grpic_ctx *ctx, const grpic_particles *in, grpic_particles *p, const int32_t *perm,
+                              const int32_t *live, int32_t *cnt9, grpic_fields *f, bool histogram)
 {
     Push64Args A;
     A.g = ctx->g;
@@ -463,20 +505,42 @@ cudaError_t launch_push64(grpic_ctx *ctx, const grpic_particles *in, grpic_parti
     A.step = ctx->step_count;
     A.spawn = ctx->prm.radiation ? ctx->d_spawn : nullptr;
     A.status = ctx->d_status;
+    A.tape = nullptr;
+    A.tape_ld = 0;
+    return A;
+}
+
+cudaError_t launch_push64(grpic_ctx *ctx, const grpic_particles *in, grpic_particles *p, const int32_t *perm,
+                          const int32_t *live, int32_t *cnt9, grpic_fields *f, bool histogram, cudaStream_t s)
+{
+    Push64Args A = push64_args(ctx, in, p, perm, live, cnt9, f, histogram);
     if (p->n <= 0) return cudaSuccess;
     int64_t blocks = (p->n + 255) / 256;
     const bool rad = ctx->prm.radiation != 0;
     if (ctx->prm.shape_order == 3) {
         if (rad)
-            push64_kernel<3, true><<<(unsigned)blocks, 256, 0, s>>>(A);
+            push64_kernel<3, true, false><<<(unsigned)blocks, 256, 0, s>>>(A);
         else
-            push64_kernel<3, false><<<(unsigned)blocks, 256, 0, s>>>(A);
+            push64_kernel<3, false, false><<<(unsigned)blocks, 256, 0, s>>>(A);
     } else {
         if (rad)
-            push64_kernel<1, true><<<(unsigned)blocks, 256, 0, s>>>(A);
+            push64_kernel<1, true, false><<<(unsigned)blocks, 256, 0, s>>>(A);
         else
-            push64_kernel<1, false><<<(unsigned)blocks, 256, 0, s>>>(A);
+            push64_kernel<1, false, false><<<(unsigned)blocks, 256, 0, s>>>(A);
     }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_push64_tape(grpic_ctx *ctx, grpic_particles *p, grpic_fields *f, double *tape, int64_t tape_ld,
+                               cudaStream_t s)
+{
+    if (ctx->prm.shape_order != 1 || ctx->prm.radiation || ctx->prm.pusher != 0 || tape_ld < p->n)
+        return cudaErrorInvalidValue;
+    Push64Args A = push64_args(ctx, p, p, nullptr, nullptr, nullptr, f, false);
+    A.tape = tape;
+    A.tape_ld = tape_ld;
+    if (p->n <= 0) return cudaSuccess;
+    push64_kernel<1, false, true><<<(unsigned)((p->n + 255) / 256), 256, 0, s>>>(A);
     return cudaGetLastError();
 }
 
