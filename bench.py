@@ -52,14 +52,21 @@ B0 = 1.0
 # Arithmetic per particle-step of the push kernels, counted by ncu on the same
 # kernels (flop_count = 2 FMA + MUL + ADD of the SASS instruction counters;
 # the capture commands and counts are in profiles/).
-PUSH64_FP64_FLOP = 1528.0   # profiles/push64_fp64_512x512_64ppc.md
-PUSH64_DRAM_B = 95.9        # the same capture: DRAM bytes per particle (read + write)
+PUSH64_FP64_FLOP = 1342.0   # profiles/push64_fp64_512x512_64ppc.md
+PUSH64_DRAM_B = 95.8        # the same capture: DRAM bytes per particle (read + write)
 PUSH32_FP32_FLOP = 1136.0   # profiles/push32_fp32form_1024x1024_64ppc.md
 # the same capture: instructions issued per particle (warp instructions x 32)
 # and DRAM bytes per particle (read + write), scaled to a launch by the
 # number of particles
 PUSH32_INST = 1942.0
 PUSH32_DRAM_B = 70.0
+# batched 1D lines, b1_kernel (profiles/b1_kernel_256lines_4096cells.md):
+# instructions issued per particle-step (warp instructions x 32) and DRAM
+# bytes per particle-step; algorithmic bytes: the particle record (cell, offset,
+# u_r, u_phi, tag as 4 B each, id 8 B) read and written once per step
+B1_INST = None
+B1_DRAM_B = None
+B1_ALG_B = 2 * 28
 # ALU peaks from unit counts x clock: 152 SMs x 2.07 GHz x (4 FP64 flops,
 # 256 FP32 flops) per SM per clock; instruction issue: 4 schedulers x 1 warp
 # instruction per SM per clock
@@ -411,9 +418,10 @@ def batch1d_inputs(nl, n, seed=2024):
     return theta, lines
 
 
-def batch1d_measure(steps, warmup):
+def batch1d_measure(steps, warmup, n_lines=None, capacity=None):
     """Tuned persistent run of the 512 lines; returns the figures and the
-    oracle's throughput on a bounded sample (the 8 smallest lines, 3 steps)."""
+    oracle's throughput on a bounded sample (the 8 smallest lines, 3 steps).
+    n_lines / capacity shrink the workload for profiling runs."""
     import numpy as np
     import torch
     from paper_2503_04558_gb300 import build, grpic as G
@@ -421,11 +429,13 @@ def batch1d_measure(steps, warmup):
     build.build()
     G.load()
     rh = horizon(B1_A)
-    cfg = G.Batch1DConfig(B1_LINES, B1_CELLS, B1_A, rh, B1_ROUT, B1_CAP, gamma_thr=100.0, eps_ph=4.0, tau=2.0,
+    n_lines = n_lines or B1_LINES
+    capacity = capacity or B1_CAP
+    cfg = G.Batch1DConfig(n_lines, B1_CELLS, B1_A, rh, B1_ROUT, capacity, gamma_thr=100.0, eps_ph=4.0, tau=2.0,
                           B0=2.0e3, seed=7)
     B = G.Batch1D(cfg)
     L = G.Lines(cfg)
-    theta, lines = batch1d_inputs(B1_LINES, B1_CELLS)
+    theta, lines = batch1d_inputs(n_lines, B1_CELLS)
     L.theta.copy_(torch.from_numpy(theta))
     omega_h = B1_A / (2.0 * rh)
     L.I0.copy_(torch.from_numpy(omega_h * cfg.B0 * np.sin(theta) ** 2))
@@ -458,7 +468,7 @@ def batch1d_measure(steps, warmup):
     st = B.sync()
     ev1 = L.events.cpu().numpy()
     pushes = int(ev1[2] - ev0[2])
-    cells = B1_LINES * B1_CELLS * steps
+    cells = n_lines * B1_CELLS * steps
     import oracle as O
     t = time.perf_counter()
     oracle_pushes = 0
@@ -475,10 +485,22 @@ def batch1d_measure(steps, warmup):
             oracle_pushes += S.n
             O.line_step(Lo, s, S, D)
     osec = time.perf_counter() - t
-    out = {"value": pushes / (ms * 1e-3), "unit": "particle-steps/s", "steps": steps, "warmup": warmup + done,
+    rate = pushes / (ms * 1e-3)
+    pk, pk_kind = peaks()
+    # the timed region is one launch of the persistent kernel running every step
+    roof = {"kernel": "b1_kernel (one persistent launch for all timed steps)", "bound": "issue",
+            "achieved": rate * B1_INST / 32 / 1e9 if B1_INST else None, "peak": ISSUE_PEAK_GWARP,
+            "unit": "G warp-instructions/s", "frac": rate * B1_INST / 32 / 1e9 / ISSUE_PEAK_GWARP if B1_INST else None,
+            "traffic": pushes * B1_DRAM_B if B1_DRAM_B else None, "inst_per_particle": B1_INST,
+            "peak_source": "152 SMs x 4 schedulers x 2.07 GHz",
+            "hbm": {"bound": "hbm", "achieved": rate * B1_ALG_B / 1e9, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                    "frac": rate * B1_ALG_B / 1e9 / pk["hbm_gbs"], "bytes_per_particle": B1_ALG_B,
+                    "peak_source": f"{pk_kind} hbm_gbs (MEASURED_PEAKS)"}}
+    out = {"value": rate, "unit": "particle-steps/s", "steps": steps, "warmup": warmup + done, "roofline": roof,
            "ms_per_step": ms / steps, "dtype": "f32",
-           "workload": "512 radial lines x 4096 cells, a=0.99, r in [r_H, 20], monopole B0=2e3, gamma_thr=100, "
-                       "eps_ph=4, tau=2, initial 10^U(3,5) particles per line, capacity 1e6 per line",
+           "workload": "%d radial lines x 4096 cells, a=0.99, r in [r_H, 20], monopole B0=2e3, gamma_thr=100, "
+                       "eps_ph=4, tau=2, initial 10^U(3,5) particles per line, capacity %.0e per line"
+                       % (n_lines, capacity),
            "initial_particles": n0, "particles_now": int(L.count.sum().item()), "tuned_launch": list(best),
            "cell_updates_per_s": cells / (ms * 1e-3),
            "events": {"emitted": int(ev1[0] - ev0[0]), "converted": int(ev1[1] - ev0[1])},
@@ -492,7 +514,7 @@ def batch1d_measure(steps, warmup):
 
 
 def run_batch1d(args):
-    m = batch1d_measure(args.steps, args.warmup)
+    m = batch1d_measure(args.steps, args.warmup, args.b1_lines, args.b1_capacity)
     line = {"metric": "batched 1D spark gaps: particle push+deposit/s (one persistent launch)",
             "value": m["value"], "unit": m["unit"], "n_gpus": 1, "steps": args.steps, "warmup": m["warmup"],
             "ms_per_step": m["ms_per_step"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -500,7 +522,7 @@ def run_batch1d(args):
             "config": {"workload": m["workload"], "initial_particles": m["initial_particles"],
                        "particles_now": m["particles_now"], "tuned_launch": m["tuned_launch"], "l2": m["l2"]},
             "cell_updates_per_s": m["cell_updates_per_s"], "events": m["events"], "status": m["status"],
-            "clocks": m["clocks"], "gpu_launches": 2, "cpu_baseline": m["cpu_baseline"]}
+            "roofline": m["roofline"], "clocks": m["clocks"], "gpu_launches": 2, "cpu_baseline": m["cpu_baseline"]}
     print(json.dumps(line), flush=True)
 
 
@@ -715,6 +737,8 @@ def main():
     ap.add_argument("--workload", default="grpic2d", choices=["grpic2d", "batch1d", "adjoint"])
     ap.add_argument("--adj-particles", type=int, default=None, help="adjoint workload size (profiling runs)")
     ap.add_argument("--adj-steps", type=int, default=None, help="adjoint steps (profiling runs)")
+    ap.add_argument("--b1-lines", type=int, default=None, help="batch1d lines (profiling runs)")
+    ap.add_argument("--b1-capacity", type=int, default=None, help="batch1d capacity per line (profiling runs)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -21,6 +21,7 @@
 //   6. cell key of x^{n+1} (dead -> n_cells) and a warp-aggregated histogram
 //      for the sort.
 #include "grpic_internal.cuh"
+#include "grpic_geo.cuh"
 #include "grpic_window.cuh"
 #include "grpic_vay.cuh"
 #include "grpic_shape3.cuh"
@@ -76,13 +77,13 @@ __device__ __forceinline__ void geo_rhs_sc(double a, double eps, double r, doubl
 {
     double a2 = a * a, r2 = r * r;
     double rho2 = r2 + a2 * c * c;
-    double ir = 1.0 / rho2;
+    double ir = rcp_t(rho2);
     double ir2 = ir * ir;
     double z = 2.0 * r * ir;
-    double iopz = 1.0 / (1.0 + z);
+    double iopz = rcp_t(1.0 + z);
     double alpha = sqrt(iopz);
     double beta = z * iopz;
-    double is2 = 1.0 / (s * s);
+    double is2 = rcp_t(s * s);
     double grr = (a2 + r2) * ir - beta, grp = a * ir, gtt = ir, gpp = ir * is2;
     double drho_t = -2.0 * a2 * c * s;
     double dz_r = 2.0 * ir * (1.0 - 2.0 * r2 * ir);
@@ -100,7 +101,7 @@ __device__ __forceinline__ void geo_rhs_sc(double a, double eps, double r, doubl
 
     double uu = grr * ur * ur + 2.0 * grp * ur * up + gtt * ut * ut + gpp * up * up;
     double au0 = sqrt(eps + uu);   // alpha u^0
-    double iu0 = alpha / au0;      // 1 / u^0
+    double iu0 = alpha * rcp_t(au0);  // 1 / u^0
     f.xr = (grr * ur + grp * up) * iu0 - beta;
     f.xt = gtt * ut * iu0;
     f.xp = (grp * ur + gpp * up) * iu0;
@@ -108,20 +109,39 @@ __device__ __forceinline__ void geo_rhs_sc(double a, double eps, double r, doubl
     f.ur = -au0 * da_r + ur * db_r - h * (ur * ur * dgrr_r + 2.0 * ur * up * dgrp_r + ut * ut * dgtt_r + up * up * dgpp_r);
     f.ut = -au0 * da_t + ur * db_t - h * (ur * ur * dgrr_t + 2.0 * ur * up * dgrp_t + ut * ut * dgtt_t + up * up * dgpp_t);
 }
-__device__ __forceinline__ void geo_rhs(double a, double eps, double r, double th, double ur, double ut, double up,
-                                        Rhs &f)
+
+// the 3+1 metric at (r, theta) from sin, cos of theta (reciprocals by the
+// FP32 seed and two Newton steps of rcp_t)
+__device__ __forceinline__ void ks_point_sc(double a, double r, double s, double c, KS &m)
 {
-    double s, c;
-    sincos(th, &s, &c);
-    geo_rhs_sc(a, eps, r, s, c, ur, ut, up, f);
+    double s2 = s * s, a2 = a * a;
+    double rho2 = r * r + a2 * c * c;
+    double irho2 = rcp_t(rho2);
+    double z = 2.0 * r * irho2;
+    double opz = 1.0 + z;
+    double iopz = rcp_t(opz);
+    double Dl = r * r + a2 - 2.0 * r;
+    double Sg = (r * r + a2) * (r * r + a2) - a2 * Dl * s2;
+    m.alpha = sqrt(iopz);
+    m.beta = z * iopz;
+    m.g_rr = opz;
+    m.g_tt = rho2;
+    m.g_pp = Sg * s2 * irho2;
+    m.g_rp = -a * s2 * opz;
+    m.gi_rr = (a2 + r * r) * irho2 - m.beta;
+    m.gi_rp = a * irho2;
+    m.gi_tt = irho2;
+    m.gi_pp = irho2 * rcp_t(s2);
+    m.sqrtg = rho2 * s * sqrt(opz);
 }
 
-// Generalized Boris step over dt at the particle (u covariant, D, B contravariant)
-__device__ __forceinline__ void boris(double a, double r, double th, double qm, double dt, const double D[3],
+// Generalized Boris step over dt at the particle (u covariant, D, B
+// contravariant); s, c = sin, cos of theta
+__device__ __forceinline__ void boris(double a, double r, double s, double c, double qm, double dt, const double D[3],
                                       const double B[3], double u[3])
 {
     KS m;
-    ks_point(a, r, th, m);
+    ks_point_sc(a, r, s, c, m);
     double Dl0 = m.g_rr * D[0] + m.g_rp * D[2];
     double Dl1 = m.g_tt * D[1];
     double Dl2 = m.g_rp * D[0] + m.g_pp * D[2];
@@ -129,11 +149,11 @@ __device__ __forceinline__ void boris(double a, double r, double th, double qm, 
     double um0 = u[0] + h * Dl0, um1 = u[1] + h * Dl1, um2 = u[2] + h * Dl2;
     // raised u^-
     double v0 = m.gi_rr * um0 + m.gi_rp * um2, v1 = m.gi_tt * um1, v2 = m.gi_rp * um0 + m.gi_pp * um2;
-    double u0b = sqrt(1.0 + um0 * v0 + um1 * v1 + um2 * v2) / m.alpha;
-    double kt = 0.5 * qm * dt / u0b;
+    double iu0b = m.alpha * rcp_t(sqrt(1.0 + um0 * v0 + um1 * v1 + um2 * v2));  // 1 / u0bar
+    double kt = 0.5 * qm * dt * iu0b;
     double t0 = kt * B[0], t1 = kt * B[1], t2 = kt * B[2];
     double tt = t0 * (m.g_rr * t0 + m.g_rp * t2) + t1 * (m.g_tt * t1) + t2 * (m.g_rp * t0 + m.g_pp * t2);
-    double ks = 2.0 / (1.0 + tt);
+    double ks = 2.0 * rcp_t(1.0 + tt);
     double s0 = ks * t0, s1 = ks * t1, s2 = ks * t2;
     double sg = m.sqrtg;
     // u~ = u^- + e_ijk v^j t^k
@@ -267,6 +287,10 @@ __global__ void __launch_bounds__(256) push64_kernel(Push64Args A)
         double x1a = (log(r) - g.ln_rin) / g.dx1, x2a = th / g.dth;
         if (x1a >= (double)g.nr) x1a = nextafter((double)g.nr, 0.0);  // rounding just below r_out
         if (x1a < 0.0) x1a = 0.0;
+        // sin, cos of theta^n: shared by the Boris step and the first
+        // right-hand side, shifted for the corrector iterates
+        double s0, c0;
+        sincos(th, &s0, &c0);
         if (A.massive[sp] && A.qm[sp] != 0.0) {
             double Dv[3], Bv[3];
             if constexpr (SHAPE == 3) {
@@ -288,7 +312,7 @@ __global__ void __launch_bounds__(256) push64_kernel(Push64Args A)
             if (A.pusher)
                 vay(g.a, r, th, A.qm[sp], A.dt, Dv, Bv, u);
             else
-                boris(g.a, r, th, A.qm[sp], A.dt, Dv, Bv, u);
+                boris(g.a, r, s0, c0, A.qm[sp], A.dt, Dv, Bv, u);
         }
         // geodesic predictor-corrector (Sec. 2.2)
         double eps = A.massive[sp] ? 1.0 : 0.0;
@@ -296,24 +320,27 @@ __global__ void __launch_bounds__(256) push64_kernel(Push64Args A)
         double *tape = TAPE ? A.tape + p : nullptr;
         const int64_t tl = A.tape_ld;
         if constexpr (TAPE) {
-            double s0, c0;
-            sincos(th, &s0, &c0);
             tape[(TAPE_U + 0) * tl] = u[0];
             tape[(TAPE_U + 1) * tl] = u[1];
             tape[(TAPE_U + 2) * tl] = u[2];
             tape[TAPE_SC0 * tl] = s0;
             tape[(TAPE_SC0 + 1) * tl] = c0;
-            geo_rhs_sc(g.a, eps, r, s0, c0, u[0], u[1], u[2], f0);
-        } else {
-            geo_rhs(g.a, eps, r, th, u[0], u[1], u[2], f0);
         }
+        geo_rhs_sc(g.a, eps, r, s0, c0, u[0], u[1], u[2], f0);
         double dt = A.dt;
         double rt = r + dt * f0.xr, tt = th + dt * f0.xt, pt = dt * f0.xp;
         double urt = u[0] + dt * f0.ur, utt = u[1] + dt * f0.ut;
         for (int it = 0; it < A.n_iter; ++it) {
-            if constexpr (TAPE) {
-                double st, ct;
+            // theta of the iterate within 0.05 of theta^n (the usual case: one
+            // step moves a particle less than two cells): the series of
+            // sincos_shift, truncated below 1e-17
+            double st, ct;
+            const double dth = tt - th;
+            if (fabs(dth) <= 0.05)
+                sincos_shift<double>(s0, c0, dth, st, ct);
+            else
                 sincos(tt, &st, &ct);
+            if constexpr (TAPE) {
                 double *q = tape + (int64_t)(TAPE_IT + 6 * it) * tl;
                 q[0] = rt;
                 q[tl] = tt;
@@ -321,10 +348,8 @@ __global__ void __launch_bounds__(256) push64_kernel(Push64Args A)
                 q[3 * tl] = utt;
                 q[4 * tl] = st;
                 q[5 * tl] = ct;
-                geo_rhs_sc(g.a, eps, rt, st, ct, urt, utt, u[2], ft);
-            } else {
-                geo_rhs(g.a, eps, rt, tt, urt, utt, u[2], ft);
             }
+            geo_rhs_sc(g.a, eps, rt, st, ct, urt, utt, u[2], ft);
             double h = 0.5 * dt;
             rt = r + h * (ft.xr + f0.xr);
             tt = th + h * (ft.xt + f0.xt);
