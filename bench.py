@@ -64,9 +64,16 @@ PUSH32_DRAM_B = 70.0
 # instructions issued per particle-step (warp instructions x 32) and DRAM
 # bytes per particle-step; algorithmic bytes: the particle record (cell, offset,
 # u_r, u_phi, tag as 4 B each, id 8 B) read and written once per step
-B1_INST = None
-B1_DRAM_B = None
+B1_INST = 977.0
+B1_DRAM_B = 50.9
 B1_ALG_B = 2 * 28
+# the widened rows' push kernels, counted the same way (profiles/ summaries
+# named for each): the FP32 push with Vay's update, the FP64 push with the
+# cubic shape, the FP64 push with photon emission and conversion decisions
+VAY32_FP32_FLOP = 1158.0    # profiles/push32_vay_1024x1024_64ppc.md
+VAY32_INST = 1925.0
+CUBIC64_FP64_FLOP = 1978.0  # profiles/push64_cubic_512x512_64ppc.md
+RAD64_FP64_FLOP = 1685.0    # profiles/push64_rad_512x512_16ppc.md
 # ALU peaks from unit counts x clock: 152 SMs x 2.07 GHz x (4 FP64 flops,
 # 256 FP32 flops) per SM per clock; instruction issue: 4 schedulers x 1 warp
 # instruction per SM per clock
@@ -645,10 +652,11 @@ def pairs_2d_measure(n=1024, ppc=16, steps=3):
     torch.cuda.synchronize()
     ctx.set_timing(True)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
-    ctx.step(S, F, steps)
-    e1.record()
-    torch.cuda.synchronize()
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        e0.record()
+        ctx.step(S, F, steps)
+        e1.record()
+        torch.cuda.synchronize()
     tp, tf, ts, tn = ctx.get_timing()
     ctx.set_timing(False)
     st = st or ctx.sync()
@@ -658,10 +666,81 @@ def pairs_2d_measure(n=1024, ppc=16, steps=3):
            "particles_start": live0, "particles_end": live1, "steps": steps, "warmup": 1, "ms_per_step": ms,
            "value": 0.5 * (live0 + live1) / (ms * 1e-3), "unit": "particle-steps/s",
            "phases": {"push_and_appends_ms": tp / tn, "field_and_injection_ms": tf / tn, "sort_ms": ts / tn},
+           "roofline": alu_roofline("push+deposit with emission/conversion decisions (FP64), with the appends",
+                                    0.5 * (live0 + live1), tp / tn, RAD64_FP64_FLOP, 64, None,
+                                    "profiles/push64_rad_512x512_16ppc.md"),
+           "clocks": clk.summary(),
            "status": ["OK", "EINVAL", "ENOMEM", "ECUDA", "ERANGE", "ENAN", "EOVERFLOW"][st] if st < 7 else st}
     del S, F, ctx
     torch.cuda.empty_cache()
     return out
+
+
+def alu_roofline(kernel, n_units, kernel_ms, flop_per_unit, prec, inst_per_unit=None, source=""):
+    """Roofline of an ALU-bound push kernel from its ncu-counted flop (and
+    instruction) count per particle and its duration measured in the timed
+    region; null figures where the count has not been taken."""
+    peak = FP32_PEAK_TFLOPS if prec == 32 else FP64_PEAK_TFLOPS
+    ach = n_units * flop_per_unit / (kernel_ms * 1e-3) / 1e12 if flop_per_unit else None
+    roof = {"kernel": kernel, "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+            "frac": ach / peak if ach is not None else None, "traffic": None,
+            "peak_source": "152 SMs x 2.07 GHz x %d %s flop/clk/SM (recipe unit counts and clock)"
+                           % ((256, "FP32") if prec == 32 else (4, "FP64")),
+            "flop_per_particle": flop_per_unit, "count_source": source}
+    if inst_per_unit:
+        iss = n_units * inst_per_unit / 32 / (kernel_ms * 1e-3) / 1e9
+        roof["issue"] = {"achieved": iss, "peak": ISSUE_PEAK_GWARP, "unit": "G warp-instructions/s",
+                         "frac": iss / ISSUE_PEAK_GWARP, "inst_per_particle": inst_per_unit,
+                         "peak_source": "152 SMs x 4 schedulers x 2.07 GHz"}
+    return roof
+
+
+def vay_measure(args, rank=0, world=1):
+    """The FP32 form step with Vay's update in the FIDO frame instead of the
+    generalized Boris step, same workload and timed region as the headline."""
+    rv = run_grpic(args, 32, rank, world, 0, pusher=1)
+    rv["total_ms"] = max_over_ranks(rv["total_ms"], world)
+    tp = rv["timed_phases"]
+    return {"what": "FP32 form step with Vay's update in the FIDO frame instead of the generalized Boris step",
+            "value": job_value(rv["n"], args.steps, world, rv["total_ms"]), "unit": UNIT,
+            "ms_per_step": rv["total_ms"] / args.steps, "steps": args.steps,
+            "phases": {"timed_region": tp}, "particle_statuses": rv["statuses"],
+            "roofline": alu_roofline("push+deposit, Vay (FP32 form)", rv["n"], tp["push_ms"], VAY32_FP32_FLOP, 32,
+                                     VAY32_INST, "profiles/push32_vay_1024x1024_64ppc.md"),
+            "clocks": rv["clocks"]}
+
+
+def cubic_measure(args, rank=0, world=1):
+    """The FP64 step with the third-order (cubic B-spline) shape, same
+    workload, a short run (2 timed steps)."""
+    short = argparse.Namespace(**vars(args))
+    short.steps, short.warmup = 2, 1
+    rc = run_grpic(short, 64, rank, world, 0, shape_order=3)
+    rc["total_ms"] = max_over_ranks(rc["total_ms"], world)
+    tp = rc["timed_phases"]
+    return {"what": "FP64 step with the third-order (cubic B-spline) shape for interpolation and deposit",
+            "steps": 2, "warmup": 1, "value": job_value(rc["n"], 2, world, rc["total_ms"]), "unit": UNIT,
+            "ms_per_step": rc["total_ms"] / 2, "phases": {"timed_region": tp},
+            "particle_statuses": rc["statuses"],
+            "roofline": alu_roofline("push+deposit, cubic shape (FP64)", rc["n"], tp["push_ms"], CUBIC64_FP64_FLOP,
+                                     64, None, "profiles/push64_cubic_512x512_64ppc.md"),
+            "clocks": rc["clocks"]}
+
+
+def run_extra(args, name):
+    """One of the widened rows alone, as its own JSON line."""
+    if name == "vay":
+        m = vay_measure(args)
+    elif name == "cubic":
+        m = cubic_measure(args)
+    else:
+        m = pairs_2d_measure(args.grid or 1024, args.ppc or 16, max(1, args.steps))
+    line = {"metric": m["what"] + ": particle-steps/s", "value": m["value"], "unit": m["unit"], "n_gpus": 1,
+            "steps": m["steps"], "warmup": m.get("warmup", args.warmup), "ms_per_step": m["ms_per_step"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32" if name == "vay" else "f64", "data": "synthetic"}
+    line.update({k: v for k, v in m.items() if k not in line})
+    print(json.dumps(line), flush=True)
 
 
 def grpic_summary(res, args, world, esz_prec):
@@ -732,9 +811,11 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the adjoint and batch1d sub-measurements")
-    ap.add_argument("--grid", type=int, default=NR, help="cells per dimension (profiling runs use smaller grids)")
-    ap.add_argument("--ppc", type=int, default=PPC, help="particles per cell")
-    ap.add_argument("--workload", default="grpic2d", choices=["grpic2d", "batch1d", "adjoint"])
+    ap.add_argument("--grid", type=int, default=None,
+                    help="cells per dimension (default 2048; 1024 for pairs2d; profiling runs use smaller grids)")
+    ap.add_argument("--ppc", type=int, default=None, help="particles per cell (default 100; 16 for pairs2d)")
+    ap.add_argument("--workload", default="grpic2d",
+                    choices=["grpic2d", "batch1d", "adjoint", "vay", "cubic", "pairs2d"])
     ap.add_argument("--adj-particles", type=int, default=None, help="adjoint workload size (profiling runs)")
     ap.add_argument("--adj-steps", type=int, default=None, help="adjoint steps (profiling runs)")
     ap.add_argument("--b1-lines", type=int, default=None, help="batch1d lines (profiling runs)")
@@ -748,6 +829,14 @@ def main():
         return
     if args.workload == "adjoint":
         run_adjoint(args)
+        return
+    if args.workload == "pairs2d":
+        run_extra(args, "pairs2d")
+        return
+    args.grid = args.grid or NR
+    args.ppc = args.ppc or PPC
+    if args.workload in ("vay", "cubic"):
+        run_extra(args, args.workload)
         return
     import torch
     world = int(os.environ.get("WORLD_SIZE", 1))
@@ -763,37 +852,13 @@ def main():
         second["total_ms"] = max_over_ranks(second["total_ms"], world)
     extras = {}
     if not args.no_extras and head_prec == 32:
-        # the alternative momentum update (Vay in the FIDO frame) on the same
-        # workload, same timed region
-        try:
-            rv = run_grpic(args, 32, rank, world, 0, pusher=1)
-            rv["total_ms"] = max_over_ranks(rv["total_ms"], world)
-            extras["vay"] = {"what": "FP32 form step with Vay's update in the FIDO frame instead of the "
-                                     "generalized Boris step", "value": job_value(rv["n"], args.steps, world,
-                                                                                   rv["total_ms"]),
-                             "unit": UNIT, "ms_per_step": rv["total_ms"] / args.steps,
-                             "phases": {"timed_region": rv["timed_phases"]}, "particle_statuses": rv["statuses"],
-                             "clocks": rv["clocks"].get("sm_mhz") if isinstance(rv["clocks"], dict) else None}
-        except Exception as e:  # reported, not hidden: the headline stands on its own
-            extras["vay"] = {"error": f"{type(e).__name__}: {e}"}
-        # the third-order (cubic) shape, FP64 path, same workload, a short run
-        try:
-            short = argparse.Namespace(**vars(args))
-            short.steps, short.warmup = 2, 1
-            rc = run_grpic(short, 64, rank, world, 0, shape_order=3)
-            rc["total_ms"] = max_over_ranks(rc["total_ms"], world)
-            extras["cubic_shape"] = {"what": "FP64 step with the third-order (cubic B-spline) shape for "
-                                             "interpolation and deposit", "steps": 2, "warmup": 1,
-                                     "value": job_value(rc["n"], 2, world, rc["total_ms"]), "unit": UNIT,
-                                     "ms_per_step": rc["total_ms"] / 2,
-                                     "phases": {"timed_region": rc["timed_phases"]},
-                                     "particle_statuses": rc["statuses"]}
-        except Exception as e:
-            extras["cubic_shape"] = {"error": f"{type(e).__name__}: {e}"}
-        try:
-            extras["pairs_2d"] = pairs_2d_measure()
-        except Exception as e:
-            extras["pairs_2d"] = {"error": f"{type(e).__name__}: {e}"}
+        for name, fn in (("vay", lambda: vay_measure(args, rank, world)),
+                         ("cubic_shape", lambda: cubic_measure(args, rank, world)),
+                         ("pairs_2d", lambda: pairs_2d_measure())):
+            try:
+                extras[name] = fn()
+            except Exception as e:  # reported, not hidden: the headline stands on its own
+                extras[name] = {"error": f"{type(e).__name__}: {e}"}
     if not args.no_extras:
         for name, fn in (("adjoint", lambda: adjoint_measure(2)), ("batch1d", lambda: batch1d_measure(200, 600))):
             try:

@@ -111,7 +111,7 @@ struct Kid {
     uint64_t id;
 };
 
-__global__ void b1_kernel(B1Args A)
+__global__ void __launch_bounds__(1024) b1_kernel(B1Args A)
 {
     extern __shared__ float smem[];
     const int n = A.n;

@@ -127,14 +127,18 @@ __device__ __forceinline__ void deposit3(int nr, int nth, int64_t ld, double *J0
 #pragma unroll
         for (int k = 0; k < 5; ++k) fold_add3(J1, ld, nr, nth, b1 + k, b2 + l, true, -1.0, cr * (S1r[k] + S0r[k]) * Pt);
     }
+    // J^phi dV weights S1r S1t / 3 + S1r S0t / 6 + S0r S1t / 6 + S0r S0t / 3,
+    // factored per row: S1r A_t + S0r B_t
+    double At[5], Bt[5];
+#pragma unroll
+    for (int l = 0; l < 5; ++l) {
+        At[l] = cp * (S1t[l] * (1.0 / 3.0) + S0t[l] * (1.0 / 6.0));
+        Bt[l] = cp * (S1t[l] * (1.0 / 6.0) + S0t[l] * (1.0 / 3.0));
+    }
 #pragma unroll
     for (int k = 0; k < 5; ++k)
 #pragma unroll
-        for (int l = 0; l < 5; ++l) {
-            const double w = S1r[k] * S1t[l] * (1.0 / 3.0) + S1r[k] * S0t[l] * (1.0 / 6.0) +
-                             S0r[k] * S1t[l] * (1.0 / 6.0) + S0r[k] * S0t[l] * (1.0 / 3.0);
-            fold_add3(J2, ld, nr, nth, b1 + k, b2 + l, false, 1.0, cp * w);
-        }
+        for (int l = 0; l < 5; ++l) fold_add3(J2, ld, nr, nth, b1 + k, b2 + l, false, 1.0, S1r[k] * At[l] + S0r[k] * Bt[l]);
 }
 
 }  // namespace grpic
