@@ -54,12 +54,12 @@ B0 = 1.0
 # the capture commands and counts are in profiles/).
 PUSH64_FP64_FLOP = 1342.0   # profiles/push64_fp64_512x512_64ppc.md
 PUSH64_DRAM_B = 95.8        # the same capture: DRAM bytes per particle (read + write)
-PUSH32_FP32_FLOP = 1136.0   # profiles/push32_fp32form_1024x1024_64ppc.md
+PUSH32_FP32_FLOP = 1058.0   # profiles/push32_fp32form_1024x1024_64ppc.md
 # the same capture: instructions issued per particle (warp instructions x 32)
 # and DRAM bytes per particle (read + write), scaled to a launch by the
 # number of particles
-PUSH32_INST = 1942.0
-PUSH32_DRAM_B = 70.0
+PUSH32_INST = 1780.0
+PUSH32_DRAM_B = 69.3
 # batched 1D lines, b1_kernel (profiles/b1_kernel_256lines_4096cells.md):
 # instructions issued per particle-step (warp instructions x 32) and DRAM
 # bytes per particle-step; algorithmic bytes: the particle record (cell, offset,
@@ -364,7 +364,7 @@ def oracle_sample(steps, n_side=128):
             "steps": steps, "grid": f"{n_side}x{n_side}"}
 
 
-def cpu_baseline_block(steps=2, n_side=256):
+def cpu_baseline_block(steps=3, n_side=256):
     s = oracle_sample(steps, n_side)
     return {"value": s["value"], "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"{s['grid']} sub-grid of the 2048x2048 workload, {PPC} ppc ({s['particles']} particles), "
@@ -399,6 +399,7 @@ def run_reference(args):
 # batched 1D spark gaps (separate workload: --workload batch1d)
 # ---------------------------------------------------------------------------
 B1_LINES, B1_CELLS, B1_A, B1_ROUT, B1_CAP = 512, 4096, 0.99, 20.0, 1_000_000
+B1_ORACLE_LINES, B1_ORACLE_STEPS = 32, 80   # the oracle's bounded sample (a few seconds)
 
 
 def batch1d_inputs(nl, n, seed=2024):
@@ -427,7 +428,7 @@ def batch1d_inputs(nl, n, seed=2024):
 
 def batch1d_measure(steps, warmup, n_lines=None, capacity=None):
     """Tuned persistent run of the 512 lines; returns the figures and the
-    oracle's throughput on a bounded sample (the 8 smallest lines, 3 steps).
+    oracle's throughput on a bounded sample (the smallest lines, a few seconds).
     n_lines / capacity shrink the workload for profiling runs."""
     import numpy as np
     import torch
@@ -479,7 +480,7 @@ def batch1d_measure(steps, warmup, n_lines=None, capacity=None):
     import oracle as O
     t = time.perf_counter()
     oracle_pushes = 0
-    order = np.argsort([len(ln[0]) for ln in lines])[:8]
+    order = np.argsort([len(ln[0]) for ln in lines])[:B1_ORACLE_LINES]
     for k in order:
         Lo = O.make_line(B1_CELLS, B1_A, theta[k], rh, B1_ROUT, dt=cfg.dt, qw=cfg.q_weight, qm=cfg.q_over_m,
                          I0=omega_h * cfg.B0 * math.sin(theta[k]) ** 2, gamma_thr=100.0, eps_ph=4.0, tau=2.0,
@@ -488,7 +489,7 @@ def batch1d_measure(steps, warmup, n_lines=None, capacity=None):
         S = O.LineState(cell + off.astype(np.float64), ur.astype(np.float64), up.astype(np.float64), tag, pid,
                         4 * len(cell) + 1000)
         D = O.line_init_D(Lo, cfg.B0)
-        for s in range(3):
+        for s in range(B1_ORACLE_STEPS):
             oracle_pushes += S.n
             O.line_step(Lo, s, S, D)
     osec = time.perf_counter() - t
@@ -514,7 +515,8 @@ def batch1d_measure(steps, warmup, n_lines=None, capacity=None):
            "status": int(st), "clocks": clk.summary(), "gpu_launches": 2,
            "l2": "inputs larger than L2 (particle state %.0f MB)" % (n0 * 24 / 1e6),
            "cpu_baseline": {"value": oracle_pushes / osec, "unit": "particle-steps/s", "cores": 1,
-                            "kind": "oracle", "sample": f"8 smallest lines, 3 steps, FP64, {osec:.1f} s"}}
+                            "kind": "oracle", "sample": f"{B1_ORACLE_LINES} smallest lines, {B1_ORACLE_STEPS} steps, FP64, "
+                                                  f"{osec:.1f} s"}}
     del B, L
     torch.cuda.empty_cache()
     return out

@@ -119,7 +119,7 @@ __global__ void __launch_bounds__(1024) b1_kernel(B1Args A)
     float *sA = sD + n;
     float *sJ = sA + n;                      // n + 2 faces (-1..n)
     int *wsum = (int *)(sJ + n + 2);         // 33 ints
-    int *sv = wsum + 34;                     // [0] line, [1] wptr, [2] sptr, [3] emit, [4] conv, [5] flags
+    int *sv = wsum + 34;                     // [0] line, [3] emitted, [4] converted, [5] pushed
     const int tid = threadIdx.x, B = blockDim.x;
 
     for (;;) {
@@ -147,13 +147,14 @@ __global__ void __launch_bounds__(1024) b1_kernel(B1Args A)
             const int src = (A.cur + st) & 1, dst = src ^ 1;
             for (int i = tid; i < n + 2; i += B) sJ[i] = 0.0f;
             if (tid == 0) {
-                sv[1] = 0;
-                sv[2] = 0;
                 sv[3] = 0;
                 sv[4] = 0;
                 sv[5] = cnt;
             }
             __syncthreads();
+            // running write offsets of the survivors and of the children: every
+            // thread advances its own copy by the block totals of each chunk
+            int wp = 0, sp0 = 0;
             for (int cb = 0; cb < cnt; cb += B) {
                 const int idx = cb + tid;
                 bool alive = false;
@@ -286,7 +287,6 @@ __global__ void __launch_bounds__(1024) b1_kernel(B1Args A)
                 // placement: survivors in order, children in parent order
                 int excl;
                 int tot = block_scan((alive ? 1 : 0) | (napp << 16), wsum, excl);
-                int wp = sv[1], sp0 = sv[2];
                 if (alive) {
                     size_t d = base + wp + (excl & 0xffff);
                     A.cell[dst][d] = ci;
@@ -310,15 +310,12 @@ __global__ void __launch_bounds__(1024) b1_kernel(B1Args A)
                 }
                 if (napp == 1) atomicAdd(&sv[3], 1);
                 if (napp == 2) atomicAdd(&sv[4], 1);
-                __syncthreads();
-                if (tid == 0) {
-                    sv[1] = wp + (tot & 0xffff);
-                    sv[2] = sp0 + (tot >> 16);
-                }
-                __syncthreads();
+                wp += tot & 0xffff;
+                sp0 += tot >> 16;
             }
+            __syncthreads();  // the staging writes, the J atomics and the counters are complete
             // children after the survivors
-            const int wptr = sv[1], sptr = sv[2];
+            const int wptr = wp, sptr = sp0;
             int nap = min(sptr, (int)A.Cs);
             int room = (int)(A.C - wptr);
             int ncopy = min(nap, room);

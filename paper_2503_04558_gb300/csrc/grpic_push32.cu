@@ -38,7 +38,7 @@ struct Push32Args {
     int i64;  // first column whose inner edge is at or beyond fp64_radius
     int island_fp64;   // 1: native FP64 island, 0: double-FP32 pairs
     int use_tol;       // convergence test of the correctors
-    float af, dthf, idthf, dx1f;  // a, dtheta, 1/dtheta, dx1 in FP32
+    float af, dthf, idthf, dx1f, idx1f;  // a, dtheta, 1/dtheta, dx1, 1/dx1 in FP32
     df a_df, dth_df;              // a, dtheta as float pairs
     const float *rcol2;  // r_i as (hi, lo) float pairs, index i + NG
     const float *rowsc;  // sin, cos theta_j as float pairs, index j
@@ -113,11 +113,12 @@ __device__ __forceinline__ void boris32(const KSPoint<M> &mm, float qm, float dt
     float h = 0.5f * qm * alpha * dt;
     float um0 = u[0] + h * Dl0, um1 = u[1] + h * Dl1, um2 = u[2] + h * Dl2;
     float v0 = irr * um0 + irp * um2, v1 = itt * um1, v2 = irp * um0 + ipp * um2;
-    float u0b = sqrtf(1.0f + um0 * v0 + um1 * v1 + um2 * v2) / alpha;
-    float kt = 0.5f * qm * dt / u0b;
+    // 1 / u0bar = alpha / sqrt(1 + u^- . v) (hardware reciprocal square root and
+    // reciprocal: a few ulp, within the FP32 form's budget)
+    float kt = 0.5f * qm * dt * alpha * rsqrtf(1.0f + um0 * v0 + um1 * v1 + um2 * v2);
     float t0 = kt * B[0], t1 = kt * B[1], t2 = kt * B[2];
     float tt = t0 * (grr * t0 + grp * t2) + t1 * (gtt * t1) + t2 * (grp * t0 + gpp * t2);
-    float ks = 2.0f / (1.0f + tt);
+    float ks = __fdividef(2.0f, 1.0f + tt);
     float s0 = ks * t0, s1 = ks * t1, s2 = ks * t2;
     float w0 = um0 + sg * (v1 * t2 - v2 * t1);
     float w1 = um1 + sg * (v2 * t0 - v0 * t2);
@@ -126,6 +127,24 @@ __device__ __forceinline__ void boris32(const KSPoint<M> &mm, float qm, float dt
     u[0] = um0 + sg * (x1 * s2 - x2 * s1) + h * Dl0;
     u[1] = um1 + sg * (x2 * s0 - x0 * s2) + h * Dl1;
     u[2] = um2 + sg * (x0 * s1 - x1 * s0) + h * Dl2;
+}
+
+// exp(x) - 1 for x = o1 dx1 in [0, dx1]: Taylor polynomial to x^6 when the
+// cells are narrow (dx1 <= 0.1: truncation below x^7 / 7! = 2e-11, under
+// FP32 rounding), the library function otherwise
+__device__ __forceinline__ float expm1_cell(float x, float dx1)
+{
+    if (dx1 > 0.1f) return expm1f(x);
+    return x * (1.0f + x * (0.5f + x * (1.0f / 6.0f + x * (1.0f / 24.0f + x * (1.0f / 120.0f + x * (1.0f / 720.0f))))));
+}
+
+// log(1 + y) for the relative move y of r against the cell's inner edge:
+// alternating Taylor polynomial to y^8 for |y| <= 0.05 (truncation below
+// y^9 / 9 = 2e-13), the library function otherwise
+__device__ __forceinline__ float log1p_cell(float y)
+{
+    if (fabsf(y) > 0.05f) return log1pf(y);
+    return y * (1.0f - y * (0.5f - y * (1.0f / 3.0f - y * (0.25f - y * (0.2f - y * (1.0f / 6.0f - y * (1.0f / 7.0f - y * 0.125f)))))));
 }
 
 struct St32 {
@@ -193,7 +212,7 @@ __device__ __forceinline__ void boris_geo(const KSGeo<M> &m, M a, M r, M s, floa
     mm.gi_rp = (float)m.grp;
     mm.gi_tt = (float)m.gtt;
     mm.gi_pp = (float)m.gpp;
-    mm.sqrtg = (float)(m.rho2 * s / m.alpha);
+    mm.sqrtg = (float)(m.rho2 * s * m.opz * m.alpha);  // rho^2 sin sqrt(1+z), sqrt(1+z) = (1+z) alpha
     if (pusher) {
         const VayMetric<float> vm{mm.alpha, mm.g_rr, mm.g_rp, mm.g_tt, mm.g_pp, mm.gi_rr, mm.gi_rp, mm.gi_tt,
                                   mm.gi_pp, mm.sqrtg};
@@ -211,7 +230,7 @@ __device__ __forceinline__ void push_one(const Push32Args &A, int i, int j, floa
     const GridDev &g = A.g;
     const float2 rc2 = __ldg(reinterpret_cast<const float2 *>(A.rcol2) + i + NG);
     const float rcf = IS_D ? (float)A.rcol[i + NG] : __fadd_rn(rc2.x, rc2.y);
-    const float d0 = rcf * expm1f(o1 * A.dx1f);  // r - r_i
+    const float d0 = rcf * expm1_cell(o1 * A.dx1f, A.dx1f);  // r - r_i
     // metric at x^n, shared by the Boris step and the first right-hand side
     M am, r0, s0, c0;
     if constexpr (IS_D) {
@@ -309,7 +328,7 @@ __device__ __forceinline__ void push_one(const Push32Args &A, int i, int j, floa
         b2 = nb2;
         if (done) break;
     }
-    o1 = log1pf(a1 / rcf) / A.dx1f;  // back to the logical offset
+    o1 = log1p_cell(__fdividef(a1, rcf)) * A.idx1f;  // back to the logical offset
     o2 = a2;
     u[0] = b1;
     u[1] = b2;
@@ -473,6 +492,7 @@ cudaError_t launch_push32(grpic_ctx *ctx, const grpic_particles *in, grpic_parti
     A.dthf = (float)ctx->g.dth;
     A.idthf = (float)(1.0 / ctx->g.dth);
     A.dx1f = (float)ctx->g.dx1;
+    A.idx1f = (float)(1.0 / ctx->g.dx1);
     A.a_df = df_const(ctx->g.a);
     A.dth_df = df_const(ctx->g.dth);
     A.rcol2 = ctx->rcol2;

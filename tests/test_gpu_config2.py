@@ -1,0 +1,196 @@
+"""Config 2 at full size, the workload the bench times: 2048 x 2048, a = 0.99,
+r in [0.9 r_H, 100], split monopole B0 = 1, 100 particles per cell (4.19e8
+e+/e-), Maxwell-Juettner momenta at T = 0.3, FP64 plain and the FP32 form
+with the bench's settings (double-FP32 metric inside 1.5 r_H, corrector
+tolerance 1e-6).
+
+  * FP64, one push: 20 000 sampled particles against the oracle's push of the
+    same particles in the oracle's own initial fields (computed on the host
+    in a spawned process while the GPU runs), bar 1e-10 per component;
+  * the sort at full size, by properties that hold at any size: after a
+    separate-call step the cell keys are non-decreasing and each cell keeps
+    its particles in loading order (the loading index rides in tag bits
+    2..30); after a two-step `grpic_step` call (deferred sort, neighbour
+    path) the keys are non-decreasing and the surviving indices are distinct;
+  * charge: the running FP64 continuity check over the three steps, below
+    1e-12 of max|rho|;
+  * FP32 form: the sample's momenta after one push against the oracle (bar
+    2e-5) and the fields after three steps against the FP64 path (bar 1e-4).
+
+As in config 3, the particles that start within 0.01 rad of the polar axis
+are marked dead in both paths (there the push is ill-conditioned: J^phi ~
+u_phi / sin^2 theta of a grazing path dominates any field comparison
+between two precisions).  Both paths at once hold ~80 GB of device memory."""
+import math
+import multiprocessing as mp
+
+import numpy as np
+import pytest
+
+import oracle as O
+from gpu_common import configs, relerr
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+A = 0.99
+RH = 1.0 + math.sqrt(1 - A * A)
+RIN = 0.9 * RH
+ROUT = 100.0
+N = 2048
+PPC = 100
+NSUB = 20000
+THETA_C = 0.01
+IDX_SHIFT = 2          # loading index in tag bits 2..30 (species in 0..1, DEAD in 31)
+
+
+def _oracle_fields(nr, nth, a, rin, rout):
+    """Runs in a spawned process: the oracle's initial split-monopole fields."""
+    c = O.make_cfg(nr, nth, a, rin, rout)
+    return O.init_fields(c, O.SPLIT_MONOPOLE, 1.0)
+
+
+def _cells64(cfg, r, th):
+    x1 = ((torch.log(r) - math.log(cfg.r_in)) / cfg.dx1).floor().clamp(0, cfg.n_r - 1)
+    x2 = (th / cfg.dth).floor().clamp(0, cfg.n_theta - 1)
+    return (x2 * cfg.n_r + x1).to(torch.int64)
+
+
+def _sorted_and_stable(keys, idx):
+    """keys non-decreasing; within equal keys, idx increasing."""
+    ok_keys = bool((keys[1:] >= keys[:-1]).all())
+    same = keys[1:] == keys[:-1]
+    ok_stable = bool((idx[1:][same] > idx[:-1][same]).all())
+    return ok_keys, ok_stable
+
+
+@pytest.fixture(scope="module")
+def runs():
+    pool = mp.get_context("spawn").Pool(1)
+    fut = pool.apply_async(_oracle_fields, (N, N, A, RIN, ROUT))
+    from paper_2503_04558_gb300 import build, grpic as G, synth
+    build.build()
+    G.load()
+    free, _ = torch.cuda.mem_get_info()
+    if free < 120e9:
+        pool.terminate()
+        pytest.skip(f"needs ~80 GB of free device memory ({free / 1e9:.0f} GB free)")
+    oc, g64 = configs(N, N, A, RIN, ROUT)
+    g32 = G.Config(N, N, A, RIN, ROUT, dt=oc.dt, damp_cells=oc.damp_cells, damp_max=oc.damp_max,
+                   q_over_m=tuple(oc.qm), q_weight=tuple(oc.qw), massive=tuple(oc.massive), precision=32,
+                   sort_every=1, fp64_radius=1.5 * RH, push_tol=1e-6)
+    n = N * N * PPC
+    gen = synth.particles_torch(N, N, RIN, ROUT, n, seed=1234, thermal_T=0.3, device="cuda")
+    near_axis = torch.minimum(gen["th"], math.pi - gen["th"]) < THETA_C
+    idx = torch.arange(n, device="cuda", dtype=torch.int64)
+    t = gen["tag"].to(torch.int64) | (idx << IDX_SHIFT) | (near_axis.to(torch.int64) << 31)
+    gen["tag"] = torch.where(t >= 2**31, t - 2**32, t).to(torch.int32)
+    del t, idx
+    live = torch.nonzero(~near_axis).squeeze(1)
+    rng = np.random.default_rng(11)
+    sub = np.sort(live[torch.from_numpy(rng.choice(live.numel(), NSUB, replace=False)).cuda()].cpu().numpy())
+    del live, near_axis
+    subt = torch.from_numpy(sub).cuda()
+    P0 = O.Particles(*[gen[k][subt].cpu().numpy() for k in ("r", "th", "u1", "u2", "u3")],
+                     gen["tag"][subt].cpu().numpy().view(np.uint32))
+    out = {}
+    # FP32 state first (from the same draw), then the FP64 one
+    S32 = G.ParticleSet(g32, n)
+    x1 = (torch.log(gen["r"]) - math.log(RIN)) / g32.dx1
+    x2 = gen["th"] / g32.dth
+    i = torch.floor(x1).clamp(0, N - 1)
+    j = torch.floor(x2).clamp(0, N - 1)
+    S32.load((x1 - i).float(), (x2 - j).float(), gen["u1"].float(), gen["u2"].float(), gen["u3"].float(),
+             gen["tag"], (j * N + i).to(torch.int32))
+    del x1, x2, i, j
+    S64 = G.ParticleSet(g64, n)
+    S64.load(gen["r"], gen["th"], gen["u1"], gen["u2"], gen["u3"], gen["tag"])
+    del gen
+    torch.cuda.empty_cache()
+    for name, g, S in (("fp64", g64, S64), ("fp32", g32, S32)):
+        ctx = G.Context(g)
+        F = G.Fields(g)
+        ctx.init_fields(F, G.SPLIT_MONOPOLE, 1.0)
+        res = {}
+        if name == "fp64":
+            _, _, state0 = ctx.charge_check(S, F, want_state=True)
+        ctx.push(S, F)                      # one push, slots unchanged: the sample is comparable
+        assert ctx.sync() == 0
+        res["u"] = [t[subt].double().cpu().numpy() for t in (S.a.u1, S.a.u2, S.a.u3)]
+        if name == "fp64":
+            res["x"] = [t[subt].cpu().numpy() for t in (S.a.x1, S.a.x2)]
+            res["tag"] = S.a.tag[subt].cpu().numpy().view(np.uint32)
+        ctx.field_update(F)
+        ctx.sort(S)
+        assert ctx.sync() == 0
+        if name == "fp64":
+            m = S.live()                    # the sort drops the dead: live slots first
+            keys = _cells64(g, S.a.x1[:m], S.a.x2[:m])
+            lidx = (S.a.tag[:m].to(torch.int64) & 0x7FFFFFFF) >> IDX_SHIFT
+            res["sort1"] = _sorted_and_stable(keys, lidx)
+            res["n1"] = m
+        ctx.step(S, F, 2)
+        st = ctx.sync()
+        assert st in (0, 4, 5), st          # single-particle statuses are reported, the step goes on
+        if name == "fp64":
+            m = S.live()                    # the sort drops the dead: live slots first
+            keys = _cells64(g, S.a.x1[:m], S.a.x2[:m])
+            lidx = (S.a.tag[:m].to(torch.int64) & 0x7FFFFFFF) >> IDX_SHIFT
+            res["sort2_keys"] = bool((keys[1:] >= keys[:-1]).all())
+            res["sort2_distinct"] = int(torch.unique(lidx).numel()) == m
+            res["n2"] = m
+            res["charge"] = ctx.charge_check(S, F, base=state0)[:2]
+        res["F"] = [t.double().cpu().numpy() for t in F.D + F.B]
+        out[name] = res
+        del ctx, F
+    del S64, S32
+    torch.cuda.empty_cache()
+    D, B = fut.get(timeout=1800)
+    pool.close()
+    P = P0.copy()
+    st, _, _ = O.push_deposit(oc, P, D, B)
+    return dict(out=out, P=P, P0=P0, st=st, n=n)
+
+
+def test_config2_fp64_push_matches_oracle_on_a_sample(runs):
+    out, P = runs["out"]["fp64"], runs["P"]
+    alive = ((runs["P"].tag & 0x80000000) == 0) & ((out["tag"] & 0x80000000) == 0)
+    assert alive.sum() > 0.99 * NSUB
+    errs = [relerr(out["x"][0][alive], P.r[alive]), relerr(out["x"][1][alive], P.th[alive])]
+    errs += [relerr(out["u"][k][alive], ref[alive]) for k, ref in enumerate((P.u1, P.u2, P.u3))]
+    print("config 2, FP64: one-push error of 20 000 sampled particles vs the oracle (r, th, u_r, u_th, u_ph):",
+          " ".join(f"{e:.1e}" for e in errs))
+    assert max(errs) < 1e-10, errs
+
+
+def test_config2_sort_at_full_size(runs):
+    out = runs["out"]["fp64"]
+    ok_keys, ok_stable = out["sort1"]
+    assert ok_keys and ok_stable
+    assert out["sort2_keys"] and out["sort2_distinct"]
+    assert out["n2"] <= out["n1"] <= runs["n"]
+    print(f"config 2: live after 1 and 3 steps: {out['n1']}, {out['n2']} of {runs['n']}")
+
+
+def test_config2_fp64_charge_conservation(runs):
+    res, rmax = runs["out"]["fp64"]["charge"]
+    print(f"config 2, FP64: continuity residual over 3 steps {res / rmax:.2e} of max|rho|")
+    assert res / rmax < 1e-12
+
+
+def test_config2_fp32_momentum_error_against_the_oracle(runs):
+    P0, P = runs["P0"], runs["P"]
+    u = runs["out"]["fp32"]["u"]
+    alive = (P.tag & 0x80000000) == 0
+    errs = [relerr(u[k][alive], ref[alive]) for k, ref in enumerate((P.u1, P.u2, P.u3))]
+    print("config 2, FP32 form: one-push momentum error vs the oracle (u_r, u_th, u_ph):",
+          " ".join(f"{e:.1e}" for e in errs))
+    assert max(errs) < 2e-5, errs
+
+
+def test_config2_fp32_field_error_against_fp64(runs):
+    f32, f64 = runs["out"]["fp32"]["F"], runs["out"]["fp64"]["F"]
+    errs = [relerr(a, b) for a, b in zip(f32, f64)]
+    print("config 2, FP32 form: field error after 3 steps vs FP64 (D^r, D^th, D^ph, B^r, B^th, B^ph):",
+          " ".join(f"{e:.1e}" for e in errs))
+    assert max(errs) < 1e-4, errs
