@@ -64,8 +64,8 @@ PUSH32_DRAM_B = 69.3
 # instructions issued per particle-step (warp instructions x 32) and DRAM
 # bytes per particle-step; algorithmic bytes: the particle record (cell, offset,
 # u_r, u_phi, tag as 4 B each, id 8 B) read and written once per step
-B1_INST = 977.0
-B1_DRAM_B = 50.9
+B1_INST = 998.0
+B1_DRAM_B = 50.7
 B1_ALG_B = 2 * 28
 # the widened rows' push kernels, counted the same way (profiles/ summaries
 # named for each): the FP32 push with Vay's update, the FP64 push with the
@@ -426,10 +426,11 @@ def batch1d_inputs(nl, n, seed=2024):
     return theta, lines
 
 
-def batch1d_measure(steps, warmup, n_lines=None, capacity=None):
+def batch1d_measure(steps, warmup, n_lines=None, capacity=None, shape=None):
     """Tuned persistent run of the 512 lines; returns the figures and the
     oracle's throughput on a bounded sample (the smallest lines, a few seconds).
-    n_lines / capacity shrink the workload for profiling runs."""
+    n_lines / capacity shrink the workload for profiling runs; shape fixes the
+    launch shape (threads, CTAs per SM, CTAs per line) instead of tuning."""
     import numpy as np
     import torch
     from paper_2503_04558_gb300 import build, grpic as G
@@ -453,10 +454,17 @@ def batch1d_measure(steps, warmup, n_lines=None, capacity=None):
     n0 = int(L.count.sum().item())
     stream = torch.cuda.current_stream()
     step = 0
-    done, best = B.tune(L, 2, step)         # the tuner's trial steps are real steps
-    step += done
+    if shape:
+        B.set_launch(*shape)
+    # warm up first (the cascade starts), then tune in that state: the best
+    # launch shape depends on how the particles are spread over the lines
     B.run(L, warmup, step)
     step += warmup
+    if shape:
+        done, best = 0, tuple(shape)
+    else:
+        done, best = B.tune(L, 4, step)     # the tuner's trial steps are real steps
+    step += done
     st = B.sync()
     if st != 0:
         raise RuntimeError(f"device status {st}")
@@ -523,7 +531,8 @@ def batch1d_measure(steps, warmup, n_lines=None, capacity=None):
 
 
 def run_batch1d(args):
-    m = batch1d_measure(args.steps, args.warmup, args.b1_lines, args.b1_capacity)
+    shape = tuple(int(v) for v in args.b1_shape.split(",")) if args.b1_shape else None
+    m = batch1d_measure(args.steps, args.warmup, args.b1_lines, args.b1_capacity, shape)
     line = {"metric": "batched 1D spark gaps: particle push+deposit/s (one persistent launch)",
             "value": m["value"], "unit": m["unit"], "n_gpus": 1, "steps": args.steps, "warmup": m["warmup"],
             "ms_per_step": m["ms_per_step"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -822,6 +831,8 @@ def main():
     ap.add_argument("--adj-steps", type=int, default=None, help="adjoint steps (profiling runs)")
     ap.add_argument("--b1-lines", type=int, default=None, help="batch1d lines (profiling runs)")
     ap.add_argument("--b1-capacity", type=int, default=None, help="batch1d capacity per line (profiling runs)")
+    ap.add_argument("--b1-shape", default=None,
+                    help="batch1d launch shape threads,ctas_per_sm,ctas_per_line instead of the tuner (profiling runs)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -405,7 +405,9 @@ grpic_status grpic_batch1d_init_fields(grpic_batch1d_ctx *ctx, grpic_lines *line
 /* nsteps steps (global step numbers step0 .. step0+nsteps-1) of every line
  * in one persistent launch: CTAs take lines from a device queue ordered by
  * decreasing particle count, keep D^r and J^r A_r of their line in shared
- * memory and run all nsteps for it.  Capacity overflow drops the excess
+ * memory and run all nsteps for it.  J^r A_r is summed in 64-bit fixed point
+ * (units of 2^-32 |q w|_max / dt), so the current does not depend on the
+ * order of the deposits and repeated runs give the same D^r bit for bit.  Capacity overflow drops the excess
  * appended particles and latches GRPIC_EOVERFLOW (read by
  * grpic_batch1d_sync). */
 grpic_status grpic_batch1d_run(grpic_batch1d_ctx *ctx, grpic_lines *lines, int nsteps, int64_t step0, void *stream);
@@ -418,12 +420,23 @@ grpic_status grpic_batch1d_run_graph(grpic_batch1d_ctx *ctx, grpic_lines *lines,
                                      void *stream);
 
 /* Autotuner: runs trial_steps real steps (starting at step0) with each
- * candidate (threads per block, blocks per SM), times them with CUDA events
- * and keeps the fastest for later runs.  Advances the state by
- * trial_steps * (number of candidates) steps, returned in *steps_done;
- * best[0] = threads per block, best[1] = blocks per SM. */
+ * candidate launch shape (threads per CTA, CTAs per SM, CTAs per line),
+ * times them with CUDA events and keeps the fastest for later runs.
+ * Advances the state by trial_steps * (number of candidates) steps, returned
+ * in *steps_done; best[0] = threads per CTA, best[1] = CTAs per SM,
+ * best[2] = CTAs per line (1, or 2 as a thread-block cluster on two SMs that
+ * share the line: each pushes half of its particles, the two currents are
+ * summed through distributed shared memory in a fixed order, the line's
+ * particle order is the same as with one CTA). */
 grpic_status grpic_batch1d_tune(grpic_batch1d_ctx *ctx, grpic_lines *lines, int trial_steps, int64_t step0,
-                                int64_t *steps_done, int32_t best[2], void *stream);
+                                int64_t *steps_done, int32_t best[3], void *stream);
+
+/* Set the launch shape of later runs (as the tuner would): threads per CTA
+ * (a multiple of 32 in [32, 1024]), CTAs per SM (at most what the CTA's
+ * registers and shared memory allow), CTAs per line (1 or 2).  GRPIC_EINVAL
+ * for a shape that cannot run.  No device work. */
+grpic_status grpic_batch1d_set_launch(grpic_batch1d_ctx *ctx, int32_t threads, int32_t ctas_per_sm,
+                                      int32_t ctas_per_line);
 
 /* Wait for `stream`, return and clear the first latched device error. */
 grpic_status grpic_batch1d_sync(grpic_batch1d_ctx *ctx, void *stream);

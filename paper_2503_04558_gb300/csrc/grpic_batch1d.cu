@@ -12,9 +12,20 @@
 // decisions with Philox4x64-10, then one packed block scan places survivors
 // (in order) in the other buffer and the children (in parent order) in a
 // staging area that is appended after the survivors at the end of the step.
+//
+// A line can also be shared by a cluster of two CTAs on two SMs (the largest
+// lines otherwise set the time of a step): each pushes one half of the
+// line's particles into its own shared J^r A_r, the two halves are summed
+// through distributed shared memory in a fixed order so that both CTAs update
+// identical copies of D^r, the second CTA's survivors are moved down behind
+// the first's and the children follow in parent order: the same line state
+// as one CTA would leave, up to the rounding of the current's sum.
 #include "grpic_geo.cuh"
 #include "grpic_philox.cuh"
 
+#include <cooperative_groups.h>
+#include <algorithm>
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -29,6 +40,7 @@ struct B1Args {
     int nl, n;
     double a, r_in, dx1, dt, gthr, eps_ph, Pconv;
     float af, dx1f, dtf;
+    float junit, jinv;  // J^r A_r per fixed-point unit of the line current, and its inverse
     int n_iter;
     float qm[4], qw[4];
     int massive[4];
@@ -111,22 +123,39 @@ struct Kid {
     uint64_t id;
 };
 
-__global__ void __launch_bounds__(1024) b1_kernel(B1Args A)
+// CL CTAs per line (1, or 2 as a thread-block cluster)
+template <int CL>
+__device__ __forceinline__ void b1_body(const B1Args &A)
 {
+    namespace cg = cooperative_groups;
     extern __shared__ float smem[];
     const int n = A.n;
-    float *sD = smem;
+    // J^r A_r at faces -1..n in fixed point (units of A.junit): integer sums
+    // do not depend on the order of the atomics, so a line's current is the
+    // same whichever warps and CTAs deposit it
+    long long *sJ = reinterpret_cast<long long *>(smem);
+    float *sD = reinterpret_cast<float *>(sJ + n + 2);
     float *sA = sD + n;
-    float *sJ = sA + n;                      // n + 2 faces (-1..n)
-    int *wsum = (int *)(sJ + n + 2);         // 33 ints
-    int *sv = wsum + 34;                     // [0] line, [3] emitted, [4] converted, [5] pushed
+    int *wsum = (int *)(sA + n);             // 33 ints
+    int *sv = wsum + 34;                     // [0] line, [3] emitted, [4] converted, [5] pushed,
+                                             // [6] survivors, [7] children of this CTA
     const int tid = threadIdx.x, B = blockDim.x;
+    const int rank = CL > 1 ? (int)cg::this_cluster().block_rank() : 0;
+    const int64_t CsR = A.Cs / CL;           // staging slots of this CTA
 
     for (;;) {
-        if (tid == 0) sv[0] = atomicAdd(A.queue, 1);
-        __syncthreads();
-        int q = sv[0];
-        __syncthreads();
+        int q;
+        if (tid == 0 && rank == 0) sv[0] = atomicAdd(A.queue, 1);
+        if constexpr (CL == 1) {
+            __syncthreads();
+            q = sv[0];
+            __syncthreads();
+        } else {
+            cg::cluster_group cl = cg::this_cluster();
+            cl.sync();
+            q = cl.map_shared_rank(sv, 0)[0];
+            cl.sync();
+        }
         if (q >= A.nl) break;
         const int k = A.order[q];
         const double th = A.theta[k];
@@ -145,17 +174,21 @@ __global__ void __launch_bounds__(1024) b1_kernel(B1Args A)
         for (int st = 0; st < A.nsteps; ++st) {
             const int64_t step = A.step0 + st;
             const int src = (A.cur + st) & 1, dst = src ^ 1;
-            for (int i = tid; i < n + 2; i += B) sJ[i] = 0.0f;
+            for (int i = tid; i < n + 2; i += B) sJ[i] = 0;
             if (tid == 0) {
                 sv[3] = 0;
                 sv[4] = 0;
                 sv[5] = cnt;
             }
             __syncthreads();
+            // this CTA's part of the line: whole chunks of B particles, the first
+            // half of the chunks to rank 0; its survivors go to [lo, ...) for now
+            const int nch = (cnt + B - 1) / B, per = (nch + CL - 1) / CL;
+            const int lo = min(cnt, rank * per * B), hi = min(cnt, (rank + 1) * per * B);
             // running write offsets of the survivors and of the children: every
             // thread advances its own copy by the block totals of each chunk
             int wp = 0, sp0 = 0;
-            for (int cb = 0; cb < cnt; cb += B) {
+            for (int cb = lo; cb < hi; cb += B) {
                 const int idx = cb + tid;
                 bool alive = false;
                 int napp = 0;
@@ -164,7 +197,7 @@ __global__ void __launch_bounds__(1024) b1_kernel(B1Args A)
                 float o = 0.f, ur = 0.f, up = 0.f;
                 uint32_t tg = DEAD;
                 uint64_t pid = 0;
-                if (idx < cnt) {
+                if (idx < hi) {
                     size_t p = base + idx;
                     ci = A.cell[src][p];
                     o = A.off[src][p];
@@ -173,7 +206,7 @@ __global__ void __launch_bounds__(1024) b1_kernel(B1Args A)
                     tg = A.tag[src][p];
                     pid = A.id[src][p];
                 }
-                if (idx < cnt && !(tg & DEAD) && ci >= 0 && ci < n) {
+                if (idx < hi && !(tg & DEAD) && ci >= 0 && ci < n) {
                     const int sp = tg & 3u;
                     const bool massive = A.massive[sp] != 0, charged = A.qm[sp] != 0.0f;
                     const float rcf = (float)A.rcol[ci];
@@ -221,7 +254,9 @@ __global__ void __launch_bounds__(1024) b1_kernel(B1Args A)
                                 for (int w = 0; w < 4; ++w) {
                                     acc += W1f(on - (float)(w - 1)) - W1f(o - (float)(w - 1));
                                     int face = ci - 1 + w;
-                                    if (acc != 0.0f && face >= -1 && face <= n) atomicAdd(&sJ[face + 1], cq * acc);
+                                    if (acc != 0.0f && face >= -1 && face <= n)
+                                        atomicAdd(reinterpret_cast<unsigned long long *>(&sJ[face + 1]),
+                                                  (unsigned long long)__float2ll_rn(cq * acc * A.jinv));
                                 }
                             }
                             int ni = ci + di;
@@ -288,7 +323,7 @@ __global__ void __launch_bounds__(1024) b1_kernel(B1Args A)
                 int excl;
                 int tot = block_scan((alive ? 1 : 0) | (napp << 16), wsum, excl);
                 if (alive) {
-                    size_t d = base + wp + (excl & 0xffff);
+                    size_t d = base + lo + wp + (excl & 0xffff);
                     A.cell[dst][d] = ci;
                     A.off[dst][d] = o;
                     A.ur[dst][d] = ur;
@@ -298,8 +333,8 @@ __global__ void __launch_bounds__(1024) b1_kernel(B1Args A)
                 }
                 int ap = sp0 + (excl >> 16);
                 for (int w = 0; w < napp; ++w) {
-                    if (ap + w < A.Cs) {
-                        size_t d = sbase + ap + w;
+                    if (ap + w < CsR) {
+                        size_t d = sbase + rank * CsR + ap + w;
                         A.s_cell[d] = kid[w].cell;
                         A.s_off[d] = kid[w].off;
                         A.s_ur[d] = kid[w].ur;
@@ -314,38 +349,116 @@ __global__ void __launch_bounds__(1024) b1_kernel(B1Args A)
                 sp0 += tot >> 16;
             }
             __syncthreads();  // the staging writes, the J atomics and the counters are complete
-            // children after the survivors
-            const int wptr = wp, sptr = sp0;
-            int nap = min(sptr, (int)A.Cs);
-            int room = (int)(A.C - wptr);
-            int ncopy = min(nap, room);
-            if (tid == 0 && ncopy < sptr) set_status(A.status, GRPIC_EOVERFLOW);
-            for (int j = tid; j < ncopy; j += B) {
-                size_t s = sbase + j, d = base + wptr + j;
-                A.cell[dst][d] = A.s_cell[s];
-                A.off[dst][d] = A.s_off[s];
-                A.ur[dst][d] = A.s_ur[s];
-                A.up[dst][d] = A.s_up[s];
-                A.tag[dst][d] = A.s_tag[s];
-                A.id[dst][d] = A.s_id[s];
+            if constexpr (CL == 1) {
+                // children after the survivors
+                const int wptr = wp, sptr = sp0;
+                int nap = min(sptr, (int)A.Cs);
+                int room = (int)(A.C - wptr);
+                int ncopy = min(nap, room);
+                if (tid == 0 && ncopy < sptr) set_status(A.status, GRPIC_EOVERFLOW);
+                for (int j = tid; j < ncopy; j += B) {
+                    size_t s = sbase + j, d = base + wptr + j;
+                    A.cell[dst][d] = A.s_cell[s];
+                    A.off[dst][d] = A.s_off[s];
+                    A.ur[dst][d] = A.s_ur[s];
+                    A.up[dst][d] = A.s_up[s];
+                    A.tag[dst][d] = A.s_tag[s];
+                    A.id[dst][d] = A.s_id[s];
+                }
+                cnt = wptr + ncopy;
+                // field: d(A D)/dt = I0 - J A
+                for (int i = tid; i < n; i += B) sD[i] += A.dtf * (I0 - __ll2float_rn(sJ[i + 1]) * A.junit) / sA[i];
+                if (A.JA && st == A.nsteps - 1)
+                    for (int i = tid; i < n + 2; i += B) A.JA[(size_t)k * (n + 2) + i] = __ll2float_rn(sJ[i]) * A.junit;
+            } else {
+                cg::cluster_group cl = cg::this_cluster();
+                if (tid == 0) {
+                    sv[6] = wp;
+                    sv[7] = sp0;
+                }
+                cl.sync();  // both halves pushed: J, counts and staging complete
+                const int *v0 = cl.map_shared_rank(sv, 0), *v1 = cl.map_shared_rank(sv, 1);
+                const int S0 = v0[6], S1 = v1[6];
+                const int K0 = (int)min((int64_t)v0[7], CsR), K1 = (int)min((int64_t)v1[7], CsR);
+                // field with the current of the whole line, summed in rank order so
+                // that both copies of D^r stay identical
+                const long long *J0 = cl.map_shared_rank(sJ, 0), *J1 = cl.map_shared_rank(sJ, 1);
+                for (int i = tid; i < n; i += B)
+                    sD[i] += A.dtf * (I0 - __ll2float_rn(J0[i + 1] + J1[i + 1]) * A.junit) / sA[i];
+                if (A.JA && st == A.nsteps - 1 && rank == 0)
+                    for (int i = tid; i < n + 2; i += B)
+                        A.JA[(size_t)k * (n + 2) + i] = __ll2float_rn(J0[i] + J1[i]) * A.junit;
+                // rank 1's survivors (written from its first particle's slot) move
+                // down behind rank 0's, a chunk at a time: every chunk is read
+                // before it is written and its destination lies below the next
+                // chunk's source, so the move is safe in increasing order
+                if (rank == 1 && S0 < lo) {
+                    for (int c0 = 0; c0 < S1; c0 += B) {
+                        const int q2 = c0 + tid;
+                        const bool v = q2 < S1;
+                        int32_t mc = 0;
+                        float mo = 0.f, mu = 0.f, mp = 0.f;
+                        uint32_t mt = 0;
+                        uint64_t mi = 0;
+                        if (v) {
+                            const size_t s2 = base + lo + q2;
+                            mc = A.cell[dst][s2];
+                            mo = A.off[dst][s2];
+                            mu = A.ur[dst][s2];
+                            mp = A.up[dst][s2];
+                            mt = A.tag[dst][s2];
+                            mi = A.id[dst][s2];
+                        }
+                        __syncthreads();
+                        if (v) {
+                            const size_t d2 = base + S0 + q2;
+                            A.cell[dst][d2] = mc;
+                            A.off[dst][d2] = mo;
+                            A.ur[dst][d2] = mu;
+                            A.up[dst][d2] = mp;
+                            A.tag[dst][d2] = mt;
+                            A.id[dst][d2] = mi;
+                        }
+                        __syncthreads();
+                    }
+                }
+                cl.sync();  // survivors in place, the remote J and counts read
+                // children after all survivors: rank 0's, then rank 1's
+                const int Stot = S0 + S1, room = (int)(A.C - Stot);
+                const int c0n = min(K0, max(room, 0)), c1n = min(K1, max(room - c0n, 0));
+                if (tid == 0 && rank == 0 && c0n + c1n < v0[7] + v1[7]) set_status(A.status, GRPIC_EOVERFLOW);
+                const int mine = rank == 0 ? c0n : c1n, at = Stot + (rank == 0 ? 0 : c0n);
+                for (int j = tid; j < mine; j += B) {
+                    size_t s2 = sbase + rank * CsR + j, d2 = base + at + j;
+                    A.cell[dst][d2] = A.s_cell[s2];
+                    A.off[dst][d2] = A.s_off[s2];
+                    A.ur[dst][d2] = A.s_ur[s2];
+                    A.up[dst][d2] = A.s_up[s2];
+                    A.tag[dst][d2] = A.s_tag[s2];
+                    A.id[dst][d2] = A.s_id[s2];
+                }
+                cnt = Stot + c0n + c1n;
             }
-            cnt = wptr + ncopy;
-            // field: d(A D)/dt = I0 - J A
-            for (int i = tid; i < n; i += B) sD[i] += A.dtf * (I0 - sJ[i + 1]) / sA[i];
-            if (A.JA && st == A.nsteps - 1)
-                for (int i = tid; i < n + 2; i += B) A.JA[(size_t)k * (n + 2) + i] = sJ[i];
             if (tid == 0) {
                 if (sv[3]) atomicAdd(&A.events[0], (unsigned long long)sv[3]);
                 if (sv[4]) atomicAdd(&A.events[1], (unsigned long long)sv[4]);
-                atomicAdd(&A.events[2], (unsigned long long)sv[5]);  // particles pushed this step
+                if (rank == 0) atomicAdd(&A.events[2], (unsigned long long)sv[5]);  // particles pushed this step
             }
-            __syncthreads();
+            if constexpr (CL == 1)
+                __syncthreads();
+            else
+                cg::this_cluster().sync();  // the line's next state complete before the next step reads it
         }
-        for (int i = tid; i < n; i += B) A.D[(size_t)k * n + i] = sD[i];
-        if (tid == 0) A.count[k] = cnt;
+        if (rank == 0) {
+            for (int i = tid; i < n; i += B) A.D[(size_t)k * n + i] = sD[i];
+            if (tid == 0) A.count[k] = cnt;
+        }
         __syncthreads();
     }
 }
+
+__global__ void __launch_bounds__(1024) b1_kernel(B1Args A) { b1_body<1>(A); }
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(1024) b1_kernel_cl2(B1Args A) { b1_body<2>(A); }
 
 // order the lines by decreasing particle count (ties by index) and reset the
 // work queue: one block, bitonic network in shared memory
@@ -411,14 +524,14 @@ struct grpic_batch1d_ctx {
     uint32_t *s_tag;
     uint64_t *s_id;
     int64_t Cs;
-    int block, per_sm, sms;
+    int block, per_sm, cluster, sms;  // launch shape: threads per CTA, CTAs per SM, CTAs per line
     size_t smem;
     // CUDA graph of one run (line order + persistent kernel) and what it was built for
     cudaGraph_t graph;
     cudaGraphExec_t gexec;
     cudaGraphNode_t g_b1;
     const void *gkey[20];
-    int gshape[2];
+    int gshape[3];
 };
 
 using namespace grpic;
@@ -451,6 +564,13 @@ B1Args make_args(grpic_batch1d_ctx *c, grpic_lines *L, int nsteps, int64_t step0
     A.seed = p.seed;
     A.C = p.capacity;
     A.Cs = c->Cs;
+    // fixed-point unit of the current: 2^-32 of the largest contribution of
+    // one particle (|q w| / dt), so that 2^30 particles cannot overflow a sum
+    double qmax = 0.0;
+    for (int s = 0; s < 4; ++s) qmax = std::max(qmax, std::fabs(p.q_weight[s]));
+    const double unit = qmax > 0.0 ? qmax / p.dt * std::ldexp(1.0, -32) : 1.0;
+    A.junit = (float)unit;
+    A.jinv = (float)(1.0 / unit);
     A.theta = L->theta;
     A.I0 = L->I0;
     A.D = L->D;
@@ -490,12 +610,48 @@ bool lines_ok(const grpic_lines *L)
     return true;
 }
 
+// CTAs of a launch: per_sm on every SM; with two CTAs per line, as many
+// clusters as can be resident at once (a cluster needs two SMs of one GPC)
+int b1_grid(grpic_batch1d_ctx *c, int block, int per_sm, int cluster)
+{
+    if (cluster == 1) return c->sms * per_sm;
+    cudaLaunchConfig_t cfg;
+    memset(&cfg, 0, sizeof cfg);
+    cfg.gridDim = dim3((unsigned)(c->sms * per_sm));
+    cfg.blockDim = dim3((unsigned)block);
+    cfg.dynamicSmemBytes = c->smem;
+    int ncl = 0;
+    if (cudaOccupancyMaxActiveClusters(&ncl, (void *)b1_kernel_cl2, &cfg) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return 2 * std::min(ncl, c->sms * per_sm / 2);
+}
+
+const void *b1_func(int cluster) { return cluster == 2 ? (const void *)b1_kernel_cl2 : (const void *)b1_kernel; }
+
+bool shape_ok(grpic_batch1d_ctx *c, int block, int per_sm, int cluster)
+{
+    if (block < 32 || block > 1024 || block % 32 != 0 || per_sm < 1 || (cluster != 1 && cluster != 2)) return false;
+    int maxb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&maxb, b1_kernel, block, c->smem) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return per_sm <= maxb && b1_grid(c, block, per_sm, cluster) >= cluster;
+}
+
 cudaError_t launch_b1(grpic_batch1d_ctx *c, grpic_lines *L, int nsteps, int64_t step0, int block, int per_sm,
-                      cudaStream_t s)
+                      int cluster, cudaStream_t s)
 {
     order_kernel<<<1, 1024, 0, s>>>(L->count, c->p.n_lines, c->order, c->queue);
     B1Args A = make_args(c, L, nsteps, step0);
-    b1_kernel<<<c->sms * per_sm, block, c->smem, s>>>(A);
+    const int grid = b1_grid(c, block, per_sm, cluster);
+    if (grid < 1) return cudaErrorInvalidConfiguration;
+    if (cluster == 2)
+        b1_kernel_cl2<<<grid, block, c->smem, s>>>(A);
+    else
+        b1_kernel<<<grid, block, c->smem, s>>>(A);
     return cudaGetLastError();
 }
 
@@ -521,7 +677,7 @@ grpic_status grpic_batch1d_init(const grpic_batch1d_params *p, grpic_batch1d_ctx
     int dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, dev);
-    c->smem = sizeof(float) * (3 * (size_t)n + 2) + sizeof(int) * 48;
+    c->smem = sizeof(long long) * ((size_t)n + 2) + sizeof(float) * 2 * (size_t)n + sizeof(int) * 48;
     size_t ns = (size_t)p->n_lines * c->Cs;
     cudaError_t e = cudaMalloc(&c->rcol, sizeof(double) * (n + 1));
     if (e == cudaSuccess) e = cudaMalloc(&c->Ar, sizeof(float) * (size_t)p->n_lines * n);
@@ -535,6 +691,8 @@ grpic_status grpic_batch1d_init(const grpic_batch1d_params *p, grpic_batch1d_ctx
     if (e == cudaSuccess) e = cudaMalloc(&c->s_tag, sizeof(uint32_t) * ns);
     if (e == cudaSuccess) e = cudaMalloc(&c->s_id, sizeof(uint64_t) * ns);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(b1_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(b1_kernel_cl2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->smem);
     if (e != cudaSuccess) {
         grpic_batch1d_destroy(c);
         return GRPIC_ENOMEM;
@@ -547,6 +705,7 @@ grpic_status grpic_batch1d_init(const grpic_batch1d_params *p, grpic_batch1d_ctx
     // default launch shape until the tuner picks one
     c->block = 256;
     c->per_sm = 2;
+    c->cluster = 1;
     int maxb = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&maxb, b1_kernel, c->block, c->smem);
     if (maxb < 1) {
@@ -573,32 +732,31 @@ grpic_status grpic_batch1d_run(grpic_batch1d_ctx *c, grpic_lines *L, int nsteps,
 {
     if (!c || !lines_ok(L) || nsteps < 0) return GRPIC_EINVAL;
     if (nsteps == 0) return GRPIC_OK;
-    cudaError_t e = launch_b1(c, L, nsteps, step0, c->block, c->per_sm, (cudaStream_t)stream);
+    cudaError_t e = launch_b1(c, L, nsteps, step0, c->block, c->per_sm, c->cluster, (cudaStream_t)stream);
     if (e != cudaSuccess) return GRPIC_ECUDA;
     if (nsteps & 1) L->cur ^= 1;
     return GRPIC_OK;
 }
 
 grpic_status grpic_batch1d_tune(grpic_batch1d_ctx *c, grpic_lines *L, int trial_steps, int64_t step0,
-                                int64_t *steps_done, int32_t best[2], void *stream)
+                                int64_t *steps_done, int32_t best[3], void *stream)
 {
     if (!c || !lines_ok(L) || trial_steps < 1 || !steps_done || !best) return GRPIC_EINVAL;
     cudaStream_t s = (cudaStream_t)stream;
     const int blocks[4] = {128, 256, 512, 1024};
     const int persm[3] = {1, 2, 4};
     float best_ms = 1e30f;
-    int bb = c->block, bp = c->per_sm;
+    int bb = c->block, bp = c->per_sm, bc = c->cluster;
     int64_t done = 0;
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
-    for (int b : blocks) {
+    for (int cl = 1; cl <= 2; ++cl) {
+      for (int b : blocks) {
         for (int ps : persm) {
-            int maxb = 0;
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&maxb, b1_kernel, b, c->smem);
-            if (ps > maxb) continue;
+            if (!shape_ok(c, b, ps, cl)) continue;
             cudaEventRecord(e0, s);
-            if (launch_b1(c, L, trial_steps, step0 + done, b, ps, s) != cudaSuccess) {
+            if (launch_b1(c, L, trial_steps, step0 + done, b, ps, cl, s) != cudaSuccess) {
                 cudaEventDestroy(e0);
                 cudaEventDestroy(e1);
                 return GRPIC_ECUDA;
@@ -613,16 +771,29 @@ grpic_status grpic_batch1d_tune(grpic_batch1d_ctx *c, grpic_lines *L, int trial_
                 best_ms = ms;
                 bb = b;
                 bp = ps;
+                bc = cl;
             }
         }
+      }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     c->block = bb;
     c->per_sm = bp;
+    c->cluster = bc;
     best[0] = bb;
     best[1] = bp;
+    best[2] = bc;
     *steps_done = done;
+    return GRPIC_OK;
+}
+
+grpic_status grpic_batch1d_set_launch(grpic_batch1d_ctx *c, int32_t threads, int32_t ctas_per_sm, int32_t ctas_per_line)
+{
+    if (!c || !shape_ok(c, threads, ctas_per_sm, ctas_per_line)) return GRPIC_EINVAL;
+    c->block = threads;
+    c->per_sm = ctas_per_sm;
+    c->cluster = ctas_per_line;
     return GRPIC_OK;
 }
 
@@ -637,14 +808,15 @@ grpic_status grpic_batch1d_run_graph(grpic_batch1d_ctx *c, grpic_lines *L, int n
     cudaKernelNodeParams pb;
     memset(&pb, 0, sizeof pb);
     void *bargs[] = {&A};
-    pb.func = (void *)b1_kernel;
-    pb.gridDim = dim3((unsigned)(c->sms * c->per_sm));
+    pb.func = (void *)b1_func(c->cluster);
+    pb.gridDim = dim3((unsigned)b1_grid(c, c->block, c->per_sm, c->cluster));
     pb.blockDim = dim3((unsigned)c->block);
     pb.sharedMemBytes = (unsigned)c->smem;
     pb.kernelParams = bargs;
     cudaError_t e = cudaSuccess;
+    if (pb.gridDim.x < 1) return GRPIC_ECUDA;
     bool same = c->gexec && memcmp(key, c->gkey, sizeof key) == 0 && c->gshape[0] == c->block &&
-                c->gshape[1] == c->per_sm;
+                c->gshape[1] == c->per_sm && c->gshape[2] == c->cluster;
     if (same) {
         // only the run's arguments (steps, first step, current buffer) change
         e = cudaGraphExecKernelNodeSetParams(c->gexec, c->g_b1, &pb);
@@ -676,6 +848,7 @@ grpic_status grpic_batch1d_run_graph(grpic_batch1d_ctx *c, grpic_lines *L, int n
         memcpy(c->gkey, key, sizeof key);
         c->gshape[0] = c->block;
         c->gshape[1] = c->per_sm;
+        c->gshape[2] = c->cluster;
     }
     if (e == cudaSuccess) e = cudaGraphLaunch(c->gexec, (cudaStream_t)stream);
     if (e != cudaSuccess) return GRPIC_ECUDA;

@@ -444,6 +444,7 @@ def _load_b1(lib):
                        "grpic_batch1d_run": [v, p(LinesC), C.c_int, C.c_int64, v],
                        "grpic_batch1d_run_graph": [v, p(LinesC), C.c_int, C.c_int64, v],
                        "grpic_batch1d_tune": [v, p(LinesC), C.c_int, C.c_int64, p(C.c_int64), p(C.c_int32), v],
+                       "grpic_batch1d_set_launch": [v, C.c_int32, C.c_int32, C.c_int32],
                        "grpic_batch1d_sync": [v, v]}.items():
         fn = getattr(lib, name)
         fn.argtypes = args
@@ -453,7 +454,7 @@ def _load_b1(lib):
 
 
 EXPORTS += ["grpic_batch1d_init", "grpic_batch1d_init_fields", "grpic_batch1d_run", "grpic_batch1d_run_graph",
-            "grpic_batch1d_tune",
+            "grpic_batch1d_tune", "grpic_batch1d_set_launch",
             "grpic_batch1d_sync", "grpic_batch1d_destroy"]
 
 
@@ -610,12 +611,19 @@ class Batch1D:
 
     def tune(self, L: Lines, trial_steps, step0, stream=None):
         done = C.c_int64()
-        best = (C.c_int32 * 2)()
+        best = (C.c_int32 * 3)()
         st = self.lib.grpic_batch1d_tune(self.h, C.byref(L._c), trial_steps, step0, C.byref(done), best,
                                          _stream(stream))
         if st != OK:
             raise GrpicError(st, "grpic_batch1d_tune")
-        return done.value, (best[0], best[1])
+        return done.value, (best[0], best[1], best[2])
+
+    def set_launch(self, threads: int, ctas_per_sm: int, ctas_per_line: int = 1):
+        """Launch shape of later runs: threads per CTA, CTAs per SM, CTAs per
+        line (2: a cluster of two CTAs shares each line)."""
+        st = self.lib.grpic_batch1d_set_launch(self.h, threads, ctas_per_sm, ctas_per_line)
+        if st != OK:
+            raise GrpicError(st, "grpic_batch1d_set_launch")
 
     def sync(self, stream=None):
         return self.lib.grpic_batch1d_sync(self.h, _stream(stream))
