@@ -576,12 +576,12 @@ def adjoint_measure(reps=2, n_particles=None, nsteps=None):
     flush = torch.empty(256 * 2**20 // 4, dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
 
-    def timed(want):
+    def timed(want, ck=20):
         flush.fill_(1.0)
         torch.cuda.synchronize()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
-        L, gp, gf = G.adjoint_grad(ctx, x, tag, F.D, F.B, nsteps, iH, want_grad=want)
+        L, gp, gf = G.adjoint_grad(ctx, x, tag, F.D, F.B, nsteps, iH, checkpoint_every=ck, want_grad=want)
         b.record(stream)
         torch.cuda.synchronize()
         return a.elapsed_time(b), L
@@ -593,9 +593,19 @@ def adjoint_measure(reps=2, n_particles=None, nsteps=None):
         grad = [timed(True) for _ in range(reps)]
     f_ms = statistics.mean(t for t, _ in fwd)
     g_ms = statistics.mean(t for t, _ in grad)
+    # the same gradient with one segment (the forward pass records every step:
+    # more memory, no recomputation), where the device has the room
+    one_seg = None
+    free, _ = torch.cuda.mem_get_info()
+    need = nsteps * n_particles * 8 * (10 + 6 * cfg.n_push_iter + 6) * 1.2
+    if free > need:
+        timed(True, nsteps)
+        one_seg = statistics.mean(timed(True, nsteps)[0] for _ in range(reps))
     out = {"value": n_particles * nsteps / (g_ms * 1e-3), "unit": "particle-steps/s (objective + gradient)",
            "forward_s": f_ms / 1e3, "gradient_s": g_ms / 1e3, "gradient_over_forward": g_ms / f_ms,
            "objective": grad[0][1], "dtype": "f64", "checkpoint_every": 20, "reps": reps,
+           "gradient_s_one_segment": one_seg / 1e3 if one_seg else None,
+           "one_segment_over_forward": one_seg / f_ms if one_seg else None,
            "workload": "256x256, a=0.9, r in [0.9 r_H, 50], Wald B0=1, %.0e e+/e- (sigma 0.1), %d steps, "
                        "L = time-averaged horizon Poynting flux, gradient w.r.t. the initial particle state "
                        "and fields" % (n_particles, nsteps), "l2": "state below L2: 256 MB written before each timed run",
@@ -613,7 +623,8 @@ def run_adjoint(args):
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": m["workload"], "l2": m["l2"]}, "forward_s": m["forward_s"],
             "gradient_over_forward": m["gradient_over_forward"], "objective": m["objective"],
-            "clocks": m["clocks"]}
+            "gradient_s_one_segment": m["gradient_s_one_segment"],
+            "one_segment_over_forward": m["one_segment_over_forward"], "clocks": m["clocks"]}
     print(json.dumps(line), flush=True)
 
 

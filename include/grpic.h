@@ -301,7 +301,10 @@ grpic_status grpic_adjoint_field_step(grpic_ctx *ctx, const grpic_fields *lam_in
  * the transposed interpolation; fields by the transposed stage sequence.  The forward
  * states are recomputed from checkpoints taken every checkpoint_every steps
  * (memory: ceil(nsteps/checkpoint_every) + checkpoint_every + 2 copies of
- * the particle and field state).
+ * the particle and field state, and the FP64 push's record of one segment:
+ * checkpoint_every x (10 + 6 n_push_iter) doubles per particle).  The last
+ * segment is recorded during the forward pass itself, so checkpoint_every >=
+ * nsteps trades that memory for no recomputation at all.
  *   p0:  n live or dead particles (FP64 SoA r, theta, u_r, u_theta, u_phi,
  *        tag); not modified.  p0->d_count is ignored (p0->n is used).
  *   f0:  the fields at step 0 (D, B; f0->J unused); not modified.

@@ -1498,9 +1498,22 @@ extern "C" grpic_status grpic_adjoint_grad(grpic_ctx *ctx, const grpic_particles
         cleanup();
         return GRPIC_ENOMEM;
     }
+    // the last segment, the first the reverse sweep needs, is recorded here
+    // (its states, the push's record and, for the spin derivative, its
+    // currents) instead of being recomputed from its checkpoint
+    const int last0 = (nseg - 1) * ck;
     for (int n = 0; n < nsteps && st == GRPIC_OK; ++n) {
         if (want && n % ck == 0) copy_state(cks[n / ck], W);
-        st = fwd_step(nullptr);
+        const bool rec = want && n >= last0;
+        const int m = n - last0;
+        if (rec && m == 0) copy_state(seg[0], W);
+        st = fwd_step(rec ? tape + (size_t)m * TW * (size_t)np : nullptr);
+        if (rec) {
+            copy_state(seg[m + 1], W);
+            if (spin)
+                for (int k = 0; k < 3; ++k)
+                    cudaMemcpyAsync(segJ[3 * m + k], Jw[k], fn * sizeof(double), cudaMemcpyDeviceToDevice, s);
+        }
         flux_kernel<<<1, 256, 0, s>>>(A, dWf, i_horizon, dth, wL, Ldev);
         if (spin)  // the objective's own tables at F^{n+1}
             flux_da<<<(ctx->g.nth + 255) / 256, 256, 0, s>>>(A, dtab, dWf, i_horizon, dth, wL, Ladev);
@@ -1548,10 +1561,12 @@ extern "C" grpic_status grpic_adjoint_grad(grpic_ctx *ctx, const grpic_particles
     dim3 gfull((ctx->g.ld_tab + 63) / 64, (ctx->g.nth + 1 + 3) / 4), blk(64, 4);
     for (int sgi = nseg - 1; sgi >= 0 && st == GRPIC_OK; --sgi) {
         int n0 = sgi * ck, len = std::min(ck, nsteps - n0);
-        // recompute the segment's states
-        copy_state(W, cks[sgi]);
-        copy_state(seg[0], W);
-        for (int m = 0; m < len && st == GRPIC_OK; ++m) {
+        // recompute the segment's states (the last one was recorded in the forward pass)
+        if (sgi != nseg - 1) {
+            copy_state(W, cks[sgi]);
+            copy_state(seg[0], W);
+        }
+        for (int m = 0; m < len && st == GRPIC_OK && sgi != nseg - 1; ++m) {
             st = fwd_step(tape + (size_t)m * TW * (size_t)np);
             copy_state(seg[m + 1], W);
             if (spin)
