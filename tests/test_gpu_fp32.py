@@ -162,7 +162,7 @@ def test_fp32_sort_is_bit_exact(G):
 
 @pytest.fixture(scope="module")
 def run20(G):
-    """Config 1 (128^2, a = 0.9, Wald, 2e5 particles, 20 steps) in the FP32 form
+    """The 128^2 Wald workload (a = 0.9, 2e5 particles, 20 steps) in the FP32 form
     next to the FP64 oracle, on the inputs without the axis-grazing particles
     (ill-conditioned paths, see gpu_common.axis_grazers)."""
     oc, gc = cfg32(128)
@@ -190,7 +190,7 @@ def run20(G):
     return dict(oc=oc, F=F, S=S, P=P, D=D, B=B, charge=worst, check=chk[:2])
 
 
-def test_fp32_config1_field_error(run20):
+def test_fp32_wald128_field_error(run20):
     c = run20
     errs = [relerr(host(c["F"].D[k]), c["D"][k]) for k in range(3)] + \
            [relerr(host(c["F"].B[k]), c["B"][k]) for k in range(3)]
@@ -198,7 +198,7 @@ def test_fp32_config1_field_error(run20):
     assert max(errs) < 1e-4, errs
 
 
-def test_fp32_config1_particle_error(run20):
+def test_fp32_wald128_particle_error(run20):
     c = run20
     oc, P = c["oc"], c["P"]
     h = c["S"].host()
@@ -212,7 +212,7 @@ def test_fp32_config1_particle_error(run20):
     assert agree > 0.99
 
 
-def test_fp32_config1_charge_conservation(run20):
+def test_fp32_wald128_charge_conservation(run20):
     print("FP32 form charge residual / max|rho|:", run20["charge"])
     assert run20["charge"] < 1e-4
 

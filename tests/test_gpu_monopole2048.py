@@ -1,4 +1,4 @@
-"""Config 2 at full size, the workload the bench times: 2048 x 2048, a = 0.99,
+"""The split-monopole workload at full size, the one the bench times: 2048 x 2048, a = 0.99,
 r in [0.9 r_H, 100], split monopole B0 = 1, 100 particles per cell (4.19e8
 e+/e-), Maxwell-Juettner momenta at T = 0.3, FP64 plain and the FP32 form
 with the bench's settings (double-FP32 metric inside 1.5 r_H, corrector
@@ -17,7 +17,7 @@ tolerance 1e-6).
   * FP32 form: the sample's momenta after one push against the oracle (bar
     2e-5) and the fields after three steps against the FP64 path (bar 1e-4).
 
-As in config 3, the particles that start within 0.01 rad of the polar axis
+As in the 4096^2 Wald test, the particles that start within 0.01 rad of the polar axis
 are marked dead in both paths (there the push is ill-conditioned: J^phi ~
 u_phi / sin^2 theta of a grazing path dominates any field comparison
 between two precisions).  Both paths at once hold ~80 GB of device memory."""
@@ -152,45 +152,45 @@ def runs():
     return dict(out=out, P=P, P0=P0, st=st, n=n)
 
 
-def test_config2_fp64_push_matches_oracle_on_a_sample(runs):
+def test_monopole2048_fp64_push_matches_oracle_on_a_sample(runs):
     out, P = runs["out"]["fp64"], runs["P"]
     alive = ((runs["P"].tag & 0x80000000) == 0) & ((out["tag"] & 0x80000000) == 0)
     assert alive.sum() > 0.99 * NSUB
     errs = [relerr(out["x"][0][alive], P.r[alive]), relerr(out["x"][1][alive], P.th[alive])]
     errs += [relerr(out["u"][k][alive], ref[alive]) for k, ref in enumerate((P.u1, P.u2, P.u3))]
-    print("config 2, FP64: one-push error of 20 000 sampled particles vs the oracle (r, th, u_r, u_th, u_ph):",
+    print("2048^2 monopole, FP64: one-push error of 20 000 sampled particles vs the oracle (r, th, u_r, u_th, u_ph):",
           " ".join(f"{e:.1e}" for e in errs))
     assert max(errs) < 1e-10, errs
 
 
-def test_config2_sort_at_full_size(runs):
+def test_monopole2048_sort_at_full_size(runs):
     out = runs["out"]["fp64"]
     ok_keys, ok_stable = out["sort1"]
     assert ok_keys and ok_stable
     assert out["sort2_keys"] and out["sort2_distinct"]
     assert out["n2"] <= out["n1"] <= runs["n"]
-    print(f"config 2: live after 1 and 3 steps: {out['n1']}, {out['n2']} of {runs['n']}")
+    print(f"2048^2 monopole: live after 1 and 3 steps: {out['n1']}, {out['n2']} of {runs['n']}")
 
 
-def test_config2_fp64_charge_conservation(runs):
+def test_monopole2048_fp64_charge_conservation(runs):
     res, rmax = runs["out"]["fp64"]["charge"]
-    print(f"config 2, FP64: continuity residual over 3 steps {res / rmax:.2e} of max|rho|")
+    print(f"2048^2 monopole, FP64: continuity residual over 3 steps {res / rmax:.2e} of max|rho|")
     assert res / rmax < 1e-12
 
 
-def test_config2_fp32_momentum_error_against_the_oracle(runs):
+def test_monopole2048_fp32_momentum_error_against_the_oracle(runs):
     P0, P = runs["P0"], runs["P"]
     u = runs["out"]["fp32"]["u"]
     alive = (P.tag & 0x80000000) == 0
     errs = [relerr(u[k][alive], ref[alive]) for k, ref in enumerate((P.u1, P.u2, P.u3))]
-    print("config 2, FP32 form: one-push momentum error vs the oracle (u_r, u_th, u_ph):",
+    print("2048^2 monopole, FP32 form: one-push momentum error vs the oracle (u_r, u_th, u_ph):",
           " ".join(f"{e:.1e}" for e in errs))
     assert max(errs) < 2e-5, errs
 
 
-def test_config2_fp32_field_error_against_fp64(runs):
+def test_monopole2048_fp32_field_error_against_fp64(runs):
     f32, f64 = runs["out"]["fp32"]["F"], runs["out"]["fp64"]["F"]
     errs = [relerr(a, b) for a, b in zip(f32, f64)]
-    print("config 2, FP32 form: field error after 3 steps vs FP64 (D^r, D^th, D^ph, B^r, B^th, B^ph):",
+    print("2048^2 monopole, FP32 form: field error after 3 steps vs FP64 (D^r, D^th, D^ph, B^r, B^th, B^ph):",
           " ".join(f"{e:.1e}" for e in errs))
     assert max(errs) < 1e-4, errs

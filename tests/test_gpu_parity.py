@@ -173,8 +173,8 @@ def charge_residual(G, ctx, S, F, rho0_div0, oc):
 
 
 @pytest.fixture(scope="module")
-def config1(G):
-    """Config 1: 128 x 128, a = 0.9, r in [0.9 r_H, 50], rotating Wald B0 = 1,
+def wald128(G):
+    """The 128 x 128 Wald workload: a = 0.9, r in [0.9 r_H, 50], rotating Wald B0 = 1,
     2e5 e+/e- uniform per cell (seed 0), Gaussian u sigma = 0.1, CFL 0.5,
     20 steps, sort every step; GPU and oracle side by side.  The particles
     whose oracle path grazes the polar axis (ill-conditioned, see
@@ -209,22 +209,22 @@ def config1(G):
                 check=chk[:2], host_check=host_check)
 
 
-def test_config1_axis_grazers_are_few(config1):
-    print("config 1: particles left out as axis-grazing:", config1["ngraze"], "of 200000;",
-          "closest approach of the rest:", config1["mind"])
-    assert config1["ngraze"] < 400
-    assert config1["mind"] > 1e-4
+def test_wald128_axis_grazers_are_few(wald128):
+    print("128^2 Wald: particles left out as axis-grazing:", wald128["ngraze"], "of 200000;",
+          "closest approach of the rest:", wald128["mind"])
+    assert wald128["ngraze"] < 400
+    assert wald128["mind"] > 1e-4
 
 
-def test_config1_fields_after_20_steps(config1):
-    c = config1
+def test_wald128_fields_after_20_steps(wald128):
+    c = wald128
     for k in range(3):
         assert relerr(host(c["F"].D[k]), c["D"][k]) < TOL, ("D", k)
         assert relerr(host(c["F"].B[k]), c["B"][k]) < TOL, ("B", k)
 
 
-def test_config1_particles_after_20_steps(config1):
-    c = config1
+def test_wald128_particles_after_20_steps(wald128):
+    c = wald128
     P, oc = c["P"], c["oc"]
     h = c["S"].host()
     assert len(h["x1"]) == P.n
@@ -241,21 +241,21 @@ def test_config1_particles_after_20_steps(config1):
         assert relerr(h[k], ref) < TOL, k
 
 
-def test_config1_charge_conservation(config1):
-    assert config1["charge"] < 1e-12, config1["charge"]
+def test_wald128_charge_conservation(wald128):
+    assert wald128["charge"] < 1e-12, wald128["charge"]
 
 
-def test_config1_running_charge_check(config1):
+def test_wald128_running_charge_check(wald128):
     """grpic_charge_check reduces max|div D - rho - base| and max|rho| over the
     interior vertices on the device; on the FP64 path it reproduces the
     host-side reduction of the diagnostics arrays."""
-    (res, rmax), (hres, hmax) = config1["check"], config1["host_check"]
+    (res, rmax), (hres, hmax) = wald128["check"], wald128["host_check"]
     assert rmax == pytest.approx(hmax, rel=1e-12)
     assert res / rmax < 1e-12
     assert abs(res - hres) <= 1e-12 * rmax
 
 
-def test_config1_full_input_conserves_charge(G):
+def test_wald128_full_input_conserves_charge(G):
     """All 2e5 particles (axis-grazing ones included): the discrete continuity
     residual stays at round-off through 20 steps."""
     oc, gc = configs(128, 128, A09, 0.9 * RH, 50.0)
@@ -456,7 +456,7 @@ def test_deferred_order_matches_separate_calls(G):
 def test_vay_pusher_steps_match_oracle(G):
     """Ten full steps with Vay's update in the FIDO frame (48 x 40, Wald
     B0 = 2, 2e4 particles, sigma = 0.5) against the oracle: fields and
-    particles to 1e-10, the axis-grazing paths left out as in config 1."""
+    particles to 1e-10, the axis-grazing paths left out as in the 128^2 Wald workload."""
     oc, gc = configs(48, 40, A09, 0.9 * RH, 20.0, qw=(-0.01, 0.01, 0.01, 0.0), pusher=1)
     ctx, F = gpu_fields(G, gc, O.WALD, 2.0)
     D, B = O.init_fields(oc, O.WALD, 2.0)

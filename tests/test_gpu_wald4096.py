@@ -1,4 +1,4 @@
-"""Config 3: the FP32 form at scale -- 4096 x 4096, a = 0.9, r in [0.9 r_H, 50],
+"""The FP32 form at scale -- 4096 x 4096, a = 0.9, r in [0.9 r_H, 50],
 Wald B0 = 1, 64 particles per cell (1.07e9 e+/e-), Gaussian momenta sigma
 0.1 -- with its error against FP64 reported per result:
 
@@ -8,9 +8,9 @@ Wald B0 = 1, 64 particles per cell (1.07e9 e+/e-), Gaussian momenta sigma
     at this resolution, is far below the FP32 error measured);
   * fields after three steps, against the FP64 GPU path on the same inputs
     (at this size that path stands for FP64: it matches the oracle to 1e-10
-    on config 1), max-norm relative per array, bar 1e-4.
+    on the 128^2 Wald workload), max-norm relative per array, bar 1e-4.
 
-As in config 1, the particles whose paths graze the polar axis are left
+As in the 128^2 Wald workload, the particles whose paths graze the polar axis are left
 out: there gamma^{phi phi} ~ 1/sin^2(theta) makes the push ill-conditioned,
 so FP32 and FP64 (or two FP64 libms) follow different paths and their J^phi
 (~ u_phi / sin^2(theta), 1e3 times the bulk value at the last rows) dominates
@@ -114,18 +114,18 @@ def runs():
     return dict(out=out, uo=uo, th0=y0["th"])
 
 
-def test_config3_momentum_error_against_the_oracle(runs):
+def test_wald4096_momentum_error_against_the_oracle(runs):
     uo, th0 = runs["uo"], runs["th0"]
     away = np.minimum(th0, math.pi - th0) > 0.05     # the closest ones to the axis (ill-conditioned) apart
     for name, bound in (("fp64", 1e-6), ("fp32", 2e-5)):
         u = runs["out"][name]["u"]
         errs = [relerr(u[k][away], uo[away, k]) for k in range(3)]
-        print(f"config 3, {name}: one-step momentum error vs the oracle (u_r, u_th, u_ph):", errs)
+        print(f"4096^2 Wald, {name}: one-step momentum error vs the oracle (u_r, u_th, u_ph):", errs)
         assert max(errs) < bound, (name, errs)
 
 
-def test_config3_fp32_field_error_against_fp64(runs):
+def test_wald4096_fp32_field_error_against_fp64(runs):
     f32, f64 = runs["out"]["fp32"]["F"], runs["out"]["fp64"]["F"]
     errs = [relerr(a, b) for a, b in zip(f32, f64)]
-    print("config 3: FP32-form field error after 3 steps vs FP64 (D^r, D^th, D^ph, B^r, B^th, B^ph):", errs)
+    print("4096^2 Wald: FP32-form field error after 3 steps vs FP64 (D^r, D^th, D^ph, B^r, B^th, B^ph):", errs)
     assert max(errs) < 1e-4, errs
