@@ -296,11 +296,16 @@ __device__ __forceinline__ void b1_body(const B1Args &A)
                                         }
                                     }
                                 } else if (!massive) {
-                                    double rd = A.rcol[ci] * exp((double)o * A.dx1), grr, grp, gpp;
-                                    ginv64(A.a, rd, sd, cd, grr, grp, gpp);
-                                    double urd = ur, upd = up;
-                                    double e = sqrt(grr * urd * urd + 2.0 * grp * urd * upd + gpp * upd * upd);
-                                    double u = uniform53(A.seed, pid, step, 1);
+                                    // the draw first: it fails for all but ~tau dt of the
+                                    // photons, which then skip the FP64 energy (the same
+                                    // decision: both conditions must hold)
+                                    const double u = uniform53(A.seed, pid, step, 1);
+                                    double e = 0.0, urd = ur, upd = up;
+                                    if (u < A.Pconv) {
+                                        double rd = A.rcol[ci] * exp((double)o * A.dx1), grr, grp, gpp;
+                                        ginv64(A.a, rd, sd, cd, grr, grp, gpp);
+                                        e = sqrt(grr * urd * urd + 2.0 * grp * urd * upd + gpp * upd * upd);
+                                    }
                                     if (e > 2.0 && u < A.Pconv) {
                                         double s = sqrt(0.25 * e * e - 1.0) / e;
                                         for (int w = 0; w < 2; ++w) {

@@ -407,22 +407,26 @@ __global__ void __launch_bounds__(256) push64_kernel(Push64Args A)
                 key = (tag & DEAD) ? ncell : (jcell(g, x2b) * g.nr + ib);
                 if (RAD && !(tag & DEAD)) {
                     // at the new position: emission by a charged particle above
-                    // gamma_thr, conversion of a photon above 2 m c^2
-                    KS m;
-                    ks_point(g.a, r, th, m);
-                    const double uu = m.gi_rr * u[0] * u[0] + 2.0 * m.gi_rp * u[0] * u[2] + m.gi_tt * u[1] * u[1] +
-                                      m.gi_pp * u[2] * u[2];
-                    if (A.massive[sp] && A.qm[sp] != 0.0) {
-                        const double G = sqrt(1.0 + uu), G2 = G - A.eps_ph;
-                        if (G >= A.gamma_thr && G2 >= 1.0) {
-                            const double f = sqrt(G2 * G2 - 1.0) / sqrt(uu);
-                            u[0] *= f;
-                            u[1] *= f;
-                            u[2] *= f;
-                            spawn = 1;
-                        }
-                    } else if (!A.massive[sp]) {
-                        if (sqrt(uu) > 2.0 && uniform53(A.seed, (uint64_t)p, A.step, 1) < A.pconv) {
+                    // gamma_thr, conversion of a photon above 2 m c^2; a photon
+                    // draws first (the draw fails for all but ~tau dt of them,
+                    // which then skip the metric: the same decision)
+                    const bool charged = A.massive[sp] && A.qm[sp] != 0.0;
+                    const bool drawn = !A.massive[sp] && uniform53(A.seed, (uint64_t)p, A.step, 1) < A.pconv;
+                    if (charged || drawn) {
+                        KS m;
+                        ks_point(g.a, r, th, m);
+                        const double uu = m.gi_rr * u[0] * u[0] + 2.0 * m.gi_rp * u[0] * u[2] +
+                                          m.gi_tt * u[1] * u[1] + m.gi_pp * u[2] * u[2];
+                        if (charged) {
+                            const double G = sqrt(1.0 + uu), G2 = G - A.eps_ph;
+                            if (G >= A.gamma_thr && G2 >= 1.0) {
+                                const double f = sqrt(G2 * G2 - 1.0) / sqrt(uu);
+                                u[0] *= f;
+                                u[1] *= f;
+                                u[2] *= f;
+                                spawn = 1;
+                            }
+                        } else if (sqrt(uu) > 2.0) {
                             spawn = 2;
                             tag |= DEAD;
                             key = ncell;
