@@ -60,12 +60,12 @@ PUSH32_FP32_FLOP = 1058.0   # profiles/push32_fp32form_1024x1024_64ppc.md
 # number of particles
 PUSH32_INST = 1780.0
 PUSH32_DRAM_B = 69.3
-# batched 1D lines, b1_kernel (profiles/b1_kernel_256lines_4096cells.md):
+# batched 1D lines, b1_kernel with the cascade running (profiles/b1_kernel_256lines_4096cells.md):
 # instructions issued per particle-step (warp instructions x 32) and DRAM
 # bytes per particle-step; algorithmic bytes: the particle record (cell, offset,
 # u_r, u_phi, tag as 4 B each, id 8 B) read and written once per step
-B1_INST = 998.0
-B1_DRAM_B = 50.7
+B1_INST = 1037.0
+B1_DRAM_B = 51.7
 B1_ALG_B = 2 * 28
 # the widened rows' push kernels, counted the same way (profiles/ summaries
 # named for each): the FP32 push with Vay's update, the FP64 push with the

@@ -41,6 +41,12 @@ struct B1Args {
     double a, r_in, dx1, dt, gthr, eps_ph, Pconv;
     float af, dx1f, dtf;
     float junit, jinv;  // J^r A_r per fixed-point unit of the line current, and its inverse
+    // per-particle work kept off the FP64 pipe: r_i in FP32, the FP32 screen of
+    // the emission threshold, the conversion probability as a 53-bit integer
+    // threshold (bits < ceil(P 2^53) exactly when the uniform is below P)
+    const float *rcolf;
+    float gthr2s;
+    uint64_t pconv53;
     int n_iter;
     float qm[4], qw[4];
     int massive[4];
@@ -78,6 +84,16 @@ __device__ __forceinline__ void ginv64(double a, double r, double s, double c, d
     grr = (a * a + r * r) * ir - z / (1.0 + z);
     grp = a * ir;
     gpp = ir / (s * s);
+}
+
+// round(c) as a 64-bit integer for |c| <= 2^32 without a 64-bit conversion
+// (those run on the FP64 pipe): c = hi 2^16 + lo with hi = trunc(c / 2^16),
+// lo = c - hi 2^16 exact in FP32, then two 32-bit conversions
+__device__ __forceinline__ long long fixed_units(float c)
+{
+    const float hi = truncf(c * (1.0f / 65536.0f));
+    const float lo = fmaf(hi, -65536.0f, c);
+    return ((long long)__float2int_rz(hi) << 16) + (long long)__float2int_rn(lo);
 }
 
 __device__ __forceinline__ float W1f(float d)
@@ -209,7 +225,7 @@ __device__ __forceinline__ void b1_body(const B1Args &A)
                 if (idx < hi && !(tg & DEAD) && ci >= 0 && ci < n) {
                     const int sp = tg & 3u;
                     const bool massive = A.massive[sp] != 0, charged = A.qm[sp] != 0.0f;
-                    const float rcf = (float)A.rcol[ci];
+                    const float rcf = A.rcolf[ci];
                     const float d0 = rcf * expm1f(o * A.dx1f);  // r - r_i
                     if (massive && charged) {
                         // electric part of the Boris step along the line
@@ -256,7 +272,7 @@ __device__ __forceinline__ void b1_body(const B1Args &A)
                                     int face = ci - 1 + w;
                                     if (acc != 0.0f && face >= -1 && face <= n)
                                         atomicAdd(reinterpret_cast<unsigned long long *>(&sJ[face + 1]),
-                                                  (unsigned long long)__float2ll_rn(cq * acc * A.jinv));
+                                                  (unsigned long long)fixed_units(cq * acc * A.jinv));
                                 }
                             }
                             int ni = ci + di;
@@ -271,12 +287,12 @@ __device__ __forceinline__ void b1_body(const B1Args &A)
                                 // FP64 decisions at the new position
                                 if (massive && charged) {
                                     // FP32 screen, FP64 decision inside the ambiguity band
-                                    float rf = (float)A.rcol[ci] * (1.0f + expm1f(o * A.dx1f));
+                                    float rf = A.rcolf[ci] * (1.0f + expm1f(o * A.dx1f));
                                     float rho2 = rf * rf + A.af * A.af * cf * cf, ir = 1.0f / rho2, z = 2.0f * rf * ir;
                                     float gr = (A.af * A.af + rf * rf) * ir - z / (1.0f + z), gp = A.af * ir,
                                           gq = ir / (sf * sf);
                                     float G2 = 1.0f + gr * ur * ur + 2.0f * gp * ur * up + gq * up * up;
-                                    if (G2 >= (float)(A.gthr * A.gthr) * 0.9999f) {
+                                    if (G2 >= A.gthr2s) {
                                         double rd = A.rcol[ci] * exp((double)o * A.dx1), grr, grp, gpp;
                                         ginv64(A.a, rd, sd, cd, grr, grp, gpp);
                                         double urd = ur, upd = up;
@@ -299,14 +315,14 @@ __device__ __forceinline__ void b1_body(const B1Args &A)
                                     // the draw first: it fails for all but ~tau dt of the
                                     // photons, which then skip the FP64 energy (the same
                                     // decision: both conditions must hold)
-                                    const double u = uniform53(A.seed, pid, step, 1);
+                                    const bool hit = uniform53_bits(A.seed, pid, step, 1) < A.pconv53;
                                     double e = 0.0, urd = ur, upd = up;
-                                    if (u < A.Pconv) {
+                                    if (hit) {
                                         double rd = A.rcol[ci] * exp((double)o * A.dx1), grr, grp, gpp;
                                         ginv64(A.a, rd, sd, cd, grr, grp, gpp);
                                         e = sqrt(grr * urd * urd + 2.0 * grp * urd * upd + gpp * upd * upd);
                                     }
-                                    if (e > 2.0 && u < A.Pconv) {
+                                    if (e > 2.0 && hit) {
                                         double s = sqrt(0.25 * e * e - 1.0) / e;
                                         for (int w = 0; w < 2; ++w) {
                                             kid[w].cell = ci;
@@ -521,6 +537,7 @@ __global__ void b1_fields_kernel(int nl, int n, double a, double r_in, double dx
 struct grpic_batch1d_ctx {
     grpic_batch1d_params p;
     double *rcol;
+    float *rcolf;
     float *Ar;
     int32_t *order, *queue;
     int *status;
@@ -576,6 +593,9 @@ B1Args make_args(grpic_batch1d_ctx *c, grpic_lines *L, int nsteps, int64_t step0
     const double unit = qmax > 0.0 ? qmax / p.dt * std::ldexp(1.0, -32) : 1.0;
     A.junit = (float)unit;
     A.jinv = (float)(1.0 / unit);
+    A.rcolf = c->rcolf;
+    A.gthr2s = (float)(p.gamma_thr * p.gamma_thr) * 0.9999f;
+    A.pconv53 = (uint64_t)std::ceil(A.Pconv * 9007199254740992.0);
     A.theta = L->theta;
     A.I0 = L->I0;
     A.D = L->D;
@@ -685,6 +705,7 @@ grpic_status grpic_batch1d_init(const grpic_batch1d_params *p, grpic_batch1d_ctx
     c->smem = sizeof(long long) * ((size_t)n + 2) + sizeof(float) * 2 * (size_t)n + sizeof(int) * 48;
     size_t ns = (size_t)p->n_lines * c->Cs;
     cudaError_t e = cudaMalloc(&c->rcol, sizeof(double) * (n + 1));
+    if (e == cudaSuccess) e = cudaMalloc(&c->rcolf, sizeof(float) * (n + 1));
     if (e == cudaSuccess) e = cudaMalloc(&c->Ar, sizeof(float) * (size_t)p->n_lines * n);
     if (e == cudaSuccess) e = cudaMalloc(&c->order, sizeof(int32_t) * p->n_lines);
     if (e == cudaSuccess) e = cudaMalloc(&c->queue, sizeof(int32_t) * 4);
@@ -706,6 +727,8 @@ grpic_status grpic_batch1d_init(const grpic_batch1d_params *p, grpic_batch1d_ctx
     double dx1 = std::log(p->r_out / p->r_in) / n;
     for (int i = 0; i <= n; ++i) r[i] = p->r_in * std::exp(i * dx1);
     cudaMemcpy(c->rcol, r.data(), sizeof(double) * (n + 1), cudaMemcpyHostToDevice);
+    std::vector<float> rf(r.begin(), r.end());
+    cudaMemcpy(c->rcolf, rf.data(), sizeof(float) * (n + 1), cudaMemcpyHostToDevice);
     cudaMemset(c->status, 0, sizeof(int) * 4);
     // default launch shape until the tuner picks one
     c->block = 256;
@@ -876,7 +899,7 @@ void grpic_batch1d_destroy(grpic_batch1d_ctx *c)
     if (!c) return;
     if (c->gexec) cudaGraphExecDestroy(c->gexec);
     if (c->graph) cudaGraphDestroy(c->graph);
-    void *ptrs[] = {c->rcol, c->Ar, c->order, c->queue, c->status, c->s_cell,
+    void *ptrs[] = {c->rcol, c->rcolf, c->Ar, c->order, c->queue, c->status, c->s_cell,
                     c->s_off, c->s_ur, c->s_up, c->s_tag, c->s_id};
     for (void *q : ptrs)
         if (q) cudaFree(q);

@@ -27,12 +27,19 @@ __device__ __forceinline__ void philox4x64_10(uint64_t c[4], uint64_t k0, uint64
     }
 }
 
-// uniform in [0, 1) from counter (id, step, event, 0) and key (seed, 0)
-__device__ __forceinline__ double uniform53(uint64_t seed, uint64_t id, int64_t step, int event)
+// the top 53 bits of the first output word for counter (id, step, event, 0)
+// and key (seed, 0)
+__device__ __forceinline__ uint64_t uniform53_bits(uint64_t seed, uint64_t id, int64_t step, int event)
 {
     uint64_t c[4] = {id, (uint64_t)step, (uint64_t)event, 0ULL};
     philox4x64_10(c, seed, 0ULL);
-    return (double)(c[0] >> 11) * (1.0 / 9007199254740992.0);
+    return c[0] >> 11;
+}
+
+// uniform in [0, 1): those bits times 2^-53
+__device__ __forceinline__ double uniform53(uint64_t seed, uint64_t id, int64_t step, int event)
+{
+    return (double)uniform53_bits(seed, id, step, event) * (1.0 / 9007199254740992.0);
 }
 
 __device__ __forceinline__ uint64_t splitmix64(uint64_t x)
