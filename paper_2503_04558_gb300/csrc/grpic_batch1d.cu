@@ -102,7 +102,10 @@ __device__ __forceinline__ float W1f(float d)
     return d < 1.0f ? 1.0f - d : 0.0f;
 }
 
-// block-wide exclusive scan of one int per thread; returns the total
+// block-wide exclusive scan of one int per thread; returns the total.  No
+// barrier after the totals are read: successive calls alternate between two
+// wsum buffers (a warp can start the call after next only once every thread
+// has passed the next call's first barrier, so this call's buffer is free)
 __device__ __forceinline__ int block_scan(int v, int *wsum, int &excl)
 {
     int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
@@ -127,9 +130,7 @@ __device__ __forceinline__ int block_scan(int v, int *wsum, int &excl)
     }
     __syncthreads();
     excl = wsum[warp] + x - v;
-    int total = wsum[32];
-    __syncthreads();
-    return total;
+    return wsum[32];
 }
 
 struct Kid {
@@ -152,8 +153,8 @@ __device__ __forceinline__ void b1_body(const B1Args &A)
     long long *sJ = reinterpret_cast<long long *>(smem);
     float *sD = reinterpret_cast<float *>(sJ + n + 2);
     float *sA = sD + n;
-    int *wsum = (int *)(sA + n);             // 33 ints
-    int *sv = wsum + 34;                     // [0] line, [3] emitted, [4] converted, [5] pushed,
+    int *wsum = (int *)(sA + n);             // two scan buffers of 33 ints (34 apart)
+    int *sv = wsum + 68;                     // [0] line, [3] emitted, [4] converted, [5] pushed,
                                              // [6] survivors, [7] children of this CTA
     const int tid = threadIdx.x, B = blockDim.x;
     const int rank = CL > 1 ? (int)cg::this_cluster().block_rank() : 0;
@@ -342,7 +343,7 @@ __device__ __forceinline__ void b1_body(const B1Args &A)
                 }
                 // placement: survivors in order, children in parent order
                 int excl;
-                int tot = block_scan((alive ? 1 : 0) | (napp << 16), wsum, excl);
+                int tot = block_scan((alive ? 1 : 0) | (napp << 16), wsum + (((cb - lo) / B) & 1) * 34, excl);
                 if (alive) {
                     size_t d = base + lo + wp + (excl & 0xffff);
                     A.cell[dst][d] = ci;
@@ -702,7 +703,7 @@ grpic_status grpic_batch1d_init(const grpic_batch1d_params *p, grpic_batch1d_ctx
     int dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, dev);
-    c->smem = sizeof(long long) * ((size_t)n + 2) + sizeof(float) * 2 * (size_t)n + sizeof(int) * 48;
+    c->smem = sizeof(long long) * ((size_t)n + 2) + sizeof(float) * 2 * (size_t)n + sizeof(int) * 80;
     size_t ns = (size_t)p->n_lines * c->Cs;
     cudaError_t e = cudaMalloc(&c->rcol, sizeof(double) * (n + 1));
     if (e == cudaSuccess) e = cudaMalloc(&c->rcolf, sizeof(float) * (n + 1));
