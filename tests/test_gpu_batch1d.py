@@ -146,9 +146,12 @@ def test_many_steps_track_the_oracle_statistically(G):
         assert abs((tg == 3).sum() - (S.view()["tag"] == 3).sum()) <= 0.1 * max(1, (S.view()["tag"] == 3).sum()) + 10
 
 
-def test_capacity_overflow_is_reported(G):
+@pytest.mark.parametrize("shape", [None, (128, 2, 2)], ids=["one_cta_per_line", "cluster_of_two"])
+def test_capacity_overflow_is_reported(G, shape):
     from paper_2503_04558_gb300 import grpic as GG
     cfg, B, L, lines, thetas = setup(G, nl=2, species=3, ur_scale=8.0, tau=1e4, cap=2000, per_line=(1900, 2000))
+    if shape:
+        B.set_launch(*shape)
     B.run(L, 1, 0)
     assert B.sync() == GG.EOVERFLOW
     assert int(L.count.max().item()) <= cfg.capacity
