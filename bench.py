@@ -72,7 +72,7 @@ B1_ALG_B = 2 * 28
 # cubic shape, the FP64 push with photon emission and conversion decisions
 VAY32_FP32_FLOP = 1158.0    # profiles/push32_vay_1024x1024_64ppc.md
 VAY32_INST = 1925.0
-CUBIC64_FP64_FLOP = 1978.0  # profiles/push64_cubic_512x512_64ppc.md
+CUBIC64_FP64_FLOP = 1772.0  # profiles/push64_cubic_512x512_64ppc.md
 RAD64_FP64_FLOP = 1685.0    # profiles/push64_rad_512x512_16ppc.md
 # ALU peaks from unit counts x clock: 152 SMs x 2.07 GHz x (4 FP64 flops,
 # 256 FP32 flops) per SM per clock; instruction issue: 4 schedulers x 1 warp

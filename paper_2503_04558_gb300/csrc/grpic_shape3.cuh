@@ -30,6 +30,45 @@ __device__ __forceinline__ double w3(double d)
     return 0.0;
 }
 
+// the four weights W3(t + 1), W3(t), W3(t - 1), W3(t - 2) of the taps at
+// floor(x) - 1 .. floor(x) + 2 for t = x - floor(x) in [0, 1), without branches:
+// (1-t)^3/6, 2/3 - t^2 + t^3/2, 2/3 - (1-t)^2 + (1-t)^3/2, t^3/6
+__device__ __forceinline__ void w3_taps(double t, double w[4])
+{
+    const double u = 1.0 - t, t2 = t * t, u2 = u * u;
+    w[0] = u2 * u * (1.0 / 6.0);
+    w[1] = 2.0 / 3.0 - t2 + 0.5 * t2 * t;
+    w[2] = 2.0 / 3.0 - u2 + 0.5 * u2 * u;
+    w[3] = t2 * t * (1.0 / 6.0);
+}
+
+// one lattice's taps at a point: the first tap index floor(x) - 1 and the weights
+struct Taps3 {
+    int i;
+    double w[4];
+};
+__device__ __forceinline__ void taps3(double x, Taps3 &T)
+{
+    const double f = floor(x);
+    T.i = (int)f - 1;
+    w3_taps(x - f, T.w);
+}
+
+// W3(x - (b + k)) for k = 0..4: the taps placed in a window starting at b
+// (taps that fall outside the window carry W3 = 0 there, as their distance
+// is 2 or more)
+__device__ __forceinline__ void w3_window5(double x, int b, double S[5])
+{
+    Taps3 T;
+    taps3(x, T);
+    const int o = T.i - b;  // window position of the first tap
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+        const int a = k - o;
+        S[k] = a == 0 ? T.w[0] : (a == 1 ? T.w[1] : (a == 2 ? T.w[2] : (a == 3 ? T.w[3] : 0.0)));
+    }
+}
+
 // mirror of row j (integer rows theta_j, or half rows theta_{j+1/2})
 __device__ __forceinline__ int mirror_row(int j, bool half_t, int nth, bool &flip)
 {
@@ -46,42 +85,42 @@ __device__ __forceinline__ int mirror_row(int j, bool half_t, int nth, bool &fli
     return j;
 }
 
-// field component on its lattice (staggered by sr in r, half rows if half_t;
-// par = the parity across the axis) at logical (x1, x2)
-__device__ __forceinline__ double gather3(const double *__restrict__ F, int64_t ld, int nth, double x1, double x2,
-                                          double sr, bool half_t, double par)
+// a component from its lattice's taps in r (R) and theta (T)
+__device__ __forceinline__ double gather3t(const double *__restrict__ F, int64_t ld, int nth, const Taps3 &R,
+                                           const Taps3 &T, bool half_t, double par)
 {
-    const double xi = x1 - sr, eta = x2 - (half_t ? 0.5 : 0.0);
-    const int i = (int)floor(xi), j = (int)floor(eta);
-    double wr[4];
-#pragma unroll
-    for (int a = 0; a < 4; ++a) wr[a] = w3(xi - (i - 1 + a));
     double v = 0.0;
 #pragma unroll
     for (int b = 0; b < 4; ++b) {
         bool flip;
-        const int jj = mirror_row(j - 1 + b, half_t, nth, flip);
-        const double wt = w3(eta - (j - 1 + b)) * (flip ? par : 1.0);
-        const double *row = F + (size_t)jj * ld + (i - 1 + NG);
+        const int jj = mirror_row(T.i + b, half_t, nth, flip);
+        const double *row = F + (size_t)jj * ld + (R.i + NG);
         double s = 0.0;
 #pragma unroll
-        for (int a = 0; a < 4; ++a) s += wr[a] * __ldg(row + a);
-        v += wt * s;
+        for (int a = 0; a < 4; ++a) s += R.w[a] * __ldg(row + a);
+        v += T.w[b] * (flip ? par : 1.0) * s;
     }
     return v;
 }
 
-// the six fields at the particle (D^r, D^th, D^ph, B^r, B^th, B^ph)
+// the six fields at the particle (D^r, D^th, D^ph, B^r, B^th, B^ph); the
+// components share two r lattices (integer, half) and two theta lattices, so
+// four tap sets serve all six
 __device__ __forceinline__ void gather3_fields(const double *D0, const double *D1, const double *D2, const double *B0,
                                                const double *B1, const double *B2, int64_t ld, int nth, double x1,
                                                double x2, double Dv[3], double Bv[3])
 {
-    Dv[0] = gather3(D0, ld, nth, x1, x2, 0.5, false, 1.0);
-    Dv[1] = gather3(D1, ld, nth, x1, x2, 0.0, true, -1.0);
-    Dv[2] = gather3(D2, ld, nth, x1, x2, 0.0, false, 1.0);
-    Bv[0] = gather3(B0, ld, nth, x1, x2, 0.0, true, 1.0);
-    Bv[1] = gather3(B1, ld, nth, x1, x2, 0.5, false, -1.0);
-    Bv[2] = gather3(B2, ld, nth, x1, x2, 0.5, true, 1.0);
+    Taps3 r0, rh, t0, th;
+    taps3(x1, r0);
+    taps3(x1 - 0.5, rh);
+    taps3(x2, t0);
+    taps3(x2 - 0.5, th);
+    Dv[0] = gather3t(D0, ld, nth, rh, t0, false, 1.0);
+    Dv[1] = gather3t(D1, ld, nth, r0, th, true, -1.0);
+    Dv[2] = gather3t(D2, ld, nth, r0, t0, false, 1.0);
+    Bv[0] = gather3t(B0, ld, nth, r0, th, true, 1.0);
+    Bv[1] = gather3t(B1, ld, nth, rh, t0, false, -1.0);
+    Bv[2] = gather3t(B2, ld, nth, rh, th, true, 1.0);
 }
 
 __device__ __forceinline__ void fold_add3(double *F, int64_t ld, int nr, int nth, int i, int j, bool half_t, double odd,
@@ -104,13 +143,10 @@ __device__ __forceinline__ void deposit3(int nr, int nth, int64_t ld, double *J0
     const int ga = (int)floor(x2a), gb = (int)floor(x2b);
     const int b2 = (ga < gb ? ga : gb) - 1;
     double S0r[5], S1r[5], S0t[5], S1t[5];
-#pragma unroll
-    for (int k = 0; k < 5; ++k) {
-        S0r[k] = w3(x1a - (b1 + k));
-        S1r[k] = w3(x1b - (b1 + k));
-        S0t[k] = w3(x2a - (b2 + k));
-        S1t[k] = w3(x2b - (b2 + k));
-    }
+    w3_window5(x1a, b1, S0r);
+    w3_window5(x1b, b1, S1r);
+    w3_window5(x2a, b2, S0t);
+    w3_window5(x2b, b2, S1t);
     const double cr = -qw / (2.0 * dt), cp = qw * dphi / dt;
     // J^r A at faces b1 + k + 1/2 (k = 0..3): prefix sums of (S1r - S0r) (S1t + S0t)
     double Pr = 0.0;
