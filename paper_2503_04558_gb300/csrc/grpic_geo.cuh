@@ -129,4 +129,41 @@ __device__ __forceinline__ void geo_rhs_m(const KSGeo<M> &m, T eps, T ur, T ut, 
            h * (ur * ur * (T)m.dgrr_t + T(2) * ur * up * (T)m.dgrp_t + ut * ut * (T)m.dgtt_t + up * up * (T)m.dgpp_t);
 }
 
+// X^i, U_i of Eq. particle-eom from (r, sin theta, cos theta) without the
+// metric's derivatives as separate fields: gamma^{jk} = rho^-2 [(a^2 + r^2,
+// a, 1, 1/sin^2) in (rr, r phi, th th, phi phi)] - beta dr dr, so with
+// P = (a^2 + r^2) u_r^2 + 2 a u_r u_ph + u_th^2 + u_ph^2 / sin^2 the forms in u
+// collect into gamma^{jk} u_j u_k = P / rho^2 - beta u_r^2,
+// d_r gamma^{jk} u_j u_k = u_r^2 (z - d_r beta) - 2 r P / rho^4 and
+// d_th gamma^{jk} u_j u_k = -d_th rho^2 P / rho^4 - d_th beta u_r^2
+//                           - 2 sin cos u_ph^2 / (rho^2 sin^4)
+template <typename T>
+__device__ __forceinline__ void geo_rhs_direct(T a, T eps, T r, T s, T c, T ur, T ut, T up, RhsT<T> &f)
+{
+    const T a2 = a * a, r2 = r * r;
+    const T ir = rcp_t(r2 + a2 * c * c);
+    const T ir2 = ir * ir;
+    const T z = T(2) * r * ir;
+    const T iopz = rcp_t(T(1) + z);
+    const T alpha = sqrt_t(iopz);
+    const T beta = z * iopz;
+    const T is2 = rcp_t(s * s);
+    const T drho_t = T(-2) * a2 * c * s;
+    const T dz_r = T(2) * ir * (T(1) - T(2) * r2 * ir);
+    const T dz_t = T(-2) * r * drho_t * ir2;
+    const T ka = T(-0.5) * alpha * iopz, kb = iopz * iopz;
+    const T db_r = kb * dz_r, db_t = kb * dz_t;
+    const T ur2 = ur * ur, up2 = up * up;
+    const T P = (a2 + r2) * ur2 + T(2) * a * ur * up + ut * ut + up2 * is2;
+    const T au0 = sqrt_t(eps + ir * P - beta * ur2);  // alpha u^0
+    const T iu0 = alpha * rcp_t(au0);
+    const T grp = a * ir;
+    f.xr = (((a2 + r2) * ir - beta) * ur + grp * up) * iu0 - beta;
+    f.xt = ir * ut * iu0;
+    f.xp = (grp * ur + ir * is2 * up) * iu0;
+    const T h = T(0.5) * iu0;
+    f.ur = -au0 * ka * dz_r + ur * db_r - h * (ur2 * (z - db_r) - T(2) * r * ir2 * P);
+    f.ut = -au0 * ka * dz_t + ur * db_t - h * (-drho_t * ir2 * P - db_t * ur2 - T(2) * s * c * ir * is2 * is2 * up2);
+}
+
 }  // namespace grpic

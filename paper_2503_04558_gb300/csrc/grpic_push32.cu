@@ -303,9 +303,13 @@ __device__ __forceinline__ void push_one(const Push32Args &A, int i, int j, floa
                 sincosf(((float)j + o2) * A.dthf + d, &s, &c);
             ri = rcf + a1;
         }
-        KSGeo<M> mi;
-        ks_geo_sc<M>(am, ri, s, c, mi);
-        geo_rhs_m<M, float>(mi, eps, b1, b2, u[2], ft);
+        if constexpr (std::is_same<M, float>::value) {
+            geo_rhs_direct<float>(am, eps, ri, s, c, b1, b2, u[2], ft);
+        } else {
+            KSGeo<M> mi;
+            ks_geo_sc<M>(am, ri, s, c, mi);
+            geo_rhs_m<M, float>(mi, eps, b1, b2, u[2], ft);
+        }
         ft.xt *= idth;
         float n1 = d0 + h * (ft.xr + f0.xr), n2 = o2 + h * (ft.xt + f0.xt);
         float nb1 = u[0] + h * (ft.ur + f0.ur), nb2 = u[1] + h * (ft.ut + f0.ut);

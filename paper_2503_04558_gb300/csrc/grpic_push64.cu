@@ -84,7 +84,6 @@ __device__ __forceinline__ void geo_rhs_sc(double a, double eps, double r, doubl
     double alpha = sqrt(iopz);
     double beta = z * iopz;
     double is2 = rcp_t(s * s);
-    double grr = (a2 + r2) * ir - beta, grp = a * ir, gtt = ir, gpp = ir * is2;
     double drho_t = -2.0 * a2 * c * s;
     double dz_r = 2.0 * ir * (1.0 - 2.0 * r2 * ir);
     double dz_t = -2.0 * r * drho_t * ir2;
@@ -92,22 +91,28 @@ __device__ __forceinline__ void geo_rhs_sc(double a, double eps, double r, doubl
     double kb = iopz * iopz;          // d beta / dz
     double da_r = ka * dz_r, da_t = ka * dz_t;
     double db_r = kb * dz_r, db_t = kb * dz_t;
-    double dgrr_r = 2.0 * r * ir - (a2 + r2) * 2.0 * r * ir2 - db_r;
-    double dgrr_t = -(a2 + r2) * drho_t * ir2 - db_t;
-    double dgrp_r = -a * 2.0 * r * ir2, dgrp_t = -a * drho_t * ir2;
-    double dgtt_r = -2.0 * r * ir2, dgtt_t = -drho_t * ir2;
-    double dgpp_r = -2.0 * r * ir2 * is2;
-    double dgpp_t = -drho_t * ir2 * is2 - 2.0 * s * c * ir * is2 * is2;
-
-    double uu = grr * ur * ur + 2.0 * grp * ur * up + gtt * ut * ut + gpp * up * up;
+    // gamma^{jk} = rho^-2 [(a^2 + r^2, a, 1, 1/sin^2) in (rr, r phi, th th,
+    // phi phi)] - beta dr dr, so with P = (a^2 + r^2) u_r^2 + 2 a u_r u_ph
+    // + u_th^2 + u_ph^2 / sin^2 the forms in u of gamma^{jk} and of its r and
+    // theta derivatives collect into
+    //   gamma^{jk} u_j u_k        = P / rho^2 - beta u_r^2,
+    //   d_r gamma^{jk} u_j u_k    = u_r^2 (z - d_r beta) - 2 r P / rho^4,
+    //   d_th gamma^{jk} u_j u_k   = -d_th rho^2 P / rho^4 - d_th beta u_r^2
+    //                               - 2 sin cos u_ph^2 / (rho^2 sin^4)
+    double ur2 = ur * ur, up2 = up * up;
+    double P = (a2 + r2) * ur2 + 2.0 * a * ur * up + ut * ut + up2 * is2;
+    double uu = ir * P - beta * ur2;
     double au0 = sqrt(eps + uu);   // alpha u^0
     double iu0 = alpha * rcp_t(au0);  // 1 / u^0
-    f.xr = (grr * ur + grp * up) * iu0 - beta;
-    f.xt = gtt * ut * iu0;
-    f.xp = (grp * ur + gpp * up) * iu0;
+    double grp = a * ir;
+    f.xr = (((a2 + r2) * ir - beta) * ur + grp * up) * iu0 - beta;
+    f.xt = ir * ut * iu0;
+    f.xp = (grp * ur + ir * is2 * up) * iu0;
     double h = 0.5 * iu0;
-    f.ur = -au0 * da_r + ur * db_r - h * (ur * ur * dgrr_r + 2.0 * ur * up * dgrp_r + ut * ut * dgtt_r + up * up * dgpp_r);
-    f.ut = -au0 * da_t + ur * db_t - h * (ur * ur * dgrr_t + 2.0 * ur * up * dgrp_t + ut * ut * dgtt_t + up * up * dgpp_t);
+    double Qr = ur2 * (z - db_r) - 2.0 * r * ir2 * P;
+    double Qt = -drho_t * ir2 * P - db_t * ur2 - 2.0 * s * c * ir * is2 * is2 * up2;
+    f.ur = -au0 * da_r + ur * db_r - h * Qr;
+    f.ut = -au0 * da_t + ur * db_t - h * Qt;
 }
 
 // the 3+1 metric at (r, theta) from sin, cos of theta (reciprocals by the
