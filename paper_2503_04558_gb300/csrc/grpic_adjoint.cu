@@ -250,6 +250,139 @@ __device__ void rhs_vjp(double a, double eps, const double y[5], double sv, doub
     out[4] = L_up;
 }
 
+// The same vector-Jacobian product for the right-hand side written as the
+// push evaluates it: with P = (a^2 + r^2) u_r^2 + 2 a u_r u_ph + u_th^2 +
+// u_ph^2 / sin^2,  u.u = P / rho^2 - beta u_r^2,  X^r = (g^rr u_r + g^rph u_ph)
+// / u^0 - beta,  Q_r = u_r^2 (z - d_r beta) - 2 r P / rho^4,  Q_th = -d_th rho^2
+// P / rho^4 - d_th beta u_r^2 - 2 sin cos u_ph^2 / (rho^2 sin^4),  U_i =
+// -alpha u^0 d_i alpha + u_r d_i beta - Q_i / (2 u^0).  The reverse pass runs
+// through those formulas; the r, theta (and a) derivatives of the thirteen
+// metric quantities they use come from dual numbers.  sv, cv = sin, cos y[1].
+template <int ND>
+__device__ void rhs_vjp_p(double a, double eps, const double y[5], double sv, double cv, const double w[5], double wp,
+                          double out[5], double *out_a = nullptr)
+{
+    typedef DN<ND> D;
+    D r(y[0]), aD(a), s(sv), c(cv);
+    r.d[0] = 1.0;
+    s.d[1] = cv;
+    c.d[1] = -sv;
+    if constexpr (ND > 2) aD.d[2] = 1.0;
+    // metric quantities (dual)
+    const D a2 = aD * aD, r2 = r * r;
+    const D A2 = a2 + r2;
+    const D ir = rcp_t(r2 + a2 * c * c);
+    const D ir2 = ir * ir;
+    const D z = D(2.0) * r * ir;
+    const D iopz = rcp_t(D(1.0) + z);
+    const D alphaD = sqrt_t(iopz);
+    const D betaD = z * iopz;
+    const D is2 = rcp_t(s * s);
+    const D drho_t = D(-2.0) * a2 * c * s;
+    const D dz_r = D(2.0) * ir * (D(1.0) - D(2.0) * r2 * ir);
+    const D dz_t = D(-2.0) * r * drho_t * ir2;
+    const D ka = D(-0.5) * alphaD * iopz, kb = iopz * iopz;
+    const D da_r = ka * dz_r, da_t = ka * dz_t, db_r = kb * dz_r, db_t = kb * dz_t;
+    const D M2 = D(2.0) * r * ir2, M3 = drho_t * ir2, M4 = D(2.0) * s * c * ir * is2 * is2;
+    // forward values
+    const double ur = y[2], ut = y[3], up = y[4];
+    const double vA2 = A2.v, vir = ir.v, vbe = betaD.v, val = alphaD.v, vis2 = is2.v, vz = z.v;
+    const double ur2 = ur * ur, up2 = up * up;
+    const double P = vA2 * ur2 + 2.0 * a * ur * up + ut * ut + vis2 * up2;
+    const double uu = vir * P - vbe * ur2;
+    const double au0 = sqrt_t(eps + uu);
+    const double iau = rcp_t(au0);
+    const double iu0 = val * iau, h = 0.5 * iu0;
+    const double G1 = vA2 * vir - vbe, G2 = a * vir;
+    const double Qr = ur2 * (vz - db_r.v) - M2.v * P;
+    const double Qt = -M3.v * P - db_t.v * ur2 - M4.v * up2;
+    // reverse; adjoints of the outputs X^r, X^th, U_r, U_th, X^ph
+    const double Lxr = w[0], Lxt = w[1], Lur = w[2], Lut = w[3], Lxp = wp;
+    double L_ur = 0.0, L_ut = 0.0, L_up = 0.0, L_a = 0.0;
+    double L_A2 = 0.0, L_ir = 0.0, L_be = 0.0, L_al = 0.0, L_is2 = 0.0, L_z = 0.0;
+    double L_dar = 0.0, L_dat = 0.0, L_dbr = 0.0, L_dbt = 0.0, L_M2 = 0.0, L_M3 = 0.0, L_M4 = 0.0;
+    double L_au0 = 0.0, L_iu0 = 0.0, L_P = 0.0;
+    // U_r = -au0 da_r + ur db_r - h Qr,  U_th likewise
+    L_au0 -= Lur * da_r.v + Lut * da_t.v;
+    L_dar -= Lur * au0;
+    L_dat -= Lut * au0;
+    L_dbr += Lur * ur;
+    L_dbt += Lut * ur;
+    L_ur += Lur * db_r.v + Lut * db_t.v;
+    const double L_h = -Lur * Qr - Lut * Qt;
+    const double L_Qr = -Lur * h, L_Qt = -Lut * h;
+    // Qr = ur^2 (z - db_r) - M2 P
+    L_ur += L_Qr * 2.0 * ur * (vz - db_r.v);
+    L_z += L_Qr * ur2;
+    L_dbr -= L_Qr * ur2;
+    L_M2 -= L_Qr * P;
+    L_P -= L_Qr * M2.v;
+    // Qt = -M3 P - db_t ur^2 - M4 up^2
+    L_M3 -= L_Qt * P;
+    L_P -= L_Qt * M3.v;
+    L_dbt -= L_Qt * ur2;
+    L_ur -= L_Qt * 2.0 * db_t.v * ur;
+    L_M4 -= L_Qt * up2;
+    L_up -= L_Qt * 2.0 * M4.v * up;
+    // h = iu0 / 2
+    L_iu0 += 0.5 * L_h;
+    // X^r = (G1 ur + G2 up) iu0 - beta, G1 = A2 ir - beta, G2 = a ir
+    L_iu0 += Lxr * (G1 * ur + G2 * up);
+    L_ur += Lxr * G1 * iu0;
+    L_up += Lxr * G2 * iu0;
+    L_A2 += Lxr * ur * iu0 * vir;
+    L_ir += Lxr * iu0 * (ur * vA2 + a * up);
+    L_be -= Lxr * (ur * iu0 + 1.0);
+    L_a += Lxr * vir * up * iu0;
+    // X^th = ir ut iu0
+    L_iu0 += Lxt * vir * ut;
+    L_ut += Lxt * vir * iu0;
+    L_ir += Lxt * ut * iu0;
+    // X^ph = (a ir ur + ir is2 up) iu0
+    L_iu0 += Lxp * (a * vir * ur + vir * vis2 * up);
+    L_ur += Lxp * a * vir * iu0;
+    L_up += Lxp * vir * vis2 * iu0;
+    L_ir += Lxp * (a * ur + vis2 * up) * iu0;
+    L_is2 += Lxp * vir * up * iu0;
+    L_a += Lxp * vir * ur * iu0;
+    // iu0 = alpha / au0, au0 = sqrt(eps + uu)
+    L_al += L_iu0 * iau;
+    L_au0 -= L_iu0 * val * iau * iau;
+    const double L_uu = 0.5 * L_au0 * iau;
+    // uu = ir P - beta ur^2
+    L_ir += L_uu * P;
+    L_P += L_uu * vir;
+    L_be -= L_uu * ur2;
+    L_ur -= L_uu * 2.0 * vbe * ur;
+    // P = A2 ur^2 + 2 a ur up + ut^2 + is2 up^2
+    L_A2 += L_P * ur2;
+    L_ur += L_P * (2.0 * vA2 * ur + 2.0 * a * up);
+    L_up += L_P * (2.0 * a * ur + 2.0 * vis2 * up);
+    L_ut += L_P * 2.0 * ut;
+    L_is2 += L_P * up2;
+    L_a += L_P * 2.0 * ur * up;
+    // metric quantities -> r, theta (and a)
+    const D *q[13] = {&A2, &ir, &betaD, &alphaD, &is2, &z, &da_r, &da_t, &db_r, &db_t, &M2, &M3, &M4};
+    const double Lq[13] = {L_A2, L_ir, L_be, L_al, L_is2, L_z, L_dar, L_dat, L_dbr, L_dbt, L_M2, L_M3, L_M4};
+    double Lr = 0.0, Lth = 0.0;
+#pragma unroll
+    for (int k = 0; k < 13; ++k) {
+        Lr += Lq[k] * q[k]->d[0];
+        Lth += Lq[k] * q[k]->d[1];
+    }
+    if constexpr (ND > 2) {
+        double La = L_a;
+#pragma unroll
+        for (int k = 0; k < 13; ++k) La += Lq[k] * q[k]->d[2];
+        *out_a += La;
+    }
+    out[0] = Lr;
+    out[1] = Lth;
+    out[2] = L_ur;
+    out[3] = L_ut;
+    out[4] = L_up;
+}
+
 // lo^T d(u')/dz for the generalized Boris step (Eqs. boris-plus-minus, u0bar,
 // boris-scheme) u' = u'(z), z = (r, th, u_r, u_th, u_ph, D^r, D^th, D^ph, B^r,
 // B^th, B^ph): its reverse pass written out by hand, the metric's r and theta
@@ -672,9 +805,9 @@ __global__ void __launch_bounds__(128) particle_adjoint(PAdjArgs A)
             // the a-dependence of F(y1): w . dt/2 dF/da(y1) + dt/2 ldphi dX^ph/da(y1)
             double unused[5], s1, c1;
             sincos(y1[1], &s1, &c1);
-            rhs_vjp<ND>(g.a, eps, y1, s1, c1, hw, hh * ldphi, unused, pla);
+            rhs_vjp_p<ND>(g.a, eps, y1, s1, c1, hw, hh * ldphi, unused, pla);
         }
-        rhs_vjp<ND>(g.a, eps, y0, s0, c0, hw, hh * ldphi, v0, pla);
+        rhs_vjp_p<ND>(g.a, eps, y0, s0, c0, hw, hh * ldphi, v0, pla);
         for (int k = 0; k < 5; ++k) l0[k] = w[k] + v0[k];
     } else {
         // transpose of the iteration the push runs: y~_0 = y0 + dt F(y0),
@@ -695,7 +828,7 @@ __global__ void __launch_bounds__(128) particle_adjoint(PAdjArgs A)
                 for (int k = 0; k < 5; ++k) hg[k] = hh * gk[k];
                 const double *q = T + (int64_t)(TAPE_IT + 6 * it) * tl;
                 const double yi[5] = {q[0], q[tl], q[2 * tl], q[3 * tl], y0[4]};
-                rhs_vjp<ND>(g.a, eps, yi, q[4 * tl], q[5 * tl], hg, ap, gn, pla);
+                rhs_vjp_p<ND>(g.a, eps, yi, q[4 * tl], q[5 * tl], hg, ap, gn, pla);
                 for (int k = 0; k < 5; ++k) gk[k] = gn[k];
             }
         }
@@ -704,7 +837,7 @@ __global__ void __launch_bounds__(128) particle_adjoint(PAdjArgs A)
             lF0[k] += dt * gk[k];
         }
         double v0[5];
-        rhs_vjp<ND>(g.a, eps, y0, s0, c0, lF0, lFp0, v0, pla);
+        rhs_vjp_p<ND>(g.a, eps, y0, s0, c0, lF0, lFp0, v0, pla);
         for (int k = 0; k < 5; ++k) l0[k] = ly0[k] + v0[k];
     }
     // start point: deposit's start-weight derivatives
