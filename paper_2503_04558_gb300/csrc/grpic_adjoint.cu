@@ -164,94 +164,8 @@ __device__ void rhs_jac(double a, double eps, const double y[5], double F[5], do
 }
 
 // w^T dF/dy + wp dX^ph/dy at y = (r, th, u_r, u_th, u_ph) for F = (X^r, X^th,
-// U_r, U_th, 0): the reverse pass of the right-hand side of Eq. particle-eom
-// written out by hand, with the metric quantities and their r and theta
-// derivatives from two-slot dual numbers (their second derivatives of the
-// metric come out of the same evaluation).
-// ND = 2: slots d/dr, d/dtheta; ND = 3 adds d/da (the spin gradient), whose
-// contraction with the adjoint is added to *out_a
-// sv, cv: sin and cos of y[1]
-template <int ND>
-__device__ void rhs_vjp(double a, double eps, const double y[5], double sv, double cv, const double w[5], double wp,
-                        double out[5], double *out_a = nullptr)
-{
-    DN<ND> r(y[0]), aD(a), s(sv), c(cv);
-    r.d[0] = 1.0;
-    s.d[1] = cv;
-    c.d[1] = -sv;
-    if constexpr (ND > 2) aD.d[2] = 1.0;
-    KSGeo<DN<ND>> m;
-    ks_geo_sc<DN<ND>>(aD, r, s, c, m);
-    const double ur = y[2], ut = y[3], up = y[4];
-    const double grr = m.grr.v, grp = m.grp.v, gtt = m.gtt.v, gpp = m.gpp.v, alpha = m.alpha.v;
-    // forward values
-    const double uu = grr * ur * ur + 2.0 * grp * ur * up + gtt * ut * ut + gpp * up * up;
-    const double au0 = sqrt_t(eps + uu);
-    const double iau = rcp_t(au0);
-    const double iu0 = alpha * iau;
-    const double h = 0.5 * iu0;
-    const double Qr = ur * ur * m.dgrr_r.v + 2.0 * ur * up * m.dgrp_r.v + ut * ut * m.dgtt_r.v + up * up * m.dgpp_r.v;
-    const double Qt = ur * ur * m.dgrr_t.v + 2.0 * ur * up * m.dgrp_t.v + ut * ut * m.dgtt_t.v + up * up * m.dgpp_t.v;
-    const double Lxr = w[0], Lxt = w[1], Lur = w[2], Lut = w[3], Lxp = wp;
-    // U_r = -au0 da_r + ur db_r - h Qr,  U_th likewise
-    const double Lh = -Lur * Qr - Lut * Qt;
-    const double LQr = -Lur * h, LQt = -Lut * h;
-    double Lau0 = -Lur * m.da_r.v - Lut * m.da_t.v;
-    const double Lda_r = -Lur * au0, Lda_t = -Lut * au0, Ldb_r = Lur * ur, Ldb_t = Lut * ur;
-    double L_ur = Lur * m.db_r.v + Lut * m.db_t.v;
-    double L_ut = 0.0, L_up = 0.0;
-    L_ur += LQr * (2.0 * ur * m.dgrr_r.v + 2.0 * up * m.dgrp_r.v) + LQt * (2.0 * ur * m.dgrr_t.v + 2.0 * up * m.dgrp_t.v);
-    L_up += LQr * (2.0 * ur * m.dgrp_r.v + 2.0 * up * m.dgpp_r.v) + LQt * (2.0 * ur * m.dgrp_t.v + 2.0 * up * m.dgpp_t.v);
-    L_ut += LQr * (2.0 * ut * m.dgtt_r.v) + LQt * (2.0 * ut * m.dgtt_t.v);
-    const double Ldgrr_r = LQr * ur * ur, Ldgrp_r = LQr * 2.0 * ur * up, Ldgtt_r = LQr * ut * ut,
-                 Ldgpp_r = LQr * up * up;
-    const double Ldgrr_t = LQt * ur * ur, Ldgrp_t = LQt * 2.0 * ur * up, Ldgtt_t = LQt * ut * ut,
-                 Ldgpp_t = LQt * up * up;
-    // X^r = (grr ur + grp up) iu0 - beta, X^th = gtt ut iu0, X^ph = (grp ur + gpp up) iu0
-    double Liu0 = 0.5 * Lh + Lxr * (grr * ur + grp * up) + Lxt * gtt * ut + Lxp * (grp * ur + gpp * up);
-    const double Lbeta = -Lxr;
-    double Lgrr = Lxr * ur * iu0, Lgrp = (Lxr * up + Lxp * ur) * iu0, Lgtt = Lxt * ut * iu0, Lgpp = Lxp * up * iu0;
-    L_ur += (Lxr * grr + Lxp * grp) * iu0;
-    L_up += (Lxr * grp + Lxp * gpp) * iu0;
-    L_ut += Lxt * gtt * iu0;
-    // iu0 = alpha / au0, au0 = sqrt(eps + uu)
-    const double Lalpha = Liu0 * iau;
-    Lau0 -= Liu0 * alpha * iau * iau;
-    const double Luu = 0.5 * Lau0 * iau;
-    Lgrr += Luu * ur * ur;
-    Lgrp += Luu * 2.0 * ur * up;
-    Lgtt += Luu * ut * ut;
-    Lgpp += Luu * up * up;
-    L_ur += Luu * (2.0 * grr * ur + 2.0 * grp * up);
-    L_ut += Luu * 2.0 * gtt * ut;
-    L_up += Luu * (2.0 * grp * ur + 2.0 * gpp * up);
-    // metric quantities -> r, theta
-    const DN<ND> *q[18] = {&m.grr, &m.grp, &m.gtt, &m.gpp, &m.alpha, &m.beta, &m.da_r, &m.da_t, &m.db_r,
-                          &m.db_t, &m.dgrr_r, &m.dgrr_t, &m.dgrp_r, &m.dgrp_t, &m.dgtt_r, &m.dgtt_t, &m.dgpp_r,
-                          &m.dgpp_t};
-    const double Lq[18] = {Lgrr, Lgrp, Lgtt, Lgpp, Lalpha, Lbeta, Lda_r, Lda_t, Ldb_r,
-                           Ldb_t, Ldgrr_r, Ldgrr_t, Ldgrp_r, Ldgrp_t, Ldgtt_r, Ldgtt_t, Ldgpp_r, Ldgpp_t};
-    double Lr = 0.0, Lth = 0.0;
-#pragma unroll
-    for (int k = 0; k < 18; ++k) {
-        Lr += Lq[k] * q[k]->d[0];
-        Lth += Lq[k] * q[k]->d[1];
-    }
-    if constexpr (ND > 2) {
-        double La = 0.0;
-#pragma unroll
-        for (int k = 0; k < 18; ++k) La += Lq[k] * q[k]->d[2];
-        *out_a += La;
-    }
-    out[0] = Lr;
-    out[1] = Lth;
-    out[2] = L_ur;
-    out[3] = L_ut;
-    out[4] = L_up;
-}
-
-// The same vector-Jacobian product for the right-hand side written as the
-// push evaluates it: with P = (a^2 + r^2) u_r^2 + 2 a u_r u_ph + u_th^2 +
+// U_r, U_th, 0), the right-hand side of Eq. particle-eom written as the push
+// evaluates it: with P = (a^2 + r^2) u_r^2 + 2 a u_r u_ph + u_th^2 +
 // u_ph^2 / sin^2,  u.u = P / rho^2 - beta u_r^2,  X^r = (g^rr u_r + g^rph u_ph)
 // / u^0 - beta,  Q_r = u_r^2 (z - d_r beta) - 2 r P / rho^4,  Q_th = -d_th rho^2
 // P / rho^4 - d_th beta u_r^2 - 2 sin cos u_ph^2 / (rho^2 sin^4),  U_i =
