@@ -52,8 +52,8 @@ B0 = 1.0
 # Arithmetic per particle-step of the push kernels, counted by ncu on the same
 # kernels (flop_count = 2 FMA + MUL + ADD of the SASS instruction counters;
 # the capture commands and counts are in profiles/).
-PUSH64_FP64_FLOP = 1255.0   # profiles/push64_fp64_512x512_64ppc.md
-PUSH64_DRAM_B = 96.1        # the same capture: DRAM bytes per particle (read + write)
+PUSH64_FP64_FLOP = 1216.0   # profiles/push64_fp64_512x512_64ppc.md
+PUSH64_DRAM_B = 95.8        # the same capture: DRAM bytes per particle (read + write)
 PUSH32_FP32_FLOP = 1018.5   # profiles/push32_fp32form_1024x1024_64ppc.md
 # the same capture: instructions issued per particle (warp instructions x 32)
 # and DRAM bytes per particle (read + write), scaled to a launch by the

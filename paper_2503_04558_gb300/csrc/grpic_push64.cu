@@ -72,18 +72,32 @@ struct Rhs {
 
 // Right-hand sides of Eq. particle-eom without F_i, with the analytic
 // Kerr-Schild derivatives of alpha, beta^r and gamma^{jk}.
-__device__ __forceinline__ void geo_rhs_sc(double a, double eps, double r, double s, double c, double ur, double ut,
-                                           double up, Rhs &f)
+// the metric pieces at (r, theta) that the Boris step and the right-hand side
+// share: a^2, r^2, rho^2, 1/rho^2, z = 2 r / rho^2, 1 + z, 1/(1+z), alpha =
+// (1+z)^-1/2, beta = z/(1+z), 1/sin^2
+struct KSBase {
+    double a2, r2, rho2, ir, z, opz, iopz, alpha, beta, is2;
+};
+__device__ __forceinline__ void ks_base(double a, double r, double s, double c, KSBase &b)
 {
-    double a2 = a * a, r2 = r * r;
-    double rho2 = r2 + a2 * c * c;
-    double ir = rcp_t(rho2);
+    b.a2 = a * a;
+    b.r2 = r * r;
+    b.rho2 = b.r2 + b.a2 * c * c;
+    b.ir = rcp_t(b.rho2);
+    b.z = 2.0 * r * b.ir;
+    b.opz = 1.0 + b.z;
+    b.iopz = rcp_t(b.opz);
+    b.alpha = sqrt(b.iopz);
+    b.beta = b.z * b.iopz;
+    b.is2 = rcp_t(s * s);
+}
+
+__device__ __forceinline__ void geo_rhs_b(double a, double eps, double r, double s, double c, const KSBase &B,
+                                          double ur, double ut, double up, Rhs &f)
+{
+    const double a2 = B.a2, r2 = B.r2, ir = B.ir, z = B.z, iopz = B.iopz, alpha = B.alpha, beta = B.beta,
+                 is2 = B.is2;
     double ir2 = ir * ir;
-    double z = 2.0 * r * ir;
-    double iopz = rcp_t(1.0 + z);
-    double alpha = sqrt(iopz);
-    double beta = z * iopz;
-    double is2 = rcp_t(s * s);
     double drho_t = -2.0 * a2 * c * s;
     double dz_r = 2.0 * ir * (1.0 - 2.0 * r2 * ir);
     double dz_t = -2.0 * r * drho_t * ir2;
@@ -115,38 +129,41 @@ __device__ __forceinline__ void geo_rhs_sc(double a, double eps, double r, doubl
     f.ut = -au0 * da_t + ur * db_t - h * Qt;
 }
 
+__device__ __forceinline__ void geo_rhs_sc(double a, double eps, double r, double s, double c, double ur, double ut,
+                                           double up, Rhs &f)
+{
+    KSBase B;
+    ks_base(a, r, s, c, B);
+    geo_rhs_b(a, eps, r, s, c, B, ur, ut, up, f);
+}
+
 // the 3+1 metric at (r, theta) from sin, cos of theta (reciprocals by the
 // FP32 seed and two Newton steps of rcp_t)
-__device__ __forceinline__ void ks_point_sc(double a, double r, double s, double c, KS &m)
+__device__ __forceinline__ void ks_point_b(double a, double r, double s, const KSBase &B, KS &m)
 {
-    double s2 = s * s, a2 = a * a;
-    double rho2 = r * r + a2 * c * c;
-    double irho2 = rcp_t(rho2);
-    double z = 2.0 * r * irho2;
-    double opz = 1.0 + z;
-    double iopz = rcp_t(opz);
-    double Dl = r * r + a2 - 2.0 * r;
-    double Sg = (r * r + a2) * (r * r + a2) - a2 * Dl * s2;
-    m.alpha = sqrt(iopz);
-    m.beta = z * iopz;
-    m.g_rr = opz;
-    m.g_tt = rho2;
-    m.g_pp = Sg * s2 * irho2;
-    m.g_rp = -a * s2 * opz;
-    m.gi_rr = (a2 + r * r) * irho2 - m.beta;
-    m.gi_rp = a * irho2;
-    m.gi_tt = irho2;
-    m.gi_pp = irho2 * rcp_t(s2);
-    m.sqrtg = rho2 * s * sqrt(opz);
+    const double s2 = s * s;
+    const double Dl = B.r2 + B.a2 - 2.0 * r;
+    const double Sg = (B.r2 + B.a2) * (B.r2 + B.a2) - B.a2 * Dl * s2;
+    m.alpha = B.alpha;
+    m.beta = B.beta;
+    m.g_rr = B.opz;
+    m.g_tt = B.rho2;
+    m.g_pp = Sg * s2 * B.ir;
+    m.g_rp = -a * s2 * B.opz;
+    m.gi_rr = (B.a2 + B.r2) * B.ir - B.beta;
+    m.gi_rp = a * B.ir;
+    m.gi_tt = B.ir;
+    m.gi_pp = B.ir * B.is2;
+    m.sqrtg = B.rho2 * s * B.opz * B.alpha;  // rho^2 sin sqrt(1+z), sqrt(1+z) = (1+z) alpha
 }
 
 // Generalized Boris step over dt at the particle (u covariant, D, B
 // contravariant); s, c = sin, cos of theta
-__device__ __forceinline__ void boris(double a, double r, double s, double c, double qm, double dt, const double D[3],
-                                      const double B[3], double u[3])
+__device__ __forceinline__ void boris(double a, double r, double s, const KSBase &Bm, double qm, double dt,
+                                      const double D[3], const double B[3], double u[3])
 {
     KS m;
-    ks_point_sc(a, r, s, c, m);
+    ks_point_b(a, r, s, Bm, m);
     double Dl0 = m.g_rr * D[0] + m.g_rp * D[2];
     double Dl1 = m.g_tt * D[1];
     double Dl2 = m.g_rp * D[0] + m.g_pp * D[2];
@@ -296,6 +313,8 @@ __global__ void __launch_bounds__(256) push64_kernel(Push64Args A)
         // right-hand side, shifted for the corrector iterates
         double s0, c0;
         sincos(th, &s0, &c0);
+        KSBase B0;
+        ks_base(g.a, r, s0, c0, B0);
         if (A.massive[sp] && A.qm[sp] != 0.0) {
             double Dv[3], Bv[3];
             if constexpr (SHAPE == 3) {
@@ -317,7 +336,7 @@ __global__ void __launch_bounds__(256) push64_kernel(Push64Args A)
             if (A.pusher)
                 vay(g.a, r, th, A.qm[sp], A.dt, Dv, Bv, u);
             else
-                boris(g.a, r, s0, c0, A.qm[sp], A.dt, Dv, Bv, u);
+                boris(g.a, r, s0, B0, A.qm[sp], A.dt, Dv, Bv, u);
         }
         // geodesic predictor-corrector (Sec. 2.2)
         double eps = A.massive[sp] ? 1.0 : 0.0;
@@ -331,7 +350,7 @@ __global__ void __launch_bounds__(256) push64_kernel(Push64Args A)
             tape[TAPE_SC0 * tl] = s0;
             tape[(TAPE_SC0 + 1) * tl] = c0;
         }
-        geo_rhs_sc(g.a, eps, r, s0, c0, u[0], u[1], u[2], f0);
+        geo_rhs_b(g.a, eps, r, s0, c0, B0, u[0], u[1], u[2], f0);
         double dt = A.dt;
         double rt = r + dt * f0.xr, tt = th + dt * f0.xt, pt = dt * f0.xp;
         double urt = u[0] + dt * f0.ur, utt = u[1] + dt * f0.ut;
