@@ -27,11 +27,13 @@
  *     (bundled convention, Sec. 2.2 and Fig. stepping).
  *
  * Parity pins: see tests/test_oracle_*.py; every exported function here is
- * pinned by at least one test against something other than itself.  One part
- * is parity unpinned: the profile of the outer absorbing layer, f <- f (1 -
- * d_max s^3) over the last damp_cells columns, is a reading (the paper names
- * the layer but gives no profile or constants); the tests pin only that it
- * leaves the interior untouched and that it is off when d_max = 0.
+ * pinned by at least one test against something other than itself.  The
+ * outer absorbing layer is pinned by its job (Sec. 2.1: fields damped to
+ * zero at the outer boundary): an outgoing pulse is sent back by less than a
+ * stated fraction and the layer's energy drains monotonically, against the
+ * same run on an extended grid; its profile f <- f (1 - d_max s^3) over the
+ * last damp_cells columns is a reading (the paper gives no profile), checked
+ * entry by entry at each component's staggered column.
  */
 #include <math.h>
 #include <stdint.h>

@@ -170,15 +170,79 @@ def test_boundary_conditions_after_update():
             np.testing.assert_array_equal(X[:, g], X[:, c.ng])
 
 
-def test_damping_layer_leaves_the_interior_and_only_scales_the_outer_columns():
-    """The outer absorbing layer (a reading: the paper gives no profile) acts
-    only on the last damp_cells columns, once per step, as a factor in
-    [1 - d_max, 1] that does not increase outwards; elsewhere one update is
-    bit-identical to the undamped one."""
+def _pulse_run(nr, damp, nsteps, nth=16, src_col=36, width=100.0, probe=(46, 54), layer=(56, 64)):
+    """Vacuum Schwarzschild run (a = 0, r_in = 0.9 r_H) driven by a ring
+    current J^phi ~ sin^2(theta) exp(-((n - 3w)/w)^2) at column src_col:
+    a transient source whose wave leaves outwards (its ingoing half falls
+    into the hole).  The grid has the cell size and time step of a 64-column
+    grid on [r_in, 20]; nr > 64 extends it outwards with the same cells.
+    Returns the fields of the probe columns at every step and the
+    area-weighted field energy sum F^2 A of the layer columns."""
+    a = 0.0
+    rin = 0.9 * O.horizon(a)
+    base = O.make_cfg(64, nth, a, rin, 20.0)
+    c = O.make_cfg(nr, nth, a, rin, rin * math.exp(nr * base.dx1), dt=base.dt, damp_max=damp, damp_cells=8)
+    D, B, J = O.zeros_fields(c, 3), O.zeros_fields(c, 3), O.zeros_fields(c, 3)
+    AD, AB = O.areas(c)
+    prof = np.sin(np.arange(nth + 1) * c.dth) ** 2
+    cols = slice(probe[0] + c.ng, probe[1] + c.ng)
+    lay = slice(layer[0] + c.ng, layer[1] + c.ng)
+    hist, energy = [], []
+    for n in range(nsteps):
+        J[2][:, src_col + c.ng] = 1e-2 * math.exp(-((n - 3 * width) / width) ** 2) * prof
+        O.field_update(c, D, B, J)
+        hist.append(np.stack([x[:, cols] for x in D + B]))
+        energy.append(sum(np.sum(x[:, lay] ** 2 * w[:, lay]) for x, w in zip(D + B, AD + AB)))
+    return np.array(hist), np.array(energy)
+
+
+def test_damping_layer_absorbs_an_outgoing_pulse():
+    """The outer layer's job (Sec. 2.1: the fields are damped to zero at the
+    outer boundary, so that outgoing waves leave the domain).  An outgoing
+    pulse crosses a 64-column grid with the layer in its last 8 columns; the
+    reference is the same run on a grid extended to 112 columns with no
+    damping, whose outer boundary the pulse never reaches in the run.  The
+    difference of the two in the probe columns between source and layer is
+    the wave the layer sends back:
+      * its peak is below 13 % of the pulse's peak there (measured 10 %;
+        without the layer the zero-derivative boundary sends back 2.6 times
+        the pulse, and a layer that damps the r-staggered components D^r,
+        B^theta, B^phi at integer columns instead of their own half-integer
+        ones sends back 18 %);
+      * once the pulse has entered, the energy of the layer columns falls
+        monotonically from its peak to below 20 % of it, while the undamped
+        run still holds over half of its own peak in those columns;
+      * the layer never holds more energy than the same columns of the
+        undamped run (to 1e-6 relative: the mis-staggered layer exceeds it by
+        5e-5)."""
+    n = 1400
+    h1, e1 = _pulse_run(64, 0.1, n)
+    h2, e2 = _pulse_run(112, 0.0, n)
+    norm = lambda x: np.sqrt(np.sum(x.reshape(len(x), -1) ** 2, axis=1))
+    ref = norm(h2)
+    refl = norm(h1 - h2)
+    assert refl.max() < 0.13 * ref.max(), refl.max() / ref.max()
+    pk = int(np.argmax(e1))
+    end = pk + int(np.argmax(e1[pk:] < 0.2 * e1[pk]))
+    assert end > pk and e1[end] < 0.2 * e1[pk]
+    assert np.all(np.diff(e1[pk:end + 1]) <= 0.0)
+    assert e2[end] > 0.5 * e2.max()
+    assert np.all(e1[1:] <= e2[1:] * (1.0 + 1e-6))
+
+
+def test_damping_profile_is_the_cubic_reading():
+    """The profile the layer uses (reading: the paper names the damping, not
+    its form) is f = 1 - d_max s^3 with s = (x - (n_r - N_d)) / N_d clipped
+    to [0, 1] at each component's own r position x (i + 1/2 for D^r, B^theta,
+    B^phi; i for D^theta, D^phi, B^r), applied once after the last corrector
+    and followed by the boundary pass.  From one state, the damped update
+    equals the undamped one times f entry by entry (to rounding), every
+    column left of the layer is bit-identical, and the outer guard columns
+    copy the damped last physical column."""
     a = 0.9
     out = {}
     for damp in (0.0, 0.1):
-        c = O.make_cfg(32, 24, a, 0.9 * O.horizon(a), 20.0, damp_max=damp)
+        c = O.make_cfg(48, 24, a, 0.9 * O.horizon(a), 20.0, damp_max=damp, damp_cells=12)
         D, B = O.init_fields(c, O.WALD, 1.0)
         rng = np.random.default_rng(4)
         J = [rng.normal(size=O.field_shape(c)) * 0.01 for _ in range(3)]
@@ -186,13 +250,20 @@ def test_damping_layer_leaves_the_interior_and_only_scales_the_outer_columns():
         out[damp] = (c, D + B)
     c, und = out[0.0]
     _, dam = out[0.1]
-    first = c.nr - c.damp_cells
-    for k, (x, y) in enumerate(zip(dam, und)):
-        cols_in = slice(0, c.ng + first - 1)
-        assert np.array_equal(x[:, cols_in], y[:, cols_in]), k
-        ratio = np.divide(x[:, c.ng + first:c.ng + c.nr], y[:, c.ng + first:c.ng + c.nr],
-                          out=np.ones_like(x[:, c.ng + first:c.ng + c.nr]),
-                          where=np.abs(y[:, c.ng + first:c.ng + c.nr]) > 1e-12)
-        assert ratio.min() >= 1.0 - 0.1 - 1e-12 and ratio.max() <= 1.0 + 1e-12, k
-        prof = np.median(ratio, axis=0)
-        assert np.all(np.diff(prof) <= 1e-12), k
+    x0 = c.nr - c.damp_cells
+    for comp, (x, y) in enumerate(zip(dam, und)):
+        half_r = comp in (0, 4, 5)
+        half_t = comp in (1, 3, 5)
+        rows = slice(0, c.nth if half_t else c.nth + 1)
+        last = c.nr - 1 if half_r else c.nr
+        i = np.arange(0, last + 1)
+        s = np.clip((i + (0.5 if half_r else 0.0) - x0) / c.damp_cells, 0.0, 1.0)
+        f = 1.0 - 0.1 * s ** 3
+        cols = i + c.ng
+        xv, yv = x[rows][:, cols], y[rows][:, cols]
+        assert np.all(np.abs(xv - f * yv) <= 2e-16 * np.abs(yv) + 1e-300), comp
+        inner = cols[s == 0.0]
+        assert np.array_equal(xv[:, s == 0.0], yv[:, s == 0.0]), comp
+        assert inner.size > 0 and np.any(s > 0.9)
+        for g in range(last + 1 + c.ng, c.ld):
+            assert np.array_equal(x[rows][:, g], x[rows][:, last + c.ng]), (comp, g)
