@@ -50,51 +50,81 @@ B0 = 1.0
 
 
 # Arithmetic per particle-step of the push kernels, counted by ncu on the same
-# kernels (flop_count = 2 FMA + MUL + ADD of the SASS instruction counters;
-# the capture commands and counts are in profiles/).
-PUSH64_FP64_FLOP = 1216.0   # profiles/push64_fp64_512x512_64ppc.md
+# kernels (flop = 2 FMA + MUL + ADD of the SASS instruction counters) in one
+# capture of a smaller case of the same workload (same spin, radial range and
+# island fraction), and scaled to a launch by the number of particles.
+PUSH64_FP64_FLOP = 1216.0   # FP64 push, 512^2 x 64 ppc split monopole
 PUSH64_DRAM_B = 95.8        # the same capture: DRAM bytes per particle (read + write)
-PUSH32_FP32_FLOP = 1018.5   # profiles/push32_fp32form_1024x1024_64ppc.md
+PUSH32_FP32_FLOP = 1018.5   # FP32-form push, 1024^2 x 64 ppc split monopole
 # the same capture: instructions issued per particle (warp instructions x 32)
-# and DRAM bytes per particle (read + write), scaled to a launch by the
-# number of particles
+# and DRAM bytes per particle (read + write)
 PUSH32_INST = 1744.0
 PUSH32_DRAM_B = 69.4
-# batched 1D lines, b1_kernel with the cascade running (profiles/b1_kernel_256lines_4096cells.md):
+# batched 1D lines, b1_kernel with the cascade running (256 lines x 4096 cells):
 # instructions issued per particle-step (warp instructions x 32) and DRAM
 # bytes per particle-step; algorithmic bytes: the particle record (cell, offset,
 # u_r, u_phi, tag as 4 B each, id 8 B) read and written once per step
 B1_INST = 1037.0
 B1_DRAM_B = 51.7
 B1_ALG_B = 2 * 28
-# the widened rows' push kernels, counted the same way (profiles/ summaries
-# named for each): the FP32 push with Vay's update, the FP64 push with the
-# cubic shape, the FP64 push with photon emission and conversion decisions
-VAY32_FP32_FLOP = 1158.0    # profiles/push32_vay_1024x1024_64ppc.md
+# the widened rows' push kernels, counted the same way: the FP32 push with
+# Vay's update (1024^2 x 64 ppc), the FP64 push with the cubic shape (512^2 x
+# 64 ppc), the FP64 push with photon emission and conversion decisions (512^2
+# x 16 ppc, Wald a = 0.99, B0 = 500)
+VAY32_FP32_FLOP = 1158.0
 VAY32_INST = 1925.0
-CUBIC64_FP64_FLOP = 1772.0  # profiles/push64_cubic_512x512_64ppc.md
-RAD64_FP64_FLOP = 1685.0    # profiles/push64_rad_512x512_16ppc.md
-# ALU peaks from unit counts x clock: 152 SMs x 2.07 GHz x (4 FP64 flops,
-# 256 FP32 flops) per SM per clock; instruction issue: 4 schedulers x 1 warp
-# instruction per SM per clock
-FP64_PEAK_TFLOPS = 152 * 2.07e9 * 4 / 1e12
-FP32_PEAK_TFLOPS = 152 * 2.07e9 * 256 / 1e12
-ISSUE_PEAK_GWARP = 152 * 2.07e9 * 4 / 1e9
+CUBIC64_FP64_FLOP = 1772.0
+RAD64_FP64_FLOP = 1685.0
+VAY_COUNT = "ncu SASS counters, FP32-form push with Vay's update, 1024^2 x 64 ppc"
+CUBIC_COUNT = "ncu SASS counters, FP64 push with the cubic shape, 512^2 x 64 ppc"
+RAD_COUNT = "ncu SASS counters, FP64 push with emission/conversion decisions, 512^2 x 16 ppc"
+
+
+_ALU = None
+
+
+def measured_alu():
+    """The device's FMA ceilings measured in this run (grpic_alu_peak: one
+    full-occupancy launch of independent FMA chains, best of five): FP32,
+    FP64 and packed-FP32 TFLOP/s, the FMA instruction issue rate and the SM
+    count.  The issue ceiling is the larger of the FP32 and packed-FP32 FMA
+    warp-instruction rates (one FMA instruction per scheduler and clock)."""
+    global _ALU
+    if _ALU is None:
+        from paper_2503_04558_gb300 import build, grpic as G
+        build.build()
+        G.load()
+        f32 = G.alu_peak(0)
+        f64 = G.alu_peak(1)
+        f2 = G.alu_peak(2)
+        _ALU = {"fp32_tflops": f32[0] / 1e12, "fp64_tflops": f64[0] / 1e12, "fp32x2_tflops": f2[0] / 1e12,
+                "issue_gwarp": max(f32[1], f2[1]) / 1e9, "sms": f32[2],
+                "source": "measured in this run: grpic_alu_peak, %d SMs x 8 blocks x 256 threads, 8 independent "
+                          "FMA chains per thread, best of 5 launches" % f32[2]}
+    return _ALU
 
 
 def horizon(a):
     return 1.0 + math.sqrt(1.0 - a * a)
 
 
-def workload_config(precision, nr=NR, nth=NTH, pusher=0, shape_order=1):
+def workload_config(precision, nr=NR, nth=NTH, pusher=0, shape_order=1, island_arith=0, spin=SPIN, r_out=R_OUT):
     from paper_2503_04558_gb300 import grpic as G
-    rin = 0.9 * horizon(SPIN)
+    rin = 0.9 * horizon(spin)
     qw = 1e-3
     # FP32 form: extended-precision metric inside 1.5 r_H, correctors stop
     # once the iterate changes by less than 1e-6 (at most 3)
-    return G.Config(nr, nth, SPIN, rin, R_OUT, q_weight=(-qw, qw, qw, 0.0), precision=precision, sort_every=1,
-                    fp64_radius=1.5 * horizon(SPIN), push_tol=1e-6 if precision == 32 else 0.0, pusher=pusher,
-                    shape_order=shape_order)
+    return G.Config(nr, nth, spin, rin, r_out, q_weight=(-qw, qw, qw, 0.0), precision=precision, sort_every=1,
+                    fp64_radius=1.5 * horizon(spin), push_tol=1e-6 if precision == 32 else 0.0, pusher=pusher,
+                    shape_order=shape_order, island_arith=island_arith)
+
+
+# the workloads a step is timed on: the production split monopole (the
+# headline) and the 4096^2 Wald run (the FP32 form at scale)
+SPLIT2048 = {"name": "split monopole 2048^2", "spin": SPIN, "r_out": R_OUT, "kind": 3, "thermal_T": THERMAL_T,
+             "sigma": None, "seed": 1234}
+WALD4096 = {"name": "Wald 4096^2", "spin": 0.9, "r_out": 50.0, "kind": 0, "thermal_T": None, "sigma": 0.1,
+            "seed": 99, "grid": 4096, "ppc": 64}
 
 
 PARTICLE_STATUSES = (4, 5)  # ERANGE, ENAN: a particle refused and killed, the step goes on
@@ -182,7 +212,7 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
-def run_grpic(args, prec, rank, world, e2e_steps, pusher=0, shape_order=1):
+def run_grpic(args, prec, rank, world, e2e_steps, pusher=0, shape_order=1, island_arith=0, wl=SPLIT2048):
     import torch
     from paper_2503_04558_gb300 import build, grpic as G, synth
 
@@ -190,14 +220,16 @@ def run_grpic(args, prec, rank, world, e2e_steps, pusher=0, shape_order=1):
     G.load()
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
     torch.cuda.set_device(dev)
-    cfg = workload_config(prec, args.grid, args.grid, pusher, shape_order)
+    grid = wl.get("grid", args.grid)
+    ppc = wl.get("ppc", args.ppc)
+    cfg = workload_config(prec, grid, grid, pusher, shape_order, island_arith, wl["spin"], wl["r_out"])
     ctx = G.Context(cfg)
     F = G.Fields(cfg)
-    ctx.init_fields(F, G.SPLIT_MONOPOLE, B0)
-    n = cfg.n_r * cfg.n_theta * args.ppc
+    ctx.init_fields(F, wl["kind"], B0)
+    n = cfg.n_r * cfg.n_theta * ppc
     S = G.ParticleSet(cfg, n)
-    gen = synth.particles_torch(cfg.n_r, cfg.n_theta, cfg.r_in, cfg.r_out, n, seed=1234 + rank,
-                                thermal_T=THERMAL_T, device=dev)
+    gen = synth.particles_torch(cfg.n_r, cfg.n_theta, cfg.r_in, cfg.r_out, n, seed=wl["seed"] + rank,
+                                thermal_T=wl["thermal_T"], sigma=wl["sigma"] or 0.1, device=dev)
     if prec == 64:
         S.load(gen["r"], gen["th"], gen["u1"], gen["u2"], gen["u3"], gen["tag"])
     else:
@@ -330,15 +362,132 @@ def run_e2e(e2e_steps, ctx, S, F, cfg, stream):
             "ms_per_step": ms, "steps": e2e_steps}
 
 
+IDX_SHIFT = 2   # loading index in tag bits 2..30 (species in 0..1, dead in 31)
+
+
+def _state_by_index(S, cfg, n):
+    """(r, theta, u_r, u_theta, u_phi) of the live particles scattered to their
+    loading index (NaN where the particle is dead), as float64 device tensors."""
+    import torch
+    live = S.live()
+    P = S.a
+    idx = (P.tag[:live].to(torch.int64) & 0x7FFFFFFF) >> IDX_SHIFT
+    out = [torch.full((n,), float("nan"), dtype=torch.float64, device=P.x1.device) for _ in range(5)]
+    if cfg.precision == 64:
+        vals = [P.x1[:live], P.x2[:live]]
+    else:
+        c = P.cell[:live].to(torch.int64)
+        x1 = (c % cfg.n_r).double() + P.x1[:live].double()
+        x2 = (c // cfg.n_r).double() + P.x2[:live].double()
+        vals = [cfg.r_in * torch.exp(x1 * cfg.dx1), x2 * cfg.dth]
+    vals += [P.u1[:live].double(), P.u2[:live].double(), P.u3[:live].double()]
+    for o, v in zip(out, vals):
+        o[idx] = v
+    return out
+
+
+def fp32_error_measure(grid, ppc, nsteps, seed=4321):
+    """The FP32 form (as benchmarked: double-FP32 metric inside 1.5 r_H,
+    corrector tolerance 1e-6) against the FP64 plain path from the same
+    initial state after nsteps steps of grpic_step on the bench workload:
+      fields: per component max |F32 - F64| / max |F64| over the physical
+        columns;
+      particles (matched by loading index): position error in cells (r and
+        theta) and momentum error |du| / max(1, |u|) in the orthonormal
+        components (u_r, u_theta / r, u_phi / (r sin theta)), as median, 99th
+        percentile and max, away from and within 10 theta cells of the polar
+        axis; the particles alive in one path only are counted."""
+    import torch
+    from paper_2503_04558_gb300 import grpic as G, synth
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    c64, c32 = workload_config(64, grid, grid), workload_config(32, grid, grid)
+    n = grid * grid * ppc
+    if n >= 1 << 29:
+        raise ValueError("loading index does not fit the tag bits")
+    runs = {}
+    for cfg in (c64, c32):
+        gen = synth.particles_torch(cfg.n_r, cfg.n_theta, cfg.r_in, cfg.r_out, n, seed=seed, thermal_T=THERMAL_T,
+                                    device=dev)
+        tag = gen["tag"] | (torch.arange(n, device=dev, dtype=torch.int32) << IDX_SHIFT)
+        S = G.ParticleSet(cfg, n)
+        if cfg.precision == 64:
+            S.load(gen["r"], gen["th"], gen["u1"], gen["u2"], gen["u3"], tag)
+        else:
+            x1 = (torch.log(gen["r"]) - math.log(cfg.r_in)) / cfg.dx1
+            x2 = gen["th"] / cfg.dth
+            i = torch.floor(x1).clamp(0, cfg.n_r - 1)
+            j = torch.floor(x2).clamp(0, cfg.n_theta - 1)
+            S.load((x1 - i).float(), (x2 - j).float(), gen["u1"].float(), gen["u2"].float(), gen["u3"].float(),
+                   tag, (j * cfg.n_r + i).to(torch.int32))
+        del gen
+        ctx = G.Context(cfg)
+        F = G.Fields(cfg)
+        ctx.init_fields(F, G.SPLIT_MONOPOLE, B0)
+        ctx.step(S, F, nsteps)
+        st = ctx.sync()
+        runs[cfg.precision] = (S, F, st)
+        del ctx
+    (S64, F64, st64), (S32, F32, st32) = runs[64], runs[32]
+    cols = slice(2, 2 + grid + 1)
+    field = {}
+    for name, a, b in (("D", F32.D, F64.D), ("B", F32.B, F64.B)):
+        for k in range(3):
+            ref = b[k][:, cols]
+            field[f"{name}{k}"] = float((a[k][:, cols].double() - ref).abs().max() / ref.abs().max())
+    y64 = _state_by_index(S64, c64, n)
+    y32 = _state_by_index(S32, c32, n)
+    both = ~torch.isnan(y64[0]) & ~torch.isnan(y32[0])
+    only = int((~torch.isnan(y64[0]) ^ ~torch.isnan(y32[0])).sum())
+    r, th = y64[0][both], y64[1][both]
+    dr_cell = r * c64.dx1
+    pos_r = (y32[0][both] - r).abs() / dr_cell
+    pos_t = (y32[1][both] - th).abs() / c64.dth
+    sc = [torch.ones_like(r), r, r * torch.sin(th).abs().clamp_min(1e-300)]
+    u64 = torch.stack([y64[2 + k][both] / sc[k] for k in range(3)])
+    u32 = torch.stack([y32[2 + k][both] / sc[k] for k in range(3)])
+    du = (u32 - u64).norm(dim=0) / u64.norm(dim=0).clamp_min(1.0)
+    axis_d = torch.minimum(th, math.pi - th) / c64.dth
+    near = axis_d < 10.0
+
+    def stats(x):
+        if x.numel() == 0:
+            return None
+        xs = x[::x.numel() // (1 << 24) + 1].float()   # torch.quantile takes at most 2^24 entries
+        q = torch.quantile(xs, torch.tensor([0.5, 0.99], device=x.device))
+        return {"median": float(q[0]), "p99": float(q[1]), "max": float(x.max())}
+
+    out = {"steps": nsteps, "what": "FP32 form vs FP64 plain path, same initial state, after the steps",
+           "field_rel_max": field, "field_rel_max_all": max(field.values()),
+           "particles_compared": int(both.sum()), "alive_in_one_path_only": only,
+           "away_from_axis": {"position_cells": stats(torch.maximum(pos_r, pos_t)[~near]),
+                              "momentum_rel": stats(du[~near])},
+           "within_10_cells_of_axis": {"particles": int(near.sum()),
+                                       "position_cells": stats(torch.maximum(pos_r, pos_t)[near]),
+                                       "momentum_rel": stats(du[near])},
+           "status": [G.STATUS_NAMES[st64], G.STATUS_NAMES[st32]]}
+    del S64, S32, F64, F32, runs, y64, y32
+    torch.cuda.empty_cache()
+    return out
+
+
 # ---------------------------------------------------------------------------
 # oracle timing on the host (bounded sample of the workload)
 # ---------------------------------------------------------------------------
-def oracle_sample(steps, n_side=128):
+def host_cores():
+    """Cores this process may run on (the machine's host CPU)."""
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def oracle_sample(steps, n_side=128, threads=1):
     """The FP64 oracle on an n_side^2 sub-grid of the workload (same spin,
-    radial range, field, particles per cell and momenta), single-threaded.
-    Returns particle-steps/s and cell-updates/s of the oracle's step."""
+    radial range, field, particles per cell and momenta) on `threads` host
+    threads.  Returns particle-steps/s and cell-updates/s of the oracle's step."""
     import oracle as O
     from paper_2503_04558_gb300 import synth
+    threads = O.set_threads(threads)
     rin = 0.9 * horizon(SPIN)
     c = O.make_cfg(n_side, n_side, SPIN, rin, R_OUT, qw=(-1e-3, 1e-3, 1e-3, 0.0))
     D, B = O.init_fields(c, O.SPLIT_MONOPOLE, B0)
@@ -358,28 +507,40 @@ def oracle_sample(steps, n_side=128):
         t_push += t1 - t0
         t_field += t2 - t1
         t_sort += t3 - t2
+    O.set_threads(1)
     tot = t_push + t_field + t_sort
     return {"value": done / tot, "push_deposit_per_s": done / t_push,
             "cell_updates_per_s": n_side * n_side * steps / t_field, "seconds": tot, "particles": n,
-            "steps": steps, "grid": f"{n_side}x{n_side}"}
+            "steps": steps, "grid": f"{n_side}x{n_side}", "threads": threads}
 
 
 def cpu_baseline_block(steps=3, n_side=256):
-    s = oracle_sample(steps, n_side)
-    return {"value": s["value"], "unit": UNIT, "cores": 1, "kind": "oracle",
+    """The oracle as it stands on one host thread (the reported baseline) and
+    on every host core (OpenMP over particles with per-thread currents and over
+    the field rows; the sort stays serial), on the same bounded sample."""
+    s = oracle_sample(steps, n_side, 1)
+    ncore = host_cores()
+    allc = oracle_sample(steps, n_side, ncore)
+    return {"value": s["value"], "unit": UNIT, "cores": 1, "kind": "oracle", "host_cores": ncore,
             "sample": f"{s['grid']} sub-grid of the 2048x2048 workload, {PPC} ppc ({s['particles']} particles), "
                       f"{s['steps']} steps, FP64, single thread, {s['seconds']:.1f} s",
-            "push_deposit_per_s": s["push_deposit_per_s"], "cell_updates_per_s": s["cell_updates_per_s"]}
+            "push_deposit_per_s": s["push_deposit_per_s"], "cell_updates_per_s": s["cell_updates_per_s"],
+            "all_cores": {"value": allc["value"], "unit": UNIT, "cores": allc["threads"],
+                          "push_deposit_per_s": allc["push_deposit_per_s"],
+                          "cell_updates_per_s": allc["cell_updates_per_s"], "seconds": allc["seconds"],
+                          "sample": "the same sample on every host core (OpenMP: particles in per-thread "
+                                    "current arrays, field rows; serial sort)"}}
 
 
 def run_reference(args):
     rank = int(os.environ.get("RANK", 0))
     if rank != 0:
         return
+    ncore = host_cores()
     for _ in range(args.warmup):
-        oracle_sample(1, 64)
+        oracle_sample(1, 64, ncore)
     t0 = time.perf_counter()
-    s = oracle_sample(args.steps, 96)
+    s = oracle_sample(args.steps, 96, ncore)
     wall = time.perf_counter() - t0
     val = s["value"]
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
@@ -388,8 +549,9 @@ def run_reference(args):
             "config": {"workload": "GRPIC step, 2048x2048 log-r x theta, a=0.99, split monopole, 100 ppc "
                                    "(4.19e8 e+/e-), thermal T=0.3; oracle on a 96x96 sub-grid sample",
                        "sample_grid": s["grid"], "sample_particles": s["particles"]},
-            "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"{s['grid']} sub-grid, {PPC} ppc, {args.steps} steps, single thread"},
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": s["threads"], "kind": "oracle", "host_cores": ncore,
+                             "sample": f"{s['grid']} sub-grid, {PPC} ppc, {args.steps} steps, {s['threads']} threads "
+                                       "(OpenMP over particles with per-thread currents and over field rows)"},
             "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
             "wall_s": wall}
     print(json.dumps(line), flush=True)
@@ -402,13 +564,13 @@ B1_LINES, B1_CELLS, B1_A, B1_ROUT, B1_CAP = 512, 4096, 0.99, 20.0, 1_000_000
 B1_ORACLE_LINES, B1_ORACLE_STEPS = 32, 80   # the oracle's bounded sample (a few seconds)
 
 
-def batch1d_inputs(nl, n, seed=2024):
-    """Per line: 10^U(3,5) particles (e-/e+ pairs at the same positions,
+def batch1d_inputs(nl, n, seed=2024, lo=3.0, hi=5.0):
+    """Per line: 10^U(lo,hi) particles (e-/e+ pairs at the same positions,
     uniform along the line), u_r ~ N(0, 0.1), u_phi = 0; inclinations uniform
     in (0, pi/2); imposed current I0 = Omega_H B0 sin^2(theta) (kappa = 1)."""
     import numpy as np
     rng = np.random.Generator(np.random.Philox(seed))
-    counts = (10 ** rng.uniform(3, 5, nl)).astype(np.int64) // 2 * 2
+    counts = (10 ** rng.uniform(lo, hi, nl)).astype(np.int64) // 2 * 2
     lines = []
     nid = 0
     for k in range(nl):
@@ -426,11 +588,14 @@ def batch1d_inputs(nl, n, seed=2024):
     return theta, lines
 
 
-def batch1d_measure(steps, warmup, n_lines=None, capacity=None, shape=None):
+def batch1d_measure(steps, warmup, n_lines=None, capacity=None, shape=None, grown=False):
     """Tuned persistent run of the 512 lines; returns the figures and the
     oracle's throughput on a bounded sample (the smallest lines, a few seconds).
     n_lines / capacity shrink the workload for profiling runs; shape fixes the
-    launch shape (threads, CTAs per SM, CTAs per line) instead of tuning."""
+    launch shape (threads, CTAs per SM, CTAs per line) instead of tuning.
+    grown: the lines start at 10^U(4, 5.7) particles (up to half the 1e6
+    capacity, 6.5e7 in all), the load-imbalanced state a grown cascade
+    reaches, and the tuner chooses the launch shape in that state."""
     import numpy as np
     import torch
     from paper_2503_04558_gb300 import build, grpic as G
@@ -444,7 +609,7 @@ def batch1d_measure(steps, warmup, n_lines=None, capacity=None, shape=None):
                           B0=2.0e3, seed=7)
     B = G.Batch1D(cfg)
     L = G.Lines(cfg)
-    theta, lines = batch1d_inputs(n_lines, B1_CELLS)
+    theta, lines = batch1d_inputs(n_lines, B1_CELLS, lo=4.0 if grown else 3.0, hi=5.7 if grown else 5.0)
     L.theta.copy_(torch.from_numpy(theta))
     omega_h = B1_A / (2.0 * rh)
     L.I0.copy_(torch.from_numpy(omega_h * cfg.B0 * np.sin(theta) ** 2))
@@ -497,33 +662,35 @@ def batch1d_measure(steps, warmup, n_lines=None, capacity=None, shape=None):
         S = O.LineState(cell + off.astype(np.float64), ur.astype(np.float64), up.astype(np.float64), tag, pid,
                         4 * len(cell) + 1000)
         D = O.line_init_D(Lo, cfg.B0)
-        for s in range(B1_ORACLE_STEPS):
+        for s in range(B1_ORACLE_STEPS // (4 if grown else 1)):
             oracle_pushes += S.n
             O.line_step(Lo, s, S, D)
     osec = time.perf_counter() - t
     rate = pushes / (ms * 1e-3)
     pk, pk_kind = peaks()
     # the timed region is one launch of the persistent kernel running every step
+    alu = measured_alu()
     roof = {"kernel": "b1_kernel (one persistent launch for all timed steps)", "bound": "issue",
-            "achieved": rate * B1_INST / 32 / 1e9 if B1_INST else None, "peak": ISSUE_PEAK_GWARP,
-            "unit": "G warp-instructions/s", "frac": rate * B1_INST / 32 / 1e9 / ISSUE_PEAK_GWARP if B1_INST else None,
-            "traffic": pushes * B1_DRAM_B if B1_DRAM_B else None, "inst_per_particle": B1_INST,
-            "peak_source": "152 SMs x 4 schedulers x 2.07 GHz",
+            "achieved": rate * B1_INST / 32 / 1e9, "peak": alu["issue_gwarp"],
+            "unit": "G warp-instructions/s", "frac": rate * B1_INST / 32 / 1e9 / alu["issue_gwarp"],
+            "traffic": pushes * B1_DRAM_B, "inst_per_particle": B1_INST,
+            "count_source": "ncu SASS counters, b1_kernel with the cascade running, 256 lines x 4096 cells",
+            "peak_source": alu["source"] + " (FMA warp-instructions/s)",
             "hbm": {"bound": "hbm", "achieved": rate * B1_ALG_B / 1e9, "peak": pk["hbm_gbs"], "unit": "GB/s",
                     "frac": rate * B1_ALG_B / 1e9 / pk["hbm_gbs"], "bytes_per_particle": B1_ALG_B,
                     "peak_source": f"{pk_kind} hbm_gbs (MEASURED_PEAKS)"}}
     out = {"value": rate, "unit": "particle-steps/s", "steps": steps, "warmup": warmup + done, "roofline": roof,
            "ms_per_step": ms / steps, "dtype": "f32",
            "workload": "%d radial lines x 4096 cells, a=0.99, r in [r_H, 20], monopole B0=2e3, gamma_thr=100, "
-                       "eps_ph=4, tau=2, initial 10^U(3,5) particles per line, capacity %.0e per line"
-                       % (n_lines, capacity),
+                       "eps_ph=4, tau=2, initial 10^U(%s) particles per line, capacity %.0e per line"
+                       % (n_lines, "4,5.7" if grown else "3,5", capacity),
            "initial_particles": n0, "particles_now": int(L.count.sum().item()), "tuned_launch": list(best),
            "cell_updates_per_s": cells / (ms * 1e-3),
            "events": {"emitted": int(ev1[0] - ev0[0]), "converted": int(ev1[1] - ev0[1])},
            "status": int(st), "clocks": clk.summary(), "gpu_launches": 2,
            "l2": "inputs larger than L2 (particle state %.0f MB)" % (n0 * 24 / 1e6),
            "cpu_baseline": {"value": oracle_pushes / osec, "unit": "particle-steps/s", "cores": 1,
-                            "kind": "oracle", "sample": f"{B1_ORACLE_LINES} smallest lines, {B1_ORACLE_STEPS} steps, FP64, "
+                            "kind": "oracle", "sample": f"{B1_ORACLE_LINES} smallest lines, {B1_ORACLE_STEPS // (4 if grown else 1)} steps, FP64, "
                                                   f"{osec:.1f} s"}}
     del B, L
     torch.cuda.empty_cache()
@@ -690,7 +857,7 @@ def pairs_2d_measure(n=1024, ppc=16, steps=3):
            "phases": {"push_and_appends_ms": tp / tn, "field_and_injection_ms": tf / tn, "sort_ms": ts / tn},
            "roofline": alu_roofline("push+deposit with emission/conversion decisions (FP64), with the appends",
                                     0.5 * (live0 + live1), tp / tn, RAD64_FP64_FLOP, 64, None,
-                                    "profiles/push64_rad_512x512_16ppc.md"),
+                                    RAD_COUNT),
            "clocks": clk.summary(),
            "status": ["OK", "EINVAL", "ENOMEM", "ECUDA", "ERANGE", "ENAN", "EOVERFLOW"][st] if st < 7 else st}
     del S, F, ctx
@@ -702,19 +869,49 @@ def alu_roofline(kernel, n_units, kernel_ms, flop_per_unit, prec, inst_per_unit=
     """Roofline of an ALU-bound push kernel from its ncu-counted flop (and
     instruction) count per particle and its duration measured in the timed
     region; null figures where the count has not been taken."""
-    peak = FP32_PEAK_TFLOPS if prec == 32 else FP64_PEAK_TFLOPS
+    alu = measured_alu()
+    peak = alu["fp32_tflops"] if prec == 32 else alu["fp64_tflops"]
     ach = n_units * flop_per_unit / (kernel_ms * 1e-3) / 1e12 if flop_per_unit else None
     roof = {"kernel": kernel, "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
             "frac": ach / peak if ach is not None else None, "traffic": None,
-            "peak_source": "152 SMs x 2.07 GHz x %d %s flop/clk/SM (recipe unit counts and clock)"
-                           % ((256, "FP32") if prec == 32 else (4, "FP64")),
+            "peak_source": alu["source"] + (" (FP32 FMA)" if prec == 32 else " (FP64 FMA)"),
             "flop_per_particle": flop_per_unit, "count_source": source}
     if inst_per_unit:
         iss = n_units * inst_per_unit / 32 / (kernel_ms * 1e-3) / 1e9
-        roof["issue"] = {"achieved": iss, "peak": ISSUE_PEAK_GWARP, "unit": "G warp-instructions/s",
-                         "frac": iss / ISSUE_PEAK_GWARP, "inst_per_particle": inst_per_unit,
-                         "peak_source": "152 SMs x 4 schedulers x 2.07 GHz"}
+        roof["issue"] = {"achieved": iss, "peak": alu["issue_gwarp"], "unit": "G warp-instructions/s",
+                         "frac": iss / alu["issue_gwarp"], "inst_per_particle": inst_per_unit,
+                         "peak_source": alu["source"] + " (FMA warp-instructions/s)"}
     return roof
+
+
+def island_measure(args, rank=0, world=1):
+    """The headline FP32 step with the island near the horizon in native FP64
+    (island_arith = 1: the letter of the FP32 form) instead of double-FP32
+    pairs, same workload and timed region."""
+    ri = run_grpic(args, 32, rank, world, 0, island_arith=1)
+    ri["total_ms"] = max_over_ranks(ri["total_ms"], world)
+    tp = ri["timed_phases"]
+    return {"what": "FP32 form step with the metric inside 1.5 r_H in native FP64 (island_arith = 1)",
+            "value": job_value(ri["n"], args.steps, world, ri["total_ms"]), "unit": UNIT,
+            "ms_per_step": ri["total_ms"] / args.steps, "steps": args.steps, "phases": {"timed_region": tp},
+            "particle_statuses": ri["statuses"], "clocks": ri["clocks"]}
+
+
+def wald4096_measure(args, rank=0, world=1):
+    """The FP32 form at scale: 4096^2 log-r x theta, a = 0.9, r in [0.9 r_H,
+    50], rotating Wald B0 = 1, 64 particles per cell (1.07e9 e+/e-, Gaussian
+    momenta sigma 0.1), the headline's timed region (one grpic_step call of K
+    steps) and push roofline."""
+    rw = run_grpic(args, 32, rank, world, 0, wl=WALD4096)
+    rw["total_ms"] = max_over_ranks(rw["total_ms"], world)
+    h = grpic_summary(rw, args, world, 32)
+    return {"what": "FP32 form step, 4096x4096, a=0.9, r in [0.9 r_H, 50], Wald B0=1, 64 ppc (%.3g e+/e-), "
+                    "sigma 0.1" % rw["n"], "value": h["value"], "unit": UNIT, "ms_per_step": h["ms_per_step"],
+            "steps": args.steps, "warmup": args.warmup, "particles": rw["n"], "cells": rw["cells"],
+            "push_deposit_per_s": h["push_deposit_per_s"], "cell_updates_per_s": h["cell_updates_per_s"],
+            "phases": {"timed_region": rw["timed_phases"]}, "live_particles": rw["live"],
+            "particle_statuses": rw["statuses"], "roofline": h["roofline"], "clocks": rw["clocks"],
+            "l2": "inputs larger than L2 (particle state %.1f GB)" % (rw["n"] * 24 / 1e9)}
 
 
 def vay_measure(args, rank=0, world=1):
@@ -728,7 +925,7 @@ def vay_measure(args, rank=0, world=1):
             "ms_per_step": rv["total_ms"] / args.steps, "steps": args.steps,
             "phases": {"timed_region": tp}, "particle_statuses": rv["statuses"],
             "roofline": alu_roofline("push+deposit, Vay (FP32 form)", rv["n"], tp["push_ms"], VAY32_FP32_FLOP, 32,
-                                     VAY32_INST, "profiles/push32_vay_1024x1024_64ppc.md"),
+                                     VAY32_INST, VAY_COUNT),
             "clocks": rv["clocks"]}
 
 
@@ -745,7 +942,7 @@ def cubic_measure(args, rank=0, world=1):
             "ms_per_step": rc["total_ms"] / 2, "phases": {"timed_region": tp},
             "particle_statuses": rc["statuses"],
             "roofline": alu_roofline("push+deposit, cubic shape (FP64)", rc["n"], tp["push_ms"], CUBIC64_FP64_FLOP,
-                                     64, None, "profiles/push64_cubic_512x512_64ppc.md"),
+                                     64, None, CUBIC_COUNT),
             "clocks": rc["clocks"]}
 
 
@@ -755,12 +952,18 @@ def run_extra(args, name):
         m = vay_measure(args)
     elif name == "cubic":
         m = cubic_measure(args)
+    elif name == "wald4096":
+        m = wald4096_measure(args)
+    elif name == "fp32err":
+        m = fp32_error_measure(args.grid, args.ppc, args.steps)
+        print(json.dumps(m), flush=True)
+        return
     else:
         m = pairs_2d_measure(args.grid or 1024, args.ppc or 16, max(1, args.steps))
     line = {"metric": m["what"] + ": particle-steps/s", "value": m["value"], "unit": m["unit"], "n_gpus": 1,
             "steps": m["steps"], "warmup": m.get("warmup", args.warmup), "ms_per_step": m["ms_per_step"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32" if name == "vay" else "f64", "data": "synthetic"}
+            "dtype": "f32" if name in ("vay", "wald4096") else "f64", "data": "synthetic"}
     line.update({k: v for k, v in m.items() if k not in line})
     print(json.dumps(line), flush=True)
 
@@ -793,20 +996,23 @@ def grpic_summary(res, args, world, esz_prec):
     else:
         hbm["traffic"] = n * PUSH64_DRAM_B
         hbm["traffic_source"] = "ncu dram bytes per particle at 512^2 x 64 ppc, x particles"
-    roof = {"kernel": "push+deposit (FP32 form)", "bound": "alu", "achieved": ach32, "peak": FP32_PEAK_TFLOPS,
-            "unit": "TFLOP/s", "frac": ach32 / FP32_PEAK_TFLOPS, "traffic": n * PUSH32_DRAM_B,
-            "peak_source": "152 SMs x 2.07 GHz x 256 FP32 flop/clk/SM (recipe unit counts and clock)",
-            "flop_per_particle": PUSH32_FP32_FLOP, "hbm": hbm,
-            "issue": {"achieved": issue, "peak": ISSUE_PEAK_GWARP, "unit": "G warp-instructions/s",
-                      "frac": issue / ISSUE_PEAK_GWARP, "inst_per_particle": PUSH32_INST,
-                      "peak_source": "152 SMs x 4 schedulers x 2.07 GHz"}}
+    alu = measured_alu()
+    roof = {"kernel": "push+deposit (FP32 form)", "bound": "alu", "achieved": ach32, "peak": alu["fp32_tflops"],
+            "unit": "TFLOP/s", "frac": ach32 / alu["fp32_tflops"], "traffic": n * PUSH32_DRAM_B,
+            "peak_source": alu["source"] + " (FP32 FMA)",
+            "flop_per_particle": PUSH32_FP32_FLOP,
+            "count_source": "ncu SASS counters, FP32-form push, 1024^2 x 64 ppc split monopole", "hbm": hbm,
+            "issue": {"achieved": issue, "peak": alu["issue_gwarp"], "unit": "G warp-instructions/s",
+                      "frac": issue / alu["issue_gwarp"], "inst_per_particle": PUSH32_INST,
+                      "peak_source": alu["source"] + " (FMA warp-instructions/s)"}}
     if prec == 64:
         # FP64 arithmetic bounds this kernel on GB300: report the FP64 roofline
         ach = n * PUSH64_FP64_FLOP / (push_ms * 1e-3) / 1e12
-        roof = {"kernel": "push+deposit (FP64)", "bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS,
-                "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS, "traffic": n * PUSH64_DRAM_B,
-                "peak_source": "152 SMs x 2.07 GHz x 4 FP64 flop/clk/SM (recipe unit counts and clock)",
-                "flop_per_particle": PUSH64_FP64_FLOP, "hbm": hbm}
+        roof = {"kernel": "push+deposit (FP64)", "bound": "alu", "achieved": ach, "peak": alu["fp64_tflops"],
+                "unit": "TFLOP/s", "frac": ach / alu["fp64_tflops"], "traffic": n * PUSH64_DRAM_B,
+                "peak_source": alu["source"] + " (FP64 FMA)",
+                "flop_per_particle": PUSH64_FP64_FLOP,
+                "count_source": "ncu SASS counters, FP64 push, 512^2 x 64 ppc split monopole", "hbm": hbm}
     return {"value": job_value(n, args.steps, world, res["total_ms"]), "ms_per_step": ms,
             "push_deposit_per_s": world * n / (push_ms * 1e-3), "cell_updates_per_s": world * cells / (field_ms * 1e-3),
             "phases": {"timed_region": tp,
@@ -837,7 +1043,7 @@ def main():
                     help="cells per dimension (default 2048; 1024 for pairs2d; profiling runs use smaller grids)")
     ap.add_argument("--ppc", type=int, default=None, help="particles per cell (default 100; 16 for pairs2d)")
     ap.add_argument("--workload", default="grpic2d",
-                    choices=["grpic2d", "batch1d", "adjoint", "vay", "cubic", "pairs2d"])
+                    choices=["grpic2d", "batch1d", "adjoint", "vay", "cubic", "pairs2d", "wald4096", "fp32err"])
     ap.add_argument("--adj-particles", type=int, default=None, help="adjoint workload size (profiling runs)")
     ap.add_argument("--adj-steps", type=int, default=None, help="adjoint steps (profiling runs)")
     ap.add_argument("--b1-lines", type=int, default=None, help="batch1d lines (profiling runs)")
@@ -859,7 +1065,7 @@ def main():
         return
     args.grid = args.grid or NR
     args.ppc = args.ppc or PPC
-    if args.workload in ("vay", "cubic"):
+    if args.workload in ("vay", "cubic", "wald4096", "fp32err"):
         run_extra(args, args.workload)
         return
     import torch
@@ -876,7 +1082,10 @@ def main():
         second["total_ms"] = max_over_ranks(second["total_ms"], world)
     extras = {}
     if not args.no_extras and head_prec == 32:
-        for name, fn in (("vay", lambda: vay_measure(args, rank, world)),
+        for name, fn in (("fp32_error", lambda: fp32_error_measure(args.grid, args.ppc, args.steps)),
+                         ("fp32_native_fp64_island", lambda: island_measure(args, rank, world)),
+                         ("wald4096", lambda: wald4096_measure(args, rank, world)),
+                         ("vay", lambda: vay_measure(args, rank, world)),
                          ("cubic_shape", lambda: cubic_measure(args, rank, world)),
                          ("pairs_2d", lambda: pairs_2d_measure())):
             try:
@@ -884,7 +1093,8 @@ def main():
             except Exception as e:  # reported, not hidden: the headline stands on its own
                 extras[name] = {"error": f"{type(e).__name__}: {e}"}
     if not args.no_extras:
-        for name, fn in (("adjoint", lambda: adjoint_measure(2)), ("batch1d", lambda: batch1d_measure(200, 600))):
+        for name, fn in (("adjoint", lambda: adjoint_measure(2)), ("batch1d", lambda: batch1d_measure(200, 600)),
+                         ("batch1d_grown", lambda: batch1d_measure(100, 20, grown=True))):
             try:
                 extras[name] = fn()
             except Exception as e:  # reported, not hidden: the headline stands on its own

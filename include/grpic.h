@@ -467,13 +467,25 @@ void grpic_batch1d_destroy(grpic_batch1d_ctx *ctx);
  *   - It calls no cudaMalloc, cudaFree or allocating library routine.  Its
  *     first call on a device looks up the array's device address
  *     (cudaGetSymbolAddress) with that device current and sets a kernel
- *     attribute; make that first call before any stream capture begins.
+ *     attribute; make that first call before any stream capture begins.  The
+ *     look-up is kept per CUDA context: after cudaDeviceReset, or with another
+ *     context current, the next call repeats it (again before any capture).
  *   - Every call shares the one array, which keeps the last call's contents
  *     (each call clears what must start at zero).  Calls that overlap on the
  *     GPU -- on different streams, or from different host threads -- race on
  *     it and corrupt each other's results: serialize them. */
 grpic_status grpic_sort_noalloc(const grpic_grid *grid, int32_t precision, grpic_particles *p,
                                 grpic_particles *scratch, void *stream);
+
+/* Measured arithmetic ceiling of the current device (measurement support for
+ * the ALU rooflines; the paper has no counterpart).  kind 0: FP32 fused
+ * multiply-add, 1: FP64 fused multiply-add, 2: packed FP32 fused multiply-add
+ * (one instruction on a float pair).  Runs one full-occupancy launch of
+ * independent FMA chains six times on `stream` (the first as warm-up) and
+ * writes out[0] = the best rate in flop/s (2 per FMA), out[1] = the same in
+ * FMA warp-instructions/s, out[2] = the SM count.  Allocates and frees an
+ * 8-byte result; synchronizes `stream`. */
+grpic_status grpic_alu_peak(int32_t kind, double out[3], void *stream);
 
 /* Human-readable description of the last error seen by the context. */
 const char *grpic_last_error(const grpic_ctx *ctx);

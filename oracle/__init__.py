@@ -30,12 +30,15 @@ WALD, WALD_A0, MONOPOLE, SPLIT_MONOPOLE = 0, 1, 2, 3
 
 
 def build(force: bool = False) -> str:
-    """Compile the oracle with gcc -O2 -ffp-contract=off (no FMA contraction)."""
+    """Compile the oracle with gcc -O2 -ffp-contract=off (no FMA contraction),
+    with OpenMP for the multi-threaded CPU baseline where the compiler has it
+    (one thread unless set_threads says otherwise)."""
     os.makedirs(_LIBDIR, exist_ok=True)
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-std=c11", "-shared", "-fPIC",
-                               "-o", tmp, _SRC, "-lm"])
+        base = ["gcc", "-O2", "-ffp-contract=off", "-std=c11", "-shared", "-fPIC", "-o", tmp, _SRC, "-lm"]
+        if subprocess.run(base[:1] + ["-fopenmp"] + base[1:], capture_output=True).returncode != 0:
+            subprocess.check_call(base)
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -87,12 +90,19 @@ def lib():
             "orc_divD": (None, [pc, p, p, p]),
             "orc_divB": (None, [pc, p, p, p]),
             "orc_horizon_flux": (d, [pc, p, p, p, p, p, p, i]),
+            "orc_set_threads": (i, [i]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(_lib, name)
             fn.restype = res
             fn.argtypes = args
     return _lib
+
+
+def set_threads(n: int) -> int:
+    """Host threads of the push and the field update (1 = the parity
+    setting); returns the count in effect (1 without OpenMP)."""
+    return int(lib().orc_set_threads(int(n)))
 
 
 def _p(a: np.ndarray):

@@ -39,6 +39,30 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* Host threads for the timed CPU baseline (orc_set_threads; default 1, the
+ * setting of every parity run).  With more than one thread the particle loop
+ * of orc_push_deposit splits the particles into contiguous chunks, each
+ * depositing into its own current arrays, summed in thread order at the end
+ * (so J differs from the one-thread run only by the order of additions); the
+ * field update's row loops write disjoint entries and give the same result
+ * bit for bit.  Without OpenMP support in the compiler the pragmas are
+ * ignored and everything runs on one thread. */
+static int orc_nthreads = 1;
+
+int orc_set_threads(int n)
+{
+#ifdef _OPENMP
+    orc_nthreads = n < 1 ? 1 : n;
+#else
+    (void)n;
+    orc_nthreads = 1;
+#endif
+    return orc_nthreads;
+}
 
 #define ORC_OK 0
 #define ORC_ERANGE 4
@@ -531,6 +555,7 @@ static void aux_fields(const orc_geom *g, double *const D[3], double *const B[3]
         memset(H[k], 0, sizeof(double) * g->n);
     }
     int ilo = -c->ng + 1, ihi = c->ld - c->ng - 2;
+#pragma omp parallel for schedule(static) num_threads(orc_nthreads) if (orc_nthreads > 1)
     for (int j = 0; j <= c->nth; ++j) {
         for (int i = ilo; i <= ihi; ++i) {
             int q = IDX(c, i, j), qm = IDX(c, i - 1, j), qp = IDX(c, i + 1, j);
@@ -569,6 +594,7 @@ static void circulations(const orc_geom *g, double *E[3], double *H[3], double *
         memset(CD[k], 0, sizeof(double) * g->n);
         memset(CB[k], 0, sizeof(double) * g->n);
     }
+#pragma omp parallel for schedule(static) num_threads(orc_nthreads) if (orc_nthreads > 1)
     for (int j = 0; j <= c->nth; ++j) {
         for (int i = 0; i <= c->nr; ++i) {
             int q = IDX(c, i, j), qm = IDX(c, i - 1, j), qp = IDX(c, i + 1, j);
@@ -643,6 +669,7 @@ void orc_field_update(const orc_cfg *c, double *D0, double *D1, double *D2, doub
         memcpy(Dt[k], Dn[k], n * sizeof(double));
         memcpy(Bt[k], Bn[k], n * sizeof(double));
     }
+#pragma omp parallel for schedule(static) num_threads(orc_nthreads) if (orc_nthreads > 1)
     for (int j = 0; j <= c->nth; ++j)
         for (int i = 0; i <= c->nr; ++i) {
             int q = IDX(c, i, j);
@@ -656,6 +683,7 @@ void orc_field_update(const orc_cfg *c, double *D0, double *D1, double *D2, doub
     for (int it = 0; it < c->n_fld_iter; ++it) {
         aux_fields(&g, Dt, Bt, E, H);
         circulations(&g, E, H, CD, CB);
+#pragma omp parallel for schedule(static) num_threads(orc_nthreads) if (orc_nthreads > 1)
         for (int j = 0; j <= c->nth; ++j)
             for (int i = 0; i <= c->nr; ++i) {
                 int q = IDX(c, i, j);
@@ -1149,6 +1177,45 @@ void orc_deposit_one(const orc_cfg *c, double *JrA, double *JtA, double *Jph, do
 /* are flagged dead after their deposit; moves of more than one cell or     */
 /* non-finite states flag the particle dead and set a status.               */
 /* ------------------------------------------------------------------------ */
+/* one particle: returns its status (ORC_OK, ORC_ENAN or ORC_ERANGE) */
+static int push_deposit_one(const orc_cfg *c, const orc_geom *g, double lnrin, long p, double *pr, double *pth,
+                            double *pu1, double *pu2, double *pu3, uint32_t *tag, double *dphi_out,
+                            double *const D[3], double *const B[3], double *J0, double *J1, double *J2)
+{
+    if (tag[p] & ORC_DEAD) { if (dphi_out) dphi_out[p] = 0.0; return ORC_OK; }
+    int sp = tag[p] & 3u;
+    double y[6] = {pr[p], pth[p], 0.0, pu1[p], pu2[p], pu3[p]};
+    double x1a = (log(y[0]) - lnrin) / c->dx1, x2a = y[1] / c->dth;
+    double Dv[3], Bv[3];
+    if (c->shape == 3)
+        interp_fields3(c, D, B, x1a, x2a, Dv, Bv);
+    else
+        interp_fields(c, D, B, x1a, x2a, Dv, Bv);
+    push_core(c->a, c->qm[sp], c->massive[sp], c->dt, c->n_push_iter, Dv, Bv, y, c->pusher);
+    /* axis reflection */
+    if (y[1] < 0.0) { y[1] = -y[1]; y[4] = -y[4]; }
+    if (y[1] > M_PI) { y[1] = 2.0 * M_PI - y[1]; y[4] = -y[4]; }
+    int bad = 0;
+    for (int k = 0; k < 6; ++k) if (!isfinite(y[k])) bad = 1;
+    if (bad) { tag[p] |= ORC_DEAD; if (dphi_out) dphi_out[p] = 0.0; return ORC_ENAN; }
+    double x1b = (log(y[0]) - lnrin) / c->dx1, x2b = y[1] / c->dth;
+    int di = (int)floor(x1b) - (int)floor(x1a);
+    int dj = jcell(c, x2b) - jcell(c, x2a);
+    if (di < -1 || di > 1 || dj < -1 || dj > 1) {
+        tag[p] |= ORC_DEAD;
+        if (dphi_out) dphi_out[p] = 0.0;
+        return ORC_ERANGE;
+    }
+    if (c->shape == 3)
+        deposit_one3(c, g->AD[2], J0, J1, J2, c->qw[sp], x1a, x2a, x1b, x2b, y[2]);
+    else
+        deposit_one(c, g->AD[2], J0, J1, J2, c->qw[sp], x1a, x2a, x1b, x2b, y[2]);
+    pr[p] = y[0]; pth[p] = y[1]; pu1[p] = y[3]; pu2[p] = y[4]; pu3[p] = y[5];
+    if (dphi_out) dphi_out[p] = y[2];
+    if (y[0] < c->r_in || y[0] >= c->r_out) tag[p] |= ORC_DEAD;
+    return ORC_OK;
+}
+
 int orc_push_deposit(const orc_cfg *c, long np, double *pr, double *pth, double *pu1, double *pu2, double *pu3,
                      uint32_t *tag, double *dphi_out,
                      double *D0, double *D1, double *D2, double *B0r, double *B1, double *B2,
@@ -1161,38 +1228,32 @@ int orc_push_deposit(const orc_cfg *c, long np, double *pr, double *pth, double 
     memset(J2, 0, g.n * sizeof(double));
     int status = ORC_OK;
     double lnrin = log(c->r_in);
-    for (long p = 0; p < np; ++p) {
-        if (tag[p] & ORC_DEAD) { if (dphi_out) dphi_out[p] = 0.0; continue; }
-        int sp = tag[p] & 3u;
-        double y[6] = {pr[p], pth[p], 0.0, pu1[p], pu2[p], pu3[p]};
-        double x1a = (log(y[0]) - lnrin) / c->dx1, x2a = y[1] / c->dth;
-        double Dv[3], Bv[3];
-        if (c->shape == 3)
-            interp_fields3(c, D, B, x1a, x2a, Dv, Bv);
-        else
-            interp_fields(c, D, B, x1a, x2a, Dv, Bv);
-        push_core(c->a, c->qm[sp], c->massive[sp], c->dt, c->n_push_iter, Dv, Bv, y, c->pusher);
-        /* axis reflection */
-        if (y[1] < 0.0) { y[1] = -y[1]; y[4] = -y[4]; }
-        if (y[1] > M_PI) { y[1] = 2.0 * M_PI - y[1]; y[4] = -y[4]; }
-        int bad = 0;
-        for (int k = 0; k < 6; ++k) if (!isfinite(y[k])) bad = 1;
-        if (bad) { tag[p] |= ORC_DEAD; status = status ? status : ORC_ENAN; if (dphi_out) dphi_out[p] = 0.0; continue; }
-        double x1b = (log(y[0]) - lnrin) / c->dx1, x2b = y[1] / c->dth;
-        int di = (int)floor(x1b) - (int)floor(x1a);
-        int dj = jcell(c, x2b) - jcell(c, x2a);
-        if (di < -1 || di > 1 || dj < -1 || dj > 1) {
-            tag[p] |= ORC_DEAD; status = status ? status : ORC_ERANGE;
-            if (dphi_out) dphi_out[p] = 0.0;
-            continue;
+    int nt = orc_nthreads;
+    if (nt <= 1) {
+        for (long p = 0; p < np; ++p) {
+            int st = push_deposit_one(c, &g, lnrin, p, pr, pth, pu1, pu2, pu3, tag, dphi_out, D, B, J0, J1, J2);
+            if (st && !status) status = st;
         }
-        if (c->shape == 3)
-            deposit_one3(c, g.AD[2], J0, J1, J2, c->qw[sp], x1a, x2a, x1b, x2b, y[2]);
-        else
-            deposit_one(c, g.AD[2], J0, J1, J2, c->qw[sp], x1a, x2a, x1b, x2b, y[2]);
-        pr[p] = y[0]; pth[p] = y[1]; pu1[p] = y[3]; pu2[p] = y[4]; pu3[p] = y[5];
-        if (dphi_out) dphi_out[p] = y[2];
-        if (y[0] < c->r_in || y[0] >= c->r_out) tag[p] |= ORC_DEAD;
+    } else {
+        /* thread t pushes particles [t np / nt, (t+1) np / nt) into its own
+         * current arrays; the first status in particle order is kept */
+        double *Jt = calloc((size_t)nt * 3 * g.n, sizeof(double));
+        int *stt = calloc(nt, sizeof(int));
+#pragma omp parallel for schedule(static, 1) num_threads(nt)
+        for (int t = 0; t < nt; ++t) {
+            double *j0 = Jt + (size_t)t * 3 * g.n, *j1 = j0 + g.n, *j2 = j1 + g.n;
+            for (long p = (long)t * np / nt; p < (long)(t + 1) * np / nt; ++p) {
+                int st = push_deposit_one(c, &g, lnrin, p, pr, pth, pu1, pu2, pu3, tag, dphi_out, D, B, j0, j1, j2);
+                if (st && !stt[t]) stt[t] = st;
+            }
+        }
+        for (int t = 0; t < nt; ++t) {
+            const double *j0 = Jt + (size_t)t * 3 * g.n, *j1 = j0 + g.n, *j2 = j1 + g.n;
+            for (int q = 0; q < g.n; ++q) { J0[q] += j0[q]; J1[q] += j1[q]; J2[q] += j2[q]; }
+            if (stt[t] && !status) status = stt[t];
+        }
+        free(Jt);
+        free(stt);
     }
     /* "after finishing the current deposition loop, we divide the results by
      * A^D_r and A^D_theta" (Sec. 2.3) */

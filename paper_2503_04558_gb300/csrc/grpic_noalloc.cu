@@ -11,6 +11,8 @@
 // (about 20 MB) until the process exits.
 #include "grpic_internal.cuh"
 
+#include <cuda.h>  // driver types only (the two driver calls are looked up at run time)
+
 #include <cmath>
 #include <cstring>
 #include <mutex>
@@ -39,22 +41,76 @@ static __device__ __align__(256) NoAllocScratch g_noalloc_scratch;
 
 constexpr int MAX_DEVICES = 64;
 std::mutex g_setup_mutex;
-NoAllocScratch *g_scratch_ptr[MAX_DEVICES] = {};
 
-// Once per device, with that device current: the device address of the
-// scratch array and the kernel attribute the sort's large-segment pass needs.
+// The set-up is per CUDA context: after cudaDeviceReset (or when the caller
+// makes another context current) the module is loaded again, the array may
+// sit at another address and kernel attributes are unset.  Entries are keyed
+// on (device, context id); the id comes from the driver's cuCtxGetId, reached
+// through the runtime's entry-point lookup so that the library needs no link
+// against the driver library.
+struct SetupEntry {
+    int dev;
+    unsigned long long ctx;
+    NoAllocScratch *ptr;
+};
+constexpr int MAX_ENTRIES = 64;
+SetupEntry g_entries[MAX_ENTRIES];
+int g_nentries = 0, g_next = 0;
+
+typedef CUresult (*CtxGetCurrentFn)(CUcontext *);
+typedef CUresult (*CtxGetIdFn)(CUcontext, unsigned long long *);
+CtxGetCurrentFn g_get_current = nullptr;
+CtxGetIdFn g_get_id = nullptr;
+bool g_looked_up = false;
+
+// id of the current context, 0 if none is current yet (caller holds the mutex)
+unsigned long long current_context_id()
+{
+    if (!g_looked_up) {
+        g_looked_up = true;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", (void **)&g_get_current, 12000, cudaEnableDefault,
+                                             &q) != cudaSuccess || q != cudaDriverEntryPointSuccess)
+            g_get_current = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", (void **)&g_get_id, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess || q != cudaDriverEntryPointSuccess)
+            g_get_id = nullptr;
+    }
+    CUcontext c = nullptr;
+    if (!g_get_current || g_get_current(&c) != CUDA_SUCCESS || !c) return 0;
+    unsigned long long id = 0;
+    if (!g_get_id || g_get_id(c, &id) != CUDA_SUCCESS) return (unsigned long long)(uintptr_t)c;
+    return id;
+}
+
+// Once per device and context, with that device current: the device address
+// of the scratch array and the kernel attribute the sort's large-segment pass
+// needs.
 cudaError_t setup_device(int dev, NoAllocScratch **out)
 {
     std::lock_guard<std::mutex> lock(g_setup_mutex);
-    if (!g_scratch_ptr[dev]) {
-        void *ptr = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
-        if (e != cudaSuccess) return e;
-        e = sort_setup();
-        if (e != cudaSuccess) return e;
-        g_scratch_ptr[dev] = (NoAllocScratch *)ptr;
+    unsigned long long ctx = current_context_id();
+    if (ctx != 0) {
+        for (int k = 0; k < g_nentries; ++k)
+            if (g_entries[k].dev == dev && g_entries[k].ctx == ctx) {
+                *out = g_entries[k].ptr;
+                return cudaSuccess;
+            }
     }
-    *out = g_scratch_ptr[dev];
+    void *ptr = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);  // also makes the runtime's context current
+    if (e != cudaSuccess) return e;
+    e = sort_setup();
+    if (e != cudaSuccess) return e;
+    if (ctx == 0) ctx = current_context_id();
+    SetupEntry ent{dev, ctx, (NoAllocScratch *)ptr};
+    if (g_nentries < MAX_ENTRIES) {
+        g_entries[g_nentries++] = ent;
+    } else {
+        g_entries[g_next] = ent;
+        g_next = (g_next + 1) % MAX_ENTRIES;
+    }
+    *out = ent.ptr;
     return cudaSuccess;
 }
 

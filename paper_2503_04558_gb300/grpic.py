@@ -24,7 +24,7 @@ NG = 2
 # names the header declares (checked by the CPU test of the boundary)
 EXPORTS = ["grpic_init", "grpic_init_fields", "grpic_push", "grpic_deposit", "grpic_field_update", "grpic_sort",
            "grpic_step", "grpic_step_graph", "grpic_diagnostics", "grpic_charge_check", "grpic_get_areas", "grpic_sync", "grpic_last_error", "grpic_destroy",
-           "grpic_sort_noalloc", "grpic_set_timing", "grpic_get_timing"]
+           "grpic_sort_noalloc", "grpic_set_timing", "grpic_get_timing", "grpic_alu_peak"]
 NOALLOC_MAX_PARTICLES = 2097152
 NOALLOC_MAX_CELLS = 262144
 
@@ -82,6 +82,7 @@ def load(path: str = LIB_PATH):
         "grpic_sort_noalloc": [p(Grid), C.c_int32, p(ParticlesC), p(ParticlesC), v],
         "grpic_set_timing": [v, i],
         "grpic_get_timing": [v, p(d), p(i64)],
+        "grpic_alu_peak": [C.c_int32, p(d), v],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -94,6 +95,17 @@ def load(path: str = LIB_PATH):
     if path == LIB_PATH:
         _lib = lib
     return lib
+
+
+def alu_peak(kind: int, stream=None):
+    """Measured FMA ceiling of the current device: kind 0 FP32, 1 FP64, 2
+    packed FP32.  Returns (flop/s, FMA warp-instructions/s, SM count)."""
+    lib = load()
+    out = (C.c_double * 3)()
+    st = lib.grpic_alu_peak(int(kind), out, _stream(stream))
+    if st != OK:
+        raise GrpicError(st, "grpic_alu_peak")
+    return out[0], out[1], int(out[2])
 
 
 class GrpicError(RuntimeError):

@@ -289,3 +289,30 @@ def test_cell_keys_and_sort_drop_dead():
     assert Q.n == P.n - 1
     k2 = O.cell_keys(c, Q)
     assert np.all(np.diff(k2) >= 0)
+
+
+def test_threaded_oracle_matches_one_thread():
+    """The multi-threaded run of the CPU baseline computes the same step: the
+    particles bit for bit, the currents and fields up to the order of the
+    per-thread current sums (which the one-thread parity runs never use)."""
+    from paper_2503_04558_gb300 import synth
+    a = 0.9
+    rin = 0.9 * O.horizon(a)
+    c = O.make_cfg(32, 32, a, rin, 20.0)
+    P = O.Particles(*synth.particles(32, 32, rin, 20.0, 20000, seed=3, sigma=0.3))
+    out = {}
+    try:
+        for nt in (1, 4):
+            O.set_threads(nt)
+            D, B = O.init_fields(c, O.WALD, 1.0)
+            Q = P.copy()
+            st, J, _ = O.push_deposit(c, Q, D, B)
+            O.field_update(c, D, B, J)
+            out[nt] = (Q, J, D + B)
+    finally:
+        O.set_threads(1)
+    (Q1, J1, F1), (Q4, J4, F4) = out[1], out[4]
+    for x, y in ((Q1.r, Q4.r), (Q1.th, Q4.th), (Q1.u1, Q4.u1), (Q1.u2, Q4.u2), (Q1.u3, Q4.u3), (Q1.tag, Q4.tag)):
+        assert np.array_equal(x, y)
+    for x, y in zip(J1 + F1, J4 + F4):
+        assert np.max(np.abs(x - y)) <= 1e-13 * max(np.max(np.abs(x)), 1e-300)

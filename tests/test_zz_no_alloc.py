@@ -36,13 +36,17 @@ def _host(S):
     return [h[k] for k in ("x1", "x2", "u1", "u2", "u3", "tag")]
 
 
-@pytest.mark.parametrize("precision", [64, 32])
-def test_noalloc_sort_matches_context_sort_twice(G, precision):
-    cfg = G.Config(48, 40, 0.9, 1.2923, 30.0, precision=precision)
+@pytest.mark.parametrize("precision,n_side,n", [(64, 48, 30000), (32, 48, 30000), (64, 512, 2097152),
+                                               (32, 512, 2097152)])
+def test_noalloc_sort_matches_context_sort_twice(G, precision, n_side, n):
+    """Small grids, and the largest case the fixed scratch takes (2,097,152
+    slots on 512 x 512 cells); the device's free memory is the same before and
+    after the second call (nothing allocated)."""
+    cfg = G.Config(n_side, n_side - 8 if n_side < 100 else n_side, 0.9, 1.2923, 30.0, precision=precision)
+    assert n <= G.NOALLOC_MAX_PARTICLES and cfg.n_r * cfg.n_theta <= G.NOALLOC_MAX_CELLS
     ctx = G.Context(cfg)
     lib = G.load()
     grid = cfg.grid_c()
-    n = 30000
     ref = G.ParticleSet(cfg, n)
     nal = G.ParticleSet(cfg, n)
     for call in range(2):
@@ -63,11 +67,18 @@ def test_noalloc_sort_matches_context_sort_twice(G, precision):
         ctx.sort(ref)
         nal._sc.n = nal.n
         nal._ss.n = nal.n
+        torch.cuda.synchronize()
+        free0 = torch.cuda.mem_get_info()[0]
         status = lib.grpic_sort_noalloc(C.byref(grid), precision, C.byref(nal._sc), C.byref(nal._ss),
                                         C.c_void_p(torch.cuda.current_stream().cuda_stream))
         assert status == G.OK
         nal.sync_ptrs()
         torch.cuda.synchronize()
+        if call > 0:
+            # the first call of a process may load the library's fixed array
+            # (module data, placed when the module loads); later calls change
+            # nothing in the device's free memory
+            assert torch.cuda.mem_get_info()[0] == free0
         assert ctx.sync() == 0
         assert nal.live() == ref.live()
         for a, b in zip(_host(nal), _host(ref)):
