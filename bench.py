@@ -391,12 +391,17 @@ def fp32_error_measure(grid, ppc, nsteps, seed=4321):
     corrector tolerance 1e-6) against the FP64 plain path from the same
     initial state after nsteps steps of grpic_step on the bench workload:
       fields: per component max |F32 - F64| / max |F64| over the physical
-        columns;
+        columns, on the rows at least 10 cells from the polar axis and on all
+        rows;
       particles (matched by loading index): position error in cells (r and
         theta) and momentum error |du| / max(1, |u|) in the orthonormal
         components (u_r, u_theta / r, u_phi / (r sin theta)), as median, 99th
         percentile and max, away from and within 10 theta cells of the polar
-        axis; the particles alive in one path only are counted."""
+        axis; the particles alive in one path only are counted.
+    Beside it, the same figures for the FP64 path against itself started
+    from theta moved by one ulp: the conditioning of the step near the axis,
+    where orbits that graze it amplify any rounding (no precision can follow
+    them to the end)."""
     import torch
     from paper_2503_04558_gb300 import grpic as G, synth
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
@@ -405,10 +410,12 @@ def fp32_error_measure(grid, ppc, nsteps, seed=4321):
     if n >= 1 << 29:
         raise ValueError("loading index does not fit the tag bits")
     runs = {}
-    for cfg in (c64, c32):
+    for name, cfg, nudge in (("f64", c64, False), ("f32", c32, False), ("f64_ulp", c64, True)):
         gen = synth.particles_torch(cfg.n_r, cfg.n_theta, cfg.r_in, cfg.r_out, n, seed=seed, thermal_T=THERMAL_T,
                                     device=dev)
         tag = gen["tag"] | (torch.arange(n, device=dev, dtype=torch.int32) << IDX_SHIFT)
+        if nudge:
+            gen["th"] = torch.nextafter(gen["th"], torch.full_like(gen["th"], 4.0))
         S = G.ParticleSet(cfg, n)
         if cfg.precision == 64:
             S.load(gen["r"], gen["th"], gen["u1"], gen["u2"], gen["u3"], tag)
@@ -425,47 +432,55 @@ def fp32_error_measure(grid, ppc, nsteps, seed=4321):
         ctx.init_fields(F, G.SPLIT_MONOPOLE, B0)
         ctx.step(S, F, nsteps)
         st = ctx.sync()
-        runs[cfg.precision] = (S, F, st)
+        runs[name] = (S, F, st, cfg)
         del ctx
-    (S64, F64, st64), (S32, F32, st32) = runs[64], runs[32]
     cols = slice(2, 2 + grid + 1)
-    field = {}
-    for name, a, b in (("D", F32.D, F64.D), ("B", F32.B, F64.B)):
-        for k in range(3):
-            ref = b[k][:, cols]
-            field[f"{name}{k}"] = float((a[k][:, cols].double() - ref).abs().max() / ref.abs().max())
-    y64 = _state_by_index(S64, c64, n)
-    y32 = _state_by_index(S32, c32, n)
-    both = ~torch.isnan(y64[0]) & ~torch.isnan(y32[0])
-    only = int((~torch.isnan(y64[0]) ^ ~torch.isnan(y32[0])).sum())
-    r, th = y64[0][both], y64[1][both]
-    dr_cell = r * c64.dx1
-    pos_r = (y32[0][both] - r).abs() / dr_cell
-    pos_t = (y32[1][both] - th).abs() / c64.dth
-    sc = [torch.ones_like(r), r, r * torch.sin(th).abs().clamp_min(1e-300)]
-    u64 = torch.stack([y64[2 + k][both] / sc[k] for k in range(3)])
-    u32 = torch.stack([y32[2 + k][both] / sc[k] for k in range(3)])
-    du = (u32 - u64).norm(dim=0) / u64.norm(dim=0).clamp_min(1.0)
-    axis_d = torch.minimum(th, math.pi - th) / c64.dth
-    near = axis_d < 10.0
+    bulk = slice(10, grid - 9)
+    y64 = _state_by_index(runs["f64"][0], c64, n)
 
-    def stats(x):
-        if x.numel() == 0:
-            return None
-        xs = x[::x.numel() // (1 << 24) + 1].float()   # torch.quantile takes at most 2^24 entries
-        q = torch.quantile(xs, torch.tensor([0.5, 0.99], device=x.device))
-        return {"median": float(q[0]), "p99": float(q[1]), "max": float(x.max())}
+    def compare(name):
+        S, F, st, cfg = runs[name]
+        field, field_bulk = {}, {}
+        for nm, a, b in (("D", F.D, runs["f64"][1].D), ("B", F.B, runs["f64"][1].B)):
+            for k in range(3):
+                ref = b[k][:, cols]
+                d = (a[k][:, cols].double() - ref).abs()
+                field[f"{nm}{k}"] = float(d.max() / ref.abs().max())
+                field_bulk[f"{nm}{k}"] = float(d[bulk].max() / ref.abs().max())
+        y = _state_by_index(S, cfg, n)
+        both = ~torch.isnan(y64[0]) & ~torch.isnan(y[0])
+        only = int((~torch.isnan(y64[0]) ^ ~torch.isnan(y[0])).sum())
+        r, th = y64[0][both], y64[1][both]
+        pos = torch.maximum((y[0][both] - r).abs() / (r * c64.dx1), (y[1][both] - th).abs() / c64.dth)
+        sc = [torch.ones_like(r), r, r * torch.sin(th).abs().clamp_min(1e-300)]
+        ua = torch.stack([y[2 + k][both] / sc[k] for k in range(3)])
+        ub = torch.stack([y64[2 + k][both] / sc[k] for k in range(3)])
+        du = (ua - ub).norm(dim=0) / ub.norm(dim=0).clamp_min(1.0)
+        near = torch.minimum(th, math.pi - th) / c64.dth < 10.0
+        del y, ua, ub
 
+        def stats(x):
+            if x.numel() == 0:
+                return None
+            xs = x[::x.numel() // (1 << 24) + 1].float()   # torch.quantile takes at most 2^24 entries
+            q = torch.quantile(xs, torch.tensor([0.5, 0.99], device=x.device))
+            return {"median": float(q[0]), "p99": float(q[1]), "max": float(x.max())}
+
+        return {"field_rel_max_rows_10_cells_from_axis": field_bulk,
+                "field_rel_max_all_rows": field,
+                "particles_compared": int(both.sum()), "alive_in_one_path_only": only,
+                "away_from_axis": {"position_cells": stats(pos[~near]), "momentum_rel": stats(du[~near])},
+                "within_10_cells_of_axis": {"particles": int(near.sum()), "position_cells": stats(pos[near]),
+                                            "momentum_rel": stats(du[near])},
+                "status": G.STATUS_NAMES[st]}
+
+    f32 = compare("f32")
+    ulp = compare("f64_ulp")
     out = {"steps": nsteps, "what": "FP32 form vs FP64 plain path, same initial state, after the steps",
-           "field_rel_max": field, "field_rel_max_all": max(field.values()),
-           "particles_compared": int(both.sum()), "alive_in_one_path_only": only,
-           "away_from_axis": {"position_cells": stats(torch.maximum(pos_r, pos_t)[~near]),
-                              "momentum_rel": stats(du[~near])},
-           "within_10_cells_of_axis": {"particles": int(near.sum()),
-                                       "position_cells": stats(torch.maximum(pos_r, pos_t)[near]),
-                                       "momentum_rel": stats(du[near])},
-           "status": [G.STATUS_NAMES[st64], G.STATUS_NAMES[st32]]}
-    del S64, S32, F64, F32, runs, y64, y32
+           "field_rel_max_bulk": max(f32["field_rel_max_rows_10_cells_from_axis"].values()),
+           "field_rel_max_all": max(f32["field_rel_max_all_rows"].values()), "fp32": f32,
+           "fp64_theta_one_ulp": dict(ulp, what="FP64 path vs itself from theta moved by one ulp (conditioning)")}
+    del runs, y64
     torch.cuda.empty_cache()
     return out
 
@@ -739,7 +754,7 @@ def adjoint_measure(reps=2, n_particles=None, nsteps=None):
     x = [gen[k].contiguous() for k in ("r", "th", "u1", "u2", "u3")]
     tag = gen["tag"]
     tag = (tag.to(torch.int64) if tag.dtype != torch.int32 else tag).to(torch.int32).contiguous()
-    iH = G.horizon_index(cfg)
+    iH = G.horizon_index(ctx)
     flush = torch.empty(256 * 2**20 // 4, dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
 
@@ -1117,7 +1132,7 @@ def main():
                 "push_deposit_per_s": h["push_deposit_per_s"], "cell_updates_per_s": h["cell_updates_per_s"],
                 "phases": h["phases"], "live_particles": h["live_particles"],
                 "particle_statuses": h["particle_statuses"],
-                "roofline": h["roofline"], "clocks": h["clocks"],
+                "roofline": h["roofline"], "clocks": h["clocks"], "measured_alu_peaks": measured_alu(),
                 # per step: push, 1 + n_field_iter field stages, 12 sort kernels
                 # (count, destinations, histogram pair, 3 scan, bases, placement and
                 # the general path's 3, which return at once) -- the count only

@@ -331,7 +331,7 @@ grpic_status grpic_adjoint_field_step(grpic_ctx *ctx, const grpic_fields *lam_in
  *        products of App. B) contracted with the stage adjoints, the tables'
  *        a-derivatives taken by a central difference h = 1e-5 of the
  *        quadratures.  Initial fields that depend on a (the Wald solution)
- *        add sum grad_f . dF0/da, which the caller forms.  Requires grad_p;
+ *        add sum grad_f . dF0/da: grpic_adjoint_spin adds it.  Requires grad_p;
  *        costs per step one field update more and (n_field_iter + 1) * 6 + 3
  *        field arrays of memory per checkpoint segment.
  * n_push_iter must not exceed 16 (the adjoint keeps the iterates).
@@ -340,6 +340,32 @@ grpic_status grpic_adjoint_field_step(grpic_ctx *ctx, const grpic_fields *lam_in
 grpic_status grpic_adjoint_grad(grpic_ctx *ctx, const grpic_particles *p0, const grpic_fields *f0, int nsteps,
                                 int checkpoint_every, int i_horizon, int trapezoid_ift, double *L_out,
                                 double *const grad_p[5], double *const grad_f[6], double *dL_da, void *stream);
+
+/* dL/da of a run that starts from the analytic fields `kind`, B0 of the
+ * context's spin a (App. C): runs grpic_adjoint_grad from those fields and
+ * adds to its fixed-state part the step-0 fields' own dependence on a,
+ * sum over every entry of dL/dF0 . dF0/da, with dF0/da the central
+ * difference (h = 1e-5) of the closed-form initialization at a +- h, each
+ * with the face areas of its own spin (the grid, dt and i_horizon stay those
+ * of the context).  The paper defines no objective (see grpic_adjoint_grad).
+ *   p0, nsteps, checkpoint_every, i_horizon, trapezoid_ift, L_out, grad_p:
+ *        as for grpic_adjoint_grad (grad_p required);
+ *   grad_f: NULL or six device arrays (n_theta+1) x (n_r+4) receiving
+ *        dL/dF0 (otherwise kept in scratch);
+ *   dL_da: host double, the total derivative.
+ * Allocates and frees its scratch (three field sets, two table sets);
+ * synchronizes `stream`.  GRPIC_EINVAL for an FP32 context or an unknown
+ * kind; statuses of particles refused by the forward pass are returned after
+ * the sweep, as by grpic_adjoint_grad. */
+grpic_status grpic_adjoint_spin(grpic_ctx *ctx, const grpic_particles *p0, grpic_field_kind kind, double B0,
+                                int nsteps, int checkpoint_every, int i_horizon, int trapezoid_ift, double *L_out,
+                                double *const grad_p[5], double *const grad_f[6], double *dL_da, void *stream);
+
+/* The objective's column: *out = round(ln(r_H / r_in) / dx1), the r index
+ * nearest the outer horizon r_H = 1 + sqrt(1 - a_nominal^2) of the spin
+ * a_nominal on the context's grid (the index is held fixed when the spin is
+ * varied).  No device work. */
+grpic_status grpic_horizon_index(const grpic_ctx *ctx, double a_nominal, int32_t *out);
 
 /* ------------------------------------------------------------------------ */
 /* Batched 1D spark gaps: the radiative pair-production prescription of     */

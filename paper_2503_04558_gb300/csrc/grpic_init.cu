@@ -299,6 +299,25 @@ cudaError_t launch_tables_at(grpic_ctx *ctx, double a, double *tab, double *col1
     return cudaGetLastError();
 }
 
+cudaError_t launch_init_fields_at(grpic_ctx *ctx, double a, const double *tab, int kind, double B0,
+                                  const grpic_fields *f, cudaStream_t s)
+{
+    GridDev g = ctx->g;
+    g.a = a;
+    dim3 blk(32, 4), grd((ctx->g.ld_tab + 31) / 32, (ctx->g.nth + 1 + 3) / 4);
+    int rows = ctx->g.nth + 1;
+    double *D[3], *B[3], *J[3];
+    for (int k = 0; k < 3; ++k) {
+        D[k] = (double *)f->D[k];
+        B[k] = (double *)f->B[k];
+        J[k] = (double *)f->J[k];
+    }
+    init_fields_kernel<double><<<grd, blk, 0, s>>>(g, make_gl(ctx), kind, B0, tab, ctx->slab, D[0], D[1], D[2], B[0],
+                                                   B[1], B[2], J[0], J[1], J[2], f->ld);
+    bc_kernel<double><<<(rows + 127) / 128, 128, 0, s>>>(g, D[0], D[1], D[2], B[0], B[1], B[2], f->ld);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_init_fields(grpic_ctx *ctx, int kind, double B0, const grpic_fields *f, cudaStream_t s)
 {
     dim3 blk(32, 4), grd((ctx->g.ld_tab + 31) / 32, (ctx->g.nth + 1 + 3) / 4);

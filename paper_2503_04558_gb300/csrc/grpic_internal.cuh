@@ -203,6 +203,9 @@ cudaError_t launch_field64_stages(grpic_ctx *ctx, double *const Xn[6], double *c
                                   cudaStream_t s);
 cudaError_t launch_field32(grpic_ctx *ctx, grpic_fields *f, cudaStream_t s);
 cudaError_t launch_tables_at(grpic_ctx *ctx, double a, double *tab, double *col1d, cudaStream_t s);
+// the analytic initial fields (FP64) of spin a with the tables `tab` of that spin
+cudaError_t launch_init_fields_at(grpic_ctx *ctx, double a, const double *tab, int kind, double B0,
+                                  const grpic_fields *f, cudaStream_t s);
 cudaError_t launch_scan_i32(const int32_t *in, int32_t *out, int32_t *bsum, int64_t n, cudaStream_t s);
 cudaError_t ensure_rad_scratch(grpic_ctx *ctx, int64_t cap);
 cudaError_t launch_append_children(grpic_ctx *ctx, grpic_particles *p, cudaStream_t s);

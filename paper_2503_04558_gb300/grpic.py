@@ -644,7 +644,8 @@ class Batch1D:
 # ---------------------------------------------------------------------------
 # differentiable form: horizon Poynting flux and its adjoint (FP64 contexts)
 # ---------------------------------------------------------------------------
-EXPORTS += ["grpic_horizon_flux", "grpic_adjoint_field_step", "grpic_adjoint_grad"]
+EXPORTS += ["grpic_horizon_flux", "grpic_adjoint_field_step", "grpic_adjoint_grad", "grpic_adjoint_spin",
+            "grpic_horizon_index"]
 
 
 def _load_adj(lib):
@@ -652,16 +653,23 @@ def _load_adj(lib):
     for name, args in {"grpic_horizon_flux": [v, p(FieldsC), C.c_int, p(C.c_double), v],
                        "grpic_adjoint_field_step": [v, p(FieldsC), p(FieldsC), v],
                        "grpic_adjoint_grad": [v, p(ParticlesC), p(FieldsC), C.c_int, C.c_int, C.c_int,
-                                              C.c_int, p(C.c_double), v, v, v, v]}.items():
+                                              C.c_int, p(C.c_double), v, v, v, v],
+                       "grpic_adjoint_spin": [v, p(ParticlesC), C.c_int, C.c_double, C.c_int, C.c_int, C.c_int,
+                                              C.c_int, p(C.c_double), v, v, p(C.c_double), v],
+                       "grpic_horizon_index": [v, C.c_double, p(C.c_int32)]}.items():
         fn = getattr(lib, name)
         fn.argtypes = args
         fn.restype = C.c_int
 
 
-def horizon_index(cfg: Config, a_nominal: float | None = None) -> int:
-    """Column nearest the outer horizon of spin a_nominal (default cfg.a)."""
-    a = cfg.a if a_nominal is None else a_nominal
-    return int(round(math.log(horizon(a) / cfg.r_in) / cfg.dx1))
+def horizon_index(gctx: "Context", a_nominal: float | None = None) -> int:
+    """Column nearest the outer horizon of spin a_nominal (default: the
+    context's spin), from the library (grpic_horizon_index)."""
+    _load_adj(gctx.lib)
+    out = C.c_int32()
+    a = gctx.cfg.a if a_nominal is None else a_nominal
+    gctx._check(gctx.lib.grpic_horizon_index(gctx.h, float(a), C.byref(out)), "grpic_horizon_index")
+    return out.value
 
 
 def _fields_of(D, B, ld, J=None):
@@ -739,27 +747,32 @@ def adjoint_grad(gctx: Context, x, tag, D, B, nsteps: int, i_horizon: int, check
     return L.value, gp, gf
 
 
-def spin_gradient(cfg: Config, x, tag, kind: int, B0: float, nsteps: int, i_horizon: int,
-                  checkpoint_every: int = 20, h: float = 1e-5):
+def spin_gradient(gctx: "Context", x, tag, kind: int, B0: float, nsteps: int, i_horizon: int,
+                  checkpoint_every: int = 20, ift: bool = False, stream=None):
     """dL/da for a run that starts from the closed-form fields `kind`, B0 of
-    spin a = cfg.a (grid, dt and i_horizon held at cfg's): the adjoint's
-    part at fixed step-0 state plus grad_F0 . dF0/da, the initial fields'
-    a-derivative taken by a central difference (h) of their closed forms.
-    Returns (L, dL/da)."""
-    import dataclasses
-    ctx = Context(cfg)
-    F = Fields(cfg)
-    ctx.init_fields(F, kind, B0)
-    L, _, gf, La = adjoint_grad(ctx, x, tag, F.D, F.B, nsteps, i_horizon, checkpoint_every, want_spin=True)
-    dF = []
-    for da in (h, -h):
-        c = dataclasses.replace(cfg, a=cfg.a + da)
-        cx = Context(c)
-        Fa = Fields(c)
-        cx.init_fields(Fa, kind, B0)
-        dF.append([t.clone() for t in Fa.D + Fa.B])
-        del cx
-    return L, La + sum(float((g * (p - m)).sum()) for g, p, m in zip(gf, dF[0], dF[1])) / (2.0 * h)
+    the context's spin (grid, dt and i_horizon held fixed): the library's
+    grpic_adjoint_spin, the adjoint's part at fixed step-0 state plus the
+    step-0 fields' own a-dependence.  Returns (L, dL/da, grad_p, grad_f)."""
+    import torch
+    _load_adj(gctx.lib)
+    n = int(x[0].numel())
+    xs = [t.contiguous() for t in x]
+    pc = ParticlesC()
+    pc.n, pc.capacity, pc.d_count = n, max(n, 1), 0
+    pc.x1, pc.x2, pc.u1, pc.u2, pc.u3 = (t.data_ptr() for t in xs)
+    pc.tag = tag.data_ptr()
+    pc.cell = 0
+    cfg = gctx.cfg
+    gp = [torch.empty_like(t) for t in xs]
+    gf = [torch.empty((cfg.n_theta + 1, cfg.ld), dtype=torch.float64, device=xs[0].device) for _ in range(6)]
+    arr_p = (C.c_void_p * 5)(*[t.data_ptr() for t in gp])
+    arr_f = (C.c_void_p * 6)(*[t.data_ptr() for t in gf])
+    L, La = C.c_double(), C.c_double()
+    st = gctx.lib.grpic_adjoint_spin(gctx.h, C.byref(pc), int(kind), float(B0), int(nsteps), int(checkpoint_every),
+                                     int(i_horizon), 1 if ift else 0, C.byref(L), arr_p, arr_f, C.byref(La),
+                                     _stream(stream))
+    gctx._check(st, "grpic_adjoint_spin")
+    return L.value, La.value, gp, gf
 
 
 def _autograd_fn():
@@ -799,10 +812,3 @@ def horizon_flux_objective(gctx: Context, x, tag, D, B, nsteps: int, i_horizon: 
     if _HFN is None:
         _HFN = _autograd_fn()
     return _HFN.apply(gctx, tag, int(nsteps), int(i_horizon), int(checkpoint_every), bool(ift), *x, *D, *B)
-
-
-def spin_gradient_fd(make, h: float = 1e-6) -> float:
-    """dL/da by a central difference: make(a_offset) must build the context
-    and the inputs at spin a + a_offset on the grid of the nominal spin and
-    return L (the check of spin_gradient)."""
-    return (make(h) - make(-h)) / (2.0 * h)
