@@ -503,6 +503,76 @@ void grpic_batch1d_destroy(grpic_batch1d_ctx *ctx);
 grpic_status grpic_sort_noalloc(const grpic_grid *grid, int32_t precision, grpic_particles *p,
                                 grpic_particles *scratch, void *stream);
 
+/* ------------------------------------------------------------------------ */
+/* theta-slab domain decomposition (the paper's multi-GPU design, Sec. 1:  */
+/* the domain split among GPUs with MPI exchanges of the boundary data).    */
+/* Each rank keeps field arrays of the whole grid (global row indices) but  */
+/* updates only rows [j0 - G, j1 + G) around its own rows [j0, j1), and     */
+/* pushes only the particles of its rows.  One step (the host driver moves  */
+/* the buffers between ranks):                                              */
+/*   grpic_push (own particles, J zeroed and deposited);                    */
+/*   J halo reduction: the rows outside [j0, j1) that the deposit reached  */
+/*   go to their owners (grpic_halo_pack / grpic_halo_unpack with add);     */
+/*   then the owners' complete rows fill the G ghost rows on each side      */
+/*   (pack, unpack with copy);                                              */
+/*   grpic_field_update_rows on [j0 - G, j1 + G): a stage's D rows read   */
+/*   the B rows at and below them and its B rows the D rows at and above    */
+/*   them, so a wrong row outside the range moves half a row inwards per    */
+/*   stage; with G = ceil((N + 1) / 2) for the 1 + N stages the own rows    */
+/*   come out as in the undivided grid; the ghost rows of D, B are then     */
+/*   refilled from their owners;                                            */
+/*   migration: grpic_sort_split sorts the particles by cell and returns   */
+/*   how many left below j0 and above j1 (at most one row in a step), the   */
+/*   leavers are packed (grpic_particles_pack) and sent, and               */
+/*   grpic_slab_assemble places [arrivals from below | own | arrivals from  */
+/*   above] before a last grpic_sort; since each neighbour's order is the   */
+/*   undivided run's order of its particles and a stable sort keeps the     */
+/*   order of equal keys, the result is the undivided run's order of this   */
+/*   slab's particles.                                                      */
+/* Field sets: 0 = D^r, D^theta, D^phi, B^r, B^theta, B^phi; 1 = the three  */
+/* J arrays.  A packed halo holds the components one after the other, each  */
+/* as its rows [row0, row0 + nrows) exactly as in the field arrays          */
+/* (nrows * ld elements of the field precision per component).  A packed    */
+/* particle message of n particles holds the arrays x1, x2, u1, u2, u3 (8   */
+/* or 4 bytes each), tag (4 bytes) and, in the FP32 form, cell (4 bytes),   */
+/* n entries each, back to back.  Device buffers, caller-owned.             */
+/* ------------------------------------------------------------------------ */
+
+/* The field update of grpic_field_update restricted to rows [j_lo, j_hi) of
+ * every component (0 <= j_lo < j_hi <= n_theta + 1); rows outside are left
+ * unchanged and are read by the range's edge rows.  The axis conditions
+ * apply to rows 0 and n_theta when they lie in the range. */
+grpic_status grpic_field_update_rows(grpic_ctx *ctx, grpic_fields *f, int32_t j_lo, int32_t j_hi, void *stream);
+
+/* Copy rows [row0, row0 + nrows) of field set `set` into buf (device,
+ * ncomp * nrows * ld elements), or back: unpack with add = 0 copies, with
+ * add != 0 adds buf to the rows (the current halo reduction). */
+grpic_status grpic_halo_pack(grpic_ctx *ctx, const grpic_fields *f, int32_t set, int32_t row0, int32_t nrows,
+                             void *buf, void *stream);
+grpic_status grpic_halo_unpack(grpic_ctx *ctx, grpic_fields *f, int32_t set, int32_t row0, int32_t nrows,
+                               const void *buf, int32_t add, void *stream);
+
+/* grpic_sort (always the general counting sort, keys recomputed from the
+ * positions) followed by the segment counts of the sorted live particles:
+ * counts[0] in rows below j_lo, counts[1] in rows [j_lo, j_hi), counts[2]
+ * in rows j_hi and above (0 <= j_lo <= j_hi <= n_theta), as host int64.
+ * Synchronizes `stream`. */
+grpic_status grpic_sort_split(grpic_ctx *ctx, grpic_particles *p, grpic_particles *scratch, int32_t j_lo,
+                              int32_t j_hi, int64_t counts[3], void *stream);
+
+/* Pack slots [first, first + n) of p into buf (the message layout above). */
+grpic_status grpic_particles_pack(grpic_ctx *ctx, const grpic_particles *p, int64_t first, int64_t n, void *buf,
+                                  void *stream);
+
+/* dst slots [0, n_lower) <- the packed message `lower`, then slots
+ * [own_first, own_first + own_n) of src, then the packed message `upper`;
+ * dst->n is set to the total and written to dst->d_count when given (that
+ * copy synchronizes `stream`).  The sort's cached keys are dropped, so the
+ * next sort recomputes them. */
+grpic_status grpic_slab_assemble(grpic_ctx *ctx, grpic_particles *dst, const grpic_particles *src, int64_t own_first,
+                                 int64_t own_n, const void *lower, int64_t n_lower, const void *upper,
+                                 int64_t n_upper, void *stream);
+
 /* Measured arithmetic ceiling of the current device (measurement support for
  * the ALU rooflines; the paper has no counterpart).  kind 0: FP32 fused
  * multiply-add, 1: FP64 fused multiply-add, 2: packed FP32 fused multiply-add

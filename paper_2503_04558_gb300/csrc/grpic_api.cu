@@ -4,6 +4,7 @@
 // field update, then the sort by cell).
 #include "grpic_internal.cuh"
 
+#include <algorithm>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -233,11 +234,57 @@ grpic_status field_impl(grpic_ctx *ctx, grpic_fields *f, cudaStream_t s)
     return GRPIC_OK;
 }
 
+// scratch for the adjoint translation unit (same buffers as the step's)
 }  // namespace
 
-// scratch for the adjoint translation unit (same buffers as the step's)
 grpic_status grpic::ensure_field_scratch_ext(grpic_ctx *ctx, int64_t ld) { return ensure_field_scratch(ctx, ld); }
 grpic_status grpic::ensure_particle_scratch_ext(grpic_ctx *ctx, int64_t n) { return ensure_particle_scratch(ctx, n); }
+
+namespace {
+
+// halo add: f[k] rows [row0, row0 + nrows) += buf (component-major, rows
+// contiguous as in the field arrays); the component pointers by value
+template <typename T>
+struct HaloComps {
+    T *p[6];
+};
+
+template <typename T>
+__global__ void halo_add_kernel(HaloComps<T> comp, int ncomp, size_t off, size_t n, const T *buf)
+{
+    size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const size_t total = (size_t)ncomp * n;
+    for (; q < total; q += (size_t)gridDim.x * blockDim.x) {
+        const size_t k = q / n, e = q - k * n;
+        comp.p[k][off + e] += buf[q];
+    }
+}
+
+// the arrays of one particle buffer, with element sizes
+int particle_arrays(const grpic_ctx *ctx, const grpic_particles *p, void *arr[7], size_t esz[7])
+{
+    size_t fs = fsize(ctx);
+    void *a[7] = {p->x1, p->x2, p->u1, p->u2, p->u3, (void *)p->tag, (void *)p->cell};
+    size_t e[7] = {fs, fs, fs, fs, fs, 4, 4};
+    int na = ctx->prm.precision == 32 ? 7 : 6;
+    for (int k = 0; k < na; ++k) {
+        arr[k] = a[k];
+        esz[k] = e[k];
+    }
+    return na;
+}
+
+// the sort's caches no longer describe a buffer that was written from outside
+void drop_sort_state(grpic_ctx *ctx)
+{
+    ctx->keys_valid = 0;
+    ctx->hist_valid = 0;
+    ctx->sorted_tag = nullptr;
+    ctx->keys_tag = nullptr;
+    ctx->counts_ready = 0;
+}
+
+}  // namespace
 
 extern "C" {
 
@@ -691,6 +738,165 @@ grpic_status grpic_get_timing(grpic_ctx *ctx, double out[3], int64_t *nsteps)
         }
     }
     ctx->tsteps = 0;
+    return GRPIC_OK;
+}
+
+// ---------------------------------------------------------------------------
+// theta-slab decomposition: row-restricted field update, halos, migration
+// ---------------------------------------------------------------------------
+grpic_status grpic_field_update_rows(grpic_ctx *ctx, grpic_fields *f, int32_t j_lo, int32_t j_hi, void *stream)
+{
+    if (!ctx) return GRPIC_EINVAL;
+    if (!fields_ok(ctx, f) || j_lo < 0 || j_hi > ctx->g.nth + 1 || j_lo >= j_hi)
+        return fail(ctx, GRPIC_EINVAL, "grpic_field_update_rows: bad arguments");
+    grpic_status st = ensure_field_scratch(ctx, f->ld);
+    if (st) return st;
+    cudaError_t e = (ctx->prm.precision == 64) ? launch_field64(ctx, f, S(stream), j_lo, j_hi)
+                                                : launch_field32(ctx, f, S(stream), j_lo, j_hi);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "field update (rows)");
+    return GRPIC_OK;
+}
+
+grpic_status grpic_halo_pack(grpic_ctx *ctx, const grpic_fields *f, int32_t set, int32_t row0, int32_t nrows, void *buf,
+                             void *stream)
+{
+    if (!ctx) return GRPIC_EINVAL;
+    if (!fields_ok(ctx, f) || (set != 0 && set != 1) || row0 < 0 || nrows < 0 || row0 + nrows > ctx->g.nth + 1 ||
+        (nrows > 0 && !buf))
+        return fail(ctx, GRPIC_EINVAL, "grpic_halo_pack: bad arguments");
+    const size_t n = (size_t)nrows * f->ld, off = (size_t)row0 * f->ld, es = fsize(ctx);
+    void *comp[6] = {f->D[0], f->D[1], f->D[2], f->B[0], f->B[1], f->B[2]};
+    void *jc[3] = {f->J[0], f->J[1], f->J[2]};
+    const int nc = set == 0 ? 6 : 3;
+    for (int k = 0; k < nc && n > 0; ++k) {
+        const char *src = (const char *)(set == 0 ? comp[k] : jc[k]) + off * es;
+        cudaError_t e = cudaMemcpyAsync((char *)buf + k * n * es, src, n * es, cudaMemcpyDeviceToDevice, S(stream));
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "halo pack");
+    }
+    return GRPIC_OK;
+}
+
+grpic_status grpic_halo_unpack(grpic_ctx *ctx, grpic_fields *f, int32_t set, int32_t row0, int32_t nrows,
+                               const void *buf, int32_t add, void *stream)
+{
+    if (!ctx) return GRPIC_EINVAL;
+    if (!fields_ok(ctx, f) || (set != 0 && set != 1) || row0 < 0 || nrows < 0 || row0 + nrows > ctx->g.nth + 1 ||
+        (nrows > 0 && !buf))
+        return fail(ctx, GRPIC_EINVAL, "grpic_halo_unpack: bad arguments");
+    const size_t n = (size_t)nrows * f->ld, off = (size_t)row0 * f->ld, es = fsize(ctx);
+    void *comp[6] = {f->D[0], f->D[1], f->D[2], f->B[0], f->B[1], f->B[2]};
+    void *jc[3] = {f->J[0], f->J[1], f->J[2]};
+    const int nc = set == 0 ? 6 : 3;
+    if (n == 0) return GRPIC_OK;
+    if (!add) {
+        for (int k = 0; k < nc; ++k) {
+            char *dst = (char *)(set == 0 ? comp[k] : jc[k]) + off * es;
+            cudaError_t e =
+                cudaMemcpyAsync(dst, (const char *)buf + k * n * es, n * es, cudaMemcpyDeviceToDevice, S(stream));
+            if (e != cudaSuccess) return cuda_fail(ctx, e, "halo unpack");
+        }
+        return GRPIC_OK;
+    }
+    const size_t total = (size_t)nc * n;
+    const unsigned blocks = (unsigned)std::min<size_t>((total + 255) / 256, 4096);
+    if (ctx->prm.precision == 64) {
+        HaloComps<double> P;
+        for (int k = 0; k < 6; ++k) P.p[k] = k < nc ? (double *)(set == 0 ? comp[k] : jc[k]) : nullptr;
+        halo_add_kernel<double><<<blocks, 256, 0, S(stream)>>>(P, nc, off, n, (const double *)buf);
+    } else {
+        HaloComps<float> P;
+        for (int k = 0; k < 6; ++k) P.p[k] = k < nc ? (float *)(set == 0 ? comp[k] : jc[k]) : nullptr;
+        halo_add_kernel<float><<<blocks, 256, 0, S(stream)>>>(P, nc, off, n, (const float *)buf);
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "halo add");
+    return GRPIC_OK;
+}
+
+grpic_status grpic_sort_split(grpic_ctx *ctx, grpic_particles *p, grpic_particles *scratch, int32_t j_lo,
+                              int32_t j_hi, int64_t counts[3], void *stream)
+{
+    if (!ctx) return GRPIC_EINVAL;
+    if (!particles_ok(ctx, p) || !particles_ok(ctx, scratch) || scratch->capacity < p->n || !counts || j_lo < 0 ||
+        j_hi > ctx->g.nth || j_lo > j_hi || ctx->pending_perm)
+        return fail(ctx, GRPIC_EINVAL, "grpic_sort_split: bad arguments");
+    drop_sort_state(ctx);  // keys recomputed from the positions, general counting sort
+    grpic_status st = sort_impl(ctx, p, scratch, S(stream));
+    if (st) return st;
+    // segment starts of the new order: rows below j_lo, rows [j_lo, j_hi), the rest live
+    const int64_t nr = ctx->g.nr, ncell = nr * ctx->g.nth;
+    int32_t o[3] = {0, 0, 0};
+    cudaStream_t s = S(stream);
+    cudaError_t e = cudaMemcpyAsync(&o[0], ctx->d_offset_prev + (int64_t)j_lo * nr, 4, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(&o[1], ctx->d_offset_prev + (int64_t)j_hi * nr, 4, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&o[2], ctx->d_offset_prev + ncell, 4, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "sort split");
+    counts[0] = o[0];
+    counts[1] = o[1] - o[0];
+    counts[2] = o[2] - o[1];
+    return GRPIC_OK;
+}
+
+grpic_status grpic_particles_pack(grpic_ctx *ctx, const grpic_particles *p, int64_t first, int64_t n, void *buf,
+                                  void *stream)
+{
+    if (!ctx) return GRPIC_EINVAL;
+    if (!p || first < 0 || n < 0 || first + n > p->capacity || (n > 0 && !buf) ||
+        (n > 0 && !particles_ok(ctx, p)))
+        return fail(ctx, GRPIC_EINVAL, "grpic_particles_pack: bad arguments");
+    void *arr[7];
+    size_t esz[7];
+    const int na = particle_arrays(ctx, p, arr, esz);
+    size_t off = 0;
+    for (int k = 0; k < na && n > 0; ++k) {
+        cudaError_t e = cudaMemcpyAsync((char *)buf + off, (const char *)arr[k] + first * esz[k], n * esz[k],
+                                        cudaMemcpyDeviceToDevice, S(stream));
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "particles pack");
+        off += n * esz[k];
+    }
+    return GRPIC_OK;
+}
+
+grpic_status grpic_slab_assemble(grpic_ctx *ctx, grpic_particles *dst, const grpic_particles *src, int64_t own_first,
+                                 int64_t own_n, const void *lower, int64_t n_lower, const void *upper,
+                                 int64_t n_upper, void *stream)
+{
+    if (!ctx) return GRPIC_EINVAL;
+    const int64_t total = n_lower + own_n + n_upper;
+    if (!dst || !src || own_first < 0 || own_n < 0 || n_lower < 0 || n_upper < 0 || own_first + own_n > src->capacity ||
+        total > dst->capacity || total > INT32_MAX || (n_lower > 0 && !lower) || (n_upper > 0 && !upper) ||
+        !dst->x1 || !dst->x2 || !dst->u1 || !dst->u2 || !dst->u3 || !dst->tag ||
+        (ctx->prm.precision == 32 && !dst->cell) || (own_n > 0 && !particles_ok(ctx, src)))
+        return fail(ctx, GRPIC_EINVAL, "grpic_slab_assemble: bad arguments");
+    cudaStream_t s = S(stream);
+    void *da[7], *sa[7];
+    size_t esz[7];
+    const int na = particle_arrays(ctx, dst, da, esz);
+    particle_arrays(ctx, src, sa, esz);
+    size_t ol = 0, ou = 0;
+    for (int k = 0; k < na; ++k) {
+        char *d = (char *)da[k];
+        cudaError_t e = cudaSuccess;
+        if (n_lower > 0) e = cudaMemcpyAsync(d, (const char *)lower + ol, n_lower * esz[k], cudaMemcpyDeviceToDevice, s);
+        if (e == cudaSuccess && own_n > 0)
+            e = cudaMemcpyAsync(d + n_lower * esz[k], (const char *)sa[k] + own_first * esz[k], own_n * esz[k],
+                                cudaMemcpyDeviceToDevice, s);
+        if (e == cudaSuccess && n_upper > 0)
+            e = cudaMemcpyAsync(d + (n_lower + own_n) * esz[k], (const char *)upper + ou, n_upper * esz[k],
+                                cudaMemcpyDeviceToDevice, s);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "slab assemble");
+        ol += n_lower * esz[k];
+        ou += n_upper * esz[k];
+    }
+    dst->n = total;
+    if (dst->d_count) {
+        cudaError_t e = cudaMemcpyAsync(dst->d_count, &dst->n, sizeof(int64_t), cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // the host source lives in the caller's struct
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "slab assemble count");
+    }
+    drop_sort_state(ctx);
     return GRPIC_OK;
 }
 

@@ -36,6 +36,7 @@ struct FieldArgs {
     T *Xo[6];        // output iterate
     const T *J[3];
     int mode;        // 0 predictor, 1 corrector, 2 last corrector (damping)
+    int j_lo, j_hi;  // the rows [j_lo, j_hi) the stage updates
 };
 
 template <typename T>
@@ -132,8 +133,8 @@ template <typename T>
 __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 8 : 1) field_stage_kernel(FieldArgs<T> A)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
-    int j = blockIdx.y * blockDim.y + threadIdx.y;
-    if (i > A.nr || j > A.nth) return;
+    int j = A.j_lo + (int)(blockIdx.y * blockDim.y + threadIdx.y);
+    if (i > A.nr || j >= A.j_hi) return;
     Ctx<T> X(A);
     const int nr = A.nr, nth = A.nth;
     size_t qt = (size_t)j * A.ldt + (i + NG);
@@ -187,8 +188,11 @@ T *fslot(grpic_ctx *ctx, int k, int64_t ld)
     return (T *)ctx->fscratch + (size_t)k * n;
 }
 
+// rows [j_lo, j_hi) of every component are updated (all rows: 0, nth + 1);
+// the rows outside are left as they are and feed the range's edge rows
 template <typename T>
-cudaError_t run_field(grpic_ctx *ctx, grpic_fields *f, const T *tab, const T *col1d, cudaStream_t s)
+cudaError_t run_field(grpic_ctx *ctx, grpic_fields *f, const T *tab, const T *col1d, cudaStream_t s, int j_lo,
+                      int j_hi)
 {
     FieldArgs<T> A;
     A.nr = ctx->g.nr;
@@ -216,7 +220,9 @@ cudaError_t run_field(grpic_ctx *ctx, grpic_fields *f, const T *tab, const T *co
         A.Xn[k] = user[k];
         A.Cn[k] = Cn[k];
     }
-    dim3 blk(64, 4), grd((A.nr + 1 + 63) / 64, (A.nth + 1 + 3) / 4);
+    A.j_lo = j_lo;
+    A.j_hi = j_hi;
+    dim3 blk(64, 4), grd((A.nr + 1 + 63) / 64, (j_hi - j_lo + 3) / 4);
     int N = ctx->prm.n_field_iter;
     // predictor
     for (int k = 0; k < 6; ++k) {
@@ -239,8 +245,9 @@ cudaError_t run_field(grpic_ctx *ctx, grpic_fields *f, const T *tab, const T *co
     if (N == 0) {
         // no corrector: damp and copy the predictor result back (a corrector-free
         // step is the forward-Euler predictor alone)
-        size_t bytes = (size_t)(ctx->g.nth + 1) * f->ld * sizeof(T);
-        for (int k = 0; k < 6; ++k) cudaMemcpyAsync(user[k], buf[0][k], bytes, cudaMemcpyDeviceToDevice, s);
+        size_t off = (size_t)j_lo * f->ld, bytes = (size_t)(j_hi - j_lo) * f->ld * sizeof(T);
+        for (int k = 0; k < 6; ++k)
+            cudaMemcpyAsync(user[k] + off, buf[0][k] + off, bytes, cudaMemcpyDeviceToDevice, s);
     }
     return cudaGetLastError();
 }
@@ -271,6 +278,8 @@ cudaError_t launch_field64_stages(grpic_ctx *ctx, double *const Xn[6], double *c
         A.Xn[k] = Xn[k];
         A.Cn[k] = fslot<double>(ctx, k, ld);
     }
+    A.j_lo = 0;
+    A.j_hi = A.nth + 1;
     dim3 blk(64, 4), grd((A.nr + 1 + 63) / 64, (A.nth + 1 + 3) / 4);
     const int N = ctx->prm.n_field_iter;
     for (int st = 0; st <= N; ++st) {
@@ -284,14 +293,16 @@ cudaError_t launch_field64_stages(grpic_ctx *ctx, double *const Xn[6], double *c
     return cudaGetLastError();
 }
 
-cudaError_t launch_field64(grpic_ctx *ctx, grpic_fields *f, cudaStream_t s)
+cudaError_t launch_field64(grpic_ctx *ctx, grpic_fields *f, cudaStream_t s, int j_lo, int j_hi)
 {
-    return run_field<double>(ctx, f, ctx->tab, ctx->col1d, s);
+    if (j_hi < 0) j_hi = ctx->g.nth + 1;
+    return run_field<double>(ctx, f, ctx->tab, ctx->col1d, s, j_lo, j_hi);
 }
 
-cudaError_t launch_field32(grpic_ctx *ctx, grpic_fields *f, cudaStream_t s)
+cudaError_t launch_field32(grpic_ctx *ctx, grpic_fields *f, cudaStream_t s, int j_lo, int j_hi)
 {
-    return run_field<float>(ctx, f, ctx->tab32, ctx->col1d32, s);
+    if (j_hi < 0) j_hi = ctx->g.nth + 1;
+    return run_field<float>(ctx, f, ctx->tab32, ctx->col1d32, s, j_lo, j_hi);
 }
 
 }  // namespace grpic

@@ -198,10 +198,11 @@ cudaError_t launch_push32(grpic_ctx *ctx, const grpic_particles *in, grpic_parti
                           const int32_t *live, int32_t *cnt9, grpic_fields *f, bool histogram, cudaStream_t s);
 cudaError_t launch_deposit(grpic_ctx *ctx, const grpic_particles *b, const grpic_particles *a, const void *dphi,
                            grpic_fields *f, cudaStream_t s);
-cudaError_t launch_field64(grpic_ctx *ctx, grpic_fields *f, cudaStream_t s);
+// the field update of rows [j_lo, j_hi) (j_hi < 0: every row)
+cudaError_t launch_field64(grpic_ctx *ctx, grpic_fields *f, cudaStream_t s, int j_lo = 0, int j_hi = -1);
 cudaError_t launch_field64_stages(grpic_ctx *ctx, double *const Xn[6], double *const J[3], double *const *Y, int64_t ld,
                                   cudaStream_t s);
-cudaError_t launch_field32(grpic_ctx *ctx, grpic_fields *f, cudaStream_t s);
+cudaError_t launch_field32(grpic_ctx *ctx, grpic_fields *f, cudaStream_t s, int j_lo = 0, int j_hi = -1);
 cudaError_t launch_tables_at(grpic_ctx *ctx, double a, double *tab, double *col1d, cudaStream_t s);
 // the analytic initial fields (FP64) of spin a with the tables `tab` of that spin
 cudaError_t launch_init_fields_at(grpic_ctx *ctx, double a, const double *tab, int kind, double B0,

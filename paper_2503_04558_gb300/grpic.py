@@ -24,7 +24,9 @@ NG = 2
 # names the header declares (checked by the CPU test of the boundary)
 EXPORTS = ["grpic_init", "grpic_init_fields", "grpic_push", "grpic_deposit", "grpic_field_update", "grpic_sort",
            "grpic_step", "grpic_step_graph", "grpic_diagnostics", "grpic_charge_check", "grpic_get_areas", "grpic_sync", "grpic_last_error", "grpic_destroy",
-           "grpic_sort_noalloc", "grpic_set_timing", "grpic_get_timing", "grpic_alu_peak"]
+           "grpic_sort_noalloc", "grpic_set_timing", "grpic_get_timing", "grpic_alu_peak",
+           "grpic_field_update_rows", "grpic_halo_pack", "grpic_halo_unpack", "grpic_sort_split",
+           "grpic_particles_pack", "grpic_slab_assemble"]
 NOALLOC_MAX_PARTICLES = 2097152
 NOALLOC_MAX_CELLS = 262144
 
@@ -83,6 +85,12 @@ def load(path: str = LIB_PATH):
         "grpic_set_timing": [v, i],
         "grpic_get_timing": [v, p(d), p(i64)],
         "grpic_alu_peak": [C.c_int32, p(d), v],
+        "grpic_field_update_rows": [v, p(FieldsC), C.c_int32, C.c_int32, v],
+        "grpic_halo_pack": [v, p(FieldsC), C.c_int32, C.c_int32, C.c_int32, v, v],
+        "grpic_halo_unpack": [v, p(FieldsC), C.c_int32, C.c_int32, C.c_int32, v, C.c_int32, v],
+        "grpic_sort_split": [v, p(ParticlesC), p(ParticlesC), C.c_int32, C.c_int32, p(i64), v],
+        "grpic_particles_pack": [v, p(ParticlesC), i64, i64, v, v],
+        "grpic_slab_assemble": [v, p(ParticlesC), p(ParticlesC), i64, i64, v, i64, v, i64, v],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
