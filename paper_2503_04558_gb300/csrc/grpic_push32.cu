@@ -10,10 +10,12 @@
 //     in the paper while the position keeps FP32 precision relative to its
 //     cell whatever the grid size;
 //   * fields, tables and deposited currents are FP32;
-//   * extended precision is kept for (i) the metric (alpha, beta, gamma^ij and
-//     derivatives) of particles in cells whose inner edge lies below
-//     fp64_radius (the island near the horizon): double-FP32 pairs by
-//     default, native FP64 on request (island_arith), (ii) the corrector's
+//   * extended precision is kept for (i) the metric of particles in cells
+//     whose inner edge lies below fp64_radius (the island near the horizon):
+//     by default alpha, beta, gamma^ij and the lower metric in double-FP32
+//     pairs, rounded to FP32 for the right-hand sides, with the metric's r and
+//     theta derivatives (force terms only) in FP32; on request (island_arith)
+//     the whole metric with its derivatives in native FP64; (ii) the corrector's
 //     convergence test: after each corrector the change of the iterate is
 //     measured (exactly, see below) and the iteration stops once it is below
 //     the tolerance (at most n_push_iter correctors).
@@ -30,6 +32,7 @@ namespace {
 struct Push32Args {
     GridDev g;
     float dt;
+    float idt, m_i2dt;  // 1 / dt, -1 / (2 dt)
     int n_iter;
     float tolf;
     float qm[4], qw[4];
@@ -38,8 +41,8 @@ struct Push32Args {
     int i64;  // first column whose inner edge is at or beyond fp64_radius
     int island_fp64;   // 1: native FP64 island, 0: double-FP32 pairs
     int use_tol;       // convergence test of the correctors
-    float af, dthf, idthf, dx1f, idx1f;  // a, dtheta, 1/dtheta, dx1, 1/dx1 in FP32
-    df a_df, dth_df;              // a, dtheta as float pairs
+    float af, a2f, dthf, idthf, dx1f, idx1f;  // a, a^2, dtheta, 1/dtheta, dx1, 1/dx1 in FP32
+    df a_df, a2_df, dth_df;       // a, a^2, dtheta as float pairs
     const float *rcol2;  // r_i as (hi, lo) float pairs, index i + NG
     const float *rowsc;  // sin, cos theta_j as float pairs, index j
     int64_t n;
@@ -69,6 +72,7 @@ struct Push32Args {
     int histogram;
     int pusher;  // 0 generalized Boris, 1 Vay in the FIDO frame
     int *status;
+    unsigned long long nr_recip;  // floor(2^64 / n_r) + 1
 };
 
 template <typename T>
@@ -110,12 +114,12 @@ __device__ __forceinline__ void boris32(const KSPoint<M> &mm, float qm, float dt
     float irr = (float)mm.gi_rr, irp = (float)mm.gi_rp, itt = (float)mm.gi_tt, ipp = (float)mm.gi_pp;
     float sg = (float)mm.sqrtg;
     float Dl0 = grr * D[0] + grp * D[2], Dl1 = gtt * D[1], Dl2 = grp * D[0] + gpp * D[2];
-    float h = 0.5f * qm * alpha * dt;
+    float h = (0.5f * qm * dt) * alpha;
     float um0 = u[0] + h * Dl0, um1 = u[1] + h * Dl1, um2 = u[2] + h * Dl2;
     float v0 = irr * um0 + irp * um2, v1 = itt * um1, v2 = irp * um0 + ipp * um2;
     // 1 / u0bar = alpha / sqrt(1 + u^- . v) (hardware reciprocal square root and
     // reciprocal: a few ulp, within the FP32 form's budget)
-    float kt = 0.5f * qm * dt * alpha * rsqrtf(1.0f + um0 * v0 + um1 * v1 + um2 * v2);
+    float kt = h * rsqrtf(fmaf(um0, v0, fmaf(um1, v1, fmaf(um2, v2, 1.0f))));
     float t0 = kt * B[0], t1 = kt * B[1], t2 = kt * B[2];
     float tt = t0 * (grr * t0 + grp * t2) + t1 * (gtt * t1) + t2 * (grp * t0 + gpp * t2);
     float ks = __fdividef(2.0f, 1.0f + tt);
@@ -183,11 +187,23 @@ __device__ __forceinline__ void stencil32(const GridDev &g, int i, int j, float 
     S.w11 = f * gg;
 }
 
+// the bilinear sum of one component; a reflected row's parity is folded into
+// the weights by the caller (flip_rows)
 __device__ __forceinline__ float gather32(const float *__restrict__ F, int64_t ld, const St32 &S)
 {
     const float *a = F + (size_t)S.r0 * ld + S.c0;
     const float *b = F + (size_t)S.r1 * ld + S.c0;
-    return S.p0 * (S.w00 * __ldg(a) + S.w10 * __ldg(a + 1)) + S.p1 * (S.w01 * __ldg(b) + S.w11 * __ldg(b + 1));
+    return fmaf(S.w00, __ldg(a), fmaf(S.w10, __ldg(a + 1), fmaf(S.w01, __ldg(b), S.w11 * __ldg(b + 1))));
+}
+
+// the weights of a stencil whose rows carry the parities p0, p1
+__device__ __forceinline__ St32 flip_rows(St32 S)
+{
+    S.w00 *= S.p0;
+    S.w10 *= S.p0;
+    S.w01 *= S.p1;
+    S.w11 *= S.p1;
+    return S;
 }
 
 // generalized Boris step in FP32 with the metric of type M at x^n (the lower
@@ -213,6 +229,120 @@ __device__ __forceinline__ void boris_geo(const KSGeo<M> &m, M a, M r, M s, floa
     mm.gi_tt = (float)m.gtt;
     mm.gi_pp = (float)m.gpp;
     mm.sqrtg = (float)(m.rho2 * s * m.opz * m.alpha);  // rho^2 sin sqrt(1+z), sqrt(1+z) = (1+z) alpha
+    if (pusher) {
+        const VayMetric<float> vm{mm.alpha, mm.g_rr, mm.g_rp, mm.g_tt, mm.g_pp, mm.gi_rr, mm.gi_rp, mm.gi_tt,
+                                  mm.gi_pp, mm.sqrtg};
+        vay_step<float>(vm, qm, dt, D, B, u);
+    } else {
+        boris32<float>(mm, qm, dt, D, B, u);
+    }
+}
+
+// the metric values of the Boris step in FP32 at (r, sin, cos): alpha,
+// gamma_ij, gamma^ij and sqrt(gamma) (App. A), without the derivatives (the
+// right-hand side at x^n takes geo_rhs_direct like the correctors)
+__device__ __forceinline__ void ks_point_boris32(float a, float a2, float r, float s, float c, KSPoint<float> &m)
+{
+    const float r2 = r * r, s2 = s * s;
+    const float rho2 = fmaf(a2 * c, c, r2);
+    const float ir = __fdividef(1.0f, rho2);
+    const float z = (r + r) * ir;
+    const float opz = 1.0f + z;
+    const float iopz = __fdividef(1.0f, opz);
+    const float ra = r2 + a2;
+    const float Dl = ra - (r + r);
+    const float Sg = fmaf(ra, ra, -a2 * Dl * s2);
+    m.alpha = iopz * rsqrtf(iopz);  // iopz in (0, 1]
+    m.g_rr = opz;
+    m.g_tt = rho2;
+    m.g_pp = Sg * s2 * ir;
+    m.g_rp = -a * s2 * opz;
+    m.gi_rr = fmaf(ra, ir, -z * iopz);
+    m.gi_rp = a * ir;
+    m.gi_tt = ir;
+    m.gi_pp = __fdividef(ir, s2);
+    m.sqrtg = rho2 * s * opz * m.alpha;  // rho^2 sin sqrt(1+z), sqrt(1+z) = (1+z) alpha
+}
+
+// The metric of the near-horizon island in double-FP32 pairs: alpha, beta,
+// gamma^{ij}, rho^2, 1/rho^2, 1 + z formed in pair arithmetic and rounded to
+// FP32 for the right-hand sides; their r and theta derivatives, which enter
+// only the force terms U_i, in FP32 from the rounded values (as the FP32
+// form's own metric).  `keep` receives the pairs the Boris step's lower
+// metric reuses.
+struct IslandKeep {
+    df alpha, ir, opz, rho2;
+};
+
+__device__ __forceinline__ void ks_geo_island(const df &a, const df &a2, const df &r, const df &s, const df &c,
+                                              KSGeo<float> &m, IslandKeep *keep)
+{
+    const df r2 = r * r;
+    const df rho2 = r2 + a2 * (c * c);
+    const df ir = rcp_t(rho2);
+    const df z = mul(r, 2.0f) * ir;
+    const df opz = df(1.0f) + z;
+    const df iopz = rcp_t(opz);
+    const df alpha = sqrt_t(iopz);
+    const df beta = z * iopz;
+    const df is2 = rcp_t(s * s);
+    if (keep) {
+        keep->alpha = alpha;
+        keep->ir = ir;
+        keep->opz = opz;
+        keep->rho2 = rho2;
+    }
+    m.rho2 = (float)rho2;
+    m.ir = (float)ir;
+    m.opz = (float)opz;
+    m.alpha = (float)alpha;
+    m.beta = (float)beta;
+    m.grr = (float)((a2 + r2) * ir - beta);
+    m.grp = (float)(a * ir);
+    m.gtt = m.ir;
+    m.gpp = (float)(ir * is2);
+    // derivatives (App. A) in FP32
+    const float af = a.hi, a2f = a2.hi, rf = (float)r, sf = (float)s, cf = (float)c, irf = m.ir;
+    const float iopzf = (float)iopz, is2f = (float)is2, r2f = rf * rf;
+    const float ir2 = irf * irf;
+    const float drho_t = -2.0f * a2f * cf * sf;
+    const float dz_r = 2.0f * irf * (1.0f - 2.0f * r2f * irf);
+    const float dz_t = -2.0f * rf * drho_t * ir2;
+    const float ka = -0.5f * m.alpha * iopzf, kb = iopzf * iopzf;
+    m.da_r = ka * dz_r;
+    m.da_t = ka * dz_t;
+    m.db_r = kb * dz_r;
+    m.db_t = kb * dz_t;
+    m.dgrr_r = 2.0f * rf * irf - (a2f + r2f) * 2.0f * rf * ir2 - m.db_r;
+    m.dgrr_t = -(a2f + r2f) * drho_t * ir2 - m.db_t;
+    m.dgrp_r = -af * 2.0f * rf * ir2;
+    m.dgrp_t = -af * drho_t * ir2;
+    m.dgtt_r = -2.0f * rf * ir2;
+    m.dgtt_t = -drho_t * ir2;
+    m.dgpp_r = -2.0f * rf * ir2 * is2f;
+    m.dgpp_t = -drho_t * ir2 * is2f - 2.0f * sf * cf * irf * is2f * is2f;
+}
+
+// the Boris step of an island particle: the lower metric from the pairs
+__device__ __forceinline__ void boris_island(const KSGeo<float> &m, const IslandKeep &k, const df &a, const df &a2,
+                                             const df &r, const df &s, float qm, float dt, const float D[3],
+                                             const float B[3], float u[3], int pusher)
+{
+    const df r2 = r * r, s2 = s * s;
+    const df Dl = r2 + a2 - mul(r, 2.0f);
+    const df ra = r2 + a2;
+    const df Sg = ra * ra - a2 * Dl * s2;
+    KSPoint<float> mm;
+    mm.alpha = m.alpha;
+    mm.g_rr = m.opz;
+    mm.g_tt = m.rho2;
+    mm.g_pp = (float)(Sg * s2 * k.ir);
+    mm.g_rp = (float)(-(a * s2 * k.opz));
+    mm.gi_rr = m.grr;
+    mm.gi_rp = m.grp;
+    mm.gi_tt = m.gtt;
+    mm.gi_pp = m.gpp;
+    mm.sqrtg = (float)(k.rho2 * s * k.opz * k.alpha);  // rho^2 sin sqrt(1+z)
     if (pusher) {
         const VayMetric<float> vm{mm.alpha, mm.g_rr, mm.g_rp, mm.g_tt, mm.g_pp, mm.gi_rr, mm.gi_rp, mm.gi_tt,
                                   mm.gi_pp, mm.sqrtg};
@@ -250,29 +380,55 @@ __device__ __forceinline__ void push_one(const Push32Args &A, int i, int j, floa
         const float4 sc = __ldg(reinterpret_cast<const float4 *>(A.rowsc) + j);
         sincos_shift<float>(sc.x, sc.z, o2 * A.dthf, s0, c0);
     }
-    KSGeo<M> m;
-    ks_geo_sc<M>(am, r0, s0, c0, m);
+    // the island's metric comes as FP32 values rounded from pairs; the FP32
+    // path forms only the Boris step's metric values here
+    constexpr bool IS_F = std::is_same<M, float>::value;
+    using MG = typename std::conditional<IS_DF, float, M>::type;
+    KSGeo<MG> m;
+    IslandKeep keep;
+    if constexpr (IS_DF)
+        ks_geo_island(am, A.a2_df, r0, s0, c0, m, &keep);
+    else if constexpr (!IS_F)
+        ks_geo_sc<M>(am, r0, s0, c0, m);
     if (A.massive[sp] && A.qm[sp] != 0.0f) {
         St32 Sh0, S0h, S00, Shh;
         stencil32(g, i, j, o1, o2, true, false, 1.0f, Sh0);
         stencil32(g, i, j, o1, o2, false, true, -1.0f, S0h);
         stencil32(g, i, j, o1, o2, false, false, 1.0f, S00);
         stencil32(g, i, j, o1, o2, true, true, 1.0f, Shh);
+        // parities across the polar axis: D^theta odd (-1 on a reflected row),
+        // B^r and B^phi even; Sh0 and S00 reflect no row
         float Dv[3], Bv[3];
         Dv[0] = gather32(A.D0, A.ld, Sh0);
-        Dv[1] = gather32(A.D1, A.ld, S0h);
+        Dv[1] = gather32(A.D1, A.ld, flip_rows(S0h));
         Dv[2] = gather32(A.D2, A.ld, S00);
         Bv[1] = gather32(A.B1, A.ld, Sh0);
         Bv[2] = gather32(A.B2, A.ld, Shh);
-        S0h.p0 = S0h.p1 = 1.0f;
         Bv[0] = gather32(A.B0, A.ld, S0h);
-        boris_geo<M>(m, am, r0, s0, A.qm[sp], A.dt, Dv, Bv, u, A.pusher);
+        if constexpr (IS_DF) {
+            boris_island(m, keep, am, A.a2_df, r0, s0, A.qm[sp], A.dt, Dv, Bv, u, A.pusher);
+        } else if constexpr (IS_F) {
+            KSPoint<float> mm;
+            ks_point_boris32(am, A.a2f, r0, s0, c0, mm);
+            if (A.pusher) {
+                const VayMetric<float> vm{mm.alpha, mm.g_rr, mm.g_rp, mm.g_tt, mm.g_pp, mm.gi_rr, mm.gi_rp, mm.gi_tt,
+                                          mm.gi_pp, mm.sqrtg};
+                vay_step<float>(vm, A.qm[sp], A.dt, Dv, Bv, u);
+            } else {
+                boris32<float>(mm, A.qm[sp], A.dt, Dv, Bv, u);
+            }
+        } else {
+            boris_geo<M>(m, am, r0, s0, A.qm[sp], A.dt, Dv, Bv, u, A.pusher);
+        }
     }
     const float eps = A.massive[sp] ? 1.0f : 0.0f;
     const float dt = A.dt, h = 0.5f * dt;
     const float idth = A.idthf;
     RhsT<float> f0, ft;
-    geo_rhs_m<M, float>(m, eps, u[0], u[1], u[2], f0);
+    if constexpr (IS_F)
+        geo_rhs_direct32(am, A.a2f, eps, r0, s0, c0, u[0], u[1], u[2], f0);
+    else
+        geo_rhs_m<MG, float>(m, eps, u[0], u[1], u[2], f0);
     f0.xt *= idth;
     float a1 = d0 + dt * f0.xr, a2 = o2 + dt * f0.xt, ap = dt * f0.xp;
     float b1 = u[0] + dt * f0.ur, b2 = u[1] + dt * f0.ut;
@@ -304,7 +460,11 @@ __device__ __forceinline__ void push_one(const Push32Args &A, int i, int j, floa
             ri = rcf + a1;
         }
         if constexpr (std::is_same<M, float>::value) {
-            geo_rhs_direct<float>(am, eps, ri, s, c, b1, b2, u[2], ft);
+            geo_rhs_direct32(am, A.a2f, eps, ri, s, c, b1, b2, u[2], ft);
+        } else if constexpr (IS_DF) {
+            KSGeo<float> mi;
+            ks_geo_island(am, A.a2_df, ri, s, c, mi, nullptr);
+            geo_rhs_m<float, float>(mi, eps, b1, b2, u[2], ft);
         } else {
             KSGeo<M> mi;
             ks_geo_sc<M>(am, ri, s, c, mi);
@@ -374,8 +534,10 @@ __global__ void __launch_bounds__(256, GRPIC_PUSH32_MINB) push32_kernel(Push32Ar
                       isfinite(u[0]) && isfinite(u[1]) && isfinite(u[2]);
             if (ok) {
                 live = true;
-                i = cellk % g.nr;
-                j = cellk / g.nr;
+                // cellk / n_r as a multiply-high by ceil(2^64 / n_r): exact
+                // for cellk < 2^31 (the error term stays below 2^-33)
+                j = (int)__umul64hi((unsigned long long)cellk, A.nr_recip);
+                i = cellk - j * g.nr;
             } else {
                 bool fin = isfinite(o1) && isfinite(o2) && isfinite(u[0]) && isfinite(u[1]) && isfinite(u[2]);
                 set_status(A.status, fin ? GRPIC_ERANGE : GRPIC_ENAN);
@@ -470,7 +632,8 @@ __global__ void __launch_bounds__(256, GRPIC_PUSH32_MINB) push32_kernel(Push32Ar
     }
 
     // ---- deposit: lanes grouped by start cell, each group reduce-scattered --
-    deposit_warp_split<float, 3>(dep, i, j, g.nr, wa1, wa2, wb1, wb2, wq, wphi, A.dt, lane, g.nth, NG, A.ld, A.J0,
+    deposit_warp_split<float, 3>(dep, i, j, g.nr, wa1, wa2, wb1, wb2, wq * A.m_i2dt, wq * A.idt, wphi, lane, g.nth,
+                                 NG, A.ld, A.J0,
                                  A.J1, A.J2);
 }
 
@@ -482,6 +645,8 @@ cudaError_t launch_push32(grpic_ctx *ctx, const grpic_particles *in, grpic_parti
     Push32Args A;
     A.g = ctx->g;
     A.dt = (float)ctx->prm.dt;
+    A.idt = (float)(1.0 / ctx->prm.dt);
+    A.m_i2dt = (float)(-0.5 / ctx->prm.dt);
     A.n_iter = ctx->prm.n_push_iter;
     A.tolf = (float)ctx->prm.push_tol;
     for (int k = 0; k < 4; ++k) {
@@ -493,11 +658,13 @@ cudaError_t launch_push32(grpic_ctx *ctx, const grpic_particles *in, grpic_parti
     A.island_fp64 = ctx->prm.island_arith == 1 ? 1 : 0;
     A.use_tol = ctx->prm.push_tol > 0.0 ? 1 : 0;
     A.af = (float)ctx->g.a;
+    A.a2f = (float)(ctx->g.a * ctx->g.a);
     A.dthf = (float)ctx->g.dth;
     A.idthf = (float)(1.0 / ctx->g.dth);
     A.dx1f = (float)ctx->g.dx1;
     A.idx1f = (float)(1.0 / ctx->g.dx1);
     A.a_df = df_const(ctx->g.a);
+    A.a2_df = df_const(ctx->g.a * ctx->g.a);
     A.dth_df = df_const(ctx->g.dth);
     A.rcol2 = ctx->rcol2;
     A.rowsc = ctx->rowsc;
@@ -540,6 +707,7 @@ cudaError_t launch_push32(grpic_ctx *ctx, const grpic_particles *in, grpic_parti
     A.histogram = histogram ? 1 : 0;
     A.pusher = ctx->prm.pusher;
     A.status = ctx->d_status;
+    A.nr_recip = ~0ull / (unsigned long long)ctx->g.nr + 1ull;
     if (p->n <= 0) return cudaSuccess;
     push32_kernel<<<(unsigned)((p->n + 255) / 256), 256, 0, s>>>(A);
     return cudaGetLastError();

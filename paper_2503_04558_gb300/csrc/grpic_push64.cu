@@ -33,6 +33,7 @@ namespace {
 struct Push64Args {
     GridDev g;
     double dt;
+    double idt, m_i2dt;  // 1 / dt, -1 / (2 dt)
     int n_iter;
     double qm[4], qw[4];
     int massive[4];
@@ -479,7 +480,8 @@ __global__ void __launch_bounds__(256) push64_kernel(Push64Args A)
     // ---- deposit (CIC): the core entries reduced across the warp by start
     // cell, the entries of lanes that left their cell added directly
     if constexpr (SHAPE == 1)
-        deposit_warp_split<double, 3>(dep, i0, j0, g.nr, wa1, wa2, wb1, wb2, wq, wphi, A.dt, lane, g.nth, NG, A.ld,
+        deposit_warp_split<double, 3>(dep, i0, j0, g.nr, wa1, wa2, wb1, wb2, wq * A.m_i2dt, wq * A.idt, wphi, lane,
+                                      g.nth, NG, A.ld,
                                       A.J0, A.J1, A.J2);
 
     // ---- histogram of the new keys (warp-aggregated) -----------------------
@@ -512,6 +514,8 @@ static Push64Args push64_args(grpic_ctx *ctx, const grpic_particles *in, grpic_p
     Push64Args A;
     A.g = ctx->g;
     A.dt = ctx->prm.dt;
+    A.idt = 1.0 / ctx->prm.dt;
+    A.m_i2dt = -0.5 / ctx->prm.dt;
     A.n_iter = ctx->prm.n_push_iter;
     for (int k = 0; k < 4; ++k) {
         A.qm[k] = ctx->prm.q_over_m[k];

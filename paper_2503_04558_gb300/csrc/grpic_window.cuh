@@ -116,8 +116,7 @@ __device__ __forceinline__ void window_add(int v, T val, int i0, int j0, int nth
 template <typename T>
 __device__ __forceinline__ T cic_weight(T d)
 {
-    d = d < T(0) ? -d : d;
-    return d < T(1) ? T(1) - d : T(0);
+    return fmax(T(0), T(1) - fabs(d));
 }
 
 template <typename T>
@@ -248,9 +247,11 @@ __device__ __forceinline__ void add_at(T *J, int rmax, int i0, int j0, int k, in
     atomicAdd(J + (size_t)row * ld + (i0 - 1 + k + ng), v);
 }
 
+// cr = -q w / (2 dt) and cq = q w / dt of the particle's species (the
+// callers form them by multiplication with 1 / dt)
 template <typename T, int MAXG>
-__device__ __forceinline__ void deposit_warp_split(bool dep, int i0, int j0, int nr, T a1, T a2, T b1, T b2, T qw,
-                                                   T dphi, T dt, int lane, int nth, int ng, int64_t ld, T *J0, T *J1,
+__device__ __forceinline__ void deposit_warp_split(bool dep, int i0, int j0, int nr, T a1, T a2, T b1, T b2, T cr,
+                                                   T cq, T dphi, int lane, int nth, int ng, int64_t ld, T *J0, T *J1,
                                                    T *J2)
 {
     const unsigned FULL = 0xffffffffu;
@@ -262,7 +263,7 @@ __device__ __forceinline__ void deposit_warp_split(bool dep, int i0, int j0, int
         S1t[k] = cic_weight<T>(b2 - T(k - 1));
     }
     const T S0r1 = T(1) - a1, S0r2 = a1, S0t1 = T(1) - a2, S0t2 = a2;
-    const T cr = -qw / (T(2) * dt), cp = qw * dphi / dt;
+    const T cp = cq * dphi;
     // prefix sums: Pr(k) = sum_{k' <= k} (S1r - S0r)(k'), Pt likewise
     const T Pr0 = S1r[0], Pr1 = Pr0 + S1r[1] - S0r1, Pr2 = Pr1 + S1r[2] - S0r2;
     const T Pt0 = S1t[0], Pt1 = Pt0 + S1t[1] - S0t1, Pt2 = Pt1 + S1t[2] - S0t2;
