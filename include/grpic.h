@@ -205,6 +205,18 @@ grpic_status grpic_deposit(grpic_ctx *ctx, const grpic_particles *before, const 
  * axis), the outer damping layer once at the end. */
 grpic_status grpic_field_update(grpic_ctx *ctx, grpic_fields *f, void *stream);
 
+/* How an FP32 context runs the field update: fused != 0 (the default) by
+ * launches of four stages each on tiles staged in shared memory by the tensor
+ * copy engine (56 x 24 points per CTA plus a halo of 4, the stages inside a
+ * launch updating one point less of halo each), the result copied back into
+ * f's arrays; fused = 0 one launch per stage.  Both run the same operations
+ * per point (the fields agree to FP32 rounding: the compiler contracts a few
+ * multiply-adds differently in the two kernels).  The fused path needs
+ * 16-byte aligned arrays and ld * 4 a
+ * multiple of 16 (otherwise the per-stage path runs); the row-restricted
+ * update and FP64 contexts always use the per-stage path.  No device work. */
+grpic_status grpic_set_field_path(grpic_ctx *ctx, int32_t fused);
+
 /* Stable sort of the particles by cell key (dead particles last, dropped).
  * Keys are recomputed from the particle positions.  The sorted arrays are
  * written to `scratch` (same layout and capacity); on return the two structs'

@@ -320,6 +320,7 @@ grpic_status grpic_init(grpic_metric metric, double spin, const grpic_grid *grid
     cudaGetDevice(&ctx->device);
     ctx->grid = *grid;
     ctx->prm = *prm;
+    ctx->field_fused = 1;
     GridDev &g = ctx->g;
     g.nr = grid->n_r;
     g.nth = grid->n_theta;
@@ -897,6 +898,13 @@ grpic_status grpic_slab_assemble(grpic_ctx *ctx, grpic_particles *dst, const grp
         if (e != cudaSuccess) return cuda_fail(ctx, e, "slab assemble count");
     }
     drop_sort_state(ctx);
+    return GRPIC_OK;
+}
+
+grpic_status grpic_set_field_path(grpic_ctx *ctx, int32_t fused)
+{
+    if (!ctx) return GRPIC_EINVAL;
+    ctx->field_fused = fused ? 1 : 0;
     return GRPIC_OK;
 }
 

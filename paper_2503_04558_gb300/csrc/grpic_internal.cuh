@@ -102,6 +102,9 @@ struct grpic_ctx {
     int timing;
     std::vector<cudaEvent_t> *tevents;
     int64_t tsteps;
+    // FP32 field update by fused shared-memory launches (1, the default) or
+    // one launch per stage (0); grpic_set_field_path
+    int field_fused;
     char err[256];
 };
 

@@ -26,7 +26,7 @@ EXPORTS = ["grpic_init", "grpic_init_fields", "grpic_push", "grpic_deposit", "gr
            "grpic_step", "grpic_step_graph", "grpic_diagnostics", "grpic_charge_check", "grpic_get_areas", "grpic_sync", "grpic_last_error", "grpic_destroy",
            "grpic_sort_noalloc", "grpic_set_timing", "grpic_get_timing", "grpic_alu_peak",
            "grpic_field_update_rows", "grpic_halo_pack", "grpic_halo_unpack", "grpic_sort_split",
-           "grpic_particles_pack", "grpic_slab_assemble"]
+           "grpic_particles_pack", "grpic_slab_assemble", "grpic_set_field_path"]
 NOALLOC_MAX_PARTICLES = 2097152
 NOALLOC_MAX_CELLS = 262144
 
@@ -91,6 +91,7 @@ def load(path: str = LIB_PATH):
         "grpic_sort_split": [v, p(ParticlesC), p(ParticlesC), C.c_int32, C.c_int32, p(i64), v],
         "grpic_particles_pack": [v, p(ParticlesC), i64, i64, v, v],
         "grpic_slab_assemble": [v, p(ParticlesC), p(ParticlesC), i64, i64, v, i64, v, i64, v],
+        "grpic_set_field_path": [v, C.c_int32],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -376,6 +377,12 @@ class Context:
                                         _stream(stream)), "grpic_step")
         P.sync_ptrs()
         P.n = P._sc.n   # radiation or injection: the whole capacity is the slot range
+
+    def set_field_path(self, fused: bool):
+        """FP32 field update by fused shared-memory launches (True, the
+        default) or one launch per stage (False); the same operations, fields
+        equal to FP32 rounding."""
+        self._check(self.lib.grpic_set_field_path(self.h, 1 if fused else 0), "grpic_set_field_path")
 
     def set_timing(self, enable: bool):
         """Record per-phase CUDA events in every step of grpic_step."""

@@ -313,3 +313,36 @@ def test_fp32_deferred_order_matches_separate_calls(G):
         assert relerr(h1[k][:n], h0[k][:n], mask=same) < 1e-4, k
     for a, b in zip(f1, f0):
         assert relerr(a, b) < 1e-4
+
+
+@pytest.mark.parametrize("nr,nth", [(100, 70), (98, 64)])
+def test_fp32_fused_field_update_matches_per_stage(G, nr, nth):
+    """The FP32 field update by fused launches (four stages on tiles staged in
+    shared memory by the tensor copy) gives the per-stage kernels' fields to
+    FP32 rounding (the same operations; the compiler contracts a few
+    multiply-adds differently in the two kernels: 1-ulp differences at a few
+    percent of the entries after three updates): 100 x 70 cells (tiles of 56 x 24 with ragged edges,
+    the guard columns and both axis rows inside edge tiles) and 98 x 64,
+    whose row stride (102 floats) is no multiple of 16 bytes and takes the
+    per-stage path in both runs (bit for bit)."""
+    oc, gc = configs(nr, nth, A09, 0.9 * RH, 30.0, precision=32)
+    rng = np.random.default_rng(11)
+    J = [rng.normal(size=O.field_shape(oc)).astype(np.float32) * 1e-3 for _ in range(3)]
+    out = []
+    for fused in (True, False):
+        ctx = G.Context(gc)
+        ctx.set_field_path(fused)
+        F = G.Fields(gc)
+        ctx.init_fields(F, O.WALD, 1.0)
+        for k in range(3):
+            F.J[k].copy_(torch.from_numpy(J[k]))
+        for _ in range(3):
+            ctx.field_update(F)
+        assert ctx.sync() == 0
+        out.append([t.cpu().numpy().copy() for t in F.D + F.B])
+    for a, b in zip(*out):
+        if nr % 4 != 0:
+            assert np.array_equal(a, b)
+            continue
+        d = np.abs(a.astype(np.float64) - b)
+        assert d.max() <= 4 * 2.0 ** -24 * np.abs(b).max()
