@@ -233,13 +233,9 @@ def run_grpic(args, prec, rank, world, e2e_steps, pusher=0, shape_order=1, islan
     if prec == 64:
         S.load(gen["r"], gen["th"], gen["u1"], gen["u2"], gen["u3"], gen["tag"])
     else:
-        x1 = (torch.log(gen["r"]) - math.log(cfg.r_in)) / cfg.dx1
-        x2 = gen["th"] / cfg.dth
-        i = torch.floor(x1).clamp(0, cfg.n_r - 1)
-        j = torch.floor(x2).clamp(0, cfg.n_theta - 1)
-        cell = (j * cfg.n_r + i).to(torch.int32)
-        S.load((x1 - i).float(), (x2 - j).float(), gen["u1"].float(), gen["u2"].float(), gen["u3"].float(),
-               gen["tag"], cell)
+        cell, o1, o2 = ctx.fp32_encode(gen["r"], gen["th"])
+        S.load(o1, o2, gen["u1"].float(), gen["u2"].float(), gen["u3"].float(), gen["tag"], cell)
+        del cell, o1, o2
     del gen
     torch.cuda.empty_cache()
     stream = torch.cuda.current_stream()
@@ -365,7 +361,7 @@ def run_e2e(e2e_steps, ctx, S, F, cfg, stream):
 IDX_SHIFT = 2   # loading index in tag bits 2..30 (species in 0..1, dead in 31)
 
 
-def _state_by_index(S, cfg, n):
+def _state_by_index(S, cfg, n, ctx):
     """(r, theta, u_r, u_theta, u_phi) of the live particles scattered to their
     loading index (NaN where the particle is dead), as float64 device tensors."""
     import torch
@@ -376,10 +372,7 @@ def _state_by_index(S, cfg, n):
     if cfg.precision == 64:
         vals = [P.x1[:live], P.x2[:live]]
     else:
-        c = P.cell[:live].to(torch.int64)
-        x1 = (c % cfg.n_r).double() + P.x1[:live].double()
-        x2 = (c // cfg.n_r).double() + P.x2[:live].double()
-        vals = [cfg.r_in * torch.exp(x1 * cfg.dx1), x2 * cfg.dth]
+        vals = list(ctx.fp32_decode(P.cell[:live], P.x1[:live], P.x2[:live]))
     vals += [P.u1[:live].double(), P.u2[:live].double(), P.u3[:live].double()]
     for o, v in zip(out, vals):
         o[idx] = v
@@ -417,29 +410,25 @@ def fp32_error_measure(grid, ppc, nsteps, seed=4321):
         if nudge:
             gen["th"] = torch.nextafter(gen["th"], torch.full_like(gen["th"], 4.0))
         S = G.ParticleSet(cfg, n)
+        ctx = G.Context(cfg)
         if cfg.precision == 64:
             S.load(gen["r"], gen["th"], gen["u1"], gen["u2"], gen["u3"], tag)
         else:
-            x1 = (torch.log(gen["r"]) - math.log(cfg.r_in)) / cfg.dx1
-            x2 = gen["th"] / cfg.dth
-            i = torch.floor(x1).clamp(0, cfg.n_r - 1)
-            j = torch.floor(x2).clamp(0, cfg.n_theta - 1)
-            S.load((x1 - i).float(), (x2 - j).float(), gen["u1"].float(), gen["u2"].float(), gen["u3"].float(),
-                   tag, (j * cfg.n_r + i).to(torch.int32))
+            cell, o1, o2 = ctx.fp32_encode(gen["r"], gen["th"])
+            S.load(o1, o2, gen["u1"].float(), gen["u2"].float(), gen["u3"].float(), tag, cell)
+            del cell, o1, o2
         del gen
-        ctx = G.Context(cfg)
         F = G.Fields(cfg)
         ctx.init_fields(F, G.SPLIT_MONOPOLE, B0)
         ctx.step(S, F, nsteps)
         st = ctx.sync()
-        runs[name] = (S, F, st, cfg)
-        del ctx
+        runs[name] = (S, F, st, cfg, ctx)
     cols = slice(2, 2 + grid + 1)
     bulk = slice(10, grid - 9)
-    y64 = _state_by_index(runs["f64"][0], c64, n)
+    y64 = _state_by_index(runs["f64"][0], c64, n, runs["f64"][4])
 
     def compare(name):
-        S, F, st, cfg = runs[name]
+        S, F, st, cfg, cx = runs[name]
         field, field_bulk = {}, {}
         for nm, a, b in (("D", F.D, runs["f64"][1].D), ("B", F.B, runs["f64"][1].B)):
             for k in range(3):
@@ -447,7 +436,7 @@ def fp32_error_measure(grid, ppc, nsteps, seed=4321):
                 d = (a[k][:, cols].double() - ref).abs()
                 field[f"{nm}{k}"] = float(d.max() / ref.abs().max())
                 field_bulk[f"{nm}{k}"] = float(d[bulk].max() / ref.abs().max())
-        y = _state_by_index(S, cfg, n)
+        y = _state_by_index(S, cfg, n, cx)
         both = ~torch.isnan(y64[0]) & ~torch.isnan(y[0])
         only = int((~torch.isnan(y64[0]) ^ ~torch.isnan(y[0])).sum())
         r, th = y64[0][both], y64[1][both]

@@ -31,7 +31,12 @@
  *   precision 64: x1 = r, x2 = theta (double), u1..u3 = covariant u_r,
  *                 u_theta, u_phi (double); `cell` unused.
  *   precision 32: cell = j*n_r + i (int32), x1, x2 = offsets in [0,1] inside
- *                 the cell in logical units (float), u1..u3 float.
+ *                 the cell in logical units (float), u1..u3 float.  In the
+ *                 last theta row (j = n_theta - 1) x2 is the distance to the
+ *                 pole, q = n_theta - theta/dtheta, so that theta near pi
+ *                 keeps FP32's relative precision as theta near 0 does in
+ *                 row 0 (x2 = theta/dtheta there); grpic_fp32_encode and
+ *                 grpic_fp32_decode convert.
  *   tag: species in bits 0-1 (indexes q_over_m/q_weight/massive), bit 31 =
  *   dead.  `n` is the number of slots the call may touch; if `d_count` is not
  *   NULL it points at a device int64 holding the live count, which bounds
@@ -594,6 +599,15 @@ grpic_status grpic_slab_assemble(grpic_ctx *ctx, grpic_particles *dst, const grp
  * FMA warp-instructions/s, out[2] = the SM count.  Allocates and frees an
  * 8-byte result; synchronizes `stream`. */
 grpic_status grpic_alu_peak(int32_t kind, double out[3], void *stream);
+
+/* Conversion between FP64 positions (r, theta) and the FP32 form's cell key
+ * and offsets (the layout above, the last row's offset measured from the
+ * pole), on the context's grid, in FP64 on the device: slots [0, n) of the
+ * given device arrays.  Encoding clamps the cell to the grid. */
+grpic_status grpic_fp32_encode(grpic_ctx *ctx, int64_t n, const double *r, const double *theta, int32_t *cell,
+                               float *o1, float *o2, void *stream);
+grpic_status grpic_fp32_decode(grpic_ctx *ctx, int64_t n, const int32_t *cell, const float *o1, const float *o2,
+                               double *r, double *theta, void *stream);
 
 /* Human-readable description of the last error seen by the context. */
 const char *grpic_last_error(const grpic_ctx *ctx);

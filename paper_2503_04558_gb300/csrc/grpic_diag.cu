@@ -24,9 +24,13 @@ __device__ __forceinline__ void logical(const GridDev &g, const void *x1, const 
         a = (log(((const double *)x1)[p]) - g.ln_rin) / g.dx1;
         b = ((const double *)x2)[p] / g.dth;
     } else {
+        // FP32 form: cell key and offsets; the last row holds the distance
+        // to theta = pi
         int c = cell[p];
         a = (c % g.nr) + (double)((const float *)x1)[p];
-        b = (c / g.nr) + (double)((const float *)x2)[p];
+        const int j = c / g.nr;
+        const double o = (double)((const float *)x2)[p];
+        b = (j == g.nth - 1) ? (double)g.nth - o : j + o;
     }
 }
 
@@ -246,6 +250,32 @@ cudaError_t check_t(grpic_ctx *ctx, const grpic_particles *p, const grpic_fields
     return cudaGetLastError();
 }
 
+// FP64 (r, theta) <-> the FP32 form's (cell, o1, o2), in FP64
+__global__ void encode32_kernel(GridDev g, int64_t n, const double *r, const double *th, int32_t *cell, float *o1,
+                                float *o2)
+{
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    const double x1 = (log(r[p]) - g.ln_rin) / g.dx1, x2 = th[p] / g.dth;
+    int i = (int)floor(x1), j = (int)floor(x2);
+    i = i < 0 ? 0 : (i > g.nr - 1 ? g.nr - 1 : i);
+    j = j < 0 ? 0 : (j > g.nth - 1 ? g.nth - 1 : j);
+    cell[p] = j * g.nr + i;
+    o1[p] = (float)(x1 - i);
+    o2[p] = (float)(j == g.nth - 1 ? (double)g.nth - x2 : x2 - j);
+}
+
+__global__ void decode32_kernel(GridDev g, int64_t n, const int32_t *cell, const float *o1, const float *o2, double *r,
+                                double *th)
+{
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    const int c = cell[p], j = c / g.nr, i = c - j * g.nr;
+    const double x2 = j == g.nth - 1 ? (double)g.nth - (double)o2[p] : j + (double)o2[p];
+    r[p] = g.r_in * exp((i + (double)o1[p]) * g.dx1);
+    th[p] = x2 * g.dth;
+}
+
 }  // namespace
 
 cudaError_t launch_charge_check(grpic_ctx *ctx, const grpic_particles *p, const grpic_fields *f, double *rho,
@@ -284,3 +314,23 @@ cudaError_t launch_deposit(grpic_ctx *ctx, const grpic_particles *b, const grpic
 }
 
 }  // namespace grpic
+
+extern "C" grpic_status grpic_fp32_encode(grpic_ctx *ctx, int64_t n, const double *r, const double *theta,
+                                          int32_t *cell, float *o1, float *o2, void *stream)
+{
+    using namespace grpic;
+    if (!ctx || n < 0 || (n > 0 && (!r || !theta || !cell || !o1 || !o2))) return GRPIC_EINVAL;
+    if (n == 0) return GRPIC_OK;
+    encode32_kernel<<<(unsigned)((n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(ctx->g, n, r, theta, cell, o1, o2);
+    return cudaGetLastError() == cudaSuccess ? GRPIC_OK : GRPIC_ECUDA;
+}
+
+extern "C" grpic_status grpic_fp32_decode(grpic_ctx *ctx, int64_t n, const int32_t *cell, const float *o1,
+                                          const float *o2, double *r, double *theta, void *stream)
+{
+    using namespace grpic;
+    if (!ctx || n < 0 || (n > 0 && (!r || !theta || !cell || !o1 || !o2))) return GRPIC_EINVAL;
+    if (n == 0) return GRPIC_OK;
+    decode32_kernel<<<(unsigned)((n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(ctx->g, n, cell, o1, o2, r, theta);
+    return cudaGetLastError() == cudaSuccess ? GRPIC_OK : GRPIC_ECUDA;
+}

@@ -4,7 +4,10 @@
 // fields n, geodesic predictor + trapezoidal correctors, axis reflection,
 // Esirkepov deposit.  What changes is the number format:
 //   * a particle is an int32 cell key plus FP32 offsets (o1, o2) in [0, 1]
-//     inside the cell (logical units) and FP32 covariant momenta; the geodesic
+//     inside the cell (logical units) and FP32 covariant momenta -- in the
+//     last theta row o2 holds q = (pi - theta) / dtheta, the distance to the
+//     pole, so that theta near pi keeps FP32's relative precision as theta
+//     near 0 does in row 0; the geodesic
 //     is integrated for r - r_i (r_i the cell's inner edge) and for o2
 //     (dx2/dt = X^th / dtheta), so the trapezoidal rule acts on r and theta as
 //     in the paper while the position keeps FP32 precision relative to its
@@ -352,9 +355,14 @@ __device__ __forceinline__ void boris_island(const KSGeo<float> &m, const Island
     }
 }
 
+// o2 is the offset from the row's lower edge (stencils and window); in the
+// last row (pole) the particle's theta offset is q = (pi - theta) / dtheta,
+// stored with FP32's relative precision, and the trapezoid integrates q
+// there (dq/dt = -X^theta / dtheta): on return q (pole) or o2 hold the end
+// point's offset in that row's variable
 template <typename M>
 __device__ __forceinline__ void push_one(const Push32Args &A, int i, int j, float &o1, float &o2, float u[3], int sp,
-                                         float &dphi)
+                                         float &dphi, bool pole, float &q)
 {
     constexpr bool IS_DF = std::is_same<M, df>::value, IS_D = std::is_same<M, double>::value;
     const GridDev &g = A.g;
@@ -363,22 +371,29 @@ __device__ __forceinline__ void push_one(const Push32Args &A, int i, int j, floa
     const float d0 = rcf * expm1_cell(o1 * A.dx1f, A.dx1f);  // r - r_i
     // metric at x^n, shared by the Boris step and the first right-hand side
     M am, r0, s0, c0;
+    // the angle's sin and cos: in the pole row from theta' = pi - theta =
+    // q dtheta (row 0's table shifted by q dtheta; cos theta = -cos theta')
     if constexpr (IS_D) {
         am = g.a;
         r0 = A.rcol[i + NG] + (double)d0;
-        sincos(((double)j + (double)o2) * g.dth, &s0, &c0);
+        if (pole)
+            sincos((double)g.nth * g.dth - (double)q * g.dth, &s0, &c0);
+        else
+            sincos(((double)j + (double)o2) * g.dth, &s0, &c0);
     } else if constexpr (IS_DF) {
         am = A.a_df;
         r0 = df(rc2.x, rc2.y) + df(d0);
-        const float4 sc = __ldg(reinterpret_cast<const float4 *>(A.rowsc) + j);
-        sincos_shift_df(df(sc.x, sc.y), df(sc.z, sc.w), mul(A.dth_df, o2), s0, c0);
+        const float4 sc = __ldg(reinterpret_cast<const float4 *>(A.rowsc) + (pole ? 0 : j));
+        sincos_shift_df(df(sc.x, sc.y), df(sc.z, sc.w), mul(A.dth_df, pole ? q : o2), s0, c0);
+        if (pole) c0 = -c0;
     } else {
         // sin, cos of theta_j (row table) shifted by o2 dtheta (|shift| <= one
         // cell: the series of sincos_shift is exact to FP32 rounding there)
         am = A.af;
         r0 = rcf + d0;
-        const float4 sc = __ldg(reinterpret_cast<const float4 *>(A.rowsc) + j);
-        sincos_shift<float>(sc.x, sc.z, o2 * A.dthf, s0, c0);
+        const float4 sc = __ldg(reinterpret_cast<const float4 *>(A.rowsc) + (pole ? 0 : j));
+        sincos_shift<float>(sc.x, sc.z, (pole ? q : o2) * A.dthf, s0, c0);
+        if (pole) c0 = -c0;
     }
     // the island's metric comes as FP32 values rounded from pairs; the FP32
     // path forms only the Boris step's metric values here
@@ -430,33 +445,39 @@ __device__ __forceinline__ void push_one(const Push32Args &A, int i, int j, floa
     else
         geo_rhs_m<MG, float>(m, eps, u[0], u[1], u[2], f0);
     f0.xt *= idth;
-    float a1 = d0 + dt * f0.xr, a2 = o2 + dt * f0.xt, ap = dt * f0.xp;
+    // the theta offset integrated: o2 (X^theta / dtheta), or q in the pole
+    // row (-X^theta / dtheta); sg is the sign and t0 the start value
+    const float sg = pole ? -1.0f : 1.0f, t0 = pole ? q : o2;
+    float a1 = d0 + dt * f0.xr, a2 = t0 + sg * dt * f0.xt, ap = dt * f0.xp;
     float b1 = u[0] + dt * f0.ur, b2 = u[1] + dt * f0.ut;
     for (int it = 0; it < A.n_iter; ++it) {
-        // metric at the iterate: theta = theta^n + (a2 - o2) dtheta
+        // metric at the iterate: theta = theta^n + sg (a2 - t0) dtheta; in the
+        // pole row sin and cos of theta' shifted by (a2 - t0) dtheta
         M s, c, ri;
         if constexpr (IS_D) {
-            double d = ((double)a2 - (double)o2) * g.dth;
+            double d = sg * ((double)a2 - (double)t0) * g.dth;
             if (fabs(d) <= 0.05)
                 sincos_shift<double>(s0, c0, d, s, c);
             else
                 sincos(((double)j + (double)o2) * g.dth + d, &s, &c);
             ri = A.rcol[i + NG] + (double)a1;
         } else if constexpr (IS_DF) {
-            df d = two_sum(a2, -o2) * A.dth_df;
+            df d = two_sum(a2, -t0) * A.dth_df;
             if (fabs_hi(d) <= 0.1f) {
-                sincos_shift_df(s0, c0, d, s, c);
+                sincos_shift_df(s0, pole ? -c0 : c0, d, s, c);
             } else {
-                df th = df(j) * A.dth_df + mul(A.dth_df, o2) + d;
+                df th = df(pole ? 0 : j) * A.dth_df + mul(A.dth_df, t0) + d;
                 sincos_t(th, &s, &c);
             }
+            if (pole) c = -c;
             ri = df(rc2.x, rc2.y) + df(a1);
         } else {
-            float d = (a2 - o2) * A.dthf;
+            float d = (a2 - t0) * A.dthf;
             if (fabsf(d) <= 0.05f)
-                sincos_shift<float>(s0, c0, d, s, c);
+                sincos_shift<float>(s0, pole ? -c0 : c0, d, s, c);
             else
-                sincosf(((float)j + o2) * A.dthf + d, &s, &c);
+                sincosf(((float)(pole ? 0 : j) + t0) * A.dthf + d, &s, &c);
+            if (pole) c = -c;
             ri = rcf + a1;
         }
         if constexpr (std::is_same<M, float>::value) {
@@ -471,7 +492,7 @@ __device__ __forceinline__ void push_one(const Push32Args &A, int i, int j, floa
             geo_rhs_m<M, float>(mi, eps, b1, b2, u[2], ft);
         }
         ft.xt *= idth;
-        float n1 = d0 + h * (ft.xr + f0.xr), n2 = o2 + h * (ft.xt + f0.xt);
+        float n1 = d0 + h * (ft.xr + f0.xr), n2 = t0 + sg * h * (ft.xt + f0.xt);
         float nb1 = u[0] + h * (ft.ur + f0.ur), nb2 = u[1] + h * (ft.ut + f0.ut);
         ap = h * (ft.xp + f0.xp);
         bool done = false;
@@ -493,7 +514,10 @@ __device__ __forceinline__ void push_one(const Push32Args &A, int i, int j, floa
         if (done) break;
     }
     o1 = log1p_cell(__fdividef(a1, rcf)) * A.idx1f;  // back to the logical offset
-    o2 = a2;
+    if (pole)
+        q = a2;
+    else
+        o2 = a2;
     u[0] = b1;
     u[1] = b2;
     dphi = ap;
@@ -519,14 +543,14 @@ __global__ void __launch_bounds__(256, GRPIC_PUSH32_MINB) push32_kernel(Push32Ar
     bool live = false;
     uint32_t tag = DEAD;
     int i = 0, j = 0, cellk = 0;
-    float o1 = 0, o2 = 0, u[3] = {0, 0, 0};
+    float o1 = 0, o2 = 0, x2in = 0, u[3] = {0, 0, 0};
     if (p < n) {
         const int64_t src = permuted ? (int64_t)A.perm[p] : p;
         tag = A.in_tag[src];
         if (!(tag & DEAD)) {
             cellk = A.in_cell[src];
             o1 = A.in_o1[src];
-            o2 = A.in_o2[src];
+            o2 = x2in = A.in_o2[src];
             u[0] = A.in_u1[src];
             u[1] = A.in_u2[src];
             u[2] = A.in_u3[src];
@@ -538,6 +562,9 @@ __global__ void __launch_bounds__(256, GRPIC_PUSH32_MINB) push32_kernel(Push32Ar
                 // for cellk < 2^31 (the error term stays below 2^-33)
                 j = (int)__umul64hi((unsigned long long)cellk, A.nr_recip);
                 i = cellk - j * g.nr;
+                // the last row stores q = (pi - theta) / dtheta; its offset
+                // from the lower edge for the stencils and the window
+                if (j == g.nth - 1) o2 = 1.0f - x2in;
             } else {
                 bool fin = isfinite(o1) && isfinite(o2) && isfinite(u[0]) && isfinite(u[1]) && isfinite(u[2]);
                 set_status(A.status, fin ? GRPIC_ERANGE : GRPIC_ENAN);
@@ -549,21 +576,26 @@ __global__ void __launch_bounds__(256, GRPIC_PUSH32_MINB) push32_kernel(Push32Ar
     bool dep = false, moved = false;
     float wa1 = 0, wa2 = 0, wb1 = 0, wb2 = 0, wq = 0, wphi = 0;  // window inputs (kept for regrouping)
     int key = -1, ni = i, nj = j;
-    float n1 = o1, n2 = o2;
+    float n1 = o1, n2 = o2, x2out = x2in;
     if (live) {
         int sp = tag & 3u;
         float dphi = 0.0f;
+        const bool pole = j == g.nth - 1;
+        float q = x2in;
         // FP64 island: cells whose inner edge r_i lies below fp64_radius
         if (i >= A.i64)
-            push_one<float>(A, i, j, n1, n2, u, sp, dphi);
+            push_one<float>(A, i, j, n1, n2, u, sp, dphi, pole, q);
         else if (A.island_fp64)
-            push_one<double>(A, i, j, n1, n2, u, sp, dphi);
+            push_one<double>(A, i, j, n1, n2, u, sp, dphi, pole, q);
         else
-            push_one<df>(A, i, j, n1, n2, u, sp, dphi);
-        // axis reflection in offset space (theta = 0 is o2 = 0 of row 0,
-        // theta = pi is o2 = 1 of row nth-1)
+            push_one<df>(A, i, j, n1, n2, u, sp, dphi, pole, q);
+        // axis reflection (theta = 0 is o2 = 0 of row 0, theta = pi is q = 0
+        // of the last row); the end point relative to the start row's lower edge
         if (j == 0 && n2 < 0.0f) { n2 = -n2; u[1] = -u[1]; }
-        if (j == g.nth - 1 && n2 > 1.0f) { n2 = 2.0f - n2; u[1] = -u[1]; }
+        if (pole) {
+            if (q < 0.0f) { q = -q; u[1] = -u[1]; }
+            n2 = 1.0f - q;
+        }
         bool finite = isfinite(n1) && isfinite(n2) && isfinite(u[0]) && isfinite(u[1]) && isfinite(dphi);
         if (!finite) {
             set_status(A.status, GRPIC_ENAN);
@@ -593,6 +625,12 @@ __global__ void __launch_bounds__(256, GRPIC_PUSH32_MINB) push32_kernel(Push32Ar
                 if (n1 < 0.0f) n1 = 0.0f;
                 if (n2 > 1.0f) n2 = 1.0f;
                 if (n2 < 0.0f) n2 = 0.0f;
+                // the stored offset: q in the last row (kept as integrated when
+                // the particle stays there), the lower-edge offset elsewhere
+                if (nj == g.nth - 1)
+                    x2out = (pole && dj == 0) ? fminf(fmaxf(q, 0.0f), 1.0f) : 1.0f - n2;
+                else
+                    x2out = n2;
                 if (ni < 0 || ni >= g.nr) tag |= DEAD;  // left [r_in, r_out)
                 key = (tag & DEAD) ? ncell : nj * g.nr + ni;
             }
@@ -602,7 +640,7 @@ __global__ void __launch_bounds__(256, GRPIC_PUSH32_MINB) push32_kernel(Push32Ar
         if (moved || permuted) {
             A.cell[p] = nj * g.nr + ni;
             A.o1[p] = n1;
-            A.o2[p] = n2;
+            A.o2[p] = x2out;
             A.u1[p] = u[0];
             A.u2[p] = u[1];
             A.u3[p] = u[2];

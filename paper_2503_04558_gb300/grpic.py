@@ -26,7 +26,8 @@ EXPORTS = ["grpic_init", "grpic_init_fields", "grpic_push", "grpic_deposit", "gr
            "grpic_step", "grpic_step_graph", "grpic_diagnostics", "grpic_charge_check", "grpic_get_areas", "grpic_sync", "grpic_last_error", "grpic_destroy",
            "grpic_sort_noalloc", "grpic_set_timing", "grpic_get_timing", "grpic_alu_peak",
            "grpic_field_update_rows", "grpic_halo_pack", "grpic_halo_unpack", "grpic_sort_split",
-           "grpic_particles_pack", "grpic_slab_assemble", "grpic_set_field_path"]
+           "grpic_particles_pack", "grpic_slab_assemble", "grpic_set_field_path", "grpic_fp32_encode",
+           "grpic_fp32_decode"]
 NOALLOC_MAX_PARTICLES = 2097152
 NOALLOC_MAX_CELLS = 262144
 
@@ -92,6 +93,8 @@ def load(path: str = LIB_PATH):
         "grpic_particles_pack": [v, p(ParticlesC), i64, i64, v, v],
         "grpic_slab_assemble": [v, p(ParticlesC), p(ParticlesC), i64, i64, v, i64, v, i64, v],
         "grpic_set_field_path": [v, C.c_int32],
+        "grpic_fp32_encode": [v, i64, v, v, v, v, v, v],
+        "grpic_fp32_decode": [v, i64, v, v, v, v, v, v],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -377,6 +380,30 @@ class Context:
                                         _stream(stream)), "grpic_step")
         P.sync_ptrs()
         P.n = P._sc.n   # radiation or injection: the whole capacity is the slot range
+
+    def fp32_encode(self, r, th, stream=None):
+        """(cell, o1, o2) of the FP32 form from FP64 positions (device tensors
+        r, theta); the last theta row's offset is the distance to the pole."""
+        import torch
+        r, th = r.contiguous(), th.contiguous()
+        n = int(r.numel())
+        cell = torch.empty(n, dtype=torch.int32, device=r.device)
+        o1 = torch.empty(n, dtype=torch.float32, device=r.device)
+        o2 = torch.empty(n, dtype=torch.float32, device=r.device)
+        self._check(self.lib.grpic_fp32_encode(self.h, n, _ptr(r), _ptr(th), _ptr(cell), _ptr(o1), _ptr(o2),
+                                               _stream(stream)), "grpic_fp32_encode")
+        return cell, o1, o2
+
+    def fp32_decode(self, cell, o1, o2, stream=None):
+        """FP64 (r, theta) device tensors of FP32-form positions."""
+        import torch
+        cell, o1, o2 = cell.contiguous(), o1.contiguous(), o2.contiguous()
+        n = int(cell.numel())
+        r = torch.empty(n, dtype=torch.float64, device=cell.device)
+        th = torch.empty(n, dtype=torch.float64, device=cell.device)
+        self._check(self.lib.grpic_fp32_decode(self.h, n, _ptr(cell), _ptr(o1), _ptr(o2), _ptr(r), _ptr(th),
+                                               _stream(stream)), "grpic_fp32_decode")
+        return r, th
 
     def set_field_path(self, fused: bool):
         """FP32 field update by fused shared-memory launches (True, the

@@ -40,6 +40,25 @@ def logical(oc, r, th):
     return (np.log(r) - math.log(oc.r_in)) / oc.dx1, th / oc.dth
 
 
+def fp32_offsets(oc, r, th):
+    """The FP32 form's (cell, o1, o2) of FP64 positions, written out from the
+    documented layout (include/grpic.h): offsets from the cell's lower edges,
+    except in the last theta row, where o2 is the distance to theta = pi."""
+    x1, x2 = logical(oc, r, th)
+    i = np.clip(np.floor(x1), 0, oc.nr - 1)
+    j = np.clip(np.floor(x2), 0, oc.nth - 1)
+    o2 = np.where(j == oc.nth - 1, oc.nth - x2, x2 - j)
+    return (j * oc.nr + i).astype(np.int32), (x1 - i).astype(np.float32), o2.astype(np.float32)
+
+
+def fp32_logical(oc, cell, o1, o2):
+    """Logical coordinates (x1, x2) of FP32-form positions (inverse of fp32_offsets)."""
+    i = cell % oc.nr
+    j = cell // oc.nr
+    o2 = o2.astype(np.float64)
+    return i + o1.astype(np.float64), np.where(j == oc.nth - 1, oc.nth - o2, j + o2)
+
+
 def axis_grazers(oc, P, D, B, nsteps, theta_c=1e-3):
     """Oracle-only pre-run of nsteps full steps: indices into P of the particles
     whose path comes within theta_c of the polar axis (theta = 0 or pi).

@@ -9,7 +9,7 @@ import numpy as np
 import pytest
 
 import oracle as O
-from gpu_common import configs, relerr, flux_form, axis_grazers
+from gpu_common import configs, relerr, flux_form, axis_grazers, fp32_offsets, fp32_logical
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -27,18 +27,11 @@ def G():
 
 
 def to_fp32_state(oc, P):
-    x1 = (np.log(P.r) - math.log(oc.r_in)) / oc.dx1
-    x2 = P.th / oc.dth
-    i = np.clip(np.floor(x1), 0, oc.nr - 1)
-    j = np.clip(np.floor(x2), 0, oc.nth - 1)
-    cell = (j * oc.nr + i).astype(np.int32)
-    return cell, (x1 - i).astype(np.float32), (x2 - j).astype(np.float32)
+    return fp32_offsets(oc, P.r, P.th)
 
 
 def logical_from_fp32(oc, h):
-    i = h["cell"] % oc.nr
-    j = h["cell"] // oc.nr
-    return i + h["x1"].astype(np.float64), j + h["x2"].astype(np.float64)
+    return fp32_logical(oc, h["cell"], h["x1"], h["x2"])
 
 
 def load32(G, gc, oc, P):
@@ -113,28 +106,30 @@ def test_fp32_push_one_step_error(G, pusher):
     x1g, x2g = logical_from_fp32(oc, h)
     x1o = (np.log(P.r) - math.log(oc.r_in)) / oc.dx1
     x2o = P.th / oc.dth
-    # within 0.05 rad of the polar axis the push amplifies FP32 rounding by the
-    # 1/sin^2(theta) terms of gamma^{phi phi}: those particles get a looser bound
+    # away from and within 0.05 rad of the polar axis (where gamma^{phi phi} ~
+    # 1/sin^2(theta) amplifies any rounding; the last row's offset measured
+    # from the pole keeps theta near pi at FP32's relative precision)
     far = alive & (np.minimum(th0, math.pi - th0) > 0.05)
     near = alive & ~far
     ex1, ex2 = np.abs(x1g - x1o), np.abs(x2g - x2o)
     print("FP32 one-step position error (cells): max %.2e away from the axis, %.2e near it (%d particles)"
           % (max(ex1[far].max(), ex2[far].max()), max(ex1[near].max(), ex2[near].max()), near.sum()))
     assert ex1[far].max() < 2e-5 and ex2[far].max() < 2e-5   # cells
-    assert ex1[near].max() < 1e-2 and ex2[near].max() < 1e-2
+    assert ex1[near].max() < 2e-5 and ex2[near].max() < 2e-5
     for k, ref in (("u1", P.u1), ("u2", P.u2), ("u3", P.u3)):
         assert relerr(h[k][far], ref[far]) < 2e-5, k
-    # one-step currents: FP32 weights and atomics stay within 5e-4 of the FP64
-    # deposit on rows more than 0.05 rad from the axis; the rows next to the
-    # axis carry the ill-conditioned near-axis particles (J^phi ~ dphi/dt there)
+        assert relerr(h[k][near], ref[near], floor=np.max(np.abs(ref[far]))) < 2e-5, k
+    # one-step currents: FP32 weights and atomics, on the rows more than
+    # 0.05 rad from the axis and on all rows (the axis rows carry J^phi ~
+    # dphi/dt of the near-axis particles)
     rows = np.arange(oc.nth + 1) * oc.dth
     away = np.minimum(rows, math.pi - rows) > 0.05 + oc.dth
     jref = flux_form(oc, J)
     jerr = [relerr(host(F.J[k])[away], jref[k][away]) for k in range(3)]
     jnear = [relerr(host(F.J[k]), jref[k]) for k in range(3)]
     print("FP32 one-step current error (J^r A, J^th A, J^ph dV): away from the axis", jerr, "all rows", jnear)
-    assert max(jerr) < 5e-4, jerr
-    assert max(jnear) < 0.1, jnear
+    assert max(jerr) < 5e-6, jerr
+    assert max(jnear) < 1e-4, jnear
 
 
 def test_fp32_sort_is_bit_exact(G):
@@ -172,6 +167,7 @@ def run20(G):
     D, B = O.init_fields(oc, O.WALD, 1.0)
     P = make_particles(oc, 200000, seed=0)
     P = P.take(np.setdiff1d(np.arange(P.n), axis_grazers(oc, P, D, B, 20)))
+    P.tag = P.tag | (np.arange(P.n, dtype=np.uint32) << np.uint32(2))   # loading index in tag bits 2..30
     S = load32(G, gc, oc, P)
     rho0, div0 = ctx.diagnostics(S, F)
     base = host(div0) - host(rho0)
@@ -210,6 +206,43 @@ def test_fp32_wald128_particle_error(run20):
     agree = np.mean(ko[:same] == h["cell"][:same])
     print("FP32 form: fraction of slots with the oracle's cell after 20 steps:", agree)
     assert agree > 0.99
+
+
+def test_fp32_wald128_particle_error_by_index(run20):
+    """Per particle (matched by the loading index), after the 20 steps: the
+    position error in cells and the momentum error per covariant component
+    (relative to max(1, |u|) in the orthonormal components), away from and
+    within 0.05 rad of the polar axis."""
+    c = run20
+    oc, P = c["oc"], c["P"]
+    h = c["S"].host()
+    ig = (h["tag"] & 0x7FFFFFFF) >> 2
+    io = (P.tag & 0x7FFFFFFF) >> 2
+    common, a, b = np.intersect1d(ig, io, return_indices=True)
+    assert len(common) >= P.n - max(5, P.n // 10000)
+    x1g, x2g = fp32_logical(oc, h["cell"][a], h["x1"][a], h["x2"][a])
+    x1o, x2o = (np.log(P.r[b]) - math.log(oc.r_in)) / oc.dx1, P.th[b] / oc.dth
+    th = P.th[b]
+    r = P.r[b]
+    scale = [np.ones_like(r), r, r * np.abs(np.sin(th))]
+    uo = np.stack([getattr(P, k)[b] / sc for k, sc in zip(("u1", "u2", "u3"), scale)])
+    ug = np.stack([h[k][a].astype(np.float64) / sc for k, sc in zip(("u1", "u2", "u3"), scale)])
+    mag = np.maximum(1.0, np.linalg.norm(uo, axis=0))
+    near = np.minimum(th, math.pi - th) < 0.05
+    stats = {}
+    for name, sel in (("away", ~near), ("near", near)):
+        pos = np.maximum(np.abs(x1g - x1o), np.abs(x2g - x2o))[sel]
+        du = [np.abs(ug[k] - uo[k])[sel] / mag[sel] for k in range(3)]
+        stats[name] = (sel.sum(), pos.max(), np.percentile(pos, 99), [d.max() for d in du])
+        print(f"FP32 form after 20 steps, {name} ({sel.sum()} particles): position max {pos.max():.2e} "
+              f"p99 {np.percentile(pos, 99):.2e} cells; momentum max per component "
+              + " ".join(f"{d.max():.2e}" for d in du))
+    # measured: 2.7e-6 cells and 5.5e-7 away from the axis, 2.5e-6 cells and
+    # 5.1e-7 within 0.05 rad of it (FP32 atomics reorder the current sums
+    # from run to run, hence the margin)
+    for name in ("away", "near"):
+        n, pmax, p99, dumax = stats[name]
+        assert pmax < 2e-5 and max(dumax) < 1e-5, name
 
 
 def test_fp32_wald128_charge_conservation(run20):

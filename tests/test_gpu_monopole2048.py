@@ -96,13 +96,9 @@ def runs():
     out = {}
     # FP32 state first (from the same draw), then the FP64 one
     S32 = G.ParticleSet(g32, n)
-    x1 = (torch.log(gen["r"]) - math.log(RIN)) / g32.dx1
-    x2 = gen["th"] / g32.dth
-    i = torch.floor(x1).clamp(0, N - 1)
-    j = torch.floor(x2).clamp(0, N - 1)
-    S32.load((x1 - i).float(), (x2 - j).float(), gen["u1"].float(), gen["u2"].float(), gen["u3"].float(),
-             gen["tag"], (j * N + i).to(torch.int32))
-    del x1, x2, i, j
+    cell, o1, o2 = G.Context(g32).fp32_encode(gen["r"], gen["th"])
+    S32.load(o1, o2, gen["u1"].float(), gen["u2"].float(), gen["u3"].float(), gen["tag"], cell)
+    del cell, o1, o2
     S64 = G.ParticleSet(g64, n)
     S64.load(gen["r"], gen["th"], gen["u1"], gen["u2"], gen["u3"], gen["tag"])
     del gen

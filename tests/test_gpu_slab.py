@@ -19,7 +19,7 @@ import numpy as np
 import pytest
 
 import oracle as O
-from gpu_common import configs, relerr, axis_grazers
+from gpu_common import configs, relerr, axis_grazers, fp32_offsets
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -53,12 +53,8 @@ def case(n=20000, seed=5, precision=64):
 
 
 def fp32_state(oc, P):
-    x1 = (np.log(P.r) - math.log(oc.r_in)) / oc.dx1
-    x2 = P.th / oc.dth
-    i = np.clip(np.floor(x1), 0, oc.nr - 1)
-    j = np.clip(np.floor(x2), 0, oc.nth - 1)
-    return ((x1 - i).astype(np.float32), (x2 - j).astype(np.float32), P.u1.astype(np.float32),
-            P.u2.astype(np.float32), P.u3.astype(np.float32), P.tag, (j * oc.nr + i).astype(np.int32))
+    cell, o1, o2 = fp32_offsets(oc, P.r, P.th)
+    return (o1, o2, P.u1.astype(np.float32), P.u2.astype(np.float32), P.u3.astype(np.float32), P.tag, cell)
 
 
 def make_slabs(G, oc, gc, P):

@@ -69,19 +69,19 @@ def runs():
     # FP32 state from the FP64 one, in chunks (cell + offsets)
     a = S64.a
     chunk = 1 << 27
+    c32 = G.Context(g32)
     for s in range(0, n, chunk):
         e = min(n, s + chunk)
-        x1 = (torch.log(a.x1[s:e]) - math.log(rin)) / g32.dx1
-        x2 = a.x2[s:e] / g32.dth
-        i = torch.floor(x1).clamp(0, N - 1)
-        j = torch.floor(x2).clamp(0, N - 1)
-        S32.a.x1[s:e] = (x1 - i).float()
-        S32.a.x2[s:e] = (x2 - j).float()
+        cell, o1, o2 = c32.fp32_encode(a.x1[s:e], a.x2[s:e])
+        S32.a.x1[s:e] = o1
+        S32.a.x2[s:e] = o2
         S32.a.u1[s:e] = a.u1[s:e].float()
         S32.a.u2[s:e] = a.u2[s:e].float()
         S32.a.u3[s:e] = a.u3[s:e].float()
-        S32.a.cell[s:e] = (j * N + i).to(torch.int32)
+        S32.a.cell[s:e] = cell
         S32.a.tag[s:e] = a.tag[s:e]
+        del cell, o1, o2
+    del c32
     S32.n = n
     S32.count.fill_(n)
     S32._sc = S32._struct(S32.a)

@@ -55,13 +55,8 @@ def test_noalloc_sort_matches_context_sort_twice(G, precision, n_side, n):
             ref.load(*arrs)
             nal.load(*arrs)
         else:
-            x1 = (np.log(arrs[0] / cfg.r_in)) / cfg.dx1
-            x2 = arrs[1] / cfg.dth
-            i = np.clip(np.floor(x1), 0, cfg.n_r - 1)
-            j = np.clip(np.floor(x2), 0, cfg.n_theta - 1)
-            cell = (j * cfg.n_r + i).astype(np.int32)
-            st = [(x1 - i).astype(np.float32), (x2 - j).astype(np.float32)] + \
-                 [a.astype(np.float32) for a in arrs[2:5]] + [arrs[5], cell]
+            cell, o1, o2 = ctx.fp32_encode(torch.from_numpy(arrs[0]).cuda(), torch.from_numpy(arrs[1]).cuda())
+            st = [o1, o2] + [torch.from_numpy(a.astype(np.float32)) for a in arrs[2:5]] + [arrs[5], cell]
             ref.load(*st)
             nal.load(*st)
         ctx.sort(ref)
