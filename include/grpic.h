@@ -17,7 +17,8 @@
  * dx1 = ln(r_out/r_in)/n_r and dtheta = pi/n_theta.  Cell key = j*n_r + i.
  *
  * Field arrays (caller-owned device memory): every component is a row-major
- * array of (n_theta+1) rows and `ld` columns (ld >= n_r + 4), element type
+ * array of (n_theta+1) rows and `ld` columns (ld >= n_r + 4 and
+ * (n_theta+1) * ld < 2^31, the kernels' element offsets being 32-bit), element type
  * double (precision 64) or float (precision 32).  Row j is the theta index;
  * column c = i + 2 holds the r index i of the component's own lattice
  * (Fig. Yee): D^r, B^theta, J^r at (i+1/2, j); D^theta, B^r, J^theta at

@@ -20,6 +20,10 @@ INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-Xptxas", "-warn-spills"]
+# The FP32 push flushes subnormal floats to zero (magnitudes below 1.2e-38,
+# far under the FP32 form's error budget): its hardware reciprocals and
+# reciprocal square roots then take no rescaling of subnormal inputs.
+FILE_FLAGS = {"grpic_push32.cu": ["-ftz=true"]}
 
 
 def _nvcc():
@@ -45,7 +49,8 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
 
     def comp(so):
         s, o = so
-        cmd = [nvcc, *ARCH, *FLAGS, *extra, "-I", INCLUDE, "-c", s, "-o", o + ".tmp"]
+        cmd = [nvcc, *ARCH, *FLAGS, *FILE_FLAGS.get(os.path.basename(s), []), *extra, "-I", INCLUDE, "-c", s,
+               "-o", o + ".tmp"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed for {s}:\n{r.stderr}")

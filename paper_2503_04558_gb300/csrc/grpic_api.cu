@@ -70,6 +70,7 @@ cudaStream_t S(void *stream) { return (cudaStream_t)stream; }
 bool fields_ok(const grpic_ctx *ctx, const grpic_fields *f)
 {
     if (!f || f->ld < ctx->g.nr + 2 * NG) return false;
+    if ((int64_t)(ctx->g.nth + 1) * f->ld > INT32_MAX) return false;  // element offsets are 32-bit
     for (int k = 0; k < 3; ++k)
         if (!f->D[k] || !f->B[k] || !f->J[k]) return false;
     return true;

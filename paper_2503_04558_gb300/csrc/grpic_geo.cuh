@@ -139,76 +139,68 @@ __device__ __forceinline__ void geo_rhs_m(const KSGeo<M> &m, T eps, T ur, T ut, 
            h * (ur * ur * (T)m.dgrr_t + T(2) * ur * up * (T)m.dgrp_t + ut * ut * (T)m.dgtt_t + up * up * (T)m.dgpp_t);
 }
 
-// X^i, U_i of Eq. particle-eom from (r, sin theta, cos theta) without the
-// metric's derivatives as separate fields: gamma^{jk} = rho^-2 [(a^2 + r^2,
-// a, 1, 1/sin^2) in (rr, r phi, th th, phi phi)] - beta dr dr, so with
-// P = (a^2 + r^2) u_r^2 + 2 a u_r u_ph + u_th^2 + u_ph^2 / sin^2 the forms in u
-// collect into gamma^{jk} u_j u_k = P / rho^2 - beta u_r^2,
-// d_r gamma^{jk} u_j u_k = u_r^2 (z - d_r beta) - 2 r P / rho^4 and
-// d_th gamma^{jk} u_j u_k = -d_th rho^2 P / rho^4 - d_th beta u_r^2
-//                           - 2 sin cos u_ph^2 / (rho^2 sin^4)
-template <typename T>
-__device__ __forceinline__ void geo_rhs_direct(T a, T eps, T r, T s, T c, T ur, T ut, T up, RhsT<T> &f)
+// The FP32 form's right-hand side, split into the quantities of the point
+// (r, sin theta, cos theta) -- shared by the Boris step and the right-hand
+// side at x^n -- and the part that depends on u.  With
+//   P = (a^2 + r^2) u_r^2 + 2 a u_r u_ph + u_th^2 + u_ph^2 / sin^2,
+// gamma^{jk} u_j u_k = P / rho^2 - beta u_r^2 (gamma^{jk} of App. A), so that
+// with Q = eps + gamma^{jk} u_j u_k: alpha u^0 = sqrt(Q), 1/u^0 = alpha / sqrt(Q).
+// The force terms of Eq. particle-eom collect, with h = 1 / (2 u^0),
+// d_r z = 2/rho^2 - z^2 and d_th z = -z E (E = d_th rho^2 / rho^2), as
+//   -alpha u^0 d_i alpha + u_r d_i beta^r + h u_r^2 d_i beta^r = K d_i z,
+//   K = (1+z)^-1 (h Q + (1+z)^-1 u_r (1 + h u_r))
+// (alpha^2 = (1+z)^-1, d_i alpha = -alpha^3 d_i z / 2, d_i beta^r =
+// (1+z)^-2 d_i z), and the remaining derivatives of P / rho^2 give
+//   U_r  = K d_r z + h z (P / rho^2 - u_r^2),
+//   U_th = E (h P / rho^2 - K z) + (1/u^0) rho^-2 sin cos sin^-4 u_ph^2
+// (d_th sin^-2 = -2 sin cos / sin^4).  Reciprocals and reciprocal square
+// roots take the hardware approximations (a few ulp, inside the FP32 form's
+// budget); 1/(1+z) lies in (0, 1].
+struct Pt32 {
+    float s, rho2, ir, z, opz, al, iopz, beta, s2, is2, ar2, cs, E;
+};
+
+__device__ __forceinline__ Pt32 point32(float a2, float m2a2, float r, float s, float c)
 {
-    const T a2 = a * a, r2 = r * r;
-    const T ir = rcp_t(r2 + a2 * c * c);
-    const T ir2 = ir * ir;
-    const T z = T(2) * r * ir;
-    const T iopz = rcp_t(T(1) + z);
-    const T alpha = sqrt_t(iopz);
-    const T beta = z * iopz;
-    const T is2 = rcp_t(s * s);
-    const T drho_t = T(-2) * a2 * c * s;
-    const T dz_r = T(2) * ir * (T(1) - T(2) * r2 * ir);
-    const T dz_t = T(-2) * r * drho_t * ir2;
-    const T ka = T(-0.5) * alpha * iopz, kb = iopz * iopz;
-    const T db_r = kb * dz_r, db_t = kb * dz_t;
-    const T ur2 = ur * ur, up2 = up * up;
-    const T P = (a2 + r2) * ur2 + T(2) * a * ur * up + ut * ut + up2 * is2;
-    const T au0 = sqrt_t(eps + ir * P - beta * ur2);  // alpha u^0
-    const T iu0 = alpha * rcp_t(au0);
-    const T grp = a * ir;
-    f.xr = (((a2 + r2) * ir - beta) * ur + grp * up) * iu0 - beta;
-    f.xt = ir * ut * iu0;
-    f.xp = (grp * ur + ir * is2 * up) * iu0;
-    const T h = T(0.5) * iu0;
-    f.ur = -au0 * ka * dz_r + ur * db_r - h * (ur2 * (z - db_r) - T(2) * r * ir2 * P);
-    f.ut = -au0 * ka * dz_t + ur * db_t - h * (-drho_t * ir2 * P - db_t * ur2 - T(2) * s * c * ir * is2 * is2 * up2);
+    Pt32 m;
+    const float r2 = r * r;
+    m.s = s;
+    m.rho2 = fmaf(a2 * c, c, r2);
+    m.ir = __fdividef(1.0f, m.rho2);
+    m.z = (r + r) * m.ir;
+    m.opz = 1.0f + m.z;
+    m.al = rsqrtf(m.opz);
+    m.iopz = m.al * m.al;
+    m.beta = m.z * m.iopz;
+    m.s2 = s * s;
+    m.is2 = __fdividef(1.0f, m.s2);
+    m.ar2 = a2 + r2;
+    m.cs = c * s;
+    m.E = m2a2 * m.cs * m.ir;  // m2a2 = -2 a^2
+    return m;
 }
 
-// The same right-hand side in FP32 with a^2 given and the products ordered
-// for fused multiply-adds; 1/(1+z) lies in (0, 1], so alpha takes the
-// hardware reciprocal square root without a range test.
-__device__ __forceinline__ void geo_rhs_direct32(float a, float a2, float eps, float r, float s, float c, float ur,
-                                                 float ut, float up, RhsT<float> &f)
+// aup = a u_ph (u_ph is fixed during the correctors)
+__device__ __forceinline__ void rhs32(const Pt32 &m, float a, float eps, float ur, float ut, float up, float aup,
+                                      RhsT<float> &f)
 {
-    const float r2 = r * r;
-    const float ir = __fdividef(1.0f, fmaf(a2 * c, c, r2));
-    const float ir2 = ir * ir;
-    const float z = (r + r) * ir;
-    const float iopz = __fdividef(1.0f, 1.0f + z);
-    const float alpha = iopz * rsqrtf(iopz);
-    const float beta = z * iopz;
-    const float is2 = __fdividef(1.0f, s * s);
-    const float drho_t = -2.0f * a2 * (c * s);
-    const float dz_r = (ir + ir) * fmaf(-2.0f * r2, ir, 1.0f);
-    const float dz_t = -2.0f * r * drho_t * ir2;
-    const float kb = iopz * iopz;
-    const float db_r = kb * dz_r, db_t = kb * dz_t;
-    const float ur2 = ur * ur, up2 = up * up;
-    const float ar2 = a2 + r2;
-    const float P = fmaf(ar2, ur2, fmaf((a + a) * ur, up, fmaf(ut, ut, up2 * is2)));
-    const float au0 = sqrt_t(fmaf(ir, P, fmaf(-beta, ur2, eps)));  // alpha u^0
-    const float iu0 = alpha * __fdividef(1.0f, au0);
-    const float grp = a * ir;
-    f.xr = fmaf(fmaf(fmaf(ar2, ir, -beta), ur, grp * up), iu0, -beta);
-    f.xt = ir * ut * iu0;
-    f.xp = fmaf(grp, ur, ir * is2 * up) * iu0;
+    const float ur2 = ur * ur;
+    const float is2up = m.is2 * up;
+    const float is2up2 = is2up * up;
+    const float w = fmaf(m.ar2, ur, aup);                          // (a^2 + r^2) u_r + a u_ph
+    const float P = fmaf(ur, w + aup, fmaf(ut, ut, is2up2));
+    const float irP = m.ir * P;
+    const float Q = fmaf(m.ir, P, fmaf(-m.beta, ur2, eps));
+    const float qq = rsqrtf(Q);
+    const float iu0 = m.al * qq;                                   // 1 / u^0
     const float h = 0.5f * iu0;
-    // -alpha u^0 d alpha = alpha u^0 (alpha / (2 (1+z))) dz
-    const float kad = 0.5f * alpha * iopz * au0;
-    f.ur = fmaf(kad, dz_r, fmaf(ur, db_r, -h * fmaf(ur2, z - db_r, -2.0f * r * ir2 * P)));
-    f.ut = fmaf(kad, dz_t, fmaf(ur, db_t, h * fmaf(drho_t * ir2, P, fmaf(db_t, ur2, 2.0f * s * c * ir * is2 * is2 * up2))));
+    const float iri = m.ir * iu0;
+    f.xr = fmaf(iu0, fmaf(m.ir, w, -m.beta * ur), -m.beta);
+    f.xt = iri * ut;
+    f.xp = iri * fmaf(a, ur, is2up);
+    const float K = m.iopz * fmaf(m.iopz * ur, fmaf(h, ur, 1.0f), h * Q);
+    f.ur = fmaf(K, fmaf(-m.z, m.z, m.ir + m.ir), h * m.z * (irP - ur2));
+    f.ut = fmaf(m.E, fmaf(-K, m.z, h * irP), iri * (m.cs * m.is2) * is2up2);
 }
 
 }  // namespace grpic

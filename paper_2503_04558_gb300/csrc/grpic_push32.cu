@@ -44,7 +44,7 @@ struct Push32Args {
     int i64;  // first column whose inner edge is at or beyond fp64_radius
     int island_fp64;   // 1: native FP64 island, 0: double-FP32 pairs
     int use_tol;       // convergence test of the correctors
-    float af, a2f, dthf, idthf, dx1f, idx1f;  // a, a^2, dtheta, 1/dtheta, dx1, 1/dx1 in FP32
+    float af, a2f, m2a2f, dthf, idthf, dx1f, idx1f;  // a, a^2, -2 a^2, dtheta, 1/dtheta, dx1, 1/dx1 in FP32
     df a_df, a2_df, dth_df;       // a, a^2, dtheta as float pairs
     const float *rcol2;  // r_i as (hi, lo) float pairs, index i + NG
     const float *rowsc;  // sin, cos theta_j as float pairs, index j
@@ -69,11 +69,11 @@ struct Push32Args {
     const float *D0, *D1, *D2, *B0, *B1, *B2;
     float *J0, *J1, *J2;
     int64_t ld;
+    int ldi;  // ld as the 32-bit stride of the element offsets ((n_theta+1) ld < 2^31)
     const double *rcol;  // r at integer columns, index i + NG
     int32_t *keys;
     int32_t *count;
     int histogram;
-    int pusher;  // 0 generalized Boris, 1 Vay in the FIDO frame
     int *status;
     unsigned long long nr_recip;  // floor(2^64 / n_r) + 1
 };
@@ -155,13 +155,13 @@ __device__ __forceinline__ float log1p_cell(float y)
 }
 
 struct St32 {
-    int c0, r0, r1;
-    float w00, w10, w01, w11, p0, p1;
+    int o0, o1;           // element offsets of the stencil's two rows at its first column
+    float f, gg, p0, p1;  // fractional offsets along r and theta; the rows' parities
 };
 
 // bilinear stencil from cell (i, j) and offsets; half_r / half_t stagger
-__device__ __forceinline__ void stencil32(const GridDev &g, int i, int j, float o1, float o2, bool half_r, bool half_t,
-                                          float par, St32 &S)
+__device__ __forceinline__ void stencil32(const GridDev &g, int ld, int i, int j, float o1, float o2, bool half_r,
+                                          bool half_t, float par, St32 &S)
 {
     int is = i;
     float f = o1;
@@ -172,41 +172,56 @@ __device__ __forceinline__ void stencil32(const GridDev &g, int i, int j, float 
     int js = j;
     float gg = o2;
     S.p0 = S.p1 = 1.0f;
+    int r0 = js, r1 = js + 1;
     if (half_t) {
         gg = o2 - 0.5f;
         if (gg < 0.0f) { gg += 1.0f; js = j - 1; }
-        S.r0 = js;
-        S.r1 = js + 1;
-        if (S.r0 < 0) { S.r0 = -1 - S.r0; S.p0 = par; }
-        if (S.r1 > g.nth - 1) { S.r1 = 2 * g.nth - 1 - S.r1; S.p1 = par; }
-    } else {
-        S.r0 = js;
-        S.r1 = js + 1;
+        r0 = js;
+        r1 = js + 1;
+        if (r0 < 0) { r0 = -1 - r0; S.p0 = par; }
+        if (r1 > g.nth - 1) { r1 = 2 * g.nth - 1 - r1; S.p1 = par; }
     }
-    S.c0 = is + NG;
-    S.w00 = (1.0f - f) * (1.0f - gg);
-    S.w10 = f * (1.0f - gg);
-    S.w01 = (1.0f - f) * gg;
-    S.w11 = f * gg;
+    S.o0 = r0 * ld + is + NG;
+    S.o1 = r1 * ld + is + NG;
+    S.f = f;
+    S.gg = gg;
 }
 
-// the bilinear sum of one component; a reflected row's parity is folded into
-// the weights by the caller (flip_rows)
-__device__ __forceinline__ float gather32(const float *__restrict__ F, int64_t ld, const St32 &S)
+// the bilinear value of one component: along r on both rows, then along
+// theta; ODD applies the rows' parities (a component odd across the axis)
+template <bool ODD = false>
+__device__ __forceinline__ float gather32(const float *__restrict__ F, const St32 &S)
 {
-    const float *a = F + (size_t)S.r0 * ld + S.c0;
-    const float *b = F + (size_t)S.r1 * ld + S.c0;
-    return fmaf(S.w00, __ldg(a), fmaf(S.w10, __ldg(a + 1), fmaf(S.w01, __ldg(b), S.w11 * __ldg(b + 1))));
+    const float *a = F + S.o0;
+    const float *b = F + S.o1;
+    const float a0 = __ldg(a), a1 = __ldg(a + 1), b0 = __ldg(b), b1 = __ldg(b + 1);
+    float x = fmaf(S.f, a1 - a0, a0), y = fmaf(S.f, b1 - b0, b0);
+    if (ODD) {
+        x *= S.p0;
+        y *= S.p1;
+    }
+    return fmaf(S.gg, y - x, x);
 }
 
-// the weights of a stencil whose rows carry the parities p0, p1
-__device__ __forceinline__ St32 flip_rows(St32 S)
+// the six field components at the particle (Fig. Yee staggering): D^r and
+// B^theta at (i+1/2, j), D^theta and B^r at (i, j+1/2), D^phi at (i, j),
+// B^phi at (i+1/2, j+1/2); across the polar axis D^theta is odd, B^r and
+// B^phi even (the half-r stencils reflect no row)
+__device__ __forceinline__ void gather_fields32(const Push32Args &A, int i, int j, float o1, float o2, float Dv[3],
+                                                float Bv[3])
 {
-    S.w00 *= S.p0;
-    S.w10 *= S.p0;
-    S.w01 *= S.p1;
-    S.w11 *= S.p1;
-    return S;
+    St32 Sh0, S0h, S00, Shh;
+    const int ld = A.ldi;
+    stencil32(A.g, ld, i, j, o1, o2, true, false, 1.0f, Sh0);
+    stencil32(A.g, ld, i, j, o1, o2, false, true, -1.0f, S0h);
+    stencil32(A.g, ld, i, j, o1, o2, false, false, 1.0f, S00);
+    stencil32(A.g, ld, i, j, o1, o2, true, true, 1.0f, Shh);
+    Dv[0] = gather32(A.D0, Sh0);
+    Dv[1] = gather32<true>(A.D1, S0h);
+    Dv[2] = gather32(A.D2, S00);
+    Bv[1] = gather32(A.B1, Sh0);
+    Bv[2] = gather32(A.B2, Shh);
+    Bv[0] = gather32(A.B0, S0h);
 }
 
 // generalized Boris step in FP32 with the metric of type M at x^n (the lower
@@ -239,32 +254,6 @@ __device__ __forceinline__ void boris_geo(const KSGeo<M> &m, M a, M r, M s, floa
     } else {
         boris32<float>(mm, qm, dt, D, B, u);
     }
-}
-
-// the metric values of the Boris step in FP32 at (r, sin, cos): alpha,
-// gamma_ij, gamma^ij and sqrt(gamma) (App. A), without the derivatives (the
-// right-hand side at x^n takes geo_rhs_direct like the correctors)
-__device__ __forceinline__ void ks_point_boris32(float a, float a2, float r, float s, float c, KSPoint<float> &m)
-{
-    const float r2 = r * r, s2 = s * s;
-    const float rho2 = fmaf(a2 * c, c, r2);
-    const float ir = __fdividef(1.0f, rho2);
-    const float z = (r + r) * ir;
-    const float opz = 1.0f + z;
-    const float iopz = __fdividef(1.0f, opz);
-    const float ra = r2 + a2;
-    const float Dl = ra - (r + r);
-    const float Sg = fmaf(ra, ra, -a2 * Dl * s2);
-    m.alpha = iopz * rsqrtf(iopz);  // iopz in (0, 1]
-    m.g_rr = opz;
-    m.g_tt = rho2;
-    m.g_pp = Sg * s2 * ir;
-    m.g_rp = -a * s2 * opz;
-    m.gi_rr = fmaf(ra, ir, -z * iopz);
-    m.gi_rp = a * ir;
-    m.gi_tt = ir;
-    m.gi_pp = __fdividef(ir, s2);
-    m.sqrtg = rho2 * s * opz * m.alpha;  // rho^2 sin sqrt(1+z), sqrt(1+z) = (1+z) alpha
 }
 
 // The metric of the near-horizon island in double-FP32 pairs: alpha, beta,
@@ -355,12 +344,14 @@ __device__ __forceinline__ void boris_island(const KSGeo<float> &m, const Island
     }
 }
 
-// o2 is the offset from the row's lower edge (stencils and window); in the
-// last row (pole) the particle's theta offset is q = (pi - theta) / dtheta,
-// stored with FP32's relative precision, and the trapezoid integrates q
-// there (dq/dt = -X^theta / dtheta): on return q (pole) or o2 hold the end
-// point's offset in that row's variable
-template <typename M>
+// The push of one particle of the near-horizon island (M = df: the metric in
+// double-FP32 pairs, M = double: in FP64).  o2 is the offset from the row's
+// lower edge (stencils and window); in the last row (pole) the particle's
+// theta offset is q = (pi - theta) / dtheta, stored with FP32's relative
+// precision, and the trapezoid integrates q there (dq/dt = -X^theta /
+// dtheta): on return q (pole) or o2 hold the end point's offset in that
+// row's variable
+template <typename M, int PUSHER>
 __device__ __forceinline__ void push_one(const Push32Args &A, int i, int j, float &o1, float &o2, float u[3], int sp,
                                          float &dphi, bool pole, float &q)
 {
@@ -380,70 +371,35 @@ __device__ __forceinline__ void push_one(const Push32Args &A, int i, int j, floa
             sincos((double)g.nth * g.dth - (double)q * g.dth, &s0, &c0);
         else
             sincos(((double)j + (double)o2) * g.dth, &s0, &c0);
-    } else if constexpr (IS_DF) {
+    } else {
         am = A.a_df;
         r0 = df(rc2.x, rc2.y) + df(d0);
         const float4 sc = __ldg(reinterpret_cast<const float4 *>(A.rowsc) + (pole ? 0 : j));
         sincos_shift_df(df(sc.x, sc.y), df(sc.z, sc.w), mul(A.dth_df, pole ? q : o2), s0, c0);
         if (pole) c0 = -c0;
-    } else {
-        // sin, cos of theta_j (row table) shifted by o2 dtheta (|shift| <= one
-        // cell: the series of sincos_shift is exact to FP32 rounding there)
-        am = A.af;
-        r0 = rcf + d0;
-        const float4 sc = __ldg(reinterpret_cast<const float4 *>(A.rowsc) + (pole ? 0 : j));
-        sincos_shift<float>(sc.x, sc.z, (pole ? q : o2) * A.dthf, s0, c0);
-        if (pole) c0 = -c0;
     }
-    // the island's metric comes as FP32 values rounded from pairs; the FP32
-    // path forms only the Boris step's metric values here
-    constexpr bool IS_F = std::is_same<M, float>::value;
+    // the pair island's metric comes as FP32 values rounded from pairs
     using MG = typename std::conditional<IS_DF, float, M>::type;
     KSGeo<MG> m;
     IslandKeep keep;
     if constexpr (IS_DF)
         ks_geo_island(am, A.a2_df, r0, s0, c0, m, &keep);
-    else if constexpr (!IS_F)
+    else
         ks_geo_sc<M>(am, r0, s0, c0, m);
     if (A.massive[sp] && A.qm[sp] != 0.0f) {
-        St32 Sh0, S0h, S00, Shh;
-        stencil32(g, i, j, o1, o2, true, false, 1.0f, Sh0);
-        stencil32(g, i, j, o1, o2, false, true, -1.0f, S0h);
-        stencil32(g, i, j, o1, o2, false, false, 1.0f, S00);
-        stencil32(g, i, j, o1, o2, true, true, 1.0f, Shh);
-        // parities across the polar axis: D^theta odd (-1 on a reflected row),
-        // B^r and B^phi even; Sh0 and S00 reflect no row
         float Dv[3], Bv[3];
-        Dv[0] = gather32(A.D0, A.ld, Sh0);
-        Dv[1] = gather32(A.D1, A.ld, flip_rows(S0h));
-        Dv[2] = gather32(A.D2, A.ld, S00);
-        Bv[1] = gather32(A.B1, A.ld, Sh0);
-        Bv[2] = gather32(A.B2, A.ld, Shh);
-        Bv[0] = gather32(A.B0, A.ld, S0h);
+        gather_fields32(A, i, j, o1, o2, Dv, Bv);
         if constexpr (IS_DF) {
-            boris_island(m, keep, am, A.a2_df, r0, s0, A.qm[sp], A.dt, Dv, Bv, u, A.pusher);
-        } else if constexpr (IS_F) {
-            KSPoint<float> mm;
-            ks_point_boris32(am, A.a2f, r0, s0, c0, mm);
-            if (A.pusher) {
-                const VayMetric<float> vm{mm.alpha, mm.g_rr, mm.g_rp, mm.g_tt, mm.g_pp, mm.gi_rr, mm.gi_rp, mm.gi_tt,
-                                          mm.gi_pp, mm.sqrtg};
-                vay_step<float>(vm, A.qm[sp], A.dt, Dv, Bv, u);
-            } else {
-                boris32<float>(mm, A.qm[sp], A.dt, Dv, Bv, u);
-            }
+            boris_island(m, keep, am, A.a2_df, r0, s0, A.qm[sp], A.dt, Dv, Bv, u, PUSHER);
         } else {
-            boris_geo<M>(m, am, r0, s0, A.qm[sp], A.dt, Dv, Bv, u, A.pusher);
+            boris_geo<M>(m, am, r0, s0, A.qm[sp], A.dt, Dv, Bv, u, PUSHER);
         }
     }
     const float eps = A.massive[sp] ? 1.0f : 0.0f;
     const float dt = A.dt, h = 0.5f * dt;
     const float idth = A.idthf;
     RhsT<float> f0, ft;
-    if constexpr (IS_F)
-        geo_rhs_direct32(am, A.a2f, eps, r0, s0, c0, u[0], u[1], u[2], f0);
-    else
-        geo_rhs_m<MG, float>(m, eps, u[0], u[1], u[2], f0);
+    geo_rhs_m<MG, float>(m, eps, u[0], u[1], u[2], f0);
     f0.xt *= idth;
     // the theta offset integrated: o2 (X^theta / dtheta), or q in the pole
     // row (-X^theta / dtheta); sg is the sign and t0 the start value
@@ -461,7 +417,7 @@ __device__ __forceinline__ void push_one(const Push32Args &A, int i, int j, floa
             else
                 sincos(((double)j + (double)o2) * g.dth + d, &s, &c);
             ri = A.rcol[i + NG] + (double)a1;
-        } else if constexpr (IS_DF) {
+        } else {
             df d = two_sum(a2, -t0) * A.dth_df;
             if (fabs_hi(d) <= 0.1f) {
                 sincos_shift_df(s0, pole ? -c0 : c0, d, s, c);
@@ -471,18 +427,8 @@ __device__ __forceinline__ void push_one(const Push32Args &A, int i, int j, floa
             }
             if (pole) c = -c;
             ri = df(rc2.x, rc2.y) + df(a1);
-        } else {
-            float d = (a2 - t0) * A.dthf;
-            if (fabsf(d) <= 0.05f)
-                sincos_shift<float>(s0, pole ? -c0 : c0, d, s, c);
-            else
-                sincosf(((float)(pole ? 0 : j) + t0) * A.dthf + d, &s, &c);
-            if (pole) c = -c;
-            ri = rcf + a1;
         }
-        if constexpr (std::is_same<M, float>::value) {
-            geo_rhs_direct32(am, A.a2f, eps, ri, s, c, b1, b2, u[2], ft);
-        } else if constexpr (IS_DF) {
+        if constexpr (IS_DF) {
             KSGeo<float> mi;
             ks_geo_island(am, A.a2_df, ri, s, c, mi, nullptr);
             geo_rhs_m<float, float>(mi, eps, b1, b2, u[2], ft);
@@ -523,18 +469,130 @@ __device__ __forceinline__ void push_one(const Push32Args &A, int i, int j, floa
     dphi = ap;
 }
 
+// generalized Boris step in FP32 from the point quantities at x^n: the lower
+// metric gamma_rr = 1 + z, gamma_thth = rho^2, gamma_rph = -a sin^2 (1 + z),
+// gamma_phph = Sigma sin^2 / rho^2 with Sigma = (a^2 + r^2) rho^2 + 2 r a^2
+// sin^2 (the same Sigma as (a^2 + r^2)^2 - a^2 Delta sin^2, without its
+// cancellation), so gamma_phph = sin^2 (a^2 + r^2 + z a^2 sin^2); the upper
+// metric of App. A and sqrt(gamma) = rho^2 sin sqrt(1 + z) = rho^2 sin (1 + z) alpha
+__device__ __forceinline__ void boris_pt32(const Pt32 &m, float a, float a2, float qm, float dt, const float D[3],
+                                           const float B[3], float u[3], int pusher)
+{
+    KSPoint<float> mm;
+    mm.alpha = m.al;
+    mm.g_rr = m.opz;
+    mm.g_tt = m.rho2;
+    mm.g_pp = m.s2 * fmaf(m.z, a2 * m.s2, m.ar2);
+    mm.g_rp = -a * m.s2 * m.opz;
+    mm.gi_rr = fmaf(m.ar2, m.ir, -m.beta);
+    mm.gi_rp = a * m.ir;
+    mm.gi_tt = m.ir;
+    mm.gi_pp = m.ir * m.is2;
+    mm.sqrtg = m.rho2 * m.s * m.opz * m.al;
+    if (pusher) {
+        const VayMetric<float> vm{mm.alpha, mm.g_rr, mm.g_rp, mm.g_tt, mm.g_pp, mm.gi_rr, mm.gi_rp, mm.gi_tt,
+                                  mm.gi_pp, mm.sqrtg};
+        vay_step<float>(vm, qm, dt, D, B, u);
+    } else {
+        boris32<float>(mm, qm, dt, D, B, u);
+    }
+}
+
+// The push of one particle in FP32 (cells at or beyond fp64_radius): the
+// point quantities at x^n serve the Boris step and the first right-hand
+// side; sin and cos at the iterates from those at theta^n by the short
+// series of sincos_shift (|shift| <= one cell).  Offsets and the pole row as
+// in push_one; here sin, cos are those of theta itself (in the pole row cos
+// theta = -cos theta' from the table of theta' = pi - theta), and the shift of
+// theta per unit change of the integrated offset is +dtheta, or -dtheta in the
+// pole row.
+template <int PUSHER>
+__device__ __forceinline__ void push_fp32(const Push32Args &A, int i, int j, float &o1, float &o2, float u[3], int sp,
+                                          float &dphi, bool pole, float &q)
+{
+    const float2 rc2 = __ldg(reinterpret_cast<const float2 *>(A.rcol2) + i + NG);
+    const float rcf = __fadd_rn(rc2.x, rc2.y);
+    const float d0 = rcf * expm1_cell(o1 * A.dx1f, A.dx1f);  // r - r_i
+    const float a = A.af;
+    const float t0 = pole ? q : o2;  // the integrated theta offset at x^n
+    const float4 sc = __ldg(reinterpret_cast<const float4 *>(A.rowsc) + (pole ? 0 : j));
+    float s0, c0;
+    sincos_shift<float>(sc.x, sc.z, t0 * A.dthf, s0, c0);
+    if (pole) c0 = -c0;
+    const Pt32 m0 = point32(A.a2f, A.m2a2f, rcf + d0, s0, c0);
+    if (A.massive[sp] && A.qm[sp] != 0.0f) {
+        float Dv[3], Bv[3];
+        gather_fields32(A, i, j, o1, o2, Dv, Bv);
+        boris_pt32(m0, a, A.a2f, A.qm[sp], A.dt, Dv, Bv, u, PUSHER);
+    }
+    const float eps = A.massive[sp] ? 1.0f : 0.0f;
+    const float dt = A.dt, h = 0.5f * dt;
+    const float up = u[2], aup = a * up;
+    RhsT<float> f0, ft;
+    rhs32(m0, a, eps, u[0], u[1], up, aup, f0);
+    // d(offset)/dt = sth X^theta; d theta = dsg d(offset)
+    const float sth = pole ? -A.idthf : A.idthf, dsg = pole ? -A.dthf : A.dthf;
+    const float hsth = h * sth;
+    float a1 = fmaf(dt, f0.xr, d0), a2 = fmaf(dt * sth, f0.xt, t0);
+    float b1 = fmaf(dt, f0.ur, u[0]), b2 = fmaf(dt, f0.ut, u[1]);
+    float xpl = f0.xp;  // X^phi at the last evaluated iterate
+    const float trc = A.tolf * rcf;
+    for (int it = 0; it < A.n_iter; ++it) {
+        const float d = (a2 - t0) * dsg;  // theta - theta^n
+        float s, c;
+        if (fabsf(d) <= 0.05f) {
+            sincos_shift<float>(s0, c0, d, s, c);
+        } else if (pole) {
+            sincosf(t0 * A.dthf - d, &s, &c);  // theta' = pi - theta
+            c = -c;
+        } else {
+            sincosf(((float)j + t0) * A.dthf + d, &s, &c);
+        }
+        const Pt32 mi = point32(A.a2f, A.m2a2f, rcf + a1, s, c);
+        rhs32(mi, a, eps, b1, b2, up, aup, ft);
+        xpl = ft.xp;
+        const float n1 = fmaf(h, ft.xr + f0.xr, d0), n2 = fmaf(hsth, ft.xt + f0.xt, t0);
+        const float nb1 = fmaf(h, ft.ur + f0.ur, u[0]), nb2 = fmaf(h, ft.ut + f0.ut, u[1]);
+        bool done = false;
+        if (A.use_tol) {
+            // the convergence test of push_one: change of the iterate relative
+            // to r_i, one theta cell and max(1, |u|)
+            const float t = A.tolf;
+            done = fabsf(n1 - a1) < trc && fabsf(n2 - a2) < t && fabsf(nb1 - b1) < t * fmaxf(1.0f, fabsf(nb1)) &&
+                   fabsf(nb2 - b2) < t * fmaxf(1.0f, fabsf(nb2));
+        }
+        a1 = n1;
+        a2 = n2;
+        b1 = nb1;
+        b2 = nb2;
+        if (done) break;
+    }
+    o1 = log1p_cell(__fdividef(a1, rcf)) * A.idx1f;  // back to the logical offset
+    if (pole)
+        q = a2;
+    else
+        o2 = a2;
+    u[0] = b1;
+    u[1] = b2;
+    dphi = h * (xpl + f0.xp);  // dt X^phi(x^n) without correctors
+}
+
 // resident 256-thread blocks per SM the register allocation is sized for
 #ifndef GRPIC_PUSH32_MINB
 #define GRPIC_PUSH32_MINB 4
 #endif
 
+// PUSHER: 0 generalized Boris, 1 Vay in the FIDO frame; IX: the slot index
+// type (uint32_t while the capacity is below 2^31, int64_t beyond)
+template <int PUSHER, typename IX>
 __global__ void __launch_bounds__(256, GRPIC_PUSH32_MINB) push32_kernel(Push32Args A)
 {
     const GridDev &g = A.g;
     const bool permuted = A.perm != nullptr;
     int64_t n = permuted ? (int64_t)*A.live : (A.d_count ? *A.d_count : A.n);
     if (n > A.n) n = A.n;
-    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const IX nx = (IX)n;
+    const IX p = (IX)blockIdx.x * blockDim.x + threadIdx.x;
     const unsigned FULL = 0xffffffffu;
     int lane = threadIdx.x & 31;
     int ncell = g.nr * g.nth;
@@ -544,8 +602,8 @@ __global__ void __launch_bounds__(256, GRPIC_PUSH32_MINB) push32_kernel(Push32Ar
     uint32_t tag = DEAD;
     int i = 0, j = 0, cellk = 0;
     float o1 = 0, o2 = 0, x2in = 0, u[3] = {0, 0, 0};
-    if (p < n) {
-        const int64_t src = permuted ? (int64_t)A.perm[p] : p;
+    if (p < nx) {
+        const IX src = permuted ? (IX)A.perm[p] : p;
         tag = A.in_tag[src];
         if (!(tag & DEAD)) {
             cellk = A.in_cell[src];
@@ -584,11 +642,11 @@ __global__ void __launch_bounds__(256, GRPIC_PUSH32_MINB) push32_kernel(Push32Ar
         float q = x2in;
         // FP64 island: cells whose inner edge r_i lies below fp64_radius
         if (i >= A.i64)
-            push_one<float>(A, i, j, n1, n2, u, sp, dphi, pole, q);
+            push_fp32<PUSHER>(A, i, j, n1, n2, u, sp, dphi, pole, q);
         else if (A.island_fp64)
-            push_one<double>(A, i, j, n1, n2, u, sp, dphi, pole, q);
+            push_one<double, PUSHER>(A, i, j, n1, n2, u, sp, dphi, pole, q);
         else
-            push_one<df>(A, i, j, n1, n2, u, sp, dphi, pole, q);
+            push_one<df, PUSHER>(A, i, j, n1, n2, u, sp, dphi, pole, q);
         // axis reflection (theta = 0 is o2 = 0 of row 0, theta = pi is q = 0
         // of the last row); the end point relative to the start row's lower edge
         if (j == 0 && n2 < 0.0f) { n2 = -n2; u[1] = -u[1]; }
@@ -636,7 +694,7 @@ __global__ void __launch_bounds__(256, GRPIC_PUSH32_MINB) push32_kernel(Push32Ar
             }
         }
     }
-    if (p < n) {
+    if (p < nx) {
         if (moved || permuted) {
             A.cell[p] = nj * g.nr + ni;
             A.o1[p] = n1;
@@ -648,7 +706,7 @@ __global__ void __launch_bounds__(256, GRPIC_PUSH32_MINB) push32_kernel(Push32Ar
         if (tag & DEAD) key = ncell;
         A.tag[p] = tag;
         A.keys[p] = key;
-    } else if (permuted && p < A.n) {
+    } else if (permuted && p < (IX)A.n) {
         A.tag[p] = DEAD;  // past the live slots of the permuted order
     }
 
@@ -656,7 +714,7 @@ __global__ void __launch_bounds__(256, GRPIC_PUSH32_MINB) push32_kernel(Push32Ar
         // old cell = start cell (the slot's segment of the permuted order);
         // lanes match on cell * 9 + direction (32-bit: the cells of one warp
         // lie far closer together than 2^32 / 9)
-        const bool counted = p < n && moved && !(tag & DEAD);
+        const bool counted = p < nx && moved && !(tag & DEAD);
         const int dir = (nj - j + 1) * 3 + (ni - i + 1);
         const unsigned mk = counted ? (unsigned)cellk * 9u + (unsigned)dir : 0xffffffffu;
         const unsigned peers = __match_any_sync(FULL, mk);
@@ -664,14 +722,14 @@ __global__ void __launch_bounds__(256, GRPIC_PUSH32_MINB) push32_kernel(Push32Ar
     }
 
     if (A.histogram) {
-        int hk = (p < n) ? key : -1;
+        int hk = (p < nx) ? key : -1;
         unsigned peers = __match_any_sync(FULL, hk);
         if (hk >= 0 && lane == __ffs(peers) - 1) atomicAdd(A.count + hk, __popc(peers));
     }
 
     // ---- deposit: lanes grouped by start cell, each group reduce-scattered --
     deposit_warp_split<float, 3>(dep, i, j, g.nr, wa1, wa2, wb1, wb2, wq * A.m_i2dt, wq * A.idt, wphi, lane, g.nth,
-                                 NG, A.ld, A.J0,
+                                 NG, A.ldi, A.J0,
                                  A.J1, A.J2);
 }
 
@@ -697,6 +755,7 @@ cudaError_t launch_push32(grpic_ctx *ctx, const grpic_particles *in, grpic_parti
     A.use_tol = ctx->prm.push_tol > 0.0 ? 1 : 0;
     A.af = (float)ctx->g.a;
     A.a2f = (float)(ctx->g.a * ctx->g.a);
+    A.m2a2f = (float)(-2.0 * ctx->g.a * ctx->g.a);
     A.dthf = (float)ctx->g.dth;
     A.idthf = (float)(1.0 / ctx->g.dth);
     A.dx1f = (float)ctx->g.dx1;
@@ -739,15 +798,27 @@ cudaError_t launch_push32(grpic_ctx *ctx, const grpic_particles *in, grpic_parti
     A.J1 = (float *)f->J[1];
     A.J2 = (float *)f->J[2];
     A.ld = f->ld;
+    A.ldi = (int)f->ld;
     A.rcol = ctx->rcol;
     A.keys = ctx->d_keys;
     A.count = ctx->d_count;
     A.histogram = histogram ? 1 : 0;
-    A.pusher = ctx->prm.pusher;
     A.status = ctx->d_status;
     A.nr_recip = ~0ull / (unsigned long long)ctx->g.nr + 1ull;
     if (p->n <= 0) return cudaSuccess;
-    push32_kernel<<<(unsigned)((p->n + 255) / 256), 256, 0, s>>>(A);
+    const unsigned blocks = (unsigned)((p->n + 255) / 256);
+    const bool narrow = p->capacity < ((int64_t)1 << 31) - 256;
+    if (ctx->prm.pusher) {
+        if (narrow)
+            push32_kernel<1, uint32_t><<<blocks, 256, 0, s>>>(A);
+        else
+            push32_kernel<1, int64_t><<<blocks, 256, 0, s>>>(A);
+    } else {
+        if (narrow)
+            push32_kernel<0, uint32_t><<<blocks, 256, 0, s>>>(A);
+        else
+            push32_kernel<0, int64_t><<<blocks, 256, 0, s>>>(A);
+    }
     return cudaGetLastError();
 }
 

@@ -481,8 +481,7 @@ __global__ void __launch_bounds__(256) push64_kernel(Push64Args A)
     // cell, the entries of lanes that left their cell added directly
     if constexpr (SHAPE == 1)
         deposit_warp_split<double, 3>(dep, i0, j0, g.nr, wa1, wa2, wb1, wb2, wq * A.m_i2dt, wq * A.idt, wphi, lane,
-                                      g.nth, NG, A.ld,
-                                      A.J0, A.J1, A.J2);
+                                      g.nth, NG, (int)A.ld, A.J0, A.J1, A.J2);
 
     // ---- histogram of the new keys (warp-aggregated) -----------------------
     if (A.histogram) {
