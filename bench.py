@@ -53,13 +53,13 @@ B0 = 1.0
 # kernels (flop = 2 FMA + MUL + ADD of the SASS instruction counters) in one
 # capture of a smaller case of the same workload (same spin, radial range and
 # island fraction), and scaled to a launch by the number of particles.
-PUSH64_FP64_FLOP = 1216.0   # FP64 push, 512^2 x 64 ppc split monopole
-PUSH64_DRAM_B = 95.8        # the same capture: DRAM bytes per particle (read + write)
-PUSH32_FP32_FLOP = 827.1    # FP32-form push, 1024^2 x 64 ppc split monopole
+PUSH64_FP64_FLOP = 1181.1   # FP64 push, 512^2 x 64 ppc split monopole
+PUSH64_DRAM_B = 95.7        # the same capture: DRAM bytes per particle (read + write)
+PUSH32_FP32_FLOP = 679.3    # FP32-form push, 1024^2 x 64 ppc split monopole
 # the same capture: instructions issued per particle (warp instructions x 32)
 # and DRAM bytes per particle (read + write)
-PUSH32_INST = 1494.0
-PUSH32_DRAM_B = 66.3
+PUSH32_INST = 1165.0
+PUSH32_DRAM_B = 65.5
 # batched 1D lines, b1_kernel with the cascade running (256 lines x 4096 cells):
 # instructions issued per particle-step (warp instructions x 32) and DRAM
 # bytes per particle-step; algorithmic bytes: the particle record (cell, offset,
@@ -71,10 +71,10 @@ B1_ALG_B = 2 * 28
 # Vay's update (1024^2 x 64 ppc), the FP64 push with the cubic shape (512^2 x
 # 64 ppc), the FP64 push with photon emission and conversion decisions (512^2
 # x 16 ppc, Wald a = 0.99, B0 = 500)
-VAY32_FP32_FLOP = 1158.0
-VAY32_INST = 1925.0
+VAY32_FP32_FLOP = 737.2
+VAY32_INST = 1241.2
 CUBIC64_FP64_FLOP = 1772.0
-RAD64_FP64_FLOP = 1685.0
+RAD64_FP64_FLOP = 1401.5
 VAY_COUNT = "ncu SASS counters, FP32-form push with Vay's update, 1024^2 x 64 ppc"
 CUBIC_COUNT = "ncu SASS counters, FP64 push with the cubic shape, 512^2 x 64 ppc"
 RAD_COUNT = "ncu SASS counters, FP64 push with emission/conversion decisions, 512^2 x 16 ppc"

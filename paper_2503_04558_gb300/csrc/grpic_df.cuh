@@ -71,26 +71,33 @@ __device__ __forceinline__ df mul(const df &a, float b)
     return fast_two_sum(p.hi, fmaf(a.lo, b, p.lo));
 }
 
-// 1/x: y0 ~ 1/x.hi (2 ulp), y = y0 + y0 (1 - x y0) with the residual in pairs
+// 1/x: y0 ~ 1/x.hi (2 ulp), y = y0 + y0 e with the residual e = 1 - x y0
+// (|e| ~ 2^-22) formed as fma(-x.hi, y0, 1) - x.lo y0: the fused
+// multiply-add's single rounding of a value that small is below 2^-46, so
+// y carries about 2^-44 relative error (the square of e and the rounding of
+// y0 e), far under the FP32 rounding its consumers take
 __device__ __forceinline__ df rcp_t(const df &x)
 {
-    float y0 = __fdividef(1.0f, x.hi);
-    df xy = mul(x, y0);
-    df e = df(1.0f) - xy;
-    return fast_two_sum(y0, __fmul_rn(e.hi, y0));
+    const float y0 = __fdividef(1.0f, x.hi);
+    const float e = fmaf(-x.lo, y0, fmaf(-x.hi, y0, 1.0f));
+    return fast_two_sum(y0, __fmul_rn(e, y0));
 }
 
 __device__ __forceinline__ df operator/(const df &a, const df &b) { return a * rcp_t(b); }
 
 // sqrt(x) for x >= 0 (0 otherwise): s0 = x.hi rsqrt(x.hi), s = s0 + (x - s0^2) / (2 s0)
+// with the residual x - s0^2 = fma(-s0, s0, x.hi) + x.lo (exact to 2^-46 of x)
 __device__ __forceinline__ df sqrt_t(const df &x)
 {
     if (!(x.hi > 0.0f)) return df(0.0f);
-    float y0 = rsqrtf(x.hi);
-    float s0 = __fmul_rn(x.hi, y0);
-    df e = x - two_prod(s0, s0);
-    return fast_two_sum(s0, __fmul_rn(e.hi, __fmul_rn(0.5f, y0)));
+    const float y0 = rsqrtf(x.hi);
+    const float s0 = __fmul_rn(x.hi, y0);
+    const float e = __fadd_rn(fmaf(-s0, s0, x.hi), x.lo);
+    return fast_two_sum(s0, __fmul_rn(e, __fmul_rn(0.5f, y0)));
 }
+
+// 2^k x: exact scaling of both parts
+__device__ __forceinline__ df scale2(const df &x, float p2) { return df(__fmul_rn(x.hi, p2), __fmul_rn(x.lo, p2)); }
 
 // sin/cos of a pair through FP64 (the island takes this only for angle steps
 // beyond the Taylor range of sincos_shift_df, which the push does not reach

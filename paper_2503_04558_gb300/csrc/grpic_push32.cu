@@ -272,7 +272,7 @@ __device__ __forceinline__ void ks_geo_island(const df &a, const df &a2, const d
     const df r2 = r * r;
     const df rho2 = r2 + a2 * (c * c);
     const df ir = rcp_t(rho2);
-    const df z = mul(r, 2.0f) * ir;
+    const df z = scale2(r, 2.0f) * ir;
     const df opz = df(1.0f) + z;
     const df iopz = rcp_t(opz);
     const df alpha = sqrt_t(iopz);
@@ -321,7 +321,7 @@ __device__ __forceinline__ void boris_island(const KSGeo<float> &m, const Island
                                              const float B[3], float u[3], int pusher)
 {
     const df r2 = r * r, s2 = s * s;
-    const df Dl = r2 + a2 - mul(r, 2.0f);
+    const df Dl = r2 + a2 - scale2(r, 2.0f);
     const df ra = r2 + a2;
     const df Sg = ra * ra - a2 * Dl * s2;
     KSPoint<float> mm;
