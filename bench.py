@@ -66,6 +66,10 @@ PUSH32_DRAM_B = 65.5
 # u_r, u_phi, tag as 4 B each, id 8 B) read and written once per step
 B1_INST = 1037.0
 B1_DRAM_B = 51.7
+# the same kernel in the grown-cascade state (64 lines x 4096 cells, 10^U(4,5.5)
+# particles per line of charge weight 1/20, after 600 steps: appends running)
+B1G_INST = 1052.8
+B1G_DRAM_B = 53.1
 B1_ALG_B = 2 * 28
 # the widened rows' push kernels, counted the same way: the FP32 push with
 # Vay's update (1024^2 x 64 ppc), the FP64 push with the cubic shape (512^2 x
@@ -566,6 +570,7 @@ def run_reference(args):
 # ---------------------------------------------------------------------------
 B1_LINES, B1_CELLS, B1_A, B1_ROUT, B1_CAP = 512, 4096, 0.99, 20.0, 1_000_000
 B1_ORACLE_LINES, B1_ORACLE_STEPS = 32, 80   # the oracle's bounded sample (a few seconds)
+B1_GROWN_W = 20.0   # the grown state's macro-particles carry 1/20 of the charge
 
 
 def batch1d_inputs(nl, n, seed=2024, lo=3.0, hi=5.0):
@@ -597,9 +602,11 @@ def batch1d_measure(steps, warmup, n_lines=None, capacity=None, shape=None, grow
     oracle's throughput on a bounded sample (the smallest lines, a few seconds).
     n_lines / capacity shrink the workload for profiling runs; shape fixes the
     launch shape (threads, CTAs per SM, CTAs per line) instead of tuning.
-    grown: the lines start at 10^U(4, 5.7) particles (up to half the 1e6
-    capacity, 6.5e7 in all), the load-imbalanced state a grown cascade
-    reaches, and the tuner chooses the launch shape in that state."""
+    grown: the state a grown cascade reaches -- 10^U(4, 5.5) particles per
+    line (up to a third of the 1e6 capacity, 5e7 in all) of 1/B1_GROWN_W of
+    the macro-particle charge, so that the lines stay as charge-starved as
+    the 10^U(3, 5) start and the cascade keeps emitting and converting (the
+    appends run) -- and the tuner chooses the launch shape in that state."""
     import numpy as np
     import torch
     from paper_2503_04558_gb300 import build, grpic as G
@@ -609,11 +616,12 @@ def batch1d_measure(steps, warmup, n_lines=None, capacity=None, shape=None, grow
     rh = horizon(B1_A)
     n_lines = n_lines or B1_LINES
     capacity = capacity or B1_CAP
-    cfg = G.Batch1DConfig(n_lines, B1_CELLS, B1_A, rh, B1_ROUT, capacity, gamma_thr=100.0, eps_ph=4.0, tau=2.0,
-                          B0=2.0e3, seed=7)
+    qw = tuple(q / (B1_GROWN_W if grown else 1.0) for q in (-1.0, 1.0, 1.0, 0.0))
+    cfg = G.Batch1DConfig(n_lines, B1_CELLS, B1_A, rh, B1_ROUT, capacity, q_weight=qw, gamma_thr=100.0, eps_ph=4.0,
+                          tau=2.0, B0=2.0e3, seed=7)
     B = G.Batch1D(cfg)
     L = G.Lines(cfg)
-    theta, lines = batch1d_inputs(n_lines, B1_CELLS, lo=4.0 if grown else 3.0, hi=5.7 if grown else 5.0)
+    theta, lines = batch1d_inputs(n_lines, B1_CELLS, lo=4.0 if grown else 3.0, hi=5.5 if grown else 5.0)
     L.theta.copy_(torch.from_numpy(theta))
     omega_h = B1_A / (2.0 * rh)
     L.I0.copy_(torch.from_numpy(omega_h * cfg.B0 * np.sin(theta) ** 2))
@@ -674,11 +682,13 @@ def batch1d_measure(steps, warmup, n_lines=None, capacity=None, shape=None, grow
     pk, pk_kind = peaks()
     # the timed region is one launch of the persistent kernel running every step
     alu = measured_alu()
+    inst, dram_b = (B1G_INST, B1G_DRAM_B) if grown else (B1_INST, B1_DRAM_B)
     roof = {"kernel": "b1_kernel (one persistent launch for all timed steps)", "bound": "issue",
-            "achieved": rate * B1_INST / 32 / 1e9, "peak": alu["issue_gwarp"],
-            "unit": "G warp-instructions/s", "frac": rate * B1_INST / 32 / 1e9 / alu["issue_gwarp"],
-            "traffic": pushes * B1_DRAM_B, "inst_per_particle": B1_INST,
-            "count_source": "ncu SASS counters, b1_kernel with the cascade running, 256 lines x 4096 cells",
+            "achieved": rate * inst / 32 / 1e9, "peak": alu["issue_gwarp"],
+            "unit": "G warp-instructions/s", "frac": rate * inst / 32 / 1e9 / alu["issue_gwarp"],
+            "traffic": pushes * dram_b, "inst_per_particle": inst,
+            "count_source": "ncu SASS counters, b1_kernel with the cascade running, " +
+                            ("64 lines x 4096 cells in the grown state" if grown else "256 lines x 4096 cells"),
             "peak_source": alu["source"] + " (FMA warp-instructions/s)",
             "hbm": {"bound": "hbm", "achieved": rate * B1_ALG_B / 1e9, "peak": pk["hbm_gbs"], "unit": "GB/s",
                     "frac": rate * B1_ALG_B / 1e9 / pk["hbm_gbs"], "bytes_per_particle": B1_ALG_B,
@@ -686,8 +696,8 @@ def batch1d_measure(steps, warmup, n_lines=None, capacity=None, shape=None, grow
     out = {"value": rate, "unit": "particle-steps/s", "steps": steps, "warmup": warmup + done, "roofline": roof,
            "ms_per_step": ms / steps, "dtype": "f32",
            "workload": "%d radial lines x 4096 cells, a=0.99, r in [r_H, 20], monopole B0=2e3, gamma_thr=100, "
-                       "eps_ph=4, tau=2, initial 10^U(%s) particles per line, capacity %.0e per line"
-                       % (n_lines, "4,5.7" if grown else "3,5", capacity),
+                       "eps_ph=4, tau=2, initial 10^U(%s) particles per line of charge weight %g, capacity %.0e "
+                       "per line" % (n_lines, "4,5.5" if grown else "3,5", qw[1], capacity),
            "initial_particles": n0, "particles_now": int(L.count.sum().item()), "tuned_launch": list(best),
            "cell_updates_per_s": cells / (ms * 1e-3),
            "events": {"emitted": int(ev1[0] - ev0[0]), "converted": int(ev1[1] - ev0[1])},
@@ -703,7 +713,7 @@ def batch1d_measure(steps, warmup, n_lines=None, capacity=None, shape=None, grow
 
 def run_batch1d(args):
     shape = tuple(int(v) for v in args.b1_shape.split(",")) if args.b1_shape else None
-    m = batch1d_measure(args.steps, args.warmup, args.b1_lines, args.b1_capacity, shape)
+    m = batch1d_measure(args.steps, args.warmup, args.b1_lines, args.b1_capacity, shape, grown=args.b1_grown)
     line = {"metric": "batched 1D spark gaps: particle push+deposit/s (one persistent launch)",
             "value": m["value"], "unit": m["unit"], "n_gpus": 1, "steps": args.steps, "warmup": m["warmup"],
             "ms_per_step": m["ms_per_step"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -1052,6 +1062,7 @@ def main():
     ap.add_argument("--adj-steps", type=int, default=None, help="adjoint steps (profiling runs)")
     ap.add_argument("--b1-lines", type=int, default=None, help="batch1d lines (profiling runs)")
     ap.add_argument("--b1-capacity", type=int, default=None, help="batch1d capacity per line (profiling runs)")
+    ap.add_argument("--b1-grown", action="store_true", help="batch1d: start from the grown-cascade state")
     ap.add_argument("--b1-shape", default=None,
                     help="batch1d launch shape threads,ctas_per_sm,ctas_per_line instead of the tuner (profiling runs)")
     args = ap.parse_args()
@@ -1098,7 +1109,7 @@ def main():
                 extras[name] = {"error": f"{type(e).__name__}: {e}"}
     if not args.no_extras:
         for name, fn in (("adjoint", lambda: adjoint_measure(2)), ("batch1d", lambda: batch1d_measure(200, 600)),
-                         ("batch1d_grown", lambda: batch1d_measure(100, 20, grown=True))):
+                         ("batch1d_grown", lambda: batch1d_measure(200, 600, grown=True))):
             try:
                 extras[name] = fn()
             except Exception as e:  # reported, not hidden: the headline stands on its own
