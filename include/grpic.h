@@ -246,6 +246,31 @@ grpic_status grpic_step(grpic_ctx *ctx, grpic_particles *p, grpic_particles *scr
 grpic_status grpic_step_graph(grpic_ctx *ctx, grpic_particles *p, grpic_particles *scratch, grpic_fields *f,
                               int nsteps, void *stream);
 
+/* nsteps steps of grpic_step with the particle state resident in host
+ * memory (Fig. stepping; the end-to-end form of the step).  Each step copies
+ * host->n slots of the host arrays into the device buffers *dev, runs one
+ * grpic_step(ctx, dev, dev_scratch, f, 1), reads the live count and copies
+ * the live particles back into the same host arrays; host->n is set to the
+ * live count on return.  host_f: NULL, or host arrays of D and B (J unused)
+ * of f's layout, copied in before and out after every step as well.
+ *   host: arrays of the precision's layout (x1, x2, u1, u2, u3, tag, and cell
+ *     for precision 32) in host memory, pinned (cudaHostAlloc) for the copies
+ *     to run asynchronously; host->capacity >= host->n.  d_count unused.
+ *   dev, dev_scratch: device buffers as grpic_step's p and scratch
+ *     (capacity >= host->n; dev->d_count required); swapped as in grpic_step.
+ *   bytes: NULL or two int64 receiving the bytes copied host to device and
+ *     device to host over the call.
+ * The slot range is copied in chunks on two streams of the context (host to
+ * device, device to host), and a step's copy in of a chunk waits only for the
+ * previous step's copy out of the same slots, so the directions overlap.
+ * The host arrays are ready once `stream` has completed (the call
+ * synchronizes `stream` once per step to read the live count).  Radiation
+ * and injection contexts: GRPIC_EINVAL.  A failing step's status is returned
+ * with the host arrays holding the last completed step. */
+grpic_status grpic_step_host(grpic_ctx *ctx, grpic_particles *host, grpic_particles *dev, grpic_particles *dev_scratch,
+                             const grpic_fields *host_f, grpic_fields *f, int nsteps, int64_t bytes[2],
+                             void *stream);
+
 /* Diagnostics at vertices: rho = sum q w S / dV (cloud in cell) into rho[]
  * and the discrete div D of Eq. J-integral-eqn's integral form into divD[];
  * both (n_theta+1) x ld arrays of the field precision (device). */

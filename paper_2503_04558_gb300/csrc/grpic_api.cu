@@ -645,6 +645,173 @@ grpic_status grpic_step_graph(grpic_ctx *ctx, grpic_particles *p, grpic_particle
     return drop_pending(ctx, st);
 }
 
+// ---------------------------------------------------------------------------
+// Steps with a host-resident particle state (grpic_step_host).  The slot range
+// is cut into chunks; each step copies the chunks in on up_stream, runs one
+// grpic_step on `stream`, reads the live count, and copies the chunks back
+// on down_stream.  The next step's copy of chunk c in waits only for chunk
+// c's copy out, so the two directions overlap.
+
+}  // extern "C"
+
+namespace {
+
+__global__ void set_count_kernel(int64_t *d_count, int64_t n)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) *d_count = n;
+}
+
+constexpr int64_t HOST_CHUNK_MIN = int64_t(1) << 24;  // slots per chunk at least
+constexpr int HOST_CHUNKS_MAX = 64;
+
+struct HostArrays {
+    void *a[7];
+    size_t es[7];
+    int n;
+};
+
+HostArrays host_arrays(const grpic_ctx *ctx, const grpic_particles *p)
+{
+    HostArrays h;
+    const size_t e = ctx->prm.precision == 32 ? 4 : 8;
+    void *ptrs[7] = {p->x1, p->x2, p->u1, p->u2, p->u3, p->tag, p->cell};
+    size_t es[7] = {e, e, e, e, e, 4, 4};
+    h.n = ctx->prm.precision == 32 ? 7 : 6;
+    for (int k = 0; k < 7; ++k) {
+        h.a[k] = ptrs[k];
+        h.es[k] = es[k];
+    }
+    return h;
+}
+
+}  // namespace
+
+extern "C" {
+
+grpic_status grpic_step_host(grpic_ctx *ctx, grpic_particles *host, grpic_particles *dev, grpic_particles *dev_scratch,
+                             const grpic_fields *host_f, grpic_fields *f, int nsteps, int64_t bytes[2], void *stream)
+{
+    if (!ctx) return GRPIC_EINVAL;
+    if (bytes) bytes[0] = bytes[1] = 0;
+    if (nsteps < 0 || !host || host->n < 0 || host->capacity < host->n || !particles_ok(ctx, dev) ||
+        !particles_ok(ctx, dev_scratch) || !dev->d_count || dev->capacity < host->n ||
+        dev_scratch->capacity < host->n || !fields_ok(ctx, f) || ctx->prm.radiation || ctx->prm.injection)
+        return fail(ctx, GRPIC_EINVAL, "grpic_step_host: bad arguments");
+    const HostArrays ha = host_arrays(ctx, host);
+    for (int k = 0; k < ha.n; ++k)
+        if (!ha.a[k] && host->n > 0) return fail(ctx, GRPIC_EINVAL, "grpic_step_host: missing host array");
+    if (host_f) {
+        if (host_f->ld != f->ld) return fail(ctx, GRPIC_EINVAL, "grpic_step_host: host fields' ld differs");
+        for (int k = 0; k < 3; ++k)
+            if (!host_f->D[k] || !host_f->B[k]) return fail(ctx, GRPIC_EINVAL, "grpic_step_host: missing host field");
+    }
+    cudaError_t e = cudaSuccess;
+    if (!ctx->up_stream) e = cudaStreamCreateWithFlags(&ctx->up_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess && !ctx->down_stream) e = cudaStreamCreateWithFlags(&ctx->down_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess && !ctx->h_count) e = cudaHostAlloc(reinterpret_cast<void **>(&ctx->h_count), sizeof(int64_t), 0);
+    if (e == cudaSuccess && !ctx->hevents) {
+        ctx->hevents = new (std::nothrow) std::vector<cudaEvent_t>();
+        if (!ctx->hevents) return fail(ctx, GRPIC_ENOMEM, "grpic_step_host: events");
+    }
+    // events: [0, HOST_CHUNKS_MAX) chunks out, then fields out, copies in, step done, end
+    const int nev = HOST_CHUNKS_MAX + 4;
+    while (e == cudaSuccess && (int)ctx->hevents->size() < nev) {
+        cudaEvent_t ev;
+        e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+        if (e == cudaSuccess) ctx->hevents->push_back(ev);
+    }
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "grpic_step_host: setup");
+    std::vector<cudaEvent_t> &ev = *ctx->hevents;
+    cudaEvent_t ev_fout = ev[HOST_CHUNKS_MAX], ev_in = ev[HOST_CHUNKS_MAX + 1], ev_step = ev[HOST_CHUNKS_MAX + 2],
+                ev_end = ev[HOST_CHUNKS_MAX + 3];
+    cudaStream_t s = S(stream), up = ctx->up_stream, down = ctx->down_stream;
+    const size_t fbytes = (size_t)(ctx->g.nth + 1) * f->ld * (ctx->prm.precision == 32 ? 4 : 8);
+    int64_t n = host->n;
+    int prev_chunks = 0;  // chunks copied out by the previous step
+    int64_t prev_chunk = 0;
+    grpic_status st = GRPIC_OK;
+    // the copies in wait for the work already on `stream` (which may use the
+    // device buffers) and for the previous call's copies out
+    e = cudaEventRecord(ev_step, s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(up, ev_step, 0);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(up, ev_end, 0);
+    for (int step = 0; step < nsteps && e == cudaSuccess && !st; ++step) {
+        const int64_t chunk = std::max(HOST_CHUNK_MIN, (n + HOST_CHUNKS_MAX - 1) / HOST_CHUNKS_MAX);
+        const int nch = n > 0 ? (int)((n + chunk - 1) / chunk) : 0;
+        const HostArrays hd = host_arrays(ctx, dev);
+        // copies in: chunk c after the previous step's copy out of the slots it covers
+        for (int c = 0; c < nch && e == cudaSuccess; ++c) {
+            const int64_t lo = c * chunk, hi = std::min(n, lo + chunk);
+            if (step > 0 && prev_chunks > 0) {
+                const int last = (int)std::min<int64_t>(prev_chunks - 1, (hi - 1) / prev_chunk);
+                for (int q = (int)(lo / prev_chunk); q <= last && e == cudaSuccess; ++q)
+                    e = cudaStreamWaitEvent(up, ev[q], 0);
+            }
+            for (int k = 0; k < ha.n && e == cudaSuccess; ++k)
+                e = cudaMemcpyAsync(static_cast<char *>(hd.a[k]) + lo * ha.es[k],
+                                    static_cast<const char *>(ha.a[k]) + lo * ha.es[k], (hi - lo) * ha.es[k],
+                                    cudaMemcpyHostToDevice, up);
+        }
+        if (host_f && e == cudaSuccess) {
+            if (step > 0) e = cudaStreamWaitEvent(up, ev_fout, 0);
+            for (int k = 0; k < 3 && e == cudaSuccess; ++k) {
+                e = cudaMemcpyAsync(f->D[k], host_f->D[k], fbytes, cudaMemcpyHostToDevice, up);
+                if (e == cudaSuccess) e = cudaMemcpyAsync(f->B[k], host_f->B[k], fbytes, cudaMemcpyHostToDevice, up);
+            }
+        }
+        if (e == cudaSuccess) e = cudaEventRecord(ev_in, up);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ev_in, 0);
+        if (e != cudaSuccess) break;
+        if (bytes) bytes[0] += n * (int64_t)(ha.n == 7 ? 28 : 44) + (host_f ? 6 * (int64_t)fbytes : 0);
+        dev->n = n;
+        set_count_kernel<<<1, 32, 0, s>>>(dev->d_count, n);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) break;
+        st = grpic_step(ctx, dev, dev_scratch, f, 1, stream);
+        if (st) break;
+        // the live count decides the copies out
+        e = cudaMemcpyAsync(ctx->h_count, dev->d_count, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) break;
+        const int64_t nn = std::min(*ctx->h_count, n);
+        if (nn < 0) {
+            st = fail(ctx, GRPIC_ECUDA, "grpic_step_host: bad live count");
+            break;
+        }
+        e = cudaEventRecord(ev_step, s);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(down, ev_step, 0);
+        const int64_t ochunk = std::max(HOST_CHUNK_MIN, (nn + HOST_CHUNKS_MAX - 1) / HOST_CHUNKS_MAX);
+        const int och = nn > 0 ? (int)((nn + ochunk - 1) / ochunk) : 0;
+        const HostArrays hs = host_arrays(ctx, dev);  // the sorted state (dev swapped by the sort)
+        for (int c = 0; c < och && e == cudaSuccess; ++c) {
+            const int64_t lo = c * ochunk, hi = std::min(nn, lo + ochunk);
+            for (int k = 0; k < ha.n && e == cudaSuccess; ++k)
+                e = cudaMemcpyAsync(static_cast<char *>(ha.a[k]) + lo * ha.es[k],
+                                    static_cast<const char *>(hs.a[k]) + lo * ha.es[k], (hi - lo) * ha.es[k],
+                                    cudaMemcpyDeviceToHost, down);
+            if (e == cudaSuccess) e = cudaEventRecord(ev[c], down);
+        }
+        if (host_f && e == cudaSuccess) {
+            for (int k = 0; k < 3 && e == cudaSuccess; ++k) {
+                e = cudaMemcpyAsync(host_f->D[k], f->D[k], fbytes, cudaMemcpyDeviceToHost, down);
+                if (e == cudaSuccess) e = cudaMemcpyAsync(host_f->B[k], f->B[k], fbytes, cudaMemcpyDeviceToHost, down);
+            }
+            if (e == cudaSuccess) e = cudaEventRecord(ev_fout, down);
+        }
+        if (bytes) bytes[1] += nn * (int64_t)(ha.n == 7 ? 28 : 44) + (host_f ? 6 * (int64_t)fbytes : 0);
+        prev_chunks = och;
+        prev_chunk = ochunk;
+        n = nn;
+    }
+    // `stream` completes after the last copies out
+    cudaError_t e2 = cudaEventRecord(ev_end, down);
+    if (e2 == cudaSuccess) e2 = cudaStreamWaitEvent(s, ev_end, 0);
+    if (e == cudaSuccess) e = e2;
+    host->n = n;
+    if (st) return st;
+    return e == cudaSuccess ? GRPIC_OK : cuda_fail(ctx, e, "grpic_step_host");
+}
+
 grpic_status grpic_diagnostics(grpic_ctx *ctx, const grpic_particles *p, const grpic_fields *f, void *rho, void *divD,
                                void *stream)
 {
@@ -918,6 +1085,13 @@ void grpic_destroy(grpic_ctx *ctx)
     }
     if (ctx->graph_exec) cudaGraphExecDestroy(ctx->graph_exec);
     if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
+    if (ctx->hevents) {
+        for (cudaEvent_t e : *ctx->hevents) cudaEventDestroy(e);
+        delete ctx->hevents;
+    }
+    if (ctx->up_stream) cudaStreamDestroy(ctx->up_stream);
+    if (ctx->down_stream) cudaStreamDestroy(ctx->down_stream);
+    if (ctx->h_count) cudaFreeHost(ctx->h_count);
     void *ptrs[] = {ctx->d_spawn, ctx->d_rad, ctx->d_spqm, ctx->d_spmassive, ctx->d_offset_prev, ctx->d_cnt9, ctx->d_base9, ctx->d_sortflag, ctx->rcol, ctx->rcol2, ctx->rowsc, ctx->tab, ctx->col1d, ctx->tab32, ctx->col1d32, ctx->fscratch, ctx->d_status, ctx->d_keys,
                     ctx->d_count, ctx->d_offset, ctx->d_cursor, ctx->d_blocksum, ctx->d_perm, ctx->d_bigseg};
     for (void *q : ptrs)

@@ -105,6 +105,11 @@ struct grpic_ctx {
     // FP32 field update by fused shared-memory launches (1, the default) or
     // one launch per stage (0); grpic_set_field_path
     int field_fused;
+    // grpic_step_host: copy streams (host to device, device to host), one
+    // event per copy chunk, and a pinned word for the live count
+    cudaStream_t up_stream, down_stream;
+    std::vector<cudaEvent_t> *hevents;
+    int64_t *h_count;
     char err[256];
 };
 

@@ -27,7 +27,7 @@ EXPORTS = ["grpic_init", "grpic_init_fields", "grpic_push", "grpic_deposit", "gr
            "grpic_sort_noalloc", "grpic_set_timing", "grpic_get_timing", "grpic_alu_peak",
            "grpic_field_update_rows", "grpic_halo_pack", "grpic_halo_unpack", "grpic_sort_split",
            "grpic_particles_pack", "grpic_slab_assemble", "grpic_set_field_path", "grpic_fp32_encode",
-           "grpic_fp32_decode"]
+           "grpic_fp32_decode", "grpic_step_host"]
 NOALLOC_MAX_PARTICLES = 2097152
 NOALLOC_MAX_CELLS = 262144
 
@@ -95,6 +95,7 @@ def load(path: str = LIB_PATH):
         "grpic_set_field_path": [v, C.c_int32],
         "grpic_fp32_encode": [v, i64, v, v, v, v, v, v],
         "grpic_fp32_decode": [v, i64, v, v, v, v, v, v],
+        "grpic_step_host": [v, p(ParticlesC), p(ParticlesC), p(ParticlesC), p(FieldsC), p(FieldsC), i, p(i64), v],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -247,6 +248,54 @@ class Particles:
         return [self.x1, self.x2, self.u1, self.u2, self.u3, self.tag, self.cell]
 
 
+class HostParticles:
+    """A particle state in pinned host memory (the arrays of Particles) for
+    grpic_step_host; n live slots."""
+
+    def __init__(self, cfg: Config, capacity: int):
+        import torch
+        fdt = torch.float64 if cfg.precision == 64 else torch.float32
+        cap = max(int(capacity), 1)
+        self.capacity = cap
+        self.n = 0
+        mk = lambda dt: torch.zeros(cap, dtype=dt, pin_memory=True)
+        self.x1, self.x2, self.u1, self.u2, self.u3 = (mk(fdt) for _ in range(5))
+        self.tag = mk(torch.int32)
+        self.cell = mk(torch.int32) if cfg.precision == 32 else None
+
+    def arrays(self):
+        return [self.x1, self.x2, self.u1, self.u2, self.u3, self.tag, self.cell]
+
+    def c(self):
+        s = ParticlesC()
+        s.n = self.n
+        s.capacity = self.capacity
+        s.d_count = 0
+        s.x1, s.x2, s.u1, s.u2, s.u3 = (t.data_ptr() for t in (self.x1, self.x2, self.u1, self.u2, self.u3))
+        s.tag = self.tag.data_ptr()
+        s.cell = self.cell.data_ptr() if self.cell is not None else 0
+        return s
+
+
+class HostFields:
+    """D and B in pinned host memory, the layout of Fields (J unused)."""
+
+    def __init__(self, F):
+        import torch
+        self.ld = F.ld
+        self.D = [torch.empty(t.shape, dtype=t.dtype, pin_memory=True) for t in F.D]
+        self.B = [torch.empty(t.shape, dtype=t.dtype, pin_memory=True) for t in F.B]
+
+    def c(self):
+        f = FieldsC()
+        for k in range(3):
+            f.D[k] = self.D[k].data_ptr()
+            f.B[k] = self.B[k].data_ptr()
+            f.J[k] = 0
+        f.ld = self.ld
+        return f
+
+
 class ParticleSet:
     """Two particle buffers (sort ping-pong), the live count on the device and
     the C struct the library sees."""
@@ -380,6 +429,25 @@ class Context:
                                         _stream(stream)), "grpic_step")
         P.sync_ptrs()
         P.n = P._sc.n   # radiation or injection: the whole capacity is the slot range
+
+    def step_host(self, H: HostParticles, P: ParticleSet, F: Fields, nsteps=1, host_fields=None, stream=None):
+        """grpic_step_host: nsteps steps with the particle state in H (pinned
+        host memory), P's buffers as the device copy, H.n updated to the
+        live count; host_fields (HostFields) copied in and out every step
+        too.  Returns (bytes host to device, bytes device to host)."""
+        hc = H.c()
+        P._sc.n = H.n
+        P._ss.n = H.n
+        fc = F.c()
+        hf = host_fields.c() if host_fields is not None else None
+        out = (C.c_int64 * 2)()
+        self._check(self.lib.grpic_step_host(self.h, C.byref(hc), C.byref(P._sc), C.byref(P._ss),
+                                             C.byref(hf) if hf is not None else None, C.byref(fc), nsteps, out,
+                                             _stream(stream)), "grpic_step_host")
+        H.n = hc.n
+        P.sync_ptrs()
+        P.n = hc.n
+        return out[0], out[1]
 
     def fp32_encode(self, r, th, stream=None):
         """(cell, o1, o2) of the FP32 form from FP64 positions (device tensors
