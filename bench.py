@@ -1123,11 +1123,13 @@ def main():
                 "phases": h["phases"], "live_particles": h["live_particles"],
                 "particle_statuses": h["particle_statuses"],
                 "roofline": h["roofline"], "clocks": h["clocks"], "measured_alu_peaks": measured_alu(),
-                # per step: push, 1 + n_field_iter field stages, 12 sort kernels
+                # per step: push, the field update (FP32: fused launches of four
+                # stages; FP64: 1 + n_field_iter stage launches), 12 sort kernels
                 # (count, destinations, histogram pair, 3 scan, bases, placement and
                 # the general path's 3, which return at once) -- the count only
                 # in the first step, later pushes count -- and one gather per call
-                "gpu_launches": args.steps * (1 + 1 + cfg.n_field_iter + 12) - (args.steps - 1) + 1,
+                "gpu_launches": args.steps * (1 + ((1 + cfg.n_field_iter + 3) // 4 if head_prec == 32 else
+                                                   1 + cfg.n_field_iter) + 12) - (args.steps - 1) + 1,
                 "e2e": res["e2e"]}
         if second is not None:
             s2 = grpic_summary(second, args, world, 64)

@@ -376,6 +376,13 @@ __global__ void __launch_bounds__(FZ_THREADS, GRPIC_FZ_MINB) field_fused32_kerne
                      : "memory");
     if (__syncthreads_or(!done)) {  // every thread leaves together
         if (threadIdx.x == 0) atomicCAS(status, 0, (int)GRPIC_ETIMEOUT);
+        // a second bounded wait for copies still in flight before the CTA's
+        // shared memory is released
+        for (int tries = 0; tries < (1 << 22) && !done; ++tries)
+            asm volatile("{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0; selp.u32 %0, 1, 0, p; }"
+                         : "=r"(done)
+                         : "r"(smem_u32(bar))
+                         : "memory");
         return;
     }
     // the points a stage does not update keep the loaded values in both
