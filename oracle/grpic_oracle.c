@@ -11,7 +11,7 @@
  * Every routine takes the paper's steps in the paper's order and notation with
  * plain loops; no blocking, fusion or reordering.  Built with
  * -O2 -ffp-contract=off.  Where the paper is silent, garbled or inconsistent
- * the adopted reading is named in the comment (and listed in the design notes):
+ * the adopted reading is named in the comment:
  *   - field corrector prefactor is dt, not dt/2 (Eq. fld-corrector with
  *     alpha+beta = 1; "alpha = beta = 1/2 is Heun's method");
  *   - E_phi's shift term carries the 1/2 of the two-point average (Eq. auxE);
@@ -1364,7 +1364,7 @@ void orc_divB(const orc_cfg *c, const double *B0r, const double *B1, double *div
 /* Sec. 4, Eq. optical-depth, on single radial field lines).                 */
 /*                                                                          */
 /* The paper runs its spark gaps in 2D; this 1D line model is the reading   */
-/* used here (listed in the design notes): along a monopole field line at   */
+/* used here: along a monopole field line at                              */
 /* fixed theta_k particles slide radially (theta frozen, u_theta = 0, u_phi */
 /* kept), the electric kick is the covariant gamma_rr D^r part of the Boris */
 /* step, the geodesic step is Eq. geodesic-predictor/-corrector restricted  */

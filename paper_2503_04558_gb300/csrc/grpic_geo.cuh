@@ -203,4 +203,34 @@ __device__ __forceinline__ void rhs32(const Pt32 &m, float a, float eps, float u
     f.ut = fmaf(m.E, fmaf(-K, m.z, h * irP), iri * (m.cs * m.is2) * is2up2);
 }
 
+// The same right-hand side from the upper metric's values given apart
+// (the near-horizon island forms them in extended precision): with
+// gamma^{rj} u_j, gamma^{phi j} u_j and G = gamma^{jk} u_j u_k, Q = eps + G,
+// P / rho^2 = G + beta u_r^2, and the force terms as in rhs32.
+struct GUp32 {
+    float rr, rp, tt, pp;
+};
+
+__device__ __forceinline__ void rhs32g(const Pt32 &m, const GUp32 &g, float eps, float ur, float ut, float up,
+                                       RhsT<float> &f)
+{
+    const float ur2 = ur * ur;
+    const float gur = fmaf(g.rr, ur, g.rp * up);  // gamma^{rj} u_j
+    const float gup = fmaf(g.rp, ur, g.pp * up);  // gamma^{phi j} u_j
+    const float gtu = g.tt * ut;
+    const float G = fmaf(gur, ur, fmaf(gtu, ut, gup * up));
+    const float Q = G + eps;
+    const float qq = rsqrtf(Q);
+    const float iu0 = m.al * qq;
+    const float h = 0.5f * iu0;
+    const float iri = m.ir * iu0;
+    f.xr = fmaf(iu0, gur, -m.beta);
+    f.xt = iu0 * gtu;
+    f.xp = iu0 * gup;
+    const float irP = fmaf(m.beta, ur2, G);
+    const float K = m.iopz * fmaf(m.iopz * ur, fmaf(h, ur, 1.0f), h * Q);
+    f.ur = fmaf(K, fmaf(-m.z, m.z, m.ir + m.ir), h * m.z * (irP - ur2));
+    f.ut = fmaf(m.E, fmaf(-K, m.z, h * irP), iri * (m.cs * m.is2) * (m.is2 * up * up));
+}
+
 }  // namespace grpic

@@ -27,7 +27,7 @@
 #include "grpic_window.cuh"
 #include "grpic_vay.cuh"
 
-#include <type_traits>
+#include <cmath>
 
 namespace grpic {
 namespace {
@@ -256,150 +256,39 @@ __device__ __forceinline__ void boris_geo(const KSGeo<M> &m, M a, M r, M s, floa
     }
 }
 
-// The metric of the near-horizon island in double-FP32 pairs: alpha, beta,
-// gamma^{ij}, rho^2, 1/rho^2, 1 + z formed in pair arithmetic and rounded to
-// FP32 for the right-hand sides; their r and theta derivatives, which enter
-// only the force terms U_i, in FP32 from the rounded values (as the FP32
-// form's own metric).  `keep` receives the pairs the Boris step's lower
-// metric reuses.
-struct IslandKeep {
-    df alpha, ir, opz, rho2;
-};
-
-__device__ __forceinline__ void ks_geo_island(const df &a, const df &a2, const df &r, const df &s, const df &c,
-                                              KSGeo<float> &m, IslandKeep *keep)
+// The push of one particle of the near-horizon island with the native FP64
+// metric and its derivatives (island_arith = 1).  o2 is the offset from the
+// row's lower edge (stencils and window); in the last row (pole) the
+// particle's theta offset is q = (pi - theta) / dtheta, stored with FP32's
+// relative precision, and the trapezoid integrates q there (dq/dt =
+// -X^theta / dtheta): on return q (pole) or o2 hold the end point's offset in
+// that row's variable
+template <int PUSHER>
+__device__ __forceinline__ void push_island_fp64(const Push32Args &A, int i, int j, float &o1, float &o2, float u[3],
+                                                 int sp, float &dphi, bool pole, float &q)
 {
-    const df r2 = r * r;
-    const df rho2 = r2 + a2 * (c * c);
-    const df ir = rcp_t(rho2);
-    const df z = scale2(r, 2.0f) * ir;
-    const df opz = df(1.0f) + z;
-    const df iopz = rcp_t(opz);
-    const df alpha = sqrt_t(iopz);
-    const df beta = z * iopz;
-    const df is2 = rcp_t(s * s);
-    if (keep) {
-        keep->alpha = alpha;
-        keep->ir = ir;
-        keep->opz = opz;
-        keep->rho2 = rho2;
-    }
-    m.rho2 = (float)rho2;
-    m.ir = (float)ir;
-    m.opz = (float)opz;
-    m.alpha = (float)alpha;
-    m.beta = (float)beta;
-    m.grr = (float)((a2 + r2) * ir - beta);
-    m.grp = (float)(a * ir);
-    m.gtt = m.ir;
-    m.gpp = (float)(ir * is2);
-    // derivatives (App. A) in FP32
-    const float af = a.hi, a2f = a2.hi, rf = (float)r, sf = (float)s, cf = (float)c, irf = m.ir;
-    const float iopzf = (float)iopz, is2f = (float)is2, r2f = rf * rf;
-    const float ir2 = irf * irf;
-    const float drho_t = -2.0f * a2f * cf * sf;
-    const float dz_r = 2.0f * irf * (1.0f - 2.0f * r2f * irf);
-    const float dz_t = -2.0f * rf * drho_t * ir2;
-    const float ka = -0.5f * m.alpha * iopzf, kb = iopzf * iopzf;
-    m.da_r = ka * dz_r;
-    m.da_t = ka * dz_t;
-    m.db_r = kb * dz_r;
-    m.db_t = kb * dz_t;
-    m.dgrr_r = 2.0f * rf * irf - (a2f + r2f) * 2.0f * rf * ir2 - m.db_r;
-    m.dgrr_t = -(a2f + r2f) * drho_t * ir2 - m.db_t;
-    m.dgrp_r = -af * 2.0f * rf * ir2;
-    m.dgrp_t = -af * drho_t * ir2;
-    m.dgtt_r = -2.0f * rf * ir2;
-    m.dgtt_t = -drho_t * ir2;
-    m.dgpp_r = -2.0f * rf * ir2 * is2f;
-    m.dgpp_t = -drho_t * ir2 * is2f - 2.0f * sf * cf * irf * is2f * is2f;
-}
-
-// the Boris step of an island particle: the lower metric from the pairs
-__device__ __forceinline__ void boris_island(const KSGeo<float> &m, const IslandKeep &k, const df &a, const df &a2,
-                                             const df &r, const df &s, float qm, float dt, const float D[3],
-                                             const float B[3], float u[3], int pusher)
-{
-    const df r2 = r * r, s2 = s * s;
-    const df Dl = r2 + a2 - scale2(r, 2.0f);
-    const df ra = r2 + a2;
-    const df Sg = ra * ra - a2 * Dl * s2;
-    KSPoint<float> mm;
-    mm.alpha = m.alpha;
-    mm.g_rr = m.opz;
-    mm.g_tt = m.rho2;
-    mm.g_pp = (float)(Sg * s2 * k.ir);
-    mm.g_rp = (float)(-(a * s2 * k.opz));
-    mm.gi_rr = m.grr;
-    mm.gi_rp = m.grp;
-    mm.gi_tt = m.gtt;
-    mm.gi_pp = m.gpp;
-    mm.sqrtg = (float)(k.rho2 * s * k.opz * k.alpha);  // rho^2 sin sqrt(1+z)
-    if (pusher) {
-        const VayMetric<float> vm{mm.alpha, mm.g_rr, mm.g_rp, mm.g_tt, mm.g_pp, mm.gi_rr, mm.gi_rp, mm.gi_tt,
-                                  mm.gi_pp, mm.sqrtg};
-        vay_step<float>(vm, qm, dt, D, B, u);
-    } else {
-        boris32<float>(mm, qm, dt, D, B, u);
-    }
-}
-
-// The push of one particle of the near-horizon island (M = df: the metric in
-// double-FP32 pairs, M = double: in FP64).  o2 is the offset from the row's
-// lower edge (stencils and window); in the last row (pole) the particle's
-// theta offset is q = (pi - theta) / dtheta, stored with FP32's relative
-// precision, and the trapezoid integrates q there (dq/dt = -X^theta /
-// dtheta): on return q (pole) or o2 hold the end point's offset in that
-// row's variable
-template <typename M, int PUSHER>
-__device__ __forceinline__ void push_one(const Push32Args &A, int i, int j, float &o1, float &o2, float u[3], int sp,
-                                         float &dphi, bool pole, float &q)
-{
-    constexpr bool IS_DF = std::is_same<M, df>::value, IS_D = std::is_same<M, double>::value;
     const GridDev &g = A.g;
-    const float2 rc2 = __ldg(reinterpret_cast<const float2 *>(A.rcol2) + i + NG);
-    const float rcf = IS_D ? (float)A.rcol[i + NG] : __fadd_rn(rc2.x, rc2.y);
+    const float rcf = (float)A.rcol[i + NG];
     const float d0 = rcf * expm1_cell(o1 * A.dx1f, A.dx1f);  // r - r_i
     // metric at x^n, shared by the Boris step and the first right-hand side
-    M am, r0, s0, c0;
-    // the angle's sin and cos: in the pole row from theta' = pi - theta =
-    // q dtheta (row 0's table shifted by q dtheta; cos theta = -cos theta')
-    if constexpr (IS_D) {
-        am = g.a;
-        r0 = A.rcol[i + NG] + (double)d0;
-        if (pole)
-            sincos((double)g.nth * g.dth - (double)q * g.dth, &s0, &c0);
-        else
-            sincos(((double)j + (double)o2) * g.dth, &s0, &c0);
-    } else {
-        am = A.a_df;
-        r0 = df(rc2.x, rc2.y) + df(d0);
-        const float4 sc = __ldg(reinterpret_cast<const float4 *>(A.rowsc) + (pole ? 0 : j));
-        sincos_shift_df(df(sc.x, sc.y), df(sc.z, sc.w), mul(A.dth_df, pole ? q : o2), s0, c0);
-        if (pole) c0 = -c0;
-    }
-    // the pair island's metric comes as FP32 values rounded from pairs
-    using MG = typename std::conditional<IS_DF, float, M>::type;
-    KSGeo<MG> m;
-    IslandKeep keep;
-    if constexpr (IS_DF)
-        ks_geo_island(am, A.a2_df, r0, s0, c0, m, &keep);
+    const double am = g.a, r0 = A.rcol[i + NG] + (double)d0;
+    double s0, c0;
+    if (pole)
+        sincos((double)g.nth * g.dth - (double)q * g.dth, &s0, &c0);
     else
-        ks_geo_sc<M>(am, r0, s0, c0, m);
+        sincos(((double)j + (double)o2) * g.dth, &s0, &c0);
+    KSGeo<double> m;
+    ks_geo_sc<double>(am, r0, s0, c0, m);
     if (A.massive[sp] && A.qm[sp] != 0.0f) {
         float Dv[3], Bv[3];
         gather_fields32(A, i, j, o1, o2, Dv, Bv);
-        if constexpr (IS_DF) {
-            boris_island(m, keep, am, A.a2_df, r0, s0, A.qm[sp], A.dt, Dv, Bv, u, PUSHER);
-        } else {
-            boris_geo<M>(m, am, r0, s0, A.qm[sp], A.dt, Dv, Bv, u, PUSHER);
-        }
+        boris_geo<double>(m, am, r0, s0, A.qm[sp], A.dt, Dv, Bv, u, PUSHER);
     }
     const float eps = A.massive[sp] ? 1.0f : 0.0f;
     const float dt = A.dt, h = 0.5f * dt;
     const float idth = A.idthf;
     RhsT<float> f0, ft;
-    geo_rhs_m<MG, float>(m, eps, u[0], u[1], u[2], f0);
+    geo_rhs_m<double, float>(m, eps, u[0], u[1], u[2], f0);
     f0.xt *= idth;
     // the theta offset integrated: o2 (X^theta / dtheta), or q in the pole
     // row (-X^theta / dtheta); sg is the sign and t0 the start value
@@ -407,36 +296,17 @@ __device__ __forceinline__ void push_one(const Push32Args &A, int i, int j, floa
     float a1 = d0 + dt * f0.xr, a2 = t0 + sg * dt * f0.xt, ap = dt * f0.xp;
     float b1 = u[0] + dt * f0.ur, b2 = u[1] + dt * f0.ut;
     for (int it = 0; it < A.n_iter; ++it) {
-        // metric at the iterate: theta = theta^n + sg (a2 - t0) dtheta; in the
-        // pole row sin and cos of theta' shifted by (a2 - t0) dtheta
-        M s, c, ri;
-        if constexpr (IS_D) {
-            double d = sg * ((double)a2 - (double)t0) * g.dth;
-            if (fabs(d) <= 0.05)
-                sincos_shift<double>(s0, c0, d, s, c);
-            else
-                sincos(((double)j + (double)o2) * g.dth + d, &s, &c);
-            ri = A.rcol[i + NG] + (double)a1;
-        } else {
-            df d = two_sum(a2, -t0) * A.dth_df;
-            if (fabs_hi(d) <= 0.1f) {
-                sincos_shift_df(s0, pole ? -c0 : c0, d, s, c);
-            } else {
-                df th = df(pole ? 0 : j) * A.dth_df + mul(A.dth_df, t0) + d;
-                sincos_t(th, &s, &c);
-            }
-            if (pole) c = -c;
-            ri = df(rc2.x, rc2.y) + df(a1);
-        }
-        if constexpr (IS_DF) {
-            KSGeo<float> mi;
-            ks_geo_island(am, A.a2_df, ri, s, c, mi, nullptr);
-            geo_rhs_m<float, float>(mi, eps, b1, b2, u[2], ft);
-        } else {
-            KSGeo<M> mi;
-            ks_geo_sc<M>(am, ri, s, c, mi);
-            geo_rhs_m<M, float>(mi, eps, b1, b2, u[2], ft);
-        }
+        // metric at the iterate: theta = theta^n + sg (a2 - t0) dtheta
+        double s, c;
+        const double d = sg * ((double)a2 - (double)t0) * g.dth;
+        if (fabs(d) <= 0.05)
+            sincos_shift<double>(s0, c0, d, s, c);
+        else
+            sincos(((double)j + (double)o2) * g.dth + d, &s, &c);
+        const double ri = A.rcol[i + NG] + (double)a1;
+        KSGeo<double> mi;
+        ks_geo_sc<double>(am, ri, s, c, mi);
+        geo_rhs_m<double, float>(mi, eps, b1, b2, u[2], ft);
         ft.xt *= idth;
         float n1 = d0 + h * (ft.xr + f0.xr), n2 = t0 + sg * h * (ft.xt + f0.xt);
         float nb1 = u[0] + h * (ft.ur + f0.ur), nb2 = u[1] + h * (ft.ut + f0.ut);
@@ -502,7 +372,7 @@ __device__ __forceinline__ void boris_pt32(const Pt32 &m, float a, float a2, flo
 // point quantities at x^n serve the Boris step and the first right-hand
 // side; sin and cos at the iterates from those at theta^n by the short
 // series of sincos_shift (|shift| <= one cell).  Offsets and the pole row as
-// in push_one; here sin, cos are those of theta itself (in the pole row cos
+// in push_island_fp64; here sin, cos are those of theta itself (in the pole row cos
 // theta = -cos theta' from the table of theta' = pi - theta), and the shift of
 // theta per unit change of the integrated offset is +dtheta, or -dtheta in the
 // pole row.
@@ -555,7 +425,7 @@ __device__ __forceinline__ void push_fp32(const Push32Args &A, int i, int j, flo
         const float nb1 = fmaf(h, ft.ur + f0.ur, u[0]), nb2 = fmaf(h, ft.ut + f0.ut, u[1]);
         bool done = false;
         if (A.use_tol) {
-            // the convergence test of push_one: change of the iterate relative
+            // the convergence test of push_island_fp64: change of the iterate relative
             // to r_i, one theta cell and max(1, |u|)
             const float t = A.tolf;
             done = fabsf(n1 - a1) < trc && fabsf(n2 - a2) < t && fabsf(nb1 - b1) < t * fmaxf(1.0f, fabsf(nb1)) &&
@@ -575,6 +445,164 @@ __device__ __forceinline__ void push_fp32(const Push32Args &A, int i, int j, flo
     u[0] = b1;
     u[1] = b2;
     dphi = h * (xpl + f0.xp);  // dt X^phi(x^n) without correctors
+}
+
+// The island's point quantities in double-FP32 pairs: alpha, beta, gamma^ij,
+// rho^2, 1/rho^2, 1 + z (and sin^2, 1/sin^2, a^2 + r^2, sin cos) in pairs,
+// rounded to FP32 for the right-hand side; E = d_theta rho^2 / rho^2 in FP32
+// from the rounded values (a derivative: force terms only).  The pairs the
+// Boris step's lower metric reuses go to *keep.
+struct IslandPt {
+    df alpha, ir, opz, rho2, s2, ar2, z;
+};
+
+__device__ __forceinline__ void point_island(const df &a, const df &a2, float m2a2f, const df &r, const df &s,
+                                             const df &c, Pt32 &m, GUp32 &gu, IslandPt *keep)
+{
+    const df r2 = r * r;
+    const df rho2 = r2 + a2 * (c * c);
+    const df ir = rcp_t(rho2);
+    const df z = scale2(r, 2.0f) * ir;
+    const df opz = add_f(z, 1.0f);
+    const df iopz = rcp_t(opz);
+    const df alpha = sqrt_t(iopz);
+    const df beta = z * iopz;
+    const df s2 = s * s;
+    const df is2 = rcp_t(s2);
+    const df ar2 = a2 + r2;
+    m.s = (float)s;
+    m.rho2 = (float)rho2;
+    m.ir = (float)ir;
+    m.z = (float)z;
+    m.opz = (float)opz;
+    m.al = (float)alpha;
+    m.iopz = (float)iopz;
+    m.beta = (float)beta;
+    m.s2 = (float)s2;
+    m.is2 = (float)is2;
+    m.ar2 = (float)ar2;
+    m.cs = (float)(c * s);
+    m.E = m2a2f * m.cs * m.ir;
+    gu.rr = (float)(ar2 * ir - beta);
+    gu.rp = (float)(a * ir);
+    gu.tt = m.ir;
+    gu.pp = (float)(ir * is2);
+    if (keep) {
+        keep->alpha = alpha;
+        keep->ir = ir;
+        keep->opz = opz;
+        keep->rho2 = rho2;
+        keep->s2 = s2;
+        keep->ar2 = ar2;
+        keep->z = z;
+    }
+}
+
+// the Boris step of an island particle: the lower metric from the pairs,
+// gamma_phph = sin^2 (a^2 + r^2 + z a^2 sin^2) (Sigma without cancellation),
+// gamma_rph = -a sin^2 (1 + z), sqrt(gamma) = rho^2 sin (1 + z) alpha
+template <int PUSHER>
+__device__ __forceinline__ void boris_island_pt(const Pt32 &m, const GUp32 &gu, const IslandPt &k, const df &a,
+                                                const df &a2, const df &s, float qm, float dt, const float D[3],
+                                                const float B[3], float u[3])
+{
+    KSPoint<float> mm;
+    mm.alpha = m.al;
+    mm.g_rr = m.opz;
+    mm.g_tt = m.rho2;
+    mm.g_pp = (float)(k.s2 * (k.ar2 + k.z * (a2 * k.s2)));
+    mm.g_rp = (float)(-(a * k.s2 * k.opz));
+    mm.gi_rr = gu.rr;
+    mm.gi_rp = gu.rp;
+    mm.gi_tt = gu.tt;
+    mm.gi_pp = gu.pp;
+    mm.sqrtg = (float)(k.rho2 * s * k.opz * k.alpha);
+    if (PUSHER) {
+        const VayMetric<float> vm{mm.alpha, mm.g_rr, mm.g_rp, mm.g_tt, mm.g_pp, mm.gi_rr, mm.gi_rp, mm.gi_tt,
+                                  mm.gi_pp, mm.sqrtg};
+        vay_step<float>(vm, qm, dt, D, B, u);
+    } else {
+        boris32<float>(mm, qm, dt, D, B, u);
+    }
+}
+
+// The push of one particle of the near-horizon island with the metric in
+// double-FP32 pairs: the steps of push_fp32 with the point quantities and
+// gamma^ij from point_island (r as the pair r_i + (r - r_i), sin and cos of
+// theta in pairs from the row table shifted by the offset), the right-hand
+// sides by rhs32g.
+template <int PUSHER>
+__device__ __forceinline__ void push_island_df(const Push32Args &A, int i, int j, float &o1, float &o2, float u[3],
+                                               int sp, float &dphi, bool pole, float &q)
+{
+    const float2 rc2 = __ldg(reinterpret_cast<const float2 *>(A.rcol2) + i + NG);
+    const df rc(rc2.x, rc2.y);
+    const float rcf = __fadd_rn(rc2.x, rc2.y);
+    const float d0 = rcf * expm1_cell(o1 * A.dx1f, A.dx1f);  // r - r_i
+    const float t0 = pole ? q : o2;
+    const float4 sc = __ldg(reinterpret_cast<const float4 *>(A.rowsc) + (pole ? 0 : j));
+    df s0, c0;
+    sincos_shift_df(df(sc.x, sc.y), df(sc.z, sc.w), mul(A.dth_df, t0), s0, c0);
+    if (pole) c0 = -c0;
+    Pt32 m0;
+    GUp32 g0;
+    IslandPt keep;
+    point_island(A.a_df, A.a2_df, A.m2a2f, add_f(rc, d0), s0, c0, m0, g0, &keep);
+    if (A.massive[sp] && A.qm[sp] != 0.0f) {
+        float Dv[3], Bv[3];
+        gather_fields32(A, i, j, o1, o2, Dv, Bv);
+        boris_island_pt<PUSHER>(m0, g0, keep, A.a_df, A.a2_df, s0, A.qm[sp], A.dt, Dv, Bv, u);
+    }
+    const float eps = A.massive[sp] ? 1.0f : 0.0f;
+    const float dt = A.dt, h = 0.5f * dt;
+    const float up = u[2];
+    RhsT<float> f0, ft;
+    rhs32g(m0, g0, eps, u[0], u[1], up, f0);
+    const float sth = pole ? -A.idthf : A.idthf;
+    const df dsg = pole ? -A.dth_df : A.dth_df;
+    const float hsth = h * sth;
+    float a1 = fmaf(dt, f0.xr, d0), a2 = fmaf(dt * sth, f0.xt, t0);
+    float b1 = fmaf(dt, f0.ur, u[0]), b2 = fmaf(dt, f0.ut, u[1]);
+    float xpl = f0.xp;
+    const float trc = A.tolf * rcf;
+    for (int it = 0; it < A.n_iter; ++it) {
+        const df d = two_sum(a2, -t0) * dsg;  // theta - theta^n
+        df s, c;
+        if (fabs_hi(d) <= 0.1f) {
+            sincos_shift_df(s0, c0, d, s, c);
+        } else if (pole) {
+            sincos_t(mul(A.dth_df, t0) - d, &s, &c);  // theta' = pi - theta
+            c = -c;
+        } else {
+            sincos_t(df(j) * A.dth_df + mul(A.dth_df, t0) + d, &s, &c);
+        }
+        Pt32 mi;
+        GUp32 gi;
+        point_island(A.a_df, A.a2_df, A.m2a2f, add_f(rc, a1), s, c, mi, gi, nullptr);
+        rhs32g(mi, gi, eps, b1, b2, up, ft);
+        xpl = ft.xp;
+        const float n1 = fmaf(h, ft.xr + f0.xr, d0), n2 = fmaf(hsth, ft.xt + f0.xt, t0);
+        const float nb1 = fmaf(h, ft.ur + f0.ur, u[0]), nb2 = fmaf(h, ft.ut + f0.ut, u[1]);
+        bool done = false;
+        if (A.use_tol) {
+            const float t = A.tolf;
+            done = fabsf(n1 - a1) < trc && fabsf(n2 - a2) < t && fabsf(nb1 - b1) < t * fmaxf(1.0f, fabsf(nb1)) &&
+                   fabsf(nb2 - b2) < t * fmaxf(1.0f, fabsf(nb2));
+        }
+        a1 = n1;
+        a2 = n2;
+        b1 = nb1;
+        b2 = nb2;
+        if (done) break;
+    }
+    o1 = log1p_cell(__fdividef(a1, rcf)) * A.idx1f;
+    if (pole)
+        q = a2;
+    else
+        o2 = a2;
+    u[0] = b1;
+    u[1] = b2;
+    dphi = h * (xpl + f0.xp);
 }
 
 // resident 256-thread blocks per SM the register allocation is sized for
@@ -644,9 +672,9 @@ __global__ void __launch_bounds__(256, GRPIC_PUSH32_MINB) push32_kernel(Push32Ar
         if (i >= A.i64)
             push_fp32<PUSHER>(A, i, j, n1, n2, u, sp, dphi, pole, q);
         else if (A.island_fp64)
-            push_one<double, PUSHER>(A, i, j, n1, n2, u, sp, dphi, pole, q);
+            push_island_fp64<PUSHER>(A, i, j, n1, n2, u, sp, dphi, pole, q);
         else
-            push_one<df, PUSHER>(A, i, j, n1, n2, u, sp, dphi, pole, q);
+            push_island_df<PUSHER>(A, i, j, n1, n2, u, sp, dphi, pole, q);
         // axis reflection (theta = 0 is o2 = 0 of row 0, theta = pi is q = 0
         // of the last row); the end point relative to the start row's lower edge
         if (j == 0 && n2 < 0.0f) { n2 = -n2; u[1] = -u[1]; }
