@@ -612,19 +612,21 @@ __device__ __forceinline__ void push_island_df(const Push32Args &A, int i, int j
 
 // PUSHER: 0 generalized Boris, 1 Vay in the FIDO frame; IX: the slot index
 // type (uint32_t while the capacity is below 2^31, int64_t beyond)
+// slots per thread: a block of 256 threads takes GRPIC_PUSH32_PPT consecutive
+// runs of 256 slots in turn (the per-thread setup is paid once for them)
+#ifndef GRPIC_PUSH32_PPT
+#define GRPIC_PUSH32_PPT 8
+#endif
+
+// one slot of the push (all 32 lanes of a warp call it: the deposit and the
+// counts are warp collectives)
 template <int PUSHER, typename IX>
-__global__ void __launch_bounds__(256, GRPIC_PUSH32_MINB) push32_kernel(Push32Args A)
+__device__ __forceinline__ void push_slot(const Push32Args &A, const IX p, const IX nx, const bool permuted)
 {
     const GridDev &g = A.g;
-    const bool permuted = A.perm != nullptr;
-    int64_t n = permuted ? (int64_t)*A.live : (A.d_count ? *A.d_count : A.n);
-    if (n > A.n) n = A.n;
-    const IX nx = (IX)n;
-    const IX p = (IX)blockIdx.x * blockDim.x + threadIdx.x;
     const unsigned FULL = 0xffffffffu;
     int lane = threadIdx.x & 31;
     int ncell = g.nr * g.nth;
-    if (permuted && p == 0 && A.count_out) *A.count_out = n;
 
     bool live = false;
     uint32_t tag = DEAD;
@@ -761,6 +763,19 @@ __global__ void __launch_bounds__(256, GRPIC_PUSH32_MINB) push32_kernel(Push32Ar
                                  A.J1, A.J2);
 }
 
+template <int PUSHER, typename IX>
+__global__ void __launch_bounds__(256, GRPIC_PUSH32_MINB) push32_kernel(Push32Args A)
+{
+    const bool permuted = A.perm != nullptr;
+    int64_t n = permuted ? (int64_t)*A.live : (A.d_count ? *A.d_count : A.n);
+    if (n > A.n) n = A.n;
+    const IX nx = (IX)n;
+    const IX p0 = (IX)blockIdx.x * (blockDim.x * GRPIC_PUSH32_PPT) + threadIdx.x;
+    if (permuted && p0 == 0 && A.count_out) *A.count_out = n;
+#pragma unroll 1
+    for (int k = 0; k < GRPIC_PUSH32_PPT; ++k) push_slot<PUSHER, IX>(A, p0 + (IX)(k * blockDim.x), nx, permuted);
+}
+
 }  // namespace
 
 cudaError_t launch_push32(grpic_ctx *ctx, const grpic_particles *in, grpic_particles *p, const int32_t *perm,
@@ -834,8 +849,8 @@ cudaError_t launch_push32(grpic_ctx *ctx, const grpic_particles *in, grpic_parti
     A.status = ctx->d_status;
     A.nr_recip = ~0ull / (unsigned long long)ctx->g.nr + 1ull;
     if (p->n <= 0) return cudaSuccess;
-    const unsigned blocks = (unsigned)((p->n + 255) / 256);
-    const bool narrow = p->capacity < ((int64_t)1 << 31) - 256;
+    const unsigned blocks = (unsigned)((p->n + 256 * GRPIC_PUSH32_PPT - 1) / (256 * GRPIC_PUSH32_PPT));
+    const bool narrow = p->capacity < ((int64_t)1 << 31) - 256 * GRPIC_PUSH32_PPT;
     if (ctx->prm.pusher) {
         if (narrow)
             push32_kernel<1, uint32_t><<<blocks, 256, 0, s>>>(A);

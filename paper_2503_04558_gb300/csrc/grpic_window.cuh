@@ -96,7 +96,6 @@ __device__ __forceinline__ void deposit_warp_split(bool dep, int i0, int j0, int
         T v[8];
 #pragma unroll
         for (int k = 0; k < 8; ++k) v[k] = in ? core[k] : T(0);
-        int base = 0;
 #pragma unroll
         for (int st = 0, half = 4, m = 16; st < 3; ++st, half >>= 1, m >>= 1) {
             const bool hi = lane & m;
