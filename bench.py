@@ -353,10 +353,29 @@ def run_e2e(e2e_steps, ctx, S, F, cfg, stream, reps=2):
         torch.cuda.synchronize()
         runs.append(start.elapsed_time(stop) / e2e_steps)
     del dev_state, dev_fields
+    # the host link's plain copy rate on this machine (1 GiB pinned, each way alone
+    # and both at once), the context of the end-to-end figure
+    nb = 1 << 30
+    hb, hb2 = torch.empty(nb, dtype=torch.uint8, pin_memory=True), torch.empty(nb, dtype=torch.uint8, pin_memory=True)
+    db, db2 = torch.empty(nb, dtype=torch.uint8, device=S.a.x1.device), torch.empty(nb, dtype=torch.uint8,
+                                                                                  device=S.a.x1.device)
+    s2 = torch.cuda.Stream()
+    link = {}
+    for kind in ("h2d", "d2h", "both"):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        if kind in ("h2d", "both"):
+            db.copy_(hb, non_blocking=True)
+        if kind in ("d2h", "both"):
+            with torch.cuda.stream(s2):
+                hb2.copy_(db2, non_blocking=True)
+        torch.cuda.synchronize()
+        link[kind + "_gbs"] = nb * (2 if kind == "both" else 1) / (time.perf_counter() - t0) / 1e9
+    del hb, hb2, db, db2
     ms = min(runs)
     return {"value": n / (ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": b_in // e2e_steps,
             "d2h_bytes_per_step": b_out // e2e_steps, "ms_per_step": ms, "steps": e2e_steps,
-            "runs_ms_per_step": runs,
+            "runs_ms_per_step": runs, "host_link": link,
             "path": "grpic_step_host: pinned host particle arrays and D, B copied in and out every step"}
 
 

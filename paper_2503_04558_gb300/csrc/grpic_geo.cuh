@@ -139,9 +139,9 @@ __device__ __forceinline__ void geo_rhs_m(const KSGeo<M> &m, T eps, T ur, T ut, 
            h * (ur * ur * (T)m.dgrr_t + T(2) * ur * up * (T)m.dgrp_t + ut * ut * (T)m.dgtt_t + up * up * (T)m.dgpp_t);
 }
 
-// The FP32 form's right-hand side, split into the quantities of the point
-// (r, sin theta, cos theta) -- shared by the Boris step and the right-hand
-// side at x^n -- and the part that depends on u.  With
+// The right-hand side of the FP32 form and of the FP64 path, split into the
+// quantities of the point (r, sin theta, cos theta) -- shared by the Boris
+// step and the right-hand side at x^n -- and the part that depends on u.  With
 //   P = (a^2 + r^2) u_r^2 + 2 a u_r u_ph + u_th^2 + u_ph^2 / sin^2,
 // gamma^{jk} u_j u_k = P / rho^2 - beta u_r^2 (gamma^{jk} of App. A), so that
 // with Q = eps + gamma^{jk} u_j u_k: alpha u^0 = sqrt(Q), 1/u^0 = alpha / sqrt(Q).
@@ -153,54 +153,86 @@ __device__ __forceinline__ void geo_rhs_m(const KSGeo<M> &m, T eps, T ur, T ut, 
 // (1+z)^-2 d_i z), and the remaining derivatives of P / rho^2 give
 //   U_r  = K d_r z + h z (P / rho^2 - u_r^2),
 //   U_th = E (h P / rho^2 - K z) + (1/u^0) rho^-2 sin cos sin^-4 u_ph^2
-// (d_th sin^-2 = -2 sin cos / sin^4).  Reciprocals and reciprocal square
-// roots take the hardware approximations (a few ulp, inside the FP32 form's
-// budget); 1/(1+z) lies in (0, 1].
-struct Pt32 {
-    float s, rho2, ir, z, opz, al, iopz, beta, s2, is2, ar2, cs, E;
-};
-
-__device__ __forceinline__ Pt32 point32(float a2, float m2a2, float r, float s, float c)
+// (d_th sin^-2 = -2 sin cos / sin^4).  1/(1+z) lies in (0, 1].
+//
+// Per type: the reciprocal and reciprocal square root the right-hand side
+// takes (FP32: the hardware approximations; FP64: an FP32 seed refined by
+// two Newton steps, the residual formed by a fused multiply-add, relative
+// error a few ulp of FP64; arguments within FP32's normal range) and the
+// fused multiply-add
+__device__ __forceinline__ float rcp_fast(float x) { return __fdividef(1.0f, x); }
+__device__ __forceinline__ double rcp_fast(double x) { return rcp_t(x); }
+__device__ __forceinline__ float rsqrt_fast(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double rsqrt_fast(double x)
 {
-    Pt32 m;
-    const float r2 = r * r;
+    double y = (double)rsqrtf((float)x);  // 2^-22
+    double e = fma(-x * y, y, 1.0);       // 1 - x y^2
+    y = fma(0.5 * y, e, y);               // 2^-43
+    e = fma(-x * y, y, 1.0);
+    return fma(0.5 * y, e, y);
+}
+__device__ __forceinline__ float fmat(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double fmat(double a, double b, double c) { return fma(a, b, c); }
+
+template <typename T>
+struct PtT {
+    T s, rho2, ir, z, opz, al, iopz, beta, s2, is2, ar2, cs, E;
+};
+using Pt32 = PtT<float>;
+
+template <typename T>
+__device__ __forceinline__ PtT<T> pointT(T a2, T m2a2, T r, T s, T c)
+{
+    PtT<T> m;
+    const T r2 = r * r;
     m.s = s;
-    m.rho2 = fmaf(a2 * c, c, r2);
-    m.ir = __fdividef(1.0f, m.rho2);
+    m.rho2 = fmat(a2 * c, c, r2);
+    m.ir = rcp_fast(m.rho2);
     m.z = (r + r) * m.ir;
-    m.opz = 1.0f + m.z;
-    m.al = rsqrtf(m.opz);
+    m.opz = T(1) + m.z;
+    m.al = rsqrt_fast(m.opz);
     m.iopz = m.al * m.al;
     m.beta = m.z * m.iopz;
     m.s2 = s * s;
-    m.is2 = __fdividef(1.0f, m.s2);
+    m.is2 = rcp_fast(m.s2);
     m.ar2 = a2 + r2;
     m.cs = c * s;
     m.E = m2a2 * m.cs * m.ir;  // m2a2 = -2 a^2
     return m;
 }
 
+__device__ __forceinline__ Pt32 point32(float a2, float m2a2, float r, float s, float c)
+{
+    return pointT<float>(a2, m2a2, r, s, c);
+}
+
 // aup = a u_ph (u_ph is fixed during the correctors)
+template <typename T>
+__device__ __forceinline__ void rhsT(const PtT<T> &m, T a, T eps, T ur, T ut, T up, T aup, RhsT<T> &f)
+{
+    const T ur2 = ur * ur;
+    const T is2up = m.is2 * up;
+    const T is2up2 = is2up * up;
+    const T w = fmat(m.ar2, ur, aup);                          // (a^2 + r^2) u_r + a u_ph
+    const T P = fmat(ur, w + aup, fmat(ut, ut, is2up2));
+    const T irP = m.ir * P;
+    const T Q = fmat(m.ir, P, fmat(-m.beta, ur2, eps));
+    const T qq = rsqrt_fast(Q);
+    const T iu0 = m.al * qq;                                   // 1 / u^0
+    const T h = T(0.5) * iu0;
+    const T iri = m.ir * iu0;
+    f.xr = fmat(iu0, fmat(m.ir, w, -m.beta * ur), -m.beta);
+    f.xt = iri * ut;
+    f.xp = iri * fmat(a, ur, is2up);
+    const T K = m.iopz * fmat(m.iopz * ur, fmat(h, ur, T(1)), h * Q);
+    f.ur = fmat(K, fmat(-m.z, m.z, m.ir + m.ir), h * m.z * (irP - ur2));
+    f.ut = fmat(m.E, fmat(-K, m.z, h * irP), iri * (m.cs * m.is2) * is2up2);
+}
+
 __device__ __forceinline__ void rhs32(const Pt32 &m, float a, float eps, float ur, float ut, float up, float aup,
                                       RhsT<float> &f)
 {
-    const float ur2 = ur * ur;
-    const float is2up = m.is2 * up;
-    const float is2up2 = is2up * up;
-    const float w = fmaf(m.ar2, ur, aup);                          // (a^2 + r^2) u_r + a u_ph
-    const float P = fmaf(ur, w + aup, fmaf(ut, ut, is2up2));
-    const float irP = m.ir * P;
-    const float Q = fmaf(m.ir, P, fmaf(-m.beta, ur2, eps));
-    const float qq = rsqrtf(Q);
-    const float iu0 = m.al * qq;                                   // 1 / u^0
-    const float h = 0.5f * iu0;
-    const float iri = m.ir * iu0;
-    f.xr = fmaf(iu0, fmaf(m.ir, w, -m.beta * ur), -m.beta);
-    f.xt = iri * ut;
-    f.xp = iri * fmaf(a, ur, is2up);
-    const float K = m.iopz * fmaf(m.iopz * ur, fmaf(h, ur, 1.0f), h * Q);
-    f.ur = fmaf(K, fmaf(-m.z, m.z, m.ir + m.ir), h * m.z * (irP - ur2));
-    f.ut = fmaf(m.E, fmaf(-K, m.z, h * irP), iri * (m.cs * m.is2) * is2up2);
+    rhsT<float>(m, a, eps, ur, ut, up, aup, f);
 }
 
 // The same right-hand side from the upper metric's values given apart

@@ -67,104 +67,45 @@ struct Push64Args {
     int64_t tape_ld;
 };
 
-struct Rhs {
-    double xr, xt, xp, ur, ut;
-};
+using Rhs = RhsT<double>;
+using Pt64 = PtT<double>;
 
-// Right-hand sides of Eq. particle-eom without F_i, with the analytic
-// Kerr-Schild derivatives of alpha, beta^r and gamma^{jk}.
-// the metric pieces at (r, theta) that the Boris step and the right-hand side
-// share: a^2, r^2, rho^2, 1/rho^2, z = 2 r / rho^2, 1 + z, 1/(1+z), alpha =
-// (1+z)^-1/2, beta = z/(1+z), 1/sin^2
-struct KSBase {
-    double a2, r2, rho2, ir, z, opz, iopz, alpha, beta, is2;
-};
-__device__ __forceinline__ void ks_base(double a, double r, double s, double c, KSBase &b)
+// the right-hand side of Eq. particle-eom (without F_i) at a point: the
+// point quantities and the part in u of grpic_geo.cuh's pointT / rhsT
+__device__ __forceinline__ void geo_rhs_sc(double a, double a2, double m2a2, double eps, double r, double s, double c,
+                                           double ur, double ut, double up, Rhs &f)
 {
-    b.a2 = a * a;
-    b.r2 = r * r;
-    b.rho2 = b.r2 + b.a2 * c * c;
-    b.ir = rcp_t(b.rho2);
-    b.z = 2.0 * r * b.ir;
-    b.opz = 1.0 + b.z;
-    b.iopz = rcp_t(b.opz);
-    b.alpha = sqrt(b.iopz);
-    b.beta = b.z * b.iopz;
-    b.is2 = rcp_t(s * s);
+    const Pt64 m = pointT<double>(a2, m2a2, r, s, c);
+    rhsT<double>(m, a, eps, ur, ut, up, a * up, f);
 }
 
-__device__ __forceinline__ void geo_rhs_b(double a, double eps, double r, double s, double c, const KSBase &B,
-                                          double ur, double ut, double up, Rhs &f)
+// the 3+1 metric at the point (App. A): gamma_rr = 1 + z, gamma_thth = rho^2,
+// gamma_rph = -a sin^2 (1 + z), gamma_phph = Sigma sin^2 / rho^2 with Sigma =
+// (a^2 + r^2) rho^2 + 2 r a^2 sin^2 (the same Sigma as (a^2 + r^2)^2 - a^2
+// Delta sin^2, without its cancellation), so gamma_phph = sin^2 (a^2 + r^2 +
+// z a^2 sin^2); sqrt(gamma) = rho^2 sin (1 + z) alpha
+__device__ __forceinline__ void ks_point_pt(double a, double a2, const Pt64 &B, KS &m)
 {
-    const double a2 = B.a2, r2 = B.r2, ir = B.ir, z = B.z, iopz = B.iopz, alpha = B.alpha, beta = B.beta,
-                 is2 = B.is2;
-    double ir2 = ir * ir;
-    double drho_t = -2.0 * a2 * c * s;
-    double dz_r = 2.0 * ir * (1.0 - 2.0 * r2 * ir);
-    double dz_t = -2.0 * r * drho_t * ir2;
-    double ka = -0.5 * alpha * iopz;  // d alpha / dz
-    double kb = iopz * iopz;          // d beta / dz
-    double da_r = ka * dz_r, da_t = ka * dz_t;
-    double db_r = kb * dz_r, db_t = kb * dz_t;
-    // gamma^{jk} = rho^-2 [(a^2 + r^2, a, 1, 1/sin^2) in (rr, r phi, th th,
-    // phi phi)] - beta dr dr, so with P = (a^2 + r^2) u_r^2 + 2 a u_r u_ph
-    // + u_th^2 + u_ph^2 / sin^2 the forms in u of gamma^{jk} and of its r and
-    // theta derivatives collect into
-    //   gamma^{jk} u_j u_k        = P / rho^2 - beta u_r^2,
-    //   d_r gamma^{jk} u_j u_k    = u_r^2 (z - d_r beta) - 2 r P / rho^4,
-    //   d_th gamma^{jk} u_j u_k   = -d_th rho^2 P / rho^4 - d_th beta u_r^2
-    //                               - 2 sin cos u_ph^2 / (rho^2 sin^4)
-    double ur2 = ur * ur, up2 = up * up;
-    double P = (a2 + r2) * ur2 + 2.0 * a * ur * up + ut * ut + up2 * is2;
-    double uu = ir * P - beta * ur2;
-    double au0 = sqrt(eps + uu);   // alpha u^0
-    double iu0 = alpha * rcp_t(au0);  // 1 / u^0
-    double grp = a * ir;
-    f.xr = (((a2 + r2) * ir - beta) * ur + grp * up) * iu0 - beta;
-    f.xt = ir * ut * iu0;
-    f.xp = (grp * ur + ir * is2 * up) * iu0;
-    double h = 0.5 * iu0;
-    double Qr = ur2 * (z - db_r) - 2.0 * r * ir2 * P;
-    double Qt = -drho_t * ir2 * P - db_t * ur2 - 2.0 * s * c * ir * is2 * is2 * up2;
-    f.ur = -au0 * da_r + ur * db_r - h * Qr;
-    f.ut = -au0 * da_t + ur * db_t - h * Qt;
-}
-
-__device__ __forceinline__ void geo_rhs_sc(double a, double eps, double r, double s, double c, double ur, double ut,
-                                           double up, Rhs &f)
-{
-    KSBase B;
-    ks_base(a, r, s, c, B);
-    geo_rhs_b(a, eps, r, s, c, B, ur, ut, up, f);
-}
-
-// the 3+1 metric at (r, theta) from sin, cos of theta (reciprocals by the
-// FP32 seed and two Newton steps of rcp_t)
-__device__ __forceinline__ void ks_point_b(double a, double r, double s, const KSBase &B, KS &m)
-{
-    const double s2 = s * s;
-    const double Dl = B.r2 + B.a2 - 2.0 * r;
-    const double Sg = (B.r2 + B.a2) * (B.r2 + B.a2) - B.a2 * Dl * s2;
-    m.alpha = B.alpha;
+    m.alpha = B.al;
     m.beta = B.beta;
     m.g_rr = B.opz;
     m.g_tt = B.rho2;
-    m.g_pp = Sg * s2 * B.ir;
-    m.g_rp = -a * s2 * B.opz;
-    m.gi_rr = (B.a2 + B.r2) * B.ir - B.beta;
+    m.g_pp = B.s2 * fma(B.z, a2 * B.s2, B.ar2);
+    m.g_rp = -a * B.s2 * B.opz;
+    m.gi_rr = fma(B.ar2, B.ir, -B.beta);
     m.gi_rp = a * B.ir;
     m.gi_tt = B.ir;
     m.gi_pp = B.ir * B.is2;
-    m.sqrtg = B.rho2 * s * B.opz * B.alpha;  // rho^2 sin sqrt(1+z), sqrt(1+z) = (1+z) alpha
+    m.sqrtg = B.rho2 * B.s * B.opz * B.al;
 }
 
 // Generalized Boris step over dt at the particle (u covariant, D, B
-// contravariant); s, c = sin, cos of theta
-__device__ __forceinline__ void boris(double a, double r, double s, const KSBase &Bm, double qm, double dt,
-                                      const double D[3], const double B[3], double u[3])
+// contravariant) with the point quantities at x^n
+__device__ __forceinline__ void boris(double a, double a2, const Pt64 &Bm, double qm, double dt, const double D[3],
+                                      const double B[3], double u[3])
 {
     KS m;
-    ks_point_b(a, r, s, Bm, m);
+    ks_point_pt(a, a2, Bm, m);
     double Dl0 = m.g_rr * D[0] + m.g_rp * D[2];
     double Dl1 = m.g_tt * D[1];
     double Dl2 = m.g_rp * D[0] + m.g_pp * D[2];
@@ -172,7 +113,7 @@ __device__ __forceinline__ void boris(double a, double r, double s, const KSBase
     double um0 = u[0] + h * Dl0, um1 = u[1] + h * Dl1, um2 = u[2] + h * Dl2;
     // raised u^-
     double v0 = m.gi_rr * um0 + m.gi_rp * um2, v1 = m.gi_tt * um1, v2 = m.gi_rp * um0 + m.gi_pp * um2;
-    double iu0b = m.alpha * rcp_t(sqrt(1.0 + um0 * v0 + um1 * v1 + um2 * v2));  // 1 / u0bar
+    double iu0b = m.alpha * rsqrt_fast(1.0 + um0 * v0 + um1 * v1 + um2 * v2);  // 1 / u0bar
     double kt = 0.5 * qm * dt * iu0b;
     double t0 = kt * B[0], t1 = kt * B[1], t2 = kt * B[2];
     double tt = t0 * (m.g_rr * t0 + m.g_rp * t2) + t1 * (m.g_tt * t1) + t2 * (m.g_rp * t0 + m.g_pp * t2);
@@ -314,8 +255,8 @@ __global__ void __launch_bounds__(256) push64_kernel(Push64Args A)
         // right-hand side, shifted for the corrector iterates
         double s0, c0;
         sincos(th, &s0, &c0);
-        KSBase B0;
-        ks_base(g.a, r, s0, c0, B0);
+        const double a2 = g.a * g.a, m2a2 = -2.0 * a2;
+        const Pt64 B0 = pointT<double>(a2, m2a2, r, s0, c0);
         if (A.massive[sp] && A.qm[sp] != 0.0) {
             double Dv[3], Bv[3];
             if constexpr (SHAPE == 3) {
@@ -337,7 +278,7 @@ __global__ void __launch_bounds__(256) push64_kernel(Push64Args A)
             if (A.pusher)
                 vay(g.a, r, th, A.qm[sp], A.dt, Dv, Bv, u);
             else
-                boris(g.a, r, s0, B0, A.qm[sp], A.dt, Dv, Bv, u);
+                boris(g.a, a2, B0, A.qm[sp], A.dt, Dv, Bv, u);
         }
         // geodesic predictor-corrector (Sec. 2.2)
         double eps = A.massive[sp] ? 1.0 : 0.0;
@@ -351,7 +292,7 @@ __global__ void __launch_bounds__(256) push64_kernel(Push64Args A)
             tape[TAPE_SC0 * tl] = s0;
             tape[(TAPE_SC0 + 1) * tl] = c0;
         }
-        geo_rhs_b(g.a, eps, r, s0, c0, B0, u[0], u[1], u[2], f0);
+        rhsT<double>(B0, g.a, eps, u[0], u[1], u[2], g.a * u[2], f0);
         double dt = A.dt;
         double rt = r + dt * f0.xr, tt = th + dt * f0.xt, pt = dt * f0.xp;
         double urt = u[0] + dt * f0.ur, utt = u[1] + dt * f0.ut;
@@ -374,7 +315,7 @@ __global__ void __launch_bounds__(256) push64_kernel(Push64Args A)
                 q[4 * tl] = st;
                 q[5 * tl] = ct;
             }
-            geo_rhs_sc(g.a, eps, rt, st, ct, urt, utt, u[2], ft);
+            geo_rhs_sc(g.a, a2, m2a2, eps, rt, st, ct, urt, utt, u[2], ft);
             double h = 0.5 * dt;
             rt = r + h * (ft.xr + f0.xr);
             tt = th + h * (ft.xt + f0.xt);
