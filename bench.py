@@ -53,8 +53,8 @@ B0 = 1.0
 # kernels (flop = 2 FMA + MUL + ADD of the SASS instruction counters) in one
 # capture of a smaller case of the same workload (same spin, radial range and
 # island fraction), and scaled to a launch by the number of particles.
-PUSH64_FP64_FLOP = 1181.1   # FP64 push, 512^2 x 64 ppc split monopole
-PUSH64_DRAM_B = 95.7        # the same capture: DRAM bytes per particle (read + write)
+PUSH64_FP64_FLOP = 1039.3   # FP64 push, 512^2 x 64 ppc split monopole
+PUSH64_DRAM_B = 95.6        # the same capture: DRAM bytes per particle (read + write)
 PUSH32_FP32_FLOP = 661.0    # FP32-form push, 1024^2 x 64 ppc split monopole
 # the same capture: instructions issued per particle (warp instructions x 32)
 # and DRAM bytes per particle (read + write)
@@ -77,8 +77,8 @@ B1_ALG_B = 2 * 28
 # x 16 ppc, Wald a = 0.99, B0 = 500)
 VAY32_FP32_FLOP = 718.7
 VAY32_INST = 1221.1
-CUBIC64_FP64_FLOP = 1772.0
-RAD64_FP64_FLOP = 1401.5
+CUBIC64_FP64_FLOP = 1471.4
+RAD64_FP64_FLOP = 1248.5
 VAY_COUNT = "ncu SASS counters, FP32-form push with Vay's update, 1024^2 x 64 ppc"
 CUBIC_COUNT = "ncu SASS counters, FP64 push with the cubic shape, 512^2 x 64 ppc"
 RAD_COUNT = "ncu SASS counters, FP64 push with emission/conversion decisions, 512^2 x 16 ppc"
