@@ -55,11 +55,11 @@ B0 = 1.0
 # island fraction), and scaled to a launch by the number of particles.
 PUSH64_FP64_FLOP = 1039.3   # FP64 push, 512^2 x 64 ppc split monopole
 PUSH64_DRAM_B = 95.6        # the same capture: DRAM bytes per particle (read + write)
-PUSH32_FP32_FLOP = 661.0    # FP32-form push, 1024^2 x 64 ppc split monopole
+PUSH32_FP32_FLOP = 668.8    # FP32-form push, 1024^2 x 64 ppc split monopole
 # the same capture: instructions issued per particle (warp instructions x 32)
 # and DRAM bytes per particle (read + write)
-PUSH32_INST = 1145.3
-PUSH32_DRAM_B = 66.0
+PUSH32_INST = 1149.4
+PUSH32_DRAM_B = 67.6
 # batched 1D lines, b1_kernel with the cascade running (256 lines x 4096 cells):
 # instructions issued per particle-step (warp instructions x 32) and DRAM
 # bytes per particle-step; algorithmic bytes: the particle record (cell, offset,
@@ -75,8 +75,8 @@ B1_ALG_B = 2 * 28
 # Vay's update (1024^2 x 64 ppc), the FP64 push with the cubic shape (512^2 x
 # 64 ppc), the FP64 push with photon emission and conversion decisions (512^2
 # x 16 ppc, Wald a = 0.99, B0 = 500)
-VAY32_FP32_FLOP = 718.7
-VAY32_INST = 1221.1
+VAY32_FP32_FLOP = 726.5
+VAY32_INST = 1225.5
 CUBIC64_FP64_FLOP = 1471.4
 RAD64_FP64_FLOP = 1248.5
 VAY_COUNT = "ncu SASS counters, FP32-form push with Vay's update, 1024^2 x 64 ppc"
