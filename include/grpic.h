@@ -261,8 +261,9 @@ grpic_status grpic_step_graph(grpic_ctx *ctx, grpic_particles *p, grpic_particle
  *   bytes: NULL or two int64 receiving the bytes copied host to device and
  *     device to host over the call.
  * The slot range is copied in chunks on two streams of the context (host to
- * device, device to host), and a step's copy in of a chunk waits only for the
- * previous step's copy out of the same slots, so the directions overlap.
+ * device, device to host), a step's copy in of a chunk waits only for the
+ * previous step's copy out of the same slots, so the directions overlap, and
+ * the push runs chunk by chunk as the copies land (D and B first).
  * The host arrays are ready once `stream` has completed (the call
  * synchronizes `stream` once per step to read the live count).  Radiation
  * and injection contexts: GRPIC_EINVAL.  A failing step's status is returned

@@ -645,6 +645,63 @@ grpic_status grpic_step_graph(grpic_ctx *ctx, grpic_particles *p, grpic_particle
     return drop_pending(ctx, st);
 }
 
+// One step of grpic_step_host: the in-place push of push_impl over the slot
+// range in chunks, chunk c launched once its copy in (event in[c]) has landed,
+// then the field update and a sort that moves the data.
+static grpic_status step_one_chunks(grpic_ctx *ctx, grpic_particles *p, grpic_particles *scratch, grpic_fields *f,
+                                    int nch, int64_t chunk, const cudaEvent_t *in, cudaStream_t s)
+{
+    if (ctx->pending_perm) return fail(ctx, GRPIC_EINVAL, "grpic_step_host: a sort's order is pending");
+    const int64_t ncell = (int64_t)ctx->g.nr * ctx->g.nth;
+    const int every = ctx->prm.sort_every;
+    const bool sort_now = every > 0 && ((ctx->step_count + 1) % every == 0);
+    cudaEvent_t *ev = timing_slot(ctx);
+    if (ev) cudaEventRecord(ev[0], s);
+    const bool neighbour_next = p->n > 0 && p->tag && p->tag == ctx->sorted_tag && ctx->pushes_since_sort == 0;
+    const bool histogram = sort_now && !neighbour_next;
+    grpic_status st = ensure_particle_scratch(ctx, p->n);
+    if (st) return st;
+    const size_t bytes = (size_t)(ctx->g.nth + 1) * f->ld * fsize(ctx);
+    for (int k = 0; k < 3; ++k) cudaMemsetAsync(f->J[k], 0, bytes, s);
+    if (histogram) cudaMemsetAsync(ctx->d_count, 0, sizeof(int32_t) * (ncell + 1), s);
+    ctx->counts_ready = 0;
+    const size_t es = ctx->prm.precision == 64 ? 8 : 4;
+    cudaError_t e = cudaSuccess;
+    for (int c = 0; c < nch && e == cudaSuccess; ++c) {
+        const int64_t lo = c * chunk, hi = std::min(p->n, lo + chunk);
+        e = cudaStreamWaitEvent(s, in[c], 0);
+        grpic_particles q = *p;
+        q.n = hi - lo;
+        q.capacity = hi - lo;
+        q.d_count = nullptr;
+        q.x1 = static_cast<char *>(p->x1) + lo * es;
+        q.x2 = static_cast<char *>(p->x2) + lo * es;
+        q.u1 = static_cast<char *>(p->u1) + lo * es;
+        q.u2 = static_cast<char *>(p->u2) + lo * es;
+        q.u3 = static_cast<char *>(p->u3) + lo * es;
+        q.tag = p->tag + lo;
+        q.cell = p->cell ? p->cell + lo : nullptr;
+        if (e == cudaSuccess)
+            e = (ctx->prm.precision == 64) ? launch_push64(ctx, &q, &q, nullptr, nullptr, nullptr, f, histogram, s, lo)
+                                           : launch_push32(ctx, &q, &q, nullptr, nullptr, nullptr, f, histogram, s, lo);
+    }
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "push");
+    ctx->keys_valid = 1;
+    ctx->hist_valid = histogram ? 1 : 0;
+    ctx->keys_tag = p->tag;
+    ctx->pushes_since_sort = (p->tag == ctx->sorted_tag) ? ctx->pushes_since_sort + 1 : 2;
+    if (ev) cudaEventRecord(ev[1], s);
+    st = field_impl(ctx, f, s);
+    if (ev) cudaEventRecord(ev[2], s);
+    if (!st && sort_now) st = sort_impl(ctx, p, scratch, s, true);
+    if (ev) {
+        cudaEventRecord(ev[3], s);
+        ctx->tsteps++;
+    }
+    if (!st) ctx->step_count++;
+    return st;
+}
+
 // ---------------------------------------------------------------------------
 // Steps with a host-resident particle state (grpic_step_host).  The slot range
 // is cut into chunks; each step copies the chunks in on up_stream, runs one
@@ -713,8 +770,9 @@ grpic_status grpic_step_host(grpic_ctx *ctx, grpic_particles *host, grpic_partic
         ctx->hevents = new (std::nothrow) std::vector<cudaEvent_t>();
         if (!ctx->hevents) return fail(ctx, GRPIC_ENOMEM, "grpic_step_host: events");
     }
-    // events: [0, HOST_CHUNKS_MAX) chunks out, then fields out, copies in, step done, end
-    const int nev = HOST_CHUNKS_MAX + 4;
+    // events: [0, HOST_CHUNKS_MAX) chunks out, [HOST_CHUNKS_MAX, 2 HOST_CHUNKS_MAX)
+    // chunks in, then fields out, fields in, step done, end
+    const int nev = 2 * HOST_CHUNKS_MAX + 4;
     while (e == cudaSuccess && (int)ctx->hevents->size() < nev) {
         cudaEvent_t ev;
         e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
@@ -722,8 +780,9 @@ grpic_status grpic_step_host(grpic_ctx *ctx, grpic_particles *host, grpic_partic
     }
     if (e != cudaSuccess) return cuda_fail(ctx, e, "grpic_step_host: setup");
     std::vector<cudaEvent_t> &ev = *ctx->hevents;
-    cudaEvent_t ev_fout = ev[HOST_CHUNKS_MAX], ev_in = ev[HOST_CHUNKS_MAX + 1], ev_step = ev[HOST_CHUNKS_MAX + 2],
-                ev_end = ev[HOST_CHUNKS_MAX + 3];
+    cudaEvent_t *ev_cin = ev.data() + HOST_CHUNKS_MAX;
+    cudaEvent_t ev_fout = ev[2 * HOST_CHUNKS_MAX], ev_fin = ev[2 * HOST_CHUNKS_MAX + 1],
+                ev_step = ev[2 * HOST_CHUNKS_MAX + 2], ev_end = ev[2 * HOST_CHUNKS_MAX + 3];
     cudaStream_t s = S(stream), up = ctx->up_stream, down = ctx->down_stream;
     const size_t fbytes = (size_t)(ctx->g.nth + 1) * f->ld * (ctx->prm.precision == 32 ? 4 : 8);
     int64_t n = host->n;
@@ -739,7 +798,17 @@ grpic_status grpic_step_host(grpic_ctx *ctx, grpic_particles *host, grpic_partic
         const int64_t chunk = std::max(HOST_CHUNK_MIN, (n + HOST_CHUNKS_MAX - 1) / HOST_CHUNKS_MAX);
         const int nch = n > 0 ? (int)((n + chunk - 1) / chunk) : 0;
         const HostArrays hd = host_arrays(ctx, dev);
-        // copies in: chunk c after the previous step's copy out of the slots it covers
+        // copies in: the fields, then chunk c after the previous step's copy
+        // out of the slots it covers; the push of a chunk waits for its copy
+        if (host_f && e == cudaSuccess) {
+            if (step > 0) e = cudaStreamWaitEvent(up, ev_fout, 0);
+            for (int k = 0; k < 3 && e == cudaSuccess; ++k) {
+                e = cudaMemcpyAsync(f->D[k], host_f->D[k], fbytes, cudaMemcpyHostToDevice, up);
+                if (e == cudaSuccess) e = cudaMemcpyAsync(f->B[k], host_f->B[k], fbytes, cudaMemcpyHostToDevice, up);
+            }
+        }
+        if (e == cudaSuccess) e = cudaEventRecord(ev_fin, up);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ev_fin, 0);
         for (int c = 0; c < nch && e == cudaSuccess; ++c) {
             const int64_t lo = c * chunk, hi = std::min(n, lo + chunk);
             if (step > 0 && prev_chunks > 0) {
@@ -751,23 +820,16 @@ grpic_status grpic_step_host(grpic_ctx *ctx, grpic_particles *host, grpic_partic
                 e = cudaMemcpyAsync(static_cast<char *>(hd.a[k]) + lo * ha.es[k],
                                     static_cast<const char *>(ha.a[k]) + lo * ha.es[k], (hi - lo) * ha.es[k],
                                     cudaMemcpyHostToDevice, up);
+            if (e == cudaSuccess) e = cudaEventRecord(ev_cin[c], up);
         }
-        if (host_f && e == cudaSuccess) {
-            if (step > 0) e = cudaStreamWaitEvent(up, ev_fout, 0);
-            for (int k = 0; k < 3 && e == cudaSuccess; ++k) {
-                e = cudaMemcpyAsync(f->D[k], host_f->D[k], fbytes, cudaMemcpyHostToDevice, up);
-                if (e == cudaSuccess) e = cudaMemcpyAsync(f->B[k], host_f->B[k], fbytes, cudaMemcpyHostToDevice, up);
-            }
-        }
-        if (e == cudaSuccess) e = cudaEventRecord(ev_in, up);
-        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ev_in, 0);
         if (e != cudaSuccess) break;
         if (bytes) bytes[0] += n * (int64_t)(ha.n == 7 ? 28 : 44) + (host_f ? 6 * (int64_t)fbytes : 0);
         dev->n = n;
         set_count_kernel<<<1, 32, 0, s>>>(dev->d_count, n);
         e = cudaGetLastError();
         if (e != cudaSuccess) break;
-        st = grpic_step(ctx, dev, dev_scratch, f, 1, stream);
+        st = step_one_chunks(ctx, dev, dev_scratch, f, nch, chunk, ev_cin, s);
+        st = drop_pending(ctx, st);
         if (st) break;
         // the live count decides the copies out
         e = cudaMemcpyAsync(ctx->h_count, dev->d_count, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
@@ -783,6 +845,14 @@ grpic_status grpic_step_host(grpic_ctx *ctx, grpic_particles *host, grpic_partic
         const int64_t ochunk = std::max(HOST_CHUNK_MIN, (nn + HOST_CHUNKS_MAX - 1) / HOST_CHUNKS_MAX);
         const int och = nn > 0 ? (int)((nn + ochunk - 1) / ochunk) : 0;
         const HostArrays hs = host_arrays(ctx, dev);  // the sorted state (dev swapped by the sort)
+        // the fields first: the next step's copy in starts with them
+        if (host_f && e == cudaSuccess) {
+            for (int k = 0; k < 3 && e == cudaSuccess; ++k) {
+                e = cudaMemcpyAsync(host_f->D[k], f->D[k], fbytes, cudaMemcpyDeviceToHost, down);
+                if (e == cudaSuccess) e = cudaMemcpyAsync(host_f->B[k], f->B[k], fbytes, cudaMemcpyDeviceToHost, down);
+            }
+            if (e == cudaSuccess) e = cudaEventRecord(ev_fout, down);
+        }
         for (int c = 0; c < och && e == cudaSuccess; ++c) {
             const int64_t lo = c * ochunk, hi = std::min(nn, lo + ochunk);
             for (int k = 0; k < ha.n && e == cudaSuccess; ++k)
@@ -790,13 +860,6 @@ grpic_status grpic_step_host(grpic_ctx *ctx, grpic_particles *host, grpic_partic
                                     static_cast<const char *>(hs.a[k]) + lo * ha.es[k], (hi - lo) * ha.es[k],
                                     cudaMemcpyDeviceToHost, down);
             if (e == cudaSuccess) e = cudaEventRecord(ev[c], down);
-        }
-        if (host_f && e == cudaSuccess) {
-            for (int k = 0; k < 3 && e == cudaSuccess; ++k) {
-                e = cudaMemcpyAsync(host_f->D[k], f->D[k], fbytes, cudaMemcpyDeviceToHost, down);
-                if (e == cudaSuccess) e = cudaMemcpyAsync(host_f->B[k], f->B[k], fbytes, cudaMemcpyDeviceToHost, down);
-            }
-            if (e == cudaSuccess) e = cudaEventRecord(ev_fout, down);
         }
         if (bytes) bytes[1] += nn * (int64_t)(ha.n == 7 ? 28 : 44) + (host_f ? 6 * (int64_t)fbytes : 0);
         prev_chunks = och;

@@ -196,14 +196,18 @@ cudaError_t launch_init_fields(grpic_ctx *ctx, int kind, double B0, const grpic_
 // perm[k] of in for k < *live (the last sort's permutation, data not moved)
 // and, when cnt9 is given (zeroed), the push also counts per start cell and
 // direction for the next neighbour sort
+// slot0: the first slot of the arrays given (a chunk of the slot range: the
+// keys are written from d_keys + slot0)
 cudaError_t launch_push64(grpic_ctx *ctx, const grpic_particles *in, grpic_particles *p, const int32_t *perm,
-                          const int32_t *live, int32_t *cnt9, grpic_fields *f, bool histogram, cudaStream_t s);
+                          const int32_t *live, int32_t *cnt9, grpic_fields *f, bool histogram, cudaStream_t s,
+                          int64_t slot0 = 0);
 // the FP64 push in place, writing the adjoint's record of every particle
 // (layout above, tape_ld >= p->n)
 cudaError_t launch_push64_tape(grpic_ctx *ctx, grpic_particles *p, grpic_fields *f, double *tape, int64_t tape_ld,
                                cudaStream_t s);
 cudaError_t launch_push32(grpic_ctx *ctx, const grpic_particles *in, grpic_particles *p, const int32_t *perm,
-                          const int32_t *live, int32_t *cnt9, grpic_fields *f, bool histogram, cudaStream_t s);
+                          const int32_t *live, int32_t *cnt9, grpic_fields *f, bool histogram, cudaStream_t s,
+                          int64_t slot0 = 0);
 cudaError_t launch_deposit(grpic_ctx *ctx, const grpic_particles *b, const grpic_particles *a, const void *dphi,
                            grpic_fields *f, cudaStream_t s);
 // the field update of rows [j_lo, j_hi) (j_hi < 0: every row)

@@ -779,7 +779,8 @@ __global__ void __launch_bounds__(256, GRPIC_PUSH32_MINB) push32_kernel(Push32Ar
 }  // namespace
 
 cudaError_t launch_push32(grpic_ctx *ctx, const grpic_particles *in, grpic_particles *p, const int32_t *perm,
-                          const int32_t *live, int32_t *cnt9, grpic_fields *f, bool histogram, cudaStream_t s)
+                          const int32_t *live, int32_t *cnt9, grpic_fields *f, bool histogram, cudaStream_t s,
+                          int64_t slot0)
 {
     Push32Args A;
     A.g = ctx->g;
@@ -843,7 +844,7 @@ cudaError_t launch_push32(grpic_ctx *ctx, const grpic_particles *in, grpic_parti
     A.ld = f->ld;
     A.ldi = (int)f->ld;
     A.rcol = ctx->rcol;
-    A.keys = ctx->d_keys;
+    A.keys = ctx->d_keys + slot0;
     A.count = ctx->d_count;
     A.histogram = histogram ? 1 : 0;
     A.status = ctx->d_status;

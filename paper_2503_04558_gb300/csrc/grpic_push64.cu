@@ -508,9 +508,11 @@ static Push64Args push64_args(grpic_ctx *ctx, const grpic_particles *in, grpic_p
 }
 
 cudaError_t launch_push64(grpic_ctx *ctx, const grpic_particles *in, grpic_particles *p, const int32_t *perm,
-                          const int32_t *live, int32_t *cnt9, grpic_fields *f, bool histogram, cudaStream_t s)
+                          const int32_t *live, int32_t *cnt9, grpic_fields *f, bool histogram, cudaStream_t s,
+                          int64_t slot0)
 {
     Push64Args A = push64_args(ctx, in, p, perm, live, cnt9, f, histogram);
+    A.keys = ctx->d_keys + slot0;
     if (p->n <= 0) return cudaSuccess;
     int64_t blocks = (p->n + 255) / 256;
     const bool rad = ctx->prm.radiation != 0;
