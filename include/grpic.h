@@ -213,7 +213,7 @@ grpic_status grpic_field_update(grpic_ctx *ctx, grpic_fields *f, void *stream);
 
 /* How an FP32 context runs the field update: fused != 0 (the default) by
  * launches of four stages each on tiles staged in shared memory by the tensor
- * copy engine (56 x 24 points per CTA plus a halo of 4, the stages inside a
+ * copy engine (56 x 16 points per CTA plus a halo of 4, the stages inside a
  * launch updating one point less of halo each), the result copied back into
  * f's arrays; fused = 0 one launch per stage.  Both run the same operations
  * per point (the fields agree to FP32 rounding: the compiler contracts a few

@@ -228,24 +228,27 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 8 : 1) field_stage_kerne
 // slabs are read from global memory (each CTA's slabs stay in L1/L2 over its
 // stages); X^n and J at the point itself.  The operations per point are the
 // per-stage kernel's (the results agree to FP32 rounding: the compiler
-// contracts a few multiply-adds differently in the two kernels).
+// contracts a few multiply-adds differently in the two kernels).  Two CTAs of
+// 512 threads share an SM (110.7 KB of shared memory each), so that one CTA's
+// tile load and barriers overlap the other's passes (1.37 -> 1.29 ms per
+// update at 2048^2 against one CTA of 1024 threads on 56 x 24 points).
 #ifndef GRPIC_FZ_OW
 #define GRPIC_FZ_OW 56
 #endif
 #ifndef GRPIC_FZ_OH
-#define GRPIC_FZ_OH 24
+#define GRPIC_FZ_OH 16
 #endif
 constexpr int FZ_NS = 4, FZ_OW = GRPIC_FZ_OW, FZ_OH = GRPIC_FZ_OH;
-constexpr int FZ_BW = FZ_OW + 2 * FZ_NS, FZ_BH = FZ_OH + 2 * FZ_NS;   // 64 x 32 box
+constexpr int FZ_BW = FZ_OW + 2 * FZ_NS, FZ_BH = FZ_OH + 2 * FZ_NS;   // 64 x 24 box
 constexpr int FZ_BOX = FZ_BW * FZ_BH;
 #ifndef GRPIC_FZ_THREADS
-#define GRPIC_FZ_THREADS 1024
+#define GRPIC_FZ_THREADS 512
 #endif
 #ifndef GRPIC_FZ_MINB
-#define GRPIC_FZ_MINB 1
+#define GRPIC_FZ_MINB 2
 #endif
 constexpr int FZ_THREADS = GRPIC_FZ_THREADS;
-constexpr int FZ_SMEM = (4 * 6 * FZ_BOX) * 4 + 128;   // two iterate copies, C^n, E and H (floats); the barrier
+constexpr int FZ_SMEM = (3 * 6 * FZ_BOX) * 4 + 128;   // the iterate, C^n, E and H (floats); the barrier
 
 struct FusedMaps {
     CUtensorMap x[6];   // the iterate at the launch's first stage
@@ -339,8 +342,7 @@ __global__ void __launch_bounds__(FZ_THREADS, GRPIC_FZ_MINB) field_fused32_kerne
 {
     extern __shared__ __align__(128) unsigned char fz_smem[];
     float *X0 = reinterpret_cast<float *>(fz_smem);
-    float *X1 = X0 + 6 * FZ_BOX;
-    float *CN = X1 + 6 * FZ_BOX;
+    float *CN = X0 + 6 * FZ_BOX;
     float *EH = CN + 6 * FZ_BOX;
     uint64_t *bar = reinterpret_cast<uint64_t *>(EH + 6 * FZ_BOX);
     const int a0 = blockIdx.x * FZ_OW, row0 = blockIdx.y * FZ_OH;  // the rectangle's first column and row
@@ -385,21 +387,20 @@ __global__ void __launch_bounds__(FZ_THREADS, GRPIC_FZ_MINB) field_fused32_kerne
                          : "memory");
         return;
     }
-    // the points a stage does not update keep the loaded values in both
-    // copies; C^n of the points the predictor does not reach stays 0
-    for (int e = threadIdx.x; e < 6 * FZ_BOX; e += FZ_THREADS) {
-        X1[e] = X0[e];
-        if (!load_cn) CN[e] = 0.0f;
+    // the iterate is updated in place: a stage's first pass reads it (into E
+    // and H), its second pass reads only E, H, C^n, X^n and J; the points a
+    // stage does not update keep their values.  C^n of the points the
+    // predictor does not reach stays 0
+    if (!load_cn) {
+        for (int e = threadIdx.x; e < 6 * FZ_BOX; e += FZ_THREADS) CN[e] = 0.0f;
+        __syncthreads();
     }
-    __syncthreads();
     for (int k = 0; k < ns; ++k) {
         const int st = s0 + k;
         FieldArgs<float> B = A;
         B.mode = st == 0 ? 0 : (st == last_stage ? 2 : 1);
         const int w = ns - 1 - k;  // halo this stage still updates
-        const float *cur = (k & 1) ? X1 : X0;
-        float *nxt = (k & 1) ? X0 : X1;
-        const Ctx<float, SmemX32> X(B, SmemX32{cur, c0, r0});
+        const Ctx<float, SmemX32> X(B, SmemX32{X0, c0, r0});
         // pass 1: E_i, H_i (Eqs. auxE, auxH) one point beyond the stage's
         // region, each where its own reads stay in the box and the grid: the
         // kinds reading column i + 1 (H_theta, H_phi, E_r) for i in [-1, n_r],
@@ -425,7 +426,7 @@ __global__ void __launch_bounds__(FZ_THREADS, GRPIC_FZ_MINB) field_fused32_kerne
         __syncthreads();
         // pass 2: circulations and the update on the region
         const AuxSmem32 H{B, EH, c0, r0};
-        const SmemPut32 put{B, nxt, CN, c0, r0};
+        const SmemPut32 put{B, X0, CN, c0, r0};
 #pragma unroll
         for (int e = threadIdx.x; e < FZ_BOX; e += FZ_THREADS) {
             const int bc = e % FZ_BW, br = e / FZ_BW;
@@ -437,7 +438,7 @@ __global__ void __launch_bounds__(FZ_THREADS, GRPIC_FZ_MINB) field_fused32_kerne
         __syncthreads();
     }
     // the rectangle's iterate (and C^n after the first stage) to global memory
-    const float *res = (ns & 1) ? X1 : X0;
+    const float *res = X0;
     for (int e = threadIdx.x; e < FZ_OW * FZ_OH; e += FZ_THREADS) {
         const int col = a0 + e % FZ_OW, j = row0 + e / FZ_OW;
         if (col >= A.ld || j > A.nth) continue;
