@@ -599,7 +599,6 @@ __global__ void __launch_bounds__(256) neighbour_perm_kernel(const int32_t *off_
         if (lane < m)
 #pragma unroll
             for (int d = 0; d < 9; ++d) run[lane * 9 + d] = base9[(int64_t)d * ncell + s0 + lane];
-        const int s0i = (int)(s0 % nr);
         __syncwarp();
         for (int b = beg; b < end; b += 4 * 32) {
             int kk[4];
@@ -614,18 +613,25 @@ __global__ void __launch_bounds__(256) neighbour_perm_kernel(const int32_t *off_
                 const int p = b + u * 32 + lane;
                 const int c = task_cell(b + u * 32, lane, o, m);
                 const int k = kk[u];
+                // the precondition holds here (checked by the count pass, or
+                // by construction when the push counted: moves of at most one
+                // cell), so the direction follows from k - s alone; a key out
+                // of the 9 (never seen) is dropped rather than indexing run[]
                 int key2 = -1;
-                if (p < end && k >= 0 && k < ncell) {
-                    const int cls = dir_of(k, (int)(s0 + c), task_col(s0i, c, nr), nr);
-                    if (cls >= 0) key2 = c * 9 + cls;
+                if (p < end && (unsigned)k < (unsigned)ncell) {
+                    const int delta = k - (int)(s0 + c);
+                    const int dj = (delta > 1) - (delta < -1);
+                    const int di = delta - dj * nr;
+                    if ((unsigned)(di + 1) <= 2u) key2 = c * 9 + (dj + 1) * 3 + (di + 1);
                 }
                 const unsigned peers = __match_any_sync(FULL, key2);
-                int dst = 0;
-                if (key2 >= 0) dst = run[key2] + __popc(peers & ((1u << lane) - 1u));
+                const bool has = key2 >= 0;
+                int dst = -1;
+                if (has) dst = run[key2] + __popc(peers & ((1u << lane) - 1u));
                 __syncwarp();
-                if (key2 >= 0 && lane == __ffs(peers) - 1) run[key2] += __popc(peers);
+                if (has && lane == __ffs(peers) - 1) run[key2] += __popc(peers);
                 __syncwarp();
-                if (key2 >= 0 && dst >= 0 && dst < nmax) perm[dst] = p;
+                if ((uint64_t)(int64_t)dst < (uint64_t)nmax) perm[dst] = p;  // dst in [0, nmax)
             }
         }
         __syncwarp();
