@@ -104,9 +104,9 @@ typedef struct {
  * fp64_radius run in extended precision (<= 0: never), with the arithmetic
  * island_arith selects: 0 double-FP32 pairs (~48-bit significands on the
  * FP32 pipes, the default), 1 native FP64.  push_tol: in the FP32 form, the
- * geodesic corrector stops once the change of the iterate (relative to r_i,
- * in theta cells, relative to max(1, |u|)) falls below push_tol (<= 0: always
- * n_push_iter correctors).  The change is exact: two floats within a factor 2
+ * geodesic corrector stops once the change of the iterate (r relative to r_i,
+ * theta in radians, u relative to max(1, |u|)) falls below push_tol (<= 0:
+ * always n_push_iter correctors).  The change is exact: two floats within a factor 2
  * subtract exactly (Sterbenz's lemma), so the test takes the FP64 decision
  * for converging iterates.  The FP64 path always runs n_push_iter.
  * pusher: the momentum update of charged particles (Sec. 2.2): 0 the

@@ -37,7 +37,7 @@ struct Push32Args {
     float dt;
     float idt, m_i2dt;  // 1 / dt, -1 / (2 dt)
     int n_iter;
-    float tolf;
+    float tolf, tol_o2;  // push_tol; push_tol / dtheta (the theta test in offset units)
     float qm[4], qw[4];
     int massive[4];
     double r64;
@@ -314,13 +314,15 @@ __device__ __forceinline__ void push_island_fp64(const Push32Args &A, int i, int
         bool done = false;
         if (A.use_tol) {
             // convergence test of the implicit iteration: change of the
-            // iterate relative to r_i, one theta cell and max(1, |u|).  The
+            // iterate in r relative to r_i, in theta in radians (the same
+            // relative length, r dtheta / r) and in u relative to max(1,
+            // |u|).  The
             // difference of two floats within a factor 2 of each other is
             // exact in FP32 (Sterbenz's lemma), so for converging iterates
             // these differences are the FP64 ones; only the thresholds are
             // rounded to FP32.
             const float t = A.tolf;
-            done = fabsf(n1 - a1) < t * rcf && fabsf(n2 - a2) < t &&
+            done = fabsf(n1 - a1) < t * rcf && fabsf(n2 - a2) < A.tol_o2 &&
                    fabsf(nb1 - b1) < t * fmaxf(1.0f, fabsf(nb1)) && fabsf(nb2 - b2) < t * fmaxf(1.0f, fabsf(nb2));
         }
         a1 = n1;
@@ -425,10 +427,10 @@ __device__ __forceinline__ void push_fp32(const Push32Args &A, int i, int j, flo
         const float nb1 = fmaf(h, ft.ur + f0.ur, u[0]), nb2 = fmaf(h, ft.ut + f0.ut, u[1]);
         bool done = false;
         if (A.use_tol) {
-            // the convergence test of push_island_fp64: change of the iterate relative
-            // to r_i, one theta cell and max(1, |u|)
+            // the convergence test of push_island_fp64: change of the iterate in r
+            // relative to r_i, in theta in radians, in u relative to max(1, |u|)
             const float t = A.tolf;
-            done = fabsf(n1 - a1) < trc && fabsf(n2 - a2) < t && fabsf(nb1 - b1) < t * fmaxf(1.0f, fabsf(nb1)) &&
+            done = fabsf(n1 - a1) < trc && fabsf(n2 - a2) < A.tol_o2 && fabsf(nb1 - b1) < t * fmaxf(1.0f, fabsf(nb1)) &&
                    fabsf(nb2 - b2) < t * fmaxf(1.0f, fabsf(nb2));
         }
         a1 = n1;
@@ -586,7 +588,7 @@ __device__ __forceinline__ void push_island_df(const Push32Args &A, int i, int j
         bool done = false;
         if (A.use_tol) {
             const float t = A.tolf;
-            done = fabsf(n1 - a1) < trc && fabsf(n2 - a2) < t && fabsf(nb1 - b1) < t * fmaxf(1.0f, fabsf(nb1)) &&
+            done = fabsf(n1 - a1) < trc && fabsf(n2 - a2) < A.tol_o2 && fabsf(nb1 - b1) < t * fmaxf(1.0f, fabsf(nb1)) &&
                    fabsf(nb2 - b2) < t * fmaxf(1.0f, fabsf(nb2));
         }
         a1 = n1;
@@ -789,6 +791,7 @@ cudaError_t launch_push32(grpic_ctx *ctx, const grpic_particles *in, grpic_parti
     A.m_i2dt = (float)(-0.5 / ctx->prm.dt);
     A.n_iter = ctx->prm.n_push_iter;
     A.tolf = (float)ctx->prm.push_tol;
+    A.tol_o2 = (float)(ctx->prm.push_tol / ctx->g.dth);
     for (int k = 0; k < 4; ++k) {
         A.qm[k] = (float)ctx->prm.q_over_m[k];
         A.qw[k] = (float)ctx->prm.q_weight[k];

@@ -260,23 +260,36 @@ def test_fp32_running_charge_check_in_fp64(run20):
 
 
 def test_fp32_convergence_tolerance(G):
-    """With push_tol > 0 the convergence test stops the corrector early; the
-    result stays within FP32 precision of the fixed-count push."""
-    oc, gc = cfg32(32)
+    """With push_tol > 0 the correctors stop once the iterate changes by less
+    than push_tol (r relative to r_i, theta in radians, momenta relative to
+    max(1, |u|)), which leaves it within about the contraction
+    rate times push_tol of the trapezoid's fixed point.  At 256^2 three
+    correctors converge far below FP32 rounding (contraction ~3e-3 per
+    corrector), so the fixed-count push stands for the fixed point: per
+    particle the tolerance run stays within a few push_tol of it, in cells
+    and relative momentum."""
+    oc, gc = cfg32(256)
     out = []
     for tol in (0.0, 1e-6):
         gc.push_tol = tol
         ctx = G.Context(gc)
         F = G.Fields(gc)
         ctx.init_fields(F, O.WALD, 1.0)
-        P = make_particles(oc, 5000, seed=5, sigma=0.3)
+        P = make_particles(oc, 20000, seed=5, sigma=0.3)
         S = load32(G, gc, oc, P)
         ctx.push(S, F)
         assert ctx.sync() == 0
         out.append(S.host())
-    for k in ("x1", "x2", "u1", "u2", "u3"):
-        a, b = out[0][k].astype(np.float64), out[1][k].astype(np.float64)
-        assert np.max(np.abs(a - b)) <= 1e-5 * max(1.0, np.max(np.abs(a))), k
+    a, b = out
+    same = (a["cell"] == b["cell"]) & ((a["tag"] & 0x80000000) == 0)
+    assert same.mean() > 0.999
+    dpos = max(np.max(np.abs(a[k][same].astype(np.float64) - b[k][same])) for k in ("x1", "x2"))
+    ua = np.stack([a[k][same].astype(np.float64) for k in ("u1", "u2", "u3")])
+    ub = np.stack([b[k][same].astype(np.float64) for k in ("u1", "u2", "u3")])
+    dmom = np.max(np.abs(ua - ub) / np.maximum(1.0, np.abs(ua).max(axis=0)))
+    print(f"FP32 form, push_tol 1e-6 against three correctors at 256^2: position {dpos:.2e} cells, "
+          f"momentum {dmom:.2e} relative (max over {same.sum()} particles)")
+    assert dpos <= 5e-6 and dmom <= 5e-6, (dpos, dmom)
 
 
 def test_fp32_island_arithmetic(G):
