@@ -91,16 +91,36 @@ size_t fsize(const grpic_ctx *ctx) { return ctx->prm.precision == 64 ? sizeof(do
 grpic_status ensure_field_scratch(grpic_ctx *ctx, int64_t ld)
 {
     static_assert(sizeof(int64_t) == 8, "");
-    // 18 arrays: C^n (6) and two iterate buffers (12), stride ld
+    // 18 arrays: C^n (6) and two iterate buffers (12), stride ld; in the
+    // FP32 form also the push's stencil quads of the six components
     size_t need = 18 * (size_t)(ctx->g.nth + 1) * (size_t)ld * fsize(ctx);
+    size_t qneed = ctx->prm.precision == 32 ? 6 * (size_t)(ctx->g.nth + 1) * (size_t)ld * 16 : 0;
     if (ctx->fscratch && ctx->fscratch_ld == ld) return GRPIC_OK;
     if (ctx->fscratch) cudaFree(ctx->fscratch);
-    ctx->fscratch = nullptr;
+    if (ctx->q32) cudaFree(ctx->q32);
+    ctx->fscratch = ctx->q32 = nullptr;
+    ctx->fscratch_ld = 0;
     cudaError_t e = cudaMalloc(&ctx->fscratch, need);
-    if (e != cudaSuccess) return fail(ctx, GRPIC_ENOMEM, "field scratch allocation failed");
+    if (e == cudaSuccess && qneed) e = cudaMalloc(&ctx->q32, qneed);
+    if (e != cudaSuccess) {
+        if (ctx->fscratch) cudaFree(ctx->fscratch);
+        ctx->fscratch = ctx->q32 = nullptr;
+        return fail(ctx, GRPIC_ENOMEM, "field scratch allocation failed");
+    }
     cudaMemset(ctx->fscratch, 0, need);
     ctx->fscratch_ld = ld;
     return GRPIC_OK;
+}
+
+// the FP32 push's view of the fields: their stencil quads, rebuilt from D
+// and B on stream s ahead of each push (the FP64 push reads the arrays)
+grpic_status prepare_push_fields(grpic_ctx *ctx, grpic_fields *f, cudaStream_t s)
+{
+    if (ctx->prm.precision != 32) return GRPIC_OK;
+    grpic_status st = ensure_field_scratch(ctx, f->ld);
+    if (st) return st;
+    cudaError_t e = launch_quad32(ctx, f, s);
+    return e == cudaSuccess ? GRPIC_OK : cuda_fail(ctx, e, "field quads");
 }
 
 grpic_status ensure_particle_scratch(grpic_ctx *ctx, int64_t n)
@@ -177,6 +197,8 @@ grpic_status push_impl(grpic_ctx *ctx, grpic_particles *p, grpic_fields *f, bool
         // the last sort left its order in d_perm: read p through it and write
         // the pushed particles, in that order, into scratch's arrays
         if (!scratch || p->tag != ctx->pending_tag) return fail(ctx, GRPIC_EINVAL, "push: a sort's order is pending");
+        grpic_status fs = prepare_push_fields(ctx, f, s);
+        if (fs) return fs;
         ctx->pending_perm = 0;
         size_t bytes = (size_t)(ctx->g.nth + 1) * f->ld * fsize(ctx);
         for (int k = 0; k < 3; ++k) cudaMemsetAsync(f->J[k], 0, bytes, s);
@@ -211,6 +233,7 @@ grpic_status push_impl(grpic_ctx *ctx, grpic_particles *p, grpic_fields *f, bool
     const bool neighbour_next = p->n > 0 && p->tag && p->tag == ctx->sorted_tag && ctx->pushes_since_sort == 0;
     const bool histogram = for_sort && !neighbour_next;
     grpic_status st = ensure_particle_scratch(ctx, p->n);
+    if (!st) st = prepare_push_fields(ctx, f, s);
     if (st) return st;
     size_t bytes = (size_t)(ctx->g.nth + 1) * f->ld * fsize(ctx);
     for (int k = 0; k < 3; ++k) cudaMemsetAsync(f->J[k], 0, bytes, s);
@@ -660,6 +683,7 @@ static grpic_status step_one_chunks(grpic_ctx *ctx, grpic_particles *p, grpic_pa
     const bool neighbour_next = p->n > 0 && p->tag && p->tag == ctx->sorted_tag && ctx->pushes_since_sort == 0;
     const bool histogram = sort_now && !neighbour_next;
     grpic_status st = ensure_particle_scratch(ctx, p->n);
+    if (!st) st = prepare_push_fields(ctx, f, s);  // the fields are in place: s waited for their copy
     if (st) return st;
     const size_t bytes = (size_t)(ctx->g.nth + 1) * f->ld * fsize(ctx);
     for (int k = 0; k < 3; ++k) cudaMemsetAsync(f->J[k], 0, bytes, s);
@@ -1155,7 +1179,7 @@ void grpic_destroy(grpic_ctx *ctx)
     if (ctx->up_stream) cudaStreamDestroy(ctx->up_stream);
     if (ctx->down_stream) cudaStreamDestroy(ctx->down_stream);
     if (ctx->h_count) cudaFreeHost(ctx->h_count);
-    void *ptrs[] = {ctx->d_spawn, ctx->d_rad, ctx->d_spqm, ctx->d_spmassive, ctx->d_offset_prev, ctx->d_cnt9, ctx->d_base9, ctx->d_sortflag, ctx->rcol, ctx->rcol2, ctx->rowsc, ctx->tab, ctx->col1d, ctx->tab32, ctx->col1d32, ctx->fscratch, ctx->d_status, ctx->d_keys,
+    void *ptrs[] = {ctx->d_spawn, ctx->d_rad, ctx->d_spqm, ctx->d_spmassive, ctx->d_offset_prev, ctx->d_cnt9, ctx->d_base9, ctx->d_sortflag, ctx->rcol, ctx->rcol2, ctx->rowsc, ctx->tab, ctx->col1d, ctx->tab32, ctx->col1d32, ctx->fscratch, ctx->q32, ctx->d_status, ctx->d_keys,
                     ctx->d_count, ctx->d_offset, ctx->d_cursor, ctx->d_blocksum, ctx->d_perm, ctx->d_bigseg};
     for (void *q : ptrs)
         if (q) cudaFree(q);

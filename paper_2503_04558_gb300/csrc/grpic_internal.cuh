@@ -110,6 +110,10 @@ struct grpic_ctx {
     cudaStream_t up_stream, down_stream;
     std::vector<cudaEvent_t> *hevents;
     int64_t *h_count;
+    // FP32 form: the field components as float4 quads of the push's bilinear
+    // stencils (launch_quad32, before each push), 6 x (nth+1) x fscratch_ld,
+    // allocated with the field scratch
+    void *q32;
     char err[256];
 };
 
@@ -205,6 +209,11 @@ cudaError_t launch_push64(grpic_ctx *ctx, const grpic_particles *in, grpic_parti
 // (layout above, tape_ld >= p->n)
 cudaError_t launch_push64_tape(grpic_ctx *ctx, grpic_particles *p, grpic_fields *f, double *tape, int64_t tape_ld,
                                cudaStream_t s);
+// the FP32 push reads the fields through their stencil quads (ctx->q32),
+// which launch_quad32 builds from f; launch it after every change of D, B
+// and before the push (both fail with cudaErrorInvalidValue unless the field
+// scratch is allocated for f->ld)
+cudaError_t launch_quad32(grpic_ctx *ctx, const grpic_fields *f, cudaStream_t s);
 cudaError_t launch_push32(grpic_ctx *ctx, const grpic_particles *in, grpic_particles *p, const int32_t *perm,
                           const int32_t *live, int32_t *cnt9, grpic_fields *f, bool histogram, cudaStream_t s,
                           int64_t slot0 = 0);

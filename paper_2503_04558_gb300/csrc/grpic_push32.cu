@@ -66,7 +66,9 @@ struct Push32Args {
     const int32_t *in_cell;
     const float *in_o1, *in_o2, *in_u1, *in_u2, *in_u3;
     const uint32_t *in_tag;
-    const float *D0, *D1, *D2, *B0, *B1, *B2;
+    // the field components D^r, D^th, D^ph, B^r, B^th, B^ph as stencil quads
+    // (quad32_kernel), element (js + 1) ld + is + NG for the stencil at (is, js)
+    const float4 *Q[6];
     float *J0, *J1, *J2;
     int64_t ld;
     int ldi;  // ld as the 32-bit stride of the element offsets ((n_theta+1) ld < 2^31)
@@ -154,14 +156,16 @@ __device__ __forceinline__ float log1p_cell(float y)
     return y * (1.0f - y * (0.5f - y * (1.0f / 3.0f - y * (0.25f - y * (0.2f - y * (1.0f / 6.0f - y * (1.0f / 7.0f - y * 0.125f)))))));
 }
 
-struct St32 {
-    int o0, o1;           // element offsets of the stencil's two rows at its first column
-    float f, gg, p0, p1;  // fractional offsets along r and theta; the rows' parities
+// bilinear stencil from cell (i, j) and offsets; half_r / half_t stagger
+// the component by half a cell in r / theta: the stencil's first column is
+// and first row js (js = -1 below the first half row), f and gg its
+// fractional offsets
+struct Sq32 {
+    int o;  // element offset of the stencil's quad
+    float f, gg;
 };
 
-// bilinear stencil from cell (i, j) and offsets; half_r / half_t stagger
-__device__ __forceinline__ void stencil32(const GridDev &g, int ld, int i, int j, float o1, float o2, bool half_r,
-                                          bool half_t, float par, St32 &S)
+__device__ __forceinline__ void stencilq32(int ld, int i, int j, float o1, float o2, bool half_r, bool half_t, Sq32 &S)
 {
     int is = i;
     float f = o1;
@@ -171,57 +175,43 @@ __device__ __forceinline__ void stencil32(const GridDev &g, int ld, int i, int j
     }
     int js = j;
     float gg = o2;
-    S.p0 = S.p1 = 1.0f;
-    int r0 = js, r1 = js + 1;
     if (half_t) {
         gg = o2 - 0.5f;
         if (gg < 0.0f) { gg += 1.0f; js = j - 1; }
-        r0 = js;
-        r1 = js + 1;
-        if (r0 < 0) { r0 = -1 - r0; S.p0 = par; }
-        if (r1 > g.nth - 1) { r1 = 2 * g.nth - 1 - r1; S.p1 = par; }
     }
-    S.o0 = r0 * ld + is + NG;
-    S.o1 = r1 * ld + is + NG;
+    S.o = (js + 1) * ld + is + NG;
     S.f = f;
     S.gg = gg;
 }
 
-// the bilinear value of one component: along r on both rows, then along
-// theta; ODD applies the rows' parities (a component odd across the axis)
-template <bool ODD = false>
-__device__ __forceinline__ float gather32(const float *__restrict__ F, const St32 &S)
+// the bilinear value of one component from its quad: along r on both rows,
+// then along theta (the rows' axis parities are in the quad)
+__device__ __forceinline__ float gatherq32(const float4 *__restrict__ Q, const Sq32 &S)
 {
-    const float *a = F + S.o0;
-    const float *b = F + S.o1;
-    const float a0 = __ldg(a), a1 = __ldg(a + 1), b0 = __ldg(b), b1 = __ldg(b + 1);
-    float x = fmaf(S.f, a1 - a0, a0), y = fmaf(S.f, b1 - b0, b0);
-    if (ODD) {
-        x *= S.p0;
-        y *= S.p1;
-    }
+    const float4 v = __ldg(Q + S.o);
+    const float x = fmaf(S.f, v.y - v.x, v.x), y = fmaf(S.f, v.w - v.z, v.z);
     return fmaf(S.gg, y - x, x);
 }
 
 // the six field components at the particle (Fig. Yee staggering): D^r and
 // B^theta at (i+1/2, j), D^theta and B^r at (i, j+1/2), D^phi at (i, j),
 // B^phi at (i+1/2, j+1/2); across the polar axis D^theta is odd, B^r and
-// B^phi even (the half-r stencils reflect no row)
+// B^phi even (the quads hold the reflected rows)
 __device__ __forceinline__ void gather_fields32(const Push32Args &A, int i, int j, float o1, float o2, float Dv[3],
                                                 float Bv[3])
 {
-    St32 Sh0, S0h, S00, Shh;
+    Sq32 Sh0, S0h, S00, Shh;
     const int ld = A.ldi;
-    stencil32(A.g, ld, i, j, o1, o2, true, false, 1.0f, Sh0);
-    stencil32(A.g, ld, i, j, o1, o2, false, true, -1.0f, S0h);
-    stencil32(A.g, ld, i, j, o1, o2, false, false, 1.0f, S00);
-    stencil32(A.g, ld, i, j, o1, o2, true, true, 1.0f, Shh);
-    Dv[0] = gather32(A.D0, Sh0);
-    Dv[1] = gather32<true>(A.D1, S0h);
-    Dv[2] = gather32(A.D2, S00);
-    Bv[1] = gather32(A.B1, Sh0);
-    Bv[2] = gather32(A.B2, Shh);
-    Bv[0] = gather32(A.B0, S0h);
+    stencilq32(ld, i, j, o1, o2, true, false, Sh0);
+    stencilq32(ld, i, j, o1, o2, false, true, S0h);
+    stencilq32(ld, i, j, o1, o2, false, false, S00);
+    stencilq32(ld, i, j, o1, o2, true, true, Shh);
+    Dv[0] = gatherq32(A.Q[0], Sh0);
+    Dv[1] = gatherq32(A.Q[1], S0h);
+    Dv[2] = gatherq32(A.Q[2], S00);
+    Bv[0] = gatherq32(A.Q[3], S0h);
+    Bv[1] = gatherq32(A.Q[4], Sh0);
+    Bv[2] = gatherq32(A.Q[5], Shh);
 }
 
 // generalized Boris step in FP32 with the metric of type M at x^n (the lower
@@ -778,7 +768,67 @@ __global__ void __launch_bounds__(256, GRPIC_PUSH32_MINB) push32_kernel(Push32Ar
     for (int k = 0; k < GRPIC_PUSH32_PPT; ++k) push_slot<PUSHER, IX>(A, p0 + (IX)(k * blockDim.x), nx, permuted);
 }
 
+// The stencil quads of the six field components: for the stencil whose
+// first row is js (-1 .. n_theta - 1) and first column col,
+//   Q_c[(js + 1) ld + col] = (F[r0][col], F[r0][col + 1], F[r1][col], F[r1][col + 1])
+// with r0 = js, r1 = js + 1.  The components at half-integer theta (D^theta,
+// odd across the axis; B^r and B^phi, even) have rows 0 .. n_theta - 1: a row
+// beyond them is its mirror across the axis (-1 -> 0, n_theta -> n_theta - 1)
+// times the parity.  Entries no stencil reads (the last column, row js = -1
+// of the integer-theta components) are zero.  A parity of -1 commutes with
+// rounding, so the gathers equal those from the arrays themselves bit for bit.
+struct Quad32Args {
+    const float *F[6];
+    float4 *Q[6];
+    int nth, ld;
+};
+
+__global__ void quad32_kernel(Quad32Args A)
+{
+    const int col = blockIdx.x * blockDim.x + threadIdx.x;
+    const int qr = blockIdx.y;  // js + 1
+    if (col >= A.ld || qr > A.nth) return;
+    const int js = qr - 1;
+    const size_t o = (size_t)qr * A.ld + col;
+    const bool last = col + 1 >= A.ld;
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+        const bool half_t = c == 1 || c == 3 || c == 5;
+        const float par = c == 1 ? -1.0f : 1.0f;
+        int r0 = js, r1 = js + 1;
+        float p0 = 1.0f, p1 = 1.0f;
+        if (half_t) {
+            if (r0 < 0) { r0 = -1 - r0; p0 = par; }
+            if (r1 > A.nth - 1) { r1 = 2 * A.nth - 1 - r1; p1 = par; }
+        }
+        float4 v = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        if (r0 >= 0 && !last) {
+            const float *a = A.F[c] + (size_t)r0 * A.ld + col;
+            const float *b = A.F[c] + (size_t)r1 * A.ld + col;
+            v = make_float4(p0 * a[0], p0 * a[1], p1 * b[0], p1 * b[1]);
+        }
+        A.Q[c][o] = v;
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_quad32(grpic_ctx *ctx, const grpic_fields *f, cudaStream_t s)
+{
+    if (!ctx->q32 || ctx->fscratch_ld != f->ld) return cudaErrorInvalidValue;
+    Quad32Args A;
+    const size_t per = (size_t)(ctx->g.nth + 1) * (size_t)f->ld;
+    for (int c = 0; c < 3; ++c) {
+        A.F[c] = (const float *)f->D[c];
+        A.F[c + 3] = (const float *)f->B[c];
+    }
+    for (int c = 0; c < 6; ++c) A.Q[c] = static_cast<float4 *>(ctx->q32) + c * per;
+    A.nth = ctx->g.nth;
+    A.ld = (int)f->ld;
+    const dim3 grid((unsigned)((f->ld + 255) / 256), (unsigned)(ctx->g.nth + 1));
+    quad32_kernel<<<grid, 256, 0, s>>>(A);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_push32(grpic_ctx *ctx, const grpic_particles *in, grpic_particles *p, const int32_t *perm,
                           const int32_t *live, int32_t *cnt9, grpic_fields *f, bool histogram, cudaStream_t s,
@@ -835,12 +885,9 @@ cudaError_t launch_push32(grpic_ctx *ctx, const grpic_particles *in, grpic_parti
     A.in_u2 = (const float *)in->u2;
     A.in_u3 = (const float *)in->u3;
     A.in_tag = in->tag;
-    A.D0 = (const float *)f->D[0];
-    A.D1 = (const float *)f->D[1];
-    A.D2 = (const float *)f->D[2];
-    A.B0 = (const float *)f->B[0];
-    A.B1 = (const float *)f->B[1];
-    A.B2 = (const float *)f->B[2];
+    if (!ctx->q32 || ctx->fscratch_ld != f->ld) return cudaErrorInvalidValue;  // launch_quad32 comes first
+    for (int c = 0; c < 6; ++c)
+        A.Q[c] = static_cast<const float4 *>(ctx->q32) + c * (size_t)(ctx->g.nth + 1) * (size_t)f->ld;
     A.J0 = (float *)f->J[0];
     A.J1 = (float *)f->J[1];
     A.J2 = (float *)f->J[2];
