@@ -75,8 +75,8 @@ B1_ALG_B = 2 * 28
 # Vay's update (1024^2 x 64 ppc), the FP64 push with the cubic shape (512^2 x
 # 64 ppc), the FP64 push with photon emission and conversion decisions (512^2
 # x 16 ppc, Wald a = 0.99, B0 = 500)
-VAY32_FP32_FLOP = 726.5
-VAY32_INST = 1225.5
+VAY32_FP32_FLOP = 653.8
+VAY32_INST = 1116.2
 CUBIC64_FP64_FLOP = 1471.4
 RAD64_FP64_FLOP = 1248.5
 VAY_COUNT = "ncu SASS counters, FP32-form push with Vay's update, 1024^2 x 64 ppc"
@@ -172,10 +172,15 @@ class ClockSampler:
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
+            # the timed work starts once the sampler is running (its first
+            # line in), so that the region's own samples are taken
+            t0 = time.time()
+            while not self.lines and self.proc.poll() is None and time.time() - t0 < 10.0:
+                time.sleep(0.01)
         except Exception:
             self.proc = None
         return self
