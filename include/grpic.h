@@ -196,7 +196,13 @@ grpic_status grpic_init_fields(grpic_ctx *ctx, grpic_field_kind kind, double B0,
  * axis reflection, then the Esirkepov deposit of the move x^n -> x^{n+1}
  * (Eqs. esirkepov-decomp, j-phi-deposit) into f->J (zeroed first).
  * Particles that leave [r_in, r_out) are marked dead after their deposit.
- * The cell keys of the new positions are kept in the context for grpic_sort. */
+ * The cell keys of the new positions are kept in the context for grpic_sort.
+ * In an FP32 context each push (here and inside grpic_step, grpic_step_graph
+ * and grpic_step_host) first copies D and B, on `stream`, into the context's
+ * stencil quads (the four corners of each component's bilinear stencil as
+ * one 16-byte element, 96 bytes per grid point, allocated with the field
+ * scratch on first use), which the push's interpolation reads: changes to
+ * D, B between pushes are always seen. */
 grpic_status grpic_push(grpic_ctx *ctx, grpic_particles *p, grpic_fields *f, void *stream);
 
 /* Deposit only: adds the Esirkepov currents of the moves from `before` to
