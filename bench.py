@@ -1155,12 +1155,13 @@ def main():
                 "phases": h["phases"], "live_particles": h["live_particles"],
                 "particle_statuses": h["particle_statuses"],
                 "roofline": h["roofline"], "clocks": h["clocks"], "measured_alu_peaks": measured_alu(),
-                # per step: push, the field update (FP32: fused launches of four
+                # per step: push (FP32: with the fields' stencil quads built
+                # first), the field update (FP32: fused launches of four
                 # stages; FP64: 1 + n_field_iter stage launches), 12 sort kernels
                 # (count, destinations, histogram pair, 3 scan, bases, placement and
                 # the general path's 3, which return at once) -- the count only
                 # in the first step, later pushes count -- and one gather per call
-                "gpu_launches": args.steps * (1 + ((1 + cfg.n_field_iter + 3) // 4 if head_prec == 32 else
+                "gpu_launches": args.steps * (1 + ((1 + (1 + cfg.n_field_iter + 3) // 4) if head_prec == 32 else
                                                    1 + cfg.n_field_iter) + 12) - (args.steps - 1) + 1,
                 "e2e": res["e2e"]}
         if second is not None:

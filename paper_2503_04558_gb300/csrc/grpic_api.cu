@@ -112,14 +112,21 @@ grpic_status ensure_field_scratch(grpic_ctx *ctx, int64_t ld)
     return GRPIC_OK;
 }
 
-// the FP32 push's view of the fields: their stencil quads, rebuilt from D
-// and B on stream s ahead of each push (the FP64 push reads the arrays)
-grpic_status prepare_push_fields(grpic_ctx *ctx, grpic_fields *f, cudaStream_t s)
+// Ahead of each push on stream s: J zeroed and, if cnt9 is given, the 9 x
+// n_cells direction counts of the next neighbour sort zeroed; in the FP32
+// form one kernel does both while it rebuilds the push's view of the fields,
+// their stencil quads, from D and B (the FP64 push reads the arrays).
+grpic_status prepare_push(grpic_ctx *ctx, grpic_fields *f, int32_t *cnt9, cudaStream_t s)
 {
-    if (ctx->prm.precision != 32) return GRPIC_OK;
+    if (ctx->prm.precision != 32) {
+        const size_t bytes = (size_t)(ctx->g.nth + 1) * f->ld * fsize(ctx);
+        for (int k = 0; k < 3; ++k) cudaMemsetAsync(f->J[k], 0, bytes, s);
+        if (cnt9) cudaMemsetAsync(cnt9, 0, sizeof(int32_t) * 9 * (size_t)ctx->g.nr * ctx->g.nth, s);
+        return GRPIC_OK;
+    }
     grpic_status st = ensure_field_scratch(ctx, f->ld);
     if (st) return st;
-    cudaError_t e = launch_quad32(ctx, f, s);
+    cudaError_t e = launch_quad32(ctx, f, true, cnt9, s);
     return e == cudaSuccess ? GRPIC_OK : cuda_fail(ctx, e, "field quads");
 }
 
@@ -197,17 +204,14 @@ grpic_status push_impl(grpic_ctx *ctx, grpic_particles *p, grpic_fields *f, bool
         // the last sort left its order in d_perm: read p through it and write
         // the pushed particles, in that order, into scratch's arrays
         if (!scratch || p->tag != ctx->pending_tag) return fail(ctx, GRPIC_EINVAL, "push: a sort's order is pending");
-        grpic_status fs = prepare_push_fields(ctx, f, s);
+        // the counts of the next neighbour sort come from this push
+        grpic_status fs = prepare_push(ctx, f, ctx->d_cnt9, s);
         if (fs) return fs;
         ctx->pending_perm = 0;
-        size_t bytes = (size_t)(ctx->g.nth + 1) * f->ld * fsize(ctx);
-        for (int k = 0; k < 3; ++k) cudaMemsetAsync(f->J[k], 0, bytes, s);
         grpic_particles out = *scratch;
         out.n = p->n;
         out.d_count = p->d_count;
         const int32_t *live = ctx->d_offset_prev + ncell;
-        // the counts of the next neighbour sort come from this push
-        cudaMemsetAsync(ctx->d_cnt9, 0, sizeof(int32_t) * 9 * (size_t)ncell, s);
         cudaError_t e = (ctx->prm.precision == 64)
                             ? launch_push64(ctx, p, &out, ctx->d_perm, live, ctx->d_cnt9, f, false, s)
                             : launch_push32(ctx, p, &out, ctx->d_perm, live, ctx->d_cnt9, f, false, s);
@@ -233,10 +237,8 @@ grpic_status push_impl(grpic_ctx *ctx, grpic_particles *p, grpic_fields *f, bool
     const bool neighbour_next = p->n > 0 && p->tag && p->tag == ctx->sorted_tag && ctx->pushes_since_sort == 0;
     const bool histogram = for_sort && !neighbour_next;
     grpic_status st = ensure_particle_scratch(ctx, p->n);
-    if (!st) st = prepare_push_fields(ctx, f, s);
+    if (!st) st = prepare_push(ctx, f, nullptr, s);
     if (st) return st;
-    size_t bytes = (size_t)(ctx->g.nth + 1) * f->ld * fsize(ctx);
-    for (int k = 0; k < 3; ++k) cudaMemsetAsync(f->J[k], 0, bytes, s);
     if (histogram) cudaMemsetAsync(ctx->d_count, 0, sizeof(int32_t) * (ncell + 1), s);
     ctx->counts_ready = 0;
     cudaError_t e = (ctx->prm.precision == 64) ? launch_push64(ctx, p, p, nullptr, nullptr, nullptr, f, histogram, s)
@@ -683,10 +685,8 @@ static grpic_status step_one_chunks(grpic_ctx *ctx, grpic_particles *p, grpic_pa
     const bool neighbour_next = p->n > 0 && p->tag && p->tag == ctx->sorted_tag && ctx->pushes_since_sort == 0;
     const bool histogram = sort_now && !neighbour_next;
     grpic_status st = ensure_particle_scratch(ctx, p->n);
-    if (!st) st = prepare_push_fields(ctx, f, s);  // the fields are in place: s waited for their copy
+    if (!st) st = prepare_push(ctx, f, nullptr, s);  // the fields are in place: s waited for their copy
     if (st) return st;
-    const size_t bytes = (size_t)(ctx->g.nth + 1) * f->ld * fsize(ctx);
-    for (int k = 0; k < 3; ++k) cudaMemsetAsync(f->J[k], 0, bytes, s);
     if (histogram) cudaMemsetAsync(ctx->d_count, 0, sizeof(int32_t) * (ncell + 1), s);
     ctx->counts_ready = 0;
     const size_t es = ctx->prm.precision == 64 ? 8 : 4;

@@ -212,8 +212,9 @@ cudaError_t launch_push64_tape(grpic_ctx *ctx, grpic_particles *p, grpic_fields 
 // the FP32 push reads the fields through their stencil quads (ctx->q32),
 // which launch_quad32 builds from f; launch it after every change of D, B
 // and before the push (both fail with cudaErrorInvalidValue unless the field
-// scratch is allocated for f->ld)
-cudaError_t launch_quad32(grpic_ctx *ctx, const grpic_fields *f, cudaStream_t s);
+// scratch is allocated for f->ld).  On the way it zeroes f->J (zero_j) and
+// the 9 x n_cells counts zero_cnt9 (if not null).
+cudaError_t launch_quad32(grpic_ctx *ctx, grpic_fields *f, bool zero_j, int32_t *zero_cnt9, cudaStream_t s);
 cudaError_t launch_push32(grpic_ctx *ctx, const grpic_particles *in, grpic_particles *p, const int32_t *perm,
                           const int32_t *live, int32_t *cnt9, grpic_fields *f, bool histogram, cudaStream_t s,
                           int64_t slot0 = 0);

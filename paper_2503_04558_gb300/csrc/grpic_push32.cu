@@ -40,6 +40,8 @@ struct Push32Args {
     float tolf, tol_o2;  // push_tol; push_tol / dtheta (the theta test in offset units)
     float qm[4], qw[4];
     int massive[4];
+    // per species (bit sp): massive (eps = 1 in u^0); massive and charged (the Boris step runs)
+    unsigned massive_mask, boris_mask;
     double r64;
     int i64;  // first column whose inner edge is at or beyond fp64_radius
     int island_fp64;   // 1: native FP64 island, 0: double-FP32 pairs
@@ -269,12 +271,12 @@ __device__ __forceinline__ void push_island_fp64(const Push32Args &A, int i, int
         sincos(((double)j + (double)o2) * g.dth, &s0, &c0);
     KSGeo<double> m;
     ks_geo_sc<double>(am, r0, s0, c0, m);
-    if (A.massive[sp] && A.qm[sp] != 0.0f) {
+    if ((A.boris_mask >> sp) & 1u) {
         float Dv[3], Bv[3];
         gather_fields32(A, i, j, o1, o2, Dv, Bv);
         boris_geo<double>(m, am, r0, s0, A.qm[sp], A.dt, Dv, Bv, u, PUSHER);
     }
-    const float eps = A.massive[sp] ? 1.0f : 0.0f;
+    const float eps = ((A.massive_mask >> sp) & 1u) ? 1.0f : 0.0f;
     const float dt = A.dt, h = 0.5f * dt;
     const float idth = A.idthf;
     RhsT<float> f0, ft;
@@ -382,12 +384,12 @@ __device__ __forceinline__ void push_fp32(const Push32Args &A, int i, int j, flo
     sincos_shift<float>(sc.x, sc.z, t0 * A.dthf, s0, c0);
     if (pole) c0 = -c0;
     const Pt32 m0 = point32(A.a2f, A.m2a2f, rcf + d0, s0, c0);
-    if (A.massive[sp] && A.qm[sp] != 0.0f) {
+    if ((A.boris_mask >> sp) & 1u) {
         float Dv[3], Bv[3];
         gather_fields32(A, i, j, o1, o2, Dv, Bv);
         boris_pt32(m0, a, A.a2f, A.qm[sp], A.dt, Dv, Bv, u, PUSHER);
     }
-    const float eps = A.massive[sp] ? 1.0f : 0.0f;
+    const float eps = ((A.massive_mask >> sp) & 1u) ? 1.0f : 0.0f;
     const float dt = A.dt, h = 0.5f * dt;
     const float up = u[2], aup = a * up;
     RhsT<float> f0, ft;
@@ -540,12 +542,12 @@ __device__ __forceinline__ void push_island_df(const Push32Args &A, int i, int j
     GUp32 g0;
     IslandPt keep;
     point_island(A.a_df, A.a2_df, A.m2a2f, add_f(rc, d0), s0, c0, m0, g0, &keep);
-    if (A.massive[sp] && A.qm[sp] != 0.0f) {
+    if ((A.boris_mask >> sp) & 1u) {
         float Dv[3], Bv[3];
         gather_fields32(A, i, j, o1, o2, Dv, Bv);
         boris_island_pt<PUSHER>(m0, g0, keep, A.a_df, A.a2_df, s0, A.qm[sp], A.dt, Dv, Bv, u);
     }
-    const float eps = A.massive[sp] ? 1.0f : 0.0f;
+    const float eps = ((A.massive_mask >> sp) & 1u) ? 1.0f : 0.0f;
     const float dt = A.dt, h = 0.5f * dt;
     const float up = u[2];
     RhsT<float> f0, ft;
@@ -781,6 +783,11 @@ struct Quad32Args {
     const float *F[6];
     float4 *Q[6];
     int nth, ld;
+    // zeroed on the way (the push deposits into J and counts into cnt9):
+    // J[c] over the same (nth+1) x ld points, cnt9 (9 x nr x nth) if given
+    float *J[3];
+    int32_t *cnt9;
+    int nr;
 };
 
 __global__ void quad32_kernel(Quad32Args A)
@@ -809,14 +816,27 @@ __global__ void quad32_kernel(Quad32Args A)
         }
         A.Q[c][o] = v;
     }
+    if (A.J[0]) {
+        A.J[0][o] = 0.0f;
+        A.J[1][o] = 0.0f;
+        A.J[2][o] = 0.0f;
+    }
+    if (A.cnt9 && qr < A.nth && col < A.nr) {
+        const size_t ncell = (size_t)A.nr * A.nth, k = (size_t)qr * A.nr + col;
+#pragma unroll
+        for (int d = 0; d < 9; ++d) A.cnt9[d * ncell + k] = 0;
+    }
 }
 
 }  // namespace
 
-cudaError_t launch_quad32(grpic_ctx *ctx, const grpic_fields *f, cudaStream_t s)
+cudaError_t launch_quad32(grpic_ctx *ctx, grpic_fields *f, bool zero_j, int32_t *zero_cnt9, cudaStream_t s)
 {
-    if (!ctx->q32 || ctx->fscratch_ld != f->ld) return cudaErrorInvalidValue;
+    if (!ctx->q32 || ctx->fscratch_ld != f->ld || f->ld < ctx->g.nr) return cudaErrorInvalidValue;
     Quad32Args A;
+    for (int c = 0; c < 3; ++c) A.J[c] = zero_j ? (float *)f->J[c] : nullptr;
+    A.cnt9 = zero_cnt9;
+    A.nr = ctx->g.nr;
     const size_t per = (size_t)(ctx->g.nth + 1) * (size_t)f->ld;
     for (int c = 0; c < 3; ++c) {
         A.F[c] = (const float *)f->D[c];
@@ -842,10 +862,13 @@ cudaError_t launch_push32(grpic_ctx *ctx, const grpic_particles *in, grpic_parti
     A.n_iter = ctx->prm.n_push_iter;
     A.tolf = (float)ctx->prm.push_tol;
     A.tol_o2 = (float)(ctx->prm.push_tol / ctx->g.dth);
+    A.massive_mask = A.boris_mask = 0u;
     for (int k = 0; k < 4; ++k) {
         A.qm[k] = (float)ctx->prm.q_over_m[k];
         A.qw[k] = (float)ctx->prm.q_weight[k];
         A.massive[k] = ctx->prm.massive[k];
+        if (A.massive[k]) A.massive_mask |= 1u << k;
+        if (A.massive[k] && A.qm[k] != 0.0f) A.boris_mask |= 1u << k;
     }
     A.r64 = ctx->prm.fp64_radius;
     A.island_fp64 = ctx->prm.island_arith == 1 ? 1 : 0;
