@@ -55,10 +55,10 @@ B0 = 1.0
 # island fraction), and scaled to a launch by the number of particles.
 PUSH64_FP64_FLOP = 1039.3   # FP64 push, 512^2 x 64 ppc split monopole
 PUSH64_DRAM_B = 95.6        # the same capture: DRAM bytes per particle (read + write)
-PUSH32_FP32_FLOP = 596.2    # FP32-form push, 1024^2 x 64 ppc split monopole
+PUSH32_FP32_FLOP = 594.2    # FP32-form push, 1024^2 x 64 ppc split monopole
 # the same capture: instructions issued per particle (warp instructions x 32)
 # and DRAM bytes per particle (read + write)
-PUSH32_INST = 1036.2
+PUSH32_INST = 1029.8
 PUSH32_DRAM_B = 68.0
 # batched 1D lines, b1_kernel with the cascade running (256 lines x 4096 cells):
 # instructions issued per particle-step (warp instructions x 32) and DRAM

@@ -68,9 +68,10 @@ struct Push32Args {
     const int32_t *in_cell;
     const float *in_o1, *in_o2, *in_u1, *in_u2, *in_u3;
     const uint32_t *in_tag;
-    // the field components D^r, D^th, D^ph, B^r, B^th, B^ph as stencil quads
-    // (quad32_kernel), element (js + 1) ld + is + NG for the stencil at (is, js)
-    const float4 *Q[6];
+    // the field components D^r, D^th, D^ph, B^r, B^th, B^ph (c = 0..5) as
+    // stencil quads (quad32_kernel), component c of the stencil at (is, js)
+    // at element 6 ((js + 1) ld + is + NG) + c
+    const float4 *Q;
     float *J0, *J1, *J2;
     int64_t ld;
     int ldi;  // ld as the 32-bit stride of the element offsets ((n_theta+1) ld < 2^31)
@@ -186,11 +187,11 @@ __device__ __forceinline__ void stencilq32(int ld, int i, int j, float o1, float
     S.gg = gg;
 }
 
-// the bilinear value of one component from its quad: along r on both rows,
+// the bilinear value of component c from its quad: along r on both rows,
 // then along theta (the rows' axis parities are in the quad)
-__device__ __forceinline__ float gatherq32(const float4 *__restrict__ Q, const Sq32 &S)
+__device__ __forceinline__ float gatherq32(const float4 *__restrict__ Q, const Sq32 &S, int c)
 {
-    const float4 v = __ldg(Q + S.o);
+    const float4 v = __ldg(Q + ((size_t)(unsigned)S.o * 6u + (unsigned)c));  // 32 x 32 -> 64-bit multiply
     const float x = fmaf(S.f, v.y - v.x, v.x), y = fmaf(S.f, v.w - v.z, v.z);
     return fmaf(S.gg, y - x, x);
 }
@@ -208,12 +209,12 @@ __device__ __forceinline__ void gather_fields32(const Push32Args &A, int i, int 
     stencilq32(ld, i, j, o1, o2, false, true, S0h);
     stencilq32(ld, i, j, o1, o2, false, false, S00);
     stencilq32(ld, i, j, o1, o2, true, true, Shh);
-    Dv[0] = gatherq32(A.Q[0], Sh0);
-    Dv[1] = gatherq32(A.Q[1], S0h);
-    Dv[2] = gatherq32(A.Q[2], S00);
-    Bv[0] = gatherq32(A.Q[3], S0h);
-    Bv[1] = gatherq32(A.Q[4], Sh0);
-    Bv[2] = gatherq32(A.Q[5], Shh);
+    Dv[0] = gatherq32(A.Q, Sh0, 0);
+    Dv[1] = gatherq32(A.Q, S0h, 1);
+    Dv[2] = gatherq32(A.Q, S00, 2);
+    Bv[0] = gatherq32(A.Q, S0h, 3);
+    Bv[1] = gatherq32(A.Q, Sh0, 4);
+    Bv[2] = gatherq32(A.Q, Shh, 5);
 }
 
 // generalized Boris step in FP32 with the metric of type M at x^n (the lower
@@ -770,9 +771,10 @@ __global__ void __launch_bounds__(256, GRPIC_PUSH32_MINB) push32_kernel(Push32Ar
     for (int k = 0; k < GRPIC_PUSH32_PPT; ++k) push_slot<PUSHER, IX>(A, p0 + (IX)(k * blockDim.x), nx, permuted);
 }
 
-// The stencil quads of the six field components: for the stencil whose
+// The stencil quads of the six field components, interleaved by point (the
+// components of one stencil point share 96 bytes): for the stencil whose
 // first row is js (-1 .. n_theta - 1) and first column col,
-//   Q_c[(js + 1) ld + col] = (F[r0][col], F[r0][col + 1], F[r1][col], F[r1][col + 1])
+//   Q[6 ((js + 1) ld + col) + c] = (F_c[r0][col], F_c[r0][col + 1], F_c[r1][col], F_c[r1][col + 1])
 // with r0 = js, r1 = js + 1.  The components at half-integer theta (D^theta,
 // odd across the axis; B^r and B^phi, even) have rows 0 .. n_theta - 1: a row
 // beyond them is its mirror across the axis (-1 -> 0, n_theta -> n_theta - 1)
@@ -781,7 +783,7 @@ __global__ void __launch_bounds__(256, GRPIC_PUSH32_MINB) push32_kernel(Push32Ar
 // rounding, so the gathers equal those from the arrays themselves bit for bit.
 struct Quad32Args {
     const float *F[6];
-    float4 *Q[6];
+    float4 *Q;
     int nth, ld;
     // zeroed on the way (the push deposits into J and counts into cnt9):
     // J[c] over the same (nth+1) x ld points, cnt9 (9 x nr x nth) if given
@@ -814,7 +816,7 @@ __global__ void quad32_kernel(Quad32Args A)
             const float *b = A.F[c] + (size_t)r1 * A.ld + col;
             v = make_float4(p0 * a[0], p0 * a[1], p1 * b[0], p1 * b[1]);
         }
-        A.Q[c][o] = v;
+        A.Q[6 * o + c] = v;
     }
     if (A.J[0]) {
         A.J[0][o] = 0.0f;
@@ -837,12 +839,11 @@ cudaError_t launch_quad32(grpic_ctx *ctx, grpic_fields *f, bool zero_j, int32_t 
     for (int c = 0; c < 3; ++c) A.J[c] = zero_j ? (float *)f->J[c] : nullptr;
     A.cnt9 = zero_cnt9;
     A.nr = ctx->g.nr;
-    const size_t per = (size_t)(ctx->g.nth + 1) * (size_t)f->ld;
     for (int c = 0; c < 3; ++c) {
         A.F[c] = (const float *)f->D[c];
         A.F[c + 3] = (const float *)f->B[c];
     }
-    for (int c = 0; c < 6; ++c) A.Q[c] = static_cast<float4 *>(ctx->q32) + c * per;
+    A.Q = static_cast<float4 *>(ctx->q32);
     A.nth = ctx->g.nth;
     A.ld = (int)f->ld;
     const dim3 grid((unsigned)((f->ld + 255) / 256), (unsigned)(ctx->g.nth + 1));
@@ -909,8 +910,7 @@ cudaError_t launch_push32(grpic_ctx *ctx, const grpic_particles *in, grpic_parti
     A.in_u3 = (const float *)in->u3;
     A.in_tag = in->tag;
     if (!ctx->q32 || ctx->fscratch_ld != f->ld) return cudaErrorInvalidValue;  // launch_quad32 comes first
-    for (int c = 0; c < 6; ++c)
-        A.Q[c] = static_cast<const float4 *>(ctx->q32) + c * (size_t)(ctx->g.nth + 1) * (size_t)f->ld;
+    A.Q = static_cast<const float4 *>(ctx->q32);
     A.J0 = (float *)f->J[0];
     A.J1 = (float *)f->J[1];
     A.J2 = (float *)f->J[2];
