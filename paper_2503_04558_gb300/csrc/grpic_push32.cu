@@ -27,6 +27,7 @@
 #include "grpic_window.cuh"
 #include "grpic_vay.cuh"
 
+#include <algorithm>
 #include <cmath>
 
 namespace grpic {
@@ -792,17 +793,19 @@ struct Quad32Args {
     int nr;
 };
 
+// One block row per stencil row js + 1 (blockIdx.y); along x the row's work
+// elements e: quad element 6 col + c (consecutive lanes store consecutive
+// 16-byte quads), the zeroed J entries k ld + col, the zeroed counts d n_r + i.
 __global__ void quad32_kernel(Quad32Args A)
 {
-    const int col = blockIdx.x * blockDim.x + threadIdx.x;
     const int qr = blockIdx.y;  // js + 1
-    if (col >= A.ld || qr > A.nth) return;
-    const int js = qr - 1;
-    const size_t o = (size_t)qr * A.ld + col;
-    const bool last = col + 1 >= A.ld;
-#pragma unroll
-    for (int c = 0; c < 6; ++c) {
-        const bool half_t = c == 1 || c == 3 || c == 5;
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (qr > A.nth) return;
+    const int ld = A.ld;
+    if (e < 6 * ld) {
+        const int col = e / 6, c = e - 6 * col;
+        const int js = qr - 1;
+        const bool half_t = (c & 1) != 0;  // D^theta (1), B^r (3), B^phi (5)
         const float par = c == 1 ? -1.0f : 1.0f;
         int r0 = js, r1 = js + 1;
         float p0 = 1.0f, p1 = 1.0f;
@@ -811,22 +814,25 @@ __global__ void quad32_kernel(Quad32Args A)
             if (r1 > A.nth - 1) { r1 = 2 * A.nth - 1 - r1; p1 = par; }
         }
         float4 v = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-        if (r0 >= 0 && !last) {
-            const float *a = A.F[c] + (size_t)r0 * A.ld + col;
-            const float *b = A.F[c] + (size_t)r1 * A.ld + col;
+        if (r0 >= 0 && col + 1 < ld) {
+            // by selects: a run-time index into the parameter array would
+            // copy the array to local memory in every thread
+            const float *F = c < 3 ? (c == 0 ? A.F[0] : (c == 1 ? A.F[1] : A.F[2]))
+                                   : (c == 3 ? A.F[3] : (c == 4 ? A.F[4] : A.F[5]));
+            const float *a = F + (size_t)r0 * ld + col;
+            const float *b = F + (size_t)r1 * ld + col;
             v = make_float4(p0 * a[0], p0 * a[1], p1 * b[0], p1 * b[1]);
         }
-        A.Q[6 * o + c] = v;
+        A.Q[(size_t)qr * 6 * ld + e] = v;
     }
-    if (A.J[0]) {
-        A.J[0][o] = 0.0f;
-        A.J[1][o] = 0.0f;
-        A.J[2][o] = 0.0f;
+    if (A.J[0] && e < 3 * ld) {
+        const int k = e / ld;
+        float *J = k == 0 ? A.J[0] : (k == 1 ? A.J[1] : A.J[2]);
+        J[(size_t)qr * ld + (e - k * ld)] = 0.0f;
     }
-    if (A.cnt9 && qr < A.nth && col < A.nr) {
-        const size_t ncell = (size_t)A.nr * A.nth, k = (size_t)qr * A.nr + col;
-#pragma unroll
-        for (int d = 0; d < 9; ++d) A.cnt9[d * ncell + k] = 0;
+    if (A.cnt9 && qr < A.nth && e < 9 * A.nr) {
+        const int d = e / A.nr;
+        A.cnt9[(size_t)d * A.nr * A.nth + (size_t)qr * A.nr + (e - d * A.nr)] = 0;
     }
 }
 
@@ -846,7 +852,8 @@ cudaError_t launch_quad32(grpic_ctx *ctx, grpic_fields *f, bool zero_j, int32_t 
     A.Q = static_cast<float4 *>(ctx->q32);
     A.nth = ctx->g.nth;
     A.ld = (int)f->ld;
-    const dim3 grid((unsigned)((f->ld + 255) / 256), (unsigned)(ctx->g.nth + 1));
+    const int64_t w = std::max<int64_t>(6 * f->ld, 9 * (int64_t)ctx->g.nr);  // work elements per row
+    const dim3 grid((unsigned)((w + 255) / 256), (unsigned)(ctx->g.nth + 1));
     quad32_kernel<<<grid, 256, 0, s>>>(A);
     return cudaGetLastError();
 }
