@@ -75,8 +75,8 @@ B1_ALG_B = 2 * 28
 # Vay's update (1024^2 x 64 ppc), the FP64 push with the cubic shape (512^2 x
 # 64 ppc), the FP64 push with photon emission and conversion decisions (512^2
 # x 16 ppc, Wald a = 0.99, B0 = 500)
-VAY32_FP32_FLOP = 653.8
-VAY32_INST = 1116.2
+VAY32_FP32_FLOP = 651.8
+VAY32_INST = 1107.7
 CUBIC64_FP64_FLOP = 1471.4
 RAD64_FP64_FLOP = 1248.5
 VAY_COUNT = "ncu SASS counters, FP32-form push with Vay's update, 1024^2 x 64 ppc"
